@@ -1,0 +1,380 @@
+"""Pins for the oracle's geometry half against what the paper and mathematics fix.
+
+Each test ties an oracle function to something other than itself: the printed DP table and
+its order conditions (Table tab:dp), the printed spherical KS metric (Sec. 2), finite
+differences of the metric, conserved quantities of Kerr geodesics, the Schwarzschild shadow,
+the Kerr photon-ring impact parameters and the Iyer-Hansen deflection integral (Sec. 3.1).
+"""
+import math
+import os
+from fractions import Fraction as F
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle as O
+from paper_2203_15963_gb300 import synth as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "dp_tableau.txt")
+
+
+def _golden_tableau():
+    a = [[F(0)] * 7 for _ in range(7)]
+    c = [F(0)] * 7
+    w = {"b5": [F(0)] * 7, "b4": [F(0)] * 7, "bmid": [F(0)] * 7}
+    for line in open(GOLDEN):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, i, j, num, den = line.split()
+        i, j = int(i), int(j)
+        v = F(int(num), int(den))
+        if name == "a":
+            a[i][j] = v
+        elif name == "c":
+            c[i] = v
+        else:
+            w[name][i] = v
+    return a, c, w
+
+
+def test_tableau_matches_printed_table():
+    a, c, w = _golden_tableau()
+    A, b5, b4, bm, cc = O.dp_tableau()
+    for i in range(7):
+        assert cc[i] == pytest.approx(float(c[i]), abs=1e-16)
+        for j in range(7):
+            assert A[i, j] == pytest.approx(float(a[i][j]), rel=1e-15, abs=1e-16)
+    for name, arr in (("b5", b5), ("b4", b4), ("bmid", bm)):
+        for i in range(7):
+            assert arr[i] == pytest.approx(float(w[name][i]), rel=1e-15, abs=1e-16)
+
+
+def test_printed_tableau_order_conditions_exact():
+    """Exact rational checks: consistency, 5th/4th order, and the midpoint reading."""
+    a, c, w = _golden_tableau()
+    for i in range(7):
+        assert sum(a[i]) == c[i]
+
+    def ac(v):  # (A v)_i
+        return [sum(a[i][j] * v[j] for j in range(7)) for i in range(7)]
+
+    def dot(u, v):
+        return sum(x * y for x, y in zip(u, v))
+
+    one = [F(1)] * 7
+    c2 = [x * x for x in c]
+    c3 = [x ** 3 for x in c]
+    for name, order in (("b5", 5), ("b4", 4)):
+        b = w[name]
+        conds = [(dot(b, one), F(1)), (dot(b, c), F(1, 2)), (dot(b, c2), F(1, 3)),
+                 (dot(b, ac(c)), F(1, 6)), (dot(b, c3), F(1, 4)),
+                 (dot(b, [ci * x for ci, x in zip(c, ac(c))]), F(1, 8)),
+                 (dot(b, ac(c2)), F(1, 12)), (dot(b, ac(ac(c))), F(1, 24))]
+        if order == 5:
+            c4 = [x ** 4 for x in c]
+            conds += [(dot(b, c4), F(1, 5)), (dot(b, ac(c3)), F(1, 20)),
+                      (dot(b, ac(ac(ac(c)))), F(1, 120))]
+        for got, want in conds:
+            assert got == want, (name, got, want)
+    # Printed midpoint weights sum to 1; scaled by h/2 they meet the 4th-order conditions
+    # for y(h/2): sum b = theta, b.c = theta^2/2, b.c^2 = theta^3/3, b.c^3 = theta^4/4,
+    # b.Ac = theta^3/6, b.(c*Ac) = theta^4/8, b.Ac^2 = theta^4/12, b.AAc = theta^4/24.
+    bm = [x / 2 for x in w["bmid"]]
+    th = F(1, 2)
+    assert sum(w["bmid"]) == 1
+    assert dot(bm, one) == th
+    assert dot(bm, c) == th ** 2 / 2
+    assert dot(bm, c2) == th ** 3 / 3
+    assert dot(bm, c3) == th ** 4 / 4
+    assert dot(bm, ac(c)) == th ** 3 / 6
+    assert dot(bm, [ci * x for ci, x in zip(c, ac(c))]) == th ** 4 / 8
+    assert dot(bm, ac(c2)) == th ** 4 / 12
+    assert dot(bm, ac(ac(c))) == th ** 4 / 24
+
+
+def _rand_points(rng, n, rmin=1.6, rmax=60.0):
+    pts = []
+    while len(pts) < n:
+        p = rng.uniform(-rmax, rmax, 3)
+        if rmin < np.linalg.norm(p) < rmax:
+            pts.append(np.array([0.0, *p]))
+    return pts
+
+
+@pytest.mark.parametrize("spin", [0.0, 0.5, 0.94])
+def test_metric_inverse(spin):
+    rng = np.random.default_rng(1)
+    for x in _rand_points(rng, 20):
+        glo, ghi = O.metric_cks(x, 1.0, spin)
+        assert np.allclose(glo @ ghi, np.eye(4), atol=1e-12)
+        assert np.linalg.det(glo) == pytest.approx(-1.0, abs=1e-11)   # sqrt(-g) = 1 in CKS
+
+
+def _jac(r, th, ph, a):
+    """d(x, y, z) / d(r, theta, phi) from the inverse map of Sec. 2."""
+    st, ct, sp, cp = math.sin(th), math.cos(th), math.sin(ph), math.cos(ph)
+    return np.array([[st * cp, ct * (r * cp - a * sp), st * (-r * sp - a * cp)],
+                     [st * sp, ct * (r * sp + a * cp), st * (r * cp - a * sp)],
+                     [ct, -r * st, 0.0]])
+
+
+def _printed_sks_metric(r, th, a, m=1.0):
+    s = math.sin(th)
+    f = 2 * m * r ** 3 / (r ** 4 + a * a * (r * math.cos(th)) ** 2)
+    return np.array([
+        [-(1 - f), f, 0, -a * f * s * s],
+        [f, 1 + f, 0, -a * (1 + f) * s * s],
+        [0, 0, 2 * m * r / f, 0],
+        [-a * f * s * s, -a * (1 + f) * s * s, 0, (r * r + a * a + a * a * f * s * s) * s * s]])
+
+
+@pytest.mark.parametrize("spin", [0.0, 0.7, 0.99])
+def test_cks_metric_maps_to_printed_sks_metric(spin):
+    """Pins l_t = +1 and the spatial l_a against the printed spherical KS metric."""
+    for r, th, ph in [(3.0, 0.4, 0.3), (7.5, 1.9, 4.0), (40.0, 1.2, 2.2), (2.0, 2.8, 5.9)]:
+        x = np.array([0.0, math.sin(th) * (r * math.cos(ph) - spin * math.sin(ph)),
+                      math.sin(th) * (r * math.sin(ph) + spin * math.cos(ph)), r * math.cos(th)])
+        assert O.r_of_x(x, spin) == pytest.approx(r, rel=1e-13)
+        glo, _ = O.metric_cks(x, 1.0, spin)
+        J = np.zeros((4, 4))
+        J[0, 0] = 1.0
+        J[1:, 1:] = _jac(r, th, ph, spin)
+        g_sks = J.T @ glo @ J
+        want = _printed_sks_metric(r, th, spin)
+        assert np.allclose(g_sks, want, rtol=1e-12, atol=1e-12)
+        assert np.allclose(O.metric_sks(r, th, 1.0, spin), want, rtol=1e-13, atol=1e-13)
+
+
+def test_limits_minkowski_and_schwarzschild():
+    x = np.array([0.0, 3.0, -4.0, 12.0])
+    glo, ghi = O.metric_cks(x, 0.0, 0.6)
+    assert np.allclose(glo, np.diag([-1, 1, 1, 1]))
+    glo, _ = O.metric_cks(x, 1.0, 0.6, flat=1)
+    assert np.allclose(glo, np.diag([-1, 1, 1, 1]))
+    # a = 0: g_tt = -(1 - 2M/r), g_ti = 2M x_i / r^2 (Kerr-Schild Schwarzschild)
+    glo, _ = O.metric_cks(x, 1.0, 0.0)
+    r = 13.0
+    assert glo[0, 0] == pytest.approx(-(1 - 2 / r), rel=1e-14)
+    assert np.allclose(glo[0, 1:], 2 * x[1:] / r ** 2, rtol=1e-13)
+
+
+@pytest.mark.parametrize("spin", [0.0, 0.9])
+def test_christoffel_vs_finite_differences(spin):
+    rng = np.random.default_rng(2)
+    for x in _rand_points(rng, 6, rmin=2.5, rmax=20):
+        gam = O.christoffel(x, 1.0, spin)
+        dg = np.zeros((4, 4, 4))
+        for mu in range(1, 4):
+            e = np.zeros(4)
+            h = 1e-5
+            e[mu] = h
+            gp, _ = O.metric_cks(x + e, 1.0, spin)
+            gm, _ = O.metric_cks(x - e, 1.0, spin)
+            g2p, _ = O.metric_cks(x + 2 * e, 1.0, spin)
+            g2m, _ = O.metric_cks(x - 2 * e, 1.0, spin)
+            dg[mu] = (8 * (gp - gm) - (g2p - g2m)) / (12 * h)
+        _, ghi = O.metric_cks(x, 1.0, spin)
+        want = 0.5 * (np.einsum("ad,bdc->abc", ghi, dg) + np.einsum("ad,cdb->abc", ghi, dg)
+                      - np.einsum("ad,dbc->abc", ghi, dg))
+        assert np.allclose(gam, want, atol=1e-9)
+    assert np.allclose(O.christoffel(np.array([0, 3.0, 1.0, 2.0]), 1.0, 0.9, flat=1), 0.0)
+
+
+def test_geodesic_rhs_vs_hamiltonian_finite_differences():
+    rng = np.random.default_rng(3)
+    for x in _rand_points(rng, 6, rmin=2.5, rmax=30):
+        k = np.array([-1.0, *rng.normal(size=3)])
+        y = np.concatenate([x, k])
+        dy = O.geodesic_rhs(y, 1.0, 0.9)
+        _, ghi = O.metric_cks(x, 1.0, 0.9)
+        assert np.allclose(dy[:4], ghi @ k, rtol=1e-14)
+        assert dy[4] == 0.0
+        for mu in range(1, 4):
+            e = np.zeros(4)
+            h = 1e-5
+            e[mu] = h
+            hp = 0.5 * k @ O.metric_cks(x + e, 1.0, 0.9)[1] @ k
+            hm = 0.5 * k @ O.metric_cks(x - e, 1.0, 0.9)[1] @ k
+            assert dy[4 + mu] == pytest.approx(-(hp - hm) / (2 * h), rel=1e-7, abs=1e-10)
+
+
+def test_camera_frame_orthonormal():
+    cam = S.Camera(r=100.0, theta=math.radians(45), n=8, width=24.0)
+    met = S.Metric(spin=0.9)
+    x, k, H, V, n = O.camera_pixel(cam, met, 3, 5)
+    glo, ghi = O.metric_cks(x, 1.0, 0.9)
+    assert k @ ghi @ k == pytest.approx(0.0, abs=1e-13)
+    kup = ghi @ k
+    assert kup[0] > 0.0                                  # future-directed received photon
+    assert H @ glo @ H == pytest.approx(1.0, abs=2e-3)   # pixel metric differs from centre
+    # At the camera centre the frame is exactly orthonormal.
+    th, r = cam.theta, cam.r
+    xc = np.array([0.0, math.sin(th) * r, math.sin(th) * 0.9, r * math.cos(th)])
+    gc, _ = O.metric_cks(xc, 1.0, 0.9)
+    assert H @ gc @ H == pytest.approx(1.0, abs=1e-12)
+    assert V @ gc @ V == pytest.approx(1.0, abs=1e-12)
+    assert H @ gc @ V == pytest.approx(0.0, abs=1e-12)
+    assert n == pytest.approx(1.0 / -k[0], rel=1e-15)
+
+
+def test_flat_camera_plane_and_straight_rays():
+    cam = S.Camera(r=200.0, theta=math.radians(60), n=6, width=30.0)
+    met = S.Metric(spin=0.0, flat=1)
+    xs, ks = [], []
+    for j in range(6):
+        for i in range(6):
+            x, k, H, V, _ = O.camera_pixel(cam, met, i, j)
+            xs.append(x[1:])
+            ks.append(k)
+    xs = np.array(xs)
+    ks = np.array(ks)
+    # all momenta equal, pixel plane perpendicular to k with spacing w/N
+    assert np.allclose(ks, ks[0], atol=1e-14)
+    d = xs - xs.mean(axis=0)
+    assert np.allclose(d @ ks[0, 1:], 0.0, atol=1e-11)
+    assert np.linalg.norm(xs[1] - xs[0]) == pytest.approx(5.0, rel=1e-13)
+    # straight rays: the end point lies on the line x0 + s k^a
+    y0 = np.concatenate([[0.0, *xs[7]], ks[7]])
+    res = O.geodesic(met, cam.r, y0)
+    assert res["status"] == 2
+    disp = res["end"][1:4] - y0[1:4]
+    kup = np.array([1, 1, 1]) * ks[7, 1:]
+    cross = np.cross(disp, kup)
+    assert np.linalg.norm(cross) <= 1e-10 * np.linalg.norm(disp)
+    assert res["end"][4:] == pytest.approx(y0[4:], abs=0)
+
+
+def _carter(y, a):
+    """L_z and Carter constant from a CKS state (test's own coordinate algebra)."""
+    x = y[:4]
+    k = y[4:]
+    r = O.r_of_x(x, a)
+    th = math.acos(x[3] / r)
+    ph = math.atan2(x[2], x[1]) - math.atan(a / r)
+    J = _jac(r, th, ph, a)           # d(x,y,z)/d(r,th,ph)
+    k_sks = J.T @ k[1:]              # covariant k_r, k_th, k_ph
+    lz = k_sks[2]
+    q = k_sks[1] ** 2 + math.cos(th) ** 2 * (-a * a * k[0] ** 2 + lz ** 2 / math.sin(th) ** 2)
+    return lz, q
+
+
+@pytest.mark.parametrize("pix", [(3, 4), (12, 9), (7, 14)])
+def test_geodesic_conservation_kerr(pix):
+    cam = S.Camera(r=1000.0, theta=math.radians(60), n=16, width=30.0)
+    met = S.Metric(spin=0.9)
+    x, k, _, _, _ = O.camera_pixel(cam, met, *pix)
+    y0 = np.concatenate([x, k])
+    res = O.geodesic(met, cam.r, y0, max_path=5000)
+    path = res["path"]
+    lz0, q0 = _carter(y0, 0.9)
+    for y in path:
+        _, ghi = O.metric_cks(y[:4], 1.0, 0.9)
+        kk = y[4:]
+        assert abs(0.5 * kk @ ghi @ kk) < 1e-7
+        assert y[4] == y0[4]                                  # k_t exactly conserved
+        lz, q = _carter(y, 0.9)
+        assert lz == pytest.approx(lz0, abs=1e-6)
+        assert q == pytest.approx(q0, rel=1e-6, abs=1e-6)
+    assert lz0 == pytest.approx(y0[1] * y0[6] - y0[2] * y0[5], rel=1e-12)
+
+
+def _ray_from_offset(y_off, spin, r0=1000.0):
+    """Equatorial ray received at (r0, 0, 0) moving along +x, offset by y_off (test's own set-up)."""
+    x = np.array([0.0, r0, y_off, 0.0])
+    glo, _ = O.metric_cks(x, 1.0, spin)
+    ka = np.array([1.0, 0.0, 0.0])
+    A, B, Cc = glo[0, 0], glo[0, 1:] @ ka, ka @ glo[1:, 1:] @ ka
+    kt = (-B - math.sqrt(B * B - A * Cc)) / A
+    kup = np.array([kt, *ka])
+    return np.concatenate([x, glo @ kup])
+
+
+def _impact(y):
+    return -(y[1] * y[6] - y[2] * y[5]) / y[4]
+
+
+def _offset_for_impact(b, spin):
+    """Offset whose ray has impact parameter b (b decreases as the offset grows)."""
+    lo, hi = -b - 2.0, -b + 2.0
+    assert _impact(_ray_from_offset(lo, spin)) > b > _impact(_ray_from_offset(hi, spin))
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if _impact(_ray_from_offset(mid, spin)) > b:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_schwarzschild_shadow_sqrt27():
+    met = S.Metric(spin=0.0)
+    bc = math.sqrt(27.0)
+    for fac, want in ((1 - 1e-3, 1), (1 + 1e-3, 2), (0.5, 1), (2.0, 2)):
+        y0 = _ray_from_offset(_offset_for_impact(fac * bc, 0.0), 0.0)
+        assert O.geodesic(met, 1000.0, y0)["status"] == want, fac
+
+
+def test_kerr_photon_ring_critical_impact_parameters():
+    a = 0.9
+    b_plus = -a + 6 * math.cos(math.acos(-a) / 3)
+    b_minus = -a - 6 * math.cos(math.acos(a) / 3)
+    met = S.Metric(spin=a)
+    for b, want in ((b_plus * (1 + 2e-3), 2), (b_plus * (1 - 2e-3), 1),
+                    (b_minus * (1 + 2e-3), 2), (b_minus * (1 - 2e-3), 1)):
+        y0 = _ray_from_offset(_offset_for_impact(b, a), a)
+        assert O.geodesic(met, 1000.0, y0)["status"] == want, b
+
+
+def _iyer_hansen(b, a, u_src, u_cam):
+    """Finite-distance deflection (Eq. deflection) by quadrature with u = u0 - t^2."""
+    ab = a / b
+    r0 = (2 * abs(b) / math.sqrt(3)) * math.sqrt(1 - ab * ab) * math.cos(
+        math.acos(-3 * math.sqrt(3) * (1 - ab) ** 2 / (abs(b) * (1 - ab * ab) ** 1.5)) / 3)
+    u0 = 1.0 / r0
+
+    def dphi(u):
+        num = 1 - 2 * (1 - ab) * u
+        den = 1 - 2 * u + a * a * u * u
+        inner = 2 * (1 - ab) ** 2 * u ** 3 - (1 - ab * ab) * u * u + 1 / (b * b)
+        return num / den / math.sqrt(inner)
+
+    def part(u1):
+        tmax = math.sqrt(u0 - u1)
+        val, _ = integrate.quad(lambda t: dphi(u0 - t * t) * 2 * t, 0.0, tmax,
+                                epsabs=1e-13, epsrel=1e-13, limit=400)
+        return val
+
+    return part(u_src) + part(u_cam)
+
+
+def test_iyer_hansen_deflection():
+    """Sec. 3.1: a = 0.9, camera at r = 1000, 51 pixels over w = 36, DP tol 1e-8."""
+    a = 0.9
+    met = S.Metric(spin=a)
+    b_plus = -a + 6 * math.cos(math.acos(-a) / 3)
+    b_minus = -a - 6 * math.cos(math.acos(a) / 3)
+    rp, rm = 1 + math.sqrt(1 - a * a), 1 - math.sqrt(1 - a * a)
+
+    def ks_minus_bl(r):   # int a / Delta dr
+        return a / (rp - rm) * math.log((r - rp) / (r - rm))
+
+    errs = []
+    for i in range(51):
+        off = (i - 51 / 2 + 0.5) * 36.0 / 51   # pixel centres of Sec. 2.1
+        y0 = _ray_from_offset(off, a)
+        b = _impact(y0)
+        if b_minus <= b <= b_plus or abs(b) < 1e-9:
+            continue
+        res = O.geodesic(met, 1000.0, y0, max_path=20000)
+        assert res["status"] == 2
+        path = np.vstack([y0, res["path"]])
+        rs = np.array([O.r_of_x(y, a) for y in path])
+        phis = np.unwrap([math.atan2(y[2], y[1]) - math.atan(a / r) for y, r in zip(path, rs)])
+        d_bl = (phis[-1] - phis[0]) - (ks_minus_bl(rs[-1]) - ks_minus_bl(rs[0]))
+        want = _iyer_hansen(b, a, 1 / rs[-1], 1 / rs[0])
+        got = abs(d_bl)
+        errs.append(abs(got - want))
+    assert len(errs) == 37
+    print("max deflection error", max(errs))
+    assert max(errs) < 1e-5, max(errs)

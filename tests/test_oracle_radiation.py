@@ -1,0 +1,302 @@
+"""Pins for the oracle's radiation half (Secs. 2.3-2.5) against closed forms and libraries.
+
+- Bessel K_n: scipy.special.kve.
+- Constant-coefficient Stokes step: scipy.linalg.expm of the augmented matrix; the
+  unpolarized exact solution (Eq. unpolarized); Faraday rotation / conversion closed forms.
+- Coefficients: Kirchhoff's law, parity in cos(theta_B), quadrature of the exact thermal
+  synchrotron emissivity (total and linear), high-frequency limits of the rotativities.
+- Sampling: trilinear interpolation reproduces functions linear in (ln r, theta, phi).
+- Plasma: hand values at a uniform state; u.u = -1, b.u = 0.
+- Coherency transport: equals the outer product of parallel-transported vectors.
+- Whole image: 90-degree symmetry of a face-on, non-spinning, axisymmetric torus.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, linalg, special
+
+import oracle as O
+from paper_2203_15963_gb300 import synth as S
+
+# Test's own CGS constants
+C = 2.99792458e10
+E = 4.80320471e-10
+ME = 9.1093837015e-28
+MP = 1.67262192369e-24
+H = 6.62607015e-27
+
+
+@pytest.mark.parametrize("nu", [0, 1, 2])
+def test_bessel_vs_scipy(nu):
+    for x in np.logspace(-2, 2, 25):
+        assert O.bessel_kx(nu, x) == pytest.approx(special.kve(nu, x), rel=1e-12)
+
+
+def _mueller(c):
+    eI, eQ, eV, aI, aQ, aV, rQ, rV = c
+    M = np.array([[aI, aQ, 0, aV], [aQ, aI, rV, 0], [0, -rV, aI, rQ], [aV, 0, -rQ, aI]])
+    J = np.array([eI, eQ, 0, eV])
+    return M, J
+
+
+def _expm_step(c, s0, dl):
+    M, J = _mueller(c)
+    B = np.zeros((5, 5))
+    B[:4, :4] = -M * dl
+    B[:4, 4] = J * dl
+    Ex = linalg.expm(B)
+    return Ex[:4, :4] @ s0 + Ex[:4, 4]
+
+
+def test_stokes_step_vs_expm_random():
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        aI = 10 ** rng.uniform(-4, 0.5)
+        aQ, aV = aI * rng.uniform(-0.7, 0.7), aI * rng.uniform(-0.3, 0.3)
+        rQ, rV = 10 ** rng.uniform(-4, 1) * rng.choice([-1, 1]), 10 ** rng.uniform(-4, 2) * rng.choice([-1, 1])
+        eI = 10 ** rng.uniform(-3, 0)
+        c = [eI, eI * rng.uniform(-0.7, 0.7), eI * rng.uniform(-0.3, 0.3), aI, aQ, aV, rQ, rV]
+        s0 = rng.normal(size=4)
+        dl = 10 ** rng.uniform(-2, 1)
+        got = O.stokes_step(c, s0, dl)
+        want = _expm_step(c, s0, dl)
+        assert np.allclose(got, want, rtol=1e-10, atol=1e-12 * (1 + np.abs(want).max()))
+
+
+def test_stokes_step_unpolarized_exact_solution():
+    """Eq. (unpolarized): I+ = exp(-dtau)(I- + expm1(dtau) j/alpha), I- + j dl if alpha = 0."""
+    for j, a, dl, i0 in [(2.0, 0.3, 1.7, 0.5), (1e-3, 4.0, 0.2, 0.0), (0.7, 0.0, 3.0, 1.0)]:
+        got = O.stokes_step([j, 0, 0, a, 0, 0, 0, 0], [i0, 0, 0, 0], dl)
+        if a > 0:
+            want = math.exp(-a * dl) * (i0 + math.expm1(a * dl) * j / a)
+        else:
+            want = i0 + j * dl
+        assert got[0] == pytest.approx(want, rel=1e-13)
+        assert np.allclose(got[1:], 0.0)
+    # optically thick segment: Delta tau >= 100 gives j / alpha
+    got = O.stokes_step([3.0, 0, 0, 50.0, 0, 0, 0, 0], [7.0, 0, 0, 0], 2.5)
+    assert got[0] == pytest.approx(3.0 / 50.0, rel=1e-14)
+
+
+def test_stokes_step_faraday_rotation_and_conversion():
+    q0, u0, v0 = 0.3, -0.2, 0.1
+    for rv, dl in [(0.7, 2.0), (25.0, 3.1)]:
+        got = O.stokes_step([0, 0, 0, 0, 0, 0, 0, rv], [1.0, q0, u0, v0], dl)
+        ang = rv * dl
+        assert got[1] == pytest.approx(q0 * math.cos(ang) - u0 * math.sin(ang), abs=1e-12)
+        assert got[2] == pytest.approx(u0 * math.cos(ang) + q0 * math.sin(ang), abs=1e-12)
+        assert got[0] == pytest.approx(1.0) and got[3] == pytest.approx(v0)
+    rq, dl = 1.3, 0.9
+    got = O.stokes_step([0, 0, 0, 0, 0, 0, rq, 0], [1.0, q0, u0, v0], dl)
+    ang = rq * dl
+    assert got[2] == pytest.approx(u0 * math.cos(ang) - v0 * math.sin(ang), abs=1e-12)
+    assert got[3] == pytest.approx(v0 * math.cos(ang) + u0 * math.sin(ang), abs=1e-12)
+    assert got[1] == pytest.approx(q0)
+
+
+def test_stokes_step_uniform_polarized_slab_steady_state():
+    """Long uniform slab: S tends to M^-1 J, and the degree of polarization stays <= 1."""
+    c = [1.0, 0.6, 0.1, 0.8, 0.45, 0.07, 0.3, 2.0]
+    M, J = _mueller(c)
+    s = np.zeros(4)
+    for _ in range(400):
+        s = O.stokes_step(c, s, 0.25)
+        assert math.sqrt(s[1] ** 2 + s[2] ** 2 + s[3] ** 2) <= s[0] * (1 + 1e-12)
+    assert np.allclose(s, np.linalg.solve(M, J), rtol=1e-9)
+
+
+def _bnu(nu, te):
+    return 2 * H * nu ** 3 / C ** 2 / math.expm1(H * nu / (te * ME * C ** 2))
+
+
+def test_coefficients_kirchhoff_and_parity():
+    for ne, te, b, nu, ct in [(1e6, 5.0, 30.0, 230e9, 0.3), (3e5, 40.0, 5.0, 86e9, -0.8),
+                              (1e7, 1.5, 100.0, 690e9, 0.05)]:
+        c = O.coefficients(ne, te, b, nu, ct)
+        bn = _bnu(nu, te)
+        for s in range(3):
+            assert c[3 + s] == pytest.approx(c[s] / bn, rel=1e-13)
+        cm = O.coefficients(ne, te, b, nu, -ct)
+        assert np.allclose(cm[[0, 1, 3, 4, 6]], c[[0, 1, 3, 4, 6]], rtol=1e-13)
+        assert np.allclose(cm[[2, 5, 7]], -c[[2, 5, 7]], rtol=1e-13)
+        assert c[0] > 0 and c[1] > 0 and abs(c[1]) < c[0] and abs(c[2]) < c[0]
+    # no emission along the field
+    c = O.coefficients(1e6, 5.0, 30.0, 230e9, 1.0)
+    assert np.all(c[:7] == 0.0) and c[7] > 0
+
+
+def _synchrotron_F(x):
+    val, _ = integrate.quad(lambda t: special.kv(5.0 / 3.0, t), x, np.inf, limit=200)
+    return x * val
+
+
+def _exact_thermal(ne, te, b, nu, ct, which):
+    """Exact thermal emissivity: int N(gamma) P_nu(gamma) / 4 pi with the synchrotron kernel."""
+    st = math.sqrt(1 - ct * ct)
+    nub = E * b / (2 * math.pi * ME * C)
+    pre = math.sqrt(3) * E ** 3 * b * st / (4 * math.pi * ME * C ** 2)
+    k2 = special.kv(2, 1 / te)
+
+    def kern(g):
+        xc = nu / (1.5 * g * g * nub * st)
+        if which == "I":
+            k = _synchrotron_F(xc)
+        else:
+            k = xc * special.kv(2.0 / 3.0, xc)
+        beta = math.sqrt(1 - 1 / (g * g))
+        return ne * g * g * beta * math.exp(-g / te) / (te * k2) * k
+
+    gmax = 60 * te + 10
+    val, _ = integrate.quad(kern, 1.0 + 1e-9, gmax, limit=400, epsrel=1e-9)
+    return pre * val
+
+
+@pytest.mark.parametrize("te,x", [(10.0, 3.0), (10.0, 30.0), (30.0, 300.0), (5.0, 10.0)])
+def test_emissivity_fits_vs_exact_quadrature(te, x):
+    ne, b, ct = 1e6, 20.0, 0.5
+    st = math.sqrt(1 - ct * ct)
+    nub = E * b / (2 * math.pi * ME * C)
+    nu = x * 1.5 * nub * st * te * te
+    c = O.coefficients(ne, te, b, nu, ct)
+    ji = _exact_thermal(ne, te, b, nu, ct, "I")
+    jq = _exact_thermal(ne, te, b, nu, ct, "Q")
+    assert c[0] == pytest.approx(ji, rel=0.06)
+    assert c[1] == pytest.approx(jq, rel=0.08)
+
+
+def test_rotativities_high_frequency_limit():
+    ne, te, b, ct = 1e6, 8.0, 20.0, 0.6
+    st = math.sqrt(1 - ct * ct)
+    nub = E * b / (2 * math.pi * ME * C)
+    nu = 1e13 * nub
+    c = O.coefficients(ne, te, b, nu, ct)
+    k0, k1, k2 = (special.kv(n, 1 / te) for n in (0, 1, 2))
+    rv = 2 * ne * E ** 2 * nub * ct / (ME * C * nu ** 2) * k0 / k2
+    rq = ne * E ** 2 * nub ** 2 * st ** 2 / (ME * C * nu ** 3) * (k1 / k2 + 6 * te)
+    assert c[7] == pytest.approx(rv, rel=1e-4)
+    assert c[6] == pytest.approx(rq, rel=1e-3)
+    # cold limit of the Faraday rotation coefficient: e^3 n B cos / (pi m^2 c^2 nu^2)
+    c = O.coefficients(ne, 0.06, b, nu, ct)
+    cold = E ** 3 * ne * b * ct / (math.pi * ME ** 2 * C ** 2 * nu ** 2)
+    assert c[7] == pytest.approx(cold, rel=0.1)
+
+
+def _uniform_grid(vals, gp):
+    prim = np.empty((8, gp.n_phi, gp.n_theta, gp.n_r), dtype=np.float32)
+    for v in range(8):
+        prim[v] = vals[v]
+    return prim
+
+
+def test_trilinear_reproduces_linear_functions():
+    gp = S.GridParams(n_r=12, n_theta=10, n_phi=16)
+    rc, tc, pc = S.r_centres(gp), S.theta_centres(gp), S.phi_centres(gp)
+    a = 0.7
+    prim = np.zeros((8, gp.n_phi, gp.n_theta, gp.n_r), dtype=np.float32)
+    P, T, R = np.meshgrid(pc, tc, rc, indexing="ij")
+    prim[0] = 1.0 + 0.5 * np.log(R) - 0.3 * T + 0.2 * P
+    prim[1] = 2.0 * np.log(R)
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        r = math.exp(rng.uniform(math.log(rc[0]), math.log(rc[-1])))
+        th = rng.uniform(tc[0], tc[-1])
+        ph = rng.uniform(pc[0], pc[-1])
+        x = np.array([0.0, math.sin(th) * (r * math.cos(ph) - a * math.sin(ph)),
+                      math.sin(th) * (r * math.sin(ph) + a * math.cos(ph)), r * math.cos(th)])
+        ok, out = O.sample_grid(gp, prim, a, x)
+        assert ok
+        assert out[0] == pytest.approx(1.0 + 0.5 * math.log(r) - 0.3 * th + 0.2 * ph, rel=2e-6)
+        assert out[1] == pytest.approx(2.0 * math.log(r), rel=2e-6)
+    ok, _ = O.sample_grid(gp, prim, a, np.array([0.0, 0.0, 0.0, 60.0]))
+    assert not ok
+
+
+def test_plasma_hand_values():
+    gp = S.GridParams(n_r=4, n_theta=4, n_phi=4, r_high=1.0, r_low=1.0)
+    rho, ug = float(np.float32(0.8)), float(np.float32(0.05))
+    br, bth = float(np.float32(0.02)), float(np.float32(0.001))
+    prim = _uniform_grid([rho, ug, 0.0, 0.0, 0.0, br, bth, 0.0], gp)
+    met = S.Metric(spin=0.5)
+    r, th, ph = 10.0, 1.1, 0.4
+    a = 0.5
+    x = np.array([0.0, math.sin(th) * (r * math.cos(ph) - a * math.sin(ph)),
+                  math.sin(th) * (r * math.sin(ph) + a * math.cos(ph)), r * math.cos(th)])
+    ok, p = O.plasma(gp, prim, met, x)
+    assert ok
+    glo, _ = O.metric_cks(x, 1.0, a)
+    u, b = p["u"], p["b"]
+    assert u @ glo @ u == pytest.approx(-1.0, abs=1e-12)
+    assert b @ glo @ u == pytest.approx(0.0, abs=1e-12)
+    pres = (13 / 9 - 1) * ug
+    assert p["theta_e"] == pytest.approx(0.5 * MP / ME * pres / rho, rel=1e-12)   # T_i = T_e
+    assert p["ne"] == pytest.approx(rho * 1e-17 / MP, rel=1e-12)
+    # normal observer: u_i = 0 so b^t = 0, b^i = B^i / u^t = alpha B^i, alpha^2 = 1 / (1 + f)
+    g = O.metric_sks(r, th, 1.0, a)
+    f = 2 * r / (r * r + a * a * math.cos(th) ** 2)
+    bsq = (g[1, 1] * br * br + g[2, 2] * bth * bth) / (1 + f)
+    assert p["b_gauss"] == pytest.approx(math.sqrt(bsq) * C * math.sqrt(4 * math.pi * 1e-17), rel=1e-10)
+
+
+def test_coherency_transport_is_outer_product_of_parallel_transport():
+    """Eq. polarized_n read as parallel transport: N = e e^T stays e(l) e(l)^T."""
+    met = S.Metric(spin=0.9)
+    a = 0.9
+    x = np.array([0.0, 12.0, 3.0, 5.0])
+    glo, ghi = O.metric_cks(x, 1.0, a)
+    ka = np.array([-0.8, 0.3, 0.1])
+    A, B, Cc = glo[0, 0], glo[0, 1:] @ ka, ka @ glo[1:, 1:] @ ka
+    kt = (-B - math.sqrt(B * B - A * Cc)) / A
+    kup = np.array([kt, *ka])
+    y = np.concatenate([x, glo @ kup])
+    # a unit spacelike e orthogonal to k
+    e = np.array([0.0, 0.0, 1.0, 0.0])
+    e = e - (e @ glo @ kup) / (kup @ glo @ np.array([1.0, 0, 0, 0])) * np.array([1.0, 0, 0, 0])
+    e /= math.sqrt(e @ glo @ e)
+    nre = np.outer(e, e)
+    nim = np.zeros((4, 4))
+
+    def rhs(state):
+        yy, ee = state[:8], state[8:]
+        dy = O.geodesic_rhs(yy, 1.0, a)
+        gam = O.christoffel(yy[:4], 1.0, a)
+        de = -np.einsum("abc,b,c->a", gam, dy[:4], ee)
+        return np.concatenate([dy, de])
+
+    st = np.concatenate([y, e])
+    h = 0.05
+    for _ in range(200):
+        k1 = rhs(st)
+        k2 = rhs(st + 0.5 * h * k1)
+        k3 = rhs(st + 0.5 * h * k2)
+        k4 = rhs(st + h * k3)
+        mid = st + 0.5 * h * k1 + 0.0
+        ymid = (st + 0.5 * h * (k1 + k2) / 2)[:8]   # second-order midpoint state
+        nre, nim = O.transport_step(met, st[:4], st[4:8], ymid[:4], ymid[4:8], h, nre, nim)
+        st = st + h * (k1 + 2 * k2 + 2 * k3 + k4) / 6
+        del mid
+    ee = st[8:]
+    want = np.outer(ee, ee)
+    assert np.allclose(nre, want, atol=2e-5)
+    g_end, _ = O.metric_cks(st[:4], 1.0, a)
+    assert np.sum(g_end * nre) == pytest.approx(1.0, abs=2e-5)
+
+
+def test_face_on_nonspinning_image_symmetry():
+    gp = S.GridParams(n_r=48, n_theta=32, n_phi=32)
+    prim = S.make_torus(gp, 0.0, seed=1, noise=0.0)
+    cam = S.Camera(theta=0.0, n=16, width=40.0)
+    met = S.Metric(spin=0.0)
+    res = O.trace(cam, met, gp, prim, 230e9)
+    img = res["stokes"].reshape(16, 16, 4)       # [j][i][s]
+    n = 16
+    rot = np.empty_like(img)
+    for j in range(n):
+        for i in range(n):
+            rot[j, i] = img[i, n - 1 - j]
+    scale = np.abs(img[..., 0]).max()
+    assert scale > 0
+    assert np.abs(img[..., 1:3]).max() > 1e-3 * scale         # polarization is present
+    assert np.allclose(rot[..., 0], img[..., 0], atol=1e-6 * scale)
+    assert np.allclose(rot[..., 3], img[..., 3], atol=1e-6 * scale)
+    assert np.allclose(rot[..., 1:3], -img[..., 1:3], atol=1e-6 * scale)
