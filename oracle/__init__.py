@@ -88,6 +88,12 @@ def lib():
         L.ora_coefficients.argtypes = [C.c_double] * 5 + [_D]
         L.ora_stokes_step.argtypes = [_D, _D, C.c_double, _D]
         L.ora_transport_step.argtypes = [C.POINTER(Metric), _D, _D, _D, _D, C.c_double, _D, _D]
+        L.ora_ray_samples.argtypes = [C.POINTER(Metric), C.POINTER(Grid), C.c_double, _D,
+                                      C.c_int64, _D]
+        L.ora_ray_samples.restype = C.c_int64
+        L.ora_fluid_frame.argtypes = [_D] * 6
+        L.ora_n_to_s.argtypes = [_D] * 6
+        L.ora_s_to_n.argtypes = [_D] * 5
         L.ora_trace.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Grid),
                                 C.c_double, C.c_int64, _I32, C.c_int32, _D, _I32, _I64, _I64,
                                 _I64, _D]
@@ -222,6 +228,37 @@ def transport_step(met, x0, k0, x1, k1, h, n_re, n_im):
     nre = np.ascontiguousarray(n_re, dtype=np.float64).reshape(16).copy()
     nim = np.ascontiguousarray(n_im, dtype=np.float64).reshape(16).copy()
     lib().ora_transport_step(C.byref(ms), *[_p(v) for v in a], h, _p(nre), _p(nim))
+    return nre.reshape(4, 4), nim.reshape(4, 4)
+
+
+def ray_samples(met, gp, prim, r_cam, y0, max_out=100000):
+    """Samples of one ray, camera side first: dict of x, k, node_x, node_k, dl arrays."""
+    ms, gs = metric_struct(met), grid_struct(gp, prim)
+    y0 = np.ascontiguousarray(y0, dtype=np.float64)
+    out = _f64(17 * max_out)
+    n = lib().ora_ray_samples(C.byref(ms), C.byref(gs), r_cam, _p(y0), max_out, _p(out))
+    o = out[: 17 * min(n, max_out)].reshape(-1, 17)
+    return dict(x=o[:, 0:4], k=o[:, 4:8], node_x=o[:, 8:12], node_k=o[:, 12:16], dl=o[:, 16])
+
+
+def fluid_frame(glo, u, kup, b):
+    arr = [np.ascontiguousarray(v, dtype=np.float64).reshape(-1) for v in (glo, u, kup, b)]
+    e1, e2 = _f64(4), _f64(4)
+    lib().ora_fluid_frame(*[_p(v) for v in arr], _p(e1), _p(e2))
+    return e1, e2
+
+
+def n_to_s(glo, e1, e2, n_re, n_im):
+    arr = [np.ascontiguousarray(v, dtype=np.float64).reshape(-1) for v in (glo, e1, e2, n_re, n_im)]
+    s = _f64(4)
+    lib().ora_n_to_s(*[_p(v) for v in arr], _p(s))
+    return s
+
+
+def s_to_n(e1, e2, s):
+    arr = [np.ascontiguousarray(v, dtype=np.float64).reshape(-1) for v in (e1, e2, s)]
+    nre, nim = _f64(16), _f64(16)
+    lib().ora_s_to_n(*[_p(v) for v in arr], _p(nre), _p(nim))
     return nre.reshape(4, 4), nim.reshape(4, 4)
 
 

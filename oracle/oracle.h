@@ -96,6 +96,18 @@ void ora_transport_step(const ora_metric* met, const double x0[4], const double 
                         const double x1[4], const double k1[4], double h,
                         double n_re[16], double n_im[16]);
 
+/* samples of one ray (camera-side first): [n][17] = x[4], k[4], node x[4], node k[4], dl;
+ * returns the sample count (only the first max_out are written) */
+int64_t ora_ray_samples(const ora_metric* met, const ora_grid* grid, double r_cam,
+                        const double y0[8], int64_t max_out, double* out);
+/* fluid-frame polarization basis and the Stokes <-> coherency maps (Sec. 2.3.2) */
+void ora_fluid_frame(const double glo[16], const double u[4], const double kup[4],
+                     const double b[4], double e1[4], double e2[4]);
+void ora_n_to_s(const double glo[16], const double e1[4], const double e2[4],
+                const double n_re[16], const double n_im[16], double s[4]);
+void ora_s_to_n(const double e1[4], const double e2[4], const double s[4], double n_re[16],
+                double n_im[16]);
+
 /* ---- whole path ----
  * pix: flat pixel indices (j * n + i); out_stokes [npix][4] (I, Q, U, V in erg/s/cm^2/sr/Hz);
  * out_end [npix][8] end state; counters per pixel. nthreads <= 0 means all hardware threads. */

@@ -469,7 +469,8 @@ void s_to_n(const double e1[4], const double e2[4], const double s[4], double nr
 
 // ---------------------------------------------------------------------------------------
 // Samples along one geodesic (Sec. 2.2): each accepted step contributes its midpoint, or,
-// when its proper length exceeds ds_max inside the grid, n = ceil(ds / ds_max) equal
+// when its proper length (evaluated at the midpoint) exceeds ds_max and the step reaches
+// into the grid (start, midpoint or end inside r_max), n = ceil(ds / ds_max) equal
 // sub-segments sampled at their centres from the quartic through y0, y1, h f0, h f1, y_mid.
 // Each sample carries its affine length and the node on its camera side.
 // ---------------------------------------------------------------------------------------
@@ -513,7 +514,9 @@ static void make_samples(const ora_metric* met, const ora_grid* gr, const std::v
                          std::vector<Sample>& out) {
     for (const Step& s : steps) {
         int nsub = 1;
-        double rm = r_of_x(s.ym, met->spin);
+        // Subdivide steps that reach into the grid: start, midpoint or end inside r_max.
+        double rm = std::fmin(r_of_x(s.ym, met->spin),
+                              std::fmin(r_of_x(s.y0, met->spin), r_of_x(s.y1, met->spin)));
         if (rm < gr->r_max) {
             double ds = std::fabs(s.h) * proper_length_rate(met, s.ym);
             if (ds > met->ds_max) nsub = (int)std::ceil(ds / met->ds_max);
@@ -641,6 +644,41 @@ void ora_transport_step(const ora_metric* met, const double x0[4], const double 
                         const double x1[4], const double k1[4], double h, double n_re[16],
                         double n_im[16]) {
     ora::transport_step(met, x0, k0, x1, k1, h, n_re, n_im);
+}
+
+int64_t ora_ray_samples(const ora_metric* met, const ora_grid* grid, double r_cam,
+                        const double y0[8], int64_t max_out, double* out) {
+    std::vector<ora::Step> steps;
+    double yf[8];
+    int64_t att, acc;
+    ora::integrate(met, r_cam, y0, &steps, yf, &att, &acc, nullptr);
+    std::vector<ora::Sample> smp;
+    ora::make_samples(met, grid, steps, smp);
+    int64_t n = (int64_t)smp.size();
+    for (int64_t q = 0; q < n && q < max_out; ++q) {
+        double* o = out + 17 * q;
+        for (int c = 0; c < 4; ++c) {
+            o[c] = smp[q].x[c]; o[4 + c] = smp[q].k[c];
+            o[8 + c] = smp[q].xn[c]; o[12 + c] = smp[q].kn[c];
+        }
+        o[16] = smp[q].dl;
+    }
+    return n;
+}
+
+void ora_fluid_frame(const double glo[16], const double u[4], const double kup[4],
+                     const double b[4], double e1[4], double e2[4]) {
+    ora::tetrad(glo, u, kup, b, e1, e2);
+}
+
+void ora_n_to_s(const double glo[16], const double e1[4], const double e2[4],
+                const double n_re[16], const double n_im[16], double s[4]) {
+    ora::n_to_s(glo, e1, e2, n_re, n_im, s);
+}
+
+void ora_s_to_n(const double e1[4], const double e2[4], const double s[4], double n_re[16],
+                double n_im[16]) {
+    ora::s_to_n(e1, e2, s, n_re, n_im);
 }
 
 void ora_trace(const ora_camera* cam, const ora_metric* met, const ora_grid* grid, double freq,

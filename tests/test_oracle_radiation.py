@@ -116,10 +116,10 @@ def test_coefficients_kirchhoff_and_parity():
         c = O.coefficients(ne, te, b, nu, ct)
         bn = _bnu(nu, te)
         for s in range(3):
-            assert c[3 + s] == pytest.approx(c[s] / bn, rel=1e-13)
+            assert c[3 + s] == pytest.approx(c[s] / bn, rel=1e-13, abs=0)
         cm = O.coefficients(ne, te, b, nu, -ct)
-        assert np.allclose(cm[[0, 1, 3, 4, 6]], c[[0, 1, 3, 4, 6]], rtol=1e-13)
-        assert np.allclose(cm[[2, 5, 7]], -c[[2, 5, 7]], rtol=1e-13)
+        assert np.allclose(cm[[0, 1, 3, 4, 6]], c[[0, 1, 3, 4, 6]], rtol=1e-13, atol=0)
+        assert np.allclose(cm[[2, 5, 7]], -c[[2, 5, 7]], rtol=1e-13, atol=0)
         assert c[0] > 0 and c[1] > 0 and abs(c[1]) < c[0] and abs(c[2]) < c[0]
     # no emission along the field
     c = O.coefficients(1e6, 5.0, 30.0, 230e9, 1.0)
@@ -161,8 +161,8 @@ def test_emissivity_fits_vs_exact_quadrature(te, x):
     c = O.coefficients(ne, te, b, nu, ct)
     ji = _exact_thermal(ne, te, b, nu, ct, "I")
     jq = _exact_thermal(ne, te, b, nu, ct, "Q")
-    assert c[0] == pytest.approx(ji, rel=0.06)
-    assert c[1] == pytest.approx(jq, rel=0.08)
+    assert c[0] == pytest.approx(ji, rel=0.06, abs=0)
+    assert c[1] == pytest.approx(jq, rel=0.08, abs=0)
 
 
 def test_rotativities_high_frequency_limit():
@@ -174,12 +174,12 @@ def test_rotativities_high_frequency_limit():
     k0, k1, k2 = (special.kv(n, 1 / te) for n in (0, 1, 2))
     rv = 2 * ne * E ** 2 * nub * ct / (ME * C * nu ** 2) * k0 / k2
     rq = ne * E ** 2 * nub ** 2 * st ** 2 / (ME * C * nu ** 3) * (k1 / k2 + 6 * te)
-    assert c[7] == pytest.approx(rv, rel=1e-4)
-    assert c[6] == pytest.approx(rq, rel=1e-3)
+    assert c[7] == pytest.approx(rv, rel=1e-4, abs=0)
+    assert c[6] == pytest.approx(rq, rel=1e-3, abs=0)
     # cold limit of the Faraday rotation coefficient: e^3 n B cos / (pi m^2 c^2 nu^2)
-    c = O.coefficients(ne, 0.06, b, nu, ct)
+    c = O.coefficients(ne, 0.002, b, nu, ct)
     cold = E ** 3 * ne * b * ct / (math.pi * ME ** 2 * C ** 2 * nu ** 2)
-    assert c[7] == pytest.approx(cold, rel=0.1)
+    assert c[7] == pytest.approx(cold, rel=0.005, abs=0)
 
 
 def _uniform_grid(vals, gp):
@@ -230,7 +230,7 @@ def test_plasma_hand_values():
     assert b @ glo @ u == pytest.approx(0.0, abs=1e-12)
     pres = (13 / 9 - 1) * ug
     assert p["theta_e"] == pytest.approx(0.5 * MP / ME * pres / rho, rel=1e-12)   # T_i = T_e
-    assert p["ne"] == pytest.approx(rho * 1e-17 / MP, rel=1e-12)
+    assert p["ne"] == pytest.approx(rho * 1e-17 / MP, rel=1e-12, abs=0)
     # normal observer: u_i = 0 so b^t = 0, b^i = B^i / u^t = alpha B^i, alpha^2 = 1 / (1 + f)
     g = O.metric_sks(r, th, 1.0, a)
     f = 2 * r / (r * r + a * a * math.cos(th) ** 2)
@@ -300,3 +300,167 @@ def test_face_on_nonspinning_image_symmetry():
     assert np.allclose(rot[..., 0], img[..., 0], atol=1e-6 * scale)
     assert np.allclose(rot[..., 3], img[..., 3], atol=1e-6 * scale)
     assert np.allclose(rot[..., 1:3], -img[..., 1:3], atol=1e-6 * scale)
+
+
+def _carter_state(x, k, a):
+    r = O.r_of_x(x, a)
+    th = math.acos(x[3] / r)
+    ph = math.atan2(x[2], x[1]) - math.atan(a / r)
+    st, ct, sp, cp = math.sin(th), math.cos(th), math.sin(ph), math.cos(ph)
+    J = np.array([[st * cp, ct * (r * cp - a * sp), st * (-r * sp - a * cp)],
+                  [st * sp, ct * (r * sp + a * cp), st * (r * cp - a * sp)],
+                  [ct, -r * st, 0.0]])
+    ks = J.T @ k[1:]
+    return ks[2], ks[1] ** 2 + ct * ct * (-a * a * k[0] ** 2 + ks[2] ** 2 / (st * st))
+
+
+def test_samples_flat_space_are_segment_centres():
+    """Straight rays: samples sit at the centres of equal sub-segments, nodes equally spaced."""
+    gp = S.GridParams(n_r=8, n_theta=8, n_phi=8)
+    prim = np.zeros((8, 8, 8, 8), dtype=np.float32)
+    met = S.Metric(spin=0.0, flat=1, ds_max=0.5)
+    cam = S.Camera(r=200.0, theta=1.0, n=4, width=20.0)
+    x, k, _, _, _ = O.camera_pixel(cam, met, 1, 2)
+    smp = O.ray_samples(met, gp, prim, cam.r, np.concatenate([x, k]))
+    kup = np.array([-k[0], *k[1:]])                        # Minkowski raise
+    n = len(smp["dl"])
+    assert n > 50
+    for q in range(n):
+        # sample = node + (dl / 2) k (sample lies half a segment source-ward of its node)
+        want = smp["node_x"][q] - 0.5 * smp["dl"][q] * kup
+        assert np.allclose(smp["x"][q], want, atol=1e-9 * 200)
+        if q + 1 < n:
+            # next node is one full segment further
+            want = smp["node_x"][q] - smp["dl"][q] * kup
+            assert np.allclose(smp["node_x"][q + 1], want, atol=1e-9 * 200)
+        r = O.r_of_x(smp["x"][q], 0.0)
+        if r < gp.r_max:
+            assert smp["dl"][q] * math.sqrt(kup[1:] @ kup[1:]) <= met.ds_max * (1 + 1e-12)
+
+
+def test_samples_curved_space_lie_on_the_geodesic():
+    """Quartic sub-samples and nodes keep the null condition and the Kerr constants."""
+    gp = S.GridParams(n_r=8, n_theta=8, n_phi=8)
+    prim = np.zeros((8, 8, 8, 8), dtype=np.float32)
+    a = 0.9
+    met = S.Metric(spin=a, ds_max=0.1)
+    cam = S.Camera(r=1000.0, theta=math.radians(60), n=8, width=30.0)
+    x, k, _, _, _ = O.camera_pixel(cam, met, 2, 5)
+    y0 = np.concatenate([x, k])
+    smp = O.ray_samples(met, gp, prim, cam.r, y0)
+    lz0, q0 = _carter_state(x, k, a)
+    nsub = 0
+    for q in range(len(smp["dl"])):
+        for xx, kk in ((smp["x"][q], smp["k"][q]), (smp["node_x"][q], smp["node_k"][q])):
+            _, ghi = O.metric_cks(xx, 1.0, a)
+            assert abs(kk @ ghi @ kk) < 2e-6
+            lz, qq = _carter_state(xx, kk, a)
+            assert lz == pytest.approx(lz0, abs=2e-6)
+            assert qq == pytest.approx(q0, rel=2e-6, abs=2e-6)
+        if O.r_of_x(smp["x"][q], a) < 20:
+            nsub += 1
+    assert nsub > 100                                          # subdivision did happen
+
+
+def test_fluid_frame_and_stokes_coherency_maps():
+    a = 0.7
+    x = np.array([0.0, 6.0, -2.0, 3.0])
+    glo, ghi = O.metric_cks(x, 1.0, a)
+    gp = S.GridParams(n_r=4, n_theta=4, n_phi=4)
+    prim = _uniform_grid([1.0, 0.1, 0.05, 0.0, 0.02, 0.01, 0.002, 0.003], gp)
+    ok, p = O.plasma(gp, prim, S.Metric(spin=a), x)
+    assert ok
+    u, b = p["u"], p["b"]
+    ka = np.array([0.3, -0.8, 0.2])
+    A, B, Cc = glo[0, 0], glo[0, 1:] @ ka, ka @ glo[1:, 1:] @ ka
+    kt = (-B - math.sqrt(B * B - A * Cc)) / A
+    kup = np.array([kt, *ka])
+    e1, e2 = O.fluid_frame(glo, u, kup, b)
+    e3 = (kup + (kup @ glo @ u) * u) / (-(kup @ glo @ u))
+    basis = [u, e1, e2, e3]
+    gram = np.array([[p_ @ glo @ q_ for q_ in basis] for p_ in basis])
+    assert np.allclose(gram, np.diag([-1, 1, 1, 1]), atol=1e-12)
+    # e2 lies in the plane of b and e3 (field-aligned), e1 = e2 x e3 (right-handed with u)
+    assert abs(e1 @ glo @ b) < 1e-12 * math.sqrt(b @ glo @ b)
+    vol = np.linalg.det(np.array([u, e1, e2, e3]))       # sqrt(-g) = 1 in CKS
+    assert vol == pytest.approx(1.0, abs=1e-10)
+    # round trip and transversality
+    s = np.array([1.0, 0.3, -0.2, 0.15])
+    nre, nim = O.s_to_n(e1, e2, s)
+    assert np.allclose(O.n_to_s(glo, e1, e2, nre, nim), s, atol=1e-13)
+    klo = glo @ kup
+    assert np.allclose(nre @ klo, 0.0, atol=1e-12) and np.allclose(nim @ klo, 0.0, atol=1e-12)
+    # a basis rotated by chi rotates (Q, U) by -2 chi and leaves I, V unchanged
+    chi = 0.3
+    f1 = math.cos(chi) * e1 + math.sin(chi) * e2
+    f2 = -math.sin(chi) * e1 + math.cos(chi) * e2
+    s2 = O.n_to_s(glo, f1, f2, nre, nim)
+    assert s2[0] == pytest.approx(s[0]) and s2[3] == pytest.approx(s[3])
+    assert s2[1] == pytest.approx(s[1] * math.cos(2 * chi) + s[2] * math.sin(2 * chi))
+    assert s2[2] == pytest.approx(-s[1] * math.sin(2 * chi) + s[2] * math.cos(2 * chi))
+    # V = 2 Im(N^{ab} e1_a e2_b): a pure-V state built by hand
+    e1l, e2l = glo @ e1, glo @ e2
+    nv = 0.5 * (np.outer(e1, e2) - np.outer(e2, e1))
+    assert (e1l @ nv @ e2l) * 2 == pytest.approx(1.0)
+    assert O.n_to_s(glo, e1, e2, np.zeros((4, 4)), nv)[3] == pytest.approx(1.0)
+
+
+def test_plasma_electron_temperature_prescription():
+    """T_i/T_e = (R_high + beta^-2 R_low) / (1 + beta^-2), Sec. 2.5, at a hand-chosen state."""
+    gp = S.GridParams(n_r=4, n_theta=4, n_phi=4, r_high=20.0, r_low=1.0)
+    rho, ug, bth = (float(np.float32(v)) for v in (0.9, 0.04, 0.0015))
+    prim = _uniform_grid([rho, ug, 0.0, 0.0, 0.0, 0.0, bth, 0.0], gp)
+    r, th, ph, a = 12.0, 1.3, 2.0, 0.0
+    x = np.array([0.0, math.sin(th) * r * math.cos(ph), math.sin(th) * r * math.sin(ph),
+                  r * math.cos(th)])
+    ok, p = O.plasma(gp, prim, S.Metric(spin=a), x)
+    assert ok
+    bsq = (r * r * bth * bth) / (1 + 2 / r)          # normal observer, a = 0
+    pres = (13 / 9 - 1) * ug
+    binv2 = (bsq / (2 * pres)) ** 2
+    ratio = (20.0 + binv2 * 1.0) / (1 + binv2)
+    want = 0.5 * MP / ME * pres / rho * 2.0 / (1.0 + ratio)
+    assert p["theta_e"] == pytest.approx(want, rel=1e-10)
+
+
+def test_camera_orientation_flat():
+    """h = [abc] v_b K_c / sqrt(D): camera on +x looking in, up = z  ->  H = +y."""
+    cam = S.Camera(r=100.0, theta=math.pi / 2, phi=0.0, n=4, width=8.0)
+    met = S.Metric(spin=0.0, flat=1)
+    x, k, H, V, _ = O.camera_pixel(cam, met, 3, 1)
+    assert np.allclose(H, [0, 0, 1, 0], atol=1e-14)
+    assert np.allclose(V, [0, 0, 0, 1], atol=1e-14)
+    # pixel centres (i - N/2 + 1/2) w / N along H and V
+    assert np.allclose(x, [0, 100.0, 3.0, -1.0], atol=1e-12)
+
+
+def test_boosted_thin_shell_flat_space_doppler():
+    """Optically thin emitter moving along the line of sight (flat space): the observed
+    intensity is sum_s g_s^2 j'(nu / g_s) L_s with g = nu / nu' (invariance of I_nu / nu^3),
+    here for a radially moving shell crossed twice by a ray through the centre."""
+    beta = 0.3
+    gam = 1 / math.sqrt(1 - beta * beta)
+    gp = S.GridParams(n_r=64, n_theta=16, n_phi=16, r_min=40.0, r_max=50.0, r_high=1.0,
+                      r_low=1.0, rho_unit_cgs=1e-26)
+    rc = S.r_centres(gp)
+    b0 = 0.01                               # lab-frame field magnitude (code units)
+    rho, ug = 1.0, 0.0245
+    prim = np.zeros((8, gp.n_phi, gp.n_theta, gp.n_r), dtype=np.float32)
+    prim[0], prim[1] = rho, ug
+    prim[2] = gam * beta                    # u^p_r: radial normal-frame 4-velocity
+    prim[6] = (b0 / rc)[None, None, :]      # B^theta with |B| = r B^theta = b0 at theta = pi/2
+    met = S.Metric(spin=0.0, flat=1, ds_max=0.005)
+    cam = S.Camera(r=200.0, theta=math.pi / 2, n=2, width=0.002)
+    res = O.trace(cam, met, gp, prim, 230e9, pix=np.array([0], dtype=np.int32), nthreads=1)
+    got = res["stokes"][0, 0]
+    # fluid-frame state: B' = |B| / gamma (field perpendicular to the motion), theta_B' = 90 deg
+    pres = (13 / 9 - 1) * ug
+    te = 0.5 * MP / ME * pres / rho
+    ne = rho * 1e-26 / MP
+    bg = b0 / gam * C * math.sqrt(4 * math.pi * 1e-26)
+    length_cm = 10.0 * 6.67430e-8 * 4.152e6 * 1.98841e33 / C ** 2
+    want = 0.0
+    for g in (1 / (gam * (1 - beta)), 1 / (gam * (1 + beta))):     # near side, far side
+        j = O.coefficients(ne, te, bg, 230e9 / g, 0.0)[0]
+        want += g * g * j * length_cm
+    assert got == pytest.approx(want, rel=3e-3, abs=0)
