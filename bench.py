@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the Blacklight hot path on GB300: rays/s of geodesic + polarized transfer.
+
+Workload (one step): 9 images -- spins {0, 0.5, 0.94} x inclinations {17, 60, 90} deg -- of
+256x256 pixels each, camera at r = 1000 M with a +-20 M field of view, 230 GHz, on the seeded
+synthetic torus sampled on a 256x128x128 spherical Kerr-Schild grid (one grid per spin), traced
+in one batched persistent launch pair. Inputs stay resident in HBM; the three grids (3 x 134 MB)
+plus the per-sample records exceed the 129 MB L2, so no explicit flush is needed between steps.
+
+One JSON line is printed by rank 0. See the design notes for the roofline arithmetic.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rays/sec (geodesic+polarized transfer) at 256^2"
+SPINS = (0.0, 0.5, 0.94)
+INCS = (17.0, 60.0, 90.0)
+FREQ = 230e9
+N_PIX = 256
+GRID = (256, 128, 128)
+# Algorithmic arithmetic per unit of work (operation counts of the method, see design notes):
+# FP64 flops per Dormand-Prince attempt (6 right-hand sides, 5 stage combinations, error norm)
+FLOP64_PER_ATTEMPT = 1520
+# FP32 flops per transfer sample (2 transport matrices, predictor-corrector, sampling,
+# plasma, coefficients, fluid frame, Stokes step)
+FLOP32_PER_SAMPLE = 3300
+# Nominal peaks from the pool's profiling recipe (no measured FP64/FP32 peak is available):
+# FP64 1.25 TFLOP/s; FP32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
+PEAK_FP64_TFLOPS = 1.25
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="blacklight", choices=["blacklight", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--case", default="full", choices=["full", "small"],
+                    help="small: one 256^2 image (a=0.94, i=60 deg) of the same workload, for "
+                         "profiler captures")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def build_workload(torch, precision_code, device, case="full"):
+    from paper_2203_15963_gb300 import synth as S
+    gp = S.grid_params_for(*GRID)
+    spins, incs = (SPINS, INCS) if case == "full" else ((0.94,), (60.0,))
+    prims_host, prims = {}, {}
+    for spin in spins:
+        prims_host[spin] = S.make_torus(gp, spin, S.BASE_SEED + 1)
+        prims[spin] = torch.from_numpy(prims_host[spin]).to(device)
+    cams, mets, gps, ps, freqs = [], [], [], [], []
+    for spin in spins:
+        for inc in incs:
+            cams.append(S.Camera(theta=math.radians(inc), n=N_PIX))
+            mets.append(S.Metric(spin=spin, precision=precision_code))
+            gps.append(gp)
+            ps.append(prims[spin])
+            freqs.append(FREQ)
+    return dict(gp=gp, cams=cams, mets=mets, gps=gps, prims=ps, freqs=freqs,
+                prims_host=prims_host)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = [ln.split(",") for ln in open(self.path).read().splitlines() if ln.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(wl, n_per_image, seed=99):
+    """The oracle, as it stands, on a bounded sample of the same workload (all host cores)."""
+    import numpy as np
+    import oracle as O
+    O.build()
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    rays = 0
+    for cam, met, gp, spin in zip(wl["cams"], wl["mets"], wl["gps"],
+                                  [m.spin for m in wl["mets"]]):
+        pix = np.sort(rng.choice(cam.n * cam.n, n_per_image, replace=False)).astype(np.int32)
+        O.trace(cam, met, gp, wl["prims_host"][spin], FREQ, pix=pix, nthreads=0)
+        rays += n_per_image
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    return {"value": rays / dt, "unit": "rays/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_per_image} seeded pixels from each of the 9 images ({rays} rays), "
+                      f"{dt:.1f} s wall on {cores} threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    wl = build_workload_host()
+    n_per_image = 128
+    for _ in range(args.warmup):
+        cpu_baseline(wl, n_per_image, seed=1)
+    vals, t_total = [], 0.0
+    for k in range(args.steps):
+        r = cpu_baseline(wl, n_per_image, seed=100 + k)
+        vals.append(r["value"])
+    value = statistics.median(vals)
+    ms = 9 * n_per_image / value * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "torus256_cam256", "images": 9, "camera": N_PIX,
+                       "grid": list(GRID), "spins": list(SPINS), "inclinations_deg": list(INCS),
+                       "freq_ghz": FREQ / 1e9, "sample_per_step": f"{n_per_image} pixels x 9 images"},
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": os.cpu_count() or 1,
+                             "kind": "oracle",
+                             "sample": f"{n_per_image} seeded pixels from each of the 9 images per step"},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def build_workload_host():
+    from paper_2203_15963_gb300 import synth as S
+    gp = S.grid_params_for(*GRID)
+    prims_host = {spin: S.make_torus(gp, spin, S.BASE_SEED + 1) for spin in SPINS}
+    cams, mets, gps = [], [], []
+    for spin in SPINS:
+        for inc in INCS:
+            cams.append(S.Camera(theta=math.radians(inc), n=N_PIX))
+            mets.append(S.Metric(spin=spin))
+            gps.append(gp)
+    return dict(cams=cams, mets=mets, gps=gps, prims_host=prims_host)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    device = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(device)
+    from paper_2203_15963_gb300 import images, native
+    native.build()
+    native.load()
+    prec = native.BL_PREC_MIXED if args.precision == "mixed" else native.BL_PREC_FP64
+    wl = build_workload(torch, prec, device, args.case)
+    cams, mets = wl["cams"], wl["mets"]
+    ws = torch.empty(native.blacklight_workspace_size(cams, mets), dtype=torch.uint8,
+                     device=device)
+    dt = torch.float32 if prec == native.BL_PREC_MIXED else torch.float64
+    outs = [images.alloc_outputs(c.n, dt, device=device, samples=True) for c in cams]
+    rays_per_step = sum(c.n * c.n for c in cams)
+
+    def step():
+        return native.blacklight_trace_batch(cams, mets, wl["gps"], wl["prims"], wl["freqs"],
+                                             outs, workspace=ws, flags=native.BL_TIMING)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(device.index)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    native.blacklight_launch_count(reset=True)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    geo_ms, tr_ms, rcs = 0.0, 0.0, []
+    e0.record(stream)
+    for _ in range(args.steps):
+        rcs.append(step())
+        g, t = native.blacklight_last_kernel_ms()
+        geo_ms += g
+        tr_ms += t
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = native.blacklight_launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * rays_per_step * args.steps / elapsed
+
+    # algorithmic work of one launch pair (identical every step)
+    attempts = sum(int(o["steps"].long().sum()) for o in outs)
+    samples = sum(int(o["samples"].long().sum()) for o in outs)
+    geo_avg = geo_ms / args.steps / 1e3
+    tr_avg = tr_ms / args.steps / 1e3
+    flop_geo = attempts * FLOP64_PER_ATTEMPT
+    flop_tr = samples * FLOP32_PER_SAMPLE
+    if geo_avg >= tr_avg:
+        roof = {"kernel": "geodesic_kernel (FP64)", "bound": "alu",
+                "achieved": flop_geo / geo_avg / 1e12, "peak": PEAK_FP64_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "nominal FP64 rate (profiling recipe)"}
+    else:
+        peak = PEAK_FP32_TFLOPS if prec == native.BL_PREC_MIXED else PEAK_FP64_TFLOPS
+        roof = {"kernel": "transfer_kernel", "bound": "alu",
+                "achieved": flop_tr / tr_avg / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "nominal rate (profiling recipe unit counts x 2.07 GHz)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    status_bad = sum(int(((o["status"] != 1) & (o["status"] != 2)).sum()) for o in outs)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(torch, native, wl, prec, max(1, min(args.steps, 3)))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, 1024)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64+f32" if prec == native.BL_PREC_MIXED else "f64",
+                "data": "synthetic",
+                "config": {"workload": "torus256_cam256" if args.case == "full"
+                           else "torus256_cam256 (one image: a=0.94, i=60 deg)",
+                           "images": len(cams), "camera": N_PIX,
+                           "grid": list(GRID), "spins": list(SPINS),
+                           "inclinations_deg": list(INCS), "freq_ghz": FREQ / 1e9,
+                           "precision": args.precision, "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (3 x 134 MB grids + sample records); no flush"},
+                "kernel_ms": {"geodesic": geo_avg * 1e3, "transfer": tr_avg * 1e3},
+                "work": {"dp_attempts": attempts, "samples": samples,
+                         "rays_not_terminated_normally": status_bad},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk, "return_codes": sorted(set(rcs))}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def measure_e2e(torch, native, wl, prec, steps):
+    """Same workload through the C ABI's host-buffer entry point: per step, each image's grid
+    is copied from pinned host memory and its Stokes image copied back, inside the timing."""
+    host_prims = {s: torch.from_numpy(p).pin_memory() for s, p in wl["prims_host"].items()}
+    dt = torch.float32 if prec == native.BL_PREC_MIXED else torch.float64
+    outs = [{"stokes": torch.empty((4, c.n, c.n), dtype=dt).pin_memory()} for c in wl["cams"]]
+    h2d = sum(host_prims[m.spin].numel() * 4 for m in wl["mets"])
+    d2h = sum(o["stokes"].numel() * o["stokes"].element_size() for o in outs)
+
+    def one():
+        for cam, met, gp, o in zip(wl["cams"], wl["mets"], wl["gps"], outs):
+            native.blacklight_trace_host(cam, met, gp, host_prims[met.spin], FREQ, o)
+
+    one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    dt_s = (time.perf_counter() - t0) / steps
+    rays = sum(c.n * c.n for c in wl["cams"])
+    return {"value": rays / dt_s, "unit": "rays/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps,
+            "path": "blacklight_trace_host per image (pinned host grid in, Stokes out)"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * blacklight.h -- C ABI of the GB300 (sm_103a) ray-tracing library for the hot path of
+ * White 2022, "Blacklight: A General-Relativistic Ray-Tracing and Analysis Tool".
+ *
+ * The library computes, for every pixel of one or more plane-parallel cameras, a null
+ * geodesic traced backward through Kerr spacetime in Cartesian Kerr-Schild coordinates
+ * (Sec. 2, Eq. cks_aux; Sec. 2.2, Eq. geodesic) with the adaptive Dormand-Prince RK5(4)
+ * integrator (Table tab:dp), samples a spherical Kerr-Schild fluid grid along it (Sec. 2.4),
+ * derives the thermal-electron plasma state (Sec. 2.5), and integrates polarized radiative
+ * transfer (Sec. 2.3.2, Eqs. polarized_s / polarized_n with Strang splitting and the
+ * predictor-corrector of Table tab:pc) to Stokes I, Q, U, V at the camera.
+ *
+ * Conventions shared by every entry point:
+ *   - All structs are plain data; their first field `size` must equal sizeof(struct) (ABI
+ *     version check). All pointers are borrowed: the caller owns them and keeps them valid
+ *     until the work on `stream` has finished.
+ *   - Device pointers must belong to the current CUDA device. `stream` is a cudaStream_t
+ *     (NULL = legacy default stream). Work is stream-ordered; without BL_ASYNC the call
+ *     synchronises `stream` and reports per-ray anomalies in its return value.
+ *   - Return value: 0 = success; > 0 = completed with per-ray anomalies (BL_WRAYS; see the
+ *     per-ray status array); < 0 = error, nothing was launched or the launch failed
+ *     (BL_EINVAL bad argument, BL_ENOMEM allocation failed, BL_ECUDA CUDA runtime error,
+ *     BL_EUNSUPPORTED valid but not implemented). blacklight_last_error_detail() names the
+ *     offending field (thread-local string, valid until the next call on that thread).
+ *   - Device code never traps: rays that fail set their status word instead.
+ *   - Lengths are in units of M = G M_bh / c^2; plasma and radiation in CGS.
+ */
+#ifndef BLACKLIGHT_H
+#define BLACKLIGHT_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Camera (Sec. 2.1). The centre is given in spherical Kerr-Schild coordinates; u_p is the
+ * centre's normal-frame velocity (Sec. 2, A^p = A^i + beta^i A^t), k_p the received
+ * momentum direction as covariant spherical KS spatial components k_i. Pixel (i, j) sits at
+ * a, b = (i or j - n/2 + 1/2) w / n along the horizontal H and vertical V directions. */
+typedef struct bl_camera {
+    uint32_t size;
+    double r, theta, phi;
+    double u_p[3];
+    double k_p[3];
+    double width;           /* full width w of the image plane */
+    int32_t n;              /* pixels per side, 1..65536 */
+    double psi;             /* roll about the line of sight */
+    int32_t kind;           /* 0 = plane-parallel (only kind supported) */
+    int32_t nu_at_infinity; /* 1: -n k_t = nu (Sec. 2.1); 0: -n k_a u^a = nu at the camera */
+} bl_camera_t;
+
+/* Spacetime and integrator controls (Sec. 2.2). */
+typedef struct bl_metric {
+    uint32_t size;
+    double mass;            /* M (1 for lengths in M) */
+    double spin;            /* a, |a| < M */
+    double r_in_over_rhor;  /* inner termination radius in units of the outer horizon, > 1 */
+    double tol_abs, tol_rel;/* DP tolerances f_abs, f_rel > 0 */
+    double ds_max;          /* proper-length limit for step subdivision, > 0 */
+    double h0_frac;         /* first step = -h0_frac (r_cam - r_hor) */
+    int64_t max_steps;      /* attempted DP steps per ray before MAX_STEPS */
+    int32_t flat;           /* 1: Minkowski metric in the same coordinates (Sec. 4, flat) */
+    int32_t precision;      /* BL_PREC_FP64 or BL_PREC_MIXED */
+} bl_metric_t;
+
+/* Fluid grid and plasma model (Secs. 2.4-2.5). prim is a DEVICE pointer to float32
+ * [8][n_phi][n_theta][n_r] (r fastest): rho, u_gas, u^p_(r,theta,phi) (normal frame),
+ * B^(r,theta,phi) (coordinate components), on cells log-spaced in r over [r_min, r_max],
+ * uniform in theta over [0, pi] and in phi over [0, 2 pi). */
+typedef struct bl_grid {
+    uint32_t size;
+    const float* prim;
+    int32_t n_r, n_theta, n_phi;
+    double r_min, r_max;
+    double gamma_ad;        /* adiabatic index: p = (gamma_ad - 1) u_gas */
+    double r_high, r_low;   /* T_i / T_e prescription */
+    double mu, ne_over_ni;  /* molecular weight, electron-to-ion number ratio */
+    double sigma_cut;       /* sigma = b^2 / rho above this is vacuum */
+    double rho_unit_cgs;    /* code density unit in g / cm^3 */
+    double mass_msun;       /* black-hole mass in solar masses (sets the length unit) */
+    int32_t interp;         /* 1 = trilinear, 0 = nearest */
+} bl_grid_t;
+
+/* Outputs. stokes is a DEVICE pointer to [4][n][n] (I, Q, U, V; row j = vertical index
+ * major) in erg s^-1 cm^-2 sr^-1 Hz^-1, float64 (dtype 0) or float32 (dtype 1). status,
+ * steps (attempted DP steps) and samples (transfer samples) are optional DEVICE int32 [n][n]
+ * (may be NULL). end_state is an optional DEVICE float64 [n][n][8] receiving the geodesic end
+ * point (x^a, k_a). */
+typedef struct bl_out {
+    uint32_t size;
+    void* stokes;
+    int32_t dtype;
+    int32_t* status;
+    int32_t* steps;
+    double* end_state;
+    int32_t* samples;
+} bl_out_t;
+
+enum {
+    BL_OK = 0,
+    BL_WRAYS = 1,
+    BL_EINVAL = -1,
+    BL_ENOMEM = -2,
+    BL_ECUDA = -3,
+    BL_EUNSUPPORTED = -4
+};
+
+/* Per-ray status words. */
+enum {
+    BL_RAY_OK = 0,          /* not terminated (only before tracing) */
+    BL_RAY_HORIZON = 1,     /* crossed the inner radius (Sec. 2.2) */
+    BL_RAY_ESCAPED = 2,     /* crossed the camera radius outward (Sec. 2.2) */
+    BL_RAY_MAX_STEPS = 3,   /* max_steps attempts without terminating */
+    BL_RAY_UNDERFLOW = 4,   /* |step| fell below 1e-12 r */
+    BL_RAY_NAN = 5,         /* non-finite state */
+    BL_RAY_OVERFLOW = 6     /* sample store full: Stokes not computed (NaN) */
+};
+
+enum { BL_PREC_FP64 = 0, BL_PREC_MIXED = 1 };
+/* flags: BL_ASYNC returns without synchronising; BL_TIMING records CUDA events on `stream`
+ * around the geodesic and transfer kernels (read with blacklight_last_kernel_ms). */
+enum { BL_ASYNC = 1u, BL_TIMING = 2u };
+
+/* Trace n_images cameras in one persistent launch pair (geodesics, then transfer). Image q
+ * uses cams[q], mets[q], grids[q], freqs_hz[q] (observed frequency, > 0) and outs[q]. All
+ * images must share metric.precision. workspace may be NULL (the library then allocates
+ * stream-ordered scratch and frees it before returning) or a DEVICE buffer of at least
+ * blacklight_workspace_size() bytes, which the call uses instead. */
+int blacklight_trace_batch(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                           const bl_grid_t* grids, const double* freqs_hz, const bl_out_t* outs,
+                           void* workspace, size_t workspace_bytes, void* stream,
+                           uint32_t flags);
+
+/* One image: blacklight_trace_batch with n_images = 1 and library-managed scratch. */
+int blacklight_trace(const bl_camera_t* cam, const bl_metric_t* met, const bl_grid_t* grid,
+                     double freq_hz, const bl_out_t* out, void* stream, uint32_t flags);
+
+/* Same as blacklight_trace, but grid->prim and out->stokes/status/steps/end_state are HOST
+ * pointers: the call copies the grid in, traces, and copies the results out (all
+ * stream-ordered, device scratch allocated and freed inside). Always synchronous. */
+int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const bl_grid_t* grid,
+                          double freq_hz, const bl_out_t* out, void* stream);
+
+/* Geodesics only (Sec. 2.2): writes out->end_state, out->status and out->steps (attempted
+ * DP steps); out->stokes is ignored. */
+int blacklight_geodesics(const bl_camera_t* cam, const bl_metric_t* met, const bl_out_t* out,
+                         void* stream, uint32_t flags);
+
+/* Workspace bytes blacklight_trace_batch needs for these images. */
+size_t blacklight_workspace_size(int32_t n_images, const bl_camera_t* cams,
+                                 const bl_metric_t* mets);
+
+/* Component entry points (same device functions as the traced path), for checking each
+ * stage on its own. All arrays are DEVICE pointers; n elements; precision selects the FP64
+ * or FP32 device code.
+ *   coefficients (Sec. 2.5): in [n][5] = n_e, Theta_e, B (gauss), nu (fluid frame), cos
+ *     theta_B; out [n][8] = j_I, j_Q, j_V, alpha_I, alpha_Q, alpha_V, rho_Q, rho_V.
+ *   stokes_step (Sec. 2.3.2): coef [n][8] = e_I, e_Q, e_V, a_I, a_Q, a_V, r_Q, r_V per unit
+ *     affine parameter; s0 [n][4]; dl [n]; out s1 [n][4]: exact constant-coefficient step.
+ *   bessel_k (scaled): in x [n]; out [n][3] = exp(x) K_0, K_1, K_2. */
+int blacklight_coefficients(int64_t n, const double* in, double* out, int32_t precision,
+                            void* stream);
+int blacklight_stokes_step(int64_t n, const double* coef, const double* s0, const double* dl,
+                           double* s1, int32_t precision, void* stream);
+int blacklight_bessel_k(int64_t n, const double* x, double* out, int32_t precision,
+                        void* stream);
+
+const char* blacklight_strerror(int code);
+const char* blacklight_last_error_detail(void);
+/* Kernels launched by this thread since the last reset (launch accounting for benchmarks). */
+uint64_t blacklight_launch_count(int reset);
+/* Device time of the geodesic kernel (ms[0]) and transfer kernel (ms[1]) of this thread's
+ * last call made with BL_TIMING; waits for that call's work. Returns 0, or BL_EINVAL if no
+ * timed call was made. */
+int blacklight_last_kernel_ms(float ms[2]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

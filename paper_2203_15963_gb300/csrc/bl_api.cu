@@ -1,0 +1,480 @@
+// C ABI of the Blacklight GB300 library: argument checks, workspace layout, launches.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "../../include/blacklight.h"
+#include "bl_kernels.cuh"
+
+namespace {
+
+thread_local char g_detail[512] = "";
+thread_local uint64_t g_launches = 0;
+// events around the geodesic and transfer kernels of the last BL_TIMING call on this thread
+thread_local cudaEvent_t g_ev[3] = {nullptr, nullptr, nullptr};
+thread_local bool g_timed = false;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_detail, sizeof(g_detail), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(BL_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define BL_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Average pool chunks reserved per ray (32 samples each); rays whose samples do not fit are
+// reported with status BL_RAY_OVERFLOW.
+constexpr int64_t kChunksPerRay = 16;
+
+struct Layout {
+    size_t counters, descs, hdr, chunks, pool, total;
+    int64_t rays, pool_chunks;
+};
+
+Layout make_layout(int32_t n_images, const bl_camera_t* cams, int precision) {
+    Layout L{};
+    int64_t rays = 0;
+    for (int q = 0; q < n_images; ++q) rays += (int64_t)cams[q].n * cams[q].n;
+    L.rays = rays;
+    L.pool_chunks = rays * kChunksPerRay;
+    const size_t rec = precision == BL_PREC_MIXED ? sizeof(float) * bl::RecStride<float>::v
+                                                  : sizeof(double) * bl::RecStride<double>::v;
+    size_t off = 0;
+    L.counters = off; off = align_up(off + sizeof(bl::Counters));
+    L.descs = off;    off = align_up(off + sizeof(bl::ImageDesc) * (size_t)n_images);
+    L.hdr = off;      off = align_up(off + sizeof(bl::RayHdr) * (size_t)rays);
+    L.chunks = off;   off = align_up(off + sizeof(int32_t) * bl::kMaxChunks * (size_t)rays);
+    L.pool = off;     off = align_up(off + rec * bl::kChunk * (size_t)L.pool_chunks);
+    L.total = off;
+    return L;
+}
+
+int check_camera(const bl_camera_t* c, int q) {
+    if (!c) return fail(BL_EINVAL, "cams[%d] is NULL", q);
+    if (c->size != sizeof(bl_camera_t)) return fail(BL_EINVAL, "cams[%d].size mismatch", q);
+    if (!(c->n >= 1 && c->n <= 65536)) return fail(BL_EINVAL, "cams[%d].n out of range", q);
+    if (!(c->width > 0.0) || !std::isfinite(c->width)) return fail(BL_EINVAL, "cams[%d].width", q);
+    if (!(c->r > 0.0) || !std::isfinite(c->r)) return fail(BL_EINVAL, "cams[%d].r", q);
+    if (!std::isfinite(c->theta) || !std::isfinite(c->phi) || !std::isfinite(c->psi))
+        return fail(BL_EINVAL, "cams[%d] angles", q);
+    if (c->kind != 0) return fail(BL_EUNSUPPORTED, "cams[%d].kind: only plane-parallel", q);
+    if (c->k_p[0] == 0.0 && c->k_p[1] == 0.0 && c->k_p[2] == 0.0)
+        return fail(BL_EINVAL, "cams[%d].k_p is zero", q);
+    return 0;
+}
+
+int check_metric(const bl_metric_t* m, int q) {
+    if (!m) return fail(BL_EINVAL, "mets[%d] is NULL", q);
+    if (m->size != sizeof(bl_metric_t)) return fail(BL_EINVAL, "mets[%d].size mismatch", q);
+    if (!(m->mass > 0.0)) return fail(BL_EINVAL, "mets[%d].mass must be > 0", q);
+    if (!(std::fabs(m->spin) < m->mass)) return fail(BL_EINVAL, "mets[%d].spin: need |a| < M", q);
+    if (!(m->r_in_over_rhor > 1.0)) return fail(BL_EINVAL, "mets[%d].r_in_over_rhor must be > 1", q);
+    if (!(m->tol_abs > 0.0) || !(m->tol_rel > 0.0)) return fail(BL_EINVAL, "mets[%d] tolerances", q);
+    if (!(m->ds_max > 0.0)) return fail(BL_EINVAL, "mets[%d].ds_max must be > 0", q);
+    if (!(m->h0_frac > 0.0)) return fail(BL_EINVAL, "mets[%d].h0_frac must be > 0", q);
+    if (!(m->max_steps > 0)) return fail(BL_EINVAL, "mets[%d].max_steps must be > 0", q);
+    if (m->precision != BL_PREC_FP64 && m->precision != BL_PREC_MIXED)
+        return fail(BL_EINVAL, "mets[%d].precision", q);
+    return 0;
+}
+
+int check_grid(const bl_grid_t* g, int q) {
+    if (!g) return fail(BL_EINVAL, "grids[%d] is NULL", q);
+    if (g->size != sizeof(bl_grid_t)) return fail(BL_EINVAL, "grids[%d].size mismatch", q);
+    if (!g->prim) return fail(BL_EINVAL, "grids[%d].prim is NULL", q);
+    if (g->n_r < 1 || g->n_theta < 1 || g->n_phi < 1) return fail(BL_EINVAL, "grids[%d] dims", q);
+    if (!(g->r_min > 0.0) || !(g->r_max > g->r_min)) return fail(BL_EINVAL, "grids[%d] r range", q);
+    if (!(g->gamma_ad > 1.0)) return fail(BL_EINVAL, "grids[%d].gamma_ad", q);
+    if (!(g->mu > 0.0) || !(g->ne_over_ni > 0.0)) return fail(BL_EINVAL, "grids[%d] composition", q);
+    if (!(g->rho_unit_cgs > 0.0) || !(g->mass_msun > 0.0)) return fail(BL_EINVAL, "grids[%d] units", q);
+    if (g->interp != 0 && g->interp != 1) return fail(BL_EINVAL, "grids[%d].interp", q);
+    return 0;
+}
+
+int check_out(const bl_out_t* o, int q, bool need_stokes) {
+    if (!o) return fail(BL_EINVAL, "outs[%d] is NULL", q);
+    if (o->size != sizeof(bl_out_t)) return fail(BL_EINVAL, "outs[%d].size mismatch", q);
+    if (need_stokes && !o->stokes) return fail(BL_EINVAL, "outs[%d].stokes is NULL", q);
+    if (o->dtype != 0 && o->dtype != 1) return fail(BL_EINVAL, "outs[%d].dtype", q);
+    return 0;
+}
+
+int device_pointer(const void* p, const char* what) {
+    if (!p) return 0;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BL_EINVAL, "%s is not a CUDA pointer", what);
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(BL_EINVAL, "%s must be device memory", what);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (at.device != dev) return fail(BL_EINVAL, "%s is on device %d, current is %d", what, at.device, dev);
+    return 0;
+}
+
+void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, const bl_grid_t& g,
+               double freq, const bl_out_t& o, int64_t offset) {
+    memset(&d, 0, sizeof(d));
+    d.cam_r = c.r; d.cam_th = c.theta; d.cam_ph = c.phi;
+    for (int i = 0; i < 3; ++i) { d.u_p[i] = c.u_p[i]; d.k_p[i] = c.k_p[i]; }
+    d.width = c.width; d.psi = c.psi; d.n = c.n; d.nu_inf = c.nu_at_infinity;
+    d.mass = m.mass; d.spin = m.spin; d.r_in_over_rhor = m.r_in_over_rhor;
+    d.tol_abs = m.tol_abs; d.tol_rel = m.tol_rel; d.ds_max = m.ds_max; d.h0_frac = m.h0_frac;
+    d.max_steps = m.max_steps; d.flat = m.flat; d.precision = m.precision;
+    d.prim = g.prim; d.nr = g.n_r; d.nt = g.n_theta; d.nph = g.n_phi; d.interp = g.interp;
+    d.r_min = g.r_min; d.r_max = g.r_max; d.gamma_ad = g.gamma_ad; d.r_high = g.r_high;
+    d.r_low = g.r_low; d.mu = g.mu; d.ne_ni = g.ne_over_ni; d.sigma_cut = g.sigma_cut;
+    d.rho_unit = g.rho_unit_cgs;
+    d.length_unit = bl::kG * g.mass_msun * bl::kMsun / (bl::kC * bl::kC);
+    d.freq = freq;
+    d.stokes = o.stokes; d.dtype = o.dtype; d.status = o.status; d.steps = o.steps;
+    d.end_state = o.end_state;
+    d.samples = o.samples;
+    d.ray_offset = offset;
+}
+
+struct DevInfo {
+    int sms = 0;
+    int geo_blocks[2] = {0, 0};     // per SM, [record type float, double]
+    int tr_blocks[2] = {0, 0};      // per SM, [mixed, fp64]
+};
+
+int dev_info(DevInfo& out) {
+    static std::mutex mu;
+    static std::vector<DevInfo> cache;
+    int dev = 0;
+    BL_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= dev) cache.resize(dev + 1);
+    DevInfo& di = cache[dev];
+    if (di.sms == 0) {
+        BL_CUDA(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[0], bl::geodesic_kernel<float>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[1], bl::geodesic_kernel<double>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[0], bl::transfer_kernel<float, float>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[1], bl::transfer_kernel<double, double>, 128, 0));
+        for (int i = 0; i < 2; ++i) {
+            if (di.geo_blocks[i] < 1) di.geo_blocks[i] = 1;
+            if (di.tr_blocks[i] < 1) di.tr_blocks[i] = 1;
+        }
+    }
+    out = di;
+    return 0;
+}
+
+// Launch the camera-frame, geodesic and (optionally) transfer kernels on prepared workspace.
+int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* ws,
+               const Layout& L, int precision, bool transfer, cudaStream_t st, bool timing) {
+    DevInfo di;
+    int rc = dev_info(di);
+    if (rc) return rc;
+    if (timing) {
+        for (int i = 0; i < 3; ++i)
+            if (!g_ev[i]) BL_CUDA(cudaEventCreate(&g_ev[i]));
+    }
+    g_timed = false;
+    bl::Counters* ctr = (bl::Counters*)(ws + L.counters);
+    bl::ImageDesc* d_desc = (bl::ImageDesc*)(ws + L.descs);
+    bl::RayHdr* hdr = (bl::RayHdr*)(ws + L.hdr);
+    int32_t* chunks = (int32_t*)(ws + L.chunks);
+    BL_CUDA(cudaMemsetAsync(ctr, 0, sizeof(bl::Counters), st));
+    BL_CUDA(cudaMemcpyAsync(d_desc, descs.data(), sizeof(bl::ImageDesc) * n_images,
+                            cudaMemcpyHostToDevice, st));
+    bl::camera_frame_kernel<<<(n_images + 63) / 64, 64, 0, st>>>(d_desc, n_images);
+    ++g_launches;
+    BL_CUDA(cudaGetLastError());
+    const int pidx = precision == BL_PREC_MIXED ? 0 : 1;
+    if (timing) BL_CUDA(cudaEventRecord(g_ev[0], st));
+    if (precision == BL_PREC_MIXED) {
+        bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
+        bl::geodesic_kernel<float><<<di.sms * di.geo_blocks[pidx], 128, 0, st>>>(
+            d_desc, n_images, L.rays, hdr, sink, transfer ? 1 : 0);
+    } else {
+        bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
+        bl::geodesic_kernel<double><<<di.sms * di.geo_blocks[pidx], 128, 0, st>>>(
+            d_desc, n_images, L.rays, hdr, sink, transfer ? 1 : 0);
+    }
+    ++g_launches;
+    BL_CUDA(cudaGetLastError());
+    if (timing) BL_CUDA(cudaEventRecord(g_ev[1], st));
+    if (transfer) {
+        if (precision == BL_PREC_MIXED) {
+            bl::transfer_kernel<float, float><<<di.sms * di.tr_blocks[pidx], 128, 0, st>>>(
+                d_desc, n_images, L.rays, hdr, (const float*)(ws + L.pool), chunks, ctr);
+        } else {
+            bl::transfer_kernel<double, double><<<di.sms * di.tr_blocks[pidx], 128, 0, st>>>(
+                d_desc, n_images, L.rays, hdr, (const double*)(ws + L.pool), chunks, ctr);
+        }
+        ++g_launches;
+        BL_CUDA(cudaGetLastError());
+    }
+    if (timing) {
+        BL_CUDA(cudaEventRecord(g_ev[2], st));
+        g_timed = true;
+    }
+    return 0;
+}
+
+int finish(char* ws, const Layout& L, cudaStream_t st, bool sync) {
+    if (!sync) return 0;
+    unsigned long long bad = 0;
+    BL_CUDA(cudaMemcpyAsync(&bad, &((bl::Counters*)(ws + L.counters))->bad_rays, sizeof(bad),
+                            cudaMemcpyDeviceToHost, st));
+    BL_CUDA(cudaStreamSynchronize(st));
+    return bad ? BL_WRAYS : BL_OK;
+}
+
+int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+               const bl_grid_t* grids, const double* freqs, const bl_out_t* outs, void* workspace,
+               size_t workspace_bytes, void* stream, uint32_t flags, bool transfer) {
+    g_detail[0] = 0;
+    if (n_images < 1) return fail(BL_EINVAL, "n_images must be >= 1");
+    if (!cams || !mets || !outs || (transfer && (!grids || !freqs)))
+        return fail(BL_EINVAL, "NULL array argument");
+    int precision = -1;
+    for (int q = 0; q < n_images; ++q) {
+        int rc = check_camera(&cams[q], q);
+        if (!rc) rc = check_metric(&mets[q], q);
+        if (!rc && transfer) rc = check_grid(&grids[q], q);
+        if (!rc) rc = check_out(&outs[q], q, transfer);
+        if (rc) return rc;
+        if (transfer && !(freqs[q] > 0.0 && std::isfinite(freqs[q])))
+            return fail(BL_EINVAL, "freqs[%d] must be > 0", q);
+        if (precision < 0) precision = mets[q].precision;
+        else if (precision != mets[q].precision)
+            return fail(BL_EINVAL, "all images must share metric.precision");
+        char what[64];
+        snprintf(what, sizeof(what), "outs[%d].stokes", q);
+        if (transfer && (rc = device_pointer(outs[q].stokes, what))) return rc;
+        snprintf(what, sizeof(what), "outs[%d].status", q);
+        if ((rc = device_pointer(outs[q].status, what))) return rc;
+        snprintf(what, sizeof(what), "outs[%d].steps", q);
+        if ((rc = device_pointer(outs[q].steps, what))) return rc;
+        snprintf(what, sizeof(what), "outs[%d].end_state", q);
+        if ((rc = device_pointer(outs[q].end_state, what))) return rc;
+        snprintf(what, sizeof(what), "outs[%d].samples", q);
+        if ((rc = device_pointer(outs[q].samples, what))) return rc;
+        snprintf(what, sizeof(what), "grids[%d].prim", q);
+        if (transfer && (rc = device_pointer(grids[q].prim, what))) return rc;
+    }
+    Layout L = make_layout(n_images, cams, transfer ? precision : BL_PREC_MIXED);
+    if (!transfer) { L.pool_chunks = 0; L.total = L.pool; }
+    std::vector<bl::ImageDesc> descs(n_images);
+    int64_t off = 0;
+    static const bl_grid_t kNoGrid = {sizeof(bl_grid_t), nullptr, 1, 1, 1, 1.0, 2.0, 4.0 / 3.0,
+                                      1.0, 1.0, 0.5, 1.0, 1.0, 1.0, 1.0, 1};
+    for (int q = 0; q < n_images; ++q) {
+        fill_desc(descs[q], cams[q], mets[q], transfer ? grids[q] : kNoGrid,
+                  transfer ? freqs[q] : 1.0, outs[q], off);
+        off += (int64_t)cams[q].n * cams[q].n;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    bool own = false;
+    if (ws) {
+        if (workspace_bytes < L.total)
+            return fail(BL_EINVAL, "workspace too small: %zu < %zu bytes", workspace_bytes, L.total);
+        int rc = device_pointer(ws, "workspace");
+        if (rc) return rc;
+    } else {
+        cudaError_t e = cudaMallocAsync((void**)&ws, L.total, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BL_ENOMEM, "cudaMallocAsync(%zu bytes): %s", L.total, cudaGetErrorString(e));
+        }
+        own = true;
+    }
+    int rc = launch_all(n_images, descs, ws, L, precision, transfer, st, (flags & BL_TIMING) != 0);
+    if (rc == 0) rc = finish(ws, L, st, !(flags & BL_ASYNC));
+    if (own) {
+        cudaError_t e = cudaFreeAsync(ws, st);
+        if (rc == 0 && e != cudaSuccess) rc = cuda_fail(e, "cudaFreeAsync");
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int blacklight_trace_batch(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                           const bl_grid_t* grids, const double* freqs_hz, const bl_out_t* outs,
+                           void* workspace, size_t workspace_bytes, void* stream, uint32_t flags) {
+    return trace_impl(n_images, cams, mets, grids, freqs_hz, outs, workspace, workspace_bytes,
+                      stream, flags, true);
+}
+
+int blacklight_trace(const bl_camera_t* cam, const bl_metric_t* met, const bl_grid_t* grid,
+                     double freq_hz, const bl_out_t* out, void* stream, uint32_t flags) {
+    return trace_impl(1, cam, met, grid, &freq_hz, out, nullptr, 0, stream, flags, true);
+}
+
+int blacklight_geodesics(const bl_camera_t* cam, const bl_metric_t* met, const bl_out_t* out,
+                         void* stream, uint32_t flags) {
+    return trace_impl(1, cam, met, nullptr, nullptr, out, nullptr, 0, stream, flags, false);
+}
+
+size_t blacklight_workspace_size(int32_t n_images, const bl_camera_t* cams,
+                                 const bl_metric_t* mets) {
+    if (n_images < 1 || !cams || !mets) return 0;
+    return make_layout(n_images, cams, mets[0].precision).total;
+}
+
+int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const bl_grid_t* grid,
+                          double freq_hz, const bl_out_t* out, void* stream) {
+    g_detail[0] = 0;
+    if (!cam || !met || !grid || !out) return fail(BL_EINVAL, "NULL argument");
+    int rc = check_camera(cam, 0);
+    if (!rc) rc = check_metric(met, 0);
+    if (!rc) rc = check_grid(grid, 0);
+    if (!rc) rc = check_out(out, 0, true);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t npix = (size_t)cam->n * cam->n;
+    const size_t gbytes = sizeof(float) * 8 * (size_t)grid->n_r * grid->n_theta * grid->n_phi;
+    const size_t sbytes = 4 * npix * (out->dtype == 0 ? sizeof(double) : sizeof(float));
+    char* dev = nullptr;
+    const size_t off_s = align_up(gbytes), off_st = off_s + align_up(sbytes),
+                 off_sp = off_st + align_up(npix * 4), off_e = off_sp + align_up(npix * 4),
+                 total = off_e + align_up(npix * 8 * sizeof(double));
+    cudaError_t e = cudaMallocAsync((void**)&dev, total, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e)); }
+    bl_grid_t g = *grid;
+    g.prim = (const float*)dev;
+    bl_out_t o = *out;
+    o.stokes = dev + off_s;
+    o.status = out->status ? (int32_t*)(dev + off_st) : nullptr;
+    o.steps = out->steps ? (int32_t*)(dev + off_sp) : nullptr;
+    o.end_state = out->end_state ? (double*)(dev + off_e) : nullptr;
+    o.samples = nullptr;
+    rc = 0;
+    e = cudaMemcpyAsync(dev, grid->prim, gbytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "copy grid to device");
+    if (!rc) rc = trace_impl(1, cam, met, &g, &freq_hz, &o, nullptr, 0, stream, BL_ASYNC, true);
+    if (rc >= 0) {
+        e = cudaMemcpyAsync(out->stokes, o.stokes, sbytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && out->status)
+            e = cudaMemcpyAsync(out->status, o.status, npix * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && out->steps)
+            e = cudaMemcpyAsync(out->steps, o.steps, npix * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && out->end_state)
+            e = cudaMemcpyAsync(out->end_state, o.end_state, npix * 64, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copy results to host");
+    }
+    cudaFreeAsync(dev, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (rc == 0 && se != cudaSuccess) rc = cuda_fail(se, "cudaStreamSynchronize");
+    return rc;
+}
+
+int blacklight_coefficients(int64_t n, const double* in, double* out, int32_t precision,
+                            void* stream) {
+    g_detail[0] = 0;
+    if (n < 0 || (n > 0 && (!in || !out))) return fail(BL_EINVAL, "bad arguments");
+    if (n == 0) return 0;
+    int rc = device_pointer(in, "in");
+    if (!rc) rc = device_pointer(out, "out");
+    if (rc) return rc;
+    const int64_t blocks = (n + 127) / 128;
+    if (precision == BL_PREC_MIXED)
+        bl::coefficients_kernel<float><<<blocks, 128, 0, (cudaStream_t)stream>>>(n, in, out);
+    else
+        bl::coefficients_kernel<double><<<blocks, 128, 0, (cudaStream_t)stream>>>(n, in, out);
+    ++g_launches;
+    BL_CUDA(cudaGetLastError());
+    BL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return 0;
+}
+
+int blacklight_stokes_step(int64_t n, const double* coef, const double* s0, const double* dl,
+                           double* s1, int32_t precision, void* stream) {
+    g_detail[0] = 0;
+    if (n < 0 || (n > 0 && (!coef || !s0 || !dl || !s1))) return fail(BL_EINVAL, "bad arguments");
+    if (n == 0) return 0;
+    int rc = device_pointer(coef, "coef");
+    if (!rc) rc = device_pointer(s0, "s0");
+    if (!rc) rc = device_pointer(dl, "dl");
+    if (!rc) rc = device_pointer(s1, "s1");
+    if (rc) return rc;
+    const int64_t blocks = (n + 127) / 128;
+    if (precision == BL_PREC_MIXED)
+        bl::stokes_step_kernel<float><<<blocks, 128, 0, (cudaStream_t)stream>>>(n, coef, s0, dl, s1);
+    else
+        bl::stokes_step_kernel<double><<<blocks, 128, 0, (cudaStream_t)stream>>>(n, coef, s0, dl, s1);
+    ++g_launches;
+    BL_CUDA(cudaGetLastError());
+    BL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return 0;
+}
+
+int blacklight_bessel_k(int64_t n, const double* x, double* out, int32_t precision, void* stream) {
+    g_detail[0] = 0;
+    if (n < 0 || (n > 0 && (!x || !out))) return fail(BL_EINVAL, "bad arguments");
+    if (n == 0) return 0;
+    int rc = device_pointer(x, "x");
+    if (!rc) rc = device_pointer(out, "out");
+    if (rc) return rc;
+    const int64_t blocks = (n + 127) / 128;
+    if (precision == BL_PREC_MIXED)
+        bl::bessel_kernel<float><<<blocks, 128, 0, (cudaStream_t)stream>>>(n, x, out);
+    else
+        bl::bessel_kernel<double><<<blocks, 128, 0, (cudaStream_t)stream>>>(n, x, out);
+    ++g_launches;
+    BL_CUDA(cudaGetLastError());
+    BL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return 0;
+}
+
+const char* blacklight_strerror(int code) {
+    switch (code) {
+        case BL_OK: return "success";
+        case BL_WRAYS: return "completed; some rays did not terminate normally (see status)";
+        case BL_EINVAL: return "invalid argument";
+        case BL_ENOMEM: return "device memory allocation failed";
+        case BL_ECUDA: return "CUDA runtime error";
+        case BL_EUNSUPPORTED: return "unsupported option";
+        default: return "unknown error code";
+    }
+}
+
+const char* blacklight_last_error_detail(void) { return g_detail; }
+
+int blacklight_last_kernel_ms(float ms[2]) {
+    g_detail[0] = 0;
+    if (!ms) return fail(BL_EINVAL, "ms is NULL");
+    if (!g_timed) return fail(BL_EINVAL, "no call with BL_TIMING on this thread");
+    BL_CUDA(cudaEventSynchronize(g_ev[2]));
+    BL_CUDA(cudaEventElapsedTime(&ms[0], g_ev[0], g_ev[1]));
+    BL_CUDA(cudaEventElapsedTime(&ms[1], g_ev[1], g_ev[2]));
+    return 0;
+}
+
+uint64_t blacklight_launch_count(int reset) {
+    uint64_t v = g_launches;
+    if (reset) g_launches = 0;
+    return v;
+}
+
+}  // extern "C"

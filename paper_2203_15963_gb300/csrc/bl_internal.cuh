@@ -1,0 +1,59 @@
+// Internal data layout shared by the kernels and the host entry points.
+#pragma once
+#include <stdint.h>
+
+namespace bl {
+
+// Per-sample record written by the geodesic kernel and replayed by the transfer kernel:
+// sample position x,y,z and covariant k_x,k_y,k_z; the node on the sample's camera side
+// (same 6 values); the segment's affine length. k_t is constant per ray (Sec. 2.2) and is
+// kept in the ray header.
+constexpr int kRecVals = 13;
+template <class R> struct RecStride;
+template <> struct RecStride<double> { static constexpr int v = 14; };   // 112 B, 16-B aligned
+template <> struct RecStride<float> { static constexpr int v = 16; };    // 64 B
+
+constexpr int kChunk = 32;          // records per pool chunk
+constexpr int kMaxChunks = 128;     // chunks per ray -> at most 4096 samples per ray
+
+struct ImageDesc {
+    // camera (Sec. 2.1)
+    double cam_r, cam_th, cam_ph, u_p[3], k_p[3], width, psi;
+    int32_t n, nu_inf;
+    // metric and integrator (Sec. 2.2)
+    double mass, spin, r_in_over_rhor, tol_abs, tol_rel, ds_max, h0_frac;
+    int64_t max_steps;
+    int32_t flat, precision;
+    // grid and plasma (Secs. 2.4-2.5)
+    const float* prim;
+    int32_t nr, nt, nph, interp;
+    double r_min, r_max, gamma_ad, r_high, r_low, mu, ne_ni, sigma_cut, rho_unit, length_unit;
+    double freq;
+    // outputs
+    void* stokes;
+    int32_t dtype, pad_;
+    int32_t* status;
+    int32_t* steps;
+    double* end_state;
+    int32_t* samples;
+    int64_t ray_offset;     // first global ray index of this image
+    // filled by the camera-frame kernel
+    double x_cam[4], u_cam[4], kk[4], hh[4], vv[4];
+    double r_cam, r_hor;
+};
+
+struct RayHdr {
+    double kt;       // conserved covariant k_t
+    double nnorm;    // frequency normalisation n per unit nu (Sec. 2.1)
+    int32_t nrec;    // samples recorded
+    int32_t status;  // BL_RAY_*
+};
+
+struct Counters {
+    unsigned long long next_ray_geo;
+    unsigned long long next_ray_tr;
+    unsigned long long pool_next;
+    unsigned long long bad_rays;
+};
+
+}  // namespace bl

@@ -1,0 +1,884 @@
+// Kernels of the Blacklight hot path: camera frame, persistent geodesic kernel (FP64) and
+// persistent transfer kernel (FP64 or FP32). Included by bl_api.cu only.
+#pragma once
+#include "bl_internal.cuh"
+#include "bl_math.cuh"
+#include "../../include/blacklight.h"
+
+namespace bl {
+
+// ---------------------------------------------------------------------------------------
+// Camera frame (Sec. 2.1), one thread per image, FP64.
+// ---------------------------------------------------------------------------------------
+__global__ void camera_frame_kernel(ImageDesc* imgs, int n_images) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_images) return;
+    ImageDesc& im = imgs[q];
+    const double a = im.spin, m = im.mass;
+    const bool flat = im.flat != 0;
+    const double st = sin(im.cam_th), ct = cos(im.cam_th), sp = sin(im.cam_ph), cp = cos(im.cam_ph);
+    const double r = im.cam_r;
+    double x[4] = {0.0, st * (r * cp - a * sp), st * (r * sp + a * cp), r * ct};
+    KSGeom<double> G;
+    ks_geom<double>(x[1], x[2], x[3], a, m, flat, false, G);
+    // Jacobian columns d x^a / d (r, theta, phi)
+    const double J[3][3] = {{st * cp, ct * (r * cp - a * sp), st * (-r * sp - a * cp)},
+                            {st * sp, ct * (r * sp + a * cp), st * (r * cp - a * sp)},
+                            {ct, -r * st, 0.0}};
+    // velocity: spatial normal-frame vector v = J u^p, u^n = (1 + gamma(v, v))^1/2,
+    // u^t = u^n / alpha, u^a = v^a - beta^a u^t, alpha = (1 + f)^-1/2, beta^a = f l^a / (1 + f)
+    double v[3];
+    for (int c = 0; c < 3; ++c) v[c] = J[c][0] * im.u_p[0] + J[c][1] * im.u_p[1] + J[c][2] * im.u_p[2];
+    const double lv = G.l[1] * v[0] + G.l[2] * v[1] + G.l[3] * v[2];
+    const double un = sqrt(1.0 + v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + G.f * lv * lv);
+    double u[4];
+    u[0] = un * sqrt(1.0 + G.f);
+    for (int c = 0; c < 3; ++c) u[c + 1] = v[c] - G.f * G.l[c + 1] / (1.0 + G.f) * u[0];
+    double ul[4];
+    lower4(G, u, ul);
+    // covariant k_a = k_i d x^i / d x^a (r, theta, phi as functions of x, y, z)
+    double kl[4];
+    {
+        const double R2 = x[1] * x[1] + x[2] * x[2] + x[3] * x[3];
+        const double qq = R2 - a * a;
+        const double D = sqrt(qq * qq + 4.0 * a * a * x[3] * x[3]);
+        const double rr = G.r;
+        const double dr[3] = {rr * x[1] / D, rr * x[2] / D, x[3] * (rr * rr + a * a) / (rr * D)};
+        for (int c = 0; c < 3; ++c) kl[c + 1] = im.k_p[0] * dr[c];
+        if (im.k_p[1] != 0.0) {
+            const double zr = x[3] / rr;
+            const double s = sqrt(1.0 - zr * zr);
+            for (int c = 0; c < 3; ++c) {
+                const double dzr = ((c == 2 ? rr : 0.0) - x[3] * dr[c]) / (rr * rr);
+                kl[c + 1] += im.k_p[1] * (-dzr / s);
+            }
+        }
+        if (im.k_p[2] != 0.0) {
+            const double rho2 = x[1] * x[1] + x[2] * x[2];
+            const double dxy[3] = {-x[2] / rho2, x[1] / rho2, 0.0};
+            for (int c = 0; c < 3; ++c)
+                kl[c + 1] += im.k_p[2] * (dxy[c] + a / (rr * rr + a * a) * dr[c]);
+        }
+        // k_t from g^ab k_a k_b = 0 with k^t = g^tt k_t + g^ta k_a > 0
+        const double A = -1.0 - G.f;
+        double B = 0.0, C = 0.0;
+        const double lk = G.l[1] * kl[1] + G.l[2] * kl[2] + G.l[3] * kl[3];
+        B = G.f * lk;                                         // g^ta k_a = f l^a k_a
+        C = kl[1] * kl[1] + kl[2] * kl[2] + kl[3] * kl[3] - G.f * lk * lk;
+        const double disc = sqrt(B * B - A * C);
+        const double r1 = (-B + disc) / A, r2 = (-B - disc) / A;
+        kl[0] = (A * r1 + B > 0.0) ? r1 : r2;
+    }
+    // camera-frame metric g_{a'b'} and g^{a'b'} = g^ab + u^a u^b
+    double glo[4][4];
+    {
+        for (int al = 0; al < 4; ++al)
+            for (int be = 0; be < 4; ++be)
+                glo[al][be] = ((al == be) ? (al == 0 ? -1.0 : 1.0) : 0.0) + G.f * G.l[al] * G.l[be];
+    }
+    double gpl[3][3], gph[3][3];
+    for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) {
+            const int A_ = c + 1, B_ = d + 1;
+            gpl[c][d] = glo[A_][B_] - ul[A_] / ul[0] * glo[0][B_] - ul[B_] / ul[0] * glo[0][A_] +
+                        ul[A_] * ul[B_] / (ul[0] * ul[0]) * glo[0][0];
+            const double ghi = ((c == d) ? 1.0 : 0.0) - G.f * G.l[A_] * G.l[B_];
+            gph[c][d] = ghi + u[A_] * u[B_];
+        }
+    double Kl[3], Kh[3];
+    for (int c = 0; c < 3; ++c) Kl[c] = kl[c + 1] - ul[c + 1] / ul[0] * kl[0];
+    double Kt = -(u[0] * kl[0] + u[1] * kl[1] + u[2] * kl[2] + u[3] * kl[3]);
+    for (int c = 0; c < 3; ++c) Kh[c] = gph[c][0] * Kl[0] + gph[c][1] * Kl[1] + gph[c][2] * Kl[2];
+    double nk = 1.0 / sqrt(Kl[0] * Kh[0] + Kl[1] * Kh[1] + Kl[2] * Kh[2]);
+    for (int c = 0; c < 3; ++c) { Kl[c] *= nk; Kh[c] *= nk; }
+    Kt *= nk;
+    im.kk[0] = u[0] * Kt - (ul[1] * Kh[0] + ul[2] * Kh[1] + ul[3] * Kh[2]) / ul[0];
+    for (int c = 0; c < 3; ++c) im.kk[c + 1] = Kh[c] + u[c + 1] * Kt;
+    // vertical: Gram-Schmidt of U = z (y on the polar axis)
+    double U[3] = {0.0, 0.0, 1.0};
+    if (x[1] == 0.0 && x[2] == 0.0) { U[1] = 1.0; U[2] = 0.0; }
+    const double uk = U[0] * Kl[0] + U[1] * Kl[1] + U[2] * Kl[2];
+    double vh[3], vl[3];
+    for (int c = 0; c < 3; ++c) vh[c] = U[c] - uk * Kh[c];
+    for (int c = 0; c < 3; ++c) vl[c] = gpl[c][0] * vh[0] + gpl[c][1] * vh[1] + gpl[c][2] * vh[2];
+    const double nv = 1.0 / sqrt(vl[0] * vh[0] + vl[1] * vh[1] + vl[2] * vh[2]);
+    for (int c = 0; c < 3; ++c) { vh[c] *= nv; vl[c] *= nv; }
+    // horizontal: h^a = [abc] v_b K_c / sqrt(det g')
+    const double det = gpl[0][0] * (gpl[1][1] * gpl[2][2] - gpl[1][2] * gpl[2][1]) -
+                       gpl[0][1] * (gpl[1][0] * gpl[2][2] - gpl[1][2] * gpl[2][0]) +
+                       gpl[0][2] * (gpl[1][0] * gpl[2][1] - gpl[1][1] * gpl[2][0]);
+    const double isd = 1.0 / sqrt(det);
+    const double hh[3] = {(vl[1] * Kl[2] - vl[2] * Kl[1]) * isd, (vl[2] * Kl[0] - vl[0] * Kl[2]) * isd,
+                          (vl[0] * Kl[1] - vl[1] * Kl[0]) * isd};
+    const double cps = cos(im.psi), sps = sin(im.psi);
+    im.hh[0] = 0.0;
+    im.vv[0] = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        const double Hc = hh[c] * cps - vh[c] * sps;
+        const double Vc = vh[c] * cps + hh[c] * sps;
+        im.hh[0] -= ul[c + 1] / ul[0] * Hc;
+        im.vv[0] -= ul[c + 1] / ul[0] * Vc;
+        im.hh[c + 1] = Hc;
+        im.vv[c + 1] = Vc;
+    }
+    for (int al = 0; al < 4; ++al) { im.x_cam[al] = x[al]; im.u_cam[al] = u[al]; }
+    im.r_cam = r;
+    const double d = m * m - a * a;
+    im.r_hor = m + sqrt(d > 0.0 ? d : 0.0);
+}
+
+// ---------------------------------------------------------------------------------------
+// Ray bookkeeping helpers
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int find_image(const ImageDesc* imgs, int n_images, int64_t ray) {
+    int q = 0;
+    while (q + 1 < n_images && imgs[q + 1].ray_offset <= ray) ++q;
+    return q;
+}
+
+// Pixel order inside an image: Morton (Z) order when n is a power of two so that a warp
+// covers a compact 8x4 patch of the image, row-major otherwise.
+__device__ __forceinline__ void pixel_of(int64_t p, int n, int& i, int& j) {
+    if ((n & (n - 1)) == 0) {
+        uint32_t xi = 0, yj = 0;
+        for (int b = 0; b < 16; ++b) {
+            xi |= (uint32_t)((p >> (2 * b)) & 1) << b;
+            yj |= (uint32_t)((p >> (2 * b + 1)) & 1) << b;
+        }
+        i = (int)xi;
+        j = (int)yj;
+    } else {
+        i = (int)(p % n);
+        j = (int)(p / n);
+    }
+}
+
+// Warp-aggregated fetch-and-add: every lane that calls it gets a distinct index.
+__device__ __forceinline__ unsigned long long warp_fetch_add(unsigned long long* ctr) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+// Pixel initial state (Sec. 2.1, plane-parallel): x_pix = x + a H + b V, k^a = K^a,
+// k^t from the null condition (unique positive root outside the ergosphere, lesser positive
+// root inside), k_a = g_ab k^b.
+__device__ __forceinline__ void pixel_state(const ImageDesc& im, int i, int j, double y[8],
+                                            double& nnorm) {
+    const double n = im.n;
+    const double aa = (i - 0.5 * n + 0.5) * im.width / n;
+    const double bb = (j - 0.5 * n + 0.5) * im.width / n;
+    for (int al = 0; al < 4; ++al) y[al] = im.x_cam[al] + aa * im.hh[al] + bb * im.vv[al];
+    KSGeom<double> G;
+    ks_geom<double>(y[1], y[2], y[3], im.spin, im.mass, im.flat != 0, false, G);
+    const double ka[3] = {im.kk[1], im.kk[2], im.kk[3]};
+    // g_tt (k^t)^2 + 2 g_ta k^a k^t + g_ab k^a k^b = 0
+    const double lk = G.l[1] * ka[0] + G.l[2] * ka[1] + G.l[3] * ka[2];
+    const double A = -1.0 + G.f;
+    const double B = G.f * lk;
+    const double C = ka[0] * ka[0] + ka[1] * ka[1] + ka[2] * ka[2] + G.f * lk * lk;
+    double kt;
+    if (A == 0.0) {
+        kt = -C / (2.0 * B);
+    } else {
+        const double disc = sqrt(B * B - A * C);
+        const double r1 = (-B + disc) / A, r2 = (-B - disc) / A;
+        if (A < 0.0) {
+            kt = r1 > 0.0 ? r1 : r2;
+        } else {
+            const double lo = fmin(r1, r2), hi = fmax(r1, r2);
+            kt = lo > 0.0 ? lo : hi;
+        }
+    }
+    const double ku[4] = {kt, ka[0], ka[1], ka[2]};
+    double kl[4];
+    lower4(G, ku, kl);
+    for (int al = 0; al < 4; ++al) y[4 + al] = kl[al];
+    if (im.nu_inf) {
+        nnorm = 1.0 / (-kl[0]);
+    } else {
+        nnorm = 1.0 / -(kl[0] * im.u_cam[0] + kl[1] * im.u_cam[1] + kl[2] * im.u_cam[2] + kl[3] * im.u_cam[3]);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Persistent geodesic kernel (Sec. 2.2). Each lane owns one ray at a time and advances it
+// by one Dormand-Prince attempt per loop iteration; a lane whose ray terminates takes the
+// next ray from the global queue, so uneven step counts do not idle the warp. Accepted steps
+// emit sample records (midpoint, or quartic sub-samples when the step is longer than ds_max
+// in proper length and reaches into the grid) into a pool of fixed-size chunks.
+// ---------------------------------------------------------------------------------------
+// Dormand-Prince RK5(4)7M coefficients (Table tab:dp).
+#define DP_A21 (1.0 / 5.0)
+#define DP_A31 (3.0 / 40.0)
+#define DP_A32 (9.0 / 40.0)
+#define DP_A41 (44.0 / 45.0)
+#define DP_A42 (-56.0 / 15.0)
+#define DP_A43 (32.0 / 9.0)
+#define DP_A51 (19372.0 / 6561.0)
+#define DP_A52 (-25360.0 / 2187.0)
+#define DP_A53 (64448.0 / 6561.0)
+#define DP_A54 (-212.0 / 729.0)
+#define DP_A61 (9017.0 / 3168.0)
+#define DP_A62 (-355.0 / 33.0)
+#define DP_A63 (46732.0 / 5247.0)
+#define DP_A64 (49.0 / 176.0)
+#define DP_A65 (-5103.0 / 18656.0)
+#define DP_B1 (35.0 / 384.0)
+#define DP_B3 (500.0 / 1113.0)
+#define DP_B4 (125.0 / 192.0)
+#define DP_B5 (-2187.0 / 6784.0)
+#define DP_B6 (11.0 / 84.0)
+// error weights b5 - b4
+#define DP_E1 (35.0 / 384.0 - 5179.0 / 57600.0)
+#define DP_E3 (500.0 / 1113.0 - 7571.0 / 16695.0)
+#define DP_E4 (125.0 / 192.0 - 393.0 / 640.0)
+#define DP_E5 (-2187.0 / 6784.0 + 92097.0 / 339200.0)
+#define DP_E6 (11.0 / 84.0 - 187.0 / 2100.0)
+#define DP_E7 (-1.0 / 40.0)
+// fourth-order midpoint weights (applied with h/2)
+#define DP_M1 (6025192743.0 / 30085553152.0)
+#define DP_M3 (51252292925.0 / 65400821598.0)
+#define DP_M4 (-2691868925.0 / 45128329728.0)
+#define DP_M5 (187940372067.0 / 1594534317056.0)
+#define DP_M6 (-1776094331.0 / 19743644256.0)
+#define DP_M7 (11237099.0 / 235043384.0)
+
+template <class R>
+struct RecordSink {
+    R* pool;
+    int32_t* chunks;         // [rays][kMaxChunks]
+    unsigned long long pool_chunks;
+    Counters* ctr;
+};
+
+// Append one record for `ray`; returns false when the store is full.
+template <class R>
+__device__ __forceinline__ bool append_record(const RecordSink<R>& S, int64_t ray, int32_t& nrec,
+                                              const double ys[8], const double yn[8], double dl) {
+    const int32_t slot = nrec % kChunk;
+    const int32_t ch = nrec / kChunk;
+    if (ch >= kMaxChunks) return false;
+    int32_t* tab = S.chunks + ray * kMaxChunks;
+    if (slot == 0) {
+        const unsigned long long c = warp_fetch_add(&S.ctr->pool_next);
+        if (c >= S.pool_chunks) return false;
+        tab[ch] = (int32_t)c;
+    }
+    const int64_t idx = (int64_t)tab[ch] * kChunk + slot;
+    R* rec = S.pool + idx * RecStride<R>::v;
+    rec[0] = (R)ys[1]; rec[1] = (R)ys[2]; rec[2] = (R)ys[3];
+    rec[3] = (R)ys[5]; rec[4] = (R)ys[6]; rec[5] = (R)ys[7];
+    rec[6] = (R)yn[1]; rec[7] = (R)yn[2]; rec[8] = (R)yn[3];
+    rec[9] = (R)yn[5]; rec[10] = (R)yn[6]; rec[11] = (R)yn[7];
+    rec[12] = (R)dl;
+    ++nrec;
+    return true;
+}
+
+template <class R>
+__global__ void __launch_bounds__(128) geodesic_kernel(const ImageDesc* __restrict__ imgs,
+                                                       int n_images, int64_t total_rays,
+                                                       RayHdr* __restrict__ hdr,
+                                                       RecordSink<R> sink, int record) {
+    Counters* ctr = sink.ctr;
+    bool active = false;
+    int64_t ray = 0;
+    int q = 0, pi = 0, pj = 0;
+    double y[8], f1[8];
+    double h = 0.0, nnorm = 0.0;
+    bool been_inside = false, prev_rej = false;
+    int64_t attempts = 0;
+    int32_t nrec = 0, status = 0;
+    double r_cam = 0.0, r_in = 0.0, a = 0.0, m = 0.0, ds_max = 0.0, r_grid = 0.0;
+    double tol_abs = 0.0, tol_rel = 0.0;
+    int64_t max_steps = 0;
+    bool flat = false;
+
+    while (true) {
+        if (!active) {
+            ray = (int64_t)warp_fetch_add(&ctr->next_ray_geo);
+            if (ray >= total_rays) break;
+            q = find_image(imgs, n_images, ray);
+            const ImageDesc& im = imgs[q];
+            pixel_of(ray - im.ray_offset, im.n, pi, pj);
+            pixel_state(im, pi, pj, y, nnorm);
+            a = im.spin; m = im.mass; flat = im.flat != 0;
+            r_cam = im.r_cam;
+            r_in = im.r_in_over_rhor * im.r_hor;
+            ds_max = im.ds_max;
+            r_grid = im.r_max;
+            tol_abs = im.tol_abs; tol_rel = im.tol_rel;
+            max_steps = im.max_steps;
+            geodesic_rhs(y, a, m, flat, f1);
+            h = -im.h0_frac * (r_cam - im.r_hor);
+            been_inside = ks_r<double>(y[1], y[2], y[3], a) < r_cam;
+            prev_rej = false;
+            attempts = 0;
+            nrec = 0;
+            status = 0;
+            active = true;
+        }
+        // ---- one Dormand-Prince attempt ----
+        double k2[8], k3[8], k4[8], k5[8], k6[8], k7[8], ys[8], y5[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) ys[c] = y[c] + h * (DP_A21 * f1[c]);
+        geodesic_rhs(ys, a, m, flat, k2);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) ys[c] = y[c] + h * (DP_A31 * f1[c] + DP_A32 * k2[c]);
+        geodesic_rhs(ys, a, m, flat, k3);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) ys[c] = y[c] + h * (DP_A41 * f1[c] + DP_A42 * k2[c] + DP_A43 * k3[c]);
+        geodesic_rhs(ys, a, m, flat, k4);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            ys[c] = y[c] + h * (DP_A51 * f1[c] + DP_A52 * k2[c] + DP_A53 * k3[c] + DP_A54 * k4[c]);
+        geodesic_rhs(ys, a, m, flat, k5);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            ys[c] = y[c] + h * (DP_A61 * f1[c] + DP_A62 * k2[c] + DP_A63 * k3[c] + DP_A64 * k4[c] +
+                                DP_A65 * k5[c]);
+        geodesic_rhs(ys, a, m, flat, k6);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            y5[c] = y[c] + h * (DP_B1 * f1[c] + DP_B3 * k3[c] + DP_B4 * k4[c] + DP_B5 * k5[c] + DP_B6 * k6[c]);
+        geodesic_rhs(y5, a, m, flat, k7);
+        // eps = max_c |err_c| / sc_c, tracked as the largest fraction (num / den) by
+        // cross-multiplication so that only one division is needed
+        double num = 0.0, den = 1.0;
+        bool finite = true;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const double err = fabs(h * (DP_E1 * f1[c] + DP_E3 * k3[c] + DP_E4 * k4[c] + DP_E5 * k5[c] +
+                                         DP_E6 * k6[c] + DP_E7 * k7[c]));
+            const double sc = tol_abs + tol_rel * fmax(fabs(y[c]), fabs(y5[c]));
+            finite = finite && isfinite(err) && isfinite(y5[c]);
+            if (err * den > num * sc) { num = err; den = sc; }
+        }
+        const double eps = num / den;
+        ++attempts;
+        bool done = false;
+        if (!finite) {
+            status = BL_RAY_NAN;
+            done = true;
+        } else if (eps <= 1.0) {
+            // accepted: samples of this step (camera side first)
+            if (record) {
+                double ym[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    ym[c] = y[c] + 0.5 * h * (DP_M1 * f1[c] + DP_M3 * k3[c] + DP_M4 * k4[c] +
+                                              DP_M5 * k5[c] + DP_M6 * k6[c] + DP_M7 * k7[c]);
+                const double r0 = ks_r<double>(y[1], y[2], y[3], a);
+                const double r1 = ks_r<double>(y5[1], y5[2], y5[3], a);
+                KSGeom<double> Gm;
+                ks_geom<double>(ym[1], ym[2], ym[3], a, m, flat, false, Gm);
+                const double rmin = fmin(Gm.r, fmin(r0, r1));
+                int nsub = 1;
+                if (rmin < r_grid) {
+                    // ds/dl = (g_pq k^p k^q)^1/2 = alpha |k^t| for a null ray
+                    const double L = -ym[4] + Gm.l[1] * ym[5] + Gm.l[2] * ym[6] + Gm.l[3] * ym[7];
+                    const double kt_up = -ym[4] + Gm.f * L;
+                    const double ds = fabs(h) * fabs(kt_up) / sqrt(1.0 + Gm.f);
+                    if (ds > ds_max) {
+                        const double nd = ceil(ds / ds_max);
+                        nsub = nd > 4096.0 ? 4097 : (int)nd;
+                    }
+                }
+                bool ok = true;
+                if (nsub == 1) {
+                    ok = append_record(sink, ray, nrec, ym, y, fabs(h));
+                } else {
+                    // quartic through y0, y1, h f0, h f1 and y_mid (Shampine 1986)
+                    double c2[8], c3[8], c4[8], d0[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        d0[c] = h * f1[c];
+                        const double D1 = y5[c] - y[c] - d0[c];
+                        const double D2 = h * k7[c] - d0[c];
+                        const double D3 = ym[c] - y[c] - 0.5 * d0[c];
+                        c2[c] = -5.0 * D1 + D2 + 16.0 * D3;
+                        c3[c] = 14.0 * D1 - 3.0 * D2 - 32.0 * D3;
+                        c4[c] = -8.0 * D1 + 2.0 * D2 + 16.0 * D3;
+                    }
+                    const double inv = 1.0 / nsub;
+                    if (sizeof(R) == sizeof(float)) {
+                        // float records: evaluate the quartic in FP32 about y0 (the stored
+                        // values carry FP32 precision anyway)
+                        float y0f[8], d0f[8], c2f[8], c3f[8], c4f[8];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            y0f[c] = (float)y[c]; d0f[c] = (float)d0[c]; c2f[c] = (float)c2[c];
+                            c3f[c] = (float)c3[c]; c4f[c] = (float)c4[c];
+                        }
+                        const float invf = 1.0f / (float)nsub;
+                        for (int s = 0; s < nsub && ok; ++s) {
+                            double ysm[8], ynd[8];
+                            const float ts = (s + 0.5f) * invf, tn = s * invf;
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                ysm[c] = y0f[c] + ts * (d0f[c] + ts * (c2f[c] + ts * (c3f[c] + ts * c4f[c])));
+                                ynd[c] = (s == 0) ? y[c]
+                                                  : y0f[c] + tn * (d0f[c] + tn * (c2f[c] + tn * (c3f[c] + tn * c4f[c])));
+                            }
+                            ok = append_record(sink, ray, nrec, ysm, ynd, fabs(h) * inv);
+                        }
+                    } else {
+                        for (int s = 0; s < nsub && ok; ++s) {
+                            double ysm[8], ynd[8];
+                            const double ts = (s + 0.5) * inv, tn = s * inv;
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                ysm[c] = y[c] + ts * (d0[c] + ts * (c2[c] + ts * (c3[c] + ts * c4[c])));
+                                ynd[c] = (s == 0) ? y[c]
+                                                  : y[c] + tn * (d0[c] + tn * (c2[c] + tn * (c3[c] + tn * c4[c])));
+                            }
+                            ok = append_record(sink, ray, nrec, ysm, ynd, fabs(h) * inv);
+                        }
+                    }
+                }
+                if (!ok) { status = BL_RAY_OVERFLOW; done = true; }
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) { y[c] = y5[c]; f1[c] = k7[c]; }
+            double fac = (eps == 0.0) ? 10.0 : 0.9 * pow(eps, -0.2);
+            fac = fmin(10.0, fmax(0.2, fac));
+            if (prev_rej) fac = fmin(fac, 1.0);
+            h *= fac;
+            prev_rej = false;
+            if (!done) {
+                const double rr = ks_r<double>(y[1], y[2], y[3], a);
+                if (rr < r_in) { status = BL_RAY_HORIZON; done = true; }
+                else if (been_inside && rr > r_cam) { status = BL_RAY_ESCAPED; done = true; }
+                else if (rr < r_cam) been_inside = true;
+            }
+        } else {
+            h *= fmax(0.2, 0.9 * pow(eps, -0.2));
+            prev_rej = true;
+        }
+        if (!done) {
+            if (fabs(h) < 1e-12 * ks_r<double>(y[1], y[2], y[3], a)) { status = BL_RAY_UNDERFLOW; done = true; }
+            else if (attempts >= max_steps) { status = BL_RAY_MAX_STEPS; done = true; }
+        }
+        if (done) {
+            const ImageDesc& im = imgs[q];
+            const int64_t pix = (int64_t)pj * im.n + pi;
+            if (im.status) im.status[pix] = status;
+            if (im.steps) im.steps[pix] = (int32_t)(attempts < 2147483647 ? attempts : 2147483647);
+            if (im.end_state)
+                for (int c = 0; c < 8; ++c) im.end_state[pix * 8 + c] = y[c];
+            if (im.samples) im.samples[pix] = nrec;
+            RayHdr hd;
+            hd.kt = y[4];
+            hd.nnorm = nnorm;
+            hd.nrec = nrec;
+            hd.status = status;
+            hdr[ray] = hd;
+            if (status != BL_RAY_HORIZON && status != BL_RAY_ESCAPED)
+                atomicAdd(&ctr->bad_rays, 1ull);
+            active = false;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Plasma state at a sample (Secs. 2, 2.4, 2.5) in arithmetic T.
+// ---------------------------------------------------------------------------------------
+template <class T>
+struct Plasma {
+    T u[4], b[4];         // contravariant CKS
+    T ul[4];              // covariant u
+    T ne, th, bg, bsq;
+};
+
+template <class T>
+__device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], const KSGeom<T>& G,
+                                          Plasma<T>& P) {
+    const T a = (T)im.spin;
+    const T r = G.r;
+    if (!(r >= (T)im.r_min && r <= (T)im.r_max)) return false;
+    T cth = x[2] / r;
+    cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
+    const T th = acos(cth);
+    const T sth = sqrt(T(1) - cth * cth);
+    const T twopi = T(2.0 * kPi);
+    T ph = atan2(x[1], x[0]) - atan(a / r);
+    ph = fmod(ph, twopi);
+    if (ph < T(0)) ph += twopi;
+    if (ph >= twopi) ph -= twopi;
+    const int nr = im.nr, nt = im.nt, np = im.nph;
+    const float* __restrict__ prim = im.prim;
+    const size_t plane = (size_t)np * nt * nr;
+    T pv[8];
+    const T dlr = log((T)im.r_max / (T)im.r_min) / T(nr);
+    const T dth = T(kPi) / T(nt);
+    const T dph = twopi / T(np);
+    if (im.interp == 0) {
+        int i = (int)floor(log(r / (T)im.r_min) / dlr);
+        int j = (int)floor(th / dth);
+        int k = (int)floor(ph / dph);
+        i = min(max(i, 0), nr - 1);
+        j = min(max(j, 0), nt - 1);
+        k = ((k % np) + np) % np;
+        const size_t base = ((size_t)k * nt + j) * nr + i;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) pv[v] = (T)__ldg(prim + v * plane + base);
+    } else {
+        int i0, j0;
+        T wr, wt;
+        {
+            T fi = log(r / (T)im.r_min) / dlr - T(0.5);
+            if (nr == 1) { i0 = 0; wr = T(0); }
+            else {
+                fi = fi < T(0) ? T(0) : (fi > T(nr - 1) ? T(nr - 1) : fi);
+                i0 = (int)floor(fi);
+                if (i0 > nr - 2) i0 = nr - 2;
+                wr = fi - T(i0);
+            }
+        }
+        {
+            T fj = th / dth - T(0.5);
+            if (nt == 1) { j0 = 0; wt = T(0); }
+            else {
+                fj = fj < T(0) ? T(0) : (fj > T(nt - 1) ? T(nt - 1) : fj);
+                j0 = (int)floor(fj);
+                if (j0 > nt - 2) j0 = nt - 2;
+                wt = fj - T(j0);
+            }
+        }
+        const int i1 = nr == 1 ? 0 : i0 + 1, j1 = nt == 1 ? 0 : j0 + 1;
+        const T fk = ph / dph - T(0.5);
+        const T fkf = floor(fk);
+        const int k0 = (((int)fkf) % np + np) % np;
+        const int k1 = (k0 + 1) % np;
+        const T wp = fk - fkf;
+        const size_t o00 = ((size_t)k0 * nt + j0) * nr, o01 = ((size_t)k0 * nt + j1) * nr;
+        const size_t o10 = ((size_t)k1 * nt + j0) * nr, o11 = ((size_t)k1 * nt + j1) * nr;
+        const T w000 = (T(1) - wp) * (T(1) - wt) * (T(1) - wr), w001 = (T(1) - wp) * (T(1) - wt) * wr;
+        const T w010 = (T(1) - wp) * wt * (T(1) - wr), w011 = (T(1) - wp) * wt * wr;
+        const T w100 = wp * (T(1) - wt) * (T(1) - wr), w101 = wp * (T(1) - wt) * wr;
+        const T w110 = wp * wt * (T(1) - wr), w111 = wp * wt * wr;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const float* pp = prim + v * plane;
+            pv[v] = w000 * (T)__ldg(pp + o00 + i0) + w001 * (T)__ldg(pp + o00 + i1) +
+                    w010 * (T)__ldg(pp + o01 + i0) + w011 * (T)__ldg(pp + o01 + i1) +
+                    w100 * (T)__ldg(pp + o10 + i0) + w101 * (T)__ldg(pp + o10 + i1) +
+                    w110 * (T)__ldg(pp + o11 + i0) + w111 * (T)__ldg(pp + o11 + i1);
+        }
+    }
+    // spherical -> Cartesian KS vectors (Jacobian columns d x^a / d(r, theta, phi))
+    T sph, cph;
+    sincos(ph, &sph, &cph);
+    const T J[3][3] = {{sth * cph, cth * (r * cph - a * sph), sth * (-r * sph - a * cph)},
+                       {sth * sph, cth * (r * sph + a * cph), sth * (r * cph - a * sph)},
+                       {cth, -r * sth, T(0)}};
+    T v[3], B[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        v[c] = J[c][0] * pv[2] + J[c][1] * pv[3] + J[c][2] * pv[4];
+        B[c] = J[c][0] * pv[5] + J[c][1] * pv[6] + J[c][2] * pv[7];
+    }
+    const T f = G.f;
+    const T lv = G.l[1] * v[0] + G.l[2] * v[1] + G.l[3] * v[2];
+    const T un = sqrt(T(1) + v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + f * lv * lv);
+    P.u[0] = un * sqrt(T(1) + f);
+    const T sh = f / (T(1) + f) * P.u[0];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) P.u[c + 1] = v[c] - G.l[c + 1] * sh;
+    lower4(G, P.u, P.ul);
+    P.b[0] = B[0] * P.ul[1] + B[1] * P.ul[2] + B[2] * P.ul[3];
+    const T iut = T(1) / P.u[0];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) P.b[c + 1] = (B[c] + P.b[0] * P.u[c + 1]) * iut;
+    P.bsq = dot4(G, P.b, P.b);
+    const T rho = pv[0];
+    const T p = T(im.gamma_ad - 1.0) * pv[1];
+    if (!(rho > T(0)) || !(p > T(0)) || !(P.bsq > T(0))) return false;
+    if (P.bsq / rho > (T)im.sigma_cut) return false;
+    const T binv = P.bsq / (T(2) * p);
+    const T b2 = binv * binv;
+    const T ratio = ((T)im.r_high + b2 * (T)im.r_low) / (T(1) + b2);
+    const T rr = (T)im.ne_ni;
+    const T th_e = T(im.mu * kMp / kMe) * (p / rho) * (rr + T(1)) / (rr + ratio);
+    if (!(th_e >= T(0.05))) return false;
+    P.th = th_e;
+    P.ne = rho * T(im.rho_unit / (im.mu * kMp)) / (T(1) + T(1) / rr);
+    P.bg = sqrt(P.bsq) * T(kC * sqrt(4.0 * kPi * im.rho_unit));
+    return true;
+}
+
+// Fluid-frame basis: e3 along the photon's spatial direction, e2 along the field projected
+// perpendicular to e3, e1^a = [abcd] u_b e2_c e3_d (sqrt(-g) = 1 in Cartesian KS).
+template <class T>
+__device__ __forceinline__ void fluid_basis(const KSGeom<T>& G, const Plasma<T>& P, const T kl[4],
+                                            const T ku[4], T e1[4], T e2[4], T e1l[4], T e2l[4]) {
+    const T kdu = kl[0] * P.u[0] + kl[1] * P.u[1] + kl[2] * P.u[2] + kl[3] * P.u[3];
+    const T iw = T(-1) / kdu;
+    T e3[4], e3l[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { e3[c] = (ku[c] + kdu * P.u[c]) * iw; e3l[c] = (kl[c] + kdu * P.ul[c]) * iw; }
+    const T bu = P.b[0] * P.ul[0] + P.b[1] * P.ul[1] + P.b[2] * P.ul[2] + P.b[3] * P.ul[3];
+    T bp[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) bp[c] = P.b[c] + bu * P.u[c];
+    T b3 = bp[0] * e3l[0] + bp[1] * e3l[1] + bp[2] * e3l[2] + bp[3] * e3l[3];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) bp[c] -= b3 * e3[c];
+    T bpl[4];
+    lower4(G, bp, bpl);
+    T bb = bp[0] * bpl[0] + bp[1] * bpl[1] + bp[2] * bpl[2] + bp[3] * bpl[3];
+    const T tiny = sizeof(T) == 8 ? T(1e-20) : T(1e-10);
+    if (!(bb > tiny * P.bsq)) {
+        // field along the ray: any transverse direction (only I and V couple there)
+        for (int t = 0; t < 2; ++t) {
+            T tv[4] = {T(0), T(0), T(0), T(0)};
+            tv[t == 0 ? 3 : 1] = T(1);
+            T tl[4];
+            lower4(G, tv, tl);
+            const T pu = tl[0] * P.u[0] + tl[1] * P.u[1] + tl[2] * P.u[2] + tl[3] * P.u[3];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) bp[c] = tv[c] + pu * P.u[c];
+            b3 = bp[0] * e3l[0] + bp[1] * e3l[1] + bp[2] * e3l[2] + bp[3] * e3l[3];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) bp[c] -= b3 * e3[c];
+            lower4(G, bp, bpl);
+            bb = bp[0] * bpl[0] + bp[1] * bpl[1] + bp[2] * bpl[2] + bp[3] * bpl[3];
+            if (bb > T(1e-6)) break;
+        }
+    }
+    const T ib = rsqrt(bb);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { e2[c] = bp[c] * ib; e2l[c] = bpl[c] * ib; }
+    // e1^a = (-1)^a det(minor_a) of the rows (u_l, e2_l, e3_l)
+    const T* A0 = P.ul;
+    const T* A1 = e2l;
+    const T* A2 = e3l;
+    auto det3c = [&](int c0, int c1, int c2) -> T {
+        return A0[c0] * (A1[c1] * A2[c2] - A1[c2] * A2[c1]) - A0[c1] * (A1[c0] * A2[c2] - A1[c2] * A2[c0]) +
+               A0[c2] * (A1[c0] * A2[c1] - A1[c1] * A2[c0]);
+    };
+    e1[0] = det3c(1, 2, 3);
+    e1[1] = -det3c(0, 2, 3);
+    e1[2] = det3c(0, 1, 3);
+    e1[3] = -det3c(0, 1, 2);
+    lower4(G, e1, e1l);
+}
+
+// Stokes from the coherency tensor in the basis (e1, e2): N11 = (I+Q)/2, N22 = (I-Q)/2,
+// N12 = (U + iV)/2.
+template <class T>
+__device__ __forceinline__ void coh_to_stokes(const Coh<T>& n, const T e1l[4], const T e2l[4], T s[4]) {
+    T R[4][4], I[4][4];
+    coh_unpack(n, R, I);
+    T n11 = T(0), n22 = T(0), n12r = T(0), n12i = T(0);
+#pragma unroll
+    for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+        for (int b_ = 0; b_ < 4; ++b_) {
+            n11 += e1l[a_] * e1l[b_] * R[a_][b_];
+            n22 += e2l[a_] * e2l[b_] * R[a_][b_];
+            n12r += e1l[a_] * e2l[b_] * R[a_][b_];
+            n12i += e1l[a_] * e2l[b_] * I[a_][b_];
+        }
+    s[0] = n11 + n22;
+    s[1] = n11 - n22;
+    s[2] = T(2) * n12r;
+    s[3] = T(2) * n12i;
+}
+
+template <class T>
+__device__ __forceinline__ void stokes_to_coh(const T e1[4], const T e2[4], const T s[4], Coh<T>& n) {
+    const T p = T(0.5) * (s[0] + s[1]), qv = T(0.5) * (s[0] - s[1]), uu = T(0.5) * s[2], vv = T(0.5) * s[3];
+    int k = 0;
+#pragma unroll
+    for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+        for (int b_ = a_; b_ < 4; ++b_) {
+            n.re[k++] = p * e1[a_] * e1[b_] + qv * e2[a_] * e2[b_] + uu * (e1[a_] * e2[b_] + e2[a_] * e1[b_]);
+        }
+    k = 0;
+#pragma unroll
+    for (int a_ = 0; a_ < 4; ++a_)
+#pragma unroll
+        for (int b_ = a_ + 1; b_ < 4; ++b_) n.im[k++] = vv * (e1[a_] * e2[b_] - e2[a_] * e1[b_]);
+}
+
+// ---------------------------------------------------------------------------------------
+// Persistent transfer kernel (Sec. 2.3.2). Each lane replays one ray's samples from the
+// source end to the camera, one sample per loop iteration: merged N half-steps by the
+// predictor-corrector (stage 1 at the previous sample, stage 2 at the node it shares with
+// the current one), then, where the sample carries plasma, N -> S in the fluid frame, the
+// exact constant-coefficient Stokes step, and S -> N. A lane whose ray is done reads out the
+// Stokes parameters in the camera basis (H, V) and takes the next ray.
+// ---------------------------------------------------------------------------------------
+template <class T, class R>
+__global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restrict__ imgs,
+                                                       int n_images, int64_t total_rays,
+                                                       const RayHdr* __restrict__ hdr,
+                                                       const R* __restrict__ pool,
+                                                       const int32_t* __restrict__ chunks,
+                                                       Counters* ctr) {
+    bool active = false;
+    int64_t ray = 0;
+    int q = 0, pi = 0, pj = 0;
+    int32_t idx = 0;
+    Coh<T> N;
+    bool started = false;
+    T prev[kRecVals];
+    T kt = T(0), a = T(0), m = T(0), nu_norm = T(0);
+    bool flat = false;
+
+    while (true) {
+        if (!active) {
+            ray = (int64_t)warp_fetch_add(&ctr->next_ray_tr);
+            if (ray >= total_rays) break;
+            q = find_image(imgs, n_images, ray);
+            const ImageDesc& im = imgs[q];
+            pixel_of(ray - im.ray_offset, im.n, pi, pj);
+            const RayHdr hd = hdr[ray];
+            if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) {
+                const int64_t npix = (int64_t)im.n * im.n;
+                const int64_t pix = (int64_t)pj * im.n + pi;
+                const double val = hd.status == BL_RAY_OVERFLOW ? nan("") : 0.0;
+                for (int s = 0; s < 4; ++s) {
+                    if (im.dtype == 0) ((double*)im.stokes)[s * npix + pix] = val;
+                    else ((float*)im.stokes)[s * npix + pix] = (float)val;
+                }
+                continue;
+            }
+            idx = hd.nrec - 1;
+            kt = (T)hd.kt;
+            nu_norm = (T)(hd.nnorm * im.freq);
+            a = (T)im.spin;
+            m = (T)im.mass;
+            flat = im.flat != 0;
+#pragma unroll
+            for (int c = 0; c < 10; ++c) N.re[c] = T(0);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) N.im[c] = T(0);
+            started = false;
+            active = true;
+        }
+        const ImageDesc& im = imgs[q];
+        // load record idx
+        T cur[kRecVals];
+        {
+            const int32_t ch = chunks[ray * kMaxChunks + idx / kChunk];
+            const R* rec = pool + ((int64_t)ch * kChunk + (idx % kChunk)) * RecStride<R>::v;
+#pragma unroll
+            for (int c = 0; c < kRecVals; ++c) cur[c] = (T)rec[c];
+        }
+        if (started) {
+            // merged N half-steps from the previous sample to this one
+            T A0[4][4], A1[4][4];
+            const T kp[4] = {kt, prev[3], prev[4], prev[5]};
+            const T kn[4] = {kt, prev[9], prev[10], prev[11]};
+            transport_matrix<T>(prev, kp, a, m, flat, A0);
+            transport_matrix<T>(prev + 6, kn, a, m, flat, A1);
+            coh_pc_step(N, A0, A1, T(0.5) * (prev[12] + cur[12]));
+        }
+        {
+            const T xs[3] = {cur[0], cur[1], cur[2]};
+            KSGeom<T> G;
+            ks_geom<T>(xs[0], xs[1], xs[2], a, m, flat, false, G);
+            Plasma<T> P;
+            if (plasma_at<T>(im, xs, G, P)) {
+                const T kl[4] = {kt, cur[3], cur[4], cur[5]};
+                T ku[4];
+                raise4(G, kl, ku);
+                const T kdu = kl[0] * P.u[0] + kl[1] * P.u[1] + kl[2] * P.u[2] + kl[3] * P.u[3];
+                const T kdb = kl[0] * P.b[0] + kl[1] * P.b[1] + kl[2] * P.b[2] + kl[3] * P.b[3];
+                const T nu_fl = nu_norm * (-kdu);
+                T cth = kdb / ((-kdu) * sqrt(P.bsq));
+                cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
+                T co[8];
+                synchrotron_coefficients<T>(P.ne, P.th, P.bg, nu_fl, cth, co);
+                const T g = (T)im.freq / nu_fl;
+                const T path = (T)im.length_unit * (-kdu);
+                const T eg = g * g * g * path;
+                const T coef[8] = {co[0] * eg, co[1] * eg, co[2] * eg, co[3] * path,
+                                   co[4] * path, co[5] * path, co[6] * path, co[7] * path};
+                T e1[4], e2[4], e1l[4], e2l[4];
+                fluid_basis<T>(G, P, kl, ku, e1, e2, e1l, e2l);
+                T s0[4], s1[4];
+                coh_to_stokes(N, e1l, e2l, s0);
+                stokes_step<T>(coef, s0, cur[12], s1);
+                stokes_to_coh(e1, e2, s1, N);
+                started = true;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kRecVals; ++c) prev[c] = cur[c];
+        --idx;
+        if (idx < 0) {
+            // last half-step to the camera node, then read out in the camera basis
+            if (started) {
+                T A0[4][4], A1[4][4];
+                const T kp[4] = {kt, prev[3], prev[4], prev[5]};
+                const T kn[4] = {kt, prev[9], prev[10], prev[11]};
+                transport_matrix<T>(prev, kp, a, m, flat, A0);
+                transport_matrix<T>(prev + 6, kn, a, m, flat, A1);
+                coh_pc_step(N, A0, A1, T(0.5) * prev[12]);
+            }
+            KSGeom<T> G;
+            ks_geom<T>(prev[6], prev[7], prev[8], a, m, flat, false, G);
+            const T hv[4] = {(T)im.hh[0], (T)im.hh[1], (T)im.hh[2], (T)im.hh[3]};
+            const T vv[4] = {(T)im.vv[0], (T)im.vv[1], (T)im.vv[2], (T)im.vv[3]};
+            T hl[4], vl[4];
+            lower4(G, hv, hl);
+            lower4(G, vv, vl);
+            T s[4];
+            coh_to_stokes(N, hl, vl, s);
+            const int64_t npix = (int64_t)im.n * im.n;
+            const int64_t pix = (int64_t)pj * im.n + pi;
+            for (int c = 0; c < 4; ++c) {
+                if (im.dtype == 0) ((double*)im.stokes)[c * npix + pix] = (double)s[c];
+                else ((float*)im.stokes)[c * npix + pix] = (float)s[c];
+            }
+            active = false;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Component kernels (checks of single stages against the oracle).
+// ---------------------------------------------------------------------------------------
+template <class T>
+__global__ void coefficients_kernel(int64_t n, const double* __restrict__ in, double* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T c[8];
+    synchrotron_coefficients<T>((T)in[5 * i], (T)in[5 * i + 1], (T)in[5 * i + 2], (T)in[5 * i + 3],
+                                (T)in[5 * i + 4], c);
+    for (int q = 0; q < 8; ++q) out[8 * i + q] = (double)c[q];
+}
+
+template <class T>
+__global__ void stokes_step_kernel(int64_t n, const double* __restrict__ coef, const double* __restrict__ s0,
+                                   const double* __restrict__ dl, double* __restrict__ s1) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T c[8], a[4], b[4];
+    for (int q = 0; q < 8; ++q) c[q] = (T)coef[8 * i + q];
+    for (int q = 0; q < 4; ++q) a[q] = (T)s0[4 * i + q];
+    stokes_step<T>(c, a, (T)dl[i], b);
+    for (int q = 0; q < 4; ++q) s1[4 * i + q] = (double)b[q];
+}
+
+template <class T>
+__global__ void bessel_kernel(int64_t n, const double* __restrict__ x, double* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T k0, k1, k2;
+    bessel_k012_scaled<T>((T)x[i], k0, k1, k2);
+    out[3 * i] = k0;
+    out[3 * i + 1] = k1;
+    out[3 * i + 2] = k2;
+}
+
+}  // namespace bl

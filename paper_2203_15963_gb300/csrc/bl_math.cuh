@@ -1,0 +1,478 @@
+// Device math for the Blacklight hot path (White 2022), templated on the arithmetic type.
+// Geodesics always use double; sampling, plasma, coefficients and transfer use T = double
+// (FP64 form) or T = float (mixed form).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace bl {
+
+// float / double forms of the CUDA Bessel I_0, I_1 (only the double names are overloaded)
+__device__ __forceinline__ float cyl_bessel_i0(float x) { return cyl_bessel_i0f(x); }
+__device__ __forceinline__ float cyl_bessel_i1(float x) { return cyl_bessel_i1f(x); }
+__device__ __forceinline__ double cyl_bessel_i0(double x) { return ::cyl_bessel_i0(x); }
+__device__ __forceinline__ double cyl_bessel_i1(double x) { return ::cyl_bessel_i1(x); }
+
+// CGS constants (CODATA 2018; IAU 2015 nominal solar mass).
+constexpr double kC = 2.99792458e10;
+constexpr double kE = 4.80320471e-10;
+constexpr double kMe = 9.1093837015e-28;
+constexpr double kMp = 1.67262192369e-24;
+constexpr double kH = 6.62607015e-27;
+constexpr double kG = 6.67430e-8;
+constexpr double kMsun = 1.98841e33;
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------------------
+// Kerr metric in Cartesian Kerr-Schild form (Sec. 2, Eq. cks_aux):
+//   g_ab = eta_ab + f l_a l_b,  g^ab = eta^ab - f l^a l^b,  l_a = (1, lx, ly, lz),
+//   f = 2 M r^3 / (r^4 + a^2 z^2),  2 r^2 = R^2 - a^2 + ((R^2 - a^2)^2 + 4 a^2 z^2)^{1/2}.
+// Derivatives are hand-expanded: with D = ((R^2 - a^2)^2 + 4 a^2 z^2)^{1/2},
+//   dr/dx = r x / D, dr/dy = r y / D, dr/dz = z (r^2 + a^2) / (r D).
+// ---------------------------------------------------------------------------------------
+template <class T>
+struct KSGeom {
+    T r, f;
+    T l[4];         // covariant l_a, l[0] = 1
+    T df[3];        // d_c f
+    T dl[3][3];     // d_c l_b (b spatial)
+};
+
+template <class T>
+__device__ __forceinline__ void ks_geom(T x, T y, T z, T a, T m, bool flat, bool derivs,
+                                        KSGeom<T>& G) {
+    const T rr2 = x * x + y * y + z * z;
+    const T q = rr2 - a * a;
+    const T D = sqrt(q * q + T(4) * a * a * z * z);
+    const T r2 = T(0.5) * (q + D);
+    const T r = sqrt(r2);
+    const T s4 = r2 * r2 + a * a * z * z;
+    const T is4 = T(1) / s4;
+    const T f = flat ? T(0) : T(2) * m * r * r2 * is4;
+    const T P = r2 + a * a;
+    const T iP = T(1) / P;
+    const T ir = T(1) / r;
+    G.r = r;
+    G.f = f;
+    G.l[0] = T(1);
+    G.l[1] = (r * x + a * y) * iP;
+    G.l[2] = (r * y - a * x) * iP;
+    G.l[3] = z * ir;
+    if (!derivs) return;
+    const T iD = T(1) / D;
+    const T dr[3] = {r * x * iD, r * y * iD, z * P * ir * iD};
+    for (int c = 0; c < 3; ++c) {
+        const T extra = (c == 2) ? T(2) * a * a * z : T(0);
+        G.df[c] = flat ? T(0) : f * (T(3) * dr[c] * ir - (T(4) * r2 * r * dr[c] + extra) * is4);
+        const T two_r_dr_iP = T(2) * r * dr[c] * iP;
+        G.dl[c][0] = (dr[c] * x + (c == 0 ? r : T(0)) + (c == 1 ? a : T(0))) * iP - G.l[1] * two_r_dr_iP;
+        G.dl[c][1] = (dr[c] * y + (c == 1 ? r : T(0)) - (c == 0 ? a : T(0))) * iP - G.l[2] * two_r_dr_iP;
+        G.dl[c][2] = ((c == 2 ? T(1) : T(0)) - G.l[3] * dr[c]) * ir;
+    }
+}
+
+// r of a CKS point (Eq. cks_aux:r).
+template <class T>
+__device__ __forceinline__ T ks_r(T x, T y, T z, T a) {
+    const T q = x * x + y * y + z * z - a * a;
+    return sqrt(T(0.5) * (q + sqrt(q * q + T(4) * a * a * z * z)));
+}
+
+// Lower / raise with g = eta + f l l (contravariant l^a = (-1, lx, ly, lz)).
+template <class T>
+__device__ __forceinline__ void lower4(const KSGeom<T>& G, const T v[4], T out[4]) {
+    const T lv = G.l[0] * v[0] + G.l[1] * v[1] + G.l[2] * v[2] + G.l[3] * v[3];
+    out[0] = -v[0] + G.f * lv;
+    out[1] = v[1] + G.f * G.l[1] * lv;
+    out[2] = v[2] + G.f * G.l[2] * lv;
+    out[3] = v[3] + G.f * G.l[3] * lv;
+}
+template <class T>
+__device__ __forceinline__ void raise4(const KSGeom<T>& G, const T w[4], T out[4]) {
+    const T lw = -w[0] + G.l[1] * w[1] + G.l[2] * w[2] + G.l[3] * w[3];   // l^a w_a
+    out[0] = -w[0] + G.f * lw;                                           // -f l^t lw, l^t = -1
+    out[1] = w[1] - G.f * G.l[1] * lw;
+    out[2] = w[2] - G.f * G.l[2] * lw;
+    out[3] = w[3] - G.f * G.l[3] * lw;
+}
+template <class T>
+__device__ __forceinline__ T dot4(const KSGeom<T>& G, const T u[4], const T v[4]) {
+    const T lu = G.l[0] * u[0] + G.l[1] * u[1] + G.l[2] * u[2] + G.l[3] * u[3];
+    const T lv = G.l[0] * v[0] + G.l[1] * v[1] + G.l[2] * v[2] + G.l[3] * v[3];
+    return -u[0] * v[0] + u[1] * v[1] + u[2] * v[2] + u[3] * v[3] + G.f * lu * lv;
+}
+
+// Eq. (geodesic): dx^a/dl = g^ab k_b; dk_t/dl = 0; dk_c/dl = -1/2 d_c g^ab k_a k_b
+//   = L (1/2 d_c f L + f sum_b d_c l_b k_b),  L = l^a k_a.
+__device__ __forceinline__ void geodesic_rhs(const double y[8], double a, double m, bool flat,
+                                             double dy[8]) {
+    KSGeom<double> G;
+    ks_geom<double>(y[1], y[2], y[3], a, m, flat, true, G);
+    const double* k = y + 4;
+    const double L = -k[0] + G.l[1] * k[1] + G.l[2] * k[2] + G.l[3] * k[3];
+    dy[0] = -k[0] + G.f * L;
+    dy[1] = k[1] - G.f * G.l[1] * L;
+    dy[2] = k[2] - G.f * G.l[2] * L;
+    dy[3] = k[3] - G.f * G.l[3] * L;
+    dy[4] = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double S = G.dl[c][0] * k[1] + G.dl[c][1] * k[2] + G.dl[c][2] * k[3];
+        dy[5 + c] = L * (0.5 * G.df[c] * L + G.f * S);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Coordinate terms of Eq. (polarized_n), read as parallel transport of the coherency
+// tensor: dN/dl = A N + N A^T with A^a_d = -k^c Gamma^a_cd. For g = eta + f l l the
+// contraction is C_ed = k^c Gamma_ecd = 1/2 (D_ed + P_de - P_ed) with
+//   D_ed = k^c d_c g_ed,  P_me = d_m g_ec k^c,  and A = -g^{-1} C.
+// ---------------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void transport_matrix(const T x[3], const T klo[4], T a, T m,
+                                                 bool flat, T A[4][4]) {
+    KSGeom<T> G;
+    ks_geom<T>(x[0], x[1], x[2], a, m, flat, true, G);
+    T ku[4];
+    raise4(G, klo, ku);
+    const T* l = G.l;
+    T kdf = ku[1] * G.df[0] + ku[2] * G.df[1] + ku[3] * G.df[2];
+    T kdl[4];
+    kdl[0] = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+        kdl[b + 1] = ku[1] * G.dl[0][b] + ku[2] * G.dl[1][b] + ku[3] * G.dl[2][b];
+    const T Lp = ku[0] * l[0] + ku[1] * l[1] + ku[2] * l[2] + ku[3] * l[3];   // l_c k^c
+    T Mv[4];
+    Mv[0] = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Mv[c + 1] = G.dl[c][0] * ku[1] + G.dl[c][1] * ku[2] + G.dl[c][2] * ku[3];
+    // P[m][e] = d_m f l_e Lp + f (d_m l_e Lp + l_e M_m), zero for m = t.
+    T P[4][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) P[0][e] = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const T dle = (e == 0) ? T(0) : G.dl[c][e - 1];
+            P[c + 1][e] = G.df[c] * l[e] * Lp + G.f * (dle * Lp + l[e] * Mv[c + 1]);
+        }
+    }
+    T C[4][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const T De = kdf * l[e] * l[d] + G.f * (kdl[e] * l[d] + l[e] * kdl[d]);
+            C[e][d] = T(0.5) * (De + P[d][e] - P[e][d]);
+        }
+    // A = -g^{-1} C with g^{ae} = eta^{ae} - f l^a l^e, l^a = (-1, l1, l2, l3).
+    const T lu[4] = {-l[0], l[1], l[2], l[3]};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+        const T lc = lu[0] * C[0][d] + lu[1] * C[1][d] + lu[2] * C[2][d] + lu[3] * C[3][d];
+        A[0][d] = -(-C[0][d] - G.f * lu[0] * lc);
+#pragma unroll
+        for (int e = 1; e < 4; ++e) A[e][d] = -(C[e][d] - G.f * lu[e] * lc);
+    }
+}
+
+// Coherency tensor stored as its real symmetric part (10) and imaginary antisymmetric part
+// (6): re = [00 01 02 03 11 12 13 22 23 33], im = [01 02 03 12 13 23].
+template <class T>
+struct Coh {
+    T re[10];
+    T im[6];
+};
+
+template <class T>
+__device__ __forceinline__ void coh_unpack(const Coh<T>& n, T R[4][4], T I[4][4]) {
+    R[0][0] = n.re[0]; R[0][1] = R[1][0] = n.re[1]; R[0][2] = R[2][0] = n.re[2];
+    R[0][3] = R[3][0] = n.re[3]; R[1][1] = n.re[4]; R[1][2] = R[2][1] = n.re[5];
+    R[1][3] = R[3][1] = n.re[6]; R[2][2] = n.re[7]; R[2][3] = R[3][2] = n.re[8];
+    R[3][3] = n.re[9];
+    I[0][0] = I[1][1] = I[2][2] = I[3][3] = T(0);
+    I[0][1] = n.im[0]; I[1][0] = -n.im[0]; I[0][2] = n.im[1]; I[2][0] = -n.im[1];
+    I[0][3] = n.im[2]; I[3][0] = -n.im[2]; I[1][2] = n.im[3]; I[2][1] = -n.im[3];
+    I[1][3] = n.im[4]; I[3][1] = -n.im[4]; I[2][3] = n.im[5]; I[3][2] = -n.im[5];
+}
+
+// out = base + h (A N + N A^T) for both parts (structure preserving).
+template <class T>
+__device__ __forceinline__ void coh_axpy(const Coh<T>& base, const Coh<T>& n, const T A[4][4],
+                                         T h, Coh<T>& out) {
+    T R[4][4], I[4][4];
+    coh_unpack(n, R, I);
+    T AR[4][4], AI[4][4];   // A N
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            T sr = T(0), si = T(0);
+#pragma unroll
+            for (int d = 0; d < 4; ++d) { sr += A[i][d] * R[d][j]; si += A[i][d] * I[d][j]; }
+            AR[i][j] = sr;
+            AI[i][j] = si;
+        }
+    // (A N + N A^T)_ij = AN_ij + AN_ji for the symmetric part, AN_ij - AN_ji for the
+    // antisymmetric part (N^T = +-N).
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i; j < 4; ++j) { out.re[q] = base.re[q] + h * (AR[i][j] + AR[j][i]); ++q; }
+    q = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 4; ++j) { out.im[q] = base.im[q] + h * (AI[i][j] - AI[j][i]); ++q; }
+}
+
+// Predictor-corrector of Table tab:pc: N_h = N + h/2 F(A0, N), N' = N + h F(A1, N_h).
+template <class T>
+__device__ __forceinline__ void coh_pc_step(Coh<T>& n, const T A0[4][4], const T A1[4][4], T h) {
+    Coh<T> nh;
+    coh_axpy(n, n, A0, T(0.5) * h, nh);
+    Coh<T> out;
+    coh_axpy(n, nh, A1, h, out);
+    n = out;
+}
+
+// ---------------------------------------------------------------------------------------
+// Modified Bessel functions K_0, K_1 (scaled by exp(x)) from the polynomial approximations
+// of Abramowitz & Stegun 9.8.5-9.8.8 (|error| < 2.2e-7 relative to the scaled value);
+// K_2 from the recurrence K_2 = K_0 + (2/x) K_1.
+// ---------------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void bessel_k012_scaled(T x, T& k0, T& k1, T& k2) {
+    if (x <= T(2)) {
+        const T t = T(0.5) * x;
+        const T t2 = t * t;
+        const T lg = log(t);
+        const T ex = exp(x);
+        const T i0 = cyl_bessel_i0(x);
+        const T i1 = cyl_bessel_i1(x);
+        const T p0 = T(-0.57721566) + t2 * (T(0.42278420) + t2 * (T(0.23069756) + t2 * (T(0.03488590) +
+                     t2 * (T(0.00262698) + t2 * (T(0.00010750) + t2 * T(0.00000740))))));
+        const T p1 = T(1) + t2 * (T(0.15443144) + t2 * (T(-0.67278579) + t2 * (T(-0.18156897) +
+                     t2 * (T(-0.01919402) + t2 * (T(-0.00110404) + t2 * T(-0.00004686))))));
+        const T K0 = -lg * i0 + p0;
+        const T K1 = (x * lg * i1 + p1) / x;
+        k0 = K0 * ex;
+        k1 = K1 * ex;
+    } else {
+        const T u = T(2) / x;
+        const T sx = rsqrt(x);
+        k0 = sx * (T(1.25331414) + u * (T(-0.07832358) + u * (T(0.02189568) + u * (T(-0.01062446) +
+                   u * (T(0.00587872) + u * (T(-0.00251540) + u * T(0.00053208)))))));
+        k1 = sx * (T(1.25331414) + u * (T(0.23498619) + u * (T(-0.03655620) + u * (T(0.01504268) +
+                   u * (T(-0.00780353) + u * (T(0.00325614) + u * T(-0.00068245)))))));
+    }
+    k2 = k0 + T(2) / x * k1;
+}
+
+// ---------------------------------------------------------------------------------------
+// Thermal synchrotron coefficients in the fluid frame (Sec. 2.5), CGS:
+//   j_S = n e^2 nu / (sqrt 3 c K_2(1/Theta)) I_S(x) (S = I, Q),
+//   j_V = 4 n e^2 nu cot(theta) / (3 sqrt 3 c Theta K_2(1/Theta)) I_V(x),
+//   x = nu / (3/2 nu_B sin(theta) Theta^2), nu_B = e B / (2 pi m_e c);
+//   alpha_S = j_S / B_nu(T_e) (Kirchhoff);
+//   rho_Q = n e^2 nu_B^2 sin^2 / (m_e c nu^3) f_m(X) (K_1/K_2 + 6 Theta),
+//   rho_V = 2 n e^2 nu_B cos / (m_e c nu^2) (K_0/K_2) g_m(X),
+//   X = Theta (sqrt 2 sin(theta) 1e3 nu_B / nu)^{1/2}.
+// Q > 0 is polarization perpendicular to the projected field.
+// ---------------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void synchrotron_coefficients(T ne, T th, T bg, T nu, T cth, T out[8]) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) out[q] = T(0);
+    if (!(ne > T(0)) || !(th > T(0)) || !(bg > T(0))) return;
+    const T sth2 = T(1) - cth * cth;
+    const T sth = sqrt(sth2 > T(0) ? sth2 : T(0));
+    const T nub = T(kE / (2.0 * kPi * kMe * kC)) * bg;
+    const T z = T(1) / th;
+    T k0, k1, k2;
+    bessel_k012_scaled(z, k0, k1, k2);
+    if (sth > T(0)) {
+        const T x = nu / (T(1.5) * nub * sth * th * th);
+        const T x13 = cbrt(x);
+        const T ix13 = T(1) / x13;
+        const T ix23 = ix13 * ix13;
+        const T ex = exp(T(-1.8899) * x13);
+        const T ii = T(2.5651) * (T(1) + T(1.92) * ix13 + T(0.9977) * ix23) * ex;
+        const T iq = T(2.5651) * (T(1) + T(0.932) * ix13 + T(0.4998) * ix23) * ex;
+        const T iv = (T(1.8138) / x + T(3.423) * ix23 + T(0.02955) * rsqrt(x) + T(2.0377) * ix13) * ex;
+        // n e^2 nu / (sqrt3 c) / K_2(z) = n e^2 nu / (sqrt3 c) exp(-z) / (exp(z) K_2) * exp(z)...
+        // 1 / K_2(z) = exp(z) / k2 (k2 is scaled).
+        const T pre = ne * T(kE * kE / (1.7320508075688772 * kC)) * nu * (exp(z) / k2);
+        out[0] = pre * ii;
+        out[1] = pre * iq;
+        out[2] = pre * (T(4) / (T(3) * th)) * (cth / sth) * iv;
+        const T hkt = T(kH / (kMe * kC * kC)) * nu / th;
+        // 1 / B_nu = c^2 expm1(h nu / k T) / (2 h nu^3), ordered to stay inside float range
+        const T cnu = T(kC) / nu;
+        const T ibnu = expm1(hkt) * (cnu * cnu) * (T(0.5 / kH) / nu);
+        out[3] = out[0] * ibnu;
+        out[4] = out[1] * ibnu;
+        out[5] = out[2] * ibnu;
+    }
+    const T X = th * sqrt(T(1.4142135623730951e3) * sth * nub / nu);
+    const T fm = T(2.011) * exp(-pow(X, T(1.035)) / T(4.7)) -
+                 cos(T(0.5) * X) * exp(-pow(X, T(1.2)) / T(2.73)) - T(0.011) * exp(-X / T(47.2));
+    const T gm = T(1) - T(0.11) * log1p(T(0.035) * X);
+    const T base = ne * T(kE * kE / (kMe * kC));
+    out[6] = base * nub * nub * sth2 / (nu * nu * nu) * fm * (k1 / k2 + T(6) * th);
+    out[7] = T(2) * base * nub * cth / (nu * nu) * (k0 / k2) * gm;
+}
+
+// ---------------------------------------------------------------------------------------
+// Exact constant-coefficient polarized step over dl: S' = E S + T with
+// [E T; 0 1] = exp([[-M dl, J dl], [0, 0]]), M the absorption/rotation matrix (U-terms zero).
+// Scaling and squaring: the augmented matrix is scaled by 2^-s to norm <= 1/2, its
+// exponential taken by a Horner-form Taylor polynomial, then squared s times. For
+// alpha_I dl >= 100 the steady state M^{-1} J is returned (Eq. unpolarized's tau_max rule).
+// ---------------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void stokes_step(const T c[8], const T s0[4], T dl, T s1[4]) {
+    const T aI = c[3], aQ = c[4], aV = c[5], rQ = c[6], rV = c[7];
+    const T M[4][4] = {{aI, aQ, T(0), aV}, {aQ, aI, rV, T(0)}, {T(0), -rV, aI, rQ}, {aV, T(0), -rQ, aI}};
+    const T J[4] = {c[0], c[1], T(0), c[2]};
+    if (aI * dl >= T(100)) {
+        // Gaussian elimination with partial pivoting on [M | J].
+        T a[4][5];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a[i][j] = M[i][j];
+            a[i][4] = J[i];
+        }
+        for (int col = 0; col < 4; ++col) {
+            int p = col;
+            for (int i = col + 1; i < 4; ++i)
+                if (fabs(a[i][col]) > fabs(a[p][col])) p = i;
+            if (p != col)
+                for (int j = 0; j < 5; ++j) { T t = a[p][j]; a[p][j] = a[col][j]; a[col][j] = t; }
+            const T inv = T(1) / a[col][col];
+            for (int i = col + 1; i < 4; ++i) {
+                const T fct = a[i][col] * inv;
+                for (int j = col; j < 5; ++j) a[i][j] -= fct * a[col][j];
+            }
+        }
+        for (int i = 3; i >= 0; --i) {
+            T s = a[i][4];
+            for (int j = i + 1; j < 4; ++j) s -= a[i][j] * s1[j];
+            s1[i] = s / a[i][i];
+        }
+        return;
+    }
+    // Z = -M dl, z = J dl; infinity norm of the augmented matrix.
+    T Z[4][4], z[4];
+    T nrm = T(0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        T rs = T(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { Z[i][j] = -M[i][j] * dl; rs += fabs(Z[i][j]); }
+        z[i] = J[i] * dl;
+        rs += fabs(z[i]);
+        nrm = rs > nrm ? rs : nrm;
+    }
+    int s = 0;
+    if (nrm > T(0.5)) {
+        int e;
+        frexp(nrm / T(0.5), &e);
+        s = e;   // nrm / 2^s <= 0.5
+    }
+    const T sc = ldexp(T(1), -s);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Z[i][j] *= sc;
+        z[i] *= sc;
+    }
+    // Taylor degree: ||Z|| <= 1/2, truncation 2^-(m+1)/(m+1)! below the type's rounding.
+    constexpr int m = sizeof(T) == 8 ? 13 : 8;
+    // E = I + Z (I + Z/2 (I + Z/3 (...))),  t = (I + Z/2 (I + Z/3 (...))) z  (phi_1(Z) z)
+    T E[4][4], tv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) E[i][j] = (i == j) ? T(1) : T(0);
+        tv[i] = z[i] / T(m + 1);
+    }
+    for (int k = m; k >= 1; --k) {
+        const T ik = T(1) / T(k);
+        T En[4][4], tn[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                T acc = T(0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc += Z[i][q] * E[q][j];
+                En[i][j] = (i == j ? T(1) : T(0)) + acc * ik;
+            }
+        }
+        if (k >= 2) {
+            // tv <- z / k + Z tv / k  builds sum_n Z^n z / (n+1)!
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                T acc = T(0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc += Z[i][q] * tv[q];
+                tn[i] = (z[i] + acc) * ik;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) tv[i] = tn[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                T acc = T(0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc += Z[i][q] * tv[q];
+                tn[i] = z[i] + acc;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) tv[i] = tn[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) E[i][j] = En[i][j];
+    }
+    // Squaring: [E t; 0 1]^2 = [E^2, E t + t; 0 1].
+    for (int q = 0; q < s; ++q) {
+        T E2[4][4], t2[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                T acc = T(0);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc += E[i][r] * E[r][j];
+                E2[i][j] = acc;
+            }
+            T acc = tv[i];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc += E[i][r] * tv[r];
+            t2[i] = acc;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            tv[i] = t2[i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) E[i][j] = E2[i][j];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        T acc = tv[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc += E[i][j] * s0[j];
+        s1[i] = acc;
+    }
+}
+
+}  // namespace bl

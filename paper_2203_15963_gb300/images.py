@@ -1,0 +1,33 @@
+"""Whole-image helpers over the C ABI: allocate torch outputs and call the binding."""
+from __future__ import annotations
+
+import torch
+
+from . import native
+
+
+def alloc_outputs(n: int, dtype=torch.float64, device="cuda", status=True, steps=True,
+                  end_state=False, samples=False):
+    out = {"stokes": torch.empty((4, n, n), dtype=dtype, device=device)}
+    if samples:
+        out["samples"] = torch.empty((n, n), dtype=torch.int32, device=device)
+    if status:
+        out["status"] = torch.empty((n, n), dtype=torch.int32, device=device)
+    if steps:
+        out["steps"] = torch.empty((n, n), dtype=torch.int32, device=device)
+    if end_state:
+        out["end_state"] = torch.empty((n, n, 8), dtype=torch.float64, device=device)
+    return out
+
+
+def trace_images(cams, mets, gps, prims, freqs, dtype=None, end_state=False, workspace=None,
+                 flags=0, samples=False, outs=None):
+    """Trace a batch of images in one launch pair; returns (rc, list of output dicts)."""
+    if outs is None:
+        outs = []
+        for cam, met in zip(cams, mets):
+            dt = dtype or (torch.float64 if met.precision == native.BL_PREC_FP64 else torch.float32)
+            outs.append(alloc_outputs(cam.n, dt, end_state=end_state, samples=samples))
+    rc = native.blacklight_trace_batch(cams, mets, gps, prims, freqs, outs, workspace=workspace,
+                                       flags=flags)
+    return rc, outs

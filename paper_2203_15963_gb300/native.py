@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libblacklight.so (include/blacklight.h): argument marshalling only.
+
+Every function keeps the C name. Tensors are torch tensors on the current CUDA device; the
+binding passes their data pointers and the current torch stream. There is no CPU fallback:
+if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_SRC_DIR = os.path.join(_HERE, "csrc")
+_LIB = os.path.join(_HERE, "_lib", "libblacklight.so")
+_INCLUDE = os.path.join(_ROOT, "include")
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+BL_PREC_FP64, BL_PREC_MIXED = 0, 1
+BL_ASYNC = 1
+BL_TIMING = 2
+RAY_STATUS = {0: "ok", 1: "horizon", 2: "escaped", 3: "max_steps", 4: "underflow", 5: "nan",
+              6: "overflow"}
+
+
+def nvcc_command():
+    return ["nvcc", ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+            "-I" + _INCLUDE, "-o", _LIB, os.path.join(_SRC_DIR, "bl_api.cu")]
+
+
+def build(force: bool = False) -> str:
+    """Compile libblacklight.so for sm_103a in-tree (skipped when up to date)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    srcs = [os.path.join(_SRC_DIR, f) for f in os.listdir(_SRC_DIR)]
+    srcs.append(os.path.join(_INCLUDE, "blacklight.h"))
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(s) for s in srcs)):
+        return _LIB
+    subprocess.run(nvcc_command(), check=True)
+    return _LIB
+
+
+def library_path() -> str:
+    return _LIB
+
+
+class Camera(C.Structure):
+    _fields_ = [("size", C.c_uint32), ("r", C.c_double), ("theta", C.c_double),
+                ("phi", C.c_double), ("u_p", C.c_double * 3), ("k_p", C.c_double * 3),
+                ("width", C.c_double), ("n", C.c_int32), ("psi", C.c_double),
+                ("kind", C.c_int32), ("nu_at_infinity", C.c_int32)]
+
+
+class Metric(C.Structure):
+    _fields_ = [("size", C.c_uint32), ("mass", C.c_double), ("spin", C.c_double),
+                ("r_in_over_rhor", C.c_double), ("tol_abs", C.c_double), ("tol_rel", C.c_double),
+                ("ds_max", C.c_double), ("h0_frac", C.c_double), ("max_steps", C.c_int64),
+                ("flat", C.c_int32), ("precision", C.c_int32)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("size", C.c_uint32), ("prim", C.c_void_p), ("n_r", C.c_int32),
+                ("n_theta", C.c_int32), ("n_phi", C.c_int32), ("r_min", C.c_double),
+                ("r_max", C.c_double), ("gamma_ad", C.c_double), ("r_high", C.c_double),
+                ("r_low", C.c_double), ("mu", C.c_double), ("ne_over_ni", C.c_double),
+                ("sigma_cut", C.c_double), ("rho_unit_cgs", C.c_double),
+                ("mass_msun", C.c_double), ("interp", C.c_int32)]
+
+
+class Out(C.Structure):
+    _fields_ = [("size", C.c_uint32), ("stokes", C.c_void_p), ("dtype", C.c_int32),
+                ("status", C.c_void_p), ("steps", C.c_void_p), ("end_state", C.c_void_p),
+                ("samples", C.c_void_p)]
+
+
+_lib = None
+
+
+def load():
+    """Load libblacklight.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB):
+        raise RuntimeError(f"libblacklight.so is not built ({_LIB}); run __graft_entry__.build()")
+    L = C.CDLL(_LIB)
+    P = C.c_void_p
+    L.blacklight_trace_batch.argtypes = [C.c_int32, C.POINTER(Camera), C.POINTER(Metric),
+                                         C.POINTER(Grid), C.POINTER(C.c_double), C.POINTER(Out),
+                                         P, C.c_size_t, P, C.c_uint32]
+    L.blacklight_trace.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Grid),
+                                   C.c_double, C.POINTER(Out), P, C.c_uint32]
+    L.blacklight_trace_host.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Grid),
+                                        C.c_double, C.POINTER(Out), P]
+    L.blacklight_geodesics.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Out), P,
+                                       C.c_uint32]
+    L.blacklight_workspace_size.argtypes = [C.c_int32, C.POINTER(Camera), C.POINTER(Metric)]
+    L.blacklight_workspace_size.restype = C.c_size_t
+    L.blacklight_coefficients.argtypes = [C.c_int64, P, P, C.c_int32, P]
+    L.blacklight_stokes_step.argtypes = [C.c_int64, P, P, P, P, C.c_int32, P]
+    L.blacklight_bessel_k.argtypes = [C.c_int64, P, P, C.c_int32, P]
+    L.blacklight_strerror.argtypes = [C.c_int]
+    L.blacklight_strerror.restype = C.c_char_p
+    L.blacklight_last_error_detail.argtypes = []
+    L.blacklight_last_error_detail.restype = C.c_char_p
+    L.blacklight_launch_count.argtypes = [C.c_int]
+    L.blacklight_launch_count.restype = C.c_uint64
+    L.blacklight_last_kernel_ms.argtypes = [C.POINTER(C.c_float)]
+    _lib = L
+    return L
+
+
+class BlacklightError(RuntimeError):
+    def __init__(self, code, detail):
+        super().__init__(f"blacklight error {code}: {detail}")
+        self.code = code
+
+
+def _check(rc):
+    if rc < 0:
+        L = load()
+        raise BlacklightError(rc, (L.blacklight_strerror(rc) or b"").decode() + ": "
+                              + (L.blacklight_last_error_detail() or b"").decode())
+    return rc
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+# ------------------------------- struct builders ---------------------------------------
+def camera_struct(cam) -> Camera:
+    return Camera(C.sizeof(Camera), cam.r, cam.theta, cam.phi, (C.c_double * 3)(*cam.u_p),
+                  (C.c_double * 3)(*cam.k_p), cam.width, cam.n, cam.psi, cam.kind,
+                  cam.nu_at_infinity)
+
+
+def metric_struct(met, precision=None) -> Metric:
+    p = met.precision if precision is None else precision
+    return Metric(C.sizeof(Metric), met.mass, met.spin, met.r_in_over_rhor, met.tol_abs,
+                  met.tol_rel, met.ds_max, met.h0_frac, int(met.max_steps), met.flat, p)
+
+
+def grid_struct(gp, prim_ptr) -> Grid:
+    return Grid(C.sizeof(Grid), prim_ptr, gp.n_r, gp.n_theta, gp.n_phi, gp.r_min, gp.r_max,
+                gp.gamma_ad, gp.r_high, gp.r_low, gp.mu, gp.ne_over_ni, gp.sigma_cut,
+                gp.rho_unit_cgs, gp.mass_msun, gp.interp)
+
+
+def out_struct(stokes=None, status=None, steps=None, end_state=None, samples=None) -> Out:
+    import torch
+    dtype = 0
+    if stokes is not None:
+        dtype = 0 if stokes.dtype == torch.float64 else 1
+    return Out(C.sizeof(Out), _ptr(stokes), dtype, _ptr(status), _ptr(steps), _ptr(end_state),
+               _ptr(samples))
+
+
+# ------------------------------------ calls ---------------------------------------------
+def blacklight_trace_batch(cams, mets, gps, prims, freqs, outs, workspace=None, stream=None,
+                           flags=0):
+    """cams/mets/gps: synth dataclasses; prims: CUDA float32 tensors; outs: dicts of tensors."""
+    L = load()
+    n = len(cams)
+    ca = (Camera * n)(*[camera_struct(c) for c in cams])
+    ma = (Metric * n)(*[metric_struct(m) for m in mets])
+    ga = (Grid * n)(*[grid_struct(g, p.data_ptr()) for g, p in zip(gps, prims)])
+    fa = (C.c_double * n)(*[float(f) for f in freqs])
+    oa = (Out * n)(*[out_struct(**o) for o in outs])
+    ws_ptr, ws_bytes = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel()
+                                                           * workspace.element_size())
+    return _check(L.blacklight_trace_batch(n, ca, ma, ga, fa, oa, ws_ptr, ws_bytes,
+                                           _stream(stream), flags))
+
+
+def blacklight_trace(cam, met, gp, prim, freq, out, stream=None, flags=0):
+    L = load()
+    cs, ms, gs, os_ = camera_struct(cam), metric_struct(met), grid_struct(gp, prim.data_ptr()), \
+        out_struct(**out)
+    return _check(L.blacklight_trace(C.byref(cs), C.byref(ms), C.byref(gs), float(freq),
+                                     C.byref(os_), _stream(stream), flags))
+
+
+def blacklight_trace_host(cam, met, gp, prim_host, freq, out_host, stream=None):
+    """prim_host and the tensors in out_host are CPU tensors (pinned for speed)."""
+    L = load()
+    cs, ms = camera_struct(cam), metric_struct(met)
+    gs = grid_struct(gp, prim_host.data_ptr())
+    os_ = out_struct(**out_host)
+    return _check(L.blacklight_trace_host(C.byref(cs), C.byref(ms), C.byref(gs), float(freq),
+                                          C.byref(os_), _stream(stream)))
+
+
+def blacklight_geodesics(cam, met, out, stream=None, flags=0):
+    L = load()
+    cs, ms, os_ = camera_struct(cam), metric_struct(met), out_struct(**out)
+    return _check(L.blacklight_geodesics(C.byref(cs), C.byref(ms), C.byref(os_),
+                                         _stream(stream), flags))
+
+
+def blacklight_workspace_size(cams, mets) -> int:
+    L = load()
+    n = len(cams)
+    ca = (Camera * n)(*[camera_struct(c) for c in cams])
+    ma = (Metric * n)(*[metric_struct(m) for m in mets])
+    return int(L.blacklight_workspace_size(n, ca, ma))
+
+
+def blacklight_coefficients(inp, out, precision, stream=None):
+    return _check(load().blacklight_coefficients(inp.shape[0], _ptr(inp), _ptr(out), precision,
+                                                 _stream(stream)))
+
+
+def blacklight_stokes_step(coef, s0, dl, s1, precision, stream=None):
+    return _check(load().blacklight_stokes_step(coef.shape[0], _ptr(coef), _ptr(s0), _ptr(dl),
+                                                _ptr(s1), precision, _stream(stream)))
+
+
+def blacklight_bessel_k(x, out, precision, stream=None):
+    return _check(load().blacklight_bessel_k(x.shape[0], _ptr(x), _ptr(out), precision,
+                                             _stream(stream)))
+
+
+def blacklight_launch_count(reset=False) -> int:
+    return int(load().blacklight_launch_count(1 if reset else 0))
+
+
+def blacklight_last_kernel_ms():
+    """(geodesic_ms, transfer_ms) of this thread's last call made with BL_TIMING."""
+    ms = (C.c_float * 2)()
+    _check(load().blacklight_last_kernel_ms(ms))
+    return float(ms[0]), float(ms[1])
