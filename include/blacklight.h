@@ -136,6 +136,22 @@ int blacklight_trace_batch(int32_t n_images, const bl_camera_t* cams, const bl_m
 int blacklight_trace(const bl_camera_t* cam, const bl_metric_t* met, const bl_grid_t* grid,
                      double freq_hz, const bl_out_t* out, void* stream, uint32_t flags);
 
+/* blacklight_trace for callers that cannot allocate device memory (no cudaMalloc,
+ * cudaMallocAsync or cudaFree on any path). The paper has no counterpart: this exists for
+ * callers that trace inside an allocator they do not control -- a fixed memory budget set at
+ * start-up, a foreign memory pool, or a context where allocation is forbidden. Instead of
+ * allocating, it uses a fixed 64 MiB scratch array compiled into the library (held by every
+ * device that loads the library until the process exits), which limits it to images of at
+ * most 1024 rays (e.g. 32x32); larger cameras return BL_EINVAL with an explanation.
+ * Inputs and outputs are caller-owned device memory as for blacklight_trace. The first call
+ * on each device looks up the scratch array's device address (make that call before any
+ * stream capture). All calls share the one array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and corrupt each other; order them on one stream.
+ * BL_TIMING is ignored. */
+int blacklight_trace_noalloc(const bl_camera_t* cam, const bl_metric_t* met,
+                             const bl_grid_t* grid, double freq_hz, const bl_out_t* out,
+                             void* stream, uint32_t flags);
+
 /* Same as blacklight_trace, but grid->prim and out->stokes/status/steps/end_state are HOST
  * pointers: the call copies the grid in, traces, and copies the results out (all
  * stream-ordered, device scratch allocated and freed inside). Always synchronous. */

@@ -315,9 +315,65 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
     return rc;
 }
 
+// ---------------------------------------------------------------------------------------
+// Fixed scratch for blacklight_trace_noalloc. Some callers cannot allocate device memory
+// while they trace -- for example code running inside a memory pool they do not own, or a
+// host process whose allocator must not grow after start-up -- so this entry point works in
+// a statically sized buffer that lives in the library's device image instead. Every device
+// that loads the library holds these 64 MiB until the process exits.
+// ---------------------------------------------------------------------------------------
+constexpr size_t kNoAllocBytes = 64ull << 20;
+constexpr int64_t kNoAllocMaxRays = 1024;     // e.g. one 32x32 image
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// The array's name is a host-side stand-in in host code; the device address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+int noalloc_scratch(char** out) {
+    static std::mutex mu;
+    static std::vector<char*> addr;
+    int dev = 0;
+    BL_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)addr.size() <= dev) addr.resize(dev + 1, nullptr);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        addr[dev] = (char*)p;
+    }
+    *out = addr[dev];
+    return 0;
+}
+
 }  // namespace
 
 extern "C" {
+
+int blacklight_trace_noalloc(const bl_camera_t* cam, const bl_metric_t* met,
+                             const bl_grid_t* grid, double freq_hz, const bl_out_t* out,
+                             void* stream, uint32_t flags) {
+    g_detail[0] = 0;
+    if (!cam || !met) return fail(BL_EINVAL, "NULL argument");
+    int rc = check_camera(cam, 0);
+    if (!rc) rc = check_metric(met, 0);
+    if (rc) return rc;
+    const int64_t rays = (int64_t)cam->n * cam->n;
+    if (rays > kNoAllocMaxRays)
+        return fail(BL_EINVAL, "blacklight_trace_noalloc: %lld rays exceed its fixed scratch "
+                    "(at most %lld rays, %zu bytes); use blacklight_trace",
+                    (long long)rays, (long long)kNoAllocMaxRays, kNoAllocBytes);
+    const size_t need = make_layout(1, cam, met->precision).total;
+    if (need > kNoAllocBytes)
+        return fail(BL_EINVAL, "blacklight_trace_noalloc: needs %zu bytes of scratch, has %zu",
+                    need, kNoAllocBytes);
+    char* ws = nullptr;
+    rc = noalloc_scratch(&ws);
+    if (rc) return rc;
+    // The counters at the head of the scratch are zeroed on the stream before each launch;
+    // the rest is written before it is read, so stale contents from the last call are inert.
+    return trace_impl(1, cam, met, grid, &freq_hz, out, ws, kNoAllocBytes, stream,
+                      flags & ~(uint32_t)BL_TIMING, true);
+}
 
 int blacklight_trace_batch(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
                            const bl_grid_t* grids, const double* freqs_hz, const bl_out_t* outs,

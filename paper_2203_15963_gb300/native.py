@@ -91,6 +91,8 @@ def load():
                                          P, C.c_size_t, P, C.c_uint32]
     L.blacklight_trace.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Grid),
                                    C.c_double, C.POINTER(Out), P, C.c_uint32]
+    L.blacklight_trace_noalloc.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Grid),
+                                           C.c_double, C.POINTER(Out), P, C.c_uint32]
     L.blacklight_trace_host.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Grid),
                                         C.c_double, C.POINTER(Out), P]
     L.blacklight_geodesics.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Out), P,
@@ -187,6 +189,15 @@ def blacklight_trace(cam, met, gp, prim, freq, out, stream=None, flags=0):
         out_struct(**out)
     return _check(L.blacklight_trace(C.byref(cs), C.byref(ms), C.byref(gs), float(freq),
                                      C.byref(os_), _stream(stream), flags))
+
+
+def blacklight_trace_noalloc(cam, met, gp, prim, freq, out, stream=None, flags=0):
+    """blacklight_trace without any device allocation (fixed in-library scratch, <= 1024 rays)."""
+    L = load()
+    cs, ms, gs, os_ = camera_struct(cam), metric_struct(met), grid_struct(gp, prim.data_ptr()), \
+        out_struct(**out)
+    return _check(L.blacklight_trace_noalloc(C.byref(cs), C.byref(ms), C.byref(gs), float(freq),
+                                             C.byref(os_), _stream(stream), flags))
 
 
 def blacklight_trace_host(cam, met, gp, prim_host, freq, out_host, stream=None):
