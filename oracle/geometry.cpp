@@ -466,18 +466,21 @@ int32_t integrate(const ora_metric* met, double r_cam, const double ystart[8],
             geodesic_rhs(ys, m, a, flat, k[st]);
         }
         // ys is now the 7th-stage argument, which is the 5th-order solution (FSAL).
-        double y5[8], y4[8];
+        // y5 - y4 = h sum_p (b5_p - b4_p) k_p: the same difference of the two solutions,
+        // evaluated without subtracting two nearly equal sums (which would lose about as
+        // many digits as the tolerance has).
+        double y5[8], d54[8];
         for (int q = 0; q < 8; ++q) {
-            double s5 = 0.0, s4 = 0.0;
-            for (int p = 0; p < 7; ++p) { s5 += b5[p] * k[p][q]; s4 += b4[p] * k[p][q]; }
+            double s5 = 0.0, sd = 0.0;
+            for (int p = 0; p < 7; ++p) { s5 += b5[p] * k[p][q]; sd += (b5[p] - b4[p]) * k[p][q]; }
             y5[q] = y[q] + h * s5;
-            y4[q] = y[q] + h * s4;
+            d54[q] = h * sd;
         }
         double eps = 0.0;
         bool bad = false;
         for (int q = 0; q < 8; ++q) {
             double sc = met->tol_abs + met->tol_rel * std::fmax(std::fabs(y[q]), std::fabs(y5[q]));
-            double e = std::fabs(y5[q] - y4[q]) / sc;
+            double e = std::fabs(d54[q]) / sc;
             if (!(e == e)) bad = true;
             eps = std::fmax(eps, e);
         }
