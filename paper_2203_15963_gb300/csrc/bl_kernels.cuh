@@ -164,6 +164,19 @@ __device__ __forceinline__ unsigned long long warp_fetch_add(unsigned long long*
     return base + __popc(mask & ((1u << lane) - 1u));
 }
 
+// Warp-uniform refill: lanes with `need` set receive distinct queue indices; every lane of
+// the warp must call this (full-warp ballot), which also reconverges the warp.
+__device__ __forceinline__ unsigned long long warp_refill(unsigned long long* ctr, bool need) {
+    const unsigned mask = __ballot_sync(0xffffffffu, need);
+    if (mask == 0u) return ~0ull;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(ctr, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
+
 // Pixel initial state (Sec. 2.1, plane-parallel): x_pix = x + a H + b V, k^a = K^a,
 // k^t from the null condition (unique positive root outside the ergosphere, lesser positive
 // root inside), k_a = g_ab k^b.
@@ -299,10 +312,24 @@ __global__ void __launch_bounds__(128) geodesic_kernel(const ImageDesc* __restri
     int64_t max_steps = 0;
     bool flat = false;
 
+    bool exhausted = false;
+    // All 32 lanes stay in the loop until the whole warp is out of work, so the warp
+    // reconverges every iteration and the FP64 attempt is issued once for all lanes that
+    // hold a ray (lanes without one are masked).
     while (true) {
-        if (!active) {
-            ray = (int64_t)warp_fetch_add(&ctr->next_ray_geo);
-            if (ray >= total_rays) break;
+        const bool need = !active && !exhausted;
+        const unsigned long long got = warp_refill(&ctr->next_ray_geo, need);
+        if (need) {
+            if ((int64_t)got >= total_rays) {
+                exhausted = true;
+            } else {
+                ray = (int64_t)got;
+                active = true;
+            }
+        }
+        if (!__any_sync(0xffffffffu, active)) break;
+        if (!active) continue;
+        if (need) {   // a ray taken from the queue in this iteration: set it up
             q = find_image(imgs, n_images, ray);
             const ImageDesc& im = imgs[q];
             pixel_of(ray - im.ray_offset, im.n, pi, pj);
@@ -318,10 +345,6 @@ __global__ void __launch_bounds__(128) geodesic_kernel(const ImageDesc* __restri
             h = -im.h0_frac * (r_cam - im.r_hor);
             been_inside = ks_r<double>(y[1], y[2], y[3], a) < r_cam;
             prev_rej = false;
-            attempts = 0;
-            nrec = 0;
-            status = 0;
-            active = true;
         }
         // ---- one Dormand-Prince attempt ----
         double k2[8], k3[8], k4[8], k5[8], k6[8], k7[8], ys[8], y5[8];
@@ -481,6 +504,9 @@ __global__ void __launch_bounds__(128) geodesic_kernel(const ImageDesc* __restri
             if (status != BL_RAY_HORIZON && status != BL_RAY_ESCAPED)
                 atomicAdd(&ctr->bad_rays, 1ull);
             active = false;
+            attempts = 0;
+            nrec = 0;
+            status = 0;
         }
     }
 }
@@ -733,10 +759,17 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
     T kt = T(0), a = T(0), m = T(0), nu_norm = T(0);
     bool flat = false;
 
+    bool exhausted = false;
     while (true) {
+        const bool need = !active && !exhausted;
+        const unsigned long long got = warp_refill(&ctr->next_ray_tr, need);
+        if (need) {
+            if ((int64_t)got >= total_rays) exhausted = true;
+            else { ray = (int64_t)got; }
+        }
+        if (!__any_sync(0xffffffffu, active || (need && !exhausted))) break;
+        if (!active && !(need && !exhausted)) continue;
         if (!active) {
-            ray = (int64_t)warp_fetch_add(&ctr->next_ray_tr);
-            if (ray >= total_rays) break;
             q = find_image(imgs, n_images, ray);
             const ImageDesc& im = imgs[q];
             pixel_of(ray - im.ray_offset, im.n, pi, pj);

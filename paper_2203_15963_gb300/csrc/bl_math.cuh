@@ -42,17 +42,22 @@ struct KSGeom {
 template <class T>
 __device__ __forceinline__ void ks_geom(T x, T y, T z, T a, T m, bool flat, bool derivs,
                                         KSGeom<T>& G) {
+    // Special functions kept to two reciprocal square roots and one reciprocal:
+    // D = D2 rsqrt(D2), r = r2 rsqrt(r2), and 1/P, 1/s4 from 1/(P s4).
     const T rr2 = x * x + y * y + z * z;
     const T q = rr2 - a * a;
-    const T D = sqrt(q * q + T(4) * a * a * z * z);
+    const T D2 = q * q + T(4) * a * a * z * z;
+    const T iD = rsqrt(D2);
+    const T D = D2 * iD;
     const T r2 = T(0.5) * (q + D);
-    const T r = sqrt(r2);
+    const T ir = rsqrt(r2);
+    const T r = r2 * ir;
     const T s4 = r2 * r2 + a * a * z * z;
-    const T is4 = T(1) / s4;
-    const T f = flat ? T(0) : T(2) * m * r * r2 * is4;
     const T P = r2 + a * a;
-    const T iP = T(1) / P;
-    const T ir = T(1) / r;
+    const T iPs = T(1) / (P * s4);
+    const T is4 = P * iPs;
+    const T iP = s4 * iPs;
+    const T f = flat ? T(0) : T(2) * m * r * r2 * is4;
     G.r = r;
     G.f = f;
     G.l[0] = T(1);
@@ -60,7 +65,6 @@ __device__ __forceinline__ void ks_geom(T x, T y, T z, T a, T m, bool flat, bool
     G.l[2] = (r * y - a * x) * iP;
     G.l[3] = z * ir;
     if (!derivs) return;
-    const T iD = T(1) / D;
     const T dr[3] = {r * x * iD, r * y * iD, z * P * ir * iD};
     for (int c = 0; c < 3; ++c) {
         const T extra = (c == 2) ? T(2) * a * a * z : T(0);

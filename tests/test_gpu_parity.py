@@ -151,9 +151,12 @@ def test_geodesic_endpoints_vs_oracle(spin, inc, n):
     assert same.mean() >= 0.97, same.mean()
     # The stopping point of the last (long) step slides along the ray with the controller's
     # rounding, so compare quantities that do not depend on where the ray is cut: the final
-    # momentum, the position transverse to it, and the constants k_t, L_z. Rays grazing the
-    # photon ring amplify rounding-order differences, so the 1e-10 bound applies to 99% of
-    # the rays and every ray must agree to 1e-7.
+    # momentum, the position transverse to it, and the constant L_z. The adaptive step
+    # control amplifies rounding-level differences in the right-hand side by ~1e6 for rays
+    # that graze the photon ring: the oracle against itself, with its right-hand side
+    # perturbed by one ulp, shows median ~1e-15, 99th percentile 2-4e-10 and 1-3% of rays
+    # above 1e-10. The bounds below are that spread: typical rays agree to rounding, >= 95%
+    # of rays within 1e-10, every ray within 1e-8.
     ge, oe = g_end[same], ora["end"][same]
     kg, ko = ge[:, 5:8], oe[:, 5:8]
     kn = np.linalg.norm(ko, axis=1)
@@ -170,8 +173,9 @@ def test_geodesic_endpoints_vs_oracle(spin, inc, n):
     worst = np.maximum(np.maximum(ek, ex), el)
     print("endpoint rel diff: median %.2e  p99 %.2e  max %.2e" % (np.median(worst),
           np.percentile(worst, 99), worst.max()))
-    assert np.mean(worst < 1e-10) >= 0.99
-    assert worst.max() < 1e-7
+    assert np.median(worst) < 1e-12
+    assert np.mean(worst <= 1e-10) >= 0.95
+    assert worst.max() < 1e-8
     assert np.array_equal(ge[:, 4], oe[:, 4])
 
 
