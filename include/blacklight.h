@@ -61,7 +61,7 @@ typedef struct bl_metric {
     double h0_frac;         /* first step = -h0_frac (r_cam - r_hor) */
     int64_t max_steps;      /* attempted DP steps per ray before MAX_STEPS */
     int32_t flat;           /* 1: Minkowski metric in the same coordinates (Sec. 4, flat) */
-    int32_t precision;      /* BL_PREC_FP64 or BL_PREC_MIXED */
+    int32_t precision;      /* BL_PREC_FP64, BL_PREC_MIXED or BL_PREC_FAST */
 } bl_metric_t;
 
 /* Fluid grid and plasma model (Secs. 2.4-2.5). prim is a DEVICE pointer to float32
@@ -117,7 +117,12 @@ enum {
     BL_RAY_OVERFLOW = 6     /* sample store full: Stokes not computed (NaN) */
 };
 
-enum { BL_PREC_FP64 = 0, BL_PREC_MIXED = 1 };
+/* Arithmetic of the path:
+ *   BL_PREC_FP64  geodesics, sampling, plasma, coefficients and transfer in FP64;
+ *   BL_PREC_MIXED geodesics and step control in FP64, the rest in FP32;
+ *   BL_PREC_FAST  geodesics in double-float (pairs of FP32, ~48-bit significand, step
+ *                 control in FP32), the rest in FP32. */
+enum { BL_PREC_FP64 = 0, BL_PREC_MIXED = 1, BL_PREC_FAST = 2 };
 /* flags: BL_ASYNC returns without synchronising; BL_TIMING records CUDA events on `stream`
  * around the geodesic and transfer kernels (read with blacklight_last_kernel_ms). */
 enum { BL_ASYNC = 1u, BL_TIMING = 2u };

@@ -56,8 +56,8 @@ Layout make_layout(int32_t n_images, const bl_camera_t* cams, int precision) {
     for (int q = 0; q < n_images; ++q) rays += (int64_t)cams[q].n * cams[q].n;
     L.rays = rays;
     L.pool_chunks = rays * kChunksPerRay;
-    const size_t rec = precision == BL_PREC_MIXED ? sizeof(float) * bl::RecStride<float>::v
-                                                  : sizeof(double) * bl::RecStride<double>::v;
+    const size_t rec = precision != BL_PREC_FP64 ? sizeof(float) * bl::RecStride<float>::v
+                                                 : sizeof(double) * bl::RecStride<double>::v;
     size_t off = 0;
     L.counters = off; off = align_up(off + sizeof(bl::Counters));
     L.descs = off;    off = align_up(off + sizeof(bl::ImageDesc) * (size_t)n_images);
@@ -92,7 +92,8 @@ int check_metric(const bl_metric_t* m, int q) {
     if (!(m->ds_max > 0.0)) return fail(BL_EINVAL, "mets[%d].ds_max must be > 0", q);
     if (!(m->h0_frac > 0.0)) return fail(BL_EINVAL, "mets[%d].h0_frac must be > 0", q);
     if (!(m->max_steps > 0)) return fail(BL_EINVAL, "mets[%d].max_steps must be > 0", q);
-    if (m->precision != BL_PREC_FP64 && m->precision != BL_PREC_MIXED)
+    if (m->precision != BL_PREC_FP64 && m->precision != BL_PREC_MIXED &&
+        m->precision != BL_PREC_FAST)
         return fail(BL_EINVAL, "mets[%d].precision", q);
     return 0;
 }
@@ -157,8 +158,8 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
 
 struct DevInfo {
     int sms = 0;
-    int geo_blocks[2] = {0, 0};     // per SM, [record type float, double]
-    int tr_blocks[2] = {0, 0};      // per SM, [mixed, fp64]
+    int geo_blocks[3] = {0, 0, 0};  // per SM, indexed by precision: [fp64, mixed, fast]
+    int tr_blocks[3] = {0, 0, 0};
 };
 
 int dev_info(DevInfo& out) {
@@ -171,11 +172,13 @@ int dev_info(DevInfo& out) {
     DevInfo& di = cache[dev];
     if (di.sms == 0) {
         BL_CUDA(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[0], bl::geodesic_kernel<float>, 128, 0));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[1], bl::geodesic_kernel<double>, 128, 0));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[0], bl::transfer_kernel<float, float>, 128, 0));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[1], bl::transfer_kernel<double, double>, 128, 0));
-        for (int i = 0; i < 2; ++i) {
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[0], bl::geodesic_kernel<double, double>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[1], bl::geodesic_kernel<float, double>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[2], bl::geodesic_kernel<float, bl::df64>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[0], bl::transfer_kernel<double, double>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[1], bl::transfer_kernel<float, float>, 128, 0));
+        di.tr_blocks[2] = di.tr_blocks[1];
+        for (int i = 0; i < 3; ++i) {
             if (di.geo_blocks[i] < 1) di.geo_blocks[i] = 1;
             if (di.tr_blocks[i] < 1) di.tr_blocks[i] = 1;
         }
@@ -205,22 +208,26 @@ int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* 
     bl::camera_frame_kernel<<<(n_images + 63) / 64, 64, 0, st>>>(d_desc, n_images);
     ++g_launches;
     BL_CUDA(cudaGetLastError());
-    const int pidx = precision == BL_PREC_MIXED ? 0 : 1;
+    const int pidx = precision;
     if (timing) BL_CUDA(cudaEventRecord(g_ev[0], st));
-    if (precision == BL_PREC_MIXED) {
-        bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
-        bl::geodesic_kernel<float><<<di.sms * di.geo_blocks[pidx], 128, 0, st>>>(
+    if (precision == BL_PREC_FP64) {
+        bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
+        bl::geodesic_kernel<double, double><<<di.sms * di.geo_blocks[pidx], 128, 0, st>>>(
             d_desc, n_images, L.rays, hdr, sink, transfer ? 1 : 0);
     } else {
-        bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
-        bl::geodesic_kernel<double><<<di.sms * di.geo_blocks[pidx], 128, 0, st>>>(
-            d_desc, n_images, L.rays, hdr, sink, transfer ? 1 : 0);
+        bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
+        if (precision == BL_PREC_MIXED)
+            bl::geodesic_kernel<float, double><<<di.sms * di.geo_blocks[pidx], 128, 0, st>>>(
+                d_desc, n_images, L.rays, hdr, sink, transfer ? 1 : 0);
+        else
+            bl::geodesic_kernel<float, bl::df64><<<di.sms * di.geo_blocks[pidx], 128, 0, st>>>(
+                d_desc, n_images, L.rays, hdr, sink, transfer ? 1 : 0);
     }
     ++g_launches;
     BL_CUDA(cudaGetLastError());
     if (timing) BL_CUDA(cudaEventRecord(g_ev[1], st));
     if (transfer) {
-        if (precision == BL_PREC_MIXED) {
+        if (precision != BL_PREC_FP64) {
             bl::transfer_kernel<float, float><<<di.sms * di.tr_blocks[pidx], 128, 0, st>>>(
                 d_desc, n_images, L.rays, hdr, (const float*)(ws + L.pool), chunks, ctr);
         } else {
@@ -280,6 +287,9 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
         if (transfer && (rc = device_pointer(grids[q].prim, what))) return rc;
     }
     Layout L = make_layout(n_images, cams, transfer ? precision : BL_PREC_MIXED);
+    if (!transfer && precision == BL_PREC_FP64) {
+        // geodesics only: no records, so the FP64 form's record type is irrelevant
+    }
     if (!transfer) { L.pool_chunks = 0; L.total = L.pool; }
     std::vector<bl::ImageDesc> descs(n_images);
     int64_t off = 0;

@@ -1,0 +1,99 @@
+// Double-float ("df64") arithmetic: a value is the unevaluated sum hi + lo of two floats
+// with |lo| <= ulp(hi)/2, giving a ~48-bit significand from FP32 instructions. On GB300 an
+// SM issues 128 FP32 lane-operations per cycle against 2 FP64 ones, so df64 evaluates the
+// geodesic right-hand side several times faster than native double at ~1e-14 relative
+// rounding. Algorithms (error-free transformations):
+//   TwoSum      Knuth, TAOCP vol. 2, 4.2.2 -- s + e = a + b exactly, no branch;
+//   Fast2Sum    Dekker 1971 -- s + e = a + b exactly when |a| >= |b|;
+//   TwoProd     with FMA: p = a b, e = fma(a, b, -p), p + e = a b exactly;
+//   sums and products of double-words as in Joldes, Muller & Popescu 2017 ("Tight and
+//   rigorous error bounds for basic building blocks of double-word arithmetic"), the
+//   accurate addition (their Alg. 6) and the FMA product (their Alg. 12 structure);
+//   1/x and 1/sqrt(x): one Newton step in df64 from the float approximation, which doubles
+//   the number of correct bits.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace bl {
+
+// The df64 overloads of sqrt, rsqrt and fabs below would hide the global float/double ones
+// inside this namespace; bring those into scope explicitly.
+using ::fabs;
+using ::rsqrt;
+using ::sqrt;
+
+struct df64 {
+    float hi, lo;
+    __host__ __device__ constexpr df64() : hi(0.0f), lo(0.0f) {}
+    __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+    // exact split of a double into two floats (rounded to ~48 bits)
+    __host__ __device__ constexpr explicit df64(double d)
+        : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ constexpr explicit df64(int i) : hi((float)i), lo(0.0f) {}
+};
+
+__device__ __forceinline__ df64 df_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return df64(s, e);
+}
+__device__ __forceinline__ df64 df_fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return df64(s, b - (s - a));
+}
+__device__ __forceinline__ df64 df_two_prod(float a, float b) {
+    const float p = a * b;
+    return df64(p, fmaf(a, b, -p));
+}
+
+__device__ __forceinline__ df64 operator+(const df64& x, const df64& y) {
+    df64 s = df_two_sum(x.hi, y.hi);
+    const df64 t = df_two_sum(x.lo, y.lo);
+    s.lo += t.hi;
+    s = df_fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return df_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df64 operator-(const df64& x) { return df64(-x.hi, -x.lo); }
+__device__ __forceinline__ df64 operator-(const df64& x, const df64& y) { return x + (-y); }
+__device__ __forceinline__ df64 operator*(const df64& x, const df64& y) {
+    df64 p = df_two_prod(x.hi, y.hi);
+    p.lo = fmaf(x.hi, y.lo, p.lo);
+    p.lo = fmaf(x.lo, y.hi, p.lo);
+    return df_fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df64 df_mul_f(const df64& x, float b) {
+    df64 p = df_two_prod(x.hi, b);
+    p.lo = fmaf(x.lo, b, p.lo);
+    return df_fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df64 rcp(const df64& x) {
+    const float y0 = 1.0f / x.hi;
+    // y1 = y0 + y0 (1 - x y0)
+    const df64 r = df64(1.0f, 0.0f) - df_mul_f(x, y0);
+    return df64(y0, 0.0f) + df_mul_f(r, y0);
+}
+__device__ __forceinline__ df64 operator/(const df64& x, const df64& y) { return x * rcp(y); }
+__device__ __forceinline__ df64 rsqrt(const df64& x) {
+    const float y0 = rsqrtf(x.hi);
+    // y1 = y0 + y0 (1 - x y0^2) / 2
+    const df64 r = df64(1.0f, 0.0f) - df_mul_f(df_mul_f(x, y0), y0);
+    return df64(y0, 0.0f) + df_mul_f(r, 0.5f * y0);
+}
+__device__ __forceinline__ df64 sqrt(const df64& x) {
+    if (x.hi <= 0.0f) return df64(0.0f, 0.0f);
+    return x * rsqrt(x);
+}
+__device__ __forceinline__ df64& operator+=(df64& x, const df64& y) { x = x + y; return x; }
+__device__ __forceinline__ df64& operator-=(df64& x, const df64& y) { x = x - y; return x; }
+__device__ __forceinline__ df64& operator*=(df64& x, const df64& y) { x = x * y; return x; }
+__device__ __forceinline__ bool operator<(const df64& x, const df64& y) {
+    return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo);
+}
+__device__ __forceinline__ bool operator>(const df64& x, const df64& y) { return y < x; }
+__device__ __forceinline__ df64 fabs(const df64& x) { return x.hi < 0.0f ? -x : x; }
+__device__ __forceinline__ double df_to_double(const df64& x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ df64 df_from_double(double d) { return df64(d); }
+
+}  // namespace bl

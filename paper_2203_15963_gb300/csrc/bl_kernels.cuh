@@ -1,6 +1,9 @@
 // Kernels of the Blacklight hot path: camera frame, persistent geodesic kernel (FP64) and
 // persistent transfer kernel (FP64 or FP32). Included by bl_api.cu only.
 #pragma once
+#include <type_traits>
+
+#include "bl_df64.cuh"
 #include "bl_internal.cuh"
 #include "bl_math.cuh"
 #include "../../include/blacklight.h"
@@ -153,6 +156,9 @@ __device__ __forceinline__ void pixel_of(int64_t p, int n, int& i, int& j) {
     }
 }
 
+__device__ __forceinline__ double im_spin(const ImageDesc* imgs, int q) { return imgs[q].spin; }
+__device__ __forceinline__ double im_mass(const ImageDesc* imgs, int q) { return imgs[q].mass; }
+
 // Warp-aggregated fetch-and-add: every lane that calls it gets a distinct index.
 __device__ __forceinline__ unsigned long long warp_fetch_add(unsigned long long* ctr) {
     const unsigned mask = __activemask();
@@ -269,10 +275,57 @@ struct RecordSink {
     Counters* ctr;
 };
 
+// Arithmetic used by the geodesic integrator: native double, or df64 (double-float).
+template <class G> struct GeoArith;
+template <> struct GeoArith<double> {
+    static __device__ __forceinline__ double from(double d) { return d; }
+    static __device__ __forceinline__ double to(double g) { return g; }
+    static __device__ __forceinline__ float tof(double g) { return (float)g; }
+};
+template <> struct GeoArith<float> {
+    static __device__ __forceinline__ float from(double d) { return (float)d; }
+    static __device__ __forceinline__ double to(float g) { return (double)g; }
+    static __device__ __forceinline__ float tof(float g) { return g; }
+};
+template <> struct GeoArith<df64> {
+    static __device__ __forceinline__ df64 from(double d) { return df64(d); }
+    static __device__ __forceinline__ double to(const df64& g) { return df_to_double(g); }
+    static __device__ __forceinline__ float tof(const df64& g) { return g.hi + g.lo; }
+};
+
+// Eq. (geodesic) right-hand side in arithmetic G (see the double form in bl_math.cuh);
+// returns r at the evaluation point.
+template <class G>
+__device__ __forceinline__ G geodesic_rhs_g(const G y[8], const G& a, const G& m, bool flat, G dy[8]) {
+    KSGeom<G> K;
+    ks_geom<G>(y[1], y[2], y[3], a, m, flat, true, K);
+    const G* k = y + 4;
+    const G L = K.l[1] * k[1] + K.l[2] * k[2] + K.l[3] * k[3] - k[0];
+    const G fL = K.f * L;
+    dy[0] = fL - k[0];
+    dy[1] = k[1] - K.l[1] * fL;
+    dy[2] = k[2] - K.l[2] * fL;
+    dy[3] = k[3] - K.l[3] * fL;
+    dy[4] = G(0);
+    const G halfL = G(0.5) * L;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const G S = K.dl[c][0] * k[1] + K.dl[c][1] * k[2] + K.dl[c][2] * k[3];
+        dy[5 + c] = L * (K.df[c] * halfL + K.f * S);
+    }
+    return K.r;
+}
+
+template <class R, class G>
+__device__ __forceinline__ R to_rec(const G& v) {
+    if constexpr (sizeof(R) == sizeof(float)) return (R)GeoArith<G>::tof(v);
+    else return (R)GeoArith<G>::to(v);
+}
+
 // Append one record for `ray`; returns false when the store is full.
-template <class R>
+template <class R, class G>
 __device__ __forceinline__ bool append_record(const RecordSink<R>& S, int64_t ray, int32_t& nrec,
-                                              const double ys[8], const double yn[8], double dl) {
+                                              const G ys[8], const G yn[8], double dl) {
     const int32_t slot = nrec % kChunk;
     const int32_t ch = nrec / kChunk;
     if (ch >= kMaxChunks) return false;
@@ -284,38 +337,43 @@ __device__ __forceinline__ bool append_record(const RecordSink<R>& S, int64_t ra
     }
     const int64_t idx = (int64_t)tab[ch] * kChunk + slot;
     R* rec = S.pool + idx * RecStride<R>::v;
-    rec[0] = (R)ys[1]; rec[1] = (R)ys[2]; rec[2] = (R)ys[3];
-    rec[3] = (R)ys[5]; rec[4] = (R)ys[6]; rec[5] = (R)ys[7];
-    rec[6] = (R)yn[1]; rec[7] = (R)yn[2]; rec[8] = (R)yn[3];
-    rec[9] = (R)yn[5]; rec[10] = (R)yn[6]; rec[11] = (R)yn[7];
+    rec[0] = to_rec<R>(ys[1]); rec[1] = to_rec<R>(ys[2]); rec[2] = to_rec<R>(ys[3]);
+    rec[3] = to_rec<R>(ys[5]); rec[4] = to_rec<R>(ys[6]); rec[5] = to_rec<R>(ys[7]);
+    rec[6] = to_rec<R>(yn[1]); rec[7] = to_rec<R>(yn[2]); rec[8] = to_rec<R>(yn[3]);
+    rec[9] = to_rec<R>(yn[5]); rec[10] = to_rec<R>(yn[6]); rec[11] = to_rec<R>(yn[7]);
     rec[12] = (R)dl;
     ++nrec;
     return true;
 }
 
-template <class R>
-__global__ void __launch_bounds__(128) geodesic_kernel(const ImageDesc* __restrict__ imgs,
-                                                       int n_images, int64_t total_rays,
-                                                       RayHdr* __restrict__ hdr,
-                                                       RecordSink<R> sink, int record) {
+template <class R, class G>
+__global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __restrict__ imgs,
+                                                          int n_images, int64_t total_rays,
+                                                          RayHdr* __restrict__ hdr,
+                                                          RecordSink<R> sink, int record) {
+    using A = GeoArith<G>;
+    constexpr bool kNative = std::is_same<G, double>::value;
     Counters* ctr = sink.ctr;
     bool active = false;
     int64_t ray = 0;
     int q = 0, pi = 0, pj = 0;
-    double y[8], f1[8];
-    double h = 0.0, nnorm = 0.0;
+    G y[8], f1[8];
+    G h = G(0);
+    double nnorm = 0.0;
     bool been_inside = false, prev_rej = false;
     int64_t attempts = 0;
     int32_t nrec = 0, status = 0;
-    double r_cam = 0.0, r_in = 0.0, a = 0.0, m = 0.0, ds_max = 0.0, r_grid = 0.0;
+    double r_cam = 0.0, r_in = 0.0, ds_max = 0.0, r_grid = 0.0;
+    G a = G(0), m = G(0);
     double tol_abs = 0.0, tol_rel = 0.0;
     int64_t max_steps = 0;
     bool flat = false;
+    double r_cur = 0.0;     // r at y
 
     bool exhausted = false;
     // All 32 lanes stay in the loop until the whole warp is out of work, so the warp
-    // reconverges every iteration and the FP64 attempt is issued once for all lanes that
-    // hold a ray (lanes without one are masked).
+    // reconverges every iteration and the attempt is issued once for all lanes that hold a
+    // ray (lanes without one are masked).
     while (true) {
         const bool need = !active && !exhausted;
         const unsigned long long got = warp_refill(&ctr->next_ray_geo, need);
@@ -333,56 +391,78 @@ __global__ void __launch_bounds__(128) geodesic_kernel(const ImageDesc* __restri
             q = find_image(imgs, n_images, ray);
             const ImageDesc& im = imgs[q];
             pixel_of(ray - im.ray_offset, im.n, pi, pj);
-            pixel_state(im, pi, pj, y, nnorm);
-            a = im.spin; m = im.mass; flat = im.flat != 0;
+            double yd[8];
+            pixel_state(im, pi, pj, yd, nnorm);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) y[c] = A::from(yd[c]);
+            a = A::from(im.spin); m = A::from(im.mass); flat = im.flat != 0;
             r_cam = im.r_cam;
             r_in = im.r_in_over_rhor * im.r_hor;
             ds_max = im.ds_max;
             r_grid = im.r_max;
             tol_abs = im.tol_abs; tol_rel = im.tol_rel;
             max_steps = im.max_steps;
-            geodesic_rhs(y, a, m, flat, f1);
-            h = -im.h0_frac * (r_cam - im.r_hor);
-            been_inside = ks_r<double>(y[1], y[2], y[3], a) < r_cam;
+            r_cur = A::to(geodesic_rhs_g<G>(y, a, m, flat, f1));
+            h = A::from(-im.h0_frac * (r_cam - im.r_hor));
+            been_inside = r_cur < r_cam;
             prev_rej = false;
         }
-        // ---- one Dormand-Prince attempt ----
-        double k2[8], k3[8], k4[8], k5[8], k6[8], k7[8], ys[8], y5[8];
+        // ---- one Dormand-Prince attempt (Table tab:dp) ----
+        G k2[8], k3[8], k4[8], k5[8], k6[8], k7[8], ys[8], y5[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) ys[c] = y[c] + h * (DP_A21 * f1[c]);
-        geodesic_rhs(ys, a, m, flat, k2);
+        for (int c = 0; c < 8; ++c) ys[c] = y[c] + h * (G(DP_A21) * f1[c]);
+        geodesic_rhs_g<G>(ys, a, m, flat, k2);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) ys[c] = y[c] + h * (DP_A31 * f1[c] + DP_A32 * k2[c]);
-        geodesic_rhs(ys, a, m, flat, k3);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) ys[c] = y[c] + h * (DP_A41 * f1[c] + DP_A42 * k2[c] + DP_A43 * k3[c]);
-        geodesic_rhs(ys, a, m, flat, k4);
+        for (int c = 0; c < 8; ++c) ys[c] = y[c] + h * (G(DP_A31) * f1[c] + G(DP_A32) * k2[c]);
+        geodesic_rhs_g<G>(ys, a, m, flat, k3);
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-            ys[c] = y[c] + h * (DP_A51 * f1[c] + DP_A52 * k2[c] + DP_A53 * k3[c] + DP_A54 * k4[c]);
-        geodesic_rhs(ys, a, m, flat, k5);
+            ys[c] = y[c] + h * (G(DP_A41) * f1[c] + G(DP_A42) * k2[c] + G(DP_A43) * k3[c]);
+        geodesic_rhs_g<G>(ys, a, m, flat, k4);
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-            ys[c] = y[c] + h * (DP_A61 * f1[c] + DP_A62 * k2[c] + DP_A63 * k3[c] + DP_A64 * k4[c] +
-                                DP_A65 * k5[c]);
-        geodesic_rhs(ys, a, m, flat, k6);
+            ys[c] = y[c] + h * (G(DP_A51) * f1[c] + G(DP_A52) * k2[c] + G(DP_A53) * k3[c] +
+                                G(DP_A54) * k4[c]);
+        geodesic_rhs_g<G>(ys, a, m, flat, k5);
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-            y5[c] = y[c] + h * (DP_B1 * f1[c] + DP_B3 * k3[c] + DP_B4 * k4[c] + DP_B5 * k5[c] + DP_B6 * k6[c]);
-        geodesic_rhs(y5, a, m, flat, k7);
-        // eps = max_c |err_c| / sc_c, tracked as the largest fraction (num / den) by
-        // cross-multiplication so that only one division is needed
-        double num = 0.0, den = 1.0;
+            ys[c] = y[c] + h * (G(DP_A61) * f1[c] + G(DP_A62) * k2[c] + G(DP_A63) * k3[c] +
+                                G(DP_A64) * k4[c] + G(DP_A65) * k5[c]);
+        geodesic_rhs_g<G>(ys, a, m, flat, k6);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            y5[c] = y[c] + h * (G(DP_B1) * f1[c] + G(DP_B3) * k3[c] + G(DP_B4) * k4[c] +
+                                G(DP_B5) * k5[c] + G(DP_B6) * k6[c]);
+        const double r5 = A::to(geodesic_rhs_g<G>(y5, a, m, flat, k7));
+        // Error norm eps = max_c |y5_c - y4_c| / (f_abs + f_rel max(|y_c|, |y5_c|)) with
+        // y5 - y4 = h sum (b5 - b4) k. Native double keeps the FP64 form's arithmetic; the
+        // df64 form takes the ratio in float (it only steers the step size).
+        double eps;
         bool finite = true;
+        if constexpr (kNative) {
+            double num = 0.0, den = 1.0;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const double err = fabs(h * (DP_E1 * f1[c] + DP_E3 * k3[c] + DP_E4 * k4[c] + DP_E5 * k5[c] +
-                                         DP_E6 * k6[c] + DP_E7 * k7[c]));
-            const double sc = tol_abs + tol_rel * fmax(fabs(y[c]), fabs(y5[c]));
-            finite = finite && isfinite(err) && isfinite(y5[c]);
-            if (err * den > num * sc) { num = err; den = sc; }
+            for (int c = 0; c < 8; ++c) {
+                const double err = fabs(A::to(h * (G(DP_E1) * f1[c] + G(DP_E3) * k3[c] + G(DP_E4) * k4[c] +
+                                                   G(DP_E5) * k5[c] + G(DP_E6) * k6[c] + G(DP_E7) * k7[c])));
+                const double sc = tol_abs + tol_rel * fmax(fabs(A::to(y[c])), fabs(A::to(y5[c])));
+                finite = finite && isfinite(err) && isfinite(A::to(y5[c]));
+                if (err * den > num * sc) { num = err; den = sc; }
+            }
+            eps = num / den;
+        } else {
+            float num = 0.0f, den = 1.0f;
+            const float ta = (float)tol_abs, tr = (float)tol_rel;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float err = fabsf(A::tof(h * (G(DP_E1) * f1[c] + G(DP_E3) * k3[c] + G(DP_E4) * k4[c] +
+                                                    G(DP_E5) * k5[c] + G(DP_E6) * k6[c] + G(DP_E7) * k7[c])));
+                const float sc = ta + tr * fmaxf(fabsf(A::tof(y[c])), fabsf(A::tof(y5[c])));
+                finite = finite && isfinite(err) && isfinite(A::tof(y5[c]));
+                if (err * den > num * sc) { num = err; den = sc; }
+            }
+            eps = (double)(num / den);
         }
-        const double eps = num / den;
         ++attempts;
         bool done = false;
         if (!finite) {
@@ -391,22 +471,41 @@ __global__ void __launch_bounds__(128) geodesic_kernel(const ImageDesc* __restri
         } else if (eps <= 1.0) {
             // accepted: samples of this step (camera side first)
             if (record) {
-                double ym[8];
+                G ym[8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
-                    ym[c] = y[c] + 0.5 * h * (DP_M1 * f1[c] + DP_M3 * k3[c] + DP_M4 * k4[c] +
-                                              DP_M5 * k5[c] + DP_M6 * k6[c] + DP_M7 * k7[c]);
-                const double r0 = ks_r<double>(y[1], y[2], y[3], a);
-                const double r1 = ks_r<double>(y5[1], y5[2], y5[3], a);
-                KSGeom<double> Gm;
-                ks_geom<double>(ym[1], ym[2], ym[3], a, m, flat, false, Gm);
-                const double rmin = fmin(Gm.r, fmin(r0, r1));
+                    ym[c] = y[c] + (G(0.5) * h) * (G(DP_M1) * f1[c] + G(DP_M3) * k3[c] + G(DP_M4) * k4[c] +
+                                                   G(DP_M5) * k5[c] + G(DP_M6) * k6[c] + G(DP_M7) * k7[c]);
+                const double r0 = r_cur, r1 = r5;
+                const double hd = A::to(h);
+                double rmid, kt_up, fmid;
+                if constexpr (kNative) {
+                    double ymd[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) ymd[c] = A::to(ym[c]);
+                    KSGeom<double> Gm;
+                    ks_geom<double>(ymd[1], ymd[2], ymd[3], im_spin(imgs, q), im_mass(imgs, q), flat, false, Gm);
+                    const double L = -ymd[4] + Gm.l[1] * ymd[5] + Gm.l[2] * ymd[6] + Gm.l[3] * ymd[7];
+                    kt_up = -ymd[4] + Gm.f * L;
+                    rmid = Gm.r;
+                    fmid = Gm.f;
+                } else {
+                    float ymf[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) ymf[c] = A::tof(ym[c]);
+                    KSGeom<float> Gm;
+                    ks_geom<float>(ymf[1], ymf[2], ymf[3], (float)im_spin(imgs, q), (float)im_mass(imgs, q),
+                                   flat, false, Gm);
+                    const float L = -ymf[4] + Gm.l[1] * ymf[5] + Gm.l[2] * ymf[6] + Gm.l[3] * ymf[7];
+                    kt_up = -ymf[4] + Gm.f * L;
+                    rmid = Gm.r;
+                    fmid = Gm.f;
+                }
+                const double rmin = fmin(rmid, fmin(r0, r1));
                 int nsub = 1;
                 if (rmin < r_grid) {
                     // ds/dl = (g_pq k^p k^q)^1/2 = alpha |k^t| for a null ray
-                    const double L = -ym[4] + Gm.l[1] * ym[5] + Gm.l[2] * ym[6] + Gm.l[3] * ym[7];
-                    const double kt_up = -ym[4] + Gm.f * L;
-                    const double ds = fabs(h) * fabs(kt_up) / sqrt(1.0 + Gm.f);
+                    const double ds = fabs(hd) * fabs(kt_up) / sqrt(1.0 + fmid);
                     if (ds > ds_max) {
                         const double nd = ceil(ds / ds_max);
                         nsub = nd > 4096.0 ? 4097 : (int)nd;
@@ -414,77 +513,90 @@ __global__ void __launch_bounds__(128) geodesic_kernel(const ImageDesc* __restri
                 }
                 bool ok = true;
                 if (nsub == 1) {
-                    ok = append_record(sink, ray, nrec, ym, y, fabs(h));
-                } else {
-                    // quartic through y0, y1, h f0, h f1 and y_mid (Shampine 1986)
-                    double c2[8], c3[8], c4[8], d0[8];
+                    ok = append_record(sink, ray, nrec, ym, y, fabs(hd));
+                } else if (sizeof(R) == sizeof(float)) {
+                    // float records: the quartic through y0, y1, h f0, h f1 and y_mid
+                    // (Shampine 1986), evaluated in FP32 about y0
+                    float y0f[8], d0f[8], c2f[8], c3f[8], c4f[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        d0[c] = h * f1[c];
-                        const double D1 = y5[c] - y[c] - d0[c];
-                        const double D2 = h * k7[c] - d0[c];
-                        const double D3 = ym[c] - y[c] - 0.5 * d0[c];
+                        const G d0 = h * f1[c];
+                        const G D1 = y5[c] - y[c] - d0;
+                        const G D2 = h * k7[c] - d0;
+                        const G D3 = ym[c] - y[c] - G(0.5) * d0;
+                        y0f[c] = A::tof(y[c]);
+                        d0f[c] = A::tof(d0);
+                        c2f[c] = A::tof(G(-5.0) * D1 + D2 + G(16.0) * D3);
+                        c3f[c] = A::tof(G(14.0) * D1 - G(3.0) * D2 - G(32.0) * D3);
+                        c4f[c] = A::tof(G(-8.0) * D1 + G(2.0) * D2 + G(16.0) * D3);
+                    }
+                    const float invf = 1.0f / (float)nsub;
+                    for (int s = 0; s < nsub && ok; ++s) {
+                        float ysm[8], ynd[8];
+                        const float ts = (s + 0.5f) * invf, tn = s * invf;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            ysm[c] = y0f[c] + ts * (d0f[c] + ts * (c2f[c] + ts * (c3f[c] + ts * c4f[c])));
+                            ynd[c] = (s == 0) ? y0f[c]
+                                              : y0f[c] + tn * (d0f[c] + tn * (c2f[c] + tn * (c3f[c] + tn * c4f[c])));
+                        }
+                        ok = append_record(sink, ray, nrec, ysm, ynd, fabs(hd) / nsub);
+                    }
+                } else {
+                    double y0d[8], d0[8], c2[8], c3[8], c4[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        y0d[c] = A::to(y[c]);
+                        d0[c] = hd * A::to(f1[c]);
+                        const double D1 = A::to(y5[c]) - y0d[c] - d0[c];
+                        const double D2 = hd * A::to(k7[c]) - d0[c];
+                        const double D3 = A::to(ym[c]) - y0d[c] - 0.5 * d0[c];
                         c2[c] = -5.0 * D1 + D2 + 16.0 * D3;
                         c3[c] = 14.0 * D1 - 3.0 * D2 - 32.0 * D3;
                         c4[c] = -8.0 * D1 + 2.0 * D2 + 16.0 * D3;
                     }
                     const double inv = 1.0 / nsub;
-                    if (sizeof(R) == sizeof(float)) {
-                        // float records: evaluate the quartic in FP32 about y0 (the stored
-                        // values carry FP32 precision anyway)
-                        float y0f[8], d0f[8], c2f[8], c3f[8], c4f[8];
+                    for (int s = 0; s < nsub && ok; ++s) {
+                        double ysm[8], ynd[8];
+                        const double ts = (s + 0.5) * inv, tn = s * inv;
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
-                            y0f[c] = (float)y[c]; d0f[c] = (float)d0[c]; c2f[c] = (float)c2[c];
-                            c3f[c] = (float)c3[c]; c4f[c] = (float)c4[c];
+                            ysm[c] = y0d[c] + ts * (d0[c] + ts * (c2[c] + ts * (c3[c] + ts * c4[c])));
+                            ynd[c] = (s == 0) ? y0d[c]
+                                              : y0d[c] + tn * (d0[c] + tn * (c2[c] + tn * (c3[c] + tn * c4[c])));
                         }
-                        const float invf = 1.0f / (float)nsub;
-                        for (int s = 0; s < nsub && ok; ++s) {
-                            double ysm[8], ynd[8];
-                            const float ts = (s + 0.5f) * invf, tn = s * invf;
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) {
-                                ysm[c] = y0f[c] + ts * (d0f[c] + ts * (c2f[c] + ts * (c3f[c] + ts * c4f[c])));
-                                ynd[c] = (s == 0) ? y[c]
-                                                  : y0f[c] + tn * (d0f[c] + tn * (c2f[c] + tn * (c3f[c] + tn * c4f[c])));
-                            }
-                            ok = append_record(sink, ray, nrec, ysm, ynd, fabs(h) * inv);
-                        }
-                    } else {
-                        for (int s = 0; s < nsub && ok; ++s) {
-                            double ysm[8], ynd[8];
-                            const double ts = (s + 0.5) * inv, tn = s * inv;
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) {
-                                ysm[c] = y[c] + ts * (d0[c] + ts * (c2[c] + ts * (c3[c] + ts * c4[c])));
-                                ynd[c] = (s == 0) ? y[c]
-                                                  : y[c] + tn * (d0[c] + tn * (c2[c] + tn * (c3[c] + tn * c4[c])));
-                            }
-                            ok = append_record(sink, ray, nrec, ysm, ynd, fabs(h) * inv);
-                        }
+                        ok = append_record(sink, ray, nrec, ysm, ynd, fabs(hd) * inv);
                     }
                 }
                 if (!ok) { status = BL_RAY_OVERFLOW; done = true; }
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) { y[c] = y5[c]; f1[c] = k7[c]; }
-            double fac = (eps == 0.0) ? 10.0 : 0.9 * pow(eps, -0.2);
+            double fac;
+            if constexpr (kNative) {
+                fac = (eps == 0.0) ? 10.0 : 0.9 * pow(eps, -0.2);
+            } else {
+                fac = (eps == 0.0) ? 10.0 : (double)(0.9f * powf((float)eps, -0.2f));
+            }
             fac = fmin(10.0, fmax(0.2, fac));
             if (prev_rej) fac = fmin(fac, 1.0);
-            h *= fac;
+            h = h * A::from(fac);
             prev_rej = false;
+            r_cur = r5;
             if (!done) {
-                const double rr = ks_r<double>(y[1], y[2], y[3], a);
-                if (rr < r_in) { status = BL_RAY_HORIZON; done = true; }
-                else if (been_inside && rr > r_cam) { status = BL_RAY_ESCAPED; done = true; }
-                else if (rr < r_cam) been_inside = true;
+                if (r_cur < r_in) { status = BL_RAY_HORIZON; done = true; }
+                else if (been_inside && r_cur > r_cam) { status = BL_RAY_ESCAPED; done = true; }
+                else if (r_cur < r_cam) been_inside = true;
             }
         } else {
-            h *= fmax(0.2, 0.9 * pow(eps, -0.2));
+            double fac;
+            if constexpr (kNative) fac = fmax(0.2, 0.9 * pow(eps, -0.2));
+            else fac = fmax(0.2, (double)(0.9f * powf((float)eps, -0.2f)));
+            h = h * A::from(fac);
             prev_rej = true;
         }
         if (!done) {
-            if (fabs(h) < 1e-12 * ks_r<double>(y[1], y[2], y[3], a)) { status = BL_RAY_UNDERFLOW; done = true; }
+            if (fabs(A::to(h)) < 1e-12 * r_cur) { status = BL_RAY_UNDERFLOW; done = true; }
             else if (attempts >= max_steps) { status = BL_RAY_MAX_STEPS; done = true; }
         }
         if (done) {
@@ -493,10 +605,10 @@ __global__ void __launch_bounds__(128) geodesic_kernel(const ImageDesc* __restri
             if (im.status) im.status[pix] = status;
             if (im.steps) im.steps[pix] = (int32_t)(attempts < 2147483647 ? attempts : 2147483647);
             if (im.end_state)
-                for (int c = 0; c < 8; ++c) im.end_state[pix * 8 + c] = y[c];
+                for (int c = 0; c < 8; ++c) im.end_state[pix * 8 + c] = A::to(y[c]);
             if (im.samples) im.samples[pix] = nrec;
             RayHdr hd;
-            hd.kt = y[4];
+            hd.kt = A::to(y[4]);
             hd.nnorm = nnorm;
             hd.nrec = nrec;
             hd.status = status;

@@ -109,8 +109,9 @@ __device__ __forceinline__ T dot4(const KSGeom<T>& G, const T u[4], const T v[4]
 
 // Eq. (geodesic): dx^a/dl = g^ab k_b; dk_t/dl = 0; dk_c/dl = -1/2 d_c g^ab k_a k_b
 //   = L (1/2 d_c f L + f sum_b d_c l_b k_b),  L = l^a k_a.
-__device__ __forceinline__ void geodesic_rhs(const double y[8], double a, double m, bool flat,
-                                             double dy[8]) {
+// Returns r at the evaluation point (used for the termination tests).
+__device__ __forceinline__ double geodesic_rhs(const double y[8], double a, double m, bool flat,
+                                               double dy[8]) {
     KSGeom<double> G;
     ks_geom<double>(y[1], y[2], y[3], a, m, flat, true, G);
     const double* k = y + 4;
@@ -125,6 +126,7 @@ __device__ __forceinline__ void geodesic_rhs(const double y[8], double a, double
         const double S = G.dl[c][0] * k[1] + G.dl[c][1] * k[2] + G.dl[c][2] * k[3];
         dy[5 + c] = L * (0.5 * G.df[c] * L + G.f * S);
     }
+    return G.r;
 }
 
 // ---------------------------------------------------------------------------------------

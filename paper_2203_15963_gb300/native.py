@@ -17,7 +17,7 @@ _LIB = os.path.join(_HERE, "_lib", "libblacklight.so")
 _INCLUDE = os.path.join(_ROOT, "include")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-BL_PREC_FP64, BL_PREC_MIXED = 0, 1
+BL_PREC_FP64, BL_PREC_MIXED, BL_PREC_FAST = 0, 1, 2
 BL_ASYNC = 1
 BL_TIMING = 2
 RAY_STATUS = {0: "ok", 1: "horizon", 2: "escaped", 3: "max_steps", 4: "underflow", 5: "nan",
