@@ -69,7 +69,7 @@ __device__ __forceinline__ df64 df_mul_f(const df64& x, float b) {
     return df_fast_two_sum(p.hi, p.lo);
 }
 __device__ __forceinline__ df64 rcp(const df64& x) {
-    const float y0 = 1.0f / x.hi;
+    const float y0 = __fdividef(1.0f, x.hi);   // ~2 ulp seed; the Newton step below refines it
     // y1 = y0 + y0 (1 - x y0)
     const df64 r = df64(1.0f, 0.0f) - df_mul_f(x, y0);
     return df64(y0, 0.0f) + df_mul_f(r, y0);

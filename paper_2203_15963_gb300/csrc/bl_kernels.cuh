@@ -267,6 +267,50 @@ __device__ __forceinline__ void pixel_state(const ImageDesc& im, int i, int j, d
 #define DP_M6 (-1776094331.0 / 19743644256.0)
 #define DP_M7 (11237099.0 / 235043384.0)
 
+// Dormand-Prince RK5(4)7M coefficients (Table tab:dp) in constant memory, read with
+// warp-uniform indices by the rolled stage loop: row s of a (s = 1..6; row 6 is the
+// fifth-order weights, the first-same-as-last stage), the error weights b5 - b4 and the
+// fourth-order midpoint weights.
+struct DPTable {
+    double a[7][7];
+    double e[7];
+    double m[7];
+};
+struct DPTableF {     // the same values as double-float pairs
+    float2 a[7][7];
+    float2 e[7];
+    float2 m[7];
+};
+#define DP_ROW(...) __VA_ARGS__
+__constant__ DPTable c_dp = {
+    {{0, 0, 0, 0, 0, 0, 0},
+     {DP_A21, 0, 0, 0, 0, 0, 0},
+     {DP_A31, DP_A32, 0, 0, 0, 0, 0},
+     {DP_A41, DP_A42, DP_A43, 0, 0, 0, 0},
+     {DP_A51, DP_A52, DP_A53, DP_A54, 0, 0, 0},
+     {DP_A61, DP_A62, DP_A63, DP_A64, DP_A65, 0, 0},
+     {DP_B1, 0, DP_B3, DP_B4, DP_B5, DP_B6, 0}},
+    {DP_E1, 0, DP_E3, DP_E4, DP_E5, DP_E6, DP_E7},
+    {DP_M1, 0, DP_M3, DP_M4, DP_M5, DP_M6, DP_M7}};
+#define DF2(d) float2{(float)(d), (float)((d) - (double)(float)(d))}
+__constant__ DPTableF c_dpf = {
+    {{DF2(0.0), DF2(0.0), DF2(0.0), DF2(0.0), DF2(0.0), DF2(0.0), DF2(0.0)},
+     {DF2(DP_A21), DF2(0.0), DF2(0.0), DF2(0.0), DF2(0.0), DF2(0.0), DF2(0.0)},
+     {DF2(DP_A31), DF2(DP_A32), DF2(0.0), DF2(0.0), DF2(0.0), DF2(0.0), DF2(0.0)},
+     {DF2(DP_A41), DF2(DP_A42), DF2(DP_A43), DF2(0.0), DF2(0.0), DF2(0.0), DF2(0.0)},
+     {DF2(DP_A51), DF2(DP_A52), DF2(DP_A53), DF2(DP_A54), DF2(0.0), DF2(0.0), DF2(0.0)},
+     {DF2(DP_A61), DF2(DP_A62), DF2(DP_A63), DF2(DP_A64), DF2(DP_A65), DF2(0.0), DF2(0.0)},
+     {DF2(DP_B1), DF2(0.0), DF2(DP_B3), DF2(DP_B4), DF2(DP_B5), DF2(DP_B6), DF2(0.0)}},
+    {DF2(DP_E1), DF2(0.0), DF2(DP_E3), DF2(DP_E4), DF2(DP_E5), DF2(DP_E6), DF2(DP_E7)},
+    {DF2(DP_M1), DF2(0.0), DF2(DP_M3), DF2(DP_M4), DF2(DP_M5), DF2(DP_M6), DF2(DP_M7)}};
+
+template <class G> struct DPCoef;
+template <> struct DPCoef<double> {
+    static __device__ __forceinline__ double a(int s, int j) { return c_dp.a[s][j]; }
+    static __device__ __forceinline__ double e(int j) { return c_dp.e[j]; }
+    static __device__ __forceinline__ double m(int j) { return c_dp.m[j]; }
+};
+
 template <class R>
 struct RecordSink {
     R* pool;
@@ -306,8 +350,9 @@ __device__ __forceinline__ G geodesic_rhs_g(const G y[8], const G& a, const G& m
     dy[1] = k[1] - K.l[1] * fL;
     dy[2] = k[2] - K.l[2] * fL;
     dy[3] = k[3] - K.l[3] * fL;
-    dy[4] = G(0);
-    const G halfL = G(0.5) * L;
+    constexpr G kZero = G(0), kHalf = G(0.5);
+    dy[4] = kZero;
+    const G halfL = kHalf * L;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const G S = K.dl[c][0] * k[1] + K.dl[c][1] * k[2] + K.dl[c][2] * k[3];
@@ -315,6 +360,12 @@ __device__ __forceinline__ G geodesic_rhs_g(const G y[8], const G& a, const G& m
     }
     return K.r;
 }
+
+template <> struct DPCoef<df64> {
+    static __device__ __forceinline__ df64 a(int s, int j) { const float2 v = c_dpf.a[s][j]; return df64(v.x, v.y); }
+    static __device__ __forceinline__ df64 e(int j) { const float2 v = c_dpf.e[j]; return df64(v.x, v.y); }
+    static __device__ __forceinline__ df64 m(int j) { const float2 v = c_dpf.m[j]; return df64(v.x, v.y); }
+};
 
 template <class R, class G>
 __device__ __forceinline__ R to_rec(const G& v) {
@@ -352,12 +403,55 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
                                                           RayHdr* __restrict__ hdr,
                                                           RecordSink<R> sink, int record) {
     using A = GeoArith<G>;
+    // compile-time constants in the integrator arithmetic (a run-time double -> df64 split
+    // would cost FP64 conversions)
+    constexpr G kDP_A21 = G(DP_A21);
+    constexpr G kDP_A31 = G(DP_A31);
+    constexpr G kDP_A32 = G(DP_A32);
+    constexpr G kDP_A41 = G(DP_A41);
+    constexpr G kDP_A42 = G(DP_A42);
+    constexpr G kDP_A43 = G(DP_A43);
+    constexpr G kDP_A51 = G(DP_A51);
+    constexpr G kDP_A52 = G(DP_A52);
+    constexpr G kDP_A53 = G(DP_A53);
+    constexpr G kDP_A54 = G(DP_A54);
+    constexpr G kDP_A61 = G(DP_A61);
+    constexpr G kDP_A62 = G(DP_A62);
+    constexpr G kDP_A63 = G(DP_A63);
+    constexpr G kDP_A64 = G(DP_A64);
+    constexpr G kDP_A65 = G(DP_A65);
+    constexpr G kDP_B1 = G(DP_B1);
+    constexpr G kDP_B3 = G(DP_B3);
+    constexpr G kDP_B4 = G(DP_B4);
+    constexpr G kDP_B5 = G(DP_B5);
+    constexpr G kDP_B6 = G(DP_B6);
+    constexpr G kDP_E1 = G(DP_E1);
+    constexpr G kDP_E3 = G(DP_E3);
+    constexpr G kDP_E4 = G(DP_E4);
+    constexpr G kDP_E5 = G(DP_E5);
+    constexpr G kDP_E6 = G(DP_E6);
+    constexpr G kDP_E7 = G(DP_E7);
+    constexpr G kDP_M1 = G(DP_M1);
+    constexpr G kDP_M3 = G(DP_M3);
+    constexpr G kDP_M4 = G(DP_M4);
+    constexpr G kDP_M5 = G(DP_M5);
+    constexpr G kDP_M6 = G(DP_M6);
+    constexpr G kDP_M7 = G(DP_M7);
+    constexpr G kHalf = G(0.5);
+    constexpr G kM5 = G(-5.0);
+    constexpr G k16 = G(16.0);
+    constexpr G k14 = G(14.0);
+    constexpr G kThree = G(3.0);
+    constexpr G k32 = G(32.0);
+    constexpr G kM8 = G(-8.0);
+    constexpr G k2c = G(2.0);
     constexpr bool kNative = std::is_same<G, double>::value;
     Counters* ctr = sink.ctr;
     bool active = false;
     int64_t ray = 0;
     int q = 0, pi = 0, pj = 0;
-    G y[8], f1[8];
+    G y[8];
+    G K[7][8];          // K[0] = f(y); K[1..6] stage derivatives of the current attempt
     G h = G(0);
     double nnorm = 0.0;
     bool been_inside = false, prev_rej = false;
@@ -402,66 +496,69 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
             r_grid = im.r_max;
             tol_abs = im.tol_abs; tol_rel = im.tol_rel;
             max_steps = im.max_steps;
-            r_cur = A::to(geodesic_rhs_g<G>(y, a, m, flat, f1));
+            r_cur = A::to(geodesic_rhs_g<G>(y, a, m, flat, K[0]));
             h = A::from(-im.h0_frac * (r_cam - im.r_hor));
             been_inside = r_cur < r_cam;
             prev_rej = false;
         }
         // ---- one Dormand-Prince attempt (Table tab:dp) ----
-        G k2[8], k3[8], k4[8], k5[8], k6[8], k7[8], ys[8], y5[8];
+        // Rolled stage loop: one right-hand-side body run six times keeps the kernel small
+        // enough for the instruction cache. K[0] holds f(y) (first same as last), K[s] the
+        // stage derivatives; stage 6 is evaluated at the fifth-order solution y5.
+        G ys[8], y5[8];
+        double r5 = 0.0;
+#pragma unroll 1
+        for (int st = 1; st < 7; ++st) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) ys[c] = y[c] + h * (G(DP_A21) * f1[c]);
-        geodesic_rhs_g<G>(ys, a, m, flat, k2);
+            for (int c = 0; c < 8; ++c) {
+                G acc = DPCoef<G>::a(st, 0) * K[0][c];
+#pragma unroll 1
+                for (int j = 1; j < st; ++j) acc = acc + DPCoef<G>::a(st, j) * K[j][c];
+                ys[c] = y[c] + h * acc;
+            }
+            const G rr = geodesic_rhs_g<G>(ys, a, m, flat, K[st]);
+            if (st == 6) {
+                r5 = A::to(rr);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) ys[c] = y[c] + h * (G(DP_A31) * f1[c] + G(DP_A32) * k2[c]);
-        geodesic_rhs_g<G>(ys, a, m, flat, k3);
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            ys[c] = y[c] + h * (G(DP_A41) * f1[c] + G(DP_A42) * k2[c] + G(DP_A43) * k3[c]);
-        geodesic_rhs_g<G>(ys, a, m, flat, k4);
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            ys[c] = y[c] + h * (G(DP_A51) * f1[c] + G(DP_A52) * k2[c] + G(DP_A53) * k3[c] +
-                                G(DP_A54) * k4[c]);
-        geodesic_rhs_g<G>(ys, a, m, flat, k5);
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            ys[c] = y[c] + h * (G(DP_A61) * f1[c] + G(DP_A62) * k2[c] + G(DP_A63) * k3[c] +
-                                G(DP_A64) * k4[c] + G(DP_A65) * k5[c]);
-        geodesic_rhs_g<G>(ys, a, m, flat, k6);
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            y5[c] = y[c] + h * (G(DP_B1) * f1[c] + G(DP_B3) * k3[c] + G(DP_B4) * k4[c] +
-                                G(DP_B5) * k5[c] + G(DP_B6) * k6[c]);
-        const double r5 = A::to(geodesic_rhs_g<G>(y5, a, m, flat, k7));
+                for (int c = 0; c < 8; ++c) y5[c] = ys[c];
+            }
+        }
         // Error norm eps = max_c |y5_c - y4_c| / (f_abs + f_rel max(|y_c|, |y5_c|)) with
         // y5 - y4 = h sum (b5 - b4) k. Native double keeps the FP64 form's arithmetic; the
         // df64 form takes the ratio in float (it only steers the step size).
         double eps;
         bool finite = true;
-        if constexpr (kNative) {
-            double num = 0.0, den = 1.0;
+        {
+            G errv[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const double err = fabs(A::to(h * (G(DP_E1) * f1[c] + G(DP_E3) * k3[c] + G(DP_E4) * k4[c] +
-                                                   G(DP_E5) * k5[c] + G(DP_E6) * k6[c] + G(DP_E7) * k7[c])));
-                const double sc = tol_abs + tol_rel * fmax(fabs(A::to(y[c])), fabs(A::to(y5[c])));
-                finite = finite && isfinite(err) && isfinite(A::to(y5[c]));
-                if (err * den > num * sc) { num = err; den = sc; }
+                G acc = DPCoef<G>::e(0) * K[0][c];
+#pragma unroll 1
+                for (int j = 2; j < 7; ++j) acc = acc + DPCoef<G>::e(j) * K[j][c];
+                errv[c] = h * acc;
             }
-            eps = num / den;
-        } else {
-            float num = 0.0f, den = 1.0f;
-            const float ta = (float)tol_abs, tr = (float)tol_rel;
+            if constexpr (kNative) {
+                double num = 0.0, den = 1.0;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const float err = fabsf(A::tof(h * (G(DP_E1) * f1[c] + G(DP_E3) * k3[c] + G(DP_E4) * k4[c] +
-                                                    G(DP_E5) * k5[c] + G(DP_E6) * k6[c] + G(DP_E7) * k7[c])));
-                const float sc = ta + tr * fmaxf(fabsf(A::tof(y[c])), fabsf(A::tof(y5[c])));
-                finite = finite && isfinite(err) && isfinite(A::tof(y5[c]));
-                if (err * den > num * sc) { num = err; den = sc; }
+                for (int c = 0; c < 8; ++c) {
+                    const double err = fabs(A::to(errv[c]));
+                    const double sc = tol_abs + tol_rel * fmax(fabs(A::to(y[c])), fabs(A::to(y5[c])));
+                    finite = finite && isfinite(err) && isfinite(A::to(y5[c]));
+                    if (err * den > num * sc) { num = err; den = sc; }
+                }
+                eps = num / den;
+            } else {
+                float num = 0.0f, den = 1.0f;
+                const float ta = (float)tol_abs, tr = (float)tol_rel;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float err = fabsf(A::tof(errv[c]));
+                    const float sc = ta + tr * fmaxf(fabsf(A::tof(y[c])), fabsf(A::tof(y5[c])));
+                    finite = finite && isfinite(err) && isfinite(A::tof(y5[c]));
+                    if (err * den > num * sc) { num = err; den = sc; }
+                }
+                eps = (double)(num / den);
             }
-            eps = (double)(num / den);
         }
         ++attempts;
         bool done = false;
@@ -474,8 +571,12 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
                 G ym[8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
-                    ym[c] = y[c] + (G(0.5) * h) * (G(DP_M1) * f1[c] + G(DP_M3) * k3[c] + G(DP_M4) * k4[c] +
-                                                   G(DP_M5) * k5[c] + G(DP_M6) * k6[c] + G(DP_M7) * k7[c]);
+                {
+                    G acc = DPCoef<G>::m(0) * K[0][c];
+#pragma unroll 1
+                    for (int j = 2; j < 7; ++j) acc = acc + DPCoef<G>::m(j) * K[j][c];
+                    ym[c] = y[c] + (kHalf * h) * acc;
+                }
                 const double r0 = r_cur, r1 = r5;
                 const double hd = A::to(h);
                 double rmid, kt_up, fmid;
@@ -520,15 +621,15 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
                     float y0f[8], d0f[8], c2f[8], c3f[8], c4f[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        const G d0 = h * f1[c];
+                        const G d0 = h * K[0][c];
                         const G D1 = y5[c] - y[c] - d0;
-                        const G D2 = h * k7[c] - d0;
-                        const G D3 = ym[c] - y[c] - G(0.5) * d0;
+                        const G D2 = h * K[6][c] - d0;
+                        const G D3 = ym[c] - y[c] - kHalf * d0;
                         y0f[c] = A::tof(y[c]);
                         d0f[c] = A::tof(d0);
-                        c2f[c] = A::tof(G(-5.0) * D1 + D2 + G(16.0) * D3);
-                        c3f[c] = A::tof(G(14.0) * D1 - G(3.0) * D2 - G(32.0) * D3);
-                        c4f[c] = A::tof(G(-8.0) * D1 + G(2.0) * D2 + G(16.0) * D3);
+                        c2f[c] = A::tof(kM5 * D1 + D2 + k16 * D3);
+                        c3f[c] = A::tof(k14 * D1 - kThree * D2 - k32 * D3);
+                        c4f[c] = A::tof(kM8 * D1 + k2c * D2 + k16 * D3);
                     }
                     const float invf = 1.0f / (float)nsub;
                     for (int s = 0; s < nsub && ok; ++s) {
@@ -547,9 +648,9 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         y0d[c] = A::to(y[c]);
-                        d0[c] = hd * A::to(f1[c]);
+                        d0[c] = hd * A::to(K[0][c]);
                         const double D1 = A::to(y5[c]) - y0d[c] - d0[c];
-                        const double D2 = hd * A::to(k7[c]) - d0[c];
+                        const double D2 = hd * A::to(K[6][c]) - d0[c];
                         const double D3 = A::to(ym[c]) - y0d[c] - 0.5 * d0[c];
                         c2[c] = -5.0 * D1 + D2 + 16.0 * D3;
                         c3[c] = 14.0 * D1 - 3.0 * D2 - 32.0 * D3;
@@ -571,7 +672,7 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
                 if (!ok) { status = BL_RAY_OVERFLOW; done = true; }
             }
 #pragma unroll
-            for (int c = 0; c < 8; ++c) { y[c] = y5[c]; f1[c] = k7[c]; }
+            for (int c = 0; c < 8; ++c) { y[c] = y5[c]; K[0][c] = K[6][c]; }
             double fac;
             if constexpr (kNative) {
                 fac = (eps == 0.0) ? 10.0 : 0.9 * pow(eps, -0.2);

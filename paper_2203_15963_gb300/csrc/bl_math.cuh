@@ -44,35 +44,36 @@ __device__ __forceinline__ void ks_geom(T x, T y, T z, T a, T m, bool flat, bool
                                         KSGeom<T>& G) {
     // Special functions kept to two reciprocal square roots and one reciprocal:
     // D = D2 rsqrt(D2), r = r2 rsqrt(r2), and 1/P, 1/s4 from 1/(P s4).
+    constexpr T c1 = T(1), c2 = T(2), c3 = T(3), c4 = T(4), cHalf = T(0.5), c0 = T(0);
     const T rr2 = x * x + y * y + z * z;
     const T q = rr2 - a * a;
-    const T D2 = q * q + T(4) * a * a * z * z;
+    const T D2 = q * q + c4 * a * a * z * z;
     const T iD = rsqrt(D2);
     const T D = D2 * iD;
-    const T r2 = T(0.5) * (q + D);
+    const T r2 = cHalf * (q + D);
     const T ir = rsqrt(r2);
     const T r = r2 * ir;
     const T s4 = r2 * r2 + a * a * z * z;
     const T P = r2 + a * a;
-    const T iPs = T(1) / (P * s4);
+    const T iPs = c1 / (P * s4);
     const T is4 = P * iPs;
     const T iP = s4 * iPs;
-    const T f = flat ? T(0) : T(2) * m * r * r2 * is4;
+    const T f = flat ? c0 : c2 * m * r * r2 * is4;
     G.r = r;
     G.f = f;
-    G.l[0] = T(1);
+    G.l[0] = c1;
     G.l[1] = (r * x + a * y) * iP;
     G.l[2] = (r * y - a * x) * iP;
     G.l[3] = z * ir;
     if (!derivs) return;
     const T dr[3] = {r * x * iD, r * y * iD, z * P * ir * iD};
     for (int c = 0; c < 3; ++c) {
-        const T extra = (c == 2) ? T(2) * a * a * z : T(0);
-        G.df[c] = flat ? T(0) : f * (T(3) * dr[c] * ir - (T(4) * r2 * r * dr[c] + extra) * is4);
-        const T two_r_dr_iP = T(2) * r * dr[c] * iP;
-        G.dl[c][0] = (dr[c] * x + (c == 0 ? r : T(0)) + (c == 1 ? a : T(0))) * iP - G.l[1] * two_r_dr_iP;
-        G.dl[c][1] = (dr[c] * y + (c == 1 ? r : T(0)) - (c == 0 ? a : T(0))) * iP - G.l[2] * two_r_dr_iP;
-        G.dl[c][2] = ((c == 2 ? T(1) : T(0)) - G.l[3] * dr[c]) * ir;
+        const T extra = (c == 2) ? c2 * a * a * z : c0;
+        G.df[c] = flat ? c0 : f * (c3 * dr[c] * ir - (c4 * r2 * r * dr[c] + extra) * is4);
+        const T two_r_dr_iP = c2 * r * dr[c] * iP;
+        G.dl[c][0] = (dr[c] * x + (c == 0 ? r : c0) + (c == 1 ? a : c0)) * iP - G.l[1] * two_r_dr_iP;
+        G.dl[c][1] = (dr[c] * y + (c == 1 ? r : c0) - (c == 0 ? a : c0)) * iP - G.l[2] * two_r_dr_iP;
+        G.dl[c][2] = ((c == 2 ? c1 : c0) - G.l[3] * dr[c]) * ir;
     }
 }
 
