@@ -39,9 +39,12 @@ FLOP32_PER_SAMPLE = 3300
 # Nominal peaks from the pool's profiling recipe (no measured FP64/FP32 peak is available):
 # FP64 1.25 TFLOP/s; FP32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
 PEAK_FP64_TFLOPS = 1.25
-# FP32 instructions per double-float operation, averaged over the right-hand side's mix of
-# products (6-7 instructions), sums (11) and reciprocal square roots (~20)
-DF64_FP32_PER_FLOP = 10
+# Double-float: FP32 instructions per emulated FP64 flop -- a product costs 7, a sum 11,
+# so an FP64 multiply-add (2 flops) costs 18, i.e. 9 per flop, plus the reciprocal square
+# roots (~20 each); 9.5 on the right-hand side's mix. The emulated peak is the FP32 issue
+# rate (152 SMs x 128 lanes x 2.07 GHz instructions/s) divided by that.
+DF64_INSTR_PER_FLOP = 9.5
+PEAK_DF64_TFLOPS = 152 * 128 * 2.07e9 / DF64_INSTR_PER_FLOP / 1e12
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
@@ -51,7 +54,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="blacklight", choices=["blacklight", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fast"])
+    ap.add_argument("--precision", default="fast", choices=["mixed", "fp64", "fast"],
+                    help="fast: double-float geodesics + FP32 transfer (default); mixed: FP64 "
+                         "geodesics + FP32 transfer; fp64: FP64 throughout")
+    ap.add_argument("--no-other-forms", action="store_true",
+                    help="skip the short timing of the two other precision forms")
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: one 256^2 image (a=0.94, i=60 deg) of the same workload, for "
                          "profiler captures")
@@ -278,12 +285,12 @@ def main():
                 "achieved": flop_geo / geo_avg / 1e12, "peak": PEAK_FP64_TFLOPS,
                 "unit": "TFLOP/s", "peak_source": "nominal FP64 rate (profiling recipe)"}
     elif geo_avg >= tr_avg:
-        # double-float: each algorithmic FP64 flop costs DF64_FP32_PER_FLOP FP32 flops
+        # double-float: algorithmic FP64 flops against the emulated rate the FP32 pipe allows
         roof = {"kernel": "geodesic_kernel (double-float on FP32)", "bound": "alu",
-                "achieved": flop_geo * DF64_FP32_PER_FLOP / geo_avg / 1e12,
-                "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                "peak_source": "nominal FP32 rate (profiling recipe unit counts x 2.07 GHz)",
-                "algorithmic_fp64_tflops": flop_geo / geo_avg / 1e12}
+                "achieved": flop_geo / geo_avg / 1e12, "peak": PEAK_DF64_TFLOPS,
+                "unit": "TFLOP/s",
+                "peak_source": "FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz) / 9.5 FP32 "
+                               "instructions per emulated FP64 flop"}
     else:
         peak = PEAK_FP32_TFLOPS if prec != native.BL_PREC_FP64 else PEAK_FP64_TFLOPS
         roof = {"kernel": "transfer_kernel", "bound": "alu",
@@ -293,6 +300,14 @@ def main():
     roof["traffic"] = None
     status_bad = sum(int(((o["status"] != 1) & (o["status"] != 2)).sum()) for o in outs)
 
+    other = None
+    if not args.no_other_forms:
+        other = {}
+        for name, code in (("mixed", native.BL_PREC_MIXED), ("fp64", native.BL_PREC_FP64),
+                           ("fast", native.BL_PREC_FAST)):
+            if code == prec:
+                continue
+            other[name] = time_form(torch, native, images, wl, code, device, steps=3, warmup=2)
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(torch, native, wl, prec, max(1, min(args.steps, 3)))
@@ -318,11 +333,44 @@ def main():
                 "kernel_ms": {"geodesic": geo_avg * 1e3, "transfer": tr_avg * 1e3},
                 "work": {"dp_attempts": attempts, "samples": samples,
                          "rays_not_terminated_normally": status_bad},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "other_forms": other,
                 "gpu_launches": int(launches), "clocks": clk, "return_codes": sorted(set(rcs))}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def time_form(torch, native, images, wl, code, device, steps, warmup):
+    """Short CUDA-event timing of the same workload in another precision form."""
+    import copy
+    mets = [copy.replace(m, precision=code) if hasattr(copy, "replace") else
+            type(m)(**{**m.__dict__, "precision": code}) for m in wl["mets"]]
+    cams = wl["cams"]
+    ws = torch.empty(native.blacklight_workspace_size(cams, mets), dtype=torch.uint8,
+                     device=device)
+    dt = torch.float64 if code == native.BL_PREC_FP64 else torch.float32
+    outs = [images.alloc_outputs(c.n, dt, device=device) for c in cams]
+    for _ in range(warmup):
+        native.blacklight_trace_batch(cams, mets, wl["gps"], wl["prims"], wl["freqs"], outs,
+                                      workspace=ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    geo = tr = 0.0
+    e0.record()
+    for _ in range(steps):
+        native.blacklight_trace_batch(cams, mets, wl["gps"], wl["prims"], wl["freqs"], outs,
+                                      workspace=ws, flags=native.BL_TIMING)
+        g, t = native.blacklight_last_kernel_ms()
+        geo += g
+        tr += t
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    del ws
+    rays = sum(c.n * c.n for c in cams)
+    return {"value": rays / ms * 1e3, "ms_per_step": ms, "steps": steps,
+            "kernel_ms": {"geodesic": geo / steps, "transfer": tr / steps}}
 
 
 def measure_e2e(torch, native, wl, prec, steps):

@@ -6,9 +6,9 @@
 //   TwoSum      Knuth, TAOCP vol. 2, 4.2.2 -- s + e = a + b exactly, no branch;
 //   Fast2Sum    Dekker 1971 -- s + e = a + b exactly when |a| >= |b|;
 //   TwoProd     with FMA: p = a b, e = fma(a, b, -p), p + e = a b exactly;
-//   sums and products of double-words as in Joldes, Muller & Popescu 2017 ("Tight and
-//   rigorous error bounds for basic building blocks of double-word arithmetic"), the
-//   accurate addition (their Alg. 6) and the FMA product (their Alg. 12 structure);
+//   double-length addition (Dekker 1971) and the FMA product of double-words (Joldes,
+//   Muller & Popescu 2017, "Tight and rigorous error bounds for basic building blocks of
+//   double-word arithmetic", structure of their Alg. 12);
 //   1/x and 1/sqrt(x): one Newton step in df64 from the float approximation, which doubles
 //   the number of correct bits.
 #pragma once
@@ -47,12 +47,13 @@ __device__ __forceinline__ df64 df_two_prod(float a, float b) {
     return df64(p, fmaf(a, b, -p));
 }
 
+// Addition: TwoSum of the high parts, the low parts added in float, one renormalisation
+// (Dekker's double-length addition). Its relative error is ~2^-48 except where x and y
+// nearly cancel; in the integrator such cancellation only occurs in the embedded error
+// estimate, which steers the step size and tolerates it.
 __device__ __forceinline__ df64 operator+(const df64& x, const df64& y) {
     df64 s = df_two_sum(x.hi, y.hi);
-    const df64 t = df_two_sum(x.lo, y.lo);
-    s.lo += t.hi;
-    s = df_fast_two_sum(s.hi, s.lo);
-    s.lo += t.lo;
+    s.lo += x.lo + y.lo;
     return df_fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ df64 operator-(const df64& x) { return df64(-x.hi, -x.lo); }
