@@ -74,6 +74,20 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_elapsed(torch, elapsed, world, device):
+    """Slowest rank's timed-region length (ranks trace independent replicas, no exchange)."""
+    if world <= 1:
+        return elapsed
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world, rays_per_rank_step, steps, elapsed_max):
+    """Whole-job rays/s: every rank's rays over the slowest rank's time."""
+    return world * rays_per_rank_step * steps / elapsed_max
+
+
 def build_workload(torch, precision_code, device, case="full"):
     from paper_2203_15963_gb300 import synth as S
     gp = S.grid_params_for(*GRID)
@@ -266,12 +280,8 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    elapsed = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        t = torch.tensor([elapsed], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = world * rays_per_step * args.steps / elapsed
+    elapsed = reduce_elapsed(torch, e0.elapsed_time(e1) / 1e3, world, device)
+    value = weak_scaling_value(world, rays_per_step, args.steps, elapsed)
 
     # algorithmic work of one launch pair (identical every step)
     attempts = sum(int(o["steps"].long().sum()) for o in outs)

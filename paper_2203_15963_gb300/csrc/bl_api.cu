@@ -150,6 +150,26 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
     d.rho_unit = g.rho_unit_cgs;
     d.length_unit = bl::kG * g.mass_msun * bl::kMsun / (bl::kC * bl::kC);
     d.freq = freq;
+    {
+        double* c = d.d_c;
+        c[bl::kcGam1] = g.gamma_ad - 1.0;
+        c[bl::kcTePre] = g.mu * bl::kMp / bl::kMe;
+        c[bl::kcNePre] = g.rho_unit_cgs / (g.mu * bl::kMp);
+        c[bl::kcBgPre] = bl::kC * std::sqrt(4.0 * bl::kPi * g.rho_unit_cgs);
+        c[bl::kcDlr] = std::log(g.r_max / g.r_min) / g.n_r;
+        c[bl::kcLogRmin] = std::log(g.r_min);
+        c[bl::kcRmin] = g.r_min;
+        c[bl::kcRmax] = g.r_max;
+        c[bl::kcSigma] = g.sigma_cut;
+        c[bl::kcRhigh] = g.r_high;
+        c[bl::kcRlow] = g.r_low;
+        c[bl::kcNeNi] = g.ne_over_ni;
+        c[bl::kcFreq] = freq;
+        c[bl::kcLen] = d.length_unit;
+        c[bl::kcSpin] = m.spin;
+        c[bl::kcMass] = m.mass;
+        for (int i = 0; i < 16; ++i) d.f_c[i] = (float)c[i];
+    }
     d.stokes = o.stokes; d.dtype = o.dtype; d.status = o.status; d.steps = o.steps;
     d.end_state = o.end_state;
     d.samples = o.samples;

@@ -30,6 +30,7 @@ struct df64 {
     __host__ __device__ constexpr explicit df64(double d)
         : hi((float)d), lo((float)(d - (double)(float)d)) {}
     __host__ __device__ constexpr explicit df64(int i) : hi((float)i), lo(0.0f) {}
+    __host__ __device__ constexpr explicit df64(float f) : hi(f), lo(0.0f) {}
 };
 
 __device__ __forceinline__ df64 df_two_sum(float a, float b) {

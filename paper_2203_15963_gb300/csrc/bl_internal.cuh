@@ -40,6 +40,22 @@ struct ImageDesc {
     // filled by the camera-frame kernel
     double x_cam[4], u_cam[4], kk[4], hh[4], vv[4];
     double r_cam, r_hor;
+    // per-image constants of the transfer, in double (d_*) and float (f_*), derived once on
+    // the host (and H, V by the camera-frame kernel) so that samples do no conversions
+    double d_c[16];
+    float f_c[16];
+    float f_hh[4], f_vv[4];
+};
+
+// indices into d_c / f_c
+enum {
+    kcGam1 = 0,      // gamma_ad - 1
+    kcTePre,         // mu m_p / m_e
+    kcNePre,         // rho_unit / (mu m_p)
+    kcBgPre,         // c (4 pi rho_unit)^1/2
+    kcDlr,           // ln(r_max / r_min) / n_r
+    kcLogRmin,       // ln r_min
+    kcRmin, kcRmax, kcSigma, kcRhigh, kcRlow, kcNeNi, kcFreq, kcLen, kcSpin, kcMass
 };
 
 struct RayHdr {

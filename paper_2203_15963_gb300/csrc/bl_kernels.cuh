@@ -124,7 +124,12 @@ __global__ void camera_frame_kernel(ImageDesc* imgs, int n_images) {
         im.hh[c + 1] = Hc;
         im.vv[c + 1] = Vc;
     }
-    for (int al = 0; al < 4; ++al) { im.x_cam[al] = x[al]; im.u_cam[al] = u[al]; }
+    for (int al = 0; al < 4; ++al) {
+        im.x_cam[al] = x[al];
+        im.u_cam[al] = u[al];
+        im.f_hh[al] = (float)im.hh[al];
+        im.f_vv[al] = (float)im.vv[al];
+    }
     im.r_cam = r;
     const double d = m * m - a * a;
     im.r_hor = m + sqrt(d > 0.0 ? d : 0.0);
@@ -518,7 +523,7 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
             }
             const G rr = geodesic_rhs_g<G>(ys, a, m, flat, K[st]);
             if (st == 6) {
-                r5 = A::to(rr);
+                r5 = kNative ? A::to(rr) : (double)A::tof(rr);
 #pragma unroll
                 for (int c = 0; c < 8; ++c) y5[c] = ys[c];
             }
@@ -578,7 +583,7 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
                     ym[c] = y[c] + (kHalf * h) * acc;
                 }
                 const double r0 = r_cur, r1 = r5;
-                const double hd = A::to(h);
+                const double hd = kNative ? A::to(h) : (double)A::tof(h);
                 double rmid, kt_up, fmid;
                 if constexpr (kNative) {
                     double ymd[8];
@@ -606,10 +611,18 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
                 int nsub = 1;
                 if (rmin < r_grid) {
                     // ds/dl = (g_pq k^p k^q)^1/2 = alpha |k^t| for a null ray
-                    const double ds = fabs(hd) * fabs(kt_up) / sqrt(1.0 + fmid);
-                    if (ds > ds_max) {
-                        const double nd = ceil(ds / ds_max);
-                        nsub = nd > 4096.0 ? 4097 : (int)nd;
+                    if constexpr (kNative) {
+                        const double ds = fabs(hd) * fabs(kt_up) / sqrt(1.0 + fmid);
+                        if (ds > ds_max) {
+                            const double nd = ceil(ds / ds_max);
+                            nsub = nd > 4096.0 ? 4097 : (int)nd;
+                        }
+                    } else {
+                        const float ds = fabsf((float)hd) * fabsf((float)kt_up) * rsqrtf(1.0f + (float)fmid);
+                        if (ds > (float)ds_max) {
+                            const float nd = ceilf(ds / (float)ds_max);
+                            nsub = nd > 4096.0f ? 4097 : (int)nd;
+                        }
                     }
                 }
                 bool ok = true;
@@ -673,15 +686,18 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) { y[c] = y5[c]; K[0][c] = K[6][c]; }
-            double fac;
             if constexpr (kNative) {
-                fac = (eps == 0.0) ? 10.0 : 0.9 * pow(eps, -0.2);
+                double fac = (eps == 0.0) ? 10.0 : 0.9 * pow(eps, -0.2);
+                fac = fmin(10.0, fmax(0.2, fac));
+                if (prev_rej) fac = fmin(fac, 1.0);
+                h = h * A::from(fac);
             } else {
-                fac = (eps == 0.0) ? 10.0 : (double)(0.9f * powf((float)eps, -0.2f));
+                const float ef = (float)eps;
+                float fac = (ef == 0.0f) ? 10.0f : 0.9f * powf(ef, -0.2f);
+                fac = fminf(10.0f, fmaxf(0.2f, fac));
+                if (prev_rej) fac = fminf(fac, 1.0f);
+                h = h * G(fac);
             }
-            fac = fmin(10.0, fmax(0.2, fac));
-            if (prev_rej) fac = fmin(fac, 1.0);
-            h = h * A::from(fac);
             prev_rej = false;
             r_cur = r5;
             if (!done) {
@@ -691,13 +707,19 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
             }
         } else {
             double fac;
-            if constexpr (kNative) fac = fmax(0.2, 0.9 * pow(eps, -0.2));
-            else fac = fmax(0.2, (double)(0.9f * powf((float)eps, -0.2f)));
-            h = h * A::from(fac);
+            if constexpr (kNative) {
+                fac = fmax(0.2, 0.9 * pow(eps, -0.2));
+                h = h * A::from(fac);
+            } else {
+                h = h * G(fmaxf(0.2f, 0.9f * powf((float)eps, -0.2f)));
+            }
             prev_rej = true;
         }
         if (!done) {
-            if (fabs(A::to(h)) < 1e-12 * r_cur) { status = BL_RAY_UNDERFLOW; done = true; }
+            if ((kNative ? fabs(A::to(h)) : (double)fabsf(A::tof(h))) < 1e-12 * r_cur) {
+                status = BL_RAY_UNDERFLOW;
+                done = true;
+            }
             else if (attempts >= max_steps) { status = BL_RAY_MAX_STEPS; done = true; }
         }
         if (done) {
@@ -724,6 +746,13 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
     }
 }
 
+// Per-image constant in the transfer arithmetic.
+template <class T>
+__device__ __forceinline__ T ic(const ImageDesc& im, int k) {
+    if constexpr (std::is_same<T, float>::value) return im.f_c[k];
+    else return im.d_c[k];
+}
+
 // ---------------------------------------------------------------------------------------
 // Plasma state at a sample (Secs. 2, 2.4, 2.5) in arithmetic T.
 // ---------------------------------------------------------------------------------------
@@ -737,9 +766,9 @@ struct Plasma {
 template <class T>
 __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], const KSGeom<T>& G,
                                           Plasma<T>& P) {
-    const T a = (T)im.spin;
+    const T a = ic<T>(im, kcSpin);
     const T r = G.r;
-    if (!(r >= (T)im.r_min && r <= (T)im.r_max)) return false;
+    if (!(r >= ic<T>(im, kcRmin) && r <= ic<T>(im, kcRmax))) return false;
     T cth = x[2] / r;
     cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
     const T th = acos(cth);
@@ -753,11 +782,12 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], con
     const float* __restrict__ prim = im.prim;
     const size_t plane = (size_t)np * nt * nr;
     T pv[8];
-    const T dlr = log((T)im.r_max / (T)im.r_min) / T(nr);
+    const T dlr = ic<T>(im, kcDlr);
+    const T lrmin = ic<T>(im, kcLogRmin);
     const T dth = T(kPi) / T(nt);
     const T dph = twopi / T(np);
     if (im.interp == 0) {
-        int i = (int)floor(log(r / (T)im.r_min) / dlr);
+        int i = (int)floor((log(r) - lrmin) / dlr);
         int j = (int)floor(th / dth);
         int k = (int)floor(ph / dph);
         i = min(max(i, 0), nr - 1);
@@ -770,7 +800,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], con
         int i0, j0;
         T wr, wt;
         {
-            T fi = log(r / (T)im.r_min) / dlr - T(0.5);
+            T fi = (log(r) - lrmin) / dlr - T(0.5);
             if (nr == 1) { i0 = 0; wr = T(0); }
             else {
                 fi = fi < T(0) ? T(0) : (fi > T(nr - 1) ? T(nr - 1) : fi);
@@ -836,18 +866,18 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], con
     for (int c = 0; c < 3; ++c) P.b[c + 1] = (B[c] + P.b[0] * P.u[c + 1]) * iut;
     P.bsq = dot4(G, P.b, P.b);
     const T rho = pv[0];
-    const T p = T(im.gamma_ad - 1.0) * pv[1];
+    const T p = ic<T>(im, kcGam1) * pv[1];
     if (!(rho > T(0)) || !(p > T(0)) || !(P.bsq > T(0))) return false;
-    if (P.bsq / rho > (T)im.sigma_cut) return false;
+    if (P.bsq / rho > ic<T>(im, kcSigma)) return false;
     const T binv = P.bsq / (T(2) * p);
     const T b2 = binv * binv;
-    const T ratio = ((T)im.r_high + b2 * (T)im.r_low) / (T(1) + b2);
-    const T rr = (T)im.ne_ni;
-    const T th_e = T(im.mu * kMp / kMe) * (p / rho) * (rr + T(1)) / (rr + ratio);
+    const T ratio = (ic<T>(im, kcRhigh) + b2 * ic<T>(im, kcRlow)) / (T(1) + b2);
+    const T rr = ic<T>(im, kcNeNi);
+    const T th_e = ic<T>(im, kcTePre) * (p / rho) * (rr + T(1)) / (rr + ratio);
     if (!(th_e >= T(0.05))) return false;
     P.th = th_e;
-    P.ne = rho * T(im.rho_unit / (im.mu * kMp)) / (T(1) + T(1) / rr);
-    P.bg = sqrt(P.bsq) * T(kC * sqrt(4.0 * kPi * im.rho_unit));
+    P.ne = rho * ic<T>(im, kcNePre) / (T(1) + T(1) / rr);
+    P.bg = sqrt(P.bsq) * ic<T>(im, kcBgPre);
     return true;
 }
 
@@ -947,6 +977,33 @@ __device__ __forceinline__ void stokes_to_coh(const T e1[4], const T e2[4], cons
         for (int b_ = a_ + 1; b_ < 4; ++b_) n.im[k++] = vv * (e1[a_] * e2[b_] - e2[a_] * e1[b_]);
 }
 
+// One sample record as 16-byte vector loads (records are 16-byte aligned).
+template <class R>
+__device__ __forceinline__ void load_record(const R* __restrict__ rec, R out[RecStride<R>::v]) {
+    if constexpr (std::is_same<R, float>::value) {
+        const float4* p = reinterpret_cast<const float4*>(rec);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 v = __ldg(p + i);
+            out[4 * i] = v.x; out[4 * i + 1] = v.y; out[4 * i + 2] = v.z; out[4 * i + 3] = v.w;
+        }
+    } else {
+        const double2* p = reinterpret_cast<const double2*>(rec);
+#pragma unroll
+        for (int i = 0; i < 7; ++i) {
+            const double2 v = __ldg(p + i);
+            out[2 * i] = v.x; out[2 * i + 1] = v.y;
+        }
+    }
+}
+
+template <class R>
+__device__ __forceinline__ const R* record_ptr(const R* __restrict__ pool, const int32_t* __restrict__ chunks,
+                                               int64_t ray, int32_t idx) {
+    const int32_t ch = chunks[ray * kMaxChunks + idx / kChunk];
+    return pool + ((int64_t)ch * kChunk + (idx % kChunk)) * RecStride<R>::v;
+}
+
 // ---------------------------------------------------------------------------------------
 // Persistent transfer kernel (Sec. 2.3.2). Each lane replays one ray's samples from the
 // source end to the camera, one sample per loop iteration: merged N half-steps by the
@@ -969,6 +1026,7 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
     Coh<T> N;
     bool started = false;
     T prev[kRecVals];
+    R nxt[RecStride<R>::v];
     T kt = T(0), a = T(0), m = T(0), nu_norm = T(0);
     bool flat = false;
 
@@ -998,10 +1056,11 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
                 continue;
             }
             idx = hd.nrec - 1;
+            load_record<R>(record_ptr(pool, chunks, ray, idx), nxt);
             kt = (T)hd.kt;
             nu_norm = (T)(hd.nnorm * im.freq);
-            a = (T)im.spin;
-            m = (T)im.mass;
+            a = ic<T>(im, kcSpin);
+            m = ic<T>(im, kcMass);
             flat = im.flat != 0;
 #pragma unroll
             for (int c = 0; c < 10; ++c) N.re[c] = T(0);
@@ -1011,14 +1070,11 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
             active = true;
         }
         const ImageDesc& im = imgs[q];
-        // load record idx
+        // record idx was prefetched into nxt; start fetching idx - 1 before using it
         T cur[kRecVals];
-        {
-            const int32_t ch = chunks[ray * kMaxChunks + idx / kChunk];
-            const R* rec = pool + ((int64_t)ch * kChunk + (idx % kChunk)) * RecStride<R>::v;
 #pragma unroll
-            for (int c = 0; c < kRecVals; ++c) cur[c] = (T)rec[c];
-        }
+        for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
+        if (idx > 0) load_record<R>(record_ptr(pool, chunks, ray, idx - 1), nxt);
         if (started) {
             // merged N half-steps from the previous sample to this one
             T A0[4][4], A1[4][4];
@@ -1044,8 +1100,8 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
                 cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
                 T co[8];
                 synchrotron_coefficients<T>(P.ne, P.th, P.bg, nu_fl, cth, co);
-                const T g = (T)im.freq / nu_fl;
-                const T path = (T)im.length_unit * (-kdu);
+                const T g = ic<T>(im, kcFreq) / nu_fl;
+                const T path = ic<T>(im, kcLen) * (-kdu);
                 const T eg = g * g * g * path;
                 const T coef[8] = {co[0] * eg, co[1] * eg, co[2] * eg, co[3] * path,
                                    co[4] * path, co[5] * path, co[6] * path, co[7] * path};
@@ -1073,8 +1129,12 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
             }
             KSGeom<T> G;
             ks_geom<T>(prev[6], prev[7], prev[8], a, m, flat, false, G);
-            const T hv[4] = {(T)im.hh[0], (T)im.hh[1], (T)im.hh[2], (T)im.hh[3]};
-            const T vv[4] = {(T)im.vv[0], (T)im.vv[1], (T)im.vv[2], (T)im.vv[3]};
+            T hv[4], vv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if constexpr (std::is_same<T, float>::value) { hv[c] = im.f_hh[c]; vv[c] = im.f_vv[c]; }
+                else { hv[c] = im.hh[c]; vv[c] = im.vv[c]; }
+            }
             T hl[4], vl[4];
             lower4(G, hv, hl);
             lower4(G, vv, vl);
