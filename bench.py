@@ -64,6 +64,8 @@ def parse():
                          "profiler captures")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-hires", action="store_true",
+                    help="skip the 1024^2 image on the 512x256x256 torus")
     return ap.parse_args()
 
 
@@ -318,6 +320,9 @@ def main():
             if code == prec:
                 continue
             other[name] = time_form(torch, native, images, wl, code, device, steps=3, warmup=2)
+    hires = None
+    if not args.no_hires and args.case == "full":
+        hires = measure_hires(torch, native, images, prec, device)
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(torch, native, wl, prec, max(1, min(args.steps, 3)))
@@ -344,6 +349,7 @@ def main():
                 "work": {"dp_attempts": attempts, "samples": samples,
                          "rays_not_terminated_normally": status_bad},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "other_forms": other,
+                "hires": hires,
                 "gpu_launches": int(launches), "clocks": clk, "return_codes": sorted(set(rcs))}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -381,6 +387,42 @@ def time_form(torch, native, images, wl, code, device, steps, warmup):
     rays = sum(c.n * c.n for c in cams)
     return {"value": rays / ms * 1e3, "ms_per_step": ms, "steps": steps,
             "kernel_ms": {"geodesic": geo / steps, "transfer": tr / steps}}
+
+
+def measure_hires(torch, native, images, code, device, steps=3, warmup=2):
+    """The metric's 1024^2 point: one 1024x1024 image (a = 0.94, i = 17 deg, 230 GHz) on the
+    512x256x256 torus (1 GiB of float32), timed like the main workload."""
+    from paper_2203_15963_gb300 import synth as S
+    cam, met, gp, prim = S.workload_inputs("torus512_cam1024", 0.94, 17.0)
+    met = S.Metric(**{**met.__dict__, "precision": code})
+    p = torch.from_numpy(prim).to(device)
+    del prim
+    ws = torch.empty(native.blacklight_workspace_size([cam], [met]), dtype=torch.uint8,
+                     device=device)
+    dt = torch.float64 if code == native.BL_PREC_FP64 else torch.float32
+    out = images.alloc_outputs(cam.n, dt, device=device)
+    for _ in range(warmup):
+        native.blacklight_trace_batch([cam], [met], [gp], [p], [FREQ], [out], workspace=ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    geo = tr = 0.0
+    e0.record()
+    for _ in range(steps):
+        native.blacklight_trace_batch([cam], [met], [gp], [p], [FREQ], [out], workspace=ws,
+                                      flags=native.BL_TIMING)
+        g, t = native.blacklight_last_kernel_ms()
+        geo += g
+        tr += t
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    bad = int(((out["status"] != 1) & (out["status"] != 2)).sum())
+    del ws, p
+    return {"workload": "torus512_cam1024", "value": cam.n * cam.n / ms * 1e3, "unit": "rays/s",
+            "ms_per_step": ms, "steps": steps,
+            "kernel_ms": {"geodesic": geo / steps, "transfer": tr / steps},
+            "rays_not_terminated_normally": bad}
 
 
 def measure_e2e(torch, native, wl, prec, steps):

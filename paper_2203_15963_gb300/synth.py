@@ -118,20 +118,30 @@ def _sks_pieces(r, th, a, m=1.0):
 
 def make_torus(gp: GridParams, spin: float, seed: int, noise: float = 0.1,
                mass: float = 1.0) -> np.ndarray:
-    """Return float32 prim[8][n_phi][n_theta][n_r] for the synthetic torus."""
-    a = float(spin)
-    rc = r_centres(gp)[None, None, :]
-    thc = theta_centres(gp)[None, :, None]
-    rho_s = np.exp(-(rc - 12.0) ** 2 / 32.0) * np.exp(-np.cos(thc) ** 2 / 0.18)
-    rho_s = np.broadcast_to(rho_s, (gp.n_phi, gp.n_theta, gp.n_r))
-    rng = np.random.default_rng(seed)
-    eps = rng.standard_normal((gp.n_phi, gp.n_theta, gp.n_r))
-    rho = np.maximum(rho_s * (1.0 + noise * eps), 0.0)
-    ugas = 0.3 * rho * 6.0 / rc
+    """Return float32 prim[8][n_phi][n_theta][n_r] for the synthetic torus.
 
-    # Keplerian velocity stored as SKS normal-frame components u^p.
-    r2 = np.broadcast_to(rc, rho.shape)
-    th2 = np.broadcast_to(thc, rho.shape)
+    Everything but the density noise is axisymmetric, so it is computed on the (theta, r)
+    plane and broadcast over phi."""
+    a = float(spin)
+    rc = r_centres(gp)[None, :]                       # [1][n_r]
+    thc = theta_centres(gp)[:, None]                  # [n_theta][1]
+    rho_s = np.exp(-(rc - 12.0) ** 2 / 32.0) * np.exp(-np.cos(thc) ** 2 / 0.18)   # [th][r]
+    rng = np.random.default_rng(seed)
+    shape = (gp.n_phi, gp.n_theta, gp.n_r)
+    prim = np.empty((N_PRIM,) + shape, dtype=np.float32)
+    # rho and u_gas with the seeded noise (3-D), slab by slab to bound memory
+    pmax = 0.0
+    for k in range(gp.n_phi):
+        eps = rng.standard_normal((gp.n_theta, gp.n_r))
+        rho = np.maximum(rho_s * (1.0 + noise * eps), 0.0)
+        ugas = 0.3 * rho * 6.0 / rc
+        prim[0, k] = rho
+        prim[1, k] = ugas
+        pmax = max(pmax, float(((gp.gamma_ad - 1.0) * ugas).max()))
+
+    # Keplerian velocity stored as SKS normal-frame components u^p (axisymmetric).
+    r2 = np.broadcast_to(rc, rho_s.shape)
+    th2 = np.broadcast_to(thc, rho_s.shape)
     f, g = _sks_pieces(r2, th2, a, mass)
     omega = 1.0 / (r2 ** 1.5 + a)
     norm = -(g["tt"] + 2.0 * omega * g["tph"] + omega * omega * g["phph"])
@@ -150,11 +160,9 @@ def make_torus(gp: GridParams, spin: float, seed: int, noise: float = 0.1,
     dr = np.diff(r_faces(gp))[None, :]
     d_th = 0.5 * ((aphi[1:, :-1] - aphi[:-1, :-1]) + (aphi[1:, 1:] - aphi[:-1, 1:])) / dth
     d_r = 0.5 * ((aphi[:-1, 1:] - aphi[:-1, :-1]) + (aphi[1:, 1:] - aphi[1:, :-1])) / dr
-    rc2 = r_centres(gp)[None, :]
-    thc2 = theta_centres(gp)[:, None]
-    sqrtg = (rc2 ** 2 + a * a * np.cos(thc2) ** 2) * np.sin(thc2)
-    br = np.broadcast_to(d_th / sqrtg, rho.shape)
-    bth = np.broadcast_to(-d_r / sqrtg, rho.shape)
+    sqrtg = (rc ** 2 + a * a * np.cos(thc) ** 2) * np.sin(thc)
+    br = d_th / sqrtg
+    bth = -d_r / sqrtg
     bph = np.zeros_like(br)
 
     # Scale to plasma beta = 10 in the sense max(p) / max(b^2/2) = 10.
@@ -163,7 +171,6 @@ def make_torus(gp: GridParams, spin: float, seed: int, noise: float = 0.1,
     u_t = gam * np.sqrt(1.0 + f)
     u_r = up_r - f / (1.0 + f) * u_t
     u_th, u_ph = up_th, up_ph
-    # covariant spatial u_i = g_{i mu} u^mu
     low_r = g["tr"] * u_t + g["rr"] * u_r + g["rph"] * u_ph
     low_th = g["thth"] * u_th
     low_ph = g["tph"] * u_t + g["rph"] * u_r + g["phph"] * u_ph
@@ -174,18 +181,14 @@ def make_torus(gp: GridParams, spin: float, seed: int, noise: float = 0.1,
     bsq = (g["tt"] * b_t ** 2 + 2 * g["tr"] * b_t * b_r + 2 * g["tph"] * b_t * b_ph
            + g["rr"] * b_r ** 2 + 2 * g["rph"] * b_r * b_ph + g["thth"] * b_th ** 2
            + g["phph"] * b_ph ** 2)
-    p = (gp.gamma_ad - 1.0) * ugas
-    scale = math.sqrt(p.max() / (10.0 * max(0.5 * bsq.max(), 1e-300)))
+    scale = math.sqrt(pmax / (10.0 * max(0.5 * bsq.max(), 1e-300)))
 
-    prim = np.empty((N_PRIM, gp.n_phi, gp.n_theta, gp.n_r), dtype=np.float32)
-    prim[0] = rho
-    prim[1] = ugas
-    prim[2] = up_r
-    prim[3] = up_th
-    prim[4] = up_ph
-    prim[5] = br * scale
-    prim[6] = bth * scale
-    prim[7] = bph * scale
+    prim[2] = up_r[None]
+    prim[3] = up_th[None]
+    prim[4] = up_ph[None]
+    prim[5] = (br * scale)[None]
+    prim[6] = (bth * scale)[None]
+    prim[7] = (bph * scale)[None]
     return prim
 
 
@@ -202,6 +205,9 @@ WORKLOADS = {
     # 256x256 camera, 256x128x128 grid, 3 spins x 3 inclinations
     "torus256_cam256": dict(grid=(256, 128, 128), n=256, spins=(0.0, 0.5, 0.94),
                             incs=(17.0, 60.0, 90.0), freqs=(230e9,), seed_index=1),
+    # 1024x1024 camera, 512x256x256 grid (1 GiB of float32), a = 0.94, 230 GHz
+    "torus512_cam1024": dict(grid=(512, 256, 256), n=1024, spins=(0.94,), incs=(17.0,),
+                             freqs=(230e9,), seed_index=3),
 }
 
 

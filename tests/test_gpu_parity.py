@@ -236,6 +236,23 @@ def test_full_size_workload_sampled(precision):
     assert np.array_equal(g["status"][pix], ora["status"])
 
 
+@pytest.mark.parametrize("precision", [1, 2])
+def test_hires_workload_sampled(precision):
+    """1024x1024 camera on the 512x256x256 torus, checked against the oracle on a seeded
+    sample of pixels."""
+    cam, met, gp, prim = S.workload_inputs("torus512_cam1024", 0.94, 17.0)
+    g = _gpu_image(cam, met, gp, prim, 230e9, precision)
+    assert g["rc"] == 0
+    rng = np.random.default_rng(321)
+    pix = np.sort(rng.choice(cam.n * cam.n, 160, replace=False)).astype(np.int32)
+    ora = O.trace(cam, met, gp, prim, 230e9, pix=pix)
+    err = _rel_l2(g["stokes"][pix], ora["stokes"])
+    print("1024^2 sampled rel-L2", precision, err)
+    assert max(err) <= 1e-3
+    assert abs(np.sum(g["stokes"][pix, 0]) / np.sum(ora["stokes"][:, 0]) - 1) <= 1e-4
+    assert np.array_equal(g["status"][pix], ora["status"])
+
+
 @pytest.mark.parametrize("case", ["face_on_pole", "ragged_37", "nearest", "flat", "pixel_1"])
 def test_edge_configurations(case):
     gp = S.GridParams(n_r=48, n_theta=32, n_phi=32)
