@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-hires", action="store_true",
                     help="skip the 1024^2 image on the 512x256x256 torus")
+    ap.add_argument("--no-adaptive", action="store_true",
+                    help="skip the batched adaptive-refinement workload")
     return ap.parse_args()
 
 
@@ -311,6 +313,9 @@ def main():
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
     status_bad = sum(int(((o["status"] != 1) & (o["status"] != 2)).sum()) for o in outs)
+    # the secondary measurements below allocate their own workspaces
+    del ws
+    torch.cuda.empty_cache()
 
     other = None
     if not args.no_other_forms:
@@ -323,6 +328,9 @@ def main():
     hires = None
     if not args.no_hires and args.case == "full":
         hires = measure_hires(torch, native, images, prec, device)
+    adaptive = None
+    if not args.no_adaptive and args.case == "full":
+        adaptive = measure_adaptive(torch, native, prec, device)
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(torch, native, wl, prec, max(1, min(args.steps, 3)))
@@ -349,7 +357,7 @@ def main():
                 "work": {"dp_attempts": attempts, "samples": samples,
                          "rays_not_terminated_normally": status_bad},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "other_forms": other,
-                "hires": hires,
+                "hires": hires, "adaptive": adaptive,
                 "gpu_launches": int(launches), "clocks": clk, "return_codes": sorted(set(rcs))}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -419,10 +427,47 @@ def measure_hires(torch, native, images, code, device, steps=3, warmup=2):
     ms = e0.elapsed_time(e1) / steps
     bad = int(((out["status"] != 1) & (out["status"] != 2)).sum())
     del ws, p
+    torch.cuda.empty_cache()
     return {"workload": "torus512_cam1024", "value": cam.n * cam.n / ms * 1e3, "unit": "rays/s",
             "ms_per_step": ms, "steps": steps,
             "kernel_ms": {"geodesic": geo / steps, "transfer": tr / steps},
             "rays_not_terminated_normally": bad}
+
+
+def measure_adaptive(torch, native, code, device, steps=2, warmup=1):
+    """Batched adaptive refinement: 16 images (spins 0, 0.5, 0.94, 0.99 x 86, 230, 345, 690 GHz)
+    on the 256x128x128 torus, 128^2 root pixels in 8x8 blocks, up to 3 levels, refining blocks
+    where the relative Stokes-I gradient exceeds 0.1 on at least 5 of 64 pixels."""
+    from paper_2203_15963_gb300 import synth as S
+    gp = S.grid_params_for(*GRID)
+    spins, freqs = (0.0, 0.5, 0.94, 0.99), (86e9, 230e9, 345e9, 690e9)
+    prims = {a: torch.from_numpy(S.make_torus(gp, a, S.BASE_SEED + 2)).to(device) for a in spins}
+    cams, mets, gps, ps, fs, outs = [], [], [], [], [], []
+    dt = torch.float64 if code == native.BL_PREC_FP64 else torch.float32
+    for a in spins:
+        for f in freqs:
+            cams.append(S.Camera(theta=math.radians(17.0), n=128))
+            mets.append(S.Metric(spin=a, precision=code))
+            gps.append(gp)
+            ps.append(prims[a])
+            fs.append(f)
+            outs.append({"stokes": torch.zeros((4, 1024, 1024), dtype=dt, device=device)})
+    ad = native.adapt_struct(8, 3, native.BL_CRIT_REL_GRAD, 0.1, 5)
+    for _ in range(warmup):
+        native.blacklight_trace_adaptive(cams, mets, gps, ps, fs, ad, outs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        rc, lr = native.blacklight_trace_adaptive(cams, mets, gps, ps, fs, ad, outs)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / steps
+    rays = int(lr.sum())
+    del prims, ps, outs
+    torch.cuda.empty_cache()
+    return {"workload": "torus256 adaptive: 16 images, 128^2 root, 8x8 blocks, 3 levels",
+            "value": rays / sec, "unit": "rays/s", "ms_per_step": sec * 1e3, "steps": steps,
+            "rays_per_step": rays, "rays_per_level": lr.sum(axis=0).tolist(),
+            "timing": "host wall clock (levels synchronise to read refinement decisions)"}
 
 
 def measure_e2e(torch, native, wl, prec, steps):

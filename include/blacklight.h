@@ -124,14 +124,18 @@ enum {
  *                 control in FP32), the rest in FP32. */
 enum { BL_PREC_FP64 = 0, BL_PREC_MIXED = 1, BL_PREC_FAST = 2 };
 /* flags: BL_ASYNC returns without synchronising; BL_TIMING records CUDA events on `stream`
- * around the geodesic and transfer kernels (read with blacklight_last_kernel_ms). */
+ * around the geodesic and transfer kernels of every wave (read with
+ * blacklight_last_kernel_ms). */
 enum { BL_ASYNC = 1u, BL_TIMING = 2u };
 
-/* Trace n_images cameras in one persistent launch pair (geodesics, then transfer). Image q
+/* Trace n_images cameras with persistent launch pairs (geodesics, then transfer). Image q
  * uses cams[q], mets[q], grids[q], freqs_hz[q] (observed frequency, > 0) and outs[q]. All
- * images must share metric.precision. workspace may be NULL (the library then allocates
- * stream-ordered scratch and frees it before returning) or a DEVICE buffer of at least
- * blacklight_workspace_size() bytes, which the call uses instead. */
+ * images must share metric.precision. The rays of all images are traced in waves of at most
+ * 2^20 rays, one launch pair per wave, reusing one workspace. workspace may be NULL (the
+ * library then allocates stream-ordered scratch and frees it before returning) or a DEVICE
+ * buffer the call uses instead: blacklight_workspace_size() bytes give the default waves; a
+ * smaller buffer is accepted and runs smaller waves (BL_EINVAL if it cannot hold one ray).
+ * Results do not depend on the wave size. */
 int blacklight_trace_batch(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
                            const bl_grid_t* grids, const double* freqs_hz, const bl_out_t* outs,
                            void* workspace, size_t workspace_bytes, void* stream,
@@ -168,7 +172,42 @@ int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const 
 int blacklight_geodesics(const bl_camera_t* cam, const bl_metric_t* met, const bl_out_t* out,
                          void* stream, uint32_t flags);
 
-/* Workspace bytes blacklight_trace_batch needs for these images. */
+/* Adaptive ray tracing (Sec. 4, "Adaptive Ray Tracing"). The root n x n image is split into
+ * square blocks of `block` pixels; each traced block is judged on its own pixels' Stokes I:
+ * when at least min_count pixels have a criterion value above `threshold`, every pixel of the
+ * block is split into four and the four child blocks are traced at the next level (pixel
+ * size halved), up to max_level. Criteria, with one-sided differences at block edges:
+ *   BL_CRIT_ABS_GRAD  (D_i^2 + D_j^2)^1/2, D_i = (I[i+1] - I[i-1]) / 2
+ *   BL_CRIT_REL_GRAD  same with D_i = 2 (I[i+1] - I[i-1]) / (I[i-1] + 2 I[i] + I[i+1])
+ *   BL_CRIT_ABS_LAPL  |D_i + D_j|, D_i = I[i-1] - 2 I[i] + I[i+1]
+ *   BL_CRIT_REL_LAPL  |D_i + D_j|, D_i = 4 (I[i-1] - 2 I[i] + I[i+1]) / (I[i-1] + 2 I[i] + I[i+1])
+ * A criterion that evaluates to NaN (e.g. 0/0 in dark regions) does not count. */
+typedef struct bl_adapt {
+    uint32_t size;
+    int32_t block;          /* block side in pixels; must divide the root n */
+    int32_t max_level;      /* 0 = no refinement */
+    int32_t criterion;      /* BL_CRIT_* */
+    double threshold;
+    int32_t min_count;      /* pixels of a block that must exceed the threshold, >= 1 */
+    double min_intensity;   /* pixels with Stokes I below this never count (0 = all count);
+                               keeps relative criteria from acting on numerically dark pixels */
+} bl_adapt_t;
+
+enum { BL_CRIT_ABS_GRAD = 0, BL_CRIT_REL_GRAD = 1, BL_CRIT_ABS_LAPL = 2, BL_CRIT_REL_LAPL = 3 };
+
+/* Trace n_images cameras adaptively (one launch pair per level for all images). outs[q].stokes
+ * receives the composite image at the finest resolution, DEVICE [4][nf][nf] with
+ * nf = n * 2^max_level, each pixel taking the value of the finest traced pixel covering it
+ * (dtype 0 float64 / 1 float32); outs[q].status/steps/samples/end_state are ignored.
+ * level_rays (optional HOST int32 [n_images][max_level + 1]) receives the rays traced per level.
+ * Synchronises `stream` between levels (refinement decisions are read back). */
+int blacklight_trace_adaptive(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                              const bl_grid_t* grids, const double* freqs_hz,
+                              const bl_adapt_t* adapt, const bl_out_t* outs, int32_t* level_rays,
+                              void* stream);
+
+/* Workspace bytes blacklight_trace_batch uses for these images with its default waves
+ * (at most 2^20 rays each). */
 size_t blacklight_workspace_size(int32_t n_images, const bl_camera_t* cams,
                                  const bl_metric_t* mets);
 
@@ -186,6 +225,12 @@ int blacklight_stokes_step(int64_t n, const double* coef, const double* s0, cons
                            double* s1, int32_t precision, void* stream);
 int blacklight_bessel_k(int64_t n, const double* x, double* out, int32_t precision,
                         void* stream);
+
+/* Refinement decisions alone (Sec. 4): I is DEVICE float64 [n_blocks][block][block] (row-major
+ * Stokes I of each block), flags DEVICE int8 [n_blocks] receives 1 where the block refines
+ * under the criterion of bl_adapt_t (adapt->max_level is ignored). */
+int blacklight_adapt_flags(int64_t n_blocks, const double* I, const bl_adapt_t* adapt,
+                           int8_t* flags, void* stream);
 
 const char* blacklight_strerror(int code);
 const char* blacklight_last_error_detail(void);

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <cstddef>
 #include <mutex>
 #include <vector>
 
@@ -16,8 +17,10 @@ namespace {
 thread_local char g_detail[512] = "";
 thread_local uint64_t g_launches = 0;
 // events around the geodesic and transfer kernels of the last BL_TIMING call on this thread
-thread_local cudaEvent_t g_ev[3] = {nullptr, nullptr, nullptr};
-thread_local bool g_timed = false;
+// BL_TIMING events of the last timed call on this thread: for wave w, [2w] precedes its
+// geodesic launch, [2w+1] separates geodesics from transfer, [2w+2] follows the transfer.
+thread_local std::vector<cudaEvent_t> g_ev;
+thread_local int g_timed_waves = 0;
 
 int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 int fail(int code, const char* fmt, ...) {
@@ -44,28 +47,63 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 // Average pool chunks reserved per ray (32 samples each); rays whose samples do not fit are
 // reported with status BL_RAY_OVERFLOW.
 constexpr int64_t kChunksPerRay = 16;
+// Rays are traced in waves of at most this many: the geodesic and transfer kernels run once
+// per wave, and the per-ray headers, chunk tables and sample pool are sized for one wave
+// (about 33 GiB with float records, 58 GiB with double records), so the workspace stays
+// bounded whatever the number of images or pixels.
+constexpr int64_t kWaveRays = 1 << 20;
 
 struct Layout {
     size_t counters, descs, hdr, chunks, pool, total;
-    int64_t rays, pool_chunks;
+    int64_t rays;          // rays of the whole call
+    int64_t wave;          // rays per wave (the workspace holds one wave)
+    int64_t pool_chunks;
 };
 
-Layout make_layout(int32_t n_images, const bl_camera_t* cams, int precision) {
+Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precision,
+                        bool transfer) {
     Layout L{};
-    int64_t rays = 0;
-    for (int q = 0; q < n_images; ++q) rays += (int64_t)cams[q].n * cams[q].n;
     L.rays = rays;
-    L.pool_chunks = rays * kChunksPerRay;
+    L.wave = wave;
+    L.pool_chunks = transfer ? L.wave * kChunksPerRay : 0;
     const size_t rec = precision != BL_PREC_FP64 ? sizeof(float) * bl::RecStride<float>::v
                                                  : sizeof(double) * bl::RecStride<double>::v;
     size_t off = 0;
     L.counters = off; off = align_up(off + sizeof(bl::Counters));
     L.descs = off;    off = align_up(off + sizeof(bl::ImageDesc) * (size_t)n_images);
-    L.hdr = off;      off = align_up(off + sizeof(bl::RayHdr) * (size_t)rays);
-    L.chunks = off;   off = align_up(off + sizeof(int32_t) * bl::kMaxChunks * (size_t)rays);
+    L.hdr = off;      off = align_up(off + sizeof(bl::RayHdr) * (size_t)L.wave);
+    L.chunks = off;   off = align_up(off + sizeof(int32_t) * bl::kMaxChunks * (size_t)L.wave);
     L.pool = off;     off = align_up(off + rec * bl::kChunk * (size_t)L.pool_chunks);
     L.total = off;
     return L;
+}
+
+Layout make_layout_rays(int32_t n_images, int64_t rays, int precision, bool transfer = true) {
+    return make_layout_wave(n_images, rays, rays < kWaveRays ? rays : kWaveRays, precision,
+                            transfer);
+}
+
+// The largest wave (>= 1 ray) whose layout fits in `bytes`; wave = 0 if none does.
+Layout fit_layout(int32_t n_images, int64_t rays, int precision, bool transfer, size_t bytes) {
+    Layout L = make_layout_rays(n_images, rays, precision, transfer);
+    if (L.total <= bytes) return L;
+    int64_t lo = 0, hi = L.wave;        // total(lo) fits (or lo = 0), total(hi) does not
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (make_layout_wave(n_images, rays, mid, precision, transfer).total <= bytes) lo = mid;
+        else hi = mid;
+    }
+    return make_layout_wave(n_images, rays, lo, precision, transfer);
+}
+
+int64_t count_rays(int32_t n_images, const bl_camera_t* cams) {
+    int64_t rays = 0;
+    for (int q = 0; q < n_images; ++q) rays += (int64_t)cams[q].n * cams[q].n;
+    return rays;
+}
+
+Layout make_layout(int32_t n_images, const bl_camera_t* cams, int precision) {
+    return make_layout_rays(n_images, count_rays(n_images, cams), precision);
 }
 
 int check_camera(const bl_camera_t* c, int q) {
@@ -174,6 +212,9 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
     d.end_state = o.end_state;
     d.samples = o.samples;
     d.ray_offset = offset;
+    d.n_rays = (int64_t)c.n * c.n;
+    d.block_list = nullptr;
+    d.block = 0;
 }
 
 struct DevInfo {
@@ -207,17 +248,22 @@ int dev_info(DevInfo& out) {
     return 0;
 }
 
-// Launch the camera-frame, geodesic and (optionally) transfer kernels on prepared workspace.
+// Launch the camera-frame kernel, then the geodesic and (optionally) transfer kernels once per
+// wave of rays, on prepared workspace. Waves run in stream order and reuse the workspace.
 int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* ws,
                const Layout& L, int precision, bool transfer, cudaStream_t st, bool timing) {
     DevInfo di;
     int rc = dev_info(di);
     if (rc) return rc;
+    const int64_t n_waves = L.wave > 0 ? (L.rays + L.wave - 1) / L.wave : 0;
     if (timing) {
-        for (int i = 0; i < 3; ++i)
-            if (!g_ev[i]) BL_CUDA(cudaEventCreate(&g_ev[i]));
+        while ((int64_t)g_ev.size() < 2 * n_waves + 1) {
+            cudaEvent_t e = nullptr;
+            BL_CUDA(cudaEventCreate(&e));
+            g_ev.push_back(e);
+        }
     }
-    g_timed = false;
+    g_timed_waves = 0;
     bl::Counters* ctr = (bl::Counters*)(ws + L.counters);
     bl::ImageDesc* d_desc = (bl::ImageDesc*)(ws + L.descs);
     bl::RayHdr* hdr = (bl::RayHdr*)(ws + L.hdr);
@@ -229,38 +275,45 @@ int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* 
     ++g_launches;
     BL_CUDA(cudaGetLastError());
     const int pidx = precision;
-    if (timing) BL_CUDA(cudaEventRecord(g_ev[0], st));
-    if (precision == BL_PREC_FP64) {
-        bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
-        bl::geodesic_kernel<double, double><<<di.sms * di.geo_blocks[pidx], 128, 0, st>>>(
-            d_desc, n_images, L.rays, hdr, sink, transfer ? 1 : 0);
-    } else {
-        bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
-        if (precision == BL_PREC_MIXED)
-            bl::geodesic_kernel<float, double><<<di.sms * di.geo_blocks[pidx], 128, 0, st>>>(
-                d_desc, n_images, L.rays, hdr, sink, transfer ? 1 : 0);
-        else
-            bl::geodesic_kernel<float, bl::df64><<<di.sms * di.geo_blocks[pidx], 128, 0, st>>>(
-                d_desc, n_images, L.rays, hdr, sink, transfer ? 1 : 0);
-    }
-    ++g_launches;
-    BL_CUDA(cudaGetLastError());
-    if (timing) BL_CUDA(cudaEventRecord(g_ev[1], st));
-    if (transfer) {
-        if (precision != BL_PREC_FP64) {
-            bl::transfer_kernel<float, float><<<di.sms * di.tr_blocks[pidx], 128, 0, st>>>(
-                d_desc, n_images, L.rays, hdr, (const float*)(ws + L.pool), chunks, ctr);
+    const unsigned geo_grid = (unsigned)(di.sms * di.geo_blocks[pidx]);
+    const unsigned tr_grid = (unsigned)(di.sms * di.tr_blocks[pidx]);
+    const int record = transfer ? 1 : 0;
+    for (int64_t w = 0; w < n_waves; ++w) {
+        const int64_t b = w * L.wave;
+        const int64_t e = b + L.wave < L.rays ? b + L.wave : L.rays;
+        // the work and pool counters restart with each wave; bad_rays accumulates
+        if (w > 0) BL_CUDA(cudaMemsetAsync(ctr, 0, offsetof(bl::Counters, bad_rays), st));
+        if (timing) BL_CUDA(cudaEventRecord(g_ev[2 * w], st));
+        if (precision == BL_PREC_FP64) {
+            bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
+            bl::geodesic_kernel<double, double><<<geo_grid, 128, 0, st>>>(
+                d_desc, n_images, b, e, hdr, sink, record);
         } else {
-            bl::transfer_kernel<double, double><<<di.sms * di.tr_blocks[pidx], 128, 0, st>>>(
-                d_desc, n_images, L.rays, hdr, (const double*)(ws + L.pool), chunks, ctr);
+            bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
+            if (precision == BL_PREC_MIXED)
+                bl::geodesic_kernel<float, double><<<geo_grid, 128, 0, st>>>(
+                    d_desc, n_images, b, e, hdr, sink, record);
+            else
+                bl::geodesic_kernel<float, bl::df64><<<geo_grid, 128, 0, st>>>(
+                    d_desc, n_images, b, e, hdr, sink, record);
         }
         ++g_launches;
         BL_CUDA(cudaGetLastError());
+        if (timing) BL_CUDA(cudaEventRecord(g_ev[2 * w + 1], st));
+        if (transfer) {
+            if (precision != BL_PREC_FP64) {
+                bl::transfer_kernel<float, float><<<tr_grid, 128, 0, st>>>(
+                    d_desc, n_images, b, e, hdr, (const float*)(ws + L.pool), chunks, ctr);
+            } else {
+                bl::transfer_kernel<double, double><<<tr_grid, 128, 0, st>>>(
+                    d_desc, n_images, b, e, hdr, (const double*)(ws + L.pool), chunks, ctr);
+            }
+            ++g_launches;
+            BL_CUDA(cudaGetLastError());
+        }
+        if (timing) BL_CUDA(cudaEventRecord(g_ev[2 * w + 2], st));
     }
-    if (timing) {
-        BL_CUDA(cudaEventRecord(g_ev[2], st));
-        g_timed = true;
-    }
+    if (timing) g_timed_waves = (int)n_waves;
     return 0;
 }
 
@@ -306,11 +359,9 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
         snprintf(what, sizeof(what), "grids[%d].prim", q);
         if (transfer && (rc = device_pointer(grids[q].prim, what))) return rc;
     }
-    Layout L = make_layout(n_images, cams, transfer ? precision : BL_PREC_MIXED);
-    if (!transfer && precision == BL_PREC_FP64) {
-        // geodesics only: no records, so the FP64 form's record type is irrelevant
-    }
-    if (!transfer) { L.pool_chunks = 0; L.total = L.pool; }
+    // geodesics only: no records, so no pool
+    const int64_t rays = count_rays(n_images, cams);
+    Layout L = make_layout_rays(n_images, rays, precision, transfer);
     std::vector<bl::ImageDesc> descs(n_images);
     int64_t off = 0;
     static const bl_grid_t kNoGrid = {sizeof(bl_grid_t), nullptr, 1, 1, 1, 1.0, 2.0, 4.0 / 3.0,
@@ -324,8 +375,12 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
     char* ws = (char*)workspace;
     bool own = false;
     if (ws) {
-        if (workspace_bytes < L.total)
-            return fail(BL_EINVAL, "workspace too small: %zu < %zu bytes", workspace_bytes, L.total);
+        // a workspace smaller than the default layout runs the rays in more, smaller waves
+        L = fit_layout(n_images, rays, precision, transfer, workspace_bytes);
+        if (L.wave < 1)
+            return fail(BL_EINVAL, "workspace too small: %zu < %zu bytes (one ray)",
+                        workspace_bytes,
+                        make_layout_wave(n_images, rays, 1, precision, transfer).total);
         int rc = device_pointer(ws, "workspace");
         if (rc) return rc;
     } else {
@@ -375,9 +430,227 @@ int noalloc_scratch(char** out) {
     return 0;
 }
 
+int check_adapt(const bl_adapt_t* ad, const bl_camera_t* cams, int32_t n_images) {
+    if (!ad) return fail(BL_EINVAL, "adapt is NULL");
+    if (ad->size != sizeof(bl_adapt_t)) return fail(BL_EINVAL, "adapt.size mismatch");
+    if (ad->block < 1 || ad->max_level < 0 || ad->max_level > 8 || ad->min_count < 1 ||
+        ad->min_count > ad->block * ad->block)
+        return fail(BL_EINVAL, "adapt: block >= 1, 0 <= max_level <= 8, 1 <= min_count <= block^2");
+    if (ad->criterion < BL_CRIT_ABS_GRAD || ad->criterion > BL_CRIT_REL_LAPL)
+        return fail(BL_EINVAL, "adapt.criterion");
+    if (!std::isfinite(ad->threshold)) return fail(BL_EINVAL, "adapt.threshold");
+    if (!(ad->min_intensity >= 0.0)) return fail(BL_EINVAL, "adapt.min_intensity must be >= 0");
+    for (int q = 0; q < n_images; ++q) {
+        if (cams[q].n % ad->block) return fail(BL_EINVAL, "cams[%d].n must be a multiple of block", q);
+        if ((int64_t)cams[q].n << ad->max_level > 65536)
+            return fail(BL_EINVAL, "cams[%d]: n * 2^max_level exceeds 65536", q);
+    }
+    return 0;
+}
+
+// Adaptive tracing driven level by level from the host (refinement decisions are read back).
+int trace_adaptive_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                        const bl_grid_t* grids, const double* freqs, const bl_adapt_t* ad,
+                        const bl_out_t* outs, int32_t* level_rays, cudaStream_t st) {
+    const int B = ad->block, maxL = ad->max_level;
+    const int precision = mets[0].precision;
+    const size_t vsize = precision == BL_PREC_FP64 ? sizeof(double) : sizeof(float);
+    // host block lists per image for the current level: (bx, by) pairs
+    std::vector<std::vector<int32_t>> blocks(n_images);
+    for (int q = 0; q < n_images; ++q) {
+        const int nb = cams[q].n / B;
+        for (int by = 0; by < nb; ++by)
+            for (int bx = 0; bx < nb; ++bx) { blocks[q].push_back(bx); blocks[q].push_back(by); }
+    }
+    // device buffers grow as needed
+    char* ws = nullptr; size_t ws_bytes = 0;
+    char* lvl = nullptr; size_t lvl_bytes = 0;           // compact Stokes of the level
+    int32_t* dblk = nullptr; size_t dblk_bytes = 0;      // block lists of the level
+    int8_t* dflags = nullptr; size_t dflags_bytes = 0;
+    auto grow = [&](void** p, size_t& have, size_t need) -> int {
+        if (need <= have) return 0;
+        if (*p) cudaFreeAsync(*p, st);
+        *p = nullptr;
+        const size_t n = need;
+        cudaError_t e = cudaMallocAsync(p, n, st);
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync(%zu): %s", n, cudaGetErrorString(e)); }
+        have = n;
+        return 0;
+    };
+    int rc = 0;
+    unsigned long long bad_total = 0;
+    for (int L = 0; L <= maxL && rc == 0; ++L) {
+        // rays of this level, per image, and offsets into the compact buffers
+        std::vector<int64_t> nrays(n_images), roff(n_images), boff(n_images);
+        int64_t rays = 0, nblk = 0;
+        for (int q = 0; q < n_images; ++q) {
+            const int64_t nb = (int64_t)blocks[q].size() / 2;
+            nrays[q] = nb * B * B;
+            roff[q] = rays;
+            boff[q] = nblk;
+            rays += nrays[q];
+            nblk += nb;
+            if (level_rays) level_rays[q * (maxL + 1) + L] = (int32_t)nrays[q];
+        }
+        if (rays == 0) break;
+        std::vector<int32_t> hblk;
+        hblk.reserve(2 * nblk);
+        for (int q = 0; q < n_images; ++q) hblk.insert(hblk.end(), blocks[q].begin(), blocks[q].end());
+        if ((rc = grow((void**)&dblk, dblk_bytes, hblk.size() * sizeof(int32_t)))) break;
+        if ((rc = grow((void**)&lvl, lvl_bytes, 4 * (size_t)rays * vsize))) break;
+        BL_CUDA(cudaMemcpyAsync(dblk, hblk.data(), hblk.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        // one descriptor per image that has rays at this level
+        std::vector<bl::ImageDesc> descs;
+        std::vector<int> qmap;
+        int64_t off = 0;
+        for (int q = 0; q < n_images; ++q) {
+            if (!nrays[q]) continue;
+            bl_camera_t c = cams[q];
+            c.n = cams[q].n << L;
+            bl_out_t o{sizeof(bl_out_t), nullptr, precision == BL_PREC_FP64 ? 0 : 1, nullptr, nullptr,
+                       nullptr, nullptr};
+            bl::ImageDesc d;
+            fill_desc(d, c, mets[q], grids[q], freqs[q], o, off);
+            d.n_rays = nrays[q];
+            d.block_list = dblk + 2 * boff[q];
+            d.block = B;
+            // the compact Stokes of this image: planes of length n_rays at lvl + 4 * roff
+            d.stokes = lvl + 4 * roff[q] * vsize;
+            descs.push_back(d);
+            qmap.push_back(q);
+            off += nrays[q];
+        }
+        Layout Ly = make_layout_rays((int32_t)descs.size(), rays, precision);
+        if ((rc = grow((void**)&ws, ws_bytes, Ly.total))) break;
+        if ((rc = launch_all((int32_t)descs.size(), descs, ws, Ly, precision, true, st, false))) break;
+        unsigned long long bad = 0;
+        BL_CUDA(cudaMemcpyAsync(&bad, &((bl::Counters*)(ws + Ly.counters))->bad_rays, sizeof(bad),
+                                cudaMemcpyDeviceToHost, st));
+        // composite: paint this level into each image's finest-resolution output
+        const int s = 1 << (maxL - L);
+        for (size_t k = 0; k < descs.size(); ++k) {
+            const int q = qmap[k];
+            const int nf = cams[q].n << maxL;
+            const int64_t nr = nrays[q];
+            const int threads = 256;
+            const unsigned grid_n = (unsigned)((nr + threads - 1) / threads);
+            char* st_q = lvl + 4 * roff[q] * vsize;
+            const int32_t* bl_q = dblk + 2 * boff[q];
+            if (precision == BL_PREC_FP64) {
+                if (outs[q].dtype == 0)
+                    bl::adapt_composite_kernel<double, double><<<grid_n, threads, 0, st>>>((const double*)st_q, nr, bl_q, B, s, nf, (double*)outs[q].stokes);
+                else
+                    bl::adapt_composite_kernel<double, float><<<grid_n, threads, 0, st>>>((const double*)st_q, nr, bl_q, B, s, nf, (float*)outs[q].stokes);
+            } else {
+                if (outs[q].dtype == 0)
+                    bl::adapt_composite_kernel<float, double><<<grid_n, threads, 0, st>>>((const float*)st_q, nr, bl_q, B, s, nf, (double*)outs[q].stokes);
+                else
+                    bl::adapt_composite_kernel<float, float><<<grid_n, threads, 0, st>>>((const float*)st_q, nr, bl_q, B, s, nf, (float*)outs[q].stokes);
+            }
+            ++g_launches;
+            BL_CUDA(cudaGetLastError());
+        }
+        if (L == maxL) {
+            BL_CUDA(cudaStreamSynchronize(st));
+            bad_total += bad;
+            break;
+        }
+        // refinement decisions for every block of this level
+        if ((rc = grow((void**)&dflags, dflags_bytes, (size_t)nblk))) break;
+        for (size_t k = 0; k < descs.size(); ++k) {
+            const int q = qmap[k];
+            const int64_t nb = nrays[q] / ((int64_t)B * B);
+            const unsigned grid_n = (unsigned)((nb + 127) / 128);
+            char* st_q = lvl + 4 * roff[q] * vsize;     // plane 0 = Stokes I
+            if (precision == BL_PREC_FP64)
+                bl::adapt_criterion_kernel<double><<<grid_n, 128, 0, st>>>((const double*)st_q, nb, B, ad->criterion, ad->threshold, ad->min_count, ad->min_intensity, dflags + boff[q]);
+            else
+                bl::adapt_criterion_kernel<float><<<grid_n, 128, 0, st>>>((const float*)st_q, nb, B, ad->criterion, ad->threshold, ad->min_count, ad->min_intensity, dflags + boff[q]);
+            ++g_launches;
+            BL_CUDA(cudaGetLastError());
+        }
+        std::vector<int8_t> hflags(nblk);
+        BL_CUDA(cudaMemcpyAsync(hflags.data(), dflags, nblk, cudaMemcpyDeviceToHost, st));
+        BL_CUDA(cudaStreamSynchronize(st));
+        bad_total += bad;
+        // children of refined blocks, in parent order: (2bx+dx, 2by+dy), dy then dx
+        for (int q = 0; q < n_images; ++q) {
+            std::vector<int32_t> next;
+            const int64_t nb = (int64_t)blocks[q].size() / 2;
+            for (int64_t b = 0; b < nb; ++b) {
+                if (!hflags[boff[q] + b]) continue;
+                const int32_t bx = blocks[q][2 * b], by = blocks[q][2 * b + 1];
+                for (int dy = 0; dy < 2; ++dy)
+                    for (int dx = 0; dx < 2; ++dx) { next.push_back(2 * bx + dx); next.push_back(2 * by + dy); }
+            }
+            blocks[q].swap(next);
+        }
+        if (level_rays)
+            for (int q = 0; q < n_images; ++q)
+                for (int LL = L + 1; LL <= maxL; ++LL) level_rays[q * (maxL + 1) + LL] = 0;
+    }
+    if (ws) cudaFreeAsync(ws, st);
+    if (lvl) cudaFreeAsync(lvl, st);
+    if (dblk) cudaFreeAsync(dblk, st);
+    if (dflags) cudaFreeAsync(dflags, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (rc == 0 && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+    if (rc == 0 && bad_total) rc = BL_WRAYS;
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
+
+int blacklight_trace_adaptive(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                              const bl_grid_t* grids, const double* freqs_hz,
+                              const bl_adapt_t* adapt, const bl_out_t* outs, int32_t* level_rays,
+                              void* stream) {
+    g_detail[0] = 0;
+    if (n_images < 1) return fail(BL_EINVAL, "n_images must be >= 1");
+    if (!cams || !mets || !grids || !freqs_hz || !outs) return fail(BL_EINVAL, "NULL array argument");
+    int precision = -1;
+    for (int q = 0; q < n_images; ++q) {
+        int rc = check_camera(&cams[q], q);
+        if (!rc) rc = check_metric(&mets[q], q);
+        if (!rc) rc = check_grid(&grids[q], q);
+        if (!rc) rc = check_out(&outs[q], q, true);
+        if (rc) return rc;
+        if (!(freqs_hz[q] > 0.0 && std::isfinite(freqs_hz[q]))) return fail(BL_EINVAL, "freqs[%d] must be > 0", q);
+        if (precision < 0) precision = mets[q].precision;
+        else if (precision != mets[q].precision) return fail(BL_EINVAL, "all images must share metric.precision");
+        char what[64];
+        snprintf(what, sizeof(what), "outs[%d].stokes", q);
+        if ((rc = device_pointer(outs[q].stokes, what))) return rc;
+        snprintf(what, sizeof(what), "grids[%d].prim", q);
+        if ((rc = device_pointer(grids[q].prim, what))) return rc;
+    }
+    int rc = check_adapt(adapt, cams, n_images);
+    if (rc) return rc;
+    return trace_adaptive_impl(n_images, cams, mets, grids, freqs_hz, adapt, outs, level_rays,
+                               (cudaStream_t)stream);
+}
+
+int blacklight_adapt_flags(int64_t n_blocks, const double* I, const bl_adapt_t* adapt,
+                           int8_t* flags, void* stream) {
+    g_detail[0] = 0;
+    if (n_blocks < 0 || (n_blocks > 0 && (!I || !flags))) return fail(BL_EINVAL, "bad arguments");
+    if (!adapt || adapt->size != sizeof(bl_adapt_t) || adapt->block < 1 || adapt->min_count < 1 ||
+        adapt->criterion < BL_CRIT_ABS_GRAD || adapt->criterion > BL_CRIT_REL_LAPL)
+        return fail(BL_EINVAL, "adapt");
+    if (n_blocks == 0) return 0;
+    int rc = device_pointer(I, "I");
+    if (!rc) rc = device_pointer(flags, "flags");
+    if (rc) return rc;
+    bl::adapt_criterion_kernel<double><<<(unsigned)((n_blocks + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+        I, n_blocks, adapt->block, adapt->criterion, adapt->threshold, adapt->min_count,
+        adapt->min_intensity, flags);
+    ++g_launches;
+    BL_CUDA(cudaGetLastError());
+    BL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return 0;
+}
 
 int blacklight_trace_noalloc(const bl_camera_t* cam, const bl_metric_t* met,
                              const bl_grid_t* grid, double freq_hz, const bl_out_t* out,
@@ -550,10 +823,17 @@ const char* blacklight_last_error_detail(void) { return g_detail; }
 int blacklight_last_kernel_ms(float ms[2]) {
     g_detail[0] = 0;
     if (!ms) return fail(BL_EINVAL, "ms is NULL");
-    if (!g_timed) return fail(BL_EINVAL, "no call with BL_TIMING on this thread");
-    BL_CUDA(cudaEventSynchronize(g_ev[2]));
-    BL_CUDA(cudaEventElapsedTime(&ms[0], g_ev[0], g_ev[1]));
-    BL_CUDA(cudaEventElapsedTime(&ms[1], g_ev[1], g_ev[2]));
+    if (g_timed_waves < 1) return fail(BL_EINVAL, "no call with BL_TIMING on this thread");
+    const int w_n = g_timed_waves;
+    BL_CUDA(cudaEventSynchronize(g_ev[2 * w_n]));
+    ms[0] = ms[1] = 0.0f;
+    for (int w = 0; w < w_n; ++w) {
+        float a = 0.0f, b = 0.0f;
+        BL_CUDA(cudaEventElapsedTime(&a, g_ev[2 * w], g_ev[2 * w + 1]));
+        BL_CUDA(cudaEventElapsedTime(&b, g_ev[2 * w + 1], g_ev[2 * w + 2]));
+        ms[0] += a;
+        ms[1] += b;
+    }
     return 0;
 }
 

@@ -37,6 +37,14 @@ struct ImageDesc {
     double* end_state;
     int32_t* samples;
     int64_t ray_offset;     // first global ray index of this image
+    int64_t n_rays;         // rays traced for this image (n * n, or blocks x block^2)
+    // Block-list mode (adaptive refinement): when block_list is set, ray p traces pixel
+    // (bx * block + u, by * block + v) of the n x n pixel grid, with (bx, by) =
+    // block_list[2 (p / block^2)], and u, v the row-major position inside the block; outputs
+    // are then compact, indexed by p (Stokes [4][n_rays]).
+    const int32_t* block_list;
+    int32_t block;
+    int32_t pad2_;
     // filled by the camera-frame kernel
     double x_cam[4], u_cam[4], kk[4], hh[4], vv[4];
     double r_cam, r_hor;

@@ -144,8 +144,23 @@ __device__ __forceinline__ int find_image(const ImageDesc* imgs, int n_images, i
     return q;
 }
 
-// Pixel order inside an image: Morton (Z) order when n is a power of two so that a warp
-// covers a compact 8x4 patch of the image, row-major otherwise.
+// Pixel of local ray p and the index its outputs go to: block-list order (adaptive
+// refinement), else Morton (Z) order when n is a power of two so that a warp covers a
+// compact 8x4 patch of the image, else row-major.
+__device__ __forceinline__ void pixel_of(int64_t p, int n, int& i, int& j);
+__device__ __forceinline__ int64_t ray_pixel(const ImageDesc& im, int64_t p, int& i, int& j) {
+    if (im.block_list) {
+        const int64_t b2 = (int64_t)im.block * im.block;
+        const int64_t blk = p / b2;
+        const int r = (int)(p - blk * b2);
+        i = im.block_list[2 * blk] * im.block + r % im.block;
+        j = im.block_list[2 * blk + 1] * im.block + r / im.block;
+        return p;
+    }
+    pixel_of(p, im.n, i, j);
+    return (int64_t)j * im.n + i;
+}
+
 __device__ __forceinline__ void pixel_of(int64_t p, int n, int& i, int& j) {
     if ((n & (n - 1)) == 0) {
         uint32_t xi = 0, yj = 0;
@@ -404,9 +419,13 @@ __device__ __forceinline__ bool append_record(const RecordSink<R>& S, int64_t ra
 
 template <class R, class G>
 __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __restrict__ imgs,
-                                                          int n_images, int64_t total_rays,
+                                                          int n_images, int64_t ray_begin,
+                                                          int64_t ray_end,
                                                           RayHdr* __restrict__ hdr,
                                                           RecordSink<R> sink, int record) {
+    // rays [ray_begin, ray_end) of the batch form this wave; hdr and the chunk tables are
+    // indexed by ray - ray_begin
+    const int64_t total_rays = ray_end - ray_begin;
     using A = GeoArith<G>;
     // compile-time constants in the integrator arithmetic (a run-time double -> df64 split
     // would cost FP64 conversions)
@@ -455,6 +474,8 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
     bool active = false;
     int64_t ray = 0;
     int q = 0, pi = 0, pj = 0;
+    int64_t opix = 0;   // output index of the current ray
+    int64_t wray = 0;   // index of the current ray within this wave
     G y[8];
     G K[7][8];          // K[0] = f(y); K[1..6] stage derivatives of the current attempt
     G h = G(0);
@@ -480,7 +501,8 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
             if ((int64_t)got >= total_rays) {
                 exhausted = true;
             } else {
-                ray = (int64_t)got;
+                wray = (int64_t)got;
+                ray = ray_begin + wray;
                 active = true;
             }
         }
@@ -489,7 +511,7 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
         if (need) {   // a ray taken from the queue in this iteration: set it up
             q = find_image(imgs, n_images, ray);
             const ImageDesc& im = imgs[q];
-            pixel_of(ray - im.ray_offset, im.n, pi, pj);
+            opix = ray_pixel(im, ray - im.ray_offset, pi, pj);
             double yd[8];
             pixel_state(im, pi, pj, yd, nnorm);
 #pragma unroll
@@ -627,7 +649,7 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
                 }
                 bool ok = true;
                 if (nsub == 1) {
-                    ok = append_record(sink, ray, nrec, ym, y, fabs(hd));
+                    ok = append_record(sink, wray, nrec, ym, y, fabs(hd));
                 } else if (sizeof(R) == sizeof(float)) {
                     // float records: the quartic through y0, y1, h f0, h f1 and y_mid
                     // (Shampine 1986), evaluated in FP32 about y0
@@ -654,7 +676,7 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
                             ynd[c] = (s == 0) ? y0f[c]
                                               : y0f[c] + tn * (d0f[c] + tn * (c2f[c] + tn * (c3f[c] + tn * c4f[c])));
                         }
-                        ok = append_record(sink, ray, nrec, ysm, ynd, fabs(hd) / nsub);
+                        ok = append_record(sink, wray, nrec, ysm, ynd, fabs(hd) / nsub);
                     }
                 } else {
                     double y0d[8], d0[8], c2[8], c3[8], c4[8];
@@ -679,7 +701,7 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
                             ynd[c] = (s == 0) ? y0d[c]
                                               : y0d[c] + tn * (d0[c] + tn * (c2[c] + tn * (c3[c] + tn * c4[c])));
                         }
-                        ok = append_record(sink, ray, nrec, ysm, ynd, fabs(hd) * inv);
+                        ok = append_record(sink, wray, nrec, ysm, ynd, fabs(hd) * inv);
                     }
                 }
                 if (!ok) { status = BL_RAY_OVERFLOW; done = true; }
@@ -724,7 +746,7 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
         }
         if (done) {
             const ImageDesc& im = imgs[q];
-            const int64_t pix = (int64_t)pj * im.n + pi;
+            const int64_t pix = opix;
             if (im.status) im.status[pix] = status;
             if (im.steps) im.steps[pix] = (int32_t)(attempts < 2147483647 ? attempts : 2147483647);
             if (im.end_state)
@@ -735,7 +757,7 @@ __global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __res
             hd.nnorm = nnorm;
             hd.nrec = nrec;
             hd.status = status;
-            hdr[ray] = hd;
+            hdr[wray] = hd;
             if (status != BL_RAY_HORIZON && status != BL_RAY_ESCAPED)
                 atomicAdd(&ctr->bad_rays, 1ull);
             active = false;
@@ -1014,13 +1036,16 @@ __device__ __forceinline__ const R* record_ptr(const R* __restrict__ pool, const
 // ---------------------------------------------------------------------------------------
 template <class T, class R>
 __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restrict__ imgs,
-                                                       int n_images, int64_t total_rays,
+                                                       int n_images, int64_t ray_begin,
+                                                       int64_t ray_end,
                                                        const RayHdr* __restrict__ hdr,
                                                        const R* __restrict__ pool,
                                                        const int32_t* __restrict__ chunks,
                                                        Counters* ctr) {
+    const int64_t total_rays = ray_end - ray_begin;
+    int64_t wray = 0;
     bool active = false;
-    int64_t ray = 0;
+    int64_t ray = 0, opix = 0;
     int q = 0, pi = 0, pj = 0;
     int32_t idx = 0;
     Coh<T> N;
@@ -1036,18 +1061,18 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
         const unsigned long long got = warp_refill(&ctr->next_ray_tr, need);
         if (need) {
             if ((int64_t)got >= total_rays) exhausted = true;
-            else { ray = (int64_t)got; }
+            else { wray = (int64_t)got; ray = ray_begin + wray; }
         }
         if (!__any_sync(0xffffffffu, active || (need && !exhausted))) break;
         if (!active && !(need && !exhausted)) continue;
         if (!active) {
             q = find_image(imgs, n_images, ray);
             const ImageDesc& im = imgs[q];
-            pixel_of(ray - im.ray_offset, im.n, pi, pj);
-            const RayHdr hd = hdr[ray];
+            opix = ray_pixel(im, ray - im.ray_offset, pi, pj);
+            const RayHdr hd = hdr[wray];
             if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) {
-                const int64_t npix = (int64_t)im.n * im.n;
-                const int64_t pix = (int64_t)pj * im.n + pi;
+                const int64_t npix = im.n_rays;
+                const int64_t pix = opix;
                 const double val = hd.status == BL_RAY_OVERFLOW ? nan("") : 0.0;
                 for (int s = 0; s < 4; ++s) {
                     if (im.dtype == 0) ((double*)im.stokes)[s * npix + pix] = val;
@@ -1056,7 +1081,7 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
                 continue;
             }
             idx = hd.nrec - 1;
-            load_record<R>(record_ptr(pool, chunks, ray, idx), nxt);
+            load_record<R>(record_ptr(pool, chunks, wray, idx), nxt);
             kt = (T)hd.kt;
             nu_norm = (T)(hd.nnorm * im.freq);
             a = ic<T>(im, kcSpin);
@@ -1074,7 +1099,7 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
         T cur[kRecVals];
 #pragma unroll
         for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
-        if (idx > 0) load_record<R>(record_ptr(pool, chunks, ray, idx - 1), nxt);
+        if (idx > 0) load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
         if (started) {
             // merged N half-steps from the previous sample to this one
             T A0[4][4], A1[4][4];
@@ -1140,14 +1165,95 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
             lower4(G, vv, vl);
             T s[4];
             coh_to_stokes(N, hl, vl, s);
-            const int64_t npix = (int64_t)im.n * im.n;
-            const int64_t pix = (int64_t)pj * im.n + pi;
+            const int64_t npix = im.n_rays;
+            const int64_t pix = opix;
             for (int c = 0; c < 4; ++c) {
                 if (im.dtype == 0) ((double*)im.stokes)[c * npix + pix] = (double)s[c];
                 else ((float*)im.stokes)[c * npix + pix] = (float)s[c];
             }
             active = false;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Adaptive refinement (Sec. 4): per-block criterion and composite assembly.
+// ---------------------------------------------------------------------------------------
+// Criterion value of pixel (u, v) of a B x B block whose Stokes I is I[v * B + u].
+template <class V>
+__device__ __forceinline__ double adapt_value(const V* I, int B, int u, int v, int crit) {
+    auto at = [&](int uu, int vv) -> double { return (double)I[vv * B + uu]; };
+    // differences along one axis at position w of B with the two neighbours of w, one-sided
+    // (shifted stencil) at the block edges
+    auto d1 = [&](bool along_u, int w) -> double {
+        if (B < 2) return 0.0;
+        auto val = [&](int k) -> double { return along_u ? at(k, v) : at(u, k); };
+        int lo = w - 1, hi = w + 1;
+        double num, den;
+        if (w == 0) { lo = 0; hi = 1; }
+        else if (w == B - 1) { lo = B - 2; hi = B - 1; }
+        const bool central = (hi - lo) == 2;
+        if (crit == BL_CRIT_ABS_GRAD) {
+            num = val(hi) - val(lo);
+            return central ? 0.5 * num : num;
+        }
+        // relative gradient
+        num = val(hi) - val(lo);
+        den = central ? (val(lo) + 2.0 * val(w) + val(hi)) : 0.5 * (val(lo) + val(hi)) * 2.0;
+        return central ? 2.0 * num / den : 2.0 * num / den;
+    };
+    auto d2 = [&](bool along_u, int w) -> double {
+        if (B < 3) return 0.0;
+        auto val = [&](int k) -> double { return along_u ? at(k, v) : at(u, k); };
+        int c = w;
+        if (c == 0) c = 1;
+        else if (c == B - 1) c = B - 2;
+        const double lap = val(c - 1) - 2.0 * val(c) + val(c + 1);
+        if (crit == BL_CRIT_ABS_LAPL) return lap;
+        return 4.0 * lap / (val(c - 1) + 2.0 * val(c) + val(c + 1));
+    };
+    if (crit == BL_CRIT_ABS_GRAD || crit == BL_CRIT_REL_GRAD) {
+        const double di = d1(true, u), dj = d1(false, v);
+        return sqrt(di * di + dj * dj);
+    }
+    return fabs(d2(true, u) + d2(false, v));
+}
+
+// One thread per block: flags[b] = 1 when at least min_count pixels exceed the threshold.
+template <class V>
+__global__ void adapt_criterion_kernel(const V* __restrict__ I, int64_t n_blocks, int B, int crit,
+                                       double threshold, int min_count, double min_intensity,
+                                       int8_t* __restrict__ flags) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= n_blocks) return;
+    const V* blk = I + b * (int64_t)B * B;
+    int count = 0;
+    for (int v = 0; v < B; ++v)
+        for (int u = 0; u < B; ++u)
+            if ((double)blk[v * B + u] >= min_intensity &&
+                adapt_value(blk, B, u, v, crit) > threshold) ++count;   // NaN never counts
+    flags[b] = count >= min_count ? 1 : 0;
+}
+
+// Paint the rays of one level into the finest-level composite: the ray of block-list pixel
+// (i, j) at this level covers the s x s finest pixels starting at (i s, j s).
+template <class V, class O>
+__global__ void adapt_composite_kernel(const V* __restrict__ st, int64_t n_rays,
+                                       const int32_t* __restrict__ blocks, int B, int s, int nf,
+                                       O* __restrict__ out) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n_rays) return;
+    const int64_t b2 = (int64_t)B * B;
+    const int64_t blk = p / b2;
+    const int r = (int)(p - blk * b2);
+    const int i = blocks[2 * blk] * B + r % B;
+    const int j = blocks[2 * blk + 1] * B + r / B;
+    const int64_t plane = (int64_t)nf * nf;
+    for (int c = 0; c < 4; ++c) {
+        const O v = (O)st[c * n_rays + p];
+        for (int dj = 0; dj < s; ++dj)
+            for (int di = 0; di < s; ++di)
+                out[c * plane + (int64_t)(j * s + dj) * nf + (i * s + di)] = v;
     }
 }
 

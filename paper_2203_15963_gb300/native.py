@@ -68,6 +68,15 @@ class Grid(C.Structure):
                 ("mass_msun", C.c_double), ("interp", C.c_int32)]
 
 
+class Adapt(C.Structure):
+    _fields_ = [("size", C.c_uint32), ("block", C.c_int32), ("max_level", C.c_int32),
+                ("criterion", C.c_int32), ("threshold", C.c_double), ("min_count", C.c_int32),
+                ("min_intensity", C.c_double)]
+
+
+BL_CRIT_ABS_GRAD, BL_CRIT_REL_GRAD, BL_CRIT_ABS_LAPL, BL_CRIT_REL_LAPL = 0, 1, 2, 3
+
+
 class Out(C.Structure):
     _fields_ = [("size", C.c_uint32), ("stokes", C.c_void_p), ("dtype", C.c_int32),
                 ("status", C.c_void_p), ("steps", C.c_void_p), ("end_state", C.c_void_p),
@@ -91,6 +100,11 @@ def load():
                                          P, C.c_size_t, P, C.c_uint32]
     L.blacklight_trace.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Grid),
                                    C.c_double, C.POINTER(Out), P, C.c_uint32]
+    L.blacklight_trace_adaptive.argtypes = [C.c_int32, C.POINTER(Camera), C.POINTER(Metric),
+                                            C.POINTER(Grid), C.POINTER(C.c_double),
+                                            C.POINTER(Adapt), C.POINTER(Out),
+                                            C.POINTER(C.c_int32), P]
+    L.blacklight_adapt_flags.argtypes = [C.c_int64, P, C.POINTER(Adapt), P, P]
     L.blacklight_trace_noalloc.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Grid),
                                            C.c_double, C.POINTER(Out), P, C.c_uint32]
     L.blacklight_trace_host.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Grid),
@@ -249,3 +263,31 @@ def blacklight_last_kernel_ms():
     ms = (C.c_float * 2)()
     _check(load().blacklight_last_kernel_ms(ms))
     return float(ms[0]), float(ms[1])
+
+
+def adapt_struct(block, max_level, criterion, threshold, min_count, min_intensity=0.0) -> Adapt:
+    return Adapt(C.sizeof(Adapt), block, max_level, criterion, float(threshold), min_count,
+                 float(min_intensity))
+
+
+def blacklight_trace_adaptive(cams, mets, gps, prims, freqs, adapt, outs, stream=None):
+    """Adaptive tracing; outs[q]["stokes"] is the [4][nf][nf] composite. Returns (rc, rays per
+    level [n_images][max_level + 1])."""
+    import numpy as np
+    L = load()
+    n = len(cams)
+    ca = (Camera * n)(*[camera_struct(c) for c in cams])
+    ma = (Metric * n)(*[metric_struct(m) for m in mets])
+    ga = (Grid * n)(*[grid_struct(g, p.data_ptr()) for g, p in zip(gps, prims)])
+    fa = (C.c_double * n)(*[float(f) for f in freqs])
+    oa = (Out * n)(*[out_struct(**o) for o in outs])
+    lr = np.zeros((n, adapt.max_level + 1), dtype=np.int32)
+    rc = _check(L.blacklight_trace_adaptive(n, ca, ma, ga, fa, C.byref(adapt), oa,
+                                            lr.ctypes.data_as(C.POINTER(C.c_int32)),
+                                            _stream(stream)))
+    return rc, lr
+
+
+def blacklight_adapt_flags(I, adapt, flags, stream=None):
+    return _check(load().blacklight_adapt_flags(I.shape[0], _ptr(I), C.byref(adapt), _ptr(flags),
+                                                _stream(stream)))

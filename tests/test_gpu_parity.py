@@ -344,3 +344,25 @@ def test_caller_workspace_gives_identical_result():
     rc, a = images.trace_images([cam], [met], [gp], [p], [230e9], workspace=ws)
     rc2, b = images.trace_images([cam], [met], [gp], [p], [230e9])
     assert torch.equal(a[0]["stokes"], b[0]["stokes"])
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_small_workspace_runs_waves_with_identical_result(precision):
+    """A workspace with room for ~1/10 of the rays traces them in ~10 waves (one launch pair
+    each); every ray is computed independently, so the outputs are bit-identical."""
+    cam, met, gp, prim = C1
+    met = S.Metric(**{**met.__dict__, "precision": precision})
+    p = _gpu(prim)
+    nbytes = native.blacklight_workspace_size([cam], [met])
+    ws = torch.empty(nbytes // 10, dtype=torch.uint8, device=DEV)
+    native.blacklight_launch_count(1)
+    rc, a = images.trace_images([cam], [met], [gp], [p], [230e9], workspace=ws, samples=True,
+                                flags=native.BL_TIMING)
+    waves = (native.blacklight_launch_count(0) - 1) // 2
+    assert waves >= 10
+    ms = native.blacklight_last_kernel_ms()
+    assert ms[0] > 0.0 and ms[1] > 0.0
+    rc2, b = images.trace_images([cam], [met], [gp], [p], [230e9], samples=True)
+    assert rc == rc2
+    for key in ("stokes", "status", "steps", "samples"):
+        assert torch.equal(a[0][key], b[0][key]), key
