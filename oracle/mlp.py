@@ -20,9 +20,11 @@ Outputs (u = x^-1/3, X = (sqrt(2) 1e3 / (1.5 x))^1/2, z = 1 / Theta_e):
   K_1/K_2 follows from K_2 = K_0 + (2/z) K_1. (Only the combination sin(theta) Theta^2 of
   pitch angle and temperature enters x; the cosine input is kept so that the model has the
   three inputs of the pitch-angle-resolved coefficients, and the fits make it redundant.)
-Parameter vector (float, 4885 values): W1 [64][4] (column 3 = first-layer bias), W2 [64][64],
-b2 [64], W3 [7][64], b3 [7], output mean [7], output scale [7]; the network predicts
-(o - mean) / scale.
+Parameter vector (float, 4906 values): W1 [64][4] (column 3 = first-layer bias), W2 [64][64],
+b2 [64], W3 [7][64], b3 [7], output offset [7], output scale [7], output trend A [7][3]. The
+model is o = offset + scale * y + A f (f the three mapped inputs), y the network; offset, A and
+scale are fixed before training: the least-squares affine fit of the targets on f and the
+standard deviation of its residual, so that the network learns the non-linear remainder.
 """
 from __future__ import annotations
 
@@ -33,8 +35,9 @@ from . import bessel_kx, coefficients
 N_IN, N_H, N_OUT = 3, 64, 7
 LX_RANGE = (-3.0, 6.0)
 LT_RANGE = (-1.0, 2.0)
-OFF_W1, OFF_W2, OFF_B2, OFF_W3, OFF_B3, OFF_MEAN, OFF_SCALE = 0, 256, 4352, 4416, 4864, 4871, 4878
-N_PARAMS = 4885
+OFF_W1, OFF_W2, OFF_B2, OFF_W3, OFF_B3, OFF_MEAN, OFF_SCALE, OFF_A = (0, 256, 4352, 4416, 4864,
+                                                                     4871, 4878, 4885)
+N_PARAMS = 4906
 
 # CGS constants (CODATA 2018 / IAU nominal), the values the radiation oracle uses
 _E = 4.80320471e-10
@@ -145,7 +148,8 @@ def unpack(p):
     p = np.asarray(p, dtype=np.float64)
     return dict(W1=p[OFF_W1:OFF_W2].reshape(N_H, 4), W2=p[OFF_W2:OFF_B2].reshape(N_H, N_H),
                 b2=p[OFF_B2:OFF_W3], W3=p[OFF_W3:OFF_B3].reshape(N_OUT, N_H),
-                b3=p[OFF_B3:OFF_MEAN], mean=p[OFF_MEAN:OFF_SCALE], scale=p[OFF_SCALE:N_PARAMS])
+                b3=p[OFF_B3:OFF_MEAN], mean=p[OFF_MEAN:OFF_SCALE], scale=p[OFF_SCALE:OFF_A],
+                A=p[OFF_A:N_PARAMS].reshape(N_OUT, 3))
 
 
 def pack(d):
@@ -156,7 +160,8 @@ def pack(d):
     p[OFF_W3:OFF_B3] = np.ravel(d["W3"])
     p[OFF_B3:OFF_MEAN] = d["b3"]
     p[OFF_MEAN:OFF_SCALE] = d["mean"]
-    p[OFF_SCALE:N_PARAMS] = d["scale"]
+    p[OFF_SCALE:OFF_A] = d["scale"]
+    p[OFF_A:N_PARAMS] = np.ravel(d["A"])
     return p
 
 
@@ -182,43 +187,61 @@ def forward(p, F, quant=False):
     return Y, dict(F=Fq, Z1=Z1, H1=H1, Z2=Z2, H2=H2)
 
 
+def trend(p, F):
+    """offset + A f: the affine part of the model."""
+    d = unpack(p)
+    return d["mean"] + np.asarray(F, dtype=np.float64)[..., :3] @ d["A"].T
+
+
 def outputs(p, F, quant=False):
     d = unpack(p)
     Y, _ = forward(p, F, quant)
-    return d["mean"] + d["scale"] * Y
+    return trend(p, F) + d["scale"] * Y
+
+
+def affine_normalisation(F, O):
+    """offset, A and scale from targets O [n][7] at network inputs F [n][4]: least squares of
+    O on (f, 1), scale = root mean square of its residual."""
+    F = np.asarray(F, dtype=np.float64)
+    beta, *_ = np.linalg.lstsq(F, np.asarray(O, dtype=np.float64), rcond=None)
+    R = O - F @ beta
+    return dict(mean=beta[3], A=beta[:3].T, scale=np.sqrt(np.mean(R * R, axis=0)))
 
 
 def loss_and_grad(p, F, O, quant=False, n_total=None):
     """Mean squared error of the normalised outputs against targets O [n][7] (in o units),
     averaged over n_total samples x 7 outputs (default: this batch), and its gradient with
-    respect to the parameter vector (zero for the output mean and scale)."""
+    respect to the parameter vector (zero for the fixed offset, scale and trend)."""
     d = unpack(p)
     q = bf16 if quant else (lambda a: np.asarray(a, dtype=np.float64))
     n = F.shape[0]
     n_total = n if n_total is None else n_total
     Y, c = forward(p, F, quant)
-    T = (np.asarray(O, dtype=np.float64) - d["mean"]) / d["scale"]
+    T = (np.asarray(O, dtype=np.float64) - trend(p, F)) / d["scale"]
     E = Y - T
     loss = float(np.sum(E * E)) / (n_total * N_OUT)
     dY = 2.0 * E / (n_total * N_OUT)
     dYq = q(dY)
-    g = dict(W3=dYq.T @ c["H2"], b3=dY.sum(axis=0))
+    # bias gradients are sums of the same (rounded) errors as the weight gradients: the
+    # products carry a constant-1 operand row for them
+    g = dict(W3=dYq.T @ c["H2"], b3=dYq.sum(axis=0))
     dH2 = dYq @ q(d["W3"])
     dZ2 = dH2 * silu_grad(c["Z2"])
     dZ2q = q(dZ2)
     g["W2"] = dZ2q.T @ c["H1"]
-    g["b2"] = dZ2.sum(axis=0)
+    g["b2"] = dZ2q.sum(axis=0)
     dH1 = dZ2q @ q(d["W2"])
     dZ1 = dH1 * silu_grad(c["Z1"])
     g["W1"] = q(dZ1).T @ c["F"]
     g["mean"] = np.zeros(N_OUT)
     g["scale"] = np.zeros(N_OUT)
+    g["A"] = np.zeros((N_OUT, 3))
     return loss, pack(g)
 
 
 def adam_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
-    """One Adam update (step number t >= 1) of every trained parameter; the output mean and
-    scale are left unchanged. Returns new (p, m, v)."""
+    """One Adam update (step number t >= 1) of every trained parameter; the output offset,
+    scale and trend are left unchanged. Returns new (p, m, v)."""
     p, g, m, v = (np.array(a, dtype=np.float64) for a in (p, g, m, v))
     trained = np.zeros(N_PARAMS, dtype=bool)
     trained[:OFF_MEAN] = True

@@ -61,7 +61,8 @@ def _random_params(seed, scale=0.4):
     rng = np.random.default_rng(seed)
     p = rng.normal(0.0, scale, M.N_PARAMS)
     p[M.OFF_MEAN:M.OFF_SCALE] = rng.normal(0.0, 1.0, 7)
-    p[M.OFF_SCALE:] = rng.uniform(0.5, 2.0, 7)
+    p[M.OFF_SCALE:M.OFF_A] = rng.uniform(0.5, 2.0, 7)
+    p[M.OFF_A:] = rng.normal(0.0, 1.0, 21)
     return p
 
 
@@ -97,7 +98,8 @@ def test_zero_last_layer_blocks_gradient_to_earlier_layers():
     p[M.OFF_W3:M.OFF_B3] = 0.0
     F, Ot = _batch(17, 6)
     d = M.unpack(p)
-    np.testing.assert_array_equal(M.outputs(p, F), np.broadcast_to(d["mean"] + d["scale"] * d["b3"], (17, 7)))
+    np.testing.assert_allclose(M.outputs(p, F), d["mean"] + d["scale"] * d["b3"] + F[:, :3] @ d["A"].T,
+                               rtol=1e-15, atol=1e-15)
     _, g = M.loss_and_grad(p, F, Ot)
     assert np.all(g[M.OFF_W1:M.OFF_W3] == 0.0)
     assert np.any(g[M.OFF_W3:M.OFF_B3] != 0.0) and np.all(g[M.OFF_B3:M.OFF_MEAN] != 0.0)
@@ -110,7 +112,7 @@ def test_least_squares_last_layer_has_zero_gradient():
     F, Ot = _batch(200, 8)
     d = M.unpack(p)
     _, c = M.forward(p, F)
-    T = (Ot - d["mean"]) / d["scale"]
+    T = (Ot - M.trend(p, F)) / d["scale"]
     A = np.hstack([c["H2"], np.ones((200, 1))])
     beta, *_ = np.linalg.lstsq(A, T, rcond=None)
     d["W3"] = beta[:64].T
@@ -140,3 +142,22 @@ def test_quantized_forward_stays_within_bf16_rounding():
     # each product operand carries at most 2^-8 relative rounding; three layers deep
     assert np.max(np.abs(yq - y)) <= 0.05 * (np.max(np.abs(y)) + 1.0)
     assert np.max(np.abs(yq - y)) > 0.0
+
+
+def test_affine_normalisation_reproduces_an_affine_target_exactly():
+    """Targets that are affine in the inputs are taken up entirely by offset + A f (zero
+    residual); a random non-affine remainder is orthogonal to (f, 1) afterwards."""
+    F, _ = _batch(300, 12)
+    rng = np.random.default_rng(13)
+    A = rng.normal(size=(7, 3))
+    c0 = rng.normal(size=7)
+    O = c0 + F[:, :3] @ A.T
+    d = M.affine_normalisation(F, O)
+    np.testing.assert_allclose(d["A"], A, atol=1e-12)
+    np.testing.assert_allclose(d["mean"], c0, atol=1e-12)
+    assert np.all(d["scale"] < 1e-12)
+    O2 = O + np.sin(5 * F[:, :1]) * np.ones((1, 7))
+    d2 = M.affine_normalisation(F, O2)
+    R = O2 - (d2["mean"] + F[:, :3] @ d2["A"].T)
+    np.testing.assert_allclose(F.T @ R, 0.0, atol=1e-9)
+    np.testing.assert_allclose(d2["scale"], np.sqrt(np.mean(R * R, axis=0)), rtol=1e-12)
