@@ -68,6 +68,8 @@ def parse():
                     help="skip the 1024^2 image on the 512x256x256 torus")
     ap.add_argument("--no-adaptive", action="store_true",
                     help="skip the batched adaptive-refinement workload")
+    ap.add_argument("--no-mlp", action="store_true",
+                    help="skip the learned-coefficient line (training + 1024^2 image + FP64 form)")
     return ap.parse_args()
 
 
@@ -325,9 +327,14 @@ def main():
             if code == prec:
                 continue
             other[name] = time_form(torch, native, images, wl, code, device, steps=3, warmup=2)
-    hires = None
+    hires = hires_img = None
     if not args.no_hires and args.case == "full":
-        hires = measure_hires(torch, native, images, prec, device)
+        hires, hires_img = measure_hires(torch, native, images, prec, device,
+                                         keep_image=prec == native.BL_PREC_FAST)
+    mlp = None
+    if not args.no_mlp and args.case == "full":
+        mlp = measure_mlp(torch, native, images, device, hires_img)
+    hires_img = None
     adaptive = None
     if not args.no_adaptive and args.case == "full":
         adaptive = measure_adaptive(torch, native, prec, device)
@@ -357,7 +364,7 @@ def main():
                 "work": {"dp_attempts": attempts, "samples": samples,
                          "rays_not_terminated_normally": status_bad},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "other_forms": other,
-                "hires": hires, "adaptive": adaptive,
+                "hires": hires, "mlp": mlp, "adaptive": adaptive,
                 "gpu_launches": int(launches), "clocks": clk, "return_codes": sorted(set(rcs))}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -397,9 +404,11 @@ def time_form(torch, native, images, wl, code, device, steps, warmup):
             "kernel_ms": {"geodesic": geo / steps, "transfer": tr / steps}}
 
 
-def measure_hires(torch, native, images, code, device, steps=3, warmup=2):
+def measure_hires(torch, native, images, code, device, steps=3, warmup=2, coef_mlp=None,
+                  keep_image=False):
     """The metric's 1024^2 point: one 1024x1024 image (a = 0.94, i = 17 deg, 230 GHz) on the
-    512x256x256 torus (1 GiB of float32), timed like the main workload."""
+    512x256x256 torus (1 GiB of float32), timed like the main workload. coef_mlp selects the
+    learned coefficient model. Returns (line, Stokes image or None)."""
     from paper_2203_15963_gb300 import synth as S
     cam, met, gp, prim = S.workload_inputs("torus512_cam1024", 0.94, 17.0)
     met = S.Metric(**{**met.__dict__, "precision": code})
@@ -410,7 +419,8 @@ def measure_hires(torch, native, images, code, device, steps=3, warmup=2):
     dt = torch.float64 if code == native.BL_PREC_FP64 else torch.float32
     out = images.alloc_outputs(cam.n, dt, device=device)
     for _ in range(warmup):
-        native.blacklight_trace_batch([cam], [met], [gp], [p], [FREQ], [out], workspace=ws)
+        native.blacklight_trace_batch([cam], [met], [gp], [p], [FREQ], [out], workspace=ws,
+                                      coef_mlp=coef_mlp)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -418,7 +428,7 @@ def measure_hires(torch, native, images, code, device, steps=3, warmup=2):
     e0.record()
     for _ in range(steps):
         native.blacklight_trace_batch([cam], [met], [gp], [p], [FREQ], [out], workspace=ws,
-                                      flags=native.BL_TIMING)
+                                      flags=native.BL_TIMING, coef_mlp=coef_mlp)
         g, t = native.blacklight_last_kernel_ms()
         geo += g
         tr += t
@@ -428,10 +438,47 @@ def measure_hires(torch, native, images, code, device, steps=3, warmup=2):
     bad = int(((out["status"] != 1) & (out["status"] != 2)).sum())
     del ws, p
     torch.cuda.empty_cache()
-    return {"workload": "torus512_cam1024", "value": cam.n * cam.n / ms * 1e3, "unit": "rays/s",
+    line = {"workload": "torus512_cam1024", "value": cam.n * cam.n / ms * 1e3, "unit": "rays/s",
             "ms_per_step": ms, "steps": steps,
             "kernel_ms": {"geodesic": geo / steps, "transfer": tr / steps},
             "rays_not_terminated_normally": bad}
+    return line, (out["stokes"] if keep_image else None)
+
+
+def rel_l2(torch, got, want):
+    """per-Stokes ||got - want|| / ||I_want|| of two [4][n][n] images"""
+    g, w = got.double(), want.double()
+    nI = torch.linalg.vector_norm(w[0])
+    return [float(torch.linalg.vector_norm(g[s] - w[s]) / nI) for s in range(4)]
+
+
+def measure_mlp(torch, native, images, device, fast_image):
+    """Learned coefficients at the 1024^2 point: the model trained on the GPU (default recipe),
+    then the image traced with the fused tensor-core transfer (double-float geodesics, FP32
+    transfer), next to the plain FP64 form of the same image: speedup and image error
+    against the FP64 image, and the exact-fit fast form's error for comparison."""
+    from paper_2203_15963_gb300 import coefmodel
+    t0 = time.perf_counter()
+    params, hist = coefmodel.train(device=device)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    final_loss = float(hist[-500:].mean())
+    line, img = measure_hires(torch, native, images, native.BL_PREC_FAST, device, steps=3,
+                              warmup=2, coef_mlp=params, keep_image=True)
+    fp64, img64 = measure_hires(torch, native, images, native.BL_PREC_FP64, device, steps=1,
+                                warmup=1, keep_image=True)
+    line.update({
+        "form": "double-float geodesics, FP32 transfer, learned coefficients (BF16 tensor cores)",
+        "train": {"seconds": train_s, "samples": coefmodel.N_SAMPLES, "batch": coefmodel.BATCH,
+                  "steps": coefmodel.STEPS, "final_mse_normalised": final_loss},
+        "fp64_form": {"value": fp64["value"], "kernel_ms": fp64["kernel_ms"]},
+        "speedup_over_fp64_form": line["value"] / fp64["value"],
+        "image_rel_l2_vs_fp64_form": rel_l2(torch, img, img64),
+        "exact_fast_rel_l2_vs_fp64_form": (rel_l2(torch, fast_image, img64)
+                                           if fast_image is not None else None)})
+    del img, img64, params
+    torch.cuda.empty_cache()
+    return line
 
 
 def measure_adaptive(torch, native, code, device, steps=2, warmup=1):

@@ -80,6 +80,12 @@ typedef struct bl_grid {
     double rho_unit_cgs;    /* code density unit in g / cm^3 */
     double mass_msun;       /* black-hole mass in solar masses (sets the length unit) */
     int32_t interp;         /* 1 = trilinear, 0 = nearest */
+    const float* coef_mlp;  /* NULL: coefficients from the exact fits (Sec. 2.5). Otherwise a
+                               DEVICE parameter vector of the learned coefficient model
+                               (BL_MLP_PARAMS floats, see blacklight_mlp_train), used for
+                               samples inside its domain; all images of one call must pass the
+                               same pointer, and the precision must be BL_PREC_MIXED or
+                               BL_PREC_FAST (FP32 transfer). */
 } bl_grid_t;
 
 /* Outputs. stokes is a DEVICE pointer to [4][n][n] (I, Q, U, V; row j = vertical index
@@ -161,9 +167,10 @@ int blacklight_trace_noalloc(const bl_camera_t* cam, const bl_metric_t* met,
                              const bl_grid_t* grid, double freq_hz, const bl_out_t* out,
                              void* stream, uint32_t flags);
 
-/* Same as blacklight_trace, but grid->prim and out->stokes/status/steps/end_state are HOST
- * pointers: the call copies the grid in, traces, and copies the results out (all
- * stream-ordered, device scratch allocated and freed inside). Always synchronous. */
+/* Same as blacklight_trace, but grid->prim (and grid->coef_mlp if set) and
+ * out->stokes/status/steps/end_state are HOST pointers: the call copies the grid in, traces,
+ * and copies the results out (all stream-ordered, device scratch allocated and freed
+ * inside). Always synchronous. */
 int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const bl_grid_t* grid,
                           double freq_hz, const bl_out_t* out, void* stream);
 
@@ -210,6 +217,67 @@ int blacklight_trace_adaptive(int32_t n_images, const bl_camera_t* cams, const b
  * (at most 2^20 rays each). */
 size_t blacklight_workspace_size(int32_t n_images, const bl_camera_t* cams,
                                  const bl_metric_t* mets);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned coefficient model. The paper evaluates the thermal synchrotron fits of Sec. 2.5
+ * directly; this library can instead evaluate their transcendental parts with a small
+ * perceptron (3 -> 64 -> 64 -> 7, SiLU, BF16 weights and activations on the tensor cores,
+ * FP32 accumulation), trained on the GPU on samples of the exact fits, with the exact fits
+ * kept for samples outside its domain.
+ *   inputs  (log10 x, log10 Theta_e, |cos theta_B|), x = nu / nu_c, nu_c = 1.5 nu_B
+ *           sin(theta_B) Theta_e^2, on the domain [-3, 6] x [-1, 2] x [0, 1];
+ *   outputs o1..o7: ln of the I, Q, V emissivity shape prefactors (I_S(x) = exp(o_S -
+ *           1.8899 x^1/3)), the Faraday conversion and rotation shapes f_m, g_m, ln(e^z K_2(z))
+ *           and ln(K_0(z) / K_2(z)) with z = 1 / Theta_e. The remaining factors (n_e, nu, B,
+ *           the angle factors, the Planck function) are exact.
+ * Parameters: float [BL_MLP_PARAMS] = W1 [64][4] (column 3 = first-layer bias), W2 [64][64],
+ * b2 [64], W3 [7][64], b3 [7], output offset [7], output scale [7], output trend A [7][3].
+ * The model is o = offset + scale * y + A f, y the network output and f the three inputs
+ * mapped linearly to [-1, 1]; offset, A and scale are fixed before training. All arrays are DEVICE pointers unless stated; calls are stream-ordered
+ * and synchronise `stream` before returning; BL_ECUDA if a tensor-core wait ran out (never
+ * expected; the kernels stop instead of waiting forever).
+ * --------------------------------------------------------------------------------------- */
+#define BL_MLP_PARAMS 4906
+
+/* Glorot-uniform weights, zero biases, offset 0, scale 1, A 0, from the SplitMix64 stream
+ * `seed`. */
+int blacklight_mlp_init(float* params, uint64_t seed, void* stream);
+/* n samples uniform on the input domain (SplitMix64 stream `seed`) into inputs [n][3] and
+ * the exact learned quantities (FP64 fits, stored as float) into targets [n][7]. */
+int blacklight_mlp_dataset(int64_t n, uint64_t seed, float* inputs, float* targets,
+                           void* stream);
+/* Exact learned quantities targets [n][7] of inputs [n][3]. */
+int blacklight_mlp_targets(int64_t n, const float* inputs, float* targets, void* stream);
+/* Set offset and A of params to the least-squares affine fit of targets [n][7] on the mapped
+ * inputs [n][3], and scale to the root mean square of its residual. */
+int blacklight_mlp_normalise(int64_t n, const float* inputs, const float* targets, float* params,
+                             void* stream);
+
+typedef struct bl_mlp_train {
+    uint32_t size;
+    int64_t n;               /* training samples (>= batch) */
+    const float* inputs;     /* DEVICE [n][3] */
+    const float* targets;    /* DEVICE [n][7] */
+    int32_t batch;           /* samples per step: a multiple of 128 */
+    int64_t steps;           /* Adam steps; step t uses samples t*batch .. (mod n) */
+    double lr_start, lr_end; /* learning rate, geometric from lr_start to lr_end */
+    double beta1, beta2, eps;/* Adam (Kingma & Ba 2015) */
+} bl_mlp_train_t;
+/* Train params in place (mean squared error of the normalised outputs). loss_history:
+ * optional DEVICE float [steps] receiving each step's mean squared error. */
+int blacklight_mlp_train(const bl_mlp_train_t* cfg, float* params, float* loss_history,
+                         void* stream);
+/* Gradient of the mean squared error over the n samples into grad [BL_MLP_PARAMS] (zero for
+ * offset, scale and A) and the error itself into *loss (HOST float). */
+int blacklight_mlp_grad(const float* params, int64_t n, const float* inputs, const float* targets,
+                        float* grad, float* loss, void* stream);
+/* Model outputs o [n][7] (denormalised) for inputs [n][3]. */
+int blacklight_mlp_forward(const float* params, int64_t n, const float* inputs, float* outputs,
+                           void* stream);
+/* Like blacklight_coefficients (precision FP32) with the learned model inside its domain and
+ * the exact fits outside it. in [n][5], out [n][8], float64. */
+int blacklight_mlp_coefficients(const float* params, int64_t n, const double* in, double* out,
+                                void* stream);
 
 /* Component entry points (same device functions as the traced path), for checking each
  * stage on its own. All arrays are DEVICE pointers; n elements; precision selects the FP64

@@ -221,6 +221,7 @@ struct DevInfo {
     int sms = 0;
     int geo_blocks[3] = {0, 0, 0};  // per SM, indexed by precision: [fp64, mixed, fast]
     int tr_blocks[3] = {0, 0, 0};
+    int tr_mlp_blocks = 0;
 };
 
 int dev_info(DevInfo& out) {
@@ -239,6 +240,8 @@ int dev_info(DevInfo& out) {
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[0], bl::transfer_kernel<double, double>, 128, 0));
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[1], bl::transfer_kernel<float, float>, 128, 0));
         di.tr_blocks[2] = di.tr_blocks[1];
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_blocks, bl::transfer_mlp_kernel<float>, 128, 0));
+        if (di.tr_mlp_blocks < 1) di.tr_mlp_blocks = 1;
         for (int i = 0; i < 3; ++i) {
             if (di.geo_blocks[i] < 1) di.geo_blocks[i] = 1;
             if (di.tr_blocks[i] < 1) di.tr_blocks[i] = 1;
@@ -251,7 +254,8 @@ int dev_info(DevInfo& out) {
 // Launch the camera-frame kernel, then the geodesic and (optionally) transfer kernels once per
 // wave of rays, on prepared workspace. Waves run in stream order and reuse the workspace.
 int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* ws,
-               const Layout& L, int precision, bool transfer, cudaStream_t st, bool timing) {
+               const Layout& L, int precision, bool transfer, cudaStream_t st, bool timing,
+               const float* mlp = nullptr) {
     DevInfo di;
     int rc = dev_info(di);
     if (rc) return rc;
@@ -301,7 +305,10 @@ int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* 
         BL_CUDA(cudaGetLastError());
         if (timing) BL_CUDA(cudaEventRecord(g_ev[2 * w + 1], st));
         if (transfer) {
-            if (precision != BL_PREC_FP64) {
+            if (mlp) {
+                bl::transfer_mlp_kernel<float><<<(unsigned)(di.sms * di.tr_mlp_blocks), 128, 0, st>>>(
+                    d_desc, n_images, b, e, hdr, (const float*)(ws + L.pool), chunks, mlp, ctr);
+            } else if (precision != BL_PREC_FP64) {
                 bl::transfer_kernel<float, float><<<tr_grid, 128, 0, st>>>(
                     d_desc, n_images, b, e, hdr, (const float*)(ws + L.pool), chunks, ctr);
             } else {
@@ -319,11 +326,29 @@ int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* 
 
 int finish(char* ws, const Layout& L, cudaStream_t st, bool sync) {
     if (!sync) return 0;
-    unsigned long long bad = 0;
-    BL_CUDA(cudaMemcpyAsync(&bad, &((bl::Counters*)(ws + L.counters))->bad_rays, sizeof(bad),
-                            cudaMemcpyDeviceToHost, st));
+    bl::Counters c{};
+    BL_CUDA(cudaMemcpyAsync(&c, ws + L.counters, sizeof(c), cudaMemcpyDeviceToHost, st));
     BL_CUDA(cudaStreamSynchronize(st));
-    return bad ? BL_WRAYS : BL_OK;
+    if (c.mlp_timeouts)
+        return fail(BL_ECUDA, "%llu CTAs stopped: tensor-core wait ran out", c.mlp_timeouts);
+    return c.bad_rays ? BL_WRAYS : BL_OK;
+}
+
+// The learned-model pointer shared by all images (nullptr: exact fits), checked.
+int common_mlp(int32_t n_images, const bl_grid_t* grids, int precision, const float** out) {
+    *out = nullptr;
+    if (!grids) return 0;
+    const float* p = grids[0].coef_mlp;
+    for (int q = 1; q < n_images; ++q)
+        if (grids[q].coef_mlp != p) return fail(BL_EINVAL, "grids[%d].coef_mlp differs from grids[0]", q);
+    if (p && precision == BL_PREC_FP64)
+        return fail(BL_EUNSUPPORTED, "coef_mlp needs FP32 transfer (BL_PREC_MIXED or BL_PREC_FAST)");
+    if (p) {
+        int rc = device_pointer(p, "grids[].coef_mlp");
+        if (rc) return rc;
+    }
+    *out = p;
+    return 0;
 }
 
 int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
@@ -391,7 +416,13 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
         }
         own = true;
     }
-    int rc = launch_all(n_images, descs, ws, L, precision, transfer, st, (flags & BL_TIMING) != 0);
+    const float* mlp = nullptr;
+    int rc = transfer ? common_mlp(n_images, grids, precision, &mlp) : 0;
+    if (rc) {
+        if (own) cudaFreeAsync(ws, st);
+        return rc;
+    }
+    rc = launch_all(n_images, descs, ws, L, precision, transfer, st, (flags & BL_TIMING) != 0, mlp);
     if (rc == 0) rc = finish(ws, L, st, !(flags & BL_ASYNC));
     if (own) {
         cudaError_t e = cudaFreeAsync(ws, st);
@@ -451,7 +482,8 @@ int check_adapt(const bl_adapt_t* ad, const bl_camera_t* cams, int32_t n_images)
 // Adaptive tracing driven level by level from the host (refinement decisions are read back).
 int trace_adaptive_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
                         const bl_grid_t* grids, const double* freqs, const bl_adapt_t* ad,
-                        const bl_out_t* outs, int32_t* level_rays, cudaStream_t st) {
+                        const bl_out_t* outs, int32_t* level_rays, cudaStream_t st,
+                        const float* mlp) {
     const int B = ad->block, maxL = ad->max_level;
     const int precision = mets[0].precision;
     const size_t vsize = precision == BL_PREC_FP64 ? sizeof(double) : sizeof(float);
@@ -522,10 +554,12 @@ int trace_adaptive_impl(int32_t n_images, const bl_camera_t* cams, const bl_metr
         }
         Layout Ly = make_layout_rays((int32_t)descs.size(), rays, precision);
         if ((rc = grow((void**)&ws, ws_bytes, Ly.total))) break;
-        if ((rc = launch_all((int32_t)descs.size(), descs, ws, Ly, precision, true, st, false))) break;
-        unsigned long long bad = 0;
+        if ((rc = launch_all((int32_t)descs.size(), descs, ws, Ly, precision, true, st, false, mlp))) break;
+        unsigned long long bad = 0, tmo = 0;
         BL_CUDA(cudaMemcpyAsync(&bad, &((bl::Counters*)(ws + Ly.counters))->bad_rays, sizeof(bad),
                                 cudaMemcpyDeviceToHost, st));
+        BL_CUDA(cudaMemcpyAsync(&tmo, &((bl::Counters*)(ws + Ly.counters))->mlp_timeouts,
+                                sizeof(tmo), cudaMemcpyDeviceToHost, st));
         // composite: paint this level into each image's finest-resolution output
         const int s = 1 << (maxL - L);
         for (size_t k = 0; k < descs.size(); ++k) {
@@ -553,6 +587,7 @@ int trace_adaptive_impl(int32_t n_images, const bl_camera_t* cams, const bl_metr
         if (L == maxL) {
             BL_CUDA(cudaStreamSynchronize(st));
             bad_total += bad;
+            if (tmo) rc = fail(BL_ECUDA, "tensor-core wait ran out in %llu CTAs", tmo);
             break;
         }
         // refinement decisions for every block of this level
@@ -573,6 +608,7 @@ int trace_adaptive_impl(int32_t n_images, const bl_camera_t* cams, const bl_metr
         BL_CUDA(cudaMemcpyAsync(hflags.data(), dflags, nblk, cudaMemcpyDeviceToHost, st));
         BL_CUDA(cudaStreamSynchronize(st));
         bad_total += bad;
+        if (tmo) { rc = fail(BL_ECUDA, "tensor-core wait ran out in %llu CTAs", tmo); break; }
         // children of refined blocks, in parent order: (2bx+dx, 2by+dy), dy then dx
         for (int q = 0; q < n_images; ++q) {
             std::vector<int32_t> next;
@@ -628,8 +664,10 @@ int blacklight_trace_adaptive(int32_t n_images, const bl_camera_t* cams, const b
     }
     int rc = check_adapt(adapt, cams, n_images);
     if (rc) return rc;
+    const float* mlp = nullptr;
+    if ((rc = common_mlp(n_images, grids, precision, &mlp))) return rc;
     return trace_adaptive_impl(n_images, cams, mets, grids, freqs_hz, adapt, outs, level_rays,
-                               (cudaStream_t)stream);
+                               (cudaStream_t)stream, mlp);
 }
 
 int blacklight_adapt_flags(int64_t n_blocks, const double* I, const bl_adapt_t* adapt,
@@ -717,7 +755,8 @@ int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const 
     char* dev = nullptr;
     const size_t off_s = align_up(gbytes), off_st = off_s + align_up(sbytes),
                  off_sp = off_st + align_up(npix * 4), off_e = off_sp + align_up(npix * 4),
-                 total = off_e + align_up(npix * 8 * sizeof(double));
+                 off_m = off_e + align_up(npix * 8 * sizeof(double)),
+                 total = off_m + (grid->coef_mlp ? align_up(sizeof(float) * BL_MLP_PARAMS) : 0);
     cudaError_t e = cudaMallocAsync((void**)&dev, total, st);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e)); }
     bl_grid_t g = *grid;
@@ -731,6 +770,12 @@ int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const 
     rc = 0;
     e = cudaMemcpyAsync(dev, grid->prim, gbytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "copy grid to device");
+    if (!rc && grid->coef_mlp) {
+        g.coef_mlp = (const float*)(dev + off_m);
+        e = cudaMemcpyAsync(dev + off_m, grid->coef_mlp, sizeof(float) * BL_MLP_PARAMS,
+                            cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copy coefficient model to device");
+    }
     if (!rc) rc = trace_impl(1, cam, met, &g, &freq_hz, &o, nullptr, 0, stream, BL_ASYNC, true);
     if (rc >= 0) {
         e = cudaMemcpyAsync(out->stokes, o.stokes, sbytes, cudaMemcpyDeviceToHost, st);
@@ -746,6 +791,239 @@ int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const 
     cudaError_t se = cudaStreamSynchronize(st);
     if (rc == 0 && se != cudaSuccess) rc = cuda_fail(se, "cudaStreamSynchronize");
     return rc;
+}
+
+// ---------------------------------------------------------------------------------------
+// Learned coefficient model
+// ---------------------------------------------------------------------------------------
+static_assert(BL_MLP_PARAMS == bl::mlp::kParams, "parameter count");
+}  // extern "C"
+
+namespace {
+
+// Run `launch(err)` with a zeroed device error flag; BL_ECUDA if a kernel reported a timeout.
+template <class F>
+int with_tc_flag(cudaStream_t st, F launch) {
+    int* err = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&err, sizeof(int), st);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e)); }
+    int rc = 0;
+    e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync");
+    if (!rc) rc = launch(err);
+    int h = 0;
+    if (!rc) {
+        e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "read error flag");
+    }
+    cudaFreeAsync(err, st);
+    e = cudaStreamSynchronize(st);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+    if (!rc && h) rc = fail(BL_ECUDA, "tensor-core wait ran out");
+    return rc;
+}
+
+int mlp_grid_size() {
+    DevInfo di;
+    if (dev_info(di)) return 0;
+    return di.sms * 4;
+}
+
+int mlp_train_attr() {
+    static std::mutex mu;
+    static std::vector<bool> done;
+    int dev = 0;
+    BL_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)done.size() <= dev) done.resize(dev + 1, false);
+    if (!done[dev]) {
+        BL_CUDA(cudaFuncSetAttribute(bl::mlp::train_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bl::mlp::kTrainSmem));
+        done[dev] = true;
+    }
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int blacklight_mlp_init(float* params, uint64_t seed, void* stream) {
+    g_detail[0] = 0;
+    int rc = device_pointer(params, "params");
+    if (rc) return rc;
+    bl::mlp::init_kernel<<<(BL_MLP_PARAMS + 255) / 256, 256, 0, (cudaStream_t)stream>>>(params, seed);
+    ++g_launches;
+    BL_CUDA(cudaGetLastError());
+    BL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return 0;
+}
+
+int blacklight_mlp_dataset(int64_t n, uint64_t seed, float* inputs, float* targets, void* stream) {
+    g_detail[0] = 0;
+    if (n < 0) return fail(BL_EINVAL, "n < 0");
+    if (n == 0) return 0;
+    int rc = device_pointer(inputs, "inputs");
+    if (!rc) rc = device_pointer(targets, "targets");
+    if (rc) return rc;
+    bl::mlp::dataset_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, seed, inputs, targets);
+    ++g_launches;
+    BL_CUDA(cudaGetLastError());
+    BL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return 0;
+}
+
+int blacklight_mlp_targets(int64_t n, const float* inputs, float* targets, void* stream) {
+    g_detail[0] = 0;
+    if (n < 0) return fail(BL_EINVAL, "n < 0");
+    if (n == 0) return 0;
+    int rc = device_pointer(inputs, "inputs");
+    if (!rc) rc = device_pointer(targets, "targets");
+    if (rc) return rc;
+    bl::mlp::targets_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, inputs, targets);
+    ++g_launches;
+    BL_CUDA(cudaGetLastError());
+    BL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return 0;
+}
+
+int blacklight_mlp_normalise(int64_t n, const float* inputs, const float* targets, float* params,
+                             void* stream) {
+    g_detail[0] = 0;
+    if (n < 4) return fail(BL_EINVAL, "n < 4");
+    int rc = device_pointer(inputs, "inputs");
+    if (!rc) rc = device_pointer(targets, "targets");
+    if (!rc) rc = device_pointer(params, "params");
+    if (rc) return rc;
+    bl::mlp::normalise_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(n, inputs, targets, params);
+    ++g_launches;
+    BL_CUDA(cudaGetLastError());
+    BL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return 0;
+}
+
+int blacklight_mlp_grad(const float* params, int64_t n, const float* inputs, const float* targets,
+                        float* grad, float* loss, void* stream) {
+    g_detail[0] = 0;
+    if (n < 1 || !loss) return fail(BL_EINVAL, "n < 1 or loss is NULL");
+    int rc = device_pointer(params, "params");
+    if (!rc) rc = device_pointer(inputs, "inputs");
+    if (!rc) rc = device_pointer(targets, "targets");
+    if (!rc) rc = device_pointer(grad, "grad");
+    if (!rc) rc = mlp_train_attr();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    float* dloss = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&dloss, sizeof(float), st);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e)); }
+    rc = with_tc_flag(st, [&](int* err) -> int {
+        BL_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * BL_MLP_PARAMS, st));
+        BL_CUDA(cudaMemsetAsync(dloss, 0, sizeof(float), st));
+        bl::mlp::train_kernel<<<(unsigned)((n + 127) / 128), 128, bl::mlp::kTrainSmem, st>>>(
+            params, n, inputs, targets, 0, n, (double)n, grad, dloss, err);
+        ++g_launches;
+        BL_CUDA(cudaGetLastError());
+        float h = 0.0f;
+        BL_CUDA(cudaMemcpyAsync(&h, dloss, sizeof(float), cudaMemcpyDeviceToHost, st));
+        BL_CUDA(cudaStreamSynchronize(st));
+        *loss = (float)(h / (7.0 * (double)n));
+        return 0;
+    });
+    cudaFreeAsync(dloss, st);
+    return rc;
+}
+
+int blacklight_mlp_train(const bl_mlp_train_t* cfg, float* params, float* loss_history,
+                         void* stream) {
+    g_detail[0] = 0;
+    if (!cfg || cfg->size != sizeof(bl_mlp_train_t)) return fail(BL_EINVAL, "cfg.size mismatch");
+    if (cfg->batch < 128 || cfg->batch % 128 || cfg->n < cfg->batch || cfg->steps < 0)
+        return fail(BL_EINVAL, "need batch a positive multiple of 128, n >= batch, steps >= 0");
+    if (!(cfg->lr_start > 0.0) || !(cfg->lr_end > 0.0) || !(cfg->beta1 >= 0.0 && cfg->beta1 < 1.0) ||
+        !(cfg->beta2 >= 0.0 && cfg->beta2 < 1.0) || !(cfg->eps > 0.0))
+        return fail(BL_EINVAL, "learning rates and eps must be > 0, 0 <= beta < 1");
+    int rc = device_pointer(params, "params");
+    if (!rc) rc = device_pointer(cfg->inputs, "cfg.inputs");
+    if (!rc) rc = device_pointer(cfg->targets, "cfg.targets");
+    if (!rc && loss_history) rc = device_pointer(loss_history, "loss_history");
+    if (!rc) rc = mlp_train_attr();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    float* buf = nullptr;    // grad, m, v [BL_MLP_PARAMS] each, loss
+    const size_t bytes = sizeof(float) * (3 * (size_t)BL_MLP_PARAMS + 1);
+    cudaError_t e = cudaMallocAsync((void**)&buf, bytes, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e)); }
+    float *grad = buf, *m = buf + BL_MLP_PARAMS, *v = buf + 2 * BL_MLP_PARAMS, *loss = buf + 3 * BL_MLP_PARAMS;
+    rc = with_tc_flag(st, [&](int* err) -> int {
+        BL_CUDA(cudaMemsetAsync(buf, 0, bytes, st));
+        const unsigned blocks = (unsigned)(cfg->batch / 128);
+        const double b1 = cfg->beta1, b2 = cfg->beta2;
+        double p1 = 1.0, p2 = 1.0;
+        for (int64_t t = 0; t < cfg->steps; ++t) {
+            const int64_t first = (int64_t)((t * (int64_t)cfg->batch) % cfg->n);
+            bl::mlp::train_kernel<<<blocks, 128, bl::mlp::kTrainSmem, st>>>(
+                params, cfg->n, cfg->inputs, cfg->targets, first, cfg->batch, (double)cfg->batch,
+                grad, loss, err);
+            const double frac = cfg->steps > 1 ? (double)t / (double)(cfg->steps - 1) : 0.0;
+            const double lr = cfg->lr_start * pow(cfg->lr_end / cfg->lr_start, frac);
+            p1 *= b1;
+            p2 *= b2;
+            bl::mlp::adam_kernel<<<(bl::mlp::kOffMean + 255) / 256, 256, 0, st>>>(
+                params, grad, m, v, (float)lr, (float)b1, (float)b2, (float)cfg->eps,
+                (float)(1.0 - p1), (float)(1.0 - p2), loss, loss_history ? loss_history + t : nullptr,
+                (float)(1.0 / (7.0 * cfg->batch)));
+            g_launches += 2;
+            BL_CUDA(cudaGetLastError());
+        }
+        return 0;
+    });
+    cudaFreeAsync(buf, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (!rc && se != cudaSuccess) rc = cuda_fail(se, "cudaStreamSynchronize");
+    return rc;
+}
+
+int blacklight_mlp_forward(const float* params, int64_t n, const float* inputs, float* outputs,
+                           void* stream) {
+    g_detail[0] = 0;
+    if (n < 0) return fail(BL_EINVAL, "n < 0");
+    if (n == 0) return 0;
+    int rc = device_pointer(params, "params");
+    if (!rc) rc = device_pointer(inputs, "inputs");
+    if (!rc) rc = device_pointer(outputs, "outputs");
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t tiles = (n + 127) / 128;
+    const int g = mlp_grid_size();
+    const unsigned grid = (unsigned)(tiles < g ? tiles : g);
+    return with_tc_flag(st, [&](int* err) -> int {
+        bl::mlp::forward_kernel<<<grid, 128, 0, st>>>(params, n, inputs, outputs, err);
+        ++g_launches;
+        BL_CUDA(cudaGetLastError());
+        return 0;
+    });
+}
+
+int blacklight_mlp_coefficients(const float* params, int64_t n, const double* in, double* out,
+                                void* stream) {
+    g_detail[0] = 0;
+    if (n < 0) return fail(BL_EINVAL, "n < 0");
+    if (n == 0) return 0;
+    int rc = device_pointer(params, "params");
+    if (!rc) rc = device_pointer(in, "in");
+    if (!rc) rc = device_pointer(out, "out");
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t tiles = (n + 127) / 128;
+    const int g = mlp_grid_size();
+    const unsigned grid = (unsigned)(tiles < g ? tiles : g);
+    return with_tc_flag(st, [&](int* err) -> int {
+        bl::mlp::coefficients_kernel<<<grid, 128, 0, st>>>(params, n, in, out, err);
+        ++g_launches;
+        BL_CUDA(cudaGetLastError());
+        return 0;
+    });
 }
 
 int blacklight_coefficients(int64_t n, const double* in, double* out, int32_t precision,

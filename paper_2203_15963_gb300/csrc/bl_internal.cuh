@@ -78,6 +78,7 @@ struct Counters {
     unsigned long long next_ray_tr;
     unsigned long long pool_next;
     unsigned long long bad_rays;
+    unsigned long long mlp_timeouts;   // CTAs whose tensor-core wait ran out (never expected)
 };
 
 }  // namespace bl

@@ -6,6 +6,7 @@
 #include "bl_df64.cuh"
 #include "bl_internal.cuh"
 #include "bl_math.cuh"
+#include "bl_mlp.cuh"
 #include "../../include/blacklight.h"
 
 namespace bl {
@@ -1174,6 +1175,171 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
             active = false;
         }
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// Transfer with the learned coefficient model (FP32). The same per-sample work as
+// transfer_kernel, but the loop runs in lockstep across the CTA: every iteration each of the
+// 128 threads contributes one row (its sample's model inputs, or a masked row) to a
+// 128-sample tensor-core tile of the perceptron, so the coefficient evaluation of the whole
+// CTA is three chained MMAs. Samples outside the model's domain use the exact fits.
+// ---------------------------------------------------------------------------------------
+template <class R>
+__global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __restrict__ imgs,
+                                                           int n_images, int64_t ray_begin,
+                                                           int64_t ray_end,
+                                                           const RayHdr* __restrict__ hdr,
+                                                           const R* __restrict__ pool,
+                                                           const int32_t* __restrict__ chunks,
+                                                           const float* __restrict__ mlp_params,
+                                                           Counters* ctr) {
+    using T = float;
+    __shared__ mlp::FwdSmem S;
+    mlp::fwd_init(S, mlp_params);
+    uint32_t phase = 0;
+    bool tc_ok = true;
+    const int64_t total_rays = ray_end - ray_begin;
+    int64_t wray = 0;
+    bool active = false;
+    int64_t ray = 0, opix = 0;
+    int q = 0, pi = 0, pj = 0;
+    int32_t idx = 0;
+    Coh<T> N;
+    bool started = false;
+    T prev[kRecVals];
+    R nxt[RecStride<R>::v];
+    T kt = T(0), a = T(0), m = T(0), nu_norm = T(0);
+    bool flat = false;
+
+    bool exhausted = false;
+    while (tc_ok) {
+        const bool need = !active && !exhausted;
+        const unsigned long long got = warp_refill(&ctr->next_ray_tr, need);
+        if (need) {
+            if ((int64_t)got >= total_rays) exhausted = true;
+            else { wray = (int64_t)got; ray = ray_begin + wray; }
+        }
+        bool work = active || (need && !exhausted);
+        if (!__syncthreads_or(work)) break;
+        if (work && !active) {
+            q = find_image(imgs, n_images, ray);
+            const ImageDesc& im = imgs[q];
+            opix = ray_pixel(im, ray - im.ray_offset, pi, pj);
+            const RayHdr hd = hdr[wray];
+            if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) {
+                const int64_t npix = im.n_rays;
+                const double val = hd.status == BL_RAY_OVERFLOW ? nan("") : 0.0;
+                for (int c = 0; c < 4; ++c) {
+                    if (im.dtype == 0) ((double*)im.stokes)[c * npix + opix] = val;
+                    else ((float*)im.stokes)[c * npix + opix] = (float)val;
+                }
+                work = false;
+            } else {
+                idx = hd.nrec - 1;
+                load_record<R>(record_ptr(pool, chunks, wray, idx), nxt);
+                kt = (T)hd.kt;
+                nu_norm = (T)(hd.nnorm * im.freq);
+                a = ic<T>(im, kcSpin);
+                m = ic<T>(im, kcMass);
+                flat = im.flat != 0;
+#pragma unroll
+                for (int c = 0; c < 10; ++c) N.re[c] = T(0);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) N.im[c] = T(0);
+                started = false;
+                active = true;
+            }
+        }
+        const ImageDesc& im = imgs[q];
+        // ---- phase A: transport to this sample, plasma state
+        T cur[kRecVals];
+        bool samp = false;
+        KSGeom<T> G;
+        Plasma<T> P;
+        T kl[4], ku[4], kdu = T(0), nu_fl = T(0), cth = T(0);
+        if (work) {
+#pragma unroll
+            for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
+            if (idx > 0) load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
+            if (started) {
+                T A0[4][4], A1[4][4];
+                const T kp[4] = {kt, prev[3], prev[4], prev[5]};
+                const T kn[4] = {kt, prev[9], prev[10], prev[11]};
+                transport_matrix<T>(prev, kp, a, m, flat, A0);
+                transport_matrix<T>(prev + 6, kn, a, m, flat, A1);
+                coh_pc_step(N, A0, A1, T(0.5) * (prev[12] + cur[12]));
+            }
+            const T xs[3] = {cur[0], cur[1], cur[2]};
+            ks_geom<T>(xs[0], xs[1], xs[2], a, m, flat, false, G);
+            samp = plasma_at<T>(im, xs, G, P);
+            if (samp) {
+                kl[0] = kt; kl[1] = cur[3]; kl[2] = cur[4]; kl[3] = cur[5];
+                raise4(G, kl, ku);
+                kdu = kl[0] * P.u[0] + kl[1] * P.u[1] + kl[2] * P.u[2] + kl[3] * P.u[3];
+                const T kdb = kl[0] * P.b[0] + kl[1] * P.b[1] + kl[2] * P.b[2] + kl[3] * P.b[3];
+                nu_fl = nu_norm * (-kdu);
+                cth = kdb / ((-kdu) * sqrt(P.bsq));
+                cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
+            }
+        }
+        // ---- coefficients: one tensor-core tile for the CTA
+        const mlp::ModelIn mi = mlp::model_inputs(samp ? P.th : 0.0f, samp ? P.bg : 0.0f,
+                                                  samp ? nu_fl : 1.0f, samp ? cth : 0.0f);
+        const bool use = samp && mi.ok && P.ne > T(0);
+        float o[7];
+        tc_ok = mlp::fwd_tile(S, phase, mi.f, use, o);
+        if (!tc_ok) break;
+        // ---- phase B: Stokes step at this sample
+        if (samp) {
+            T co[8];
+            if (use) mlp::coefficients_from(o, P.ne, P.th, P.bg, nu_fl, cth, co);
+            else synchrotron_coefficients<T>(P.ne, P.th, P.bg, nu_fl, cth, co);
+            const T g = ic<T>(im, kcFreq) / nu_fl;
+            const T path = ic<T>(im, kcLen) * (-kdu);
+            const T eg = g * g * g * path;
+            const T coef[8] = {co[0] * eg, co[1] * eg, co[2] * eg, co[3] * path,
+                               co[4] * path, co[5] * path, co[6] * path, co[7] * path};
+            T e1[4], e2[4], e1l[4], e2l[4];
+            fluid_basis<T>(G, P, kl, ku, e1, e2, e1l, e2l);
+            T s0[4], s1[4];
+            coh_to_stokes(N, e1l, e2l, s0);
+            stokes_step<T>(coef, s0, cur[12], s1);
+            stokes_to_coh(e1, e2, s1, N);
+            started = true;
+        }
+        if (!work) continue;
+#pragma unroll
+        for (int c = 0; c < kRecVals; ++c) prev[c] = cur[c];
+        --idx;
+        if (idx < 0) {
+            if (started) {
+                T A0[4][4], A1[4][4];
+                const T kp[4] = {kt, prev[3], prev[4], prev[5]};
+                const T kn[4] = {kt, prev[9], prev[10], prev[11]};
+                transport_matrix<T>(prev, kp, a, m, flat, A0);
+                transport_matrix<T>(prev + 6, kn, a, m, flat, A1);
+                coh_pc_step(N, A0, A1, T(0.5) * prev[12]);
+            }
+            KSGeom<T> Gc;
+            ks_geom<T>(prev[6], prev[7], prev[8], a, m, flat, false, Gc);
+            T hv[4], vv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { hv[c] = im.f_hh[c]; vv[c] = im.f_vv[c]; }
+            T hl[4], vl[4];
+            lower4(Gc, hv, hl);
+            lower4(Gc, vv, vl);
+            T st[4];
+            coh_to_stokes(N, hl, vl, st);
+            const int64_t npix = im.n_rays;
+            for (int c = 0; c < 4; ++c) {
+                if (im.dtype == 0) ((double*)im.stokes)[c * npix + opix] = (double)st[c];
+                else ((float*)im.stokes)[c * npix + opix] = (float)st[c];
+            }
+            active = false;
+        }
+    }
+    if (!tc_ok && threadIdx.x == 0) atomicAdd(&ctr->mlp_timeouts, 1ull);
+    mlp::fwd_finish(S, phase, tc_ok);
 }
 
 // ---------------------------------------------------------------------------------------

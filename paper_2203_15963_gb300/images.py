@@ -21,7 +21,7 @@ def alloc_outputs(n: int, dtype=torch.float64, device="cuda", status=True, steps
 
 
 def trace_images(cams, mets, gps, prims, freqs, dtype=None, end_state=False, workspace=None,
-                 flags=0, samples=False, outs=None):
+                 flags=0, samples=False, outs=None, coef_mlp=None):
     """Trace a batch of images in one launch pair; returns (rc, list of output dicts)."""
     if outs is None:
         outs = []
@@ -29,5 +29,5 @@ def trace_images(cams, mets, gps, prims, freqs, dtype=None, end_state=False, wor
             dt = dtype or (torch.float64 if met.precision == native.BL_PREC_FP64 else torch.float32)
             outs.append(alloc_outputs(cam.n, dt, end_state=end_state, samples=samples))
     rc = native.blacklight_trace_batch(cams, mets, gps, prims, freqs, outs, workspace=workspace,
-                                       flags=flags)
+                                       flags=flags, coef_mlp=coef_mlp)
     return rc, outs

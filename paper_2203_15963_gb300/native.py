@@ -65,7 +65,17 @@ class Grid(C.Structure):
                 ("r_max", C.c_double), ("gamma_ad", C.c_double), ("r_high", C.c_double),
                 ("r_low", C.c_double), ("mu", C.c_double), ("ne_over_ni", C.c_double),
                 ("sigma_cut", C.c_double), ("rho_unit_cgs", C.c_double),
-                ("mass_msun", C.c_double), ("interp", C.c_int32)]
+                ("mass_msun", C.c_double), ("interp", C.c_int32), ("coef_mlp", C.c_void_p)]
+
+
+class MlpTrain(C.Structure):
+    _fields_ = [("size", C.c_uint32), ("n", C.c_int64), ("inputs", C.c_void_p),
+                ("targets", C.c_void_p), ("batch", C.c_int32), ("steps", C.c_int64),
+                ("lr_start", C.c_double), ("lr_end", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double)]
+
+
+MLP_PARAMS = 4906
 
 
 class Adapt(C.Structure):
@@ -116,6 +126,14 @@ def load():
     L.blacklight_coefficients.argtypes = [C.c_int64, P, P, C.c_int32, P]
     L.blacklight_stokes_step.argtypes = [C.c_int64, P, P, P, P, C.c_int32, P]
     L.blacklight_bessel_k.argtypes = [C.c_int64, P, P, C.c_int32, P]
+    L.blacklight_mlp_init.argtypes = [P, C.c_uint64, P]
+    L.blacklight_mlp_dataset.argtypes = [C.c_int64, C.c_uint64, P, P, P]
+    L.blacklight_mlp_targets.argtypes = [C.c_int64, P, P, P]
+    L.blacklight_mlp_normalise.argtypes = [C.c_int64, P, P, P, P]
+    L.blacklight_mlp_train.argtypes = [C.POINTER(MlpTrain), P, P, P]
+    L.blacklight_mlp_grad.argtypes = [P, C.c_int64, P, P, P, C.POINTER(C.c_float), P]
+    L.blacklight_mlp_forward.argtypes = [P, C.c_int64, P, P, P]
+    L.blacklight_mlp_coefficients.argtypes = [P, C.c_int64, P, P, P]
     L.blacklight_strerror.argtypes = [C.c_int]
     L.blacklight_strerror.restype = C.c_char_p
     L.blacklight_last_error_detail.argtypes = []
@@ -165,10 +183,12 @@ def metric_struct(met, precision=None) -> Metric:
                   met.tol_rel, met.ds_max, met.h0_frac, int(met.max_steps), met.flat, p)
 
 
-def grid_struct(gp, prim_ptr) -> Grid:
+def grid_struct(gp, prim_ptr, coef_mlp=None) -> Grid:
+    """coef_mlp: optional tensor holding the learned coefficient model's parameters."""
     return Grid(C.sizeof(Grid), prim_ptr, gp.n_r, gp.n_theta, gp.n_phi, gp.r_min, gp.r_max,
                 gp.gamma_ad, gp.r_high, gp.r_low, gp.mu, gp.ne_over_ni, gp.sigma_cut,
-                gp.rho_unit_cgs, gp.mass_msun, gp.interp)
+                gp.rho_unit_cgs, gp.mass_msun, gp.interp,
+                None if coef_mlp is None else coef_mlp.data_ptr())
 
 
 def out_struct(stokes=None, status=None, steps=None, end_state=None, samples=None) -> Out:
@@ -182,13 +202,14 @@ def out_struct(stokes=None, status=None, steps=None, end_state=None, samples=Non
 
 # ------------------------------------ calls ---------------------------------------------
 def blacklight_trace_batch(cams, mets, gps, prims, freqs, outs, workspace=None, stream=None,
-                           flags=0):
-    """cams/mets/gps: synth dataclasses; prims: CUDA float32 tensors; outs: dicts of tensors."""
+                           flags=0, coef_mlp=None):
+    """cams/mets/gps: synth dataclasses; prims: CUDA float32 tensors; outs: dicts of tensors;
+    coef_mlp: optional CUDA float32 tensor of the learned coefficient model (all images)."""
     L = load()
     n = len(cams)
     ca = (Camera * n)(*[camera_struct(c) for c in cams])
     ma = (Metric * n)(*[metric_struct(m) for m in mets])
-    ga = (Grid * n)(*[grid_struct(g, p.data_ptr()) for g, p in zip(gps, prims)])
+    ga = (Grid * n)(*[grid_struct(g, p.data_ptr(), coef_mlp) for g, p in zip(gps, prims)])
     fa = (C.c_double * n)(*[float(f) for f in freqs])
     oa = (Out * n)(*[out_struct(**o) for o in outs])
     ws_ptr, ws_bytes = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel()
@@ -214,11 +235,12 @@ def blacklight_trace_noalloc(cam, met, gp, prim, freq, out, stream=None, flags=0
                                              C.byref(os_), _stream(stream), flags))
 
 
-def blacklight_trace_host(cam, met, gp, prim_host, freq, out_host, stream=None):
-    """prim_host and the tensors in out_host are CPU tensors (pinned for speed)."""
+def blacklight_trace_host(cam, met, gp, prim_host, freq, out_host, stream=None, coef_mlp=None):
+    """prim_host, coef_mlp (optional) and the tensors in out_host are CPU tensors (pinned for
+    speed)."""
     L = load()
     cs, ms = camera_struct(cam), metric_struct(met)
-    gs = grid_struct(gp, prim_host.data_ptr())
+    gs = grid_struct(gp, prim_host.data_ptr(), coef_mlp)
     os_ = out_struct(**out_host)
     return _check(L.blacklight_trace_host(C.byref(cs), C.byref(ms), C.byref(gs), float(freq),
                                           C.byref(os_), _stream(stream)))
@@ -254,6 +276,52 @@ def blacklight_bessel_k(x, out, precision, stream=None):
                                              _stream(stream)))
 
 
+# ------------------------------- learned coefficient model ------------------------------
+def blacklight_mlp_init(params, seed, stream=None):
+    return _check(load().blacklight_mlp_init(_ptr(params), int(seed), _stream(stream)))
+
+
+def blacklight_mlp_dataset(n, seed, inputs, targets, stream=None):
+    return _check(load().blacklight_mlp_dataset(int(n), int(seed), _ptr(inputs), _ptr(targets),
+                                                _stream(stream)))
+
+
+def blacklight_mlp_targets(inputs, targets, stream=None):
+    return _check(load().blacklight_mlp_targets(inputs.shape[0], _ptr(inputs), _ptr(targets),
+                                                _stream(stream)))
+
+
+def blacklight_mlp_normalise(inputs, targets, params, stream=None):
+    return _check(load().blacklight_mlp_normalise(targets.shape[0], _ptr(inputs), _ptr(targets),
+                                                  _ptr(params), _stream(stream)))
+
+
+def blacklight_mlp_train(params, inputs, targets, batch, steps, lr_start, lr_end, beta1=0.9,
+                         beta2=0.999, eps=1e-8, loss_history=None, stream=None):
+    cfg = MlpTrain(C.sizeof(MlpTrain), inputs.shape[0], inputs.data_ptr(), targets.data_ptr(),
+                   int(batch), int(steps), float(lr_start), float(lr_end), float(beta1),
+                   float(beta2), float(eps))
+    return _check(load().blacklight_mlp_train(C.byref(cfg), _ptr(params), _ptr(loss_history),
+                                              _stream(stream)))
+
+
+def blacklight_mlp_grad(params, inputs, targets, grad, stream=None) -> float:
+    loss = C.c_float(0.0)
+    _check(load().blacklight_mlp_grad(_ptr(params), inputs.shape[0], _ptr(inputs), _ptr(targets),
+                                      _ptr(grad), C.byref(loss), _stream(stream)))
+    return float(loss.value)
+
+
+def blacklight_mlp_forward(params, inputs, outputs, stream=None):
+    return _check(load().blacklight_mlp_forward(_ptr(params), inputs.shape[0], _ptr(inputs),
+                                                _ptr(outputs), _stream(stream)))
+
+
+def blacklight_mlp_coefficients(params, inp, out, stream=None):
+    return _check(load().blacklight_mlp_coefficients(_ptr(params), inp.shape[0], _ptr(inp),
+                                                     _ptr(out), _stream(stream)))
+
+
 def blacklight_launch_count(reset=False) -> int:
     return int(load().blacklight_launch_count(1 if reset else 0))
 
@@ -270,7 +338,8 @@ def adapt_struct(block, max_level, criterion, threshold, min_count, min_intensit
                  float(min_intensity))
 
 
-def blacklight_trace_adaptive(cams, mets, gps, prims, freqs, adapt, outs, stream=None):
+def blacklight_trace_adaptive(cams, mets, gps, prims, freqs, adapt, outs, stream=None,
+                              coef_mlp=None):
     """Adaptive tracing; outs[q]["stokes"] is the [4][nf][nf] composite. Returns (rc, rays per
     level [n_images][max_level + 1])."""
     import numpy as np
@@ -278,7 +347,7 @@ def blacklight_trace_adaptive(cams, mets, gps, prims, freqs, adapt, outs, stream
     n = len(cams)
     ca = (Camera * n)(*[camera_struct(c) for c in cams])
     ma = (Metric * n)(*[metric_struct(m) for m in mets])
-    ga = (Grid * n)(*[grid_struct(g, p.data_ptr()) for g, p in zip(gps, prims)])
+    ga = (Grid * n)(*[grid_struct(g, p.data_ptr(), coef_mlp) for g, p in zip(gps, prims)])
     fa = (C.c_double * n)(*[float(f) for f in freqs])
     oa = (Out * n)(*[out_struct(**o) for o in outs])
     lr = np.zeros((n, adapt.max_level + 1), dtype=np.int32)

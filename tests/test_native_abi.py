@@ -30,6 +30,30 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(native.Out) == 56
 
 
+def test_ctypes_struct_sizes_equal_the_c_compilers(tmp_path):
+    """Compile the header with the host C compiler and compare every struct's size and the
+    parameter count with the binding's ctypes mirrors."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no host C compiler")
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "blacklight.h"\nint main(void) {\n'
+                   ' printf("%zu %zu %zu %zu %zu %zu %d\\n", sizeof(bl_camera_t), sizeof(bl_metric_t),'
+                   ' sizeof(bl_grid_t), sizeof(bl_out_t), sizeof(bl_adapt_t), sizeof(bl_mlp_train_t),'
+                   ' BL_MLP_PARAMS);\n return 0;\n}\n')
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    want = [ctypes.sizeof(native.Camera), ctypes.sizeof(native.Metric),
+            ctypes.sizeof(native.Grid), ctypes.sizeof(native.Out), ctypes.sizeof(native.Adapt),
+            ctypes.sizeof(native.MlpTrain), native.MLP_PARAMS]
+    assert got == want
+
+
 def test_strerror_without_gpu():
     L = native.load()
     assert L.blacklight_strerror(-1) == b"invalid argument"
