@@ -33,6 +33,9 @@ GRID = (256, 128, 128)
 # Algorithmic arithmetic per unit of work (operation counts of the method, see design notes):
 # FP64 flops per Dormand-Prince attempt (6 right-hand sides, 5 stage combinations, error norm)
 FLOP64_PER_ATTEMPT = 1520
+# dram__bytes_read.sum + dram__bytes_write.sum of geodesic_kernel<float, df64> per DP attempt
+# (2.207 GB for 7,845,744 attempts: the a = 0.94, i = 60 deg image of this workload at 256^2)
+GEO_DF64_DRAM_BYTES_PER_ATTEMPT = 281.6
 # FP32 flops per transfer sample (2 transport matrices, predictor-corrector, sampling,
 # plasma, coefficients, fluid frame, Stokes step)
 FLOP32_PER_SAMPLE = 3300
@@ -68,6 +71,11 @@ def parse():
                     help="skip the 1024^2 image on the 512x256x256 torus")
     ap.add_argument("--no-adaptive", action="store_true",
                     help="skip the batched adaptive-refinement workload")
+    ap.add_argument("--coef", default="exact", choices=["exact", "mlp"],
+                    help="coefficients of the main workload: exact fits, or the learned model "
+                         "(trained first; needs --precision fast or mixed)")
+    ap.add_argument("--no-plan", action="store_true",
+                    help="skip the autotuned CUDA-graph plan line")
     ap.add_argument("--no-mlp", action="store_true",
                     help="skip the learned-coefficient line (training + 1024^2 image + FP64 form)")
     return ap.parse_args()
@@ -257,9 +265,16 @@ def main():
     outs = [images.alloc_outputs(c.n, dt, device=device, samples=True) for c in cams]
     rays_per_step = sum(c.n * c.n for c in cams)
 
+    coef_mlp = None
+    if args.coef == "mlp":
+        # the learned coefficient model in the transfer (trained here, outside the timing)
+        from paper_2203_15963_gb300 import coefmodel
+        coef_mlp, _ = coefmodel.train(device=device)
+
     def step():
         return native.blacklight_trace_batch(cams, mets, wl["gps"], wl["prims"], wl["freqs"],
-                                             outs, workspace=ws, flags=native.BL_TIMING)
+                                             outs, workspace=ws, flags=native.BL_TIMING,
+                                             coef_mlp=coef_mlp)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -313,7 +328,14 @@ def main():
                 "achieved": flop_tr / tr_avg / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": "nominal rate (profiling recipe unit counts x 2.07 GHz)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes (read + written) of the dominant kernel per launch: the per-unit figure from
+    # one ncu capture of the same kernel on the one-image 256^2 case, scaled by the units of
+    # this launch (attempts for the geodesic kernel, samples for the transfer kernel)
+    if roof["kernel"].startswith("geodesic_kernel (double-float"):
+        roof["traffic"] = GEO_DF64_DRAM_BYTES_PER_ATTEMPT * attempts
+        roof["traffic_note"] = "ncu capture of the 256^2 one-image case, scaled by DP attempts"
+    else:
+        roof["traffic"] = None
     status_bad = sum(int(((o["status"] != 1) & (o["status"] != 2)).sum()) for o in outs)
     # the secondary measurements below allocate their own workspaces
     del ws
@@ -331,6 +353,9 @@ def main():
     if not args.no_hires and args.case == "full":
         hires, hires_img = measure_hires(torch, native, images, prec, device,
                                          keep_image=prec == native.BL_PREC_FAST)
+    plan = None
+    if not args.no_plan:
+        plan = measure_plan(torch, native, images, wl, prec, device)
     mlp = None
     if not args.no_mlp and args.case == "full":
         mlp = measure_mlp(torch, native, images, device, hires_img)
@@ -358,13 +383,14 @@ def main():
                            "images": len(cams), "camera": N_PIX,
                            "grid": list(GRID), "spins": list(SPINS),
                            "inclinations_deg": list(INCS), "freq_ghz": FREQ / 1e9,
-                           "precision": args.precision, "parallelism": f"replicas x{world}",
+                           "precision": args.precision, "coefficients": args.coef,
+                           "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (3 x 134 MB grids + sample records); no flush"},
                 "kernel_ms": {"geodesic": geo_avg * 1e3, "transfer": tr_avg * 1e3},
                 "work": {"dp_attempts": attempts, "samples": samples,
                          "rays_not_terminated_normally": status_bad},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "other_forms": other,
-                "hires": hires, "mlp": mlp, "adaptive": adaptive,
+                "plan": plan, "hires": hires, "mlp": mlp, "adaptive": adaptive,
                 "gpu_launches": int(launches), "clocks": clk, "return_codes": sorted(set(rcs))}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -479,6 +505,64 @@ def measure_mlp(torch, native, images, device, fast_image):
     del img, img64, params
     torch.cuda.empty_cache()
     return line
+
+
+def measure_plan(torch, native, images, wl, code, device, steps=5):
+    """The main workload as an autotuned plan (CUDA-graph replay), device-timed like the
+    headline, and the host cost of small batches (16 images of 32^2 on the 64x32x32 torus)
+    through direct calls against graph replays (wall clock per batch, synchronised)."""
+    from paper_2203_15963_gb300 import synth as S
+    cams, mets = wl["cams"], wl["mets"]
+    dt = torch.float64 if code == native.BL_PREC_FP64 else torch.float32
+    outs = [images.alloc_outputs(c.n, dt, device=device) for c in cams]
+    t0 = time.perf_counter()
+    plan = native.Plan(cams, mets, wl["gps"], wl["prims"], wl["freqs"], outs, autotune=True)
+    tune_s = time.perf_counter() - t0
+    cfg = plan.config()
+    for _ in range(2):
+        plan.run()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan.run()
+    e1.record()
+    torch.cuda.synchronize()
+    rc = plan.check()
+    ms = e0.elapsed_time(e1) / steps
+    rays = sum(c.n * c.n for c in cams)
+    plan.close()
+    del outs
+    # small batches: host overhead of direct calls against replays
+    cam, met, gp, prim = S.workload_inputs("torus64_cam32", 0.9, 17.0)
+    met = S.Metric(**{**met.__dict__, "precision": code})
+    p = torch.from_numpy(prim).to(device)
+    k = 16
+    cs, ms_, gs, ps, fs = [cam] * k, [met] * k, [gp] * k, [p] * k, [FREQ] * k
+    so = [images.alloc_outputs(cam.n, dt, device=device) for _ in range(k)]
+    ws = torch.empty(native.blacklight_workspace_size(cs, ms_), dtype=torch.uint8, device=device)
+    small = native.Plan(cs, ms_, gs, ps, fs, so)
+
+    def wall(fn, n=20):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(n):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) / n * 1e3
+
+    direct_ms = wall(lambda: native.blacklight_trace_batch(cs, ms_, gs, ps, fs, so, workspace=ws,
+                                                           flags=native.BL_ASYNC))
+    replay_ms = wall(small.run)
+    small.close()
+    del ws, so, p
+    torch.cuda.empty_cache()
+    return {"value": rays / ms * 1e3, "unit": "rays/s", "ms_per_step": ms, "steps": steps,
+            "return_code": rc, "autotune_seconds": tune_s, "config": cfg,
+            "small_batch": {"workload": "16 x 32^2 on the 64x32x32 torus",
+                            "direct_ms": direct_ms, "graph_replay_ms": replay_ms}}
 
 
 def measure_adaptive(torch, native, code, device, steps=2, warmup=1):

@@ -179,6 +179,46 @@ int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const 
 int blacklight_geodesics(const bl_camera_t* cam, const bl_metric_t* met, const bl_out_t* out,
                          void* stream, uint32_t flags);
 
+/* ---------------------------------------------------------------------------------------
+ * Plans: a batched trace prepared once and replayed as a CUDA graph (the paper's code has no
+ * counterpart; it re-traces from scratch on CPU threads). blacklight_plan_create validates
+ * the arguments exactly like blacklight_trace_batch, allocates the workspace, uploads the
+ * image descriptors, optionally autotunes the launch configuration, and captures the launch
+ * sequence (counter reset, camera frames, one geodesic + transfer pair per wave of 2^20 rays)
+ * in a CUDA graph; blacklight_plan_run replays it with one graph launch. The plan binds the
+ * pointers in grids and outs and the camera/metric/frequency values: between runs the caller
+ * may rewrite the contents of grids[q].prim (a new snapshot) and read the outputs, but must
+ * create a new plan for other pointers or parameters. Runs on different streams must not
+ * overlap (they share the plan's workspace).
+ * --------------------------------------------------------------------------------------- */
+typedef struct bl_plan bl_plan_t;
+typedef struct bl_launch_config {
+    uint32_t size;
+    int32_t ray_order;        /* 0 Morton order within each image (n a power of two), 1 rows */
+    int32_t geo_ctas_per_sm;  /* persistent geodesic CTAs per SM, 0 = occupancy limit */
+    int32_t tr_ctas_per_sm;   /* persistent transfer CTAs per SM, 0 = occupancy limit */
+    float run_ms;             /* autotuned plans: device time of one run with this configuration */
+} bl_launch_config_t;
+/* flags for blacklight_plan_create: search ray order and CTAs per SM (coordinate descent over
+ * timed runs of the plan's own workload; the images' outputs are written while tuning). The
+ * choice is cached per device and workload shape for the life of the process. */
+enum { BL_PLAN_AUTOTUNE = 4u };
+/* config: NULL = defaults (Morton, occupancy limits), ignored with BL_PLAN_AUTOTUNE. `stream`
+ * is used for the tuning runs and the capture (the legacy default stream is replaced by a
+ * private stream for the capture). */
+int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                           const bl_grid_t* grids, const double* freqs_hz, const bl_out_t* outs,
+                           const bl_launch_config_t* config, uint32_t flags, void* stream,
+                           bl_plan_t** plan);
+/* Replay the plan on `stream` (asynchronous). */
+int blacklight_plan_run(bl_plan_t* plan, void* stream);
+/* Synchronise `stream` and report the last run: 0, or BL_WRAYS if some ray ended abnormally. */
+int blacklight_plan_check(bl_plan_t* plan, void* stream);
+/* The plan's launch configuration. */
+int blacklight_plan_config(const bl_plan_t* plan, bl_launch_config_t* out);
+/* Free the plan (synchronises the device). NULL is ignored. */
+int blacklight_plan_destroy(bl_plan_t* plan);
+
 /* Adaptive ray tracing (Sec. 4, "Adaptive Ray Tracing"). The root n x n image is split into
  * square blocks of `block` pixels; each traced block is judged on its own pixels' Stokes I:
  * when at least min_count pixels have a criterion value above `threshold`, every pixel of the

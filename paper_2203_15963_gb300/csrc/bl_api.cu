@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstddef>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -251,11 +252,16 @@ int dev_info(DevInfo& out) {
     return 0;
 }
 
-// Launch the camera-frame kernel, then the geodesic and (optionally) transfer kernels once per
-// wave of rays, on prepared workspace. Waves run in stream order and reuse the workspace.
-int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* ws,
-               const Layout& L, int precision, bool transfer, cudaStream_t st, bool timing,
-               const float* mlp = nullptr) {
+// Launch shape of the persistent kernels: CTAs per SM (0 = the occupancy limit).
+struct LaunchCfg {
+    int geo_ctas = 0, tr_ctas = 0;
+};
+
+// The kernel sequence of one trace on prepared workspace whose image descriptors are already
+// on the device: counter reset, camera frames, then one geodesic + transfer pair per wave of
+// rays, in stream order (the part a plan captures in a CUDA graph).
+int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, bool transfer,
+                   cudaStream_t st, bool timing, const float* mlp, const LaunchCfg& cfg) {
     DevInfo di;
     int rc = dev_info(di);
     if (rc) return rc;
@@ -273,14 +279,14 @@ int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* 
     bl::RayHdr* hdr = (bl::RayHdr*)(ws + L.hdr);
     int32_t* chunks = (int32_t*)(ws + L.chunks);
     BL_CUDA(cudaMemsetAsync(ctr, 0, sizeof(bl::Counters), st));
-    BL_CUDA(cudaMemcpyAsync(d_desc, descs.data(), sizeof(bl::ImageDesc) * n_images,
-                            cudaMemcpyHostToDevice, st));
     bl::camera_frame_kernel<<<(n_images + 63) / 64, 64, 0, st>>>(d_desc, n_images);
     ++g_launches;
     BL_CUDA(cudaGetLastError());
     const int pidx = precision;
-    const unsigned geo_grid = (unsigned)(di.sms * di.geo_blocks[pidx]);
-    const unsigned tr_grid = (unsigned)(di.sms * di.tr_blocks[pidx]);
+    auto pick = [](int want, int occ) { return want > 0 && want < occ ? want : occ; };
+    const unsigned geo_grid = (unsigned)(di.sms * pick(cfg.geo_ctas, di.geo_blocks[pidx]));
+    const unsigned tr_grid = (unsigned)(di.sms * pick(cfg.tr_ctas, mlp ? di.tr_mlp_blocks
+                                                                       : di.tr_blocks[pidx]));
     const int record = transfer ? 1 : 0;
     for (int64_t w = 0; w < n_waves; ++w) {
         const int64_t b = w * L.wave;
@@ -306,7 +312,7 @@ int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* 
         if (timing) BL_CUDA(cudaEventRecord(g_ev[2 * w + 1], st));
         if (transfer) {
             if (mlp) {
-                bl::transfer_mlp_kernel<float><<<(unsigned)(di.sms * di.tr_mlp_blocks), 128, 0, st>>>(
+                bl::transfer_mlp_kernel<float><<<tr_grid, 128, 0, st>>>(
                     d_desc, n_images, b, e, hdr, (const float*)(ws + L.pool), chunks, mlp, ctr);
             } else if (precision != BL_PREC_FP64) {
                 bl::transfer_kernel<float, float><<<tr_grid, 128, 0, st>>>(
@@ -322,6 +328,15 @@ int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* 
     }
     if (timing) g_timed_waves = (int)n_waves;
     return 0;
+}
+
+// Upload the image descriptors, then launch_kernels.
+int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* ws,
+               const Layout& L, int precision, bool transfer, cudaStream_t st, bool timing,
+               const float* mlp = nullptr, const LaunchCfg& cfg = LaunchCfg()) {
+    BL_CUDA(cudaMemcpyAsync(ws + L.descs, descs.data(), sizeof(bl::ImageDesc) * n_images,
+                            cudaMemcpyHostToDevice, st));
+    return launch_kernels(n_images, ws, L, precision, transfer, st, timing, mlp, cfg);
 }
 
 int finish(char* ws, const Layout& L, cudaStream_t st, bool sync) {
@@ -351,14 +366,13 @@ int common_mlp(int32_t n_images, const bl_grid_t* grids, int precision, const fl
     return 0;
 }
 
-int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
-               const bl_grid_t* grids, const double* freqs, const bl_out_t* outs, void* workspace,
-               size_t workspace_bytes, void* stream, uint32_t flags, bool transfer) {
-    g_detail[0] = 0;
+int check_batch(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                const bl_grid_t* grids, const double* freqs, const bl_out_t* outs, bool transfer,
+                int* precision_out) {
+    int precision = -1;
     if (n_images < 1) return fail(BL_EINVAL, "n_images must be >= 1");
     if (!cams || !mets || !outs || (transfer && (!grids || !freqs)))
         return fail(BL_EINVAL, "NULL array argument");
-    int precision = -1;
     for (int q = 0; q < n_images; ++q) {
         int rc = check_camera(&cams[q], q);
         if (!rc) rc = check_metric(&mets[q], q);
@@ -383,6 +397,19 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
         if ((rc = device_pointer(outs[q].samples, what))) return rc;
         snprintf(what, sizeof(what), "grids[%d].prim", q);
         if (transfer && (rc = device_pointer(grids[q].prim, what))) return rc;
+    }
+    *precision_out = precision;
+    return 0;
+}
+
+int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+               const bl_grid_t* grids, const double* freqs, const bl_out_t* outs, void* workspace,
+               size_t workspace_bytes, void* stream, uint32_t flags, bool transfer) {
+    g_detail[0] = 0;
+    int precision = -1;
+    {
+        int rc = check_batch(n_images, cams, mets, grids, freqs, outs, transfer, &precision);
+        if (rc) return rc;
     }
     // geodesics only: no records, so no pool
     const int64_t rays = count_rays(n_images, cams);
@@ -428,6 +455,169 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
         cudaError_t e = cudaFreeAsync(ws, st);
         if (rc == 0 && e != cudaSuccess) rc = cuda_fail(e, "cudaFreeAsync");
     }
+    return rc;
+}
+
+// ---------------------------------------------------------------------------------------
+// Plans: prepared batched traces replayed as CUDA graphs, with an optional autotuner.
+// ---------------------------------------------------------------------------------------
+struct TuneKey {
+    int dev, precision, mlp, n_images;
+    int64_t rays;
+    bool operator<(const TuneKey& o) const {
+        if (dev != o.dev) return dev < o.dev;
+        if (precision != o.precision) return precision < o.precision;
+        if (mlp != o.mlp) return mlp < o.mlp;
+        if (n_images != o.n_images) return n_images < o.n_images;
+        return rays < o.rays;
+    }
+};
+struct TuneVal {
+    int order;
+    LaunchCfg cfg;
+    float ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+}  // namespace
+
+struct bl_plan {
+    int dev = 0;
+    int32_t n_images = 0;
+    int precision = 0;
+    const float* mlp = nullptr;
+    std::vector<bl::ImageDesc> descs;
+    Layout L{};
+    char* ws = nullptr;
+    int order = 0;
+    LaunchCfg cfg;
+    float run_ms = 0.0f;
+    int64_t kernels_per_run = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int plan_set_order(bl_plan& P, int order, cudaStream_t st) {
+    for (auto& d : P.descs) d.order = order;
+    P.order = order;
+    BL_CUDA(cudaMemcpyAsync(P.ws + P.L.descs, P.descs.data(),
+                            sizeof(bl::ImageDesc) * P.descs.size(), cudaMemcpyHostToDevice, st));
+    return 0;
+}
+
+// Device time of one run with the given configuration (best of two, after one warm-up).
+int plan_time(bl_plan& P, const LaunchCfg& cfg, cudaStream_t st, float* ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BL_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(ce, "cudaEventCreate"); }
+    int rc = 0;
+    float best = 1e30f;
+    for (int it = 0; it < 3 && rc == 0; ++it) {
+        if (it > 0 && (ce = cudaEventRecord(e0, st)) != cudaSuccess) rc = cuda_fail(ce, "record");
+        if (!rc) rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, cfg);
+        if (!rc && it > 0) {
+            if ((ce = cudaEventRecord(e1, st)) != cudaSuccess) rc = cuda_fail(ce, "record");
+            else if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(ce, "sync");
+            else {
+                float t = 0.0f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (t < best) best = t;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = best;
+    return rc;
+}
+
+// Coordinate descent: ray order at the occupancy limits, then geodesic CTAs per SM, then
+// transfer CTAs per SM. A candidate replaces the current choice only if it is faster by more
+// than kTuneMargin (run-to-run variation of these persistent kernels is about 1-2 %).
+constexpr float kTuneMargin = 0.03f;
+int plan_autotune(bl_plan& P, cudaStream_t st) {
+    DevInfo di;
+    int rc = dev_info(di);
+    if (rc) return rc;
+    const TuneKey key{P.dev, P.precision, P.mlp ? 1 : 0, P.n_images, P.L.rays};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            P.cfg = it->second.cfg;
+            P.run_ms = it->second.ms;
+            return plan_set_order(P, it->second.order, st);
+        }
+    }
+    float best = 0.0f, t = 0.0f;
+    LaunchCfg cfg;
+    int order = 0;
+    if ((rc = plan_set_order(P, 0, st)) || (rc = plan_time(P, cfg, st, &best))) return rc;
+    if ((rc = plan_set_order(P, 1, st)) || (rc = plan_time(P, cfg, st, &t))) return rc;
+    if (t < best * (1.0f - kTuneMargin)) { best = t; order = 1; }
+    if ((rc = plan_set_order(P, order, st))) return rc;
+    const int geo_max = di.geo_blocks[P.precision];
+    const int tr_max = P.mlp ? di.tr_mlp_blocks : di.tr_blocks[P.precision];
+    int geo_best = geo_max;
+    for (int c = 1; c < geo_max; ++c) {
+        LaunchCfg trial = cfg;
+        trial.geo_ctas = c;
+        if ((rc = plan_time(P, trial, st, &t))) return rc;
+        if (t < best * (1.0f - kTuneMargin)) { best = t; geo_best = c; }
+    }
+    cfg.geo_ctas = geo_best;
+    int tr_best = tr_max;
+    for (int c = 1; c < tr_max; ++c) {
+        LaunchCfg trial = cfg;
+        trial.tr_ctas = c;
+        if ((rc = plan_time(P, trial, st, &t))) return rc;
+        if (t < best * (1.0f - kTuneMargin)) { best = t; tr_best = c; }
+    }
+    cfg.tr_ctas = tr_best;
+    P.cfg = cfg;
+    P.run_ms = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = TuneVal{order, cfg, best};
+    return 0;
+}
+
+int plan_capture(bl_plan& P, cudaStream_t user) {
+    DevInfo di;                      // occupancy queries happen before, not during, capture
+    if (int rc0 = dev_info(di)) return rc0;
+    cudaStream_t st = user;
+    bool own = false;
+    if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) {
+        BL_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        own = true;
+    }
+    // descriptors must be on the device before the captured kernels first run
+    cudaError_t e = cudaStreamSynchronize(user);
+    int rc = e == cudaSuccess ? 0 : cuda_fail(e, "cudaStreamSynchronize");
+    const uint64_t before = g_launches;
+    if (!rc) {
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    if (!rc) {
+        rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, P.cfg);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(st, &g);
+        if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamEndCapture");
+        if (!rc) {
+            P.graph = g;
+            e = cudaGraphInstantiate(&P.exec, P.graph, 0);
+            if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate");
+        } else if (g) {
+            cudaGraphDestroy(g);
+        }
+    }
+    P.kernels_per_run = (int64_t)(g_launches - before);
+    g_launches = before;          // capture launches nothing; runs are counted when replayed
+    if (own) cudaStreamDestroy(st);
     return rc;
 }
 
@@ -714,6 +904,104 @@ int blacklight_trace_noalloc(const bl_camera_t* cam, const bl_metric_t* met,
     // the rest is written before it is read, so stale contents from the last call are inert.
     return trace_impl(1, cam, met, grid, &freq_hz, out, ws, kNoAllocBytes, stream,
                       flags & ~(uint32_t)BL_TIMING, true);
+}
+
+int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                           const bl_grid_t* grids, const double* freqs_hz, const bl_out_t* outs,
+                           const bl_launch_config_t* config, uint32_t flags, void* stream,
+                           bl_plan_t** plan) {
+    g_detail[0] = 0;
+    if (!plan) return fail(BL_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    int precision = -1;
+    int rc = check_batch(n_images, cams, mets, grids, freqs_hz, outs, true, &precision);
+    if (rc) return rc;
+    if (config && !(flags & BL_PLAN_AUTOTUNE)) {
+        if (config->size != sizeof(bl_launch_config_t)) return fail(BL_EINVAL, "config.size mismatch");
+        if (config->ray_order < 0 || config->ray_order > 1 || config->geo_ctas_per_sm < 0 ||
+            config->tr_ctas_per_sm < 0)
+            return fail(BL_EINVAL, "config: ray_order 0 or 1, CTAs per SM >= 0");
+    }
+    const float* mlp = nullptr;
+    if ((rc = common_mlp(n_images, grids, precision, &mlp))) return rc;
+    bl_plan* P = new bl_plan();
+    BL_CUDA(cudaGetDevice(&P->dev));
+    P->n_images = n_images;
+    P->precision = precision;
+    P->mlp = mlp;
+    P->L = make_layout_rays(n_images, count_rays(n_images, cams), precision, true);
+    P->descs.resize(n_images);
+    int64_t off = 0;
+    for (int q = 0; q < n_images; ++q) {
+        fill_desc(P->descs[q], cams[q], mets[q], grids[q], freqs_hz[q], outs[q], off);
+        off += (int64_t)cams[q].n * cams[q].n;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMalloc((void**)&P->ws, P->L.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        return fail(BL_ENOMEM, "cudaMalloc(%zu bytes): %s", P->L.total, cudaGetErrorString(e));
+    }
+    if (flags & BL_PLAN_AUTOTUNE) {
+        rc = plan_autotune(*P, st);
+    } else {
+        if (config) {
+            P->cfg.geo_ctas = config->geo_ctas_per_sm;
+            P->cfg.tr_ctas = config->tr_ctas_per_sm;
+        }
+        rc = plan_set_order(*P, config ? config->ray_order : 0, st);
+    }
+    if (!rc) rc = plan_capture(*P, st);
+    if (rc) {
+        blacklight_plan_destroy(P);
+        return rc;
+    }
+    *plan = P;
+    return 0;
+}
+
+int blacklight_plan_run(bl_plan_t* plan, void* stream) {
+    g_detail[0] = 0;
+    if (!plan || !plan->exec) return fail(BL_EINVAL, "plan is NULL or not built");
+    int dev = 0;
+    BL_CUDA(cudaGetDevice(&dev));
+    if (dev != plan->dev) return fail(BL_EINVAL, "plan belongs to device %d, current is %d", plan->dev, dev);
+    BL_CUDA(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+    g_launches += (uint64_t)plan->kernels_per_run;
+    return 0;
+}
+
+int blacklight_plan_check(bl_plan_t* plan, void* stream) {
+    g_detail[0] = 0;
+    if (!plan || !plan->ws) return fail(BL_EINVAL, "plan is NULL");
+    return finish(plan->ws, plan->L, (cudaStream_t)stream, true);
+}
+
+int blacklight_plan_config(const bl_plan_t* plan, bl_launch_config_t* out) {
+    g_detail[0] = 0;
+    if (!plan || !out || out->size != sizeof(bl_launch_config_t))
+        return fail(BL_EINVAL, "plan is NULL or out.size mismatch");
+    DevInfo di;
+    int rc = dev_info(di);
+    if (rc) return rc;
+    const int geo_max = di.geo_blocks[plan->precision];
+    const int tr_max = plan->mlp ? di.tr_mlp_blocks : di.tr_blocks[plan->precision];
+    out->ray_order = plan->order;
+    out->geo_ctas_per_sm = plan->cfg.geo_ctas > 0 && plan->cfg.geo_ctas < geo_max ? plan->cfg.geo_ctas : geo_max;
+    out->tr_ctas_per_sm = plan->cfg.tr_ctas > 0 && plan->cfg.tr_ctas < tr_max ? plan->cfg.tr_ctas : tr_max;
+    out->run_ms = plan->run_ms;
+    return 0;
+}
+
+int blacklight_plan_destroy(bl_plan_t* plan) {
+    if (!plan) return 0;
+    cudaDeviceSynchronize();
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->ws) cudaFree(plan->ws);
+    delete plan;
+    return 0;
 }
 
 int blacklight_trace_batch(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,

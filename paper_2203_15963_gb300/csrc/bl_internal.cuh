@@ -44,7 +44,7 @@ struct ImageDesc {
     // are then compact, indexed by p (Stokes [4][n_rays]).
     const int32_t* block_list;
     int32_t block;
-    int32_t pad2_;
+    int32_t order;          // ray order without a block list: 0 Morton (n a power of 2), 1 rows
     // filled by the camera-frame kernel
     double x_cam[4], u_cam[4], kk[4], hh[4], vv[4];
     double r_cam, r_hor;

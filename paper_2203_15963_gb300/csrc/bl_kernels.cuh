@@ -146,9 +146,9 @@ __device__ __forceinline__ int find_image(const ImageDesc* imgs, int n_images, i
 }
 
 // Pixel of local ray p and the index its outputs go to: block-list order (adaptive
-// refinement), else Morton (Z) order when n is a power of two so that a warp covers a
-// compact 8x4 patch of the image, else row-major.
-__device__ __forceinline__ void pixel_of(int64_t p, int n, int& i, int& j);
+// refinement), else, with order 0, Morton (Z) order when n is a power of two so that a warp
+// covers a compact 8x4 patch of the image, else row-major.
+__device__ __forceinline__ void pixel_of(int64_t p, int n, int order, int& i, int& j);
 __device__ __forceinline__ int64_t ray_pixel(const ImageDesc& im, int64_t p, int& i, int& j) {
     if (im.block_list) {
         const int64_t b2 = (int64_t)im.block * im.block;
@@ -158,12 +158,12 @@ __device__ __forceinline__ int64_t ray_pixel(const ImageDesc& im, int64_t p, int
         j = im.block_list[2 * blk + 1] * im.block + r / im.block;
         return p;
     }
-    pixel_of(p, im.n, i, j);
+    pixel_of(p, im.n, im.order, i, j);
     return (int64_t)j * im.n + i;
 }
 
-__device__ __forceinline__ void pixel_of(int64_t p, int n, int& i, int& j) {
-    if ((n & (n - 1)) == 0) {
+__device__ __forceinline__ void pixel_of(int64_t p, int n, int order, int& i, int& j) {
+    if (order == 0 && (n & (n - 1)) == 0) {
         uint32_t xi = 0, yj = 0;
         for (int b = 0; b < 16; ++b) {
             xi |= (uint32_t)((p >> (2 * b)) & 1) << b;

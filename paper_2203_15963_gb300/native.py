@@ -78,6 +78,14 @@ class MlpTrain(C.Structure):
 MLP_PARAMS = 4906
 
 
+class LaunchConfig(C.Structure):
+    _fields_ = [("size", C.c_uint32), ("ray_order", C.c_int32), ("geo_ctas_per_sm", C.c_int32),
+                ("tr_ctas_per_sm", C.c_int32), ("run_ms", C.c_float)]
+
+
+BL_PLAN_AUTOTUNE = 4
+
+
 class Adapt(C.Structure):
     _fields_ = [("size", C.c_uint32), ("block", C.c_int32), ("max_level", C.c_int32),
                 ("criterion", C.c_int32), ("threshold", C.c_double), ("min_count", C.c_int32),
@@ -134,6 +142,14 @@ def load():
     L.blacklight_mlp_grad.argtypes = [P, C.c_int64, P, P, P, C.POINTER(C.c_float), P]
     L.blacklight_mlp_forward.argtypes = [P, C.c_int64, P, P, P]
     L.blacklight_mlp_coefficients.argtypes = [P, C.c_int64, P, P, P]
+    L.blacklight_plan_create.argtypes = [C.c_int32, C.POINTER(Camera), C.POINTER(Metric),
+                                         C.POINTER(Grid), C.POINTER(C.c_double), C.POINTER(Out),
+                                         C.POINTER(LaunchConfig), C.c_uint32, P,
+                                         C.POINTER(C.c_void_p)]
+    L.blacklight_plan_run.argtypes = [P, P]
+    L.blacklight_plan_check.argtypes = [P, P]
+    L.blacklight_plan_config.argtypes = [P, C.POINTER(LaunchConfig)]
+    L.blacklight_plan_destroy.argtypes = [P]
     L.blacklight_strerror.argtypes = [C.c_int]
     L.blacklight_strerror.restype = C.c_char_p
     L.blacklight_last_error_detail.argtypes = []
@@ -274,6 +290,57 @@ def blacklight_stokes_step(coef, s0, dl, s1, precision, stream=None):
 def blacklight_bessel_k(x, out, precision, stream=None):
     return _check(load().blacklight_bessel_k(x.shape[0], _ptr(x), _ptr(out), precision,
                                              _stream(stream)))
+
+
+# ------------------------------- plans (CUDA-graph replay) ------------------------------
+class Plan:
+    """A batched trace captured once in a CUDA graph (blacklight_plan_*). Keeps references to
+    the tensors whose pointers the plan binds."""
+
+    def __init__(self, cams, mets, gps, prims, freqs, outs, autotune=False, config=None,
+                 stream=None, coef_mlp=None):
+        L = load()
+        n = len(cams)
+        ca = (Camera * n)(*[camera_struct(c) for c in cams])
+        ma = (Metric * n)(*[metric_struct(m) for m in mets])
+        ga = (Grid * n)(*[grid_struct(g, p.data_ptr(), coef_mlp) for g, p in zip(gps, prims)])
+        fa = (C.c_double * n)(*[float(f) for f in freqs])
+        oa = (Out * n)(*[out_struct(**o) for o in outs])
+        cfg = None
+        if config is not None:
+            cfg = LaunchConfig(C.sizeof(LaunchConfig), int(config.get("ray_order", 0)),
+                               int(config.get("geo_ctas_per_sm", 0)),
+                               int(config.get("tr_ctas_per_sm", 0)), 0.0)
+        h = C.c_void_p()
+        _check(L.blacklight_plan_create(n, ca, ma, ga, fa, oa,
+                                        None if cfg is None else C.byref(cfg),
+                                        BL_PLAN_AUTOTUNE if autotune else 0, _stream(stream),
+                                        C.byref(h)))
+        self._h = h
+        self._keep = (list(prims), list(outs), coef_mlp)
+
+    def run(self, stream=None):
+        return _check(load().blacklight_plan_run(self._h, _stream(stream)))
+
+    def check(self, stream=None):
+        return _check(load().blacklight_plan_check(self._h, _stream(stream)))
+
+    def config(self):
+        c = LaunchConfig(C.sizeof(LaunchConfig), 0, 0, 0, 0.0)
+        _check(load().blacklight_plan_config(self._h, C.byref(c)))
+        return {"ray_order": c.ray_order, "geo_ctas_per_sm": c.geo_ctas_per_sm,
+                "tr_ctas_per_sm": c.tr_ctas_per_sm, "run_ms": c.run_ms}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().blacklight_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------- learned coefficient model ------------------------------
