@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--coef", default="exact", choices=["exact", "mlp"],
                     help="coefficients of the main workload: exact fits, or the learned model "
                          "(trained first; needs --precision fast or mixed)")
+    ap.add_argument("--no-slow", action="store_true",
+                    help="skip the slow-light line (8 snapshots, 512^2)")
     ap.add_argument("--no-plan", action="store_true",
                     help="skip the autotuned CUDA-graph plan line")
     ap.add_argument("--no-mlp", action="store_true",
@@ -356,10 +358,21 @@ def main():
     plan = None
     if not args.no_plan:
         plan = measure_plan(torch, native, images, wl, prec, device)
+    model = None
+    if (not args.no_mlp or not args.no_slow) and args.case == "full":
+        from paper_2203_15963_gb300 import coefmodel
+        t0 = time.perf_counter()
+        params, hist = coefmodel.train(device=device)
+        torch.cuda.synchronize()
+        model = (params, time.perf_counter() - t0, float(hist[-500:].mean()))
     mlp = None
     if not args.no_mlp and args.case == "full":
-        mlp = measure_mlp(torch, native, images, device, hires_img)
+        mlp = measure_mlp(torch, native, images, device, hires_img, *model)
     hires_img = None
+    slow = None
+    if not args.no_slow and args.case == "full":
+        slow = measure_slow(torch, native, images, device, model[0] if model else None)
+    model = None
     adaptive = None
     if not args.no_adaptive and args.case == "full":
         adaptive = measure_adaptive(torch, native, prec, device)
@@ -390,7 +403,8 @@ def main():
                 "work": {"dp_attempts": attempts, "samples": samples,
                          "rays_not_terminated_normally": status_bad},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "other_forms": other,
-                "plan": plan, "hires": hires, "mlp": mlp, "adaptive": adaptive,
+                "plan": plan, "hires": hires, "mlp": mlp, "slow_light": slow,
+                "adaptive": adaptive,
                 "gpu_launches": int(launches), "clocks": clk, "return_codes": sorted(set(rcs))}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -478,17 +492,57 @@ def rel_l2(torch, got, want):
     return [float(torch.linalg.vector_norm(g[s] - w[s]) / nI) for s in range(4)]
 
 
-def measure_mlp(torch, native, images, device, fast_image):
+def measure_slow(torch, native, images, device, coef_mlp, steps=3):
+    """Slow light: 8 snapshots (10 M apart) of the 256x128x128 rotating torus, one 512^2 image
+    (a = 0.94, i = 60 deg, 230 GHz), traced through a plan (CUDA-graph replay): fast form with
+    the exact fits, and mixed form with the learned coefficients; the fast-light image of the
+    middle snapshot alone for comparison."""
+    import dataclasses
+    from paper_2203_15963_gb300 import synth as S
+    cam, met, gp, prim = S.workload_inputs("torus256_slow8_cam512", 0.94, 60.0)
+    p = torch.from_numpy(prim).to(device)
+    mid = p[4].contiguous()
+    del prim
+
+    def run(gpx, px, code, mlp):
+        m = S.Metric(**{**met.__dict__, "precision": code})
+        outs = [images.alloc_outputs(cam.n, torch.float32, device=device)]
+        plan = native.Plan([cam], [m], [gpx], [px], [FREQ], outs, coef_mlp=mlp)
+        plan.run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.run()
+        e1.record()
+        torch.cuda.synchronize()
+        rc = plan.check()
+        plan.close()
+        ms = e0.elapsed_time(e1) / steps
+        return {"value": cam.n * cam.n / ms * 1e3, "ms_per_step": ms, "return_code": rc}, outs[0]["stokes"]
+
+    slow, img = run(gp, p, native.BL_PREC_FAST, None)
+    out = {"workload": "torus256_slow8_cam512", "unit": "rays/s", "steps": steps,
+           "slow_fast_exact": slow}
+    if coef_mlp is not None:
+        slow_mlp, img_mlp = run(gp, p, native.BL_PREC_MIXED, coef_mlp)
+        slow_mlp["image_rel_l2_vs_exact_fits"] = rel_l2(torch, img_mlp, img)
+        out["slow_mixed_learned"] = slow_mlp
+    fast, img_fast = run(dataclasses.replace(gp, n_snapshots=1), mid, native.BL_PREC_FAST, None)
+    fast["image_rel_l2_slow_vs_this"] = rel_l2(torch, img, img_fast)
+    out["fast_light_middle_snapshot"] = fast
+    del p, mid, img
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_mlp(torch, native, images, device, fast_image, params, train_s, final_loss):
     """Learned coefficients at the 1024^2 point: the model trained on the GPU (default recipe),
     then the image traced with the fused tensor-core transfer (double-float geodesics, FP32
     transfer), next to the plain FP64 form of the same image: speedup and image error
     against the FP64 image, and the exact-fit fast form's error for comparison."""
     from paper_2203_15963_gb300 import coefmodel
-    t0 = time.perf_counter()
-    params, hist = coefmodel.train(device=device)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    final_loss = float(hist[-500:].mean())
     line, img = measure_hires(torch, native, images, native.BL_PREC_FAST, device, steps=3,
                               warmup=2, coef_mlp=params, keep_image=True)
     fp64, img64 = measure_hires(torch, native, images, native.BL_PREC_FP64, device, steps=1,
@@ -502,7 +556,7 @@ def measure_mlp(torch, native, images, device, fast_image):
         "image_rel_l2_vs_fp64_form": rel_l2(torch, img, img64),
         "exact_fast_rel_l2_vs_fp64_form": (rel_l2(torch, fast_image, img64)
                                            if fast_image is not None else None)})
-    del img, img64, params
+    del img, img64
     torch.cuda.empty_cache()
     return line
 

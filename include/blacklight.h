@@ -86,6 +86,18 @@ typedef struct bl_grid {
                                samples inside its domain; all images of one call must pass the
                                same pointer, and the precision must be BL_PREC_MIXED or
                                BL_PREC_FAST (FP32 transfer). */
+    /* Slow light (Sec. 4, "Slow Light"). n_snapshots <= 1: prim is one grid (fast light).
+     * n_snapshots > 1: prim holds that many consecutive grids [n_snapshots][8][...] at
+     * coordinate times t_first + s * dt_snapshots (dt_snapshots > 0); the camera centre is at
+     * coordinate time t_camera, and a sample whose coordinate time along the ray is x^t (the
+     * ray starts at the camera with x^t = 0 and runs backward) takes the fluid data at
+     * t_camera + x^t, linearly between the two adjacent snapshots (time_interp 1) or from the
+     * nearest snapshot (time_interp 0), clamped to the first and last snapshot. */
+    int32_t n_snapshots;
+    int32_t time_interp;
+    double t_first;
+    double dt_snapshots;
+    double t_camera;
 } bl_grid_t;
 
 /* Outputs. stokes is a DEVICE pointer to [4][n][n] (I, Q, U, V; row j = vertical index
@@ -139,7 +151,8 @@ enum { BL_ASYNC = 1u, BL_TIMING = 2u };
  * images must share metric.precision. The rays of all images are traced in waves of at most
  * 2^20 rays, one launch pair per wave, reusing one workspace. workspace may be NULL (the
  * library then allocates stream-ordered scratch and frees it before returning) or a DEVICE
- * buffer the call uses instead: blacklight_workspace_size() bytes give the default waves; a
+ * buffer, 256-byte aligned, the call uses instead: blacklight_workspace_size() bytes give the
+ * default waves; a
  * smaller buffer is accepted and runs smaller waves (BL_EINVAL if it cannot hold one ray).
  * Results do not depend on the wave size. */
 int blacklight_trace_batch(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,

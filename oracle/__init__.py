@@ -52,7 +52,9 @@ class Grid(C.Structure):
                 ("n_phi", C.c_int32), ("r_min", C.c_double), ("r_max", C.c_double),
                 ("gamma_ad", C.c_double), ("r_high", C.c_double), ("r_low", C.c_double),
                 ("mu", C.c_double), ("ne_over_ni", C.c_double), ("sigma_cut", C.c_double),
-                ("rho_unit_cgs", C.c_double), ("mass_msun", C.c_double), ("interp", C.c_int32)]
+                ("rho_unit_cgs", C.c_double), ("mass_msun", C.c_double), ("interp", C.c_int32),
+                ("n_snapshots", C.c_int32), ("time_interp", C.c_int32), ("t_first", C.c_double),
+                ("dt", C.c_double), ("t_camera", C.c_double)]
 
 
 STATUS = {0: "ok", 1: "horizon", 2: "escaped", 3: "max_steps", 4: "underflow", 5: "nan"}
@@ -122,10 +124,15 @@ def metric_struct(met) -> Metric:
 
 
 def grid_struct(gp, prim: np.ndarray) -> Grid:
+    """prim: [8][n_phi][n_theta][n_r], or [n_snapshots][8][...] with gp.n_snapshots > 1."""
     assert prim.dtype == np.float32 and prim.flags.c_contiguous
+    ns = getattr(gp, "n_snapshots", 1)
+    assert prim.size == max(ns, 1) * 8 * gp.n_phi * gp.n_theta * gp.n_r
     return Grid(_p(prim, C.c_float), gp.n_r, gp.n_theta, gp.n_phi, gp.r_min, gp.r_max,
                 gp.gamma_ad, gp.r_high, gp.r_low, gp.mu, gp.ne_over_ni, gp.sigma_cut,
-                gp.rho_unit_cgs, gp.mass_msun, gp.interp)
+                gp.rho_unit_cgs, gp.mass_msun, gp.interp, ns, getattr(gp, "time_interp", 1),
+                getattr(gp, "t_first", 0.0), getattr(gp, "dt_snapshots", 1.0),
+                getattr(gp, "t_camera", 0.0))
 
 
 # ------------------------------------ wrappers ------------------------------------------

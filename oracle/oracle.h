@@ -55,6 +55,13 @@ typedef struct {
     double r_min, r_max;
     double gamma_ad, r_high, r_low, mu, ne_over_ni, sigma_cut, rho_unit_cgs, mass_msun;
     int32_t interp;            /* 1 trilinear, 0 nearest */
+    /* Slow light (Sec. 4, "Slow Light"): prim holds n_snapshots consecutive grids at times
+     * t_first + s dt; a sample at coordinate time x^t is taken at t_camera + x^t, linearly
+     * between the two adjacent snapshots (time_interp 1) or from the nearest one (0), with the
+     * time clamped to the first and last snapshot. n_snapshots <= 1: one grid, no time. */
+    int32_t n_snapshots;
+    int32_t time_interp;
+    double t_first, dt, t_camera;
 } ora_grid;
 
 enum { ORA_OK = 0, ORA_HORIZON = 1, ORA_ESCAPED = 2, ORA_MAX_STEPS = 3, ORA_UNDERFLOW = 4,

@@ -99,7 +99,34 @@ void coefficients(double ne, double th_e, double bg, double nu, double cth, doub
 // Grid sampling (Sec. 2.4): trilinear in (ln r, theta, phi) between cell centres, phi
 // periodic, theta and r clamped to the edge cells; outside [r_min, r_max] there is no data.
 // ---------------------------------------------------------------------------------------
+// One snapshot (spatial sampling only); slow light combines snapshots below.
+static int32_t sample_snapshot(const ora_grid* gr, const float* data, double a, const double x[4],
+                               double prim[8]);
+
 int32_t sample_grid(const ora_grid* gr, double a, const double x[4], double prim[8]) {
+    if (gr->n_snapshots <= 1) return sample_snapshot(gr, gr->prim, a, x, prim);
+    // Slow light: the sample's time t_camera + x^t on the snapshot axis, clamped to its ends
+    const size_t snap = (size_t)8 * gr->n_phi * gr->n_theta * gr->n_r;
+    const int ns = gr->n_snapshots;
+    double s = (gr->t_camera + x[0] - gr->t_first) / gr->dt;
+    if (s < 0.0) s = 0.0;
+    if (s > ns - 1) s = ns - 1;
+    if (gr->time_interp == 0) {
+        const int k = (int)std::floor(s + 0.5);
+        return sample_snapshot(gr, gr->prim + k * snap, a, x, prim);
+    }
+    int k0 = (int)std::floor(s);
+    if (k0 > ns - 2) k0 = ns - 2;
+    const double w = s - k0;
+    double p0[8], p1[8];
+    if (!sample_snapshot(gr, gr->prim + k0 * snap, a, x, p0)) return 0;
+    sample_snapshot(gr, gr->prim + (k0 + 1) * snap, a, x, p1);
+    for (int v = 0; v < 8; ++v) prim[v] = (1.0 - w) * p0[v] + w * p1[v];
+    return 1;
+}
+
+static int32_t sample_snapshot(const ora_grid* gr, const float* data, double a, const double x[4],
+                               double prim[8]) {
     double r, th, ph;
     cks_to_sks_point(x, a, &r, &th, &ph);
     if (!(r >= gr->r_min && r <= gr->r_max)) return 0;
@@ -108,7 +135,7 @@ int32_t sample_grid(const ora_grid* gr, double a, const double x[4], double prim
     double dth = M_PI / nt;
     double dph = 2.0 * M_PI / np;
     auto at = [&](int v, int k, int j, int i) -> double {
-        return (double)gr->prim[(((size_t)v * np + k) * nt + j) * nr + i];
+        return (double)data[(((size_t)v * np + k) * nt + j) * nr + i];
     };
     if (gr->interp == 0) {
         int i = (int)std::floor(std::log(r / gr->r_min) / dlr);

@@ -147,6 +147,15 @@ int check_grid(const bl_grid_t* g, int q) {
     if (!(g->mu > 0.0) || !(g->ne_over_ni > 0.0)) return fail(BL_EINVAL, "grids[%d] composition", q);
     if (!(g->rho_unit_cgs > 0.0) || !(g->mass_msun > 0.0)) return fail(BL_EINVAL, "grids[%d] units", q);
     if (g->interp != 0 && g->interp != 1) return fail(BL_EINVAL, "grids[%d].interp", q);
+    if (g->n_snapshots > 1) {
+        if (!(g->dt_snapshots > 0.0) || !std::isfinite(g->dt_snapshots) ||
+            !std::isfinite(g->t_first) || !std::isfinite(g->t_camera))
+            return fail(BL_EINVAL, "grids[%d]: slow light needs dt_snapshots > 0 and finite times", q);
+        if (g->time_interp != 0 && g->time_interp != 1)
+            return fail(BL_EINVAL, "grids[%d].time_interp", q);
+    } else if (g->n_snapshots < 0) {
+        return fail(BL_EINVAL, "grids[%d].n_snapshots < 0", q);
+    }
     return 0;
 }
 
@@ -187,6 +196,10 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
     d.r_min = g.r_min; d.r_max = g.r_max; d.gamma_ad = g.gamma_ad; d.r_high = g.r_high;
     d.r_low = g.r_low; d.mu = g.mu; d.ne_ni = g.ne_over_ni; d.sigma_cut = g.sigma_cut;
     d.rho_unit = g.rho_unit_cgs;
+    d.n_snap = g.n_snapshots > 1 ? g.n_snapshots : 1;
+    d.time_interp = g.time_interp;
+    d.t_rel0 = g.t_first - g.t_camera;
+    d.dt_snap = g.n_snapshots > 1 ? g.dt_snapshots : 1.0;
     d.length_unit = bl::kG * g.mass_msun * bl::kMsun / (bl::kC * bl::kC);
     d.freq = freq;
     {
@@ -223,6 +236,8 @@ struct DevInfo {
     int geo_blocks[3] = {0, 0, 0};  // per SM, indexed by precision: [fp64, mixed, fast]
     int tr_blocks[3] = {0, 0, 0};
     int tr_mlp_blocks = 0;
+    int tr_slow_blocks[3] = {0, 0, 0};   // slow-light transfer variants
+    int tr_mlp_slow_blocks = 0;
 };
 
 int dev_info(DevInfo& out) {
@@ -238,11 +253,18 @@ int dev_info(DevInfo& out) {
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[0], bl::geodesic_kernel<double, double>, 128, 0));
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[1], bl::geodesic_kernel<float, double>, 128, 0));
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[2], bl::geodesic_kernel<float, bl::df64>, 128, 0));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[0], bl::transfer_kernel<double, double>, 128, 0));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[1], bl::transfer_kernel<float, float>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[0], bl::transfer_kernel<double, double, false>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[1], bl::transfer_kernel<float, float, false>, 128, 0));
         di.tr_blocks[2] = di.tr_blocks[1];
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_blocks, bl::transfer_mlp_kernel<float>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_blocks, bl::transfer_mlp_kernel<float, false>, 128, 0));
         if (di.tr_mlp_blocks < 1) di.tr_mlp_blocks = 1;
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_slow_blocks[0], bl::transfer_kernel<double, double, true>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_slow_blocks[1], bl::transfer_kernel<float, float, true>, 128, 0));
+        di.tr_slow_blocks[2] = di.tr_slow_blocks[1];
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_slow_blocks, bl::transfer_mlp_kernel<float, true>, 128, 0));
+        for (int i = 0; i < 3; ++i)
+            if (di.tr_slow_blocks[i] < 1) di.tr_slow_blocks[i] = 1;
+        if (di.tr_mlp_slow_blocks < 1) di.tr_mlp_slow_blocks = 1;
         for (int i = 0; i < 3; ++i) {
             if (di.geo_blocks[i] < 1) di.geo_blocks[i] = 1;
             if (di.tr_blocks[i] < 1) di.tr_blocks[i] = 1;
@@ -255,6 +277,7 @@ int dev_info(DevInfo& out) {
 // Launch shape of the persistent kernels: CTAs per SM (0 = the occupancy limit).
 struct LaunchCfg {
     int geo_ctas = 0, tr_ctas = 0;
+    bool slow = false;      // some image has several snapshots (slow light)
 };
 
 // The kernel sequence of one trace on prepared workspace whose image descriptors are already
@@ -285,9 +308,11 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
     const int pidx = precision;
     auto pick = [](int want, int occ) { return want > 0 && want < occ ? want : occ; };
     const unsigned geo_grid = (unsigned)(di.sms * pick(cfg.geo_ctas, di.geo_blocks[pidx]));
-    const unsigned tr_grid = (unsigned)(di.sms * pick(cfg.tr_ctas, mlp ? di.tr_mlp_blocks
-                                                                       : di.tr_blocks[pidx]));
+    const int tr_occ = mlp ? (cfg.slow ? di.tr_mlp_slow_blocks : di.tr_mlp_blocks)
+                           : (cfg.slow ? di.tr_slow_blocks[pidx] : di.tr_blocks[pidx]);
+    const unsigned tr_grid = (unsigned)(di.sms * pick(cfg.tr_ctas, tr_occ));
     const int record = transfer ? 1 : 0;
+    const bool slow = cfg.slow;
     for (int64_t w = 0; w < n_waves; ++w) {
         const int64_t b = w * L.wave;
         const int64_t e = b + L.wave < L.rays ? b + L.wave : L.rays;
@@ -311,15 +336,29 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
         BL_CUDA(cudaGetLastError());
         if (timing) BL_CUDA(cudaEventRecord(g_ev[2 * w + 1], st));
         if (transfer) {
+            const float* fpool = (const float*)(ws + L.pool);
+            const double* dpool = (const double*)(ws + L.pool);
             if (mlp) {
-                bl::transfer_mlp_kernel<float><<<tr_grid, 128, 0, st>>>(
-                    d_desc, n_images, b, e, hdr, (const float*)(ws + L.pool), chunks, mlp, ctr);
+                if (slow)
+                    bl::transfer_mlp_kernel<float, true><<<tr_grid, 128, 0, st>>>(
+                        d_desc, n_images, b, e, hdr, fpool, chunks, mlp, ctr);
+                else
+                    bl::transfer_mlp_kernel<float, false><<<tr_grid, 128, 0, st>>>(
+                        d_desc, n_images, b, e, hdr, fpool, chunks, mlp, ctr);
             } else if (precision != BL_PREC_FP64) {
-                bl::transfer_kernel<float, float><<<tr_grid, 128, 0, st>>>(
-                    d_desc, n_images, b, e, hdr, (const float*)(ws + L.pool), chunks, ctr);
+                if (slow)
+                    bl::transfer_kernel<float, float, true><<<tr_grid, 128, 0, st>>>(
+                        d_desc, n_images, b, e, hdr, fpool, chunks, ctr);
+                else
+                    bl::transfer_kernel<float, float, false><<<tr_grid, 128, 0, st>>>(
+                        d_desc, n_images, b, e, hdr, fpool, chunks, ctr);
             } else {
-                bl::transfer_kernel<double, double><<<tr_grid, 128, 0, st>>>(
-                    d_desc, n_images, b, e, hdr, (const double*)(ws + L.pool), chunks, ctr);
+                if (slow)
+                    bl::transfer_kernel<double, double, true><<<tr_grid, 128, 0, st>>>(
+                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr);
+                else
+                    bl::transfer_kernel<double, double, false><<<tr_grid, 128, 0, st>>>(
+                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr);
             }
             ++g_launches;
             BL_CUDA(cudaGetLastError());
@@ -336,7 +375,9 @@ int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* 
                const float* mlp = nullptr, const LaunchCfg& cfg = LaunchCfg()) {
     BL_CUDA(cudaMemcpyAsync(ws + L.descs, descs.data(), sizeof(bl::ImageDesc) * n_images,
                             cudaMemcpyHostToDevice, st));
-    return launch_kernels(n_images, ws, L, precision, transfer, st, timing, mlp, cfg);
+    LaunchCfg c = cfg;
+    for (const auto& d : descs) c.slow = c.slow || d.n_snap > 1;
+    return launch_kernels(n_images, ws, L, precision, transfer, st, timing, mlp, c);
 }
 
 int finish(char* ws, const Layout& L, cudaStream_t st, bool sync) {
@@ -427,6 +468,8 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
     char* ws = (char*)workspace;
     bool own = false;
     if (ws) {
+        if ((uintptr_t)ws % kAlign)
+            return fail(BL_EINVAL, "workspace must be %zu-byte aligned", kAlign);
         // a workspace smaller than the default layout runs the rays in more, smaller waves
         L = fit_layout(n_images, rays, precision, transfer, workspace_bytes);
         if (L.wave < 1)
@@ -487,6 +530,7 @@ struct bl_plan {
     int32_t n_images = 0;
     int precision = 0;
     const float* mlp = nullptr;
+    bool slow = false;
     std::vector<bl::ImageDesc> descs;
     Layout L{};
     char* ws = nullptr;
@@ -518,7 +562,9 @@ int plan_time(bl_plan& P, const LaunchCfg& cfg, cudaStream_t st, float* ms) {
     float best = 1e30f;
     for (int it = 0; it < 3 && rc == 0; ++it) {
         if (it > 0 && (ce = cudaEventRecord(e0, st)) != cudaSuccess) rc = cuda_fail(ce, "record");
-        if (!rc) rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, cfg);
+        LaunchCfg c = cfg;
+        c.slow = P.slow;
+        if (!rc) rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, c);
         if (!rc && it > 0) {
             if ((ce = cudaEventRecord(e1, st)) != cudaSuccess) rc = cuda_fail(ce, "record");
             else if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(ce, "sync");
@@ -561,7 +607,8 @@ int plan_autotune(bl_plan& P, cudaStream_t st) {
     if (t < best * (1.0f - kTuneMargin)) { best = t; order = 1; }
     if ((rc = plan_set_order(P, order, st))) return rc;
     const int geo_max = di.geo_blocks[P.precision];
-    const int tr_max = P.mlp ? di.tr_mlp_blocks : di.tr_blocks[P.precision];
+    const int tr_max = P.mlp ? (P.slow ? di.tr_mlp_slow_blocks : di.tr_mlp_blocks)
+                             : (P.slow ? di.tr_slow_blocks[P.precision] : di.tr_blocks[P.precision]);
     int geo_best = geo_max;
     for (int c = 1; c < geo_max; ++c) {
         LaunchCfg trial = cfg;
@@ -603,7 +650,9 @@ int plan_capture(bl_plan& P, cudaStream_t user) {
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamBeginCapture");
     }
     if (!rc) {
-        rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, P.cfg);
+        LaunchCfg c = P.cfg;
+        c.slow = P.slow;
+        rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, c);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(st, &g);
         if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamEndCapture");
@@ -934,6 +983,7 @@ int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_m
     int64_t off = 0;
     for (int q = 0; q < n_images; ++q) {
         fill_desc(P->descs[q], cams[q], mets[q], grids[q], freqs_hz[q], outs[q], off);
+        P->slow = P->slow || P->descs[q].n_snap > 1;
         off += (int64_t)cams[q].n * cams[q].n;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -986,7 +1036,9 @@ int blacklight_plan_config(const bl_plan_t* plan, bl_launch_config_t* out) {
     int rc = dev_info(di);
     if (rc) return rc;
     const int geo_max = di.geo_blocks[plan->precision];
-    const int tr_max = plan->mlp ? di.tr_mlp_blocks : di.tr_blocks[plan->precision];
+    const int tr_max = plan->mlp ? (plan->slow ? di.tr_mlp_slow_blocks : di.tr_mlp_blocks)
+                                 : (plan->slow ? di.tr_slow_blocks[plan->precision]
+                                               : di.tr_blocks[plan->precision]);
     out->ray_order = plan->order;
     out->geo_ctas_per_sm = plan->cfg.geo_ctas > 0 && plan->cfg.geo_ctas < geo_max ? plan->cfg.geo_ctas : geo_max;
     out->tr_ctas_per_sm = plan->cfg.tr_ctas > 0 && plan->cfg.tr_ctas < tr_max ? plan->cfg.tr_ctas : tr_max;
@@ -1038,7 +1090,8 @@ int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const 
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t npix = (size_t)cam->n * cam->n;
-    const size_t gbytes = sizeof(float) * 8 * (size_t)grid->n_r * grid->n_theta * grid->n_phi;
+    const size_t gbytes = sizeof(float) * 8 * (size_t)grid->n_r * grid->n_theta * grid->n_phi *
+                          (size_t)(grid->n_snapshots > 1 ? grid->n_snapshots : 1);
     const size_t sbytes = 4 * npix * (out->dtype == 0 ? sizeof(double) : sizeof(float));
     char* dev = nullptr;
     const size_t off_s = align_up(gbytes), off_st = off_s + align_up(sbytes),

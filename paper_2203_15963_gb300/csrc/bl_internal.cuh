@@ -8,7 +8,7 @@ namespace bl {
 // sample position x,y,z and covariant k_x,k_y,k_z; the node on the sample's camera side
 // (same 6 values); the segment's affine length. k_t is constant per ray (Sec. 2.2) and is
 // kept in the ray header.
-constexpr int kRecVals = 13;
+constexpr int kRecVals = 13;   // values of a record the transfer uses; value 13 is the time
 template <class R> struct RecStride;
 template <> struct RecStride<double> { static constexpr int v = 14; };   // 112 B, 16-B aligned
 template <> struct RecStride<float> { static constexpr int v = 16; };    // 64 B
@@ -28,6 +28,10 @@ struct ImageDesc {
     const float* prim;
     int32_t nr, nt, nph, interp;
     double r_min, r_max, gamma_ad, r_high, r_low, mu, ne_ni, sigma_cut, rho_unit, length_unit;
+    // slow light: n_snap snapshots, spacing dt_snap; t_rel0 = t_first - t_camera, so that a
+    // sample at ray time x^t sits at (x^t - t_rel0) / dt_snap on the snapshot axis
+    int32_t n_snap, time_interp;
+    double t_rel0, dt_snap;
     double freq;
     // outputs
     void* stokes;

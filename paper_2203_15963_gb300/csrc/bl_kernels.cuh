@@ -409,17 +409,34 @@ __device__ __forceinline__ bool append_record(const RecordSink<R>& S, int64_t ra
     }
     const int64_t idx = (int64_t)tab[ch] * kChunk + slot;
     R* rec = S.pool + idx * RecStride<R>::v;
-    rec[0] = to_rec<R>(ys[1]); rec[1] = to_rec<R>(ys[2]); rec[2] = to_rec<R>(ys[3]);
-    rec[3] = to_rec<R>(ys[5]); rec[4] = to_rec<R>(ys[6]); rec[5] = to_rec<R>(ys[7]);
-    rec[6] = to_rec<R>(yn[1]); rec[7] = to_rec<R>(yn[2]); rec[8] = to_rec<R>(yn[3]);
-    rec[9] = to_rec<R>(yn[5]); rec[10] = to_rec<R>(yn[6]); rec[11] = to_rec<R>(yn[7]);
-    rec[12] = (R)dl;
+    // the record is assembled in registers and stored as 16-byte vectors (records are 64 B
+    // (float) or 112 B (double) apart from a 256-byte aligned pool)
+    const R v[14] = {to_rec<R>(ys[1]), to_rec<R>(ys[2]), to_rec<R>(ys[3]), to_rec<R>(ys[5]),
+                     to_rec<R>(ys[6]), to_rec<R>(ys[7]), to_rec<R>(yn[1]), to_rec<R>(yn[2]),
+                     to_rec<R>(yn[3]), to_rec<R>(yn[5]), to_rec<R>(yn[6]), to_rec<R>(yn[7]),
+                     (R)dl, to_rec<R>(ys[0])};   // value 13: coordinate time (slow light)
+    if constexpr (std::is_same<R, float>::value) {
+        float4* q = reinterpret_cast<float4*>(rec);
+        q[0] = make_float4(v[0], v[1], v[2], v[3]);
+        q[1] = make_float4(v[4], v[5], v[6], v[7]);
+        q[2] = make_float4(v[8], v[9], v[10], v[11]);
+        q[3] = make_float4(v[12], v[13], 0.0f, 0.0f);
+    } else {
+        double2* q = reinterpret_cast<double2*>(rec);
+#pragma unroll
+        for (int i = 0; i < 7; ++i) q[i] = make_double2(v[2 * i], v[2 * i + 1]);
+    }
     ++nrec;
     return true;
 }
 
+// Resident CTAs per SM the geodesic kernel is compiled for (the register budget follows:
+// 65536 / (128 x this)).
+#ifndef BL_GEO_MIN_CTAS
+#define BL_GEO_MIN_CTAS 3
+#endif
 template <class R, class G>
-__global__ void __launch_bounds__(128, 3) geodesic_kernel(const ImageDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const ImageDesc* __restrict__ imgs,
                                                           int n_images, int64_t ray_begin,
                                                           int64_t ray_end,
                                                           RayHdr* __restrict__ hdr,
@@ -786,9 +803,9 @@ struct Plasma {
     T ne, th, bg, bsq;
 };
 
-template <class T>
-__device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], const KSGeom<T>& G,
-                                          Plasma<T>& P) {
+template <class T, bool kSlow = false>
+__device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t,
+                                          const KSGeom<T>& G, Plasma<T>& P) {
     const T a = ic<T>(im, kcSpin);
     const T r = G.r;
     if (!(r >= ic<T>(im, kcRmin) && r <= ic<T>(im, kcRmax))) return false;
@@ -802,8 +819,26 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], con
     if (ph < T(0)) ph += twopi;
     if (ph >= twopi) ph -= twopi;
     const int nr = im.nr, nt = im.nt, np = im.nph;
-    const float* __restrict__ prim = im.prim;
     const size_t plane = (size_t)np * nt * nr;
+    // slow light: the two snapshots around the sample's time and the weight of the second
+    const float* __restrict__ prim = im.prim;
+    const float* __restrict__ prim1 = nullptr;
+    T wt1 = T(0);
+    if (kSlow && im.n_snap > 1) {
+        const int ns = im.n_snap;
+        T fs = (t - (T)im.t_rel0) / (T)im.dt_snap;
+        fs = fs < T(0) ? T(0) : (fs > T(ns - 1) ? T(ns - 1) : fs);
+        int s0;
+        if (im.time_interp == 0) {
+            s0 = (int)floor(fs + T(0.5));
+        } else {
+            s0 = (int)floor(fs);
+            if (s0 > ns - 2) s0 = ns - 2;
+            wt1 = fs - T(s0);
+            prim1 = prim + (size_t)(s0 + 1) * 8 * plane;
+        }
+        prim += (size_t)s0 * 8 * plane;
+    }
     T pv[8];
     const T dlr = ic<T>(im, kcDlr);
     const T lrmin = ic<T>(im, kcLogRmin);
@@ -819,6 +854,11 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], con
         const size_t base = ((size_t)k * nt + j) * nr + i;
 #pragma unroll
         for (int v = 0; v < 8; ++v) pv[v] = (T)__ldg(prim + v * plane + base);
+        if (kSlow && prim1) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v)
+                pv[v] = (T(1) - wt1) * pv[v] + wt1 * (T)__ldg(prim1 + v * plane + base);
+        }
     } else {
         int i0, j0;
         T wr, wt;
@@ -854,13 +894,18 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], con
         const T w010 = (T(1) - wp) * wt * (T(1) - wr), w011 = (T(1) - wp) * wt * wr;
         const T w100 = wp * (T(1) - wt) * (T(1) - wr), w101 = wp * (T(1) - wt) * wr;
         const T w110 = wp * wt * (T(1) - wr), w111 = wp * wt * wr;
+        auto tri = [&](const float* __restrict__ pp) -> T {
+            return w000 * (T)__ldg(pp + o00 + i0) + w001 * (T)__ldg(pp + o00 + i1) +
+                   w010 * (T)__ldg(pp + o01 + i0) + w011 * (T)__ldg(pp + o01 + i1) +
+                   w100 * (T)__ldg(pp + o10 + i0) + w101 * (T)__ldg(pp + o10 + i1) +
+                   w110 * (T)__ldg(pp + o11 + i0) + w111 * (T)__ldg(pp + o11 + i1);
+        };
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-            const float* pp = prim + v * plane;
-            pv[v] = w000 * (T)__ldg(pp + o00 + i0) + w001 * (T)__ldg(pp + o00 + i1) +
-                    w010 * (T)__ldg(pp + o01 + i0) + w011 * (T)__ldg(pp + o01 + i1) +
-                    w100 * (T)__ldg(pp + o10 + i0) + w101 * (T)__ldg(pp + o10 + i1) +
-                    w110 * (T)__ldg(pp + o11 + i0) + w111 * (T)__ldg(pp + o11 + i1);
+        for (int v = 0; v < 8; ++v) pv[v] = tri(prim + v * plane);
+        if (kSlow && prim1) {
+#pragma unroll
+            for (int v = 0; v < 8; ++v)
+                pv[v] = (T(1) - wt1) * pv[v] + wt1 * tri(prim1 + v * plane);
         }
     }
     // spherical -> Cartesian KS vectors (Jacobian columns d x^a / d(r, theta, phi))
@@ -1035,8 +1080,11 @@ __device__ __forceinline__ const R* record_ptr(const R* __restrict__ pool, const
 // exact constant-coefficient Stokes step, and S -> N. A lane whose ray is done reads out the
 // Stokes parameters in the camera basis (H, V) and takes the next ray.
 // ---------------------------------------------------------------------------------------
-template <class T, class R>
-__global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restrict__ imgs,
+#ifndef BL_TR_MIN_CTAS
+#define BL_TR_MIN_CTAS 1
+#endif
+template <class T, class R, bool kSlow>
+__global__ void __launch_bounds__(128, BL_TR_MIN_CTAS) transfer_kernel(const ImageDesc* __restrict__ imgs,
                                                        int n_images, int64_t ray_begin,
                                                        int64_t ray_end,
                                                        const RayHdr* __restrict__ hdr,
@@ -1100,6 +1148,7 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
         T cur[kRecVals];
 #pragma unroll
         for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
+        const T nxt_t = (T)nxt[13];   // the sample's coordinate time
         if (idx > 0) load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
         if (started) {
             // merged N half-steps from the previous sample to this one
@@ -1115,7 +1164,7 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
             KSGeom<T> G;
             ks_geom<T>(xs[0], xs[1], xs[2], a, m, flat, false, G);
             Plasma<T> P;
-            if (plasma_at<T>(im, xs, G, P)) {
+            if (plasma_at<T, kSlow>(im, xs, nxt_t, G, P)) {
                 const T kl[4] = {kt, cur[3], cur[4], cur[5]};
                 T ku[4];
                 raise4(G, kl, ku);
@@ -1184,7 +1233,7 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
 // 128-sample tensor-core tile of the perceptron, so the coefficient evaluation of the whole
 // CTA is three chained MMAs. Samples outside the model's domain use the exact fits.
 // ---------------------------------------------------------------------------------------
-template <class R>
+template <class R, bool kSlow>
 __global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __restrict__ imgs,
                                                            int n_images, int64_t ray_begin,
                                                            int64_t ray_end,
@@ -1260,6 +1309,7 @@ __global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __re
         if (work) {
 #pragma unroll
             for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
+            const T ts = (T)nxt[13];   // the sample's coordinate time
             if (idx > 0) load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
             if (started) {
                 T A0[4][4], A1[4][4];
@@ -1271,7 +1321,7 @@ __global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __re
             }
             const T xs[3] = {cur[0], cur[1], cur[2]};
             ks_geom<T>(xs[0], xs[1], xs[2], a, m, flat, false, G);
-            samp = plasma_at<T>(im, xs, G, P);
+            samp = plasma_at<T, kSlow>(im, xs, ts, G, P);
             if (samp) {
                 kl[0] = kt; kl[1] = cur[3]; kl[2] = cur[4]; kl[3] = cur[5];
                 raise4(G, kl, ku);

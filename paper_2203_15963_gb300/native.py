@@ -65,7 +65,9 @@ class Grid(C.Structure):
                 ("r_max", C.c_double), ("gamma_ad", C.c_double), ("r_high", C.c_double),
                 ("r_low", C.c_double), ("mu", C.c_double), ("ne_over_ni", C.c_double),
                 ("sigma_cut", C.c_double), ("rho_unit_cgs", C.c_double),
-                ("mass_msun", C.c_double), ("interp", C.c_int32), ("coef_mlp", C.c_void_p)]
+                ("mass_msun", C.c_double), ("interp", C.c_int32), ("coef_mlp", C.c_void_p),
+                ("n_snapshots", C.c_int32), ("time_interp", C.c_int32), ("t_first", C.c_double),
+                ("dt_snapshots", C.c_double), ("t_camera", C.c_double)]
 
 
 class MlpTrain(C.Structure):
@@ -204,7 +206,10 @@ def grid_struct(gp, prim_ptr, coef_mlp=None) -> Grid:
     return Grid(C.sizeof(Grid), prim_ptr, gp.n_r, gp.n_theta, gp.n_phi, gp.r_min, gp.r_max,
                 gp.gamma_ad, gp.r_high, gp.r_low, gp.mu, gp.ne_over_ni, gp.sigma_cut,
                 gp.rho_unit_cgs, gp.mass_msun, gp.interp,
-                None if coef_mlp is None else coef_mlp.data_ptr())
+                None if coef_mlp is None else coef_mlp.data_ptr(),
+                getattr(gp, "n_snapshots", 1), getattr(gp, "time_interp", 1),
+                getattr(gp, "t_first", 0.0), getattr(gp, "dt_snapshots", 1.0),
+                getattr(gp, "t_camera", 0.0))
 
 
 def out_struct(stokes=None, status=None, steps=None, end_state=None, samples=None) -> Out:

@@ -79,6 +79,12 @@ class GridParams:
     rho_unit_cgs: float = 1e-17
     mass_msun: float = 4.152e6
     interp: int = 1                # 1 = trilinear, 0 = nearest
+    # slow light (Sec. 4): n_snapshots grids at t_first + s dt_snapshots, camera at t_camera
+    n_snapshots: int = 1
+    time_interp: int = 1           # 1 = linear in time, 0 = nearest snapshot
+    t_first: float = 0.0
+    dt_snapshots: float = 1.0
+    t_camera: float = 0.0
 
 
 def r_faces(gp: GridParams) -> np.ndarray:
@@ -192,6 +198,30 @@ def make_torus(gp: GridParams, spin: float, seed: int, noise: float = 0.1,
     return prim
 
 
+def make_torus_series(gp: GridParams, spin: float, seed: int, n_snapshots: int, dt: float,
+                      noise: float = 0.1, mass: float = 1.0) -> np.ndarray:
+    """float32 [n_snapshots][8][n_phi][n_theta][n_r]: the torus of make_torus whose density
+    (and internal energy) noise is carried around by the Keplerian flow, snapshot s showing it
+    rotated by Omega(r) s dt, Omega = 1/(r^1.5 + a), rounded to whole cells in phi per radial
+    shell. The smooth parts (velocity, field) are axisymmetric and the same in every snapshot."""
+    base = make_torus(gp, spin, seed, noise, mass)
+    out = np.empty((n_snapshots,) + base.shape, dtype=np.float32)
+    rc = r_centres(gp)
+    omega = 1.0 / (rc ** 1.5 + spin)
+    dph = 2.0 * math.pi / gp.n_phi
+    k = np.arange(gp.n_phi)
+    for s in range(n_snapshots):
+        out[s] = base
+        shift = np.rint(omega * s * dt / dph).astype(np.int64)           # [n_r]
+        src = (k[:, None] - shift[None, :]) % gp.n_phi                  # [n_phi][n_r]
+        ridx = np.arange(gp.n_r)[None, :]
+        for v in (0, 1):
+            f = base[v]                                                  # [phi][theta][r]
+            out[s, v] = f[src[:, None, :].repeat(gp.n_theta, 1),
+                          np.arange(gp.n_theta)[None, :, None], ridx[:, None, :]]
+    return out
+
+
 def grid_params_for(n_r: int, n_theta: int, n_phi: int) -> GridParams:
     return GridParams(n_r=n_r, n_theta=n_theta, n_phi=n_phi)
 
@@ -208,14 +238,29 @@ WORKLOADS = {
     # 1024x1024 camera, 512x256x256 grid (1 GiB of float32), a = 0.94, 230 GHz
     "torus512_cam1024": dict(grid=(512, 256, 256), n=1024, spins=(0.94,), incs=(17.0,),
                              freqs=(230e9,), seed_index=3),
+    # slow light: 8 snapshots 10 M apart of the 256x128x128 torus, 512x512 camera, a = 0.94,
+    # i = 60 deg, 230 GHz, camera time 1035 M (samples near r ~ 10-20 M fall inside the span)
+    "torus256_slow8_cam512": dict(grid=(256, 128, 128), n=512, spins=(0.94,), incs=(60.0,),
+                                  freqs=(230e9,), seed_index=4, snapshots=8, dt=10.0,
+                                  t_camera=1035.0),
+    # small slow-light parity case: 4 snapshots of the 64x32x32 torus, 32x32 camera
+    "torus64_slow4_cam32": dict(grid=(64, 32, 32), n=32, spins=(0.9,), incs=(60.0,),
+                                freqs=(230e9,), seed_index=5, snapshots=4, dt=10.0,
+                                t_camera=1015.0),
 }
 
 
 def workload_inputs(name: str, spin: float, inc_deg: float, n: int | None = None):
-    """Camera, metric and grid parameters plus the seeded torus for one image."""
+    """Camera, metric and grid parameters plus the seeded torus (or snapshot series) for one
+    image."""
     w = WORKLOADS[name]
     gp = grid_params_for(*w["grid"])
     cam = Camera(theta=math.radians(inc_deg), n=n if n is not None else w["n"])
     met = Metric(spin=spin)
-    prim = make_torus(gp, spin, BASE_SEED + w["seed_index"])
+    if w.get("snapshots", 1) > 1:
+        gp = dataclasses.replace(gp, n_snapshots=w["snapshots"], time_interp=1, t_first=0.0,
+                                 dt_snapshots=w["dt"], t_camera=w["t_camera"])
+        prim = make_torus_series(gp, spin, BASE_SEED + w["seed_index"], w["snapshots"], w["dt"])
+    else:
+        prim = make_torus(gp, spin, BASE_SEED + w["seed_index"])
     return cam, met, gp, prim

@@ -324,6 +324,12 @@ def test_invalid_arguments_are_rejected():
     ws = torch.empty(1024, dtype=torch.uint8, device=DEV)
     with pytest.raises(native.BlacklightError):
         native.blacklight_trace_batch([cam], [met], [gp], [p], [230e9], [out], workspace=ws)
+    # a workspace that is not 256-byte aligned is refused before anything is launched
+    big = torch.empty(native.blacklight_workspace_size([cam], [met]) + 512, dtype=torch.uint8,
+                      device=DEV)
+    with pytest.raises(native.BlacklightError) as ei:
+        native.blacklight_trace_batch([cam], [met], [gp], [p], [230e9], [out], workspace=big[16:])
+    assert ei.value.code == -1 and "aligned" in str(ei.value)
 
 
 def test_max_steps_reported_per_ray():
