@@ -96,9 +96,12 @@ def lib():
         L.ora_fluid_frame.argtypes = [_D] * 6
         L.ora_n_to_s.argtypes = [_D] * 6
         L.ora_s_to_n.argtypes = [_D] * 5
-        L.ora_trace.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Grid),
-                                C.c_double, C.c_int64, _I32, C.c_int32, _D, _I32, _I64, _I64,
-                                _I64, _D]
+        L.ora_trace.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Grid), C.c_double,
+                                C.c_int64, C.POINTER(C.c_int32), C.c_int32, _D,
+                                C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int64), _D, C.c_int32, _D]
+        L.ora_unpolarized_step.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
+        L.ora_unpolarized_step.restype = C.c_double
         _lib = L
     return _lib
 
@@ -269,8 +272,17 @@ def s_to_n(e1, e2, s):
     return nre.reshape(4, 4), nim.reshape(4, 4)
 
 
-def trace(cam, met, gp, prim, freq, pix=None, nthreads=0):
-    """Trace pixels (flat indices j*n+i; default all). Returns a dict of numpy arrays."""
+AUX_COUNT = 26
+
+
+def unpolarized_step(j, alpha, dl, i0):
+    return lib().ora_unpolarized_step(float(j), float(alpha), float(dl), float(i0))
+
+
+def trace(cam, met, gp, prim, freq, pix=None, nthreads=0, unpolarized=False, aux=False):
+    """Trace pixels (flat indices j*n+i; default all). Returns a dict of numpy arrays; with
+    unpolarized=True the transfer is Eq. unpolarized (Stokes I only); with aux=True the dict
+    also holds the auxiliary images, aux [n][26]."""
     cs, ms, gs = camera_struct(cam), metric_struct(met), grid_struct(gp, prim)
     if pix is None:
         pix = np.arange(cam.n * cam.n, dtype=np.int32)
@@ -282,11 +294,16 @@ def trace(cam, met, gp, prim, freq, pix=None, nthreads=0):
     att = np.zeros(n, dtype=np.int64)
     acc = np.zeros(n, dtype=np.int64)
     smp = np.zeros(n, dtype=np.int64)
+    ax = _f64(AUX_COUNT * n) if aux else None
     lib().ora_trace(C.byref(cs), C.byref(ms), C.byref(gs), float(freq), n, _p(pix, C.c_int32),
                     int(nthreads), _p(st), _p(status, C.c_int32), _p(att, C.c_int64),
-                    _p(acc, C.c_int64), _p(smp, C.c_int64), _p(end))
-    return dict(stokes=st.reshape(n, 4), end=end.reshape(n, 8), status=status, attempts=att,
-                accepted=acc, samples=smp, pix=pix)
+                    _p(acc, C.c_int64), _p(smp, C.c_int64), _p(end), 1 if unpolarized else 0,
+                    _p(ax) if aux else None)
+    out = dict(stokes=st.reshape(n, 4), end=end.reshape(n, 8), status=status, attempts=att,
+               accepted=acc, samples=smp, pix=pix)
+    if aux:
+        out["aux"] = ax.reshape(n, AUX_COUNT)
+    return out
 
 
 def os_cores() -> int:

@@ -89,6 +89,11 @@ int32_t ora_geodesic(const ora_metric* met, double r_cam, const double y0[8], do
                      int64_t* n_path);
 
 /* ---- sampling, plasma, coefficients, transfer (Secs. 2.3-2.5) ---- */
+/* auxiliary values per pixel of ora_trace (out_aux [npix][ORA_AUX_COUNT]); the list is in
+ * radiation.cpp above trace_pixel */
+#define ORA_AUX_COUNT 26
+/* Eq. unpolarized: one constant-coefficient segment */
+double ora_unpolarized_step(double j, double alpha, double dl, double i0);
 int32_t ora_sample_grid(const ora_grid* grid, double spin, const double x[4], double prim[8]);
 int32_t ora_plasma(const ora_grid* grid, const ora_metric* met, const double x[4],
                    double u[4], double b[4], double* ne, double* theta_e, double* b_gauss);
@@ -121,7 +126,7 @@ void ora_s_to_n(const double e1[4], const double e2[4], const double s[4], doubl
 void ora_trace(const ora_camera* cam, const ora_metric* met, const ora_grid* grid, double freq,
                int64_t npix, const int32_t* pix, int32_t nthreads, double* out_stokes,
                int32_t* out_status, int64_t* out_attempts, int64_t* out_accepted,
-               int64_t* out_samples, double* out_end);
+               int64_t* out_samples, double* out_end, int32_t unpolarized, double* out_aux);
 
 #ifdef __cplusplus
 }

@@ -186,7 +186,7 @@ static int32_t sample_snapshot(const ora_grid* gr, const float* data, double a, 
 // u, b are contravariant CKS components.
 // ---------------------------------------------------------------------------------------
 int32_t plasma(const ora_grid* gr, const ora_metric* met, const double x[4], double u[4],
-               double b[4], double* ne, double* th_e, double* bg) {
+               double b[4], double* ne, double* th_e, double* bg, double* qv) {
     const double m = met->mass, a = met->spin;
     double prim[8];
     if (!sample_grid(gr, a, x, prim)) return 0;
@@ -228,7 +228,24 @@ int32_t plasma(const ora_grid* gr, const ora_metric* met, const double x[4], dou
     *th_e = te;
     *ne = rho * gr->rho_unit_cgs / (gr->mu * M_PROTON) / (1.0 + 1.0 / rr);
     *bg = std::sqrt(bsq) * C_LIGHT * std::sqrt(4.0 * M_PI * gr->rho_unit_cgs);
+    if (qv) {   // the tracked quantities of the auxiliary images (Sec. 4)
+        qv[0] = rho; qv[1] = *ne; qv[2] = p; qv[3] = te; qv[4] = *bg; qv[5] = sigma;
+        qv[6] = beta_inv;
+    }
     return 1;
+}
+
+// ---------------------------------------------------------------------------------------
+// Unpolarized segment (Eq. unpolarized): exact solution of dI/dl = j - alpha I over dl with
+// constant coefficients; alpha dl >= 100 gives j / alpha, alpha = 0 gives I + j dl.
+// ---------------------------------------------------------------------------------------
+double unpolarized_step(double j, double alpha, double dl, double i0) {
+    if (alpha > 0.0) {
+        const double dtau = alpha * dl;
+        if (dtau >= 100.0) return j / alpha;
+        return std::exp(-dtau) * (i0 + std::expm1(dtau) * j / alpha);
+    }
+    return i0 + j * dl;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -578,10 +595,23 @@ struct PixelResult {
     double end[8];
     int32_t status;
     int64_t attempts, accepted, samples;
+    double aux[ORA_AUX_COUNT];
 };
 
+// Auxiliary images (Sec. 4, "Auxiliary Images"), per pixel:
+//   [0] Kerr-Schild time from the geodesic's termination to the camera, -x^t at the end;
+//   [1] proper length of the whole geodesic, sum over steps of |h| (g_pq k^p k^q)^1/2 at the
+//       step's midpoint; [2] affine parameter, sum of |h|;
+//   [3] I_j = integral of j_I dl, [4] tau = integral of alpha_I dl, over the samples, with the
+//       unpolarized invariants per unit affine parameter of the transfer;
+//   [5 + k]  <q_k>_lambda = integral q dl / [2];
+//   [12 + k] <q_k>_Ij = integral q j_I dl / I_j (0 if I_j = 0);
+//   [19 + k] <q_k>_tau, the solution of d<q>/dtau = q - <q> from the source end (0 there),
+//            exact for constant q over each sample: <q> -> e^-dtau <q> + (1 - e^-dtau) q;
+//   q = rho (code units), n_e, p (code units), Theta_e, B (gauss), sigma, beta^-1. Samples
+//   without plasma (outside the grid or cut) contribute q = 0 and no emission or absorption.
 static void trace_pixel(const ora_camera* cam, const ora_metric* met, const ora_grid* gr,
-                        double freq, int pix, PixelResult& res) {
+                        double freq, int pix, int unpolarized, PixelResult& res) {
     const int i = pix % cam->n, j = pix / cam->n;
     double x[4], k[4], hv[4], vv[4], nnorm, r_cam, ucam[4];
     camera_pixel(cam, met, i, j, x, k, hv, vv, &nnorm, &r_cam, ucam);
@@ -592,6 +622,13 @@ static void trace_pixel(const ora_camera* cam, const ora_metric* met, const ora_
     std::vector<Sample> samples;
     make_samples(met, gr, steps, samples);
     res.samples = (int64_t)samples.size();
+    for (int a = 0; a < ORA_AUX_COUNT; ++a) res.aux[a] = 0.0;
+    res.aux[0] = -res.end[0];
+    for (const Step& st : steps) {
+        res.aux[1] += std::fabs(st.h) * proper_length_rate(met, st.ym);
+        res.aux[2] += std::fabs(st.h);
+    }
+    double qlam[7] = {0}, qij[7] = {0}, qtau[7] = {0}, i_unpol = 0.0;
 
     const double length_unit = G_NEWTON * gr->mass_msun * M_SUN / (C_LIGHT * C_LIGHT);
     double nre[16] = {0}, nim[16] = {0};
@@ -600,13 +637,13 @@ static void trace_pixel(const ora_camera* cam, const ora_metric* met, const ora_
     // Forward order: from the source end (last sample) to the camera.
     for (int m = ns - 1; m >= 0; --m) {
         const Sample& sp = samples[m];
-        if (m < ns - 1 && started) {
+        if (!unpolarized && m < ns - 1 && started) {
             const Sample& prev = samples[m + 1];
             double h = 0.5 * (prev.dl + sp.dl);
             transport_step(met, prev.x, prev.k, prev.xn, prev.kn, h, nre, nim);
         }
-        double u[4], b[4], ne, te, bg;
-        if (!plasma(gr, met, sp.x, u, b, &ne, &te, &bg)) continue;
+        double u[4], b[4], ne, te, bg, qv[7];
+        if (!plasma(gr, met, sp.x, u, b, &ne, &te, &bg, qv)) continue;
         double glo[16], ghi[16];
         metric_cks(sp.x, met->mass, met->spin, met->flat, glo, ghi);
         double kup[4];
@@ -629,6 +666,20 @@ static void trace_pixel(const ora_camera* cam, const ora_metric* met, const ora_
         double coef[8] = {co[0] * gfac * gfac * gfac * path, co[1] * gfac * gfac * gfac * path,
                           co[2] * gfac * gfac * gfac * path, co[3] * path, co[4] * path,
                           co[5] * path, co[6] * path, co[7] * path};
+        // auxiliary accumulations (unpolarized invariants j_I = coef[0], alpha_I = coef[3])
+        const double dtau = coef[3] * sp.dl;
+        res.aux[3] += coef[0] * sp.dl;
+        res.aux[4] += dtau;
+        for (int q = 0; q < 7; ++q) {
+            qlam[q] += qv[q] * sp.dl;
+            qij[q] += qv[q] * coef[0] * sp.dl;
+            qtau[q] = std::exp(-dtau) * qtau[q] - std::expm1(-dtau) * qv[q];
+        }
+        if (unpolarized) {
+            i_unpol = unpolarized_step(coef[0], coef[3], sp.dl, i_unpol);
+            started = true;
+            continue;
+        }
         double e1[4], e2[4];
         tetrad(glo, u, kup, b, e1, e2);
         double s[4], s1[4];
@@ -636,6 +687,16 @@ static void trace_pixel(const ora_camera* cam, const ora_metric* met, const ora_
         stokes_step(coef, s, sp.dl, s1);
         s_to_n(e1, e2, s1, nre, nim);
         started = true;
+    }
+    for (int q = 0; q < 7; ++q) {
+        res.aux[5 + q] = res.aux[2] > 0.0 ? qlam[q] / res.aux[2] : 0.0;
+        res.aux[12 + q] = res.aux[3] > 0.0 ? qij[q] / res.aux[3] : 0.0;
+        res.aux[19 + q] = qtau[q];
+    }
+    if (unpolarized) {
+        res.stokes[0] = i_unpol;
+        res.stokes[1] = res.stokes[2] = res.stokes[3] = 0.0;
+        return;
     }
     if (started && ns > 0) {
         const Sample& last = samples[0];
@@ -657,7 +718,10 @@ int32_t ora_sample_grid(const ora_grid* grid, double spin, const double x[4], do
 }
 int32_t ora_plasma(const ora_grid* grid, const ora_metric* met, const double x[4], double u[4],
                    double b[4], double* ne, double* theta_e, double* b_gauss) {
-    return ora::plasma(grid, met, x, u, b, ne, theta_e, b_gauss);
+    return ora::plasma(grid, met, x, u, b, ne, theta_e, b_gauss, nullptr);
+}
+double ora_unpolarized_step(double j, double alpha, double dl, double i0) {
+    return ora::unpolarized_step(j, alpha, dl, i0);
 }
 double ora_bessel_kx(double nu, double x) { return ora::bessel_kx(nu, x); }
 void ora_coefficients(double ne, double theta_e, double b_gauss, double nu, double cos_theta,
@@ -711,7 +775,7 @@ void ora_s_to_n(const double e1[4], const double e2[4], const double s[4], doubl
 void ora_trace(const ora_camera* cam, const ora_metric* met, const ora_grid* grid, double freq,
                int64_t npix, const int32_t* pix, int32_t nthreads, double* out_stokes,
                int32_t* out_status, int64_t* out_attempts, int64_t* out_accepted,
-               int64_t* out_samples, double* out_end) {
+               int64_t* out_samples, double* out_end, int32_t unpolarized, double* out_aux) {
     int nt = nthreads > 0 ? nthreads : (int)std::thread::hardware_concurrency();
     if (nt < 1) nt = 1;
     std::atomic<int64_t> next(0);
@@ -720,8 +784,10 @@ void ora_trace(const ora_camera* cam, const ora_metric* met, const ora_grid* gri
             int64_t q = next.fetch_add(1);
             if (q >= npix) break;
             ora::PixelResult r;
-            ora::trace_pixel(cam, met, grid, freq, pix[q], r);
+            ora::trace_pixel(cam, met, grid, freq, pix[q], unpolarized, r);
             for (int s = 0; s < 4; ++s) out_stokes[4 * q + s] = r.stokes[s];
+            if (out_aux)
+                for (int a = 0; a < ORA_AUX_COUNT; ++a) out_aux[ORA_AUX_COUNT * q + a] = r.aux[a];
             if (out_end)
                 for (int s = 0; s < 8; ++s) out_end[8 * q + s] = r.end[s];
             if (out_status) out_status[q] = r.status;
