@@ -113,7 +113,22 @@ typedef struct bl_out {
     int32_t* steps;
     double* end_state;
     int32_t* samples;
+    void* aux;              /* optional DEVICE [BL_AUX_COUNT][n][n] auxiliary images (Sec. 4,
+                               "Auxiliary Images"), same dtype as stokes, or NULL */
 } bl_out_t;
+
+/* Auxiliary images, planes of bl_out_t.aux:
+ *   0 Kerr-Schild time from the geodesic's termination to the camera (-x^t at the end)
+ *   1 proper length of the geodesic, sum over steps of |dl| (g_pq k^p k^q)^1/2 at the step's
+ *     midpoint;  2 elapsed affine parameter, sum of |dl|
+ *   3 I_j = integral of j_I dl;  4 tau = integral of alpha_I dl  (unpolarized invariants per
+ *     unit affine parameter, observed frequency)
+ *   5-11  <q>_lambda = integral q dl / [2]
+ *   12-18 <q>_Ij = integral q j_I dl / I_j  (0 where I_j = 0)
+ *   19-25 <q>_tau, the solution of d<q>/dtau = q - <q> from the source end
+ *   q in the order rho (code units), n_e (cm^-3), p (code units), Theta_e, B (gauss), sigma,
+ *   beta^-1; samples without plasma contribute q = 0. */
+#define BL_AUX_COUNT 26
 
 enum {
     BL_OK = 0,
@@ -143,8 +158,10 @@ enum {
 enum { BL_PREC_FP64 = 0, BL_PREC_MIXED = 1, BL_PREC_FAST = 2 };
 /* flags: BL_ASYNC returns without synchronising; BL_TIMING records CUDA events on `stream`
  * around the geodesic and transfer kernels of every wave (read with
- * blacklight_last_kernel_ms). */
-enum { BL_ASYNC = 1u, BL_TIMING = 2u };
+ * blacklight_last_kernel_ms); BL_UNPOLARIZED integrates unpolarized transfer (Sec. 2.3.1,
+ * Eq. unpolarized) instead of the polarized equations: Stokes I only, Q = U = V = 0 (not with
+ * the learned coefficient model). */
+enum { BL_ASYNC = 1u, BL_TIMING = 2u, BL_UNPOLARIZED = 8u };
 
 /* Trace n_images cameras with persistent launch pairs (geodesics, then transfer). Image q
  * uses cams[q], mets[q], grids[q], freqs_hz[q] (observed frequency, > 0) and outs[q]. All
@@ -258,7 +275,7 @@ enum { BL_CRIT_ABS_GRAD = 0, BL_CRIT_REL_GRAD = 1, BL_CRIT_ABS_LAPL = 2, BL_CRIT
 /* Trace n_images cameras adaptively (one launch pair per level for all images). outs[q].stokes
  * receives the composite image at the finest resolution, DEVICE [4][nf][nf] with
  * nf = n * 2^max_level, each pixel taking the value of the finest traced pixel covering it
- * (dtype 0 float64 / 1 float32); outs[q].status/steps/samples/end_state are ignored.
+ * (dtype 0 float64 / 1 float32); outs[q].status/steps/samples/end_state/aux are ignored.
  * level_rays (optional HOST int32 [n_images][max_level + 1]) receives the rays traced per level.
  * Synchronises `stream` between levels (refinement decisions are read back). */
 int blacklight_trace_adaptive(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,

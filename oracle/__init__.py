@@ -44,7 +44,8 @@ class Camera(C.Structure):
 class Metric(C.Structure):
     _fields_ = [("mass", C.c_double), ("spin", C.c_double), ("r_in_over_rhor", C.c_double),
                 ("tol_abs", C.c_double), ("tol_rel", C.c_double), ("ds_max", C.c_double),
-                ("h0_frac", C.c_double), ("max_steps", C.c_int64), ("flat", C.c_int32)]
+                ("h0_frac", C.c_double), ("max_steps", C.c_int64), ("flat", C.c_int32),
+                ("integrator", C.c_int32), ("f_step", C.c_double)]
 
 
 class Grid(C.Structure):
@@ -123,7 +124,8 @@ def camera_struct(cam) -> Camera:
 
 def metric_struct(met) -> Metric:
     return Metric(met.mass, met.spin, met.r_in_over_rhor, met.tol_abs, met.tol_rel, met.ds_max,
-                  met.h0_frac, int(met.max_steps), met.flat)
+                  met.h0_frac, int(met.max_steps), met.flat, getattr(met, "integrator", 0),
+                  getattr(met, "f_step", 0.01))
 
 
 def grid_struct(gp, prim: np.ndarray) -> Grid:

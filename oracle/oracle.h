@@ -47,6 +47,10 @@ typedef struct {
     double h0_frac;            /* initial step = -h0_frac (r_cam - r_hor) */
     int64_t max_steps;         /* attempted-step limit */
     int32_t flat;              /* 1: Minkowski metric, same coordinates */
+    /* integrator: 0 Dormand-Prince RK5(4) (Table tab:dp); 1 classical RK4 (Table tab:rk4);
+     * 2 Heun RK2 (Table tab:rk2), both with steps -f_step (r - r_hor) (Eq. rk_step) */
+    int32_t integrator;
+    double f_step;
 } ora_metric;
 
 typedef struct {

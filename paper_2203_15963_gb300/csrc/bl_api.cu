@@ -225,6 +225,7 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
     d.stokes = o.stokes; d.dtype = o.dtype; d.status = o.status; d.steps = o.steps;
     d.end_state = o.end_state;
     d.samples = o.samples;
+    d.aux = o.aux;
     d.ray_offset = offset;
     d.n_rays = (int64_t)c.n * c.n;
     d.block_list = nullptr;
@@ -234,11 +235,35 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
 struct DevInfo {
     int sms = 0;
     int geo_blocks[3] = {0, 0, 0};  // per SM, indexed by precision: [fp64, mixed, fast]
-    int tr_blocks[3] = {0, 0, 0};
-    int tr_mlp_blocks = 0;
-    int tr_slow_blocks[3] = {0, 0, 0};   // slow-light transfer variants
-    int tr_mlp_slow_blocks = 0;
+    int tr_occ[2][8] = {};          // transfer variants: [double, float][feature bits]
+    int tr_mlp_occ[2] = {0, 0};     // learned-coefficient transfer: [fast light, slow light]
+    // CTAs per SM of the transfer variant a launch uses
+    int transfer(int precision, const float* mlp, int feat) const {
+        if (mlp) return tr_mlp_occ[(feat & bl::kFSlow) ? 1 : 0];
+        return tr_occ[precision == BL_PREC_FP64 ? 0 : 1][feat & 7];
+    }
 };
+
+template <class T, class R, int F>
+int occ_transfer(int* out) {
+    BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bl::transfer_kernel<T, R, F>, 128, 0));
+    if (*out < 1) *out = 1;
+    return 0;
+}
+
+template <class T, class R>
+int occ_transfer_all(int out[8]) {
+    int rc = 0;
+    if (!rc) rc = occ_transfer<T, R, 0>(&out[0]);
+    if (!rc) rc = occ_transfer<T, R, 1>(&out[1]);
+    if (!rc) rc = occ_transfer<T, R, 2>(&out[2]);
+    if (!rc) rc = occ_transfer<T, R, 3>(&out[3]);
+    if (!rc) rc = occ_transfer<T, R, 4>(&out[4]);
+    if (!rc) rc = occ_transfer<T, R, 5>(&out[5]);
+    if (!rc) rc = occ_transfer<T, R, 6>(&out[6]);
+    if (!rc) rc = occ_transfer<T, R, 7>(&out[7]);
+    return rc;
+}
 
 int dev_info(DevInfo& out) {
     static std::mutex mu;
@@ -253,31 +278,41 @@ int dev_info(DevInfo& out) {
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[0], bl::geodesic_kernel<double, double>, 128, 0));
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[1], bl::geodesic_kernel<float, double>, 128, 0));
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[2], bl::geodesic_kernel<float, bl::df64>, 128, 0));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[0], bl::transfer_kernel<double, double, false>, 128, 0));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_blocks[1], bl::transfer_kernel<float, float, false>, 128, 0));
-        di.tr_blocks[2] = di.tr_blocks[1];
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_blocks, bl::transfer_mlp_kernel<float, false>, 128, 0));
-        if (di.tr_mlp_blocks < 1) di.tr_mlp_blocks = 1;
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_slow_blocks[0], bl::transfer_kernel<double, double, true>, 128, 0));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_slow_blocks[1], bl::transfer_kernel<float, float, true>, 128, 0));
-        di.tr_slow_blocks[2] = di.tr_slow_blocks[1];
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_slow_blocks, bl::transfer_mlp_kernel<float, true>, 128, 0));
         for (int i = 0; i < 3; ++i)
-            if (di.tr_slow_blocks[i] < 1) di.tr_slow_blocks[i] = 1;
-        if (di.tr_mlp_slow_blocks < 1) di.tr_mlp_slow_blocks = 1;
-        for (int i = 0; i < 3; ++i) {
             if (di.geo_blocks[i] < 1) di.geo_blocks[i] = 1;
-            if (di.tr_blocks[i] < 1) di.tr_blocks[i] = 1;
-        }
+        int rc = occ_transfer_all<double, double>(di.tr_occ[0]);
+        if (!rc) rc = occ_transfer_all<float, float>(di.tr_occ[1]);
+        if (rc) { di.sms = 0; return rc; }
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_occ[0], bl::transfer_mlp_kernel<float, false>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_occ[1], bl::transfer_mlp_kernel<float, true>, 128, 0));
+        for (int i = 0; i < 2; ++i)
+            if (di.tr_mlp_occ[i] < 1) di.tr_mlp_occ[i] = 1;
     }
     out = di;
     return 0;
 }
 
+// One launch of the transfer variant with feature bits F.
+template <class T, class R>
+void launch_transfer(int feat, unsigned grid, cudaStream_t st, const bl::ImageDesc* d, int n,
+                     int64_t b, int64_t e, const bl::RayHdr* hdr, const R* pool,
+                     const int32_t* chunks, bl::Counters* ctr) {
+    switch (feat & 7) {
+        case 0: bl::transfer_kernel<T, R, 0><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
+        case 1: bl::transfer_kernel<T, R, 1><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
+        case 2: bl::transfer_kernel<T, R, 2><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
+        case 3: bl::transfer_kernel<T, R, 3><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
+        case 4: bl::transfer_kernel<T, R, 4><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
+        case 5: bl::transfer_kernel<T, R, 5><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
+        case 6: bl::transfer_kernel<T, R, 6><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
+        default: bl::transfer_kernel<T, R, 7><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
+    }
+}
+
 // Launch shape of the persistent kernels: CTAs per SM (0 = the occupancy limit).
 struct LaunchCfg {
     int geo_ctas = 0, tr_ctas = 0;
-    bool slow = false;      // some image has several snapshots (slow light)
+    int feat = 0;           // transfer variant: bl::kFSlow | kFUnpol | kFAux
 };
 
 // The kernel sequence of one trace on prepared workspace whose image descriptors are already
@@ -308,11 +343,9 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
     const int pidx = precision;
     auto pick = [](int want, int occ) { return want > 0 && want < occ ? want : occ; };
     const unsigned geo_grid = (unsigned)(di.sms * pick(cfg.geo_ctas, di.geo_blocks[pidx]));
-    const int tr_occ = mlp ? (cfg.slow ? di.tr_mlp_slow_blocks : di.tr_mlp_blocks)
-                           : (cfg.slow ? di.tr_slow_blocks[pidx] : di.tr_blocks[pidx]);
-    const unsigned tr_grid = (unsigned)(di.sms * pick(cfg.tr_ctas, tr_occ));
+    const unsigned tr_grid = (unsigned)(di.sms * pick(cfg.tr_ctas, di.transfer(precision, mlp, cfg.feat)));
     const int record = transfer ? 1 : 0;
-    const bool slow = cfg.slow;
+    const bool slow = (cfg.feat & bl::kFSlow) != 0;
     for (int64_t w = 0; w < n_waves; ++w) {
         const int64_t b = w * L.wave;
         const int64_t e = b + L.wave < L.rays ? b + L.wave : L.rays;
@@ -346,19 +379,11 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
                     bl::transfer_mlp_kernel<float, false><<<tr_grid, 128, 0, st>>>(
                         d_desc, n_images, b, e, hdr, fpool, chunks, mlp, ctr);
             } else if (precision != BL_PREC_FP64) {
-                if (slow)
-                    bl::transfer_kernel<float, float, true><<<tr_grid, 128, 0, st>>>(
-                        d_desc, n_images, b, e, hdr, fpool, chunks, ctr);
-                else
-                    bl::transfer_kernel<float, float, false><<<tr_grid, 128, 0, st>>>(
-                        d_desc, n_images, b, e, hdr, fpool, chunks, ctr);
+                launch_transfer<float, float>(cfg.feat, tr_grid, st, d_desc, n_images, b, e, hdr,
+                                              fpool, chunks, ctr);
             } else {
-                if (slow)
-                    bl::transfer_kernel<double, double, true><<<tr_grid, 128, 0, st>>>(
-                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr);
-                else
-                    bl::transfer_kernel<double, double, false><<<tr_grid, 128, 0, st>>>(
-                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr);
+                launch_transfer<double, double>(cfg.feat, tr_grid, st, d_desc, n_images, b, e,
+                                                hdr, dpool, chunks, ctr);
             }
             ++g_launches;
             BL_CUDA(cudaGetLastError());
@@ -376,7 +401,10 @@ int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* 
     BL_CUDA(cudaMemcpyAsync(ws + L.descs, descs.data(), sizeof(bl::ImageDesc) * n_images,
                             cudaMemcpyHostToDevice, st));
     LaunchCfg c = cfg;
-    for (const auto& d : descs) c.slow = c.slow || d.n_snap > 1;
+    for (const auto& d : descs) {
+        if (d.n_snap > 1) c.feat |= bl::kFSlow;
+        if (d.aux) c.feat |= bl::kFAux;
+    }
     return launch_kernels(n_images, ws, L, precision, transfer, st, timing, mlp, c);
 }
 
@@ -391,10 +419,16 @@ int finish(char* ws, const Layout& L, cudaStream_t st, bool sync) {
 }
 
 // The learned-model pointer shared by all images (nullptr: exact fits), checked.
-int common_mlp(int32_t n_images, const bl_grid_t* grids, int precision, const float** out) {
+int common_mlp(int32_t n_images, const bl_grid_t* grids, int precision, const float** out,
+               uint32_t flags = 0, const bl_out_t* outs = nullptr) {
     *out = nullptr;
     if (!grids) return 0;
     const float* p = grids[0].coef_mlp;
+    if (p && (flags & BL_UNPOLARIZED))
+        return fail(BL_EUNSUPPORTED, "coef_mlp with BL_UNPOLARIZED");
+    if (p && outs)
+        for (int q = 0; q < n_images; ++q)
+            if (outs[q].aux) return fail(BL_EUNSUPPORTED, "coef_mlp with auxiliary images");
     for (int q = 1; q < n_images; ++q)
         if (grids[q].coef_mlp != p) return fail(BL_EINVAL, "grids[%d].coef_mlp differs from grids[0]", q);
     if (p && precision == BL_PREC_FP64)
@@ -436,6 +470,10 @@ int check_batch(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* me
         if ((rc = device_pointer(outs[q].end_state, what))) return rc;
         snprintf(what, sizeof(what), "outs[%d].samples", q);
         if ((rc = device_pointer(outs[q].samples, what))) return rc;
+        snprintf(what, sizeof(what), "outs[%d].aux", q);
+        if ((rc = device_pointer(outs[q].aux, what))) return rc;
+        if (!transfer && outs[q].aux)
+            return fail(BL_EINVAL, "outs[%d].aux: auxiliary images need the transfer", q);
         snprintf(what, sizeof(what), "grids[%d].prim", q);
         if (transfer && (rc = device_pointer(grids[q].prim, what))) return rc;
     }
@@ -487,12 +525,15 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
         own = true;
     }
     const float* mlp = nullptr;
-    int rc = transfer ? common_mlp(n_images, grids, precision, &mlp) : 0;
+    int rc = transfer ? common_mlp(n_images, grids, precision, &mlp, flags, outs) : 0;
     if (rc) {
         if (own) cudaFreeAsync(ws, st);
         return rc;
     }
-    rc = launch_all(n_images, descs, ws, L, precision, transfer, st, (flags & BL_TIMING) != 0, mlp);
+    LaunchCfg cfg;
+    if (flags & BL_UNPOLARIZED) cfg.feat |= bl::kFUnpol;
+    rc = launch_all(n_images, descs, ws, L, precision, transfer, st, (flags & BL_TIMING) != 0, mlp,
+                    cfg);
     if (rc == 0) rc = finish(ws, L, st, !(flags & BL_ASYNC));
     if (own) {
         cudaError_t e = cudaFreeAsync(ws, st);
@@ -530,7 +571,7 @@ struct bl_plan {
     int32_t n_images = 0;
     int precision = 0;
     const float* mlp = nullptr;
-    bool slow = false;
+    int feat = 0;            // transfer variant feature bits
     std::vector<bl::ImageDesc> descs;
     Layout L{};
     char* ws = nullptr;
@@ -563,7 +604,7 @@ int plan_time(bl_plan& P, const LaunchCfg& cfg, cudaStream_t st, float* ms) {
     for (int it = 0; it < 3 && rc == 0; ++it) {
         if (it > 0 && (ce = cudaEventRecord(e0, st)) != cudaSuccess) rc = cuda_fail(ce, "record");
         LaunchCfg c = cfg;
-        c.slow = P.slow;
+        c.feat = P.feat;
         if (!rc) rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, c);
         if (!rc && it > 0) {
             if ((ce = cudaEventRecord(e1, st)) != cudaSuccess) rc = cuda_fail(ce, "record");
@@ -607,8 +648,7 @@ int plan_autotune(bl_plan& P, cudaStream_t st) {
     if (t < best * (1.0f - kTuneMargin)) { best = t; order = 1; }
     if ((rc = plan_set_order(P, order, st))) return rc;
     const int geo_max = di.geo_blocks[P.precision];
-    const int tr_max = P.mlp ? (P.slow ? di.tr_mlp_slow_blocks : di.tr_mlp_blocks)
-                             : (P.slow ? di.tr_slow_blocks[P.precision] : di.tr_blocks[P.precision]);
+    const int tr_max = di.transfer(P.precision, P.mlp, P.feat);
     int geo_best = geo_max;
     for (int c = 1; c < geo_max; ++c) {
         LaunchCfg trial = cfg;
@@ -651,7 +691,7 @@ int plan_capture(bl_plan& P, cudaStream_t user) {
     }
     if (!rc) {
         LaunchCfg c = P.cfg;
-        c.slow = P.slow;
+        c.feat = P.feat;
         rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, c);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(st, &g);
@@ -972,8 +1012,9 @@ int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_m
             return fail(BL_EINVAL, "config: ray_order 0 or 1, CTAs per SM >= 0");
     }
     const float* mlp = nullptr;
-    if ((rc = common_mlp(n_images, grids, precision, &mlp))) return rc;
+    if ((rc = common_mlp(n_images, grids, precision, &mlp, flags, outs))) return rc;
     bl_plan* P = new bl_plan();
+    if (flags & BL_UNPOLARIZED) P->feat |= bl::kFUnpol;
     BL_CUDA(cudaGetDevice(&P->dev));
     P->n_images = n_images;
     P->precision = precision;
@@ -983,7 +1024,8 @@ int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_m
     int64_t off = 0;
     for (int q = 0; q < n_images; ++q) {
         fill_desc(P->descs[q], cams[q], mets[q], grids[q], freqs_hz[q], outs[q], off);
-        P->slow = P->slow || P->descs[q].n_snap > 1;
+        if (P->descs[q].n_snap > 1) P->feat |= bl::kFSlow;
+        if (P->descs[q].aux) P->feat |= bl::kFAux;
         off += (int64_t)cams[q].n * cams[q].n;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -1036,9 +1078,7 @@ int blacklight_plan_config(const bl_plan_t* plan, bl_launch_config_t* out) {
     int rc = dev_info(di);
     if (rc) return rc;
     const int geo_max = di.geo_blocks[plan->precision];
-    const int tr_max = plan->mlp ? (plan->slow ? di.tr_mlp_slow_blocks : di.tr_mlp_blocks)
-                                 : (plan->slow ? di.tr_slow_blocks[plan->precision]
-                                               : di.tr_blocks[plan->precision]);
+    const int tr_max = di.transfer(plan->precision, plan->mlp, plan->feat);
     out->ray_order = plan->order;
     out->geo_ctas_per_sm = plan->cfg.geo_ctas > 0 && plan->cfg.geo_ctas < geo_max ? plan->cfg.geo_ctas : geo_max;
     out->tr_ctas_per_sm = plan->cfg.tr_ctas > 0 && plan->cfg.tr_ctas < tr_max ? plan->cfg.tr_ctas : tr_max;
@@ -1097,7 +1137,10 @@ int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const 
     const size_t off_s = align_up(gbytes), off_st = off_s + align_up(sbytes),
                  off_sp = off_st + align_up(npix * 4), off_e = off_sp + align_up(npix * 4),
                  off_m = off_e + align_up(npix * 8 * sizeof(double)),
-                 total = off_m + (grid->coef_mlp ? align_up(sizeof(float) * BL_MLP_PARAMS) : 0);
+                 off_a = off_m + (grid->coef_mlp ? align_up(sizeof(float) * BL_MLP_PARAMS) : 0),
+                 abytes = out->aux ? (size_t)BL_AUX_COUNT * npix *
+                                     (out->dtype == 0 ? sizeof(double) : sizeof(float)) : 0,
+                 total = off_a + align_up(abytes);
     cudaError_t e = cudaMallocAsync((void**)&dev, total, st);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e)); }
     bl_grid_t g = *grid;
@@ -1108,6 +1151,7 @@ int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const 
     o.steps = out->steps ? (int32_t*)(dev + off_sp) : nullptr;
     o.end_state = out->end_state ? (double*)(dev + off_e) : nullptr;
     o.samples = nullptr;
+    o.aux = out->aux ? (void*)(dev + off_a) : nullptr;
     rc = 0;
     e = cudaMemcpyAsync(dev, grid->prim, gbytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "copy grid to device");
@@ -1126,6 +1170,8 @@ int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const 
             e = cudaMemcpyAsync(out->steps, o.steps, npix * 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess && out->end_state)
             e = cudaMemcpyAsync(out->end_state, o.end_state, npix * 64, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && out->aux)
+            e = cudaMemcpyAsync(out->aux, o.aux, abytes, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) rc = cuda_fail(e, "copy results to host");
     }
     cudaFreeAsync(dev, st);

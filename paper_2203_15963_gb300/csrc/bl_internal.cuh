@@ -40,6 +40,7 @@ struct ImageDesc {
     int32_t* steps;
     double* end_state;
     int32_t* samples;
+    void* aux;              // auxiliary images [26][n_rays] (dtype as stokes) or nullptr
     int64_t ray_offset;     // first global ray index of this image
     int64_t n_rays;         // rays traced for this image (n * n, or blocks x block^2)
     // Block-list mode (adaptive refinement): when block_list is set, ray p traces pixel

@@ -177,6 +177,19 @@ __device__ __forceinline__ void pixel_of(int64_t p, int n, int order, int& i, in
     }
 }
 
+// auxiliary image planes (Sec. 4, "Auxiliary Images"): plane a of the image's aux array
+template <class V>
+__device__ __forceinline__ void aux_store(const ImageDesc& im, int a, int64_t pix, V v) {
+    const int64_t npix = im.n_rays;
+    if (im.dtype == 0) ((double*)im.aux)[a * npix + pix] = (double)v;
+    else ((float*)im.aux)[a * npix + pix] = (float)v;
+}
+__device__ __forceinline__ double aux_load(const ImageDesc& im, int a, int64_t pix) {
+    const int64_t npix = im.n_rays;
+    return im.dtype == 0 ? ((const double*)im.aux)[a * npix + pix]
+                         : (double)((const float*)im.aux)[a * npix + pix];
+}
+
 __device__ __forceinline__ double im_spin(const ImageDesc* imgs, int q) { return imgs[q].spin; }
 __device__ __forceinline__ double im_mass(const ImageDesc* imgs, int q) { return imgs[q].mass; }
 
@@ -507,6 +520,8 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
     int64_t max_steps = 0;
     bool flat = false;
     double r_cur = 0.0;     // r at y
+    bool want_aux = false;  // auxiliary images: proper length and affine parameter
+    double aux_len = 0.0, aux_lam = 0.0;
 
     bool exhausted = false;
     // All 32 lanes stay in the loop until the whole warp is out of work, so the warp
@@ -541,6 +556,8 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
             r_grid = im.r_max;
             tol_abs = im.tol_abs; tol_rel = im.tol_rel;
             max_steps = im.max_steps;
+            want_aux = record && im.aux != nullptr;
+            aux_len = aux_lam = 0.0;
             r_cur = A::to(geodesic_rhs_g<G>(y, a, m, flat, K[0]));
             h = A::from(-im.h0_frac * (r_cam - im.r_hor));
             been_inside = r_cur < r_cam;
@@ -646,6 +663,10 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                     kt_up = -ymf[4] + Gm.f * L;
                     rmid = Gm.r;
                     fmid = Gm.f;
+                }
+                if (want_aux) {
+                    aux_lam += fabs(hd);
+                    aux_len += fabs(hd) * fabs(kt_up) / sqrt(1.0 + fmid);
                 }
                 const double rmin = fmin(rmid, fmin(r0, r1));
                 int nsub = 1;
@@ -770,6 +791,11 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
             if (im.end_state)
                 for (int c = 0; c < 8; ++c) im.end_state[pix * 8 + c] = A::to(y[c]);
             if (im.samples) im.samples[pix] = nrec;
+            if (want_aux) {
+                aux_store(im, 0, pix, -A::to(y[0]));
+                aux_store(im, 1, pix, aux_len);
+                aux_store(im, 2, pix, aux_lam);
+            }
             RayHdr hd;
             hd.kt = A::to(y[4]);
             hd.nnorm = nnorm;
@@ -801,6 +827,7 @@ struct Plasma {
     T u[4], b[4];         // contravariant CKS
     T ul[4];              // covariant u
     T ne, th, bg, bsq;
+    T rho, p, binv;       // code-unit density and pressure, b^2 / (2 p)
 };
 
 template <class T, bool kSlow = false>
@@ -946,6 +973,9 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
     P.th = th_e;
     P.ne = rho * ic<T>(im, kcNePre) / (T(1) + T(1) / rr);
     P.bg = sqrt(P.bsq) * ic<T>(im, kcBgPre);
+    P.rho = rho;
+    P.p = p;
+    P.binv = binv;
     return true;
 }
 
@@ -1080,17 +1110,60 @@ __device__ __forceinline__ const R* record_ptr(const R* __restrict__ pool, const
 // exact constant-coefficient Stokes step, and S -> N. A lane whose ray is done reads out the
 // Stokes parameters in the camera basis (H, V) and takes the next ray.
 // ---------------------------------------------------------------------------------------
-#ifndef BL_TR_MIN_CTAS
-#define BL_TR_MIN_CTAS 1
-#endif
-template <class T, class R, bool kSlow>
-__global__ void __launch_bounds__(128, BL_TR_MIN_CTAS) transfer_kernel(const ImageDesc* __restrict__ imgs,
+// Features of a transfer-kernel variant (compile-time, so that each variant carries only the
+// registers it needs).
+enum { kFSlow = 1, kFUnpol = 2, kFAux = 4 };
+
+// Auxiliary accumulators of one ray (Sec. 4, "Auxiliary Images"): I_j, tau and the lambda-,
+// emission- and tau-weighted sums of rho, n_e, p, Theta_e, B, sigma, beta^-1.
+template <class T>
+struct AuxAcc {
+    T ij, tau, ql[7], qi[7], qt[7];
+    __device__ __forceinline__ void reset() {
+        ij = tau = T(0);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) ql[k] = qi[k] = qt[k] = T(0);
+    }
+    // one sample: emissivity e and absorptivity a per unit affine parameter over dl
+    __device__ __forceinline__ void add(const Plasma<T>& P, T e, T a, T dl) {
+        const T q[7] = {P.rho, P.ne, P.p, P.th, P.bg, P.bsq / P.rho, P.binv};
+        const T dtau = a * dl;
+        const T ex = exp(-dtau), om = -expm1(-dtau);
+        ij += e * dl;
+        tau += dtau;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            ql[k] += q[k] * dl;
+            qi[k] += q[k] * e * dl;
+            qt[k] = ex * qt[k] + om * q[k];
+        }
+    }
+};
+
+template <class T>
+__device__ __forceinline__ void aux_finish(const ImageDesc& im, int64_t pix, const AuxAcc<T>& A) {
+    const double lam = aux_load(im, 2, pix);     // written by the geodesic kernel
+    aux_store(im, 3, pix, A.ij);
+    aux_store(im, 4, pix, A.tau);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        aux_store(im, 5 + k, pix, lam > 0.0 ? (double)A.ql[k] / lam : 0.0);
+        aux_store(im, 12 + k, pix, A.ij > T(0) ? A.qi[k] / A.ij : T(0));
+        aux_store(im, 19 + k, pix, A.qt[k]);
+    }
+}
+
+template <class T, class R, int kF>
+__global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restrict__ imgs,
                                                        int n_images, int64_t ray_begin,
                                                        int64_t ray_end,
                                                        const RayHdr* __restrict__ hdr,
                                                        const R* __restrict__ pool,
                                                        const int32_t* __restrict__ chunks,
                                                        Counters* ctr) {
+    constexpr bool kSlow = (kF & kFSlow) != 0;
+    constexpr bool kUnpol = (kF & kFUnpol) != 0;
+    constexpr bool kAux = (kF & kFAux) != 0;
     const int64_t total_rays = ray_end - ray_begin;
     int64_t wray = 0;
     bool active = false;
@@ -1098,6 +1171,8 @@ __global__ void __launch_bounds__(128, BL_TR_MIN_CTAS) transfer_kernel(const Ima
     int q = 0, pi = 0, pj = 0;
     int32_t idx = 0;
     Coh<T> N;
+    T Iu = T(0);            // unpolarized intensity (Eq. unpolarized)
+    AuxAcc<T> AX;
     bool started = false;
     T prev[kRecVals];
     R nxt[RecStride<R>::v];
@@ -1127,6 +1202,13 @@ __global__ void __launch_bounds__(128, BL_TR_MIN_CTAS) transfer_kernel(const Ima
                     if (im.dtype == 0) ((double*)im.stokes)[s * npix + pix] = val;
                     else ((float*)im.stokes)[s * npix + pix] = (float)val;
                 }
+                if constexpr (kAux) {
+                    if (im.aux) {
+                        AuxAcc<T> z;
+                        z.reset();
+                        aux_finish(im, pix, z);
+                    }
+                }
                 continue;
             }
             idx = hd.nrec - 1;
@@ -1140,6 +1222,8 @@ __global__ void __launch_bounds__(128, BL_TR_MIN_CTAS) transfer_kernel(const Ima
             for (int c = 0; c < 10; ++c) N.re[c] = T(0);
 #pragma unroll
             for (int c = 0; c < 6; ++c) N.im[c] = T(0);
+            Iu = T(0);
+            if constexpr (kAux) AX.reset();
             started = false;
             active = true;
         }
@@ -1150,7 +1234,7 @@ __global__ void __launch_bounds__(128, BL_TR_MIN_CTAS) transfer_kernel(const Ima
         for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
         const T nxt_t = (T)nxt[13];   // the sample's coordinate time
         if (idx > 0) load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
-        if (started) {
+        if (!kUnpol && started) {
             // merged N half-steps from the previous sample to this one
             T A0[4][4], A1[4][4];
             const T kp[4] = {kt, prev[3], prev[4], prev[5]};
@@ -1180,19 +1264,33 @@ __global__ void __launch_bounds__(128, BL_TR_MIN_CTAS) transfer_kernel(const Ima
                 const T eg = g * g * g * path;
                 const T coef[8] = {co[0] * eg, co[1] * eg, co[2] * eg, co[3] * path,
                                    co[4] * path, co[5] * path, co[6] * path, co[7] * path};
-                T e1[4], e2[4], e1l[4], e2l[4];
-                fluid_basis<T>(G, P, kl, ku, e1, e2, e1l, e2l);
-                T s0[4], s1[4];
-                coh_to_stokes(N, e1l, e2l, s0);
-                stokes_step<T>(coef, s0, cur[12], s1);
-                stokes_to_coh(e1, e2, s1, N);
+                if constexpr (kAux) AX.add(P, coef[0], coef[3], cur[12]);
+                if constexpr (kUnpol) {
+                    Iu = unpolarized_step<T>(coef[0], coef[3], cur[12], Iu);
+                } else {
+                    T e1[4], e2[4], e1l[4], e2l[4];
+                    fluid_basis<T>(G, P, kl, ku, e1, e2, e1l, e2l);
+                    T s0[4], s1[4];
+                    coh_to_stokes(N, e1l, e2l, s0);
+                    stokes_step<T>(coef, s0, cur[12], s1);
+                    stokes_to_coh(e1, e2, s1, N);
+                }
                 started = true;
             }
         }
 #pragma unroll
         for (int c = 0; c < kRecVals; ++c) prev[c] = cur[c];
         --idx;
-        if (idx < 0) {
+        if (idx < 0 && kUnpol) {
+            const int64_t npix = im.n_rays;
+            const T sv[4] = {Iu, T(0), T(0), T(0)};
+            for (int c = 0; c < 4; ++c) {
+                if (im.dtype == 0) ((double*)im.stokes)[c * npix + opix] = (double)sv[c];
+                else ((float*)im.stokes)[c * npix + opix] = (float)sv[c];
+            }
+            if constexpr (kAux) if (im.aux) aux_finish(im, opix, AX);
+            active = false;
+        } else if (idx < 0) {
             // last half-step to the camera node, then read out in the camera basis
             if (started) {
                 T A0[4][4], A1[4][4];
@@ -1221,6 +1319,7 @@ __global__ void __launch_bounds__(128, BL_TR_MIN_CTAS) transfer_kernel(const Ima
                 if (im.dtype == 0) ((double*)im.stokes)[c * npix + pix] = (double)s[c];
                 else ((float*)im.stokes)[c * npix + pix] = (float)s[c];
             }
+            if constexpr (kAux) if (im.aux) aux_finish(im, pix, AX);
             active = false;
         }
     }

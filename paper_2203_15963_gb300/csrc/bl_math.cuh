@@ -335,6 +335,20 @@ __device__ __forceinline__ void synchrotron_coefficients(T ne, T th, T bg, T nu,
 }
 
 // ---------------------------------------------------------------------------------------
+// Unpolarized segment (Eq. unpolarized): exact solution of dI/dl = j - alpha I over dl with
+// constant coefficients; optical depth >= 100 gives j / alpha, alpha = 0 gives I + j dl.
+// ---------------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T unpolarized_step(T j, T alpha, T dl, T i0) {
+    if (alpha > T(0)) {
+        const T dtau = alpha * dl;
+        if (dtau >= T(100)) return j / alpha;
+        return exp(-dtau) * (i0 + expm1(dtau) * j / alpha);
+    }
+    return i0 + j * dl;
+}
+
+// ---------------------------------------------------------------------------------------
 // Exact constant-coefficient polarized step over dl: S' = E S + T with
 // [E T; 0 1] = exp([[-M dl, J dl], [0, 0]]), M the absorption/rotation matrix (U-terms zero).
 // Scaling and squaring: the augmented matrix is scaled by 2^-s to norm <= 1/2, its

@@ -7,8 +7,10 @@ from . import native
 
 
 def alloc_outputs(n: int, dtype=torch.float64, device="cuda", status=True, steps=True,
-                  end_state=False, samples=False):
+                  end_state=False, samples=False, aux=False):
     out = {"stokes": torch.empty((4, n, n), dtype=dtype, device=device)}
+    if aux:
+        out["aux"] = torch.empty((26, n, n), dtype=dtype, device=device)
     if samples:
         out["samples"] = torch.empty((n, n), dtype=torch.int32, device=device)
     if status:
@@ -21,13 +23,13 @@ def alloc_outputs(n: int, dtype=torch.float64, device="cuda", status=True, steps
 
 
 def trace_images(cams, mets, gps, prims, freqs, dtype=None, end_state=False, workspace=None,
-                 flags=0, samples=False, outs=None, coef_mlp=None):
+                 flags=0, samples=False, outs=None, coef_mlp=None, aux=False):
     """Trace a batch of images in one launch pair; returns (rc, list of output dicts)."""
     if outs is None:
         outs = []
         for cam, met in zip(cams, mets):
             dt = dtype or (torch.float64 if met.precision == native.BL_PREC_FP64 else torch.float32)
-            outs.append(alloc_outputs(cam.n, dt, end_state=end_state, samples=samples))
+            outs.append(alloc_outputs(cam.n, dt, end_state=end_state, samples=samples, aux=aux))
     rc = native.blacklight_trace_batch(cams, mets, gps, prims, freqs, outs, workspace=workspace,
                                        flags=flags, coef_mlp=coef_mlp)
     return rc, outs

@@ -100,7 +100,11 @@ BL_CRIT_ABS_GRAD, BL_CRIT_REL_GRAD, BL_CRIT_ABS_LAPL, BL_CRIT_REL_LAPL = 0, 1, 2
 class Out(C.Structure):
     _fields_ = [("size", C.c_uint32), ("stokes", C.c_void_p), ("dtype", C.c_int32),
                 ("status", C.c_void_p), ("steps", C.c_void_p), ("end_state", C.c_void_p),
-                ("samples", C.c_void_p)]
+                ("samples", C.c_void_p), ("aux", C.c_void_p)]
+
+
+AUX_COUNT = 26
+BL_UNPOLARIZED = 8
 
 
 _lib = None
@@ -212,13 +216,14 @@ def grid_struct(gp, prim_ptr, coef_mlp=None) -> Grid:
                 getattr(gp, "t_camera", 0.0))
 
 
-def out_struct(stokes=None, status=None, steps=None, end_state=None, samples=None) -> Out:
+def out_struct(stokes=None, status=None, steps=None, end_state=None, samples=None,
+               aux=None) -> Out:
     import torch
     dtype = 0
     if stokes is not None:
         dtype = 0 if stokes.dtype == torch.float64 else 1
     return Out(C.sizeof(Out), _ptr(stokes), dtype, _ptr(status), _ptr(steps), _ptr(end_state),
-               _ptr(samples))
+               _ptr(samples), _ptr(aux))
 
 
 # ------------------------------------ calls ---------------------------------------------

@@ -60,6 +60,8 @@ class Metric:
     max_steps: int = 100000
     flat: int = 0
     precision: int = 0             # 0 = FP64 path, 1 = mixed (FP64 geodesics, FP32 transfer)
+    integrator: int = 0            # 0 = DP RK5(4), 1 = RK4, 2 = RK2 (Sec. 2.2)
+    f_step: float = 0.01           # RK2/RK4 step -f_step (r - r_hor) (Eq. rk_step)
 
 
 @dataclasses.dataclass

@@ -27,7 +27,7 @@ def test_library_builds_loads_and_exports_header_symbols():
 def test_struct_sizes_match_header_layout():
     # the binding's ctypes structs follow the C layout; the library checks .size at run time
     assert ctypes.sizeof(native.Camera) == 4 + 4 + 8 * 3 + 8 * 3 + 8 * 3 + 8 + 4 + 4 + 8 + 4 + 4
-    assert ctypes.sizeof(native.Out) == 56
+    assert ctypes.sizeof(native.Out) == 64
 
 
 def test_ctypes_struct_sizes_equal_the_c_compilers(tmp_path):
