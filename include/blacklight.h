@@ -62,7 +62,18 @@ typedef struct bl_metric {
     int64_t max_steps;      /* attempted DP steps per ray before MAX_STEPS */
     int32_t flat;           /* 1: Minkowski metric in the same coordinates (Sec. 4, flat) */
     int32_t precision;      /* BL_PREC_FP64, BL_PREC_MIXED or BL_PREC_FAST */
+    int32_t integrator;     /* BL_INT_DP (default), BL_INT_RK4 or BL_INT_RK2; all images of a
+                               call share it */
+    double f_step;          /* RK4/RK2: step -f_step (r - r_hor) (Eq. rk_step), 0 < f_step < 1 */
 } bl_metric_t;
+
+/* Geodesic integrators (Sec. 2.2). BL_INT_DP: adaptive Dormand-Prince RK5(4) (Table tab:dp)
+ * with tol_abs, tol_rel, h0_frac. BL_INT_RK4 / BL_INT_RK2: classical RK4 (Table tab:rk4) and
+ * Heun's method (Table tab:rk2) with the fixed rule of Eq. rk_step, always in FP64 (the
+ * precision field then only selects the transfer arithmetic); a step's sample is its cubic
+ * Hermite midpoint (y0 + y1)/2 + dl (f0 - f1)/8 (the paper defines the midpoint sample only for
+ * DP), and max_steps counts steps. */
+enum { BL_INT_DP = 0, BL_INT_RK4 = 1, BL_INT_RK2 = 2 };
 
 /* Fluid grid and plasma model (Secs. 2.4-2.5). prim is a DEVICE pointer to float32
  * [8][n_phi][n_theta][n_r] (r fastest): rho, u_gas, u^p_(r,theta,phi) (normal frame),

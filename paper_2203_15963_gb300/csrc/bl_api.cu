@@ -62,11 +62,11 @@ struct Layout {
 };
 
 Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precision,
-                        bool transfer) {
+                        bool transfer, int64_t cpr = kChunksPerRay) {
     Layout L{};
     L.rays = rays;
     L.wave = wave;
-    L.pool_chunks = transfer ? L.wave * kChunksPerRay : 0;
+    L.pool_chunks = transfer ? L.wave * cpr : 0;
     const size_t rec = precision != BL_PREC_FP64 ? sizeof(float) * bl::RecStride<float>::v
                                                  : sizeof(double) * bl::RecStride<double>::v;
     size_t off = 0;
@@ -79,22 +79,24 @@ Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precis
     return L;
 }
 
-Layout make_layout_rays(int32_t n_images, int64_t rays, int precision, bool transfer = true) {
+Layout make_layout_rays(int32_t n_images, int64_t rays, int precision, bool transfer = true,
+                        int64_t cpr = kChunksPerRay) {
     return make_layout_wave(n_images, rays, rays < kWaveRays ? rays : kWaveRays, precision,
-                            transfer);
+                            transfer, cpr);
 }
 
 // The largest wave (>= 1 ray) whose layout fits in `bytes`; wave = 0 if none does.
-Layout fit_layout(int32_t n_images, int64_t rays, int precision, bool transfer, size_t bytes) {
-    Layout L = make_layout_rays(n_images, rays, precision, transfer);
+Layout fit_layout(int32_t n_images, int64_t rays, int precision, bool transfer, size_t bytes,
+                  int64_t cpr) {
+    Layout L = make_layout_rays(n_images, rays, precision, transfer, cpr);
     if (L.total <= bytes) return L;
     int64_t lo = 0, hi = L.wave;        // total(lo) fits (or lo = 0), total(hi) does not
     while (hi - lo > 1) {
         const int64_t mid = lo + (hi - lo) / 2;
-        if (make_layout_wave(n_images, rays, mid, precision, transfer).total <= bytes) lo = mid;
+        if (make_layout_wave(n_images, rays, mid, precision, transfer, cpr).total <= bytes) lo = mid;
         else hi = mid;
     }
-    return make_layout_wave(n_images, rays, lo, precision, transfer);
+    return make_layout_wave(n_images, rays, lo, precision, transfer, cpr);
 }
 
 int64_t count_rays(int32_t n_images, const bl_camera_t* cams) {
@@ -103,8 +105,25 @@ int64_t count_rays(int32_t n_images, const bl_camera_t* cams) {
     return rays;
 }
 
-Layout make_layout(int32_t n_images, const bl_camera_t* cams, int precision) {
-    return make_layout_rays(n_images, count_rays(n_images, cams), precision);
+// Average record chunks to reserve per ray. The adaptive DP integrator records a few hundred
+// samples per ray; the fixed-rule RK integrators take about 2 ln(r_cam / r_hor) / f_step steps
+// on a ray that passes the hole and leaves again, one sample each.
+int64_t chunks_per_ray(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets) {
+    int64_t c = kChunksPerRay;
+    for (int q = 0; q < n_images; ++q) {
+        if (mets[q].integrator == BL_INT_DP || !(mets[q].f_step > 0.0)) continue;
+        const double a = mets[q].spin / mets[q].mass;
+        const double r_hor = mets[q].mass * (1.0 + std::sqrt(std::fmax(1.0 - a * a, 0.0)));
+        const double recs = 2.5 * std::log(std::fmax(cams[q].r / r_hor, 2.0)) / mets[q].f_step + 128.0;
+        const int64_t need = (int64_t)std::ceil(recs / bl::kChunk) + 1;
+        if (need > c) c = need;
+    }
+    return c < bl::kMaxChunks ? c : bl::kMaxChunks;
+}
+
+Layout make_layout(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets) {
+    return make_layout_rays(n_images, count_rays(n_images, cams), mets[0].precision, true,
+                            chunks_per_ray(n_images, cams, mets));
 }
 
 int check_camera(const bl_camera_t* c, int q) {
@@ -134,6 +153,10 @@ int check_metric(const bl_metric_t* m, int q) {
     if (m->precision != BL_PREC_FP64 && m->precision != BL_PREC_MIXED &&
         m->precision != BL_PREC_FAST)
         return fail(BL_EINVAL, "mets[%d].precision", q);
+    if (m->integrator != BL_INT_DP && m->integrator != BL_INT_RK4 && m->integrator != BL_INT_RK2)
+        return fail(BL_EINVAL, "mets[%d].integrator", q);
+    if (m->integrator != BL_INT_DP && !(m->f_step > 0.0 && m->f_step < 1.0))
+        return fail(BL_EINVAL, "mets[%d].f_step must be in (0, 1)", q);
     return 0;
 }
 
@@ -192,6 +215,7 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
     d.mass = m.mass; d.spin = m.spin; d.r_in_over_rhor = m.r_in_over_rhor;
     d.tol_abs = m.tol_abs; d.tol_rel = m.tol_rel; d.ds_max = m.ds_max; d.h0_frac = m.h0_frac;
     d.max_steps = m.max_steps; d.flat = m.flat; d.precision = m.precision;
+    d.integrator = m.integrator; d.f_step = m.f_step;
     d.prim = g.prim; d.nr = g.n_r; d.nt = g.n_theta; d.nph = g.n_phi; d.interp = g.interp;
     d.r_min = g.r_min; d.r_max = g.r_max; d.gamma_ad = g.gamma_ad; d.r_high = g.r_high;
     d.r_low = g.r_low; d.mu = g.mu; d.ne_ni = g.ne_over_ni; d.sigma_cut = g.sigma_cut;
@@ -237,6 +261,7 @@ struct DevInfo {
     int geo_blocks[3] = {0, 0, 0};  // per SM, indexed by precision: [fp64, mixed, fast]
     int tr_occ[2][8] = {};          // transfer variants: [double, float][feature bits]
     int tr_mlp_occ[2] = {0, 0};     // learned-coefficient transfer: [fast light, slow light]
+    int rk_occ[2] = {0, 0};         // RK2/RK4 geodesic kernel: [double records, float records]
     // CTAs per SM of the transfer variant a launch uses
     int transfer(int precision, const float* mlp, int feat) const {
         if (mlp) return tr_mlp_occ[(feat & bl::kFSlow) ? 1 : 0];
@@ -287,6 +312,10 @@ int dev_info(DevInfo& out) {
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_occ[1], bl::transfer_mlp_kernel<float, true>, 128, 0));
         for (int i = 0; i < 2; ++i)
             if (di.tr_mlp_occ[i] < 1) di.tr_mlp_occ[i] = 1;
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.rk_occ[0], bl::geodesic_rk_kernel<double>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.rk_occ[1], bl::geodesic_rk_kernel<float>, 128, 0));
+        for (int i = 0; i < 2; ++i)
+            if (di.rk_occ[i] < 1) di.rk_occ[i] = 1;
     }
     out = di;
     return 0;
@@ -313,6 +342,7 @@ void launch_transfer(int feat, unsigned grid, cudaStream_t st, const bl::ImageDe
 struct LaunchCfg {
     int geo_ctas = 0, tr_ctas = 0;
     int feat = 0;           // transfer variant: bl::kFSlow | kFUnpol | kFAux
+    int integrator = BL_INT_DP;
 };
 
 // The kernel sequence of one trace on prepared workspace whose image descriptors are already
@@ -352,7 +382,17 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
         // the work and pool counters restart with each wave; bad_rays accumulates
         if (w > 0) BL_CUDA(cudaMemsetAsync(ctr, 0, offsetof(bl::Counters, bad_rays), st));
         if (timing) BL_CUDA(cudaEventRecord(g_ev[2 * w], st));
-        if (precision == BL_PREC_FP64) {
+        if (cfg.integrator != BL_INT_DP) {
+            const int ri = precision == BL_PREC_FP64 ? 0 : 1;
+            const unsigned rk_grid = (unsigned)(di.sms * pick(cfg.geo_ctas, di.rk_occ[ri]));
+            if (precision == BL_PREC_FP64) {
+                bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
+                bl::geodesic_rk_kernel<double><<<rk_grid, 128, 0, st>>>(d_desc, n_images, b, e, hdr, sink, record);
+            } else {
+                bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
+                bl::geodesic_rk_kernel<float><<<rk_grid, 128, 0, st>>>(d_desc, n_images, b, e, hdr, sink, record);
+            }
+        } else if (precision == BL_PREC_FP64) {
             bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
             bl::geodesic_kernel<double, double><<<geo_grid, 128, 0, st>>>(
                 d_desc, n_images, b, e, hdr, sink, record);
@@ -405,6 +445,7 @@ int launch_all(int32_t n_images, const std::vector<bl::ImageDesc>& descs, char* 
         if (d.n_snap > 1) c.feat |= bl::kFSlow;
         if (d.aux) c.feat |= bl::kFAux;
     }
+    c.integrator = descs.empty() ? BL_INT_DP : descs[0].integrator;
     return launch_kernels(n_images, ws, L, precision, transfer, st, timing, mlp, c);
 }
 
@@ -459,6 +500,8 @@ int check_batch(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* me
         if (precision < 0) precision = mets[q].precision;
         else if (precision != mets[q].precision)
             return fail(BL_EINVAL, "all images must share metric.precision");
+        if (mets[q].integrator != mets[0].integrator)
+            return fail(BL_EINVAL, "all images must share metric.integrator");
         char what[64];
         snprintf(what, sizeof(what), "outs[%d].stokes", q);
         if (transfer && (rc = device_pointer(outs[q].stokes, what))) return rc;
@@ -492,7 +535,8 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
     }
     // geodesics only: no records, so no pool
     const int64_t rays = count_rays(n_images, cams);
-    Layout L = make_layout_rays(n_images, rays, precision, transfer);
+    const int64_t cpr = chunks_per_ray(n_images, cams, mets);
+    Layout L = make_layout_rays(n_images, rays, precision, transfer, cpr);
     std::vector<bl::ImageDesc> descs(n_images);
     int64_t off = 0;
     static const bl_grid_t kNoGrid = {sizeof(bl_grid_t), nullptr, 1, 1, 1, 1.0, 2.0, 4.0 / 3.0,
@@ -509,11 +553,11 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
         if ((uintptr_t)ws % kAlign)
             return fail(BL_EINVAL, "workspace must be %zu-byte aligned", kAlign);
         // a workspace smaller than the default layout runs the rays in more, smaller waves
-        L = fit_layout(n_images, rays, precision, transfer, workspace_bytes);
+        L = fit_layout(n_images, rays, precision, transfer, workspace_bytes, cpr);
         if (L.wave < 1)
             return fail(BL_EINVAL, "workspace too small: %zu < %zu bytes (one ray)",
                         workspace_bytes,
-                        make_layout_wave(n_images, rays, 1, precision, transfer).total);
+                        make_layout_wave(n_images, rays, 1, precision, transfer, cpr).total);
         int rc = device_pointer(ws, "workspace");
         if (rc) return rc;
     } else {
@@ -605,6 +649,7 @@ int plan_time(bl_plan& P, const LaunchCfg& cfg, cudaStream_t st, float* ms) {
         if (it > 0 && (ce = cudaEventRecord(e0, st)) != cudaSuccess) rc = cuda_fail(ce, "record");
         LaunchCfg c = cfg;
         c.feat = P.feat;
+        c.integrator = P.descs[0].integrator;
         if (!rc) rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, c);
         if (!rc && it > 0) {
             if ((ce = cudaEventRecord(e1, st)) != cudaSuccess) rc = cuda_fail(ce, "record");
@@ -692,6 +737,7 @@ int plan_capture(bl_plan& P, cudaStream_t user) {
     if (!rc) {
         LaunchCfg c = P.cfg;
         c.feat = P.feat;
+        c.integrator = P.descs[0].integrator;
         rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, c);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(st, &g);
@@ -831,7 +877,8 @@ int trace_adaptive_impl(int32_t n_images, const bl_camera_t* cams, const bl_metr
             qmap.push_back(q);
             off += nrays[q];
         }
-        Layout Ly = make_layout_rays((int32_t)descs.size(), rays, precision);
+        Layout Ly = make_layout_rays((int32_t)descs.size(), rays, precision, true,
+                                     chunks_per_ray(n_images, cams, mets));
         if ((rc = grow((void**)&ws, ws_bytes, Ly.total))) break;
         if ((rc = launch_all((int32_t)descs.size(), descs, ws, Ly, precision, true, st, false, mlp))) break;
         unsigned long long bad = 0, tmo = 0;
@@ -982,7 +1029,7 @@ int blacklight_trace_noalloc(const bl_camera_t* cam, const bl_metric_t* met,
         return fail(BL_EINVAL, "blacklight_trace_noalloc: %lld rays exceed its fixed scratch "
                     "(at most %lld rays, %zu bytes); use blacklight_trace",
                     (long long)rays, (long long)kNoAllocMaxRays, kNoAllocBytes);
-    const size_t need = make_layout(1, cam, met->precision).total;
+    const size_t need = make_layout(1, cam, met).total;
     if (need > kNoAllocBytes)
         return fail(BL_EINVAL, "blacklight_trace_noalloc: needs %zu bytes of scratch, has %zu",
                     need, kNoAllocBytes);
@@ -1019,7 +1066,8 @@ int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_m
     P->n_images = n_images;
     P->precision = precision;
     P->mlp = mlp;
-    P->L = make_layout_rays(n_images, count_rays(n_images, cams), precision, true);
+    P->L = make_layout_rays(n_images, count_rays(n_images, cams), precision, true,
+                            chunks_per_ray(n_images, cams, mets));
     P->descs.resize(n_images);
     int64_t off = 0;
     for (int q = 0; q < n_images; ++q) {
@@ -1116,7 +1164,7 @@ int blacklight_geodesics(const bl_camera_t* cam, const bl_metric_t* met, const b
 size_t blacklight_workspace_size(int32_t n_images, const bl_camera_t* cams,
                                  const bl_metric_t* mets) {
     if (n_images < 1 || !cams || !mets) return 0;
-    return make_layout(n_images, cams, mets[0].precision).total;
+    return make_layout(n_images, cams, mets).total;
 }
 
 int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const bl_grid_t* grid,

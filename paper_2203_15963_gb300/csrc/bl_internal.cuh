@@ -24,6 +24,8 @@ struct ImageDesc {
     double mass, spin, r_in_over_rhor, tol_abs, tol_rel, ds_max, h0_frac;
     int64_t max_steps;
     int32_t flat, precision;
+    int32_t integrator, pad3_;
+    double f_step;
     // grid and plasma (Secs. 2.4-2.5)
     const float* prim;
     int32_t nr, nt, nph, interp;

