@@ -76,6 +76,8 @@ def parse():
                          "(trained first; needs --precision fast or mixed)")
     ap.add_argument("--no-slow", action="store_true",
                     help="skip the slow-light line (8 snapshots, 512^2)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the unpolarized, auxiliary-image and RK4/RK2 timings")
     ap.add_argument("--no-plan", action="store_true",
                     help="skip the autotuned CUDA-graph plan line")
     ap.add_argument("--no-mlp", action="store_true",
@@ -355,6 +357,9 @@ def main():
     if not args.no_hires and args.case == "full":
         hires, hires_img = measure_hires(torch, native, images, prec, device,
                                          keep_image=prec == native.BL_PREC_FAST)
+    variants = None
+    if not args.no_variants:
+        variants = measure_variants(torch, native, images, wl, prec, device)
     plan = None
     if not args.no_plan:
         plan = measure_plan(torch, native, images, wl, prec, device)
@@ -403,7 +408,8 @@ def main():
                 "work": {"dp_attempts": attempts, "samples": samples,
                          "rays_not_terminated_normally": status_bad},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "other_forms": other,
-                "plan": plan, "hires": hires, "mlp": mlp, "slow_light": slow,
+                "variants": variants, "plan": plan, "hires": hires, "mlp": mlp,
+                "slow_light": slow,
                 "adaptive": adaptive,
                 "gpu_launches": int(launches), "clocks": clk, "return_codes": sorted(set(rcs))}
         print(json.dumps(line), flush=True)
@@ -559,6 +565,42 @@ def measure_mlp(torch, native, images, device, fast_image, params, train_s, fina
     del img, img64
     torch.cuda.empty_cache()
     return line
+
+
+def measure_variants(torch, native, images, wl, code, device, steps=2):
+    """The main workload (9 x 256^2) in the method's other modes: unpolarized transfer
+    (Eq. unpolarized), polarized with the 26 auxiliary images, and the fixed-rule RK4 and RK2
+    integrators (f_step = 0.02, FP64 geodesics). Device time per step, CUDA events."""
+    import dataclasses
+    cams = wl["cams"]
+    dt = torch.float64 if code == native.BL_PREC_FP64 else torch.float32
+    rays = sum(c.n * c.n for c in cams)
+
+    def run(mets, flags=0, aux=False):
+        outs = [images.alloc_outputs(c.n, dt, device=device, aux=aux) for c in cams]
+        native.blacklight_trace_batch(cams, mets, wl["gps"], wl["prims"], wl["freqs"], outs,
+                                      flags=flags)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            rc = native.blacklight_trace_batch(cams, mets, wl["gps"], wl["prims"], wl["freqs"],
+                                               outs, flags=flags)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        del outs
+        torch.cuda.empty_cache()
+        return {"value": rays / ms * 1e3, "ms_per_step": ms, "return_code": rc}
+
+    out = {"unit": "rays/s", "steps": steps,
+           "unpolarized": run(wl["mets"], flags=native.BL_UNPOLARIZED),
+           "polarized_with_aux": run(wl["mets"], aux=True)}
+    for name, integ in (("rk4", native.BL_INT_RK4), ("rk2", native.BL_INT_RK2)):
+        mets = [dataclasses.replace(m, integrator=integ, f_step=0.02) for m in wl["mets"]]
+        out[name + "_f0.02"] = run(mets)
+    return out
 
 
 def measure_plan(torch, native, images, wl, code, device, steps=5):
