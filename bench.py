@@ -34,8 +34,8 @@ GRID = (256, 128, 128)
 # FP64 flops per Dormand-Prince attempt (6 right-hand sides, 5 stage combinations, error norm)
 FLOP64_PER_ATTEMPT = 1520
 # dram__bytes_read.sum + dram__bytes_write.sum of geodesic_kernel<float, df64> per DP attempt
-# (2.207 GB for 7,845,744 attempts: the a = 0.94, i = 60 deg image of this workload at 256^2)
-GEO_DF64_DRAM_BYTES_PER_ATTEMPT = 281.6
+# (1.508 GB for 7,845,744 attempts: the a = 0.94, i = 60 deg image of this workload at 256^2)
+GEO_DF64_DRAM_BYTES_PER_ATTEMPT = 192.2
 # FP32 flops per transfer sample (2 transport matrices, predictor-corrector, sampling,
 # plasma, coefficients, fluid frame, Stokes step)
 FLOP32_PER_SAMPLE = 3300

@@ -260,6 +260,7 @@ int blacklight_plan_config(const bl_plan_t* plan, bl_launch_config_t* out);
 /* Free the plan (synchronises the device). NULL is ignored. */
 int blacklight_plan_destroy(bl_plan_t* plan);
 
+
 /* Adaptive ray tracing (Sec. 4, "Adaptive Ray Tracing"). The root n x n image is split into
  * square blocks of `block` pixels; each traced block is judged on its own pixels' Stokes I:
  * when at least min_count pixels have a criterion value above `threshold`, every pixel of the
@@ -283,16 +284,30 @@ typedef struct bl_adapt {
 
 enum { BL_CRIT_ABS_GRAD = 0, BL_CRIT_REL_GRAD = 1, BL_CRIT_ABS_LAPL = 2, BL_CRIT_REL_LAPL = 3 };
 
-/* Trace n_images cameras adaptively (one launch pair per level for all images). outs[q].stokes
+/* Trace n_images cameras adaptively (one launch pair per level and wave for all images; the
+ * levels follow each other on the device, without host round trips). outs[q].stokes
  * receives the composite image at the finest resolution, DEVICE [4][nf][nf] with
  * nf = n * 2^max_level, each pixel taking the value of the finest traced pixel covering it
  * (dtype 0 float64 / 1 float32); outs[q].status/steps/samples/end_state/aux are ignored.
  * level_rays (optional HOST int32 [n_images][max_level + 1]) receives the rays traced per level.
- * Synchronises `stream` between levels (refinement decisions are read back). */
+ * Synchronises `stream` at the end. A level holds at most 2^26 rays (BL_EUNSUPPORTED beyond). */
 int blacklight_trace_adaptive(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
                               const bl_grid_t* grids, const double* freqs_hz,
                               const bl_adapt_t* adapt, const bl_out_t* outs, int32_t* level_rays,
                               void* stream);
+/* An adaptive trace (see blacklight_trace_adaptive) prepared as a plan: every level's launches,
+ * the composites, the refinement decisions and the next level's block lists run on the device
+ * without host round trips, captured in one CUDA graph. flags: 0 or BL_UNPOLARIZED. Run with
+ * blacklight_plan_run; blacklight_plan_check or blacklight_plan_level_rays report the last run
+ * (BL_EUNSUPPORTED if a level needed more than 2^26 rays). */
+int blacklight_plan_create_adaptive(int32_t n_images, const bl_camera_t* cams,
+                                    const bl_metric_t* mets, const bl_grid_t* grids,
+                                    const double* freqs_hz, const bl_adapt_t* adapt,
+                                    const bl_out_t* outs, uint32_t flags, void* stream,
+                                    bl_plan_t** plan);
+/* Rays traced per level in the last run of an adaptive plan (HOST int32 [n_images][max_level
+ * + 1]); synchronises `stream`; returns like blacklight_plan_check. */
+int blacklight_plan_level_rays(bl_plan_t* plan, int32_t* level_rays, void* stream);
 
 /* Workspace bytes blacklight_trace_batch uses for these images with its default waves
  * (at most 2^20 rays each). */

@@ -252,8 +252,6 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
     d.aux = o.aux;
     d.ray_offset = offset;
     d.n_rays = (int64_t)c.n * c.n;
-    d.block_list = nullptr;
-    d.block = 0;
 }
 
 struct DevInfo {
@@ -325,16 +323,16 @@ int dev_info(DevInfo& out) {
 template <class T, class R>
 void launch_transfer(int feat, unsigned grid, cudaStream_t st, const bl::ImageDesc* d, int n,
                      int64_t b, int64_t e, const bl::RayHdr* hdr, const R* pool,
-                     const int32_t* chunks, bl::Counters* ctr) {
+                     const int32_t* chunks, bl::Counters* ctr, bl::BlockSource bs) {
     switch (feat & 7) {
-        case 0: bl::transfer_kernel<T, R, 0><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
-        case 1: bl::transfer_kernel<T, R, 1><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
-        case 2: bl::transfer_kernel<T, R, 2><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
-        case 3: bl::transfer_kernel<T, R, 3><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
-        case 4: bl::transfer_kernel<T, R, 4><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
-        case 5: bl::transfer_kernel<T, R, 5><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
-        case 6: bl::transfer_kernel<T, R, 6><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
-        default: bl::transfer_kernel<T, R, 7><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr); break;
+        case 0: bl::transfer_kernel<T, R, 0><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+        case 1: bl::transfer_kernel<T, R, 1><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+        case 2: bl::transfer_kernel<T, R, 2><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+        case 3: bl::transfer_kernel<T, R, 3><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+        case 4: bl::transfer_kernel<T, R, 4><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+        case 5: bl::transfer_kernel<T, R, 5><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+        case 6: bl::transfer_kernel<T, R, 6><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+        default: bl::transfer_kernel<T, R, 7><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
     }
 }
 
@@ -343,6 +341,8 @@ struct LaunchCfg {
     int geo_ctas = 0, tr_ctas = 0;
     int feat = 0;           // transfer variant: bl::kFSlow | kFUnpol | kFAux
     int integrator = BL_INT_DP;
+    bool keep_bad = false;  // leave the bad-ray count of earlier launches in place
+    bl::BlockSource bs{nullptr, nullptr, 0};   // rays from a device block list (adaptive)
 };
 
 // The kernel sequence of one trace on prepared workspace whose image descriptors are already
@@ -366,7 +366,8 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
     bl::ImageDesc* d_desc = (bl::ImageDesc*)(ws + L.descs);
     bl::RayHdr* hdr = (bl::RayHdr*)(ws + L.hdr);
     int32_t* chunks = (int32_t*)(ws + L.chunks);
-    BL_CUDA(cudaMemsetAsync(ctr, 0, sizeof(bl::Counters), st));
+    BL_CUDA(cudaMemsetAsync(ctr, 0, cfg.keep_bad ? offsetof(bl::Counters, bad_rays)
+                                                 : sizeof(bl::Counters), st));
     bl::camera_frame_kernel<<<(n_images + 63) / 64, 64, 0, st>>>(d_desc, n_images);
     ++g_launches;
     BL_CUDA(cudaGetLastError());
@@ -387,23 +388,23 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
             const unsigned rk_grid = (unsigned)(di.sms * pick(cfg.geo_ctas, di.rk_occ[ri]));
             if (precision == BL_PREC_FP64) {
                 bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
-                bl::geodesic_rk_kernel<double><<<rk_grid, 128, 0, st>>>(d_desc, n_images, b, e, hdr, sink, record);
+                bl::geodesic_rk_kernel<double><<<rk_grid, 128, 0, st>>>(d_desc, n_images, b, e, hdr, sink, record, cfg.bs);
             } else {
                 bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
-                bl::geodesic_rk_kernel<float><<<rk_grid, 128, 0, st>>>(d_desc, n_images, b, e, hdr, sink, record);
+                bl::geodesic_rk_kernel<float><<<rk_grid, 128, 0, st>>>(d_desc, n_images, b, e, hdr, sink, record, cfg.bs);
             }
         } else if (precision == BL_PREC_FP64) {
             bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
             bl::geodesic_kernel<double, double><<<geo_grid, 128, 0, st>>>(
-                d_desc, n_images, b, e, hdr, sink, record);
+                d_desc, n_images, b, e, hdr, sink, record, cfg.bs);
         } else {
             bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
             if (precision == BL_PREC_MIXED)
                 bl::geodesic_kernel<float, double><<<geo_grid, 128, 0, st>>>(
-                    d_desc, n_images, b, e, hdr, sink, record);
+                    d_desc, n_images, b, e, hdr, sink, record, cfg.bs);
             else
                 bl::geodesic_kernel<float, bl::df64><<<geo_grid, 128, 0, st>>>(
-                    d_desc, n_images, b, e, hdr, sink, record);
+                    d_desc, n_images, b, e, hdr, sink, record, cfg.bs);
         }
         ++g_launches;
         BL_CUDA(cudaGetLastError());
@@ -414,16 +415,16 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
             if (mlp) {
                 if (slow)
                     bl::transfer_mlp_kernel<float, true><<<tr_grid, 128, 0, st>>>(
-                        d_desc, n_images, b, e, hdr, fpool, chunks, mlp, ctr);
+                        d_desc, n_images, b, e, hdr, fpool, chunks, mlp, ctr, cfg.bs);
                 else
                     bl::transfer_mlp_kernel<float, false><<<tr_grid, 128, 0, st>>>(
-                        d_desc, n_images, b, e, hdr, fpool, chunks, mlp, ctr);
+                        d_desc, n_images, b, e, hdr, fpool, chunks, mlp, ctr, cfg.bs);
             } else if (precision != BL_PREC_FP64) {
                 launch_transfer<float, float>(cfg.feat, tr_grid, st, d_desc, n_images, b, e, hdr,
-                                              fpool, chunks, ctr);
+                                              fpool, chunks, ctr, cfg.bs);
             } else {
                 launch_transfer<double, double>(cfg.feat, tr_grid, st, d_desc, n_images, b, e,
-                                                hdr, dpool, chunks, ctr);
+                                                hdr, dpool, chunks, ctr, cfg.bs);
             }
             ++g_launches;
             BL_CUDA(cudaGetLastError());
@@ -610,6 +611,8 @@ std::map<TuneKey, TuneVal> g_tune_cache;
 
 }  // namespace
 
+namespace { struct AdaptRun; }
+
 struct bl_plan {
     int dev = 0;
     int32_t n_images = 0;
@@ -625,6 +628,7 @@ struct bl_plan {
     int64_t kernels_per_run = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    AdaptRun* adapt = nullptr;   // adaptive plans: the device-driven multi-level sequence
 };
 
 namespace {
@@ -717,6 +721,8 @@ int plan_autotune(bl_plan& P, cudaStream_t st) {
     return 0;
 }
 
+int adapt_enqueue(AdaptRun& R, cudaStream_t st);
+
 int plan_capture(bl_plan& P, cudaStream_t user) {
     DevInfo di;                      // occupancy queries happen before, not during, capture
     if (int rc0 = dev_info(di)) return rc0;
@@ -735,10 +741,14 @@ int plan_capture(bl_plan& P, cudaStream_t user) {
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamBeginCapture");
     }
     if (!rc) {
-        LaunchCfg c = P.cfg;
-        c.feat = P.feat;
-        c.integrator = P.descs[0].integrator;
-        rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, c);
+        if (P.adapt) {
+            rc = adapt_enqueue(*P.adapt, st);
+        } else {
+            LaunchCfg c = P.cfg;
+            c.feat = P.feat;
+            c.integrator = P.descs[0].integrator;
+            rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, c);
+        }
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(st, &g);
         if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamEndCapture");
@@ -804,172 +814,211 @@ int check_adapt(const bl_adapt_t* ad, const bl_camera_t* cams, int32_t n_images)
     return 0;
 }
 
-// Adaptive tracing driven level by level from the host (refinement decisions are read back).
-int trace_adaptive_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
-                        const bl_grid_t* grids, const double* freqs, const bl_adapt_t* ad,
-                        const bl_out_t* outs, int32_t* level_rays, cudaStream_t st,
-                        const float* mlp) {
-    const int B = ad->block, maxL = ad->max_level;
-    const int precision = mets[0].precision;
-    const size_t vsize = precision == BL_PREC_FP64 ? sizeof(double) : sizeof(float);
-    // host block lists per image for the current level: (bx, by) pairs
-    std::vector<std::vector<int32_t>> blocks(n_images);
-    for (int q = 0; q < n_images; ++q) {
-        const int nb = cams[q].n / B;
-        for (int by = 0; by < nb; ++by)
-            for (int bx = 0; bx < nb; ++bx) { blocks[q].push_back(bx); blocks[q].push_back(by); }
+// ---------------------------------------------------------------------------------------
+// Adaptive tracing (Sec. 4) driven entirely on the device: each level's blocks of all images
+// form one device block list (image, bx, by); the persistent kernels take their rays from it,
+// the level is painted into the composites, its blocks are judged, and a one-CTA scan writes
+// the next level's list. No host round trip between levels, so the whole sequence can be
+// captured in a CUDA graph.
+// ---------------------------------------------------------------------------------------
+constexpr int64_t kMaxAdaptLevelRays = 1ll << 26;   // capacity of one level (67M rays)
+
+struct AdaptRun {
+    int32_t n_images = 0, max_level = 0, B = 0, precision = 0, feat = 0;
+    const float* mlp = nullptr;
+    bl_adapt_t ad{};
+    size_t vsize = 4;
+    std::vector<int64_t> cap_blocks;        // per level
+    int64_t max_cap_rays = 0;
+    Layout L{};                             // trace workspace (waves)
+    char* mem = nullptr;                    // one allocation for everything below
+    size_t mem_bytes = 0;
+    char* ws = nullptr;
+    bl::ImageDesc* descs = nullptr;         // [levels][n_images]
+    std::vector<int32_t*> entries;          // per level
+    unsigned long long* counts = nullptr;   // [levels] blocks, then [levels][n_images], overflow
+    int8_t* flags = nullptr;
+    char* lvl = nullptr;                    // [4][max_cap_rays] compact Stokes
+    bl::OutDesc* outd = nullptr;
+    // host copies uploaded once
+    std::vector<bl::ImageDesc> h_descs;
+    std::vector<int32_t> h_root;
+    std::vector<unsigned long long> h_counts0;
+    std::vector<bl::OutDesc> h_outd;
+};
+
+int adapt_prepare(AdaptRun& R, int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                  const bl_grid_t* grids, const double* freqs, const bl_adapt_t* ad,
+                  const bl_out_t* outs, const float* mlp, uint32_t flags, cudaStream_t st,
+                  bool persistent) {
+    R.n_images = n_images;
+    R.max_level = ad->max_level;
+    R.B = ad->block;
+    R.ad = *ad;
+    R.precision = mets[0].precision;
+    R.mlp = mlp;
+    R.vsize = R.precision == BL_PREC_FP64 ? sizeof(double) : sizeof(float);
+    if (flags & BL_UNPOLARIZED) R.feat |= bl::kFUnpol;
+    for (int q = 0; q < n_images; ++q)
+        if (grids[q].n_snapshots > 1) R.feat |= bl::kFSlow;
+    const int64_t b2 = (int64_t)R.B * R.B;
+    int64_t root = 0;
+    for (int q = 0; q < n_images; ++q) root += (int64_t)(cams[q].n / R.B) * (cams[q].n / R.B);
+    R.cap_blocks.resize(R.max_level + 1);
+    for (int l = 0; l <= R.max_level; ++l) {
+        double c = (double)root * std::pow(4.0, l);
+        const double lim = (double)(kMaxAdaptLevelRays / b2);
+        R.cap_blocks[l] = (int64_t)(c < lim ? c : lim);
+        if (R.cap_blocks[l] < root && l == 0) R.cap_blocks[l] = root;
+        R.max_cap_rays = std::max(R.max_cap_rays, R.cap_blocks[l] * b2);
     }
-    // device buffers grow as needed
-    char* ws = nullptr; size_t ws_bytes = 0;
-    char* lvl = nullptr; size_t lvl_bytes = 0;           // compact Stokes of the level
-    int32_t* dblk = nullptr; size_t dblk_bytes = 0;      // block lists of the level
-    int8_t* dflags = nullptr; size_t dflags_bytes = 0;
-    auto grow = [&](void** p, size_t& have, size_t need) -> int {
-        if (need <= have) return 0;
-        if (*p) cudaFreeAsync(*p, st);
-        *p = nullptr;
-        const size_t n = need;
-        cudaError_t e = cudaMallocAsync(p, n, st);
-        if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync(%zu): %s", n, cudaGetErrorString(e)); }
-        have = n;
-        return 0;
-    };
-    int rc = 0;
-    unsigned long long bad_total = 0;
-    for (int L = 0; L <= maxL && rc == 0; ++L) {
-        // rays of this level, per image, and offsets into the compact buffers
-        std::vector<int64_t> nrays(n_images), roff(n_images), boff(n_images);
-        int64_t rays = 0, nblk = 0;
+    R.L = make_layout_rays(n_images, R.max_cap_rays, R.precision, true,
+                           chunks_per_ray(n_images, cams, mets));
+    // one allocation: trace workspace, descriptors, block lists, counts, flags, Stokes, outputs
+    const int levels = R.max_level + 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes); return o; };
+    const size_t o_ws = take(R.L.total);
+    const size_t o_desc = take(sizeof(bl::ImageDesc) * levels * n_images);
+    std::vector<size_t> o_ent(levels);
+    for (int l = 0; l < levels; ++l) o_ent[l] = take(sizeof(int32_t) * 3 * R.cap_blocks[l]);
+    const size_t n_counts = levels + (size_t)levels * n_images + 1;
+    const size_t o_cnt = take(sizeof(unsigned long long) * n_counts);
+    int64_t max_flags = 1;
+    for (int l = 0; l < R.max_level; ++l) max_flags = std::max(max_flags, R.cap_blocks[l]);
+    const size_t o_flags = take((size_t)max_flags);
+    const size_t o_lvl = take(4 * R.vsize * (size_t)R.max_cap_rays);
+    const size_t o_out = take(sizeof(bl::OutDesc) * n_images);
+    R.mem_bytes = off;
+    cudaError_t e = persistent ? cudaMalloc((void**)&R.mem, off)
+                               : cudaMallocAsync((void**)&R.mem, off, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        R.mem = nullptr;
+        return fail(BL_ENOMEM, "adaptive buffers (%zu bytes): %s", off, cudaGetErrorString(e));
+    }
+    R.ws = R.mem + o_ws;
+    R.descs = (bl::ImageDesc*)(R.mem + o_desc);
+    R.entries.resize(levels);
+    for (int l = 0; l < levels; ++l) R.entries[l] = (int32_t*)(R.mem + o_ent[l]);
+    R.counts = (unsigned long long*)(R.mem + o_cnt);
+    R.flags = (int8_t*)(R.mem + o_flags);
+    R.lvl = R.mem + o_lvl;
+    R.outd = (bl::OutDesc*)(R.mem + o_out);
+    // level descriptors: camera at n 2^L, compact Stokes in planes of the level's capacity
+    R.h_descs.resize((size_t)levels * n_images);
+    for (int l = 0; l < levels; ++l)
         for (int q = 0; q < n_images; ++q) {
-            const int64_t nb = (int64_t)blocks[q].size() / 2;
-            nrays[q] = nb * B * B;
-            roff[q] = rays;
-            boff[q] = nblk;
-            rays += nrays[q];
-            nblk += nb;
-            if (level_rays) level_rays[q * (maxL + 1) + L] = (int32_t)nrays[q];
-        }
-        if (rays == 0) break;
-        std::vector<int32_t> hblk;
-        hblk.reserve(2 * nblk);
-        for (int q = 0; q < n_images; ++q) hblk.insert(hblk.end(), blocks[q].begin(), blocks[q].end());
-        if ((rc = grow((void**)&dblk, dblk_bytes, hblk.size() * sizeof(int32_t)))) break;
-        if ((rc = grow((void**)&lvl, lvl_bytes, 4 * (size_t)rays * vsize))) break;
-        BL_CUDA(cudaMemcpyAsync(dblk, hblk.data(), hblk.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        // one descriptor per image that has rays at this level
-        std::vector<bl::ImageDesc> descs;
-        std::vector<int> qmap;
-        int64_t off = 0;
-        for (int q = 0; q < n_images; ++q) {
-            if (!nrays[q]) continue;
             bl_camera_t c = cams[q];
-            c.n = cams[q].n << L;
-            bl_out_t o{sizeof(bl_out_t), nullptr, precision == BL_PREC_FP64 ? 0 : 1, nullptr, nullptr,
-                       nullptr, nullptr};
-            bl::ImageDesc d;
-            fill_desc(d, c, mets[q], grids[q], freqs[q], o, off);
-            d.n_rays = nrays[q];
-            d.block_list = dblk + 2 * boff[q];
-            d.block = B;
-            // the compact Stokes of this image: planes of length n_rays at lvl + 4 * roff
-            d.stokes = lvl + 4 * roff[q] * vsize;
-            descs.push_back(d);
-            qmap.push_back(q);
-            off += nrays[q];
+            c.n = cams[q].n << l;
+            bl_out_t o{sizeof(bl_out_t), nullptr, R.precision == BL_PREC_FP64 ? 0 : 1, nullptr,
+                       nullptr, nullptr, nullptr, nullptr};
+            bl::ImageDesc& d = R.h_descs[(size_t)l * n_images + q];
+            fill_desc(d, c, mets[q], grids[q], freqs[q], o, 0);
+            d.stokes = R.lvl;
+            d.n_rays = R.cap_blocks[l] * b2;
         }
-        Layout Ly = make_layout_rays((int32_t)descs.size(), rays, precision, true,
-                                     chunks_per_ray(n_images, cams, mets));
-        if ((rc = grow((void**)&ws, ws_bytes, Ly.total))) break;
-        if ((rc = launch_all((int32_t)descs.size(), descs, ws, Ly, precision, true, st, false, mlp))) break;
-        unsigned long long bad = 0, tmo = 0;
-        BL_CUDA(cudaMemcpyAsync(&bad, &((bl::Counters*)(ws + Ly.counters))->bad_rays, sizeof(bad),
-                                cudaMemcpyDeviceToHost, st));
-        BL_CUDA(cudaMemcpyAsync(&tmo, &((bl::Counters*)(ws + Ly.counters))->mlp_timeouts,
-                                sizeof(tmo), cudaMemcpyDeviceToHost, st));
-        // composite: paint this level into each image's finest-resolution output
-        const int s = 1 << (maxL - L);
-        for (size_t k = 0; k < descs.size(); ++k) {
-            const int q = qmap[k];
-            const int nf = cams[q].n << maxL;
-            const int64_t nr = nrays[q];
-            const int threads = 256;
-            const unsigned grid_n = (unsigned)((nr + threads - 1) / threads);
-            char* st_q = lvl + 4 * roff[q] * vsize;
-            const int32_t* bl_q = dblk + 2 * boff[q];
-            if (precision == BL_PREC_FP64) {
-                if (outs[q].dtype == 0)
-                    bl::adapt_composite_kernel<double, double><<<grid_n, threads, 0, st>>>((const double*)st_q, nr, bl_q, B, s, nf, (double*)outs[q].stokes);
-                else
-                    bl::adapt_composite_kernel<double, float><<<grid_n, threads, 0, st>>>((const double*)st_q, nr, bl_q, B, s, nf, (float*)outs[q].stokes);
-            } else {
-                if (outs[q].dtype == 0)
-                    bl::adapt_composite_kernel<float, double><<<grid_n, threads, 0, st>>>((const float*)st_q, nr, bl_q, B, s, nf, (double*)outs[q].stokes);
-                else
-                    bl::adapt_composite_kernel<float, float><<<grid_n, threads, 0, st>>>((const float*)st_q, nr, bl_q, B, s, nf, (float*)outs[q].stokes);
+    // root block list (image-major, blocks row by row) and level-0 counts
+    R.h_root.clear();
+    R.h_counts0.assign(n_counts, 0ull);
+    R.h_counts0[0] = (unsigned long long)root;
+    for (int q = 0; q < n_images; ++q) {
+        const int nb = cams[q].n / R.B;
+        for (int by = 0; by < nb; ++by)
+            for (int bx = 0; bx < nb; ++bx) {
+                R.h_root.push_back(q); R.h_root.push_back(bx); R.h_root.push_back(by);
             }
-            ++g_launches;
-            BL_CUDA(cudaGetLastError());
-        }
-        if (L == maxL) {
-            BL_CUDA(cudaStreamSynchronize(st));
-            bad_total += bad;
-            if (tmo) rc = fail(BL_ECUDA, "tensor-core wait ran out in %llu CTAs", tmo);
-            break;
-        }
-        // refinement decisions for every block of this level
-        if ((rc = grow((void**)&dflags, dflags_bytes, (size_t)nblk))) break;
-        for (size_t k = 0; k < descs.size(); ++k) {
-            const int q = qmap[k];
-            const int64_t nb = nrays[q] / ((int64_t)B * B);
-            const unsigned grid_n = (unsigned)((nb + 127) / 128);
-            char* st_q = lvl + 4 * roff[q] * vsize;     // plane 0 = Stokes I
-            if (precision == BL_PREC_FP64)
-                bl::adapt_criterion_kernel<double><<<grid_n, 128, 0, st>>>((const double*)st_q, nb, B, ad->criterion, ad->threshold, ad->min_count, ad->min_intensity, dflags + boff[q]);
-            else
-                bl::adapt_criterion_kernel<float><<<grid_n, 128, 0, st>>>((const float*)st_q, nb, B, ad->criterion, ad->threshold, ad->min_count, ad->min_intensity, dflags + boff[q]);
-            ++g_launches;
-            BL_CUDA(cudaGetLastError());
-        }
-        std::vector<int8_t> hflags(nblk);
-        BL_CUDA(cudaMemcpyAsync(hflags.data(), dflags, nblk, cudaMemcpyDeviceToHost, st));
-        BL_CUDA(cudaStreamSynchronize(st));
-        bad_total += bad;
-        if (tmo) { rc = fail(BL_ECUDA, "tensor-core wait ran out in %llu CTAs", tmo); break; }
-        // children of refined blocks, in parent order: (2bx+dx, 2by+dy), dy then dx
-        for (int q = 0; q < n_images; ++q) {
-            std::vector<int32_t> next;
-            const int64_t nb = (int64_t)blocks[q].size() / 2;
-            for (int64_t b = 0; b < nb; ++b) {
-                if (!hflags[boff[q] + b]) continue;
-                const int32_t bx = blocks[q][2 * b], by = blocks[q][2 * b + 1];
-                for (int dy = 0; dy < 2; ++dy)
-                    for (int dx = 0; dx < 2; ++dx) { next.push_back(2 * bx + dx); next.push_back(2 * by + dy); }
-            }
-            blocks[q].swap(next);
-        }
-        if (level_rays)
-            for (int q = 0; q < n_images; ++q)
-                for (int LL = L + 1; LL <= maxL; ++LL) level_rays[q * (maxL + 1) + LL] = 0;
+        R.h_counts0[levels + q] = (unsigned long long)nb * nb;
     }
-    if (ws) cudaFreeAsync(ws, st);
-    if (lvl) cudaFreeAsync(lvl, st);
-    if (dblk) cudaFreeAsync(dblk, st);
-    if (dflags) cudaFreeAsync(dflags, st);
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (rc == 0 && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
-    if (rc == 0 && bad_total) rc = BL_WRAYS;
-    return rc;
+    R.h_outd.resize(n_images);
+    for (int q = 0; q < n_images; ++q)
+        R.h_outd[q] = bl::OutDesc{outs[q].stokes, cams[q].n << R.max_level, outs[q].dtype};
+    BL_CUDA(cudaMemcpyAsync(R.descs, R.h_descs.data(), sizeof(bl::ImageDesc) * R.h_descs.size(),
+                            cudaMemcpyHostToDevice, st));
+    BL_CUDA(cudaMemcpyAsync(R.entries[0], R.h_root.data(), sizeof(int32_t) * R.h_root.size(),
+                            cudaMemcpyHostToDevice, st));
+    BL_CUDA(cudaMemcpyAsync(R.outd, R.h_outd.data(), sizeof(bl::OutDesc) * n_images,
+                            cudaMemcpyHostToDevice, st));
+    // the host vectors must outlive the copies from pageable memory: synchronise
+    BL_CUDA(cudaStreamSynchronize(st));
+    return 0;
 }
 
-}  // namespace
+// Enqueue one adaptive trace (all levels) on st.
+int adapt_enqueue(AdaptRun& R, cudaStream_t st) {
+    const int levels = R.max_level + 1;
+    const int64_t b2 = (int64_t)R.B * R.B;
+    const size_t n_counts = levels + (size_t)levels * R.n_images + 1;
+    // counts: level 0 from the host values; the rest zero
+    BL_CUDA(cudaMemcpyAsync(R.counts, R.h_counts0.data(), sizeof(unsigned long long) * n_counts,
+                            cudaMemcpyHostToDevice, st));
+    BL_CUDA(cudaMemsetAsync(R.ws + R.L.counters, 0, sizeof(bl::Counters), st));
+    unsigned long long* per_image = R.counts + levels;
+    unsigned long long* overflow = R.counts + levels + (size_t)levels * R.n_images;
+    for (int l = 0; l < levels; ++l) {
+        BL_CUDA(cudaMemcpyAsync(R.ws + R.L.descs, R.descs + (size_t)l * R.n_images,
+                                sizeof(bl::ImageDesc) * R.n_images, cudaMemcpyDeviceToDevice, st));
+        Layout Ll = R.L;
+        Ll.rays = R.cap_blocks[l] * b2;
+        LaunchCfg cfg;
+        cfg.feat = R.feat;
+        cfg.integrator = R.h_descs[0].integrator;
+        cfg.keep_bad = true;
+        cfg.bs = bl::BlockSource{R.entries[l], R.counts + l, R.B};
+        int rc = launch_kernels(R.n_images, R.ws, Ll, R.precision, true, st, false, R.mlp, cfg);
+        if (rc) return rc;
+        const int s = 1 << (R.max_level - l);
+        const unsigned grid_r = (unsigned)((Ll.rays + 255) / 256);
+        if (R.precision == BL_PREC_FP64)
+            bl::adapt_composite_kernel<double><<<grid_r, 256, 0, st>>>((const double*)R.lvl, Ll.rays, cfg.bs, s, R.outd);
+        else
+            bl::adapt_composite_kernel<float><<<grid_r, 256, 0, st>>>((const float*)R.lvl, Ll.rays, cfg.bs, s, R.outd);
+        ++g_launches;
+        BL_CUDA(cudaGetLastError());
+        if (l == R.max_level) break;
+        const unsigned grid_b = (unsigned)((R.cap_blocks[l] + 127) / 128);
+        const bl_adapt_t& ad = R.ad;
+        if (R.precision == BL_PREC_FP64)
+            bl::adapt_criterion_kernel<double><<<grid_b, 128, 0, st>>>((const double*)R.lvl, R.cap_blocks[l], R.B, ad.criterion, ad.threshold, ad.min_count, ad.min_intensity, R.flags, R.counts + l);
+        else
+            bl::adapt_criterion_kernel<float><<<grid_b, 128, 0, st>>>((const float*)R.lvl, R.cap_blocks[l], R.B, ad.criterion, ad.threshold, ad.min_count, ad.min_intensity, R.flags, R.counts + l);
+        bl::adapt_refine_kernel<<<1, 1024, 0, st>>>(R.flags, R.entries[l], R.counts + l,
+                                                    R.entries[l + 1], R.counts + l + 1,
+                                                    (unsigned long long)R.cap_blocks[l + 1],
+                                                    per_image + (size_t)(l + 1) * R.n_images,
+                                                    overflow);
+        g_launches += 2;
+        BL_CUDA(cudaGetLastError());
+    }
+    return 0;
+}
 
-extern "C" {
+// Read back the level counts and anomalies of the last run (synchronises st).
+int adapt_finish(AdaptRun& R, int32_t* level_rays, cudaStream_t st) {
+    const int levels = R.max_level + 1;
+    const size_t n_counts = levels + (size_t)levels * R.n_images + 1;
+    std::vector<unsigned long long> h(n_counts);
+    bl::Counters c{};
+    BL_CUDA(cudaMemcpyAsync(h.data(), R.counts, sizeof(unsigned long long) * n_counts,
+                            cudaMemcpyDeviceToHost, st));
+    BL_CUDA(cudaMemcpyAsync(&c, R.ws + R.L.counters, sizeof(c), cudaMemcpyDeviceToHost, st));
+    BL_CUDA(cudaStreamSynchronize(st));
+    const int64_t b2 = (int64_t)R.B * R.B;
+    if (level_rays)
+        for (int q = 0; q < R.n_images; ++q)
+            for (int l = 0; l < levels; ++l)
+                level_rays[q * levels + l] = (int32_t)(h[levels + (size_t)l * R.n_images + q] * b2);
+    if (c.mlp_timeouts) return fail(BL_ECUDA, "tensor-core wait ran out in %llu CTAs", c.mlp_timeouts);
+    if (h[n_counts - 1])
+        return fail(BL_EUNSUPPORTED, "adaptive refinement exceeded a level's capacity of %lld rays",
+                    (long long)kMaxAdaptLevelRays);
+    return c.bad_rays ? BL_WRAYS : BL_OK;
+}
 
-int blacklight_trace_adaptive(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
-                              const bl_grid_t* grids, const double* freqs_hz,
-                              const bl_adapt_t* adapt, const bl_out_t* outs, int32_t* level_rays,
-                              void* stream) {
-    g_detail[0] = 0;
+int check_adaptive_args(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                        const bl_grid_t* grids, const double* freqs_hz, const bl_adapt_t* adapt,
+                        const bl_out_t* outs, uint32_t flags, int* precision_out,
+                        const float** mlp_out) {
     if (n_images < 1) return fail(BL_EINVAL, "n_images must be >= 1");
     if (!cams || !mets || !grids || !freqs_hz || !outs) return fail(BL_EINVAL, "NULL array argument");
     int precision = -1;
@@ -990,10 +1039,48 @@ int blacklight_trace_adaptive(int32_t n_images, const bl_camera_t* cams, const b
     }
     int rc = check_adapt(adapt, cams, n_images);
     if (rc) return rc;
+    if (flags & ~(uint32_t)BL_UNPOLARIZED) return fail(BL_EINVAL, "adaptive flags: BL_UNPOLARIZED only");
     const float* mlp = nullptr;
-    if ((rc = common_mlp(n_images, grids, precision, &mlp))) return rc;
+    if ((rc = common_mlp(n_images, grids, precision, &mlp, flags))) return rc;
+    for (int q = 0; q < n_images; ++q)
+        if (mets[q].integrator != mets[0].integrator)
+            return fail(BL_EINVAL, "all images must share metric.integrator");
+    *precision_out = precision;
+    *mlp_out = mlp;
+    return 0;
+}
+
+int trace_adaptive_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                        const bl_grid_t* grids, const double* freqs, const bl_adapt_t* ad,
+                        const bl_out_t* outs, int32_t* level_rays, cudaStream_t st,
+                        const float* mlp, uint32_t flags) {
+    AdaptRun R;
+    int rc = adapt_prepare(R, n_images, cams, mets, grids, freqs, ad, outs, mlp, flags, st, false);
+    if (rc) return rc;
+    rc = adapt_enqueue(R, st);
+    if (!rc) rc = adapt_finish(R, level_rays, st);
+    cudaFreeAsync(R.mem, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (rc == 0 && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int blacklight_trace_adaptive(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                              const bl_grid_t* grids, const double* freqs_hz,
+                              const bl_adapt_t* adapt, const bl_out_t* outs, int32_t* level_rays,
+                              void* stream) {
+    g_detail[0] = 0;
+    int precision = -1;
+    const float* mlp = nullptr;
+    int rc = check_adaptive_args(n_images, cams, mets, grids, freqs_hz, adapt, outs, 0,
+                                 &precision, &mlp);
+    if (rc) return rc;
     return trace_adaptive_impl(n_images, cams, mets, grids, freqs_hz, adapt, outs, level_rays,
-                               (cudaStream_t)stream, mlp);
+                               (cudaStream_t)stream, mlp, 0);
 }
 
 int blacklight_adapt_flags(int64_t n_blocks, const double* I, const bl_adapt_t* adapt,
@@ -1114,7 +1201,9 @@ int blacklight_plan_run(bl_plan_t* plan, void* stream) {
 
 int blacklight_plan_check(bl_plan_t* plan, void* stream) {
     g_detail[0] = 0;
-    if (!plan || !plan->ws) return fail(BL_EINVAL, "plan is NULL");
+    if (!plan) return fail(BL_EINVAL, "plan is NULL");
+    if (plan->adapt) return adapt_finish(*plan->adapt, nullptr, (cudaStream_t)stream);
+    if (!plan->ws) return fail(BL_EINVAL, "plan is not built");
     return finish(plan->ws, plan->L, (cudaStream_t)stream, true);
 }
 
@@ -1140,8 +1229,49 @@ int blacklight_plan_destroy(bl_plan_t* plan) {
     if (plan->exec) cudaGraphExecDestroy(plan->exec);
     if (plan->graph) cudaGraphDestroy(plan->graph);
     if (plan->ws) cudaFree(plan->ws);
+    if (plan->adapt) {
+        if (plan->adapt->mem) cudaFree(plan->adapt->mem);
+        delete plan->adapt;
+    }
     delete plan;
     return 0;
+}
+
+int blacklight_plan_create_adaptive(int32_t n_images, const bl_camera_t* cams,
+                                    const bl_metric_t* mets, const bl_grid_t* grids,
+                                    const double* freqs_hz, const bl_adapt_t* adapt,
+                                    const bl_out_t* outs, uint32_t flags, void* stream,
+                                    bl_plan_t** plan) {
+    g_detail[0] = 0;
+    if (!plan) return fail(BL_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    int precision = -1;
+    const float* mlp = nullptr;
+    int rc = check_adaptive_args(n_images, cams, mets, grids, freqs_hz, adapt, outs, flags,
+                                 &precision, &mlp);
+    if (rc) return rc;
+    bl_plan* P = new bl_plan();
+    BL_CUDA(cudaGetDevice(&P->dev));
+    P->n_images = n_images;
+    P->precision = precision;
+    P->mlp = mlp;
+    P->adapt = new AdaptRun();
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = adapt_prepare(*P->adapt, n_images, cams, mets, grids, freqs_hz, adapt, outs, mlp, flags,
+                       st, true);
+    if (!rc) rc = plan_capture(*P, st);
+    if (rc) {
+        blacklight_plan_destroy(P);
+        return rc;
+    }
+    *plan = P;
+    return 0;
+}
+
+int blacklight_plan_level_rays(bl_plan_t* plan, int32_t* level_rays, void* stream) {
+    g_detail[0] = 0;
+    if (!plan || !plan->adapt) return fail(BL_EINVAL, "not an adaptive plan");
+    return adapt_finish(*plan->adapt, level_rays, (cudaStream_t)stream);
 }
 
 int blacklight_trace_batch(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,

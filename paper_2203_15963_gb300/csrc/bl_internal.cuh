@@ -45,13 +45,8 @@ struct ImageDesc {
     void* aux;              // auxiliary images [26][n_rays] (dtype as stokes) or nullptr
     int64_t ray_offset;     // first global ray index of this image
     int64_t n_rays;         // rays traced for this image (n * n, or blocks x block^2)
-    // Block-list mode (adaptive refinement): when block_list is set, ray p traces pixel
-    // (bx * block + u, by * block + v) of the n x n pixel grid, with (bx, by) =
-    // block_list[2 (p / block^2)], and u, v the row-major position inside the block; outputs
-    // are then compact, indexed by p (Stokes [4][n_rays]).
-    const int32_t* block_list;
-    int32_t block;
-    int32_t order;          // ray order without a block list: 0 Morton (n a power of 2), 1 rows
+    int32_t order;          // ray order: 0 Morton (n a power of 2), 1 rows
+    int32_t pad2_;
     // filled by the camera-frame kernel
     double x_cam[4], u_cam[4], kk[4], hh[4], vv[4];
     double r_cam, r_hor;
@@ -78,6 +73,16 @@ struct RayHdr {
     double nnorm;    // frequency normalisation n per unit nu (Sec. 2.1)
     int32_t nrec;    // samples recorded
     int32_t status;  // BL_RAY_*
+};
+
+// Rays taken from a device block list (adaptive levels) instead of consecutive image ranges:
+// ray r traces pixel (bx B + r % B, by B + (r / B) % B) of image q, where (q, bx, by) =
+// entries[r / B^2]; the number of blocks is read from the device, so a kernel earlier in the
+// same stream may produce the list. Outputs are then indexed by r.
+struct BlockSource {
+    const int32_t* entries;               // [blocks][3] or nullptr (image ranges)
+    const unsigned long long* count;      // blocks in the list
+    int32_t block;                        // B
 };
 
 struct Counters {

@@ -150,16 +150,34 @@ __device__ __forceinline__ int find_image(const ImageDesc* imgs, int n_images, i
 // covers a compact 8x4 patch of the image, else row-major.
 __device__ __forceinline__ void pixel_of(int64_t p, int n, int order, int& i, int& j);
 __device__ __forceinline__ int64_t ray_pixel(const ImageDesc& im, int64_t p, int& i, int& j) {
-    if (im.block_list) {
-        const int64_t b2 = (int64_t)im.block * im.block;
-        const int64_t blk = p / b2;
-        const int r = (int)(p - blk * b2);
-        i = im.block_list[2 * blk] * im.block + r % im.block;
-        j = im.block_list[2 * blk + 1] * im.block + r / im.block;
-        return p;
-    }
     pixel_of(p, im.n, im.order, i, j);
     return (int64_t)j * im.n + i;
+}
+
+// Image, pixel and output index of global ray `ray`: from the device block list when there is
+// one (adaptive levels), else from the images' consecutive ray ranges.
+__device__ __forceinline__ void setup_ray(const ImageDesc* imgs, int n_images, const BlockSource& bs,
+                                          int64_t ray, int& q, int64_t& opix, int& i, int& j) {
+    if (bs.entries) {
+        const int B = bs.block;
+        const int64_t b2 = (int64_t)B * B;
+        const int64_t blk = ray / b2;
+        const int r = (int)(ray - blk * b2);
+        q = bs.entries[3 * blk];
+        i = bs.entries[3 * blk + 1] * B + r % B;
+        j = bs.entries[3 * blk + 2] * B + r / B;
+        opix = ray;
+    } else {
+        q = find_image(imgs, n_images, ray);
+        opix = ray_pixel(imgs[q], ray - imgs[q].ray_offset, i, j);
+    }
+}
+
+// End of this launch's ray range: a block list may hold fewer rays than the launch covers.
+__device__ __forceinline__ int64_t wave_end(const BlockSource& bs, int64_t ray_end) {
+    if (!bs.entries) return ray_end;
+    const int64_t avail = (int64_t)(*bs.count) * bs.block * bs.block;
+    return avail < ray_end ? avail : ray_end;
 }
 
 __device__ __forceinline__ void pixel_of(int64_t p, int n, int order, int& i, int& j) {
@@ -453,10 +471,12 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                                                           int n_images, int64_t ray_begin,
                                                           int64_t ray_end,
                                                           RayHdr* __restrict__ hdr,
-                                                          RecordSink<R> sink, int record) {
+                                                          RecordSink<R> sink, int record,
+                                                          BlockSource bs) {
     // rays [ray_begin, ray_end) of the batch form this wave; hdr and the chunk tables are
     // indexed by ray - ray_begin
-    const int64_t total_rays = ray_end - ray_begin;
+    const int64_t re = wave_end(bs, ray_end);
+    const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
     using A = GeoArith<G>;
     // compile-time constants in the integrator arithmetic (a run-time double -> df64 split
     // would cost FP64 conversions)
@@ -542,9 +562,8 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
         if (!__any_sync(0xffffffffu, active)) break;
         if (!active) continue;
         if (need) {   // a ray taken from the queue in this iteration: set it up
-            q = find_image(imgs, n_images, ray);
+            setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
             const ImageDesc& im = imgs[q];
-            opix = ray_pixel(im, ray - im.ray_offset, pi, pj);
             double yd[8];
             pixel_state(im, pi, pj, yd, nnorm);
 #pragma unroll
@@ -843,8 +862,10 @@ __global__ void __launch_bounds__(128, 3) geodesic_rk_kernel(const ImageDesc* __
                                                              int n_images, int64_t ray_begin,
                                                              int64_t ray_end,
                                                              RayHdr* __restrict__ hdr,
-                                                             RecordSink<R> sink, int record) {
-    const int64_t total_rays = ray_end - ray_begin;
+                                                             RecordSink<R> sink, int record,
+                                                             BlockSource bs) {
+    const int64_t re = wave_end(bs, ray_end);
+    const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
     Counters* ctr = sink.ctr;
     bool active = false, exhausted = false;
     int64_t ray = 0, wray = 0, opix = 0;
@@ -867,9 +888,8 @@ __global__ void __launch_bounds__(128, 3) geodesic_rk_kernel(const ImageDesc* __
         if (!__any_sync(0xffffffffu, active)) break;
         if (!active) continue;
         if (need) {
-            q = find_image(imgs, n_images, ray);
+            setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
             const ImageDesc& im = imgs[q];
-            opix = ray_pixel(im, ray - im.ray_offset, pi, pj);
             pixel_state(im, pi, pj, y, nnorm);
             a = im.spin; m = im.mass; flat = im.flat != 0;
             r_cam = im.r_cam; r_hor = im.r_hor;
@@ -1329,11 +1349,12 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
                                                        const RayHdr* __restrict__ hdr,
                                                        const R* __restrict__ pool,
                                                        const int32_t* __restrict__ chunks,
-                                                       Counters* ctr) {
+                                                       Counters* ctr, BlockSource bs) {
     constexpr bool kSlow = (kF & kFSlow) != 0;
     constexpr bool kUnpol = (kF & kFUnpol) != 0;
     constexpr bool kAux = (kF & kFAux) != 0;
-    const int64_t total_rays = ray_end - ray_begin;
+    const int64_t re = wave_end(bs, ray_end);
+    const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
     int64_t wray = 0;
     bool active = false;
     int64_t ray = 0, opix = 0;
@@ -1359,9 +1380,8 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
         if (!__any_sync(0xffffffffu, active || (need && !exhausted))) break;
         if (!active && !(need && !exhausted)) continue;
         if (!active) {
-            q = find_image(imgs, n_images, ray);
+            setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
             const ImageDesc& im = imgs[q];
-            opix = ray_pixel(im, ray - im.ray_offset, pi, pj);
             const RayHdr hd = hdr[wray];
             if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) {
                 const int64_t npix = im.n_rays;
@@ -1509,13 +1529,14 @@ __global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __re
                                                            const R* __restrict__ pool,
                                                            const int32_t* __restrict__ chunks,
                                                            const float* __restrict__ mlp_params,
-                                                           Counters* ctr) {
+                                                           Counters* ctr, BlockSource bs) {
     using T = float;
     __shared__ mlp::FwdSmem S;
     mlp::fwd_init(S, mlp_params);
     uint32_t phase = 0;
     bool tc_ok = true;
-    const int64_t total_rays = ray_end - ray_begin;
+    const int64_t re = wave_end(bs, ray_end);
+    const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
     int64_t wray = 0;
     bool active = false;
     int64_t ray = 0, opix = 0;
@@ -1539,9 +1560,8 @@ __global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __re
         bool work = active || (need && !exhausted);
         if (!__syncthreads_or(work)) break;
         if (work && !active) {
-            q = find_image(imgs, n_images, ray);
+            setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
             const ImageDesc& im = imgs[q];
-            opix = ray_pixel(im, ray - im.ray_offset, pi, pj);
             const RayHdr hd = hdr[wray];
             if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) {
                 const int64_t npix = im.n_rays;
@@ -1707,9 +1727,10 @@ __device__ __forceinline__ double adapt_value(const V* I, int B, int u, int v, i
 template <class V>
 __global__ void adapt_criterion_kernel(const V* __restrict__ I, int64_t n_blocks, int B, int crit,
                                        double threshold, int min_count, double min_intensity,
-                                       int8_t* __restrict__ flags) {
+                                       int8_t* __restrict__ flags,
+                                       const unsigned long long* __restrict__ n_dev = nullptr) {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= n_blocks) return;
+    if (b >= (n_dev ? (int64_t)*n_dev : n_blocks)) return;
     const V* blk = I + b * (int64_t)B * B;
     int count = 0;
     for (int v = 0; v < B; ++v)
@@ -1719,26 +1740,85 @@ __global__ void adapt_criterion_kernel(const V* __restrict__ I, int64_t n_blocks
     flags[b] = count >= min_count ? 1 : 0;
 }
 
-// Paint the rays of one level into the finest-level composite: the ray of block-list pixel
-// (i, j) at this level covers the s x s finest pixels starting at (i s, j s).
-template <class V, class O>
-__global__ void adapt_composite_kernel(const V* __restrict__ st, int64_t n_rays,
-                                       const int32_t* __restrict__ blocks, int B, int s, int nf,
-                                       O* __restrict__ out) {
+// Output image of one adaptive trace: the finest-level composite, nf x nf per Stokes plane.
+struct OutDesc {
+    void* stokes;
+    int32_t nf, dtype;
+};
+
+// Paint the rays of one level (block list bs, Stokes in planes of length cap) into the
+// finest-level composites: the ray of level pixel (i, j) covers the s x s finest pixels
+// starting at (i s, j s).
+template <class V>
+__global__ void adapt_composite_kernel(const V* __restrict__ st, int64_t cap, BlockSource bs,
+                                       int s, const OutDesc* __restrict__ outs) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= n_rays) return;
-    const int64_t b2 = (int64_t)B * B;
+    const int64_t b2 = (int64_t)bs.block * bs.block;
+    if (p >= (int64_t)(*bs.count) * b2) return;
     const int64_t blk = p / b2;
     const int r = (int)(p - blk * b2);
-    const int i = blocks[2 * blk] * B + r % B;
-    const int j = blocks[2 * blk + 1] * B + r / B;
-    const int64_t plane = (int64_t)nf * nf;
+    const int q = bs.entries[3 * blk];
+    const int i = bs.entries[3 * blk + 1] * bs.block + r % bs.block;
+    const int j = bs.entries[3 * blk + 2] * bs.block + r / bs.block;
+    const OutDesc o = outs[q];
+    const int64_t plane = (int64_t)o.nf * o.nf;
     for (int c = 0; c < 4; ++c) {
-        const O v = (O)st[c * n_rays + p];
+        const V v = st[c * cap + p];
         for (int dj = 0; dj < s; ++dj)
-            for (int di = 0; di < s; ++di)
-                out[c * plane + (int64_t)(j * s + dj) * nf + (i * s + di)] = v;
+            for (int di = 0; di < s; ++di) {
+                const int64_t k = c * plane + (int64_t)(j * s + dj) * o.nf + (i * s + di);
+                if (o.dtype == 0) ((double*)o.stokes)[k] = (double)v;
+                else ((float*)o.stokes)[k] = (float)v;
+            }
     }
+}
+
+// Children of the refined blocks of one level, in parent order (each parent (q, bx, by) gives
+// (q, 2 bx + dx, 2 by + dy), dy then dx), written as the next level's block list; one CTA of
+// 1024 threads scans the flags. Blocks beyond the next list's capacity are counted in
+// *overflow and not written. per_image[q] accumulates the next level's blocks of image q.
+__global__ void __launch_bounds__(1024) adapt_refine_kernel(
+        const int8_t* __restrict__ flags, const int32_t* __restrict__ entries,
+        const unsigned long long* __restrict__ count, int32_t* __restrict__ next_entries,
+        unsigned long long* __restrict__ next_count, unsigned long long cap_next,
+        unsigned long long* __restrict__ per_image, unsigned long long* __restrict__ overflow) {
+    __shared__ unsigned int warp_tot[32];
+    __shared__ unsigned long long base;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int64_t n = (int64_t)*count;
+    if (t == 0) base = 0;
+    __syncthreads();
+    for (int64_t start = 0; start < n; start += 1024) {
+        const int64_t b = start + t;
+        const bool f = b < n && flags[b] != 0;
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) warp_tot[w] = __popc(m);
+        __syncthreads();
+        unsigned before = 0, total = 0;
+        for (int k = 0; k < 32; ++k) {
+            if (k < w) before += warp_tot[k];
+            total += warp_tot[k];
+        }
+        if (f) {
+            const unsigned long long out = base + before + __popc(m & ((1u << lane) - 1u));
+            if (4 * out + 4 <= cap_next) {
+                const int32_t q = entries[3 * b], bx = entries[3 * b + 1], by = entries[3 * b + 2];
+                int32_t* dst = next_entries + 12 * out;
+                for (int dy = 0; dy < 2; ++dy)
+                    for (int dx = 0; dx < 2; ++dx) {
+                        dst[0] = q; dst[1] = 2 * bx + dx; dst[2] = 2 * by + dy;
+                        dst += 3;
+                    }
+                atomicAdd(&per_image[q], 4ull);
+            } else {
+                atomicAdd(overflow, 1ull);
+            }
+        }
+        __syncthreads();
+        if (t == 0) base += total;
+        __syncthreads();
+    }
+    if (t == 0) *next_count = 4 * base < cap_next ? 4 * base : cap_next / 4 * 4;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -158,6 +158,11 @@ def load():
     L.blacklight_plan_check.argtypes = [P, P]
     L.blacklight_plan_config.argtypes = [P, C.POINTER(LaunchConfig)]
     L.blacklight_plan_destroy.argtypes = [P]
+    L.blacklight_plan_create_adaptive.argtypes = [C.c_int32, C.POINTER(Camera), C.POINTER(Metric),
+                                                  C.POINTER(Grid), C.POINTER(C.c_double),
+                                                  C.POINTER(Adapt), C.POINTER(Out), C.c_uint32, P,
+                                                  C.POINTER(C.c_void_p)]
+    L.blacklight_plan_level_rays.argtypes = [P, C.POINTER(C.c_int32), P]
     L.blacklight_strerror.argtypes = [C.c_int]
     L.blacklight_strerror.restype = C.c_char_p
     L.blacklight_last_error_detail.argtypes = []
@@ -354,6 +359,33 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class AdaptivePlan(Plan):
+    """An adaptive trace (blacklight_plan_create_adaptive) replayed as one CUDA graph."""
+
+    def __init__(self, cams, mets, gps, prims, freqs, adapt, outs, flags=0, stream=None,
+                 coef_mlp=None):
+        L = load()
+        n = len(cams)
+        ca = (Camera * n)(*[camera_struct(c) for c in cams])
+        ma = (Metric * n)(*[metric_struct(m) for m in mets])
+        ga = (Grid * n)(*[grid_struct(g, p.data_ptr(), coef_mlp) for g, p in zip(gps, prims)])
+        fa = (C.c_double * n)(*[float(f) for f in freqs])
+        oa = (Out * n)(*[out_struct(**o) for o in outs])
+        h = C.c_void_p()
+        _check(L.blacklight_plan_create_adaptive(n, ca, ma, ga, fa, C.byref(adapt), oa, flags,
+                                                 _stream(stream), C.byref(h)))
+        self._h = h
+        self._keep = (list(prims), list(outs), coef_mlp)
+        self._shape = (n, adapt.max_level + 1)
+
+    def level_rays(self, stream=None):
+        import numpy as np
+        lr = np.zeros(self._shape, dtype=np.int32)
+        _check(load().blacklight_plan_level_rays(self._h, lr.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                 _stream(stream)))
+        return lr
 
 
 # ------------------------------- learned coefficient model ------------------------------

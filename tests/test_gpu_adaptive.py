@@ -67,3 +67,36 @@ def test_adaptive_trace_vs_oracle(precision, tol):
     err = [np.linalg.norm(comp[s] - comp_o[s]) / nI for s in range(4)]
     print("composite rel-L2", err)
     assert max(err) <= tol
+
+    # the same trace as an adaptive plan (one CUDA graph for all levels), replayed twice
+    out2 = {"stokes": torch.zeros((4, nf, nf), dtype=dt, device="cuda")}
+    p = torch.from_numpy(prim).cuda()
+    plan = native.AdaptivePlan([cam], [met], [gp], [p], [230e9], ad, [out2])
+    for _ in range(2):
+        out2["stokes"].fill_(-1.0)
+        plan.run()
+        assert plan.check() == 0
+        assert torch.equal(out2["stokes"], out["stokes"])
+        assert list(plan.level_rays()[0]) == list(lr_o)
+    plan.close()
+
+
+def test_adaptive_batch_of_images_and_capacity():
+    """Several images of different sizes refine independently in one device-driven sequence:
+    each image's composite and rays per level equal those of the image traced alone."""
+    native.load()
+    gp = S.GridParams(n_r=64, n_theta=32, n_phi=32)
+    prim = torch.from_numpy(S.make_torus(gp, 0.9, S.BASE_SEED + 2)).cuda()
+    cams = [S.Camera(theta=math.radians(th), n=n) for th, n in ((17.0, 32), (60.0, 16), (85.0, 32))]
+    met = S.Metric(spin=0.9, precision=2)
+    ad = native.adapt_struct(8, 2, A.ABS_GRAD, 1e-6, 3, 1e-20)
+    outs = [{"stokes": torch.zeros((4, c.n << 2, c.n << 2), dtype=torch.float32, device="cuda")}
+            for c in cams]
+    rc, lr = native.blacklight_trace_adaptive(cams, [met] * 3, [gp] * 3, [prim] * 3,
+                                              [230e9] * 3, ad, outs)
+    assert rc == 0 and lr.shape == (3, 3)
+    for q, c in enumerate(cams):
+        single = {"stokes": torch.zeros_like(outs[q]["stokes"])}
+        rc1, lr1 = native.blacklight_trace_adaptive([c], [met], [gp], [prim], [230e9], ad, [single])
+        assert list(lr1[0]) == list(lr[q])
+        torch.testing.assert_close(single["stokes"], outs[q]["stokes"], rtol=1e-6, atol=0.0)
