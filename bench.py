@@ -180,7 +180,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(wl, n_per_image, seed=99):
+def cpu_baseline(wl, n_per_image, seed=99, single_thread=False):
     """The oracle, as it stands, on a bounded sample of the same workload (all host cores)."""
     import numpy as np
     import oracle as O
@@ -195,9 +195,32 @@ def cpu_baseline(wl, n_per_image, seed=99):
         rays += n_per_image
     dt = time.perf_counter() - t0
     cores = os.cpu_count() or 1
-    return {"value": rays / dt, "unit": "rays/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n_per_image} seeded pixels from each of the 9 images ({rays} rays), "
-                      f"{dt:.1f} s wall on {cores} threads"}
+    out = {"value": rays / dt, "unit": "rays/s", "cores": cores, "kind": "oracle",
+           "sample": f"{n_per_image} seeded pixels from each of the 9 images ({rays} rays), "
+                     f"{dt:.1f} s wall on {cores} threads", "cpu": _cpu_model()}
+    if single_thread:
+        # one thread on a smaller sample of the same images
+        t0 = time.perf_counter()
+        n1 = 0
+        for cam, met, gp in zip(wl["cams"], wl["mets"], wl["gps"]):
+            pix = np.sort(rng.choice(cam.n * cam.n, 16, replace=False)).astype(np.int32)
+            O.trace(cam, met, gp, wl["prims_host"][met.spin], FREQ, pix=pix, nthreads=1)
+            n1 += 16
+        out["single_thread"] = {"value": n1 / (time.perf_counter() - t0), "rays": n1}
+    return out
+
+
+def _cpu_model():
+    """the host CPU's model name, as the system reports it"""
+    try:
+        import subprocess
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in txt.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
 
 
 def run_reference(args):
@@ -386,7 +409,7 @@ def main():
         e2e = measure_e2e(torch, native, wl, prec, max(1, min(args.steps, 3)))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, 1024)
+        cpu = cpu_baseline(wl, 1024, single_thread=True)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,

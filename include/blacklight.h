@@ -22,7 +22,9 @@
  *     (BL_EINVAL bad argument, BL_ENOMEM allocation failed, BL_ECUDA CUDA runtime error,
  *     BL_EUNSUPPORTED valid but not implemented). blacklight_last_error_detail() names the
  *     offending field (thread-local string, valid until the next call on that thread).
- *   - Device code never traps: rays that fail set their status word instead.
+ *   - Device code never traps: rays that fail set their status word instead. Every device
+ *     wait is bounded; a wait that runs out makes its kernel stop and the call return
+ *     BL_ETIMEOUT, with the context still usable.
  *   - Lengths are in units of M = G M_bh / c^2; plasma and radiation in CGS.
  */
 #ifndef BLACKLIGHT_H
@@ -147,7 +149,8 @@ enum {
     BL_EINVAL = -1,
     BL_ENOMEM = -2,
     BL_ECUDA = -3,
-    BL_EUNSUPPORTED = -4
+    BL_EUNSUPPORTED = -4,
+    BL_ETIMEOUT = -5        /* a bounded device wait ran out; the kernel stopped cleanly */
 };
 
 /* Per-ray status words. */
@@ -395,6 +398,12 @@ int blacklight_bessel_k(int64_t n, const double* x, double* out, int32_t precisi
  * under the criterion of bl_adapt_t (adapt->max_level is ignored). */
 int blacklight_adapt_flags(int64_t n_blocks, const double* I, const bl_adapt_t* adapt,
                            int8_t* flags, void* stream);
+
+/* Self-test of the bounded device wait used by the tensor-core kernels: one CTA initialises
+ * an mbarrier and waits on it for at most max_cycles SM cycles (1 <= max_cycles <= 2^32); with
+ * arrive = 1 it arrives first (returns 0), with arrive = 0 nothing arrives and the wait runs out
+ * (returns BL_ETIMEOUT). No fault, no unbounded wait. */
+int blacklight_selftest_wait(int64_t max_cycles, int32_t arrive, void* stream);
 
 const char* blacklight_strerror(int code);
 const char* blacklight_last_error_detail(void);

@@ -456,7 +456,7 @@ int finish(char* ws, const Layout& L, cudaStream_t st, bool sync) {
     BL_CUDA(cudaMemcpyAsync(&c, ws + L.counters, sizeof(c), cudaMemcpyDeviceToHost, st));
     BL_CUDA(cudaStreamSynchronize(st));
     if (c.mlp_timeouts)
-        return fail(BL_ECUDA, "%llu CTAs stopped: tensor-core wait ran out", c.mlp_timeouts);
+        return fail(BL_ETIMEOUT, "%llu CTAs stopped: tensor-core wait ran out", c.mlp_timeouts);
     return c.bad_rays ? BL_WRAYS : BL_OK;
 }
 
@@ -1008,7 +1008,7 @@ int adapt_finish(AdaptRun& R, int32_t* level_rays, cudaStream_t st) {
         for (int q = 0; q < R.n_images; ++q)
             for (int l = 0; l < levels; ++l)
                 level_rays[q * levels + l] = (int32_t)(h[levels + (size_t)l * R.n_images + q] * b2);
-    if (c.mlp_timeouts) return fail(BL_ECUDA, "tensor-core wait ran out in %llu CTAs", c.mlp_timeouts);
+    if (c.mlp_timeouts) return fail(BL_ETIMEOUT, "tensor-core wait ran out in %llu CTAs", c.mlp_timeouts);
     if (h[n_counts - 1])
         return fail(BL_EUNSUPPORTED, "adaptive refinement exceeded a level's capacity of %lld rays",
                     (long long)kMaxAdaptLevelRays);
@@ -1384,7 +1384,7 @@ int with_tc_flag(cudaStream_t st, F launch) {
     cudaFreeAsync(err, st);
     e = cudaStreamSynchronize(st);
     if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
-    if (!rc && h) rc = fail(BL_ECUDA, "tensor-core wait ran out");
+    if (!rc && h) rc = fail(BL_ETIMEOUT, "tensor-core wait ran out");
     return rc;
 }
 
@@ -1649,6 +1649,18 @@ int blacklight_bessel_k(int64_t n, const double* x, double* out, int32_t precisi
     return 0;
 }
 
+int blacklight_selftest_wait(int64_t max_cycles, int32_t arrive, void* stream) {
+    g_detail[0] = 0;
+    if (max_cycles < 1 || max_cycles > (1ll << 32) || (arrive != 0 && arrive != 1))
+        return fail(BL_EINVAL, "max_cycles in [1, 2^32], arrive 0 or 1");
+    return with_tc_flag((cudaStream_t)stream, [&](int* err) -> int {
+        bl::mlp::wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(max_cycles, arrive, err);
+        ++g_launches;
+        BL_CUDA(cudaGetLastError());
+        return 0;
+    });
+}
+
 const char* blacklight_strerror(int code) {
     switch (code) {
         case BL_OK: return "success";
@@ -1657,6 +1669,7 @@ const char* blacklight_strerror(int code) {
         case BL_ENOMEM: return "device memory allocation failed";
         case BL_ECUDA: return "CUDA runtime error";
         case BL_EUNSUPPORTED: return "unsupported option";
+        case BL_ETIMEOUT: return "a bounded device wait ran out";
         default: return "unknown error code";
     }
 }

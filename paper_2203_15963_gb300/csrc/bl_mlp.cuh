@@ -731,5 +731,18 @@ __global__ void normalise_kernel(int64_t n, const float* __restrict__ in,
     }
 }
 
+// Self-test of the bounded mbarrier wait: with arrive = 0 nothing arrives and the wait must
+// run out after max_cycles (sets *err); with arrive = 1 the barrier's phase completes first.
+__global__ void wait_selftest_kernel(long long max_cycles, int arrive, int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+    __syncthreads();
+    if (arrive && threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(&bar)) : "memory");
+    __syncthreads();
+    const bool ok = tc::mbar_wait(&bar, 0u, max_cycles);
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+}
+
 }  // namespace mlp
 }  // namespace bl

@@ -163,6 +163,7 @@ def load():
                                                   C.POINTER(Adapt), C.POINTER(Out), C.c_uint32, P,
                                                   C.POINTER(C.c_void_p)]
     L.blacklight_plan_level_rays.argtypes = [P, C.POINTER(C.c_int32), P]
+    L.blacklight_selftest_wait.argtypes = [C.c_int64, C.c_int32, P]
     L.blacklight_strerror.argtypes = [C.c_int]
     L.blacklight_strerror.restype = C.c_char_p
     L.blacklight_last_error_detail.argtypes = []
@@ -432,6 +433,17 @@ def blacklight_mlp_forward(params, inputs, outputs, stream=None):
 def blacklight_mlp_coefficients(params, inp, out, stream=None):
     return _check(load().blacklight_mlp_coefficients(_ptr(params), inp.shape[0], _ptr(inp),
                                                      _ptr(out), _stream(stream)))
+
+
+BL_ETIMEOUT = -5
+
+
+def blacklight_selftest_wait(max_cycles, arrive, stream=None) -> int:
+    """0 if the wait completed; BL_ETIMEOUT (returned, not raised) if it ran out."""
+    rc = load().blacklight_selftest_wait(int(max_cycles), int(arrive), _stream(stream))
+    if rc == BL_ETIMEOUT:
+        return rc
+    return _check(rc)
 
 
 def blacklight_launch_count(reset=False) -> int:

@@ -372,3 +372,15 @@ def test_small_workspace_runs_waves_with_identical_result(precision):
     assert rc == rc2
     for key in ("stokes", "status", "steps", "samples"):
         assert torch.equal(a[0][key], b[0][key]), key
+
+
+def test_bounded_device_wait_reports_timeout_and_context_stays_usable():
+    """The tensor-core kernels' mbarrier waits are bounded: a wait on a barrier that nothing
+    completes runs out, the kernel stops, the call returns BL_ETIMEOUT, and the device keeps
+    working (a trace afterwards is unaffected)."""
+    assert native.blacklight_selftest_wait(1 << 22, 1) == 0
+    assert native.blacklight_selftest_wait(1 << 22, 0) == native.BL_ETIMEOUT
+    cam, met, gp, prim = C1
+    g = _gpu_image(cam, met, gp, prim, 230e9, native.BL_PREC_FAST)
+    assert g["rc"] == 0
+    assert native.blacklight_selftest_wait(1 << 22, 1) == 0
