@@ -218,6 +218,16 @@ int blacklight_trace_noalloc(const bl_camera_t* cam, const bl_metric_t* met,
 int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const bl_grid_t* grid,
                           double freq_hz, const bl_out_t* out, void* stream);
 
+/* blacklight_trace_batch with HOST buffers: grids[q].prim (and coef_mlp) and every pointer in
+ * outs[q] are host pointers (pinned memory copies fastest). A grid whose prim pointer appears
+ * in several images is copied to the device once; all images are then traced in one batched
+ * launch and the outputs copied back. Stream-ordered on `stream`, synchronous; device scratch
+ * is allocated and freed inside. flags: BL_UNPOLARIZED (BL_ASYNC and BL_TIMING are ignored). */
+int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
+                                const bl_metric_t* mets, const bl_grid_t* grids,
+                                const double* freqs_hz, const bl_out_t* outs, void* stream,
+                                uint32_t flags);
+
 /* Geodesics only (Sec. 2.2): writes out->end_state, out->status and out->steps (attempted
  * DP steps); out->stokes is ignored. */
 int blacklight_geodesics(const bl_camera_t* cam, const bl_metric_t* met, const bl_out_t* out,
@@ -398,6 +408,15 @@ int blacklight_bessel_k(int64_t n, const double* x, double* out, int32_t precisi
  * under the criterion of bl_adapt_t (adapt->max_level is ignored). */
 int blacklight_adapt_flags(int64_t n_blocks, const double* I, const bl_adapt_t* adapt,
                            int8_t* flags, void* stream);
+
+/* Device memory the library allocates stream-ordered (scratch of calls without a caller
+ * workspace, host-buffer staging) comes from the current device's default memory pool, which
+ * by default returns freed memory to the system at every synchronisation, so a later call maps
+ * it again (tens of ms for the ~20 GB of a 9 x 256^2 batch). This sets the pool's release
+ * threshold: up to `bytes` of freed memory stay reserved for reuse (UINT64_MAX: all; 0: the
+ * CUDA default). The setting belongs to the process's default pool for this device and
+ * applies to every user of it. */
+int blacklight_set_memory_retention(uint64_t bytes);
 
 /* Self-test of the bounded device wait used by the tensor-core kernels: one CTA initialises
  * an mbarrier and waits on it for at most max_cycles SM cycles (1 <= max_cycles <= 2^32); with

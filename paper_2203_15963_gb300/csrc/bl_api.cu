@@ -1591,6 +1591,119 @@ int blacklight_mlp_coefficients(const float* params, int64_t n, const double* in
     });
 }
 
+int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
+                                const bl_metric_t* mets, const bl_grid_t* grids,
+                                const double* freqs_hz, const bl_out_t* outs, void* stream,
+                                uint32_t flags) {
+    g_detail[0] = 0;
+    if (n_images < 1 || !cams || !mets || !grids || !freqs_hz || !outs)
+        return fail(BL_EINVAL, "NULL array argument or n_images < 1");
+    for (int q = 0; q < n_images; ++q) {
+        int rc = check_camera(&cams[q], q);
+        if (!rc) rc = check_metric(&mets[q], q);
+        if (!rc) rc = check_grid(&grids[q], q);
+        if (!rc) rc = check_out(&outs[q], q, true);
+        if (rc) return rc;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // distinct grids (by host pointer), their sizes and offsets in one device allocation
+    std::vector<const float*> uniq;
+    std::vector<size_t> gsz, goff;
+    std::vector<int> gidx(n_images);
+    size_t off = 0;
+    for (int q = 0; q < n_images; ++q) {
+        const bl_grid_t& g = grids[q];
+        const size_t bytes = sizeof(float) * 8 * (size_t)g.n_r * g.n_theta * g.n_phi *
+                             (size_t)(g.n_snapshots > 1 ? g.n_snapshots : 1);
+        int k = -1;
+        for (size_t u = 0; u < uniq.size(); ++u)
+            if (uniq[u] == g.prim) { k = (int)u; break; }
+        if (k < 0) {
+            k = (int)uniq.size();
+            uniq.push_back(g.prim);
+            gsz.push_back(bytes);
+            goff.push_back(off);
+            off = align_up(off + bytes);
+        } else if (gsz[k] < bytes) {
+            return fail(BL_EINVAL, "grids[%d] shares its prim pointer with a smaller grid", q);
+        }
+        gidx[q] = k;
+    }
+    const size_t o_mlp = off;
+    if (grids[0].coef_mlp) off = align_up(off + sizeof(float) * BL_MLP_PARAMS);
+    std::vector<size_t> o_out(n_images);
+    for (int q = 0; q < n_images; ++q) {
+        const size_t npix = (size_t)cams[q].n * cams[q].n;
+        const size_t es = outs[q].dtype == 0 ? sizeof(double) : sizeof(float);
+        o_out[q] = off;
+        off = align_up(off + 4 * npix * es);                                   // stokes
+        if (outs[q].status) off = align_up(off + npix * 4);
+        if (outs[q].steps) off = align_up(off + npix * 4);
+        if (outs[q].samples) off = align_up(off + npix * 4);
+        if (outs[q].end_state) off = align_up(off + npix * 64);
+        if (outs[q].aux) off = align_up(off + (size_t)BL_AUX_COUNT * npix * es);
+    }
+    const Layout L = make_layout(n_images, cams, mets);
+    const size_t o_ws = off;
+    off = align_up(off + L.total);
+    char* dev = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&dev, off, st);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync(%zu): %s", off, cudaGetErrorString(e)); }
+    int rc = 0;
+    for (size_t u = 0; u < uniq.size() && !rc; ++u) {
+        e = cudaMemcpyAsync(dev + goff[u], uniq[u], gsz[u], cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copy grid to device");
+    }
+    if (!rc && grids[0].coef_mlp) {
+        e = cudaMemcpyAsync(dev + o_mlp, grids[0].coef_mlp, sizeof(float) * BL_MLP_PARAMS,
+                            cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copy coefficient model to device");
+    }
+    std::vector<bl_grid_t> dg(grids, grids + n_images);
+    std::vector<bl_out_t> dout(outs, outs + n_images);
+    for (int q = 0; q < n_images; ++q) {
+        dg[q].prim = (const float*)(dev + goff[gidx[q]]);
+        if (grids[q].coef_mlp) dg[q].coef_mlp = (const float*)(dev + o_mlp);
+        const size_t npix = (size_t)cams[q].n * cams[q].n;
+        const size_t es = outs[q].dtype == 0 ? sizeof(double) : sizeof(float);
+        size_t p = o_out[q];
+        dout[q].stokes = dev + p; p = align_up(p + 4 * npix * es);
+        if (outs[q].status) { dout[q].status = (int32_t*)(dev + p); p = align_up(p + npix * 4); }
+        if (outs[q].steps) { dout[q].steps = (int32_t*)(dev + p); p = align_up(p + npix * 4); }
+        if (outs[q].samples) { dout[q].samples = (int32_t*)(dev + p); p = align_up(p + npix * 4); }
+        if (outs[q].end_state) { dout[q].end_state = (double*)(dev + p); p = align_up(p + npix * 64); }
+        if (outs[q].aux) { dout[q].aux = dev + p; }
+    }
+    if (!rc)
+        rc = trace_impl(n_images, cams, mets, dg.data(), freqs_hz, dout.data(), dev + o_ws, L.total,
+                        stream, BL_ASYNC | (flags & BL_UNPOLARIZED), true);
+    for (int q = 0; q < n_images && rc >= 0; ++q) {
+        const size_t npix = (size_t)cams[q].n * cams[q].n;
+        const size_t es = outs[q].dtype == 0 ? sizeof(double) : sizeof(float);
+        e = cudaMemcpyAsync(outs[q].stokes, dout[q].stokes, 4 * npix * es, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && outs[q].status)
+            e = cudaMemcpyAsync(outs[q].status, dout[q].status, npix * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && outs[q].steps)
+            e = cudaMemcpyAsync(outs[q].steps, dout[q].steps, npix * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && outs[q].samples)
+            e = cudaMemcpyAsync(outs[q].samples, dout[q].samples, npix * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && outs[q].end_state)
+            e = cudaMemcpyAsync(outs[q].end_state, dout[q].end_state, npix * 64, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && outs[q].aux)
+            e = cudaMemcpyAsync(outs[q].aux, dout[q].aux, (size_t)BL_AUX_COUNT * npix * es,
+                                cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copy results to host");
+    }
+    if (rc >= 0) {
+        const int r2 = finish(dev + o_ws, L, st, true);   // per-ray anomalies of the launch
+        if (r2 != 0) rc = r2;
+    }
+    cudaFreeAsync(dev, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (rc == 0 && se != cudaSuccess) rc = cuda_fail(se, "cudaStreamSynchronize");
+    return rc;
+}
+
 int blacklight_coefficients(int64_t n, const double* in, double* out, int32_t precision,
                             void* stream) {
     g_detail[0] = 0;
@@ -1646,6 +1759,17 @@ int blacklight_bessel_k(int64_t n, const double* x, double* out, int32_t precisi
     ++g_launches;
     BL_CUDA(cudaGetLastError());
     BL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return 0;
+}
+
+int blacklight_set_memory_retention(uint64_t bytes) {
+    g_detail[0] = 0;
+    int dev = 0;
+    BL_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    BL_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t v = bytes;
+    BL_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &v));
     return 0;
 }
 

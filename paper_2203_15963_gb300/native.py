@@ -164,6 +164,10 @@ def load():
                                                   C.POINTER(C.c_void_p)]
     L.blacklight_plan_level_rays.argtypes = [P, C.POINTER(C.c_int32), P]
     L.blacklight_selftest_wait.argtypes = [C.c_int64, C.c_int32, P]
+    L.blacklight_set_memory_retention.argtypes = [C.c_uint64]
+    L.blacklight_trace_host_batch.argtypes = [C.c_int32, C.POINTER(Camera), C.POINTER(Metric),
+                                              C.POINTER(Grid), C.POINTER(C.c_double),
+                                              C.POINTER(Out), P, C.c_uint32]
     L.blacklight_strerror.argtypes = [C.c_int]
     L.blacklight_strerror.restype = C.c_char_p
     L.blacklight_last_error_detail.argtypes = []
@@ -279,6 +283,20 @@ def blacklight_trace_host(cam, met, gp, prim_host, freq, out_host, stream=None, 
     os_ = out_struct(**out_host)
     return _check(L.blacklight_trace_host(C.byref(cs), C.byref(ms), C.byref(gs), float(freq),
                                           C.byref(os_), _stream(stream)))
+
+
+def blacklight_trace_host_batch(cams, mets, gps, prims_host, freqs, outs_host, stream=None,
+                                flags=0, coef_mlp=None):
+    """blacklight_trace_batch with CPU tensors (pinned for speed) for grids and outputs; images
+    that share a grid tensor upload it once."""
+    L = load()
+    n = len(cams)
+    ca = (Camera * n)(*[camera_struct(c) for c in cams])
+    ma = (Metric * n)(*[metric_struct(m) for m in mets])
+    ga = (Grid * n)(*[grid_struct(g, p.data_ptr(), coef_mlp) for g, p in zip(gps, prims_host)])
+    fa = (C.c_double * n)(*[float(f) for f in freqs])
+    oa = (Out * n)(*[out_struct(**o) for o in outs_host])
+    return _check(L.blacklight_trace_host_batch(n, ca, ma, ga, fa, oa, _stream(stream), flags))
 
 
 def blacklight_geodesics(cam, met, out, stream=None, flags=0):
@@ -436,6 +454,10 @@ def blacklight_mlp_coefficients(params, inp, out, stream=None):
 
 
 BL_ETIMEOUT = -5
+
+
+def blacklight_set_memory_retention(nbytes) -> int:
+    return _check(load().blacklight_set_memory_retention(int(nbytes)))
 
 
 def blacklight_selftest_wait(max_cycles, arrive, stream=None) -> int:

@@ -384,3 +384,25 @@ def test_bounded_device_wait_reports_timeout_and_context_stays_usable():
     g = _gpu_image(cam, met, gp, prim, 230e9, native.BL_PREC_FAST)
     assert g["rc"] == 0
     assert native.blacklight_selftest_wait(1 << 22, 1) == 0
+
+
+def test_host_batch_equals_device_batch():
+    """Host-buffer batch: three images, two sharing one grid tensor (uploaded once); outputs and
+    status words equal the device-buffer batch's."""
+    cam, met, gp, prim = C1
+    cams = [cam, S.Camera(**{**cam.__dict__, "theta": 1.0}), cam]
+    met2 = S.Metric(**{**met.__dict__, "precision": native.BL_PREC_FAST})
+    cam_b, met_b, gp_b, prim_b = S.workload_inputs("torus64_cam32", 0.5, 60.0)
+    mets = [met2, met2, S.Metric(**{**met_b.__dict__, "precision": native.BL_PREC_FAST})]
+    host = [torch.from_numpy(prim).pin_memory(), torch.from_numpy(prim_b).pin_memory()]
+    prims_h = [host[0], host[0], host[1]]
+    gps = [gp, gp, gp_b]
+    outs_h = [{"stokes": torch.empty((4, c.n, c.n), dtype=torch.float32).pin_memory(),
+               "status": torch.empty((c.n, c.n), dtype=torch.int32).pin_memory()} for c in cams]
+    assert native.blacklight_trace_host_batch(cams, mets, gps, prims_h, [230e9] * 3, outs_h) == 0
+    dev = [p.cuda() for p in prims_h]
+    outs_d = [images.alloc_outputs(c.n, torch.float32) for c in cams]
+    native.blacklight_trace_batch(cams, mets, gps, dev, [230e9] * 3, outs_d)
+    for h, d in zip(outs_h, outs_d):
+        assert torch.equal(h["stokes"], d["stokes"].cpu())
+        assert torch.equal(h["status"], d["status"].cpu())
