@@ -466,6 +466,29 @@ __device__ __forceinline__ bool append_record(const RecordSink<R>& S, int64_t ra
 #ifndef BL_GEO_MIN_CTAS
 #define BL_GEO_MIN_CTAS 3
 #endif
+// Records of a subdivided step from the FP32 quartic about the step's start (coefficients
+// y0, d0 = h f0, c2, c3, c4 per component): nsub samples at the centres of equal parts.
+template <class R>
+__device__ __forceinline__ bool emit_quartic_f(const RecordSink<R>& sink, int64_t wray, int32_t& nrec,
+                                       const float y0f[8], const float d0f[8], const float c2f[8],
+                                       const float c3f[8], const float c4f[8], int nsub,
+                                       double hd) {
+    bool ok = true;
+    const float invf = 1.0f / (float)nsub;
+    for (int s = 0; s < nsub && ok; ++s) {
+        float ysm[8], ynd[8];
+        const float ts = (s + 0.5f) * invf, tn = s * invf;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            ysm[c] = y0f[c] + ts * (d0f[c] + ts * (c2f[c] + ts * (c3f[c] + ts * c4f[c])));
+            ynd[c] = (s == 0) ? y0f[c]
+                              : y0f[c] + tn * (d0f[c] + tn * (c2f[c] + tn * (c3f[c] + tn * c4f[c])));
+        }
+        ok = append_record(sink, wray, nrec, ysm, ynd, hd / nsub);
+    }
+    return ok;
+}
+
 template <class R, class G>
 __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const ImageDesc* __restrict__ imgs,
                                                           int n_images, int64_t ray_begin,
@@ -724,18 +747,7 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                         c3f[c] = A::tof(k14 * D1 - kThree * D2 - k32 * D3);
                         c4f[c] = A::tof(kM8 * D1 + k2c * D2 + k16 * D3);
                     }
-                    const float invf = 1.0f / (float)nsub;
-                    for (int s = 0; s < nsub && ok; ++s) {
-                        float ysm[8], ynd[8];
-                        const float ts = (s + 0.5f) * invf, tn = s * invf;
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            ysm[c] = y0f[c] + ts * (d0f[c] + ts * (c2f[c] + ts * (c3f[c] + ts * c4f[c])));
-                            ynd[c] = (s == 0) ? y0f[c]
-                                              : y0f[c] + tn * (d0f[c] + tn * (c2f[c] + tn * (c3f[c] + tn * c4f[c])));
-                        }
-                        ok = append_record(sink, wray, nrec, ysm, ynd, fabs(hd) / nsub);
-                    }
+                    ok = emit_quartic_f(sink, wray, nrec, y0f, d0f, c2f, c3f, c4f, nsub, fabs(hd));
                 } else {
                     double y0d[8], d0[8], c2[8], c3[8], c4[8];
 #pragma unroll
