@@ -253,10 +253,12 @@ def test_hires_workload_sampled(precision):
     assert np.array_equal(g["status"][pix], ora["status"])
 
 
-@pytest.mark.parametrize("case", ["face_on_pole", "ragged_37", "nearest", "flat", "pixel_1"])
+@pytest.mark.parametrize("case", ["face_on_pole", "ragged_37", "nearest", "flat", "pixel_1",
+                                  "empty_grid", "spin_0999", "retrograde", "tiny_grid",
+                                  "moving_rolled_camera", "nu_at_camera", "optically_thick"])
 def test_edge_configurations(case):
     gp = S.GridParams(n_r=48, n_theta=32, n_phi=32)
-    spin, inc, n, met_kw, gp_kw = 0.5, 40.0, 16, {}, {}
+    spin, inc, n, met_kw, gp_kw, cam_kw = 0.5, 40.0, 16, {}, {}, {}
     if case == "face_on_pole":
         spin, inc = 0.0, 0.0
     elif case == "ragged_37":
@@ -267,9 +269,23 @@ def test_edge_configurations(case):
         met_kw = {"flat": 1}
     elif case == "pixel_1":
         n = 1
+    elif case == "spin_0999":
+        spin = 0.999
+    elif case == "retrograde":
+        spin = -0.7
+    elif case == "tiny_grid":
+        gp_kw = {"n_r": 2, "n_theta": 2, "n_phi": 1}
+    elif case == "moving_rolled_camera":
+        cam_kw = {"phi": 0.7, "psi": 0.4, "u_p": (0.0, 0.0, 0.05)}
+    elif case == "nu_at_camera":
+        cam_kw = {"nu_at_infinity": 0, "r": 60.0}
+    elif case == "optically_thick":
+        gp_kw = {"rho_unit_cgs": 1e-13}          # tau >> 1: the steady-state branch
     gp = S.GridParams(**{**gp.__dict__, **gp_kw})
     prim = S.make_torus(gp, spin, seed=7)
-    cam = S.Camera(theta=math.radians(inc), n=n)
+    if case == "empty_grid":
+        prim[0] = 0.0
+    cam = S.Camera(theta=math.radians(inc), n=n, **cam_kw)
     met = S.Metric(spin=spin, **met_kw)
     ora = O.trace(cam, met, gp, prim, 230e9)
     for precision, tol in ((0, 1e-6), (1, 1e-3), (2, 1e-3)):
