@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: one 256^2 image (a=0.94, i=60 deg) of the same workload, for "
                          "profiler captures")
+    ap.add_argument("--grid-layout", default="cells", choices=["cells", "planes"],
+                    help="memory order of the device grids: cells (repacked once by "
+                         "blacklight_grid_pack) or planes (as generated)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-hires", action="store_true",
@@ -106,24 +109,44 @@ def weak_scaling_value(world, rays_per_rank_step, steps, elapsed_max):
     return world * rays_per_rank_step * steps / elapsed_max
 
 
+# memory order of the device grids the bench traces ("cells" or "planes"; set from --grid-layout)
+GRID_LAYOUT = "cells"
+
+
+def device_grid(torch, prim, gp, device):
+    """A grid on the device in the bench's layout: the plane-layout array as uploaded, or
+    repacked once into the cell layout by the library (like the upload, outside any timing).
+    Returns (tensor, grid parameters)."""
+    from paper_2203_15963_gb300 import images
+    p = prim if torch.is_tensor(prim) else torch.from_numpy(prim)
+    p = p.to(device)
+    if GRID_LAYOUT == "cells":
+        return images.pack_grid(p, gp)
+    return p, gp
+
+
 def build_workload(torch, precision_code, device, case="full"):
     from paper_2203_15963_gb300 import synth as S
     gp = S.grid_params_for(*GRID)
     spins, incs = (SPINS, INCS) if case == "full" else ((0.94,), (60.0,))
-    prims_host, prims = {}, {}
+    prims_host, prims, planes = {}, {}, {}
     for spin in spins:
         prims_host[spin] = S.make_torus(gp, spin, S.BASE_SEED + 1)
-        prims[spin] = torch.from_numpy(prims_host[spin]).to(device)
-    cams, mets, gps, ps, freqs = [], [], [], [], []
+        planes[spin] = torch.from_numpy(prims_host[spin]).to(device)
+        prims[spin], gpd = device_grid(torch, planes[spin], gp, device)
+    cams, mets, gps, ps, pls, freqs = [], [], [], [], [], []
     for spin in spins:
         for inc in incs:
             cams.append(S.Camera(theta=math.radians(inc), n=N_PIX))
             mets.append(S.Metric(spin=spin, precision=precision_code))
-            gps.append(gp)
+            gps.append(gpd)
             ps.append(prims[spin])
+            pls.append(planes[spin])
             freqs.append(FREQ)
+    # gps/prims: the device grids as traced; gp/prims_planes: the same grids in the plane
+    # layout (host arrays for the oracle and the host-buffer path, device copies for comparison)
     return dict(gp=gp, cams=cams, mets=mets, gps=gps, prims=ps, freqs=freqs,
-                prims_host=prims_host)
+                prims_host=prims_host, prims_planes=pls)
 
 
 class ClockSampler:
@@ -188,8 +211,8 @@ def cpu_baseline(wl, n_per_image, seed=99, single_thread=False):
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
     rays = 0
-    for cam, met, gp, spin in zip(wl["cams"], wl["mets"], wl["gps"],
-                                  [m.spin for m in wl["mets"]]):
+    for cam, met, spin in zip(wl["cams"], wl["mets"], [m.spin for m in wl["mets"]]):
+        gp = wl["gp"]
         pix = np.sort(rng.choice(cam.n * cam.n, n_per_image, replace=False)).astype(np.int32)
         O.trace(cam, met, gp, wl["prims_host"][spin], FREQ, pix=pix, nthreads=0)
         rays += n_per_image
@@ -202,7 +225,8 @@ def cpu_baseline(wl, n_per_image, seed=99, single_thread=False):
         # one thread on a smaller sample of the same images
         t0 = time.perf_counter()
         n1 = 0
-        for cam, met, gp in zip(wl["cams"], wl["mets"], wl["gps"]):
+        for cam, met in zip(wl["cams"], wl["mets"]):
+            gp = wl["gp"]
             pix = np.sort(rng.choice(cam.n * cam.n, 16, replace=False)).astype(np.int32)
             O.trace(cam, met, gp, wl["prims_host"][met.spin], FREQ, pix=pix, nthreads=1)
             n1 += 16
@@ -282,6 +306,8 @@ def main():
     from paper_2203_15963_gb300 import images, native
     native.build()
     native.load()
+    global GRID_LAYOUT
+    GRID_LAYOUT = args.grid_layout
     prec = {"mixed": native.BL_PREC_MIXED, "fp64": native.BL_PREC_FP64,
             "fast": native.BL_PREC_FAST}[args.precision]
     wl = build_workload(torch, prec, device, args.case)
@@ -376,6 +402,11 @@ def main():
             if code == prec:
                 continue
             other[name] = time_form(torch, native, images, wl, code, device, steps=3, warmup=2)
+    layout_cmp = None
+    if not args.no_other_forms and GRID_LAYOUT == "cells":
+        # the same step on the grids in the plane layout (the layout as generated)
+        wl_planes = dict(wl, gps=[wl["gp"]] * len(cams), prims=wl["prims_planes"])
+        layout_cmp = time_form(torch, native, images, wl_planes, prec, device, steps=3, warmup=2)
     hires = hires_img = None
     if not args.no_hires and args.case == "full":
         hires, hires_img = measure_hires(torch, native, images, prec, device,
@@ -425,12 +456,14 @@ def main():
                            "grid": list(GRID), "spins": list(SPINS),
                            "inclinations_deg": list(INCS), "freq_ghz": FREQ / 1e9,
                            "precision": args.precision, "coefficients": args.coef,
+                           "grid_layout": GRID_LAYOUT,
                            "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (3 x 134 MB grids + sample records); no flush"},
                 "kernel_ms": {"geodesic": geo_avg * 1e3, "transfer": tr_avg * 1e3},
                 "work": {"dp_attempts": attempts, "samples": samples,
                          "rays_not_terminated_normally": status_bad},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "other_forms": other,
+                "plane_layout": layout_cmp,
                 "variants": variants, "plan": plan, "hires": hires, "mlp": mlp,
                 "slow_light": slow,
                 "adaptive": adaptive,
@@ -481,7 +514,7 @@ def measure_hires(torch, native, images, code, device, steps=3, warmup=2, coef_m
     from paper_2203_15963_gb300 import synth as S
     cam, met, gp, prim = S.workload_inputs("torus512_cam1024", 0.94, 17.0)
     met = S.Metric(**{**met.__dict__, "precision": code})
-    p = torch.from_numpy(prim).to(device)
+    p, gp = device_grid(torch, prim, gp, device)
     del prim
     ws = torch.empty(native.blacklight_workspace_size([cam], [met]), dtype=torch.uint8,
                      device=device)
@@ -529,8 +562,8 @@ def measure_slow(torch, native, images, device, coef_mlp, steps=3):
     import dataclasses
     from paper_2203_15963_gb300 import synth as S
     cam, met, gp, prim = S.workload_inputs("torus256_slow8_cam512", 0.94, 60.0)
-    p = torch.from_numpy(prim).to(device)
-    mid = p[4].contiguous()
+    p, gp = device_grid(torch, prim, gp, device)
+    mid = p[4].contiguous()       # the middle snapshot alone, in the same layout
     del prim
 
     def run(gpx, px, code, mlp):
@@ -656,7 +689,7 @@ def measure_plan(torch, native, images, wl, code, device, steps=5):
     # small batches: host overhead of direct calls against replays
     cam, met, gp, prim = S.workload_inputs("torus64_cam32", 0.9, 17.0)
     met = S.Metric(**{**met.__dict__, "precision": code})
-    p = torch.from_numpy(prim).to(device)
+    p, gp = device_grid(torch, prim, gp, device)
     k = 16
     cs, ms_, gs, ps, fs = [cam] * k, [met] * k, [gp] * k, [p] * k, [FREQ] * k
     so = [images.alloc_outputs(cam.n, dt, device=device) for _ in range(k)]
@@ -691,7 +724,10 @@ def measure_adaptive(torch, native, code, device, steps=2, warmup=1):
     from paper_2203_15963_gb300 import synth as S
     gp = S.grid_params_for(*GRID)
     spins, freqs = (0.0, 0.5, 0.94, 0.99), (86e9, 230e9, 345e9, 690e9)
-    prims = {a: torch.from_numpy(S.make_torus(gp, a, S.BASE_SEED + 2)).to(device) for a in spins}
+    prims = {}
+    for a in spins:
+        prims[a], gpd = device_grid(torch, S.make_torus(gp, a, S.BASE_SEED + 2), gp, device)
+    gp = gpd
     cams, mets, gps, ps, fs, outs = [], [], [], [], [], []
     dt = torch.float64 if code == native.BL_PREC_FP64 else torch.float32
     for a in spins:
@@ -742,7 +778,8 @@ def measure_e2e(torch, native, wl, prec, steps):
     """Same workload through the C ABI's host-buffer entry point: per step, one
     blacklight_trace_host_batch call copies the three grids (one per spin, shared by that
     spin's images) from pinned host memory, traces the 9 images in one batched launch and
-    copies the 9 Stokes images back, all inside the timing."""
+    copies the 9 Stokes images back, all inside the timing (the library repacks each grid
+    into the cell layout on the device as part of the call)."""
     host_prims = {s: torch.from_numpy(p).pin_memory() for s, p in wl["prims_host"].items()}
     dt = torch.float64 if prec == native.BL_PREC_FP64 else torch.float32
     outs = [{"stokes": torch.empty((4, c.n, c.n), dtype=dt).pin_memory()} for c in wl["cams"]]
@@ -754,8 +791,8 @@ def measure_e2e(torch, native, wl, prec, steps):
     native.blacklight_set_memory_retention(2 ** 64 - 1)
 
     def one():
-        native.blacklight_trace_host_batch(wl["cams"], wl["mets"], wl["gps"], prims, wl["freqs"],
-                                           outs)
+        native.blacklight_trace_host_batch(wl["cams"], wl["mets"], [wl["gp"]] * len(prims),
+                                           prims, wl["freqs"], outs)
 
     one()
     torch.cuda.synchronize()

@@ -111,7 +111,15 @@ typedef struct bl_grid {
     double t_first;
     double dt_snapshots;
     double t_camera;
+    /* Memory order of prim: BL_GRID_PLANES as described above, or BL_GRID_CELLS
+     * [n_phi][n_theta][n_r][8] (per snapshot), the 8 values of a cell contiguous in 32 bytes,
+     * prim 16-byte aligned; blacklight_grid_pack writes it. The values and the results are the
+     * same in both; with cells each of the 8 corners a trilinear sample reads is two 16-byte
+     * loads instead of eight scalar loads from eight planes. */
+    int32_t layout;
 } bl_grid_t;
+
+enum { BL_GRID_PLANES = 0, BL_GRID_CELLS = 1 };
 
 /* Outputs. stokes is a DEVICE pointer to [4][n][n] (I, Q, U, V; row j = vertical index
  * major) in erg s^-1 cm^-2 sr^-1 Hz^-1, float64 (dtype 0) or float32 (dtype 1). status,
@@ -190,6 +198,15 @@ int blacklight_trace_batch(int32_t n_images, const bl_camera_t* cams, const bl_m
                            const bl_grid_t* grids, const double* freqs_hz, const bl_out_t* outs,
                            void* workspace, size_t workspace_bytes, void* stream,
                            uint32_t flags);
+
+/* Repack a grid of n_snapshots >= 1 consecutive snapshots from BL_GRID_PLANES to
+ * BL_GRID_CELLS on `stream` (asynchronous, one kernel):
+ *   cells[((s n_phi + k) n_theta + j) n_r + i][v] = planes[(((s 8 + v) n_phi + k) n_theta + j) n_r + i].
+ * planes and cells are DEVICE pointers to 8 n_r n_theta n_phi n_snapshots floats each, not
+ * overlapping; cells must be 16-byte aligned and stays owned by the caller. BL_EINVAL on
+ * sizes < 1, NULL, host or misaligned pointers. */
+int blacklight_grid_pack(const float* planes, float* cells, int32_t n_r, int32_t n_theta,
+                         int32_t n_phi, int32_t n_snapshots, void* stream);
 
 /* One image: blacklight_trace_batch with n_images = 1 and library-managed scratch. */
 int blacklight_trace(const bl_camera_t* cam, const bl_metric_t* met, const bl_grid_t* grid,

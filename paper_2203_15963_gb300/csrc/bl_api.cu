@@ -170,6 +170,10 @@ int check_grid(const bl_grid_t* g, int q) {
     if (!(g->mu > 0.0) || !(g->ne_over_ni > 0.0)) return fail(BL_EINVAL, "grids[%d] composition", q);
     if (!(g->rho_unit_cgs > 0.0) || !(g->mass_msun > 0.0)) return fail(BL_EINVAL, "grids[%d] units", q);
     if (g->interp != 0 && g->interp != 1) return fail(BL_EINVAL, "grids[%d].interp", q);
+    if (g->layout != BL_GRID_PLANES && g->layout != BL_GRID_CELLS)
+        return fail(BL_EINVAL, "grids[%d].layout", q);
+    if (g->layout == BL_GRID_CELLS && ((uintptr_t)g->prim & 15u) != 0)
+        return fail(BL_EINVAL, "grids[%d].prim must be 16-byte aligned for BL_GRID_CELLS", q);
     if (g->n_snapshots > 1) {
         if (!(g->dt_snapshots > 0.0) || !std::isfinite(g->dt_snapshots) ||
             !std::isfinite(g->t_first) || !std::isfinite(g->t_camera))
@@ -217,6 +221,7 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
     d.max_steps = m.max_steps; d.flat = m.flat; d.precision = m.precision;
     d.integrator = m.integrator; d.f_step = m.f_step;
     d.prim = g.prim; d.nr = g.n_r; d.nt = g.n_theta; d.nph = g.n_phi; d.interp = g.interp;
+    d.layout = g.layout;
     d.r_min = g.r_min; d.r_max = g.r_max; d.gamma_ad = g.gamma_ad; d.r_high = g.r_high;
     d.r_low = g.r_low; d.mu = g.mu; d.ne_ni = g.ne_over_ni; d.sigma_cut = g.sigma_cut;
     d.rho_unit = g.rho_unit_cgs;
@@ -1591,6 +1596,45 @@ int blacklight_mlp_coefficients(const float* params, int64_t n, const double* in
     });
 }
 
+}  // extern "C"
+
+namespace {
+
+// Plane -> cell repacking of n_snap snapshots of `per_snap` cells (stream-ordered).
+int launch_grid_pack(const float* planes, float* cells, int64_t per_snap, int64_t n_snap,
+                     cudaStream_t st) {
+    DevInfo di;
+    int rc = dev_info(di);
+    if (rc) return rc;
+    const int64_t n = per_snap * n_snap;
+    const int64_t want = (n + 255) / 256, cap = (int64_t)di.sms * 8;
+    bl::grid_pack_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(planes, cells, per_snap, n);
+    ++g_launches;
+    BL_CUDA(cudaGetLastError());
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int blacklight_grid_pack(const float* planes, float* cells, int32_t n_r, int32_t n_theta,
+                         int32_t n_phi, int32_t n_snapshots, void* stream) {
+    g_detail[0] = 0;
+    if (!planes || !cells) return fail(BL_EINVAL, "NULL grid pointer");
+    if (n_r < 1 || n_theta < 1 || n_phi < 1 || n_snapshots < 1)
+        return fail(BL_EINVAL, "grid sizes must be >= 1");
+    if (((uintptr_t)cells & 15u) != 0) return fail(BL_EINVAL, "cells must be 16-byte aligned");
+    int rc = device_pointer(planes, "planes");
+    if (!rc) rc = device_pointer(cells, "cells");
+    if (rc) return rc;
+    const int64_t per_snap = (int64_t)n_r * n_theta * n_phi;
+    const uintptr_t bytes = (uintptr_t)(sizeof(float) * 8 * per_snap * n_snapshots);
+    const uintptr_t a = (uintptr_t)planes, b = (uintptr_t)cells;
+    if (a < b + bytes && b < a + bytes) return fail(BL_EINVAL, "planes and cells overlap");
+    return launch_grid_pack(planes, cells, per_snap, n_snapshots, (cudaStream_t)stream);
+}
+
 int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
                                 const bl_metric_t* mets, const bl_grid_t* grids,
                                 const double* freqs_hz, const bl_out_t* outs, void* stream,
@@ -1606,11 +1650,13 @@ int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
         if (rc) return rc;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    // distinct grids (by host pointer), their sizes and offsets in one device allocation
+    // distinct grids (by host pointer), their sizes and offsets in one device allocation.
+    // Grids given in the plane layout are copied through one staging region and repacked
+    // into the cell layout on the device (each trilinear corner then costs two vector loads).
     std::vector<const float*> uniq;
     std::vector<size_t> gsz, goff;
-    std::vector<int> gidx(n_images);
-    size_t off = 0;
+    std::vector<int> gidx(n_images), gfirst;
+    size_t off = 0, stage = 0;
     for (int q = 0; q < n_images; ++q) {
         const bl_grid_t& g = grids[q];
         const size_t bytes = sizeof(float) * 8 * (size_t)g.n_r * g.n_theta * g.n_phi *
@@ -1623,12 +1669,18 @@ int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
             uniq.push_back(g.prim);
             gsz.push_back(bytes);
             goff.push_back(off);
+            gfirst.push_back(q);
             off = align_up(off + bytes);
+            if (g.layout == BL_GRID_PLANES && bytes > stage) stage = bytes;
         } else if (gsz[k] < bytes) {
             return fail(BL_EINVAL, "grids[%d] shares its prim pointer with a smaller grid", q);
+        } else if (grids[gfirst[k]].layout != g.layout) {
+            return fail(BL_EINVAL, "grids[%d] shares its prim pointer with another layout", q);
         }
         gidx[q] = k;
     }
+    const size_t o_stage = off;
+    off = align_up(off + stage);
     const size_t o_mlp = off;
     if (grids[0].coef_mlp) off = align_up(off + sizeof(float) * BL_MLP_PARAMS);
     std::vector<size_t> o_out(n_images);
@@ -1651,8 +1703,15 @@ int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
     if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync(%zu): %s", off, cudaGetErrorString(e)); }
     int rc = 0;
     for (size_t u = 0; u < uniq.size() && !rc; ++u) {
-        e = cudaMemcpyAsync(dev + goff[u], uniq[u], gsz[u], cudaMemcpyHostToDevice, st);
+        const bl_grid_t& g = grids[gfirst[u]];
+        const bool pack = g.layout == BL_GRID_PLANES;
+        e = cudaMemcpyAsync(dev + (pack ? o_stage : goff[u]), uniq[u], gsz[u],
+                            cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) rc = cuda_fail(e, "copy grid to device");
+        if (!rc && pack)   // stream order: the next copy into the staging region waits for it
+            rc = launch_grid_pack((const float*)(dev + o_stage), (float*)(dev + goff[u]),
+                                  (int64_t)g.n_r * g.n_theta * g.n_phi,
+                                  g.n_snapshots > 1 ? g.n_snapshots : 1, st);
     }
     if (!rc && grids[0].coef_mlp) {
         e = cudaMemcpyAsync(dev + o_mlp, grids[0].coef_mlp, sizeof(float) * BL_MLP_PARAMS,
@@ -1663,6 +1722,7 @@ int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
     std::vector<bl_out_t> dout(outs, outs + n_images);
     for (int q = 0; q < n_images; ++q) {
         dg[q].prim = (const float*)(dev + goff[gidx[q]]);
+        dg[q].layout = BL_GRID_CELLS;
         if (grids[q].coef_mlp) dg[q].coef_mlp = (const float*)(dev + o_mlp);
         const size_t npix = (size_t)cams[q].n * cams[q].n;
         const size_t es = outs[q].dtype == 0 ? sizeof(double) : sizeof(float);

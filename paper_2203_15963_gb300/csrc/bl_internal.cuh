@@ -46,7 +46,7 @@ struct ImageDesc {
     int64_t ray_offset;     // first global ray index of this image
     int64_t n_rays;         // rays traced for this image (n * n, or blocks x block^2)
     int32_t order;          // ray order: 0 Morton (n a power of 2), 1 rows
-    int32_t pad2_;
+    int32_t layout;         // grid memory order: 0 planes [8][phi][theta][r], 1 cells [...][8]
     // filled by the camera-frame kernel
     double x_cam[4], u_cam[4], kk[4], hh[4], vv[4];
     double r_cam, r_hor;

@@ -1031,6 +1031,32 @@ struct Plasma {
     T rho, p, binv;       // code-unit density and pressure, b^2 / (2 p)
 };
 
+// The 8 primitives of cell `cell` of a grid in the cell layout ([...][8], 32 bytes a cell,
+// 16-byte aligned): two read-only 16-byte loads.
+__device__ __forceinline__ void load_cell(const float* __restrict__ base, size_t cell, float c[8]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + 2 * cell;
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+    c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+}
+
+// Plane layout [s][8][cells] -> cell layout [s][cells][8]; one thread per cell, reads
+// coalesced per plane, writes two 16-byte vectors.
+__global__ void grid_pack_kernel(const float* __restrict__ planes, float* __restrict__ cells,
+                                 int64_t cells_per_snap, int64_t n_cells) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += stride) {
+        const int64_t s = c / cells_per_snap, x = c - s * cells_per_snap;
+        const float* src = planes + s * 8 * cells_per_snap + x;
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = __ldg(src + k * cells_per_snap);
+        float4* dst = reinterpret_cast<float4*>(cells) + 2 * c;
+        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+}
+
 template <class T, bool kSlow = false>
 __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t,
                                           const KSGeom<T>& G, Plasma<T>& P) {
@@ -1080,12 +1106,24 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
         j = min(max(j, 0), nt - 1);
         k = ((k % np) + np) % np;
         const size_t base = ((size_t)k * nt + j) * nr + i;
+        if (im.layout == 1) {
+            float c[8];
+            load_cell(prim, base, c);
 #pragma unroll
-        for (int v = 0; v < 8; ++v) pv[v] = (T)__ldg(prim + v * plane + base);
-        if (kSlow && prim1) {
+            for (int v = 0; v < 8; ++v) pv[v] = (T)c[v];
+            if (kSlow && prim1) {
+                load_cell(prim1, base, c);
 #pragma unroll
-            for (int v = 0; v < 8; ++v)
-                pv[v] = (T(1) - wt1) * pv[v] + wt1 * (T)__ldg(prim1 + v * plane + base);
+                for (int v = 0; v < 8; ++v) pv[v] = (T(1) - wt1) * pv[v] + wt1 * (T)c[v];
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < 8; ++v) pv[v] = (T)__ldg(prim + v * plane + base);
+            if (kSlow && prim1) {
+#pragma unroll
+                for (int v = 0; v < 8; ++v)
+                    pv[v] = (T(1) - wt1) * pv[v] + wt1 * (T)__ldg(prim1 + v * plane + base);
+            }
         }
     } else {
         int i0, j0;
@@ -1122,18 +1160,44 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
         const T w010 = (T(1) - wp) * wt * (T(1) - wr), w011 = (T(1) - wp) * wt * wr;
         const T w100 = wp * (T(1) - wt) * (T(1) - wr), w101 = wp * (T(1) - wt) * wr;
         const T w110 = wp * wt * (T(1) - wr), w111 = wp * wt * wr;
-        auto tri = [&](const float* __restrict__ pp) -> T {
-            return w000 * (T)__ldg(pp + o00 + i0) + w001 * (T)__ldg(pp + o00 + i1) +
-                   w010 * (T)__ldg(pp + o01 + i0) + w011 * (T)__ldg(pp + o01 + i1) +
-                   w100 * (T)__ldg(pp + o10 + i0) + w101 * (T)__ldg(pp + o10 + i1) +
-                   w110 * (T)__ldg(pp + o11 + i0) + w111 * (T)__ldg(pp + o11 + i1);
-        };
+        if (im.layout == 1) {
+            // cell layout: the 8 corners as 16 vector loads, summed in the plane form's order
+            auto tri8 = [&](const float* __restrict__ pp, T out[8]) {
+                const size_t cell[8] = {o00 + i0, o00 + i1, o01 + i0, o01 + i1,
+                                        o10 + i0, o10 + i1, o11 + i0, o11 + i1};
+                const T w[8] = {w000, w001, w010, w011, w100, w101, w110, w111};
+                float c[8];
+                load_cell(pp, cell[0], c);
 #pragma unroll
-        for (int v = 0; v < 8; ++v) pv[v] = tri(prim + v * plane);
-        if (kSlow && prim1) {
+                for (int v = 0; v < 8; ++v) out[v] = w[0] * (T)c[v];
 #pragma unroll
-            for (int v = 0; v < 8; ++v)
-                pv[v] = (T(1) - wt1) * pv[v] + wt1 * tri(prim1 + v * plane);
+                for (int n = 1; n < 8; ++n) {
+                    load_cell(pp, cell[n], c);
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) out[v] = out[v] + w[n] * (T)c[v];
+                }
+            };
+            tri8(prim, pv);
+            if (kSlow && prim1) {
+                T pv1[8];
+                tri8(prim1, pv1);
+#pragma unroll
+                for (int v = 0; v < 8; ++v) pv[v] = (T(1) - wt1) * pv[v] + wt1 * pv1[v];
+            }
+        } else {
+            auto tri = [&](const float* __restrict__ pp) -> T {
+                return w000 * (T)__ldg(pp + o00 + i0) + w001 * (T)__ldg(pp + o00 + i1) +
+                       w010 * (T)__ldg(pp + o01 + i0) + w011 * (T)__ldg(pp + o01 + i1) +
+                       w100 * (T)__ldg(pp + o10 + i0) + w101 * (T)__ldg(pp + o10 + i1) +
+                       w110 * (T)__ldg(pp + o11 + i0) + w111 * (T)__ldg(pp + o11 + i1);
+            };
+#pragma unroll
+            for (int v = 0; v < 8; ++v) pv[v] = tri(prim + v * plane);
+            if (kSlow && prim1) {
+#pragma unroll
+                for (int v = 0; v < 8; ++v)
+                    pv[v] = (T(1) - wt1) * pv[v] + wt1 * tri(prim1 + v * plane);
+            }
         }
     }
     // spherical -> Cartesian KS vectors (Jacobian columns d x^a / d(r, theta, phi))

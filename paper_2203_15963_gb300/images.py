@@ -33,3 +33,15 @@ def trace_images(cams, mets, gps, prims, freqs, dtype=None, end_state=False, wor
     rc = native.blacklight_trace_batch(cams, mets, gps, prims, freqs, outs, workspace=workspace,
                                        flags=flags, coef_mlp=coef_mlp)
     return rc, outs
+
+
+def pack_grid(prim: torch.Tensor, gp):
+    """The grid tensor `prim` (plane layout, on the device) repacked into the cell layout by
+    the library; returns (cells tensor, grid parameters with layout = cells)."""
+    import dataclasses
+    n_snap = max(1, getattr(gp, "n_snapshots", 1))
+    shape = (n_snap, gp.n_phi, gp.n_theta, gp.n_r, 8) if n_snap > 1 else \
+        (gp.n_phi, gp.n_theta, gp.n_r, 8)
+    cells = torch.empty(shape, dtype=torch.float32, device=prim.device)
+    native.blacklight_grid_pack(prim, cells, gp)
+    return cells, dataclasses.replace(gp, layout=native.BL_GRID_CELLS)

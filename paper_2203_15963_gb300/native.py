@@ -18,6 +18,7 @@ _INCLUDE = os.path.join(_ROOT, "include")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 BL_PREC_FP64, BL_PREC_MIXED, BL_PREC_FAST = 0, 1, 2
+BL_GRID_PLANES, BL_GRID_CELLS = 0, 1
 BL_ASYNC = 1
 BL_TIMING = 2
 RAY_STATUS = {0: "ok", 1: "horizon", 2: "escaped", 3: "max_steps", 4: "underflow", 5: "nan",
@@ -68,7 +69,7 @@ class Grid(C.Structure):
                 ("sigma_cut", C.c_double), ("rho_unit_cgs", C.c_double),
                 ("mass_msun", C.c_double), ("interp", C.c_int32), ("coef_mlp", C.c_void_p),
                 ("n_snapshots", C.c_int32), ("time_interp", C.c_int32), ("t_first", C.c_double),
-                ("dt_snapshots", C.c_double), ("t_camera", C.c_double)]
+                ("dt_snapshots", C.c_double), ("t_camera", C.c_double), ("layout", C.c_int32)]
 
 
 class MlpTrain(C.Structure):
@@ -137,6 +138,7 @@ def load():
                                         C.c_double, C.POINTER(Out), P]
     L.blacklight_geodesics.argtypes = [C.POINTER(Camera), C.POINTER(Metric), C.POINTER(Out), P,
                                        C.c_uint32]
+    L.blacklight_grid_pack.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P]
     L.blacklight_workspace_size.argtypes = [C.c_int32, C.POINTER(Camera), C.POINTER(Metric)]
     L.blacklight_workspace_size.restype = C.c_size_t
     L.blacklight_coefficients.argtypes = [C.c_int64, P, P, C.c_int32, P]
@@ -226,7 +228,7 @@ def grid_struct(gp, prim_ptr, coef_mlp=None) -> Grid:
                 None if coef_mlp is None else coef_mlp.data_ptr(),
                 getattr(gp, "n_snapshots", 1), getattr(gp, "time_interp", 1),
                 getattr(gp, "t_first", 0.0), getattr(gp, "dt_snapshots", 1.0),
-                getattr(gp, "t_camera", 0.0))
+                getattr(gp, "t_camera", 0.0), getattr(gp, "layout", BL_GRID_PLANES))
 
 
 def out_struct(stokes=None, status=None, steps=None, end_state=None, samples=None,
@@ -297,6 +299,17 @@ def blacklight_trace_host_batch(cams, mets, gps, prims_host, freqs, outs_host, s
     fa = (C.c_double * n)(*[float(f) for f in freqs])
     oa = (Out * n)(*[out_struct(**o) for o in outs_host])
     return _check(L.blacklight_trace_host_batch(n, ca, ma, ga, fa, oa, _stream(stream), flags))
+
+
+def blacklight_grid_pack(planes, cells, gp, stream=None):
+    """Repack the grid tensor `planes` ([snapshots][8][phi][theta][r]) into `cells`
+    ([snapshots][phi][theta][r][8]), both on the device, on `stream`."""
+    n_snap = max(1, getattr(gp, "n_snapshots", 1))
+    want = 8 * gp.n_r * gp.n_theta * gp.n_phi * n_snap
+    if planes.numel() < want or cells.numel() < want:
+        raise ValueError("grid tensors smaller than the grid")
+    return _check(load().blacklight_grid_pack(_ptr(planes), _ptr(cells), gp.n_r, gp.n_theta,
+                                              gp.n_phi, n_snap, _stream(stream)))
 
 
 def blacklight_geodesics(cam, met, out, stream=None, flags=0):

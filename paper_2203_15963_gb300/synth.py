@@ -87,6 +87,7 @@ class GridParams:
     t_first: float = 0.0
     dt_snapshots: float = 1.0
     t_camera: float = 0.0
+    layout: int = 0                # memory order of prim: 0 planes [8][phi][theta][r], 1 cells
 
 
 def r_faces(gp: GridParams) -> np.ndarray:
