@@ -31,22 +31,28 @@ FREQ = 230e9
 N_PIX = 256
 GRID = (256, 128, 128)
 # Algorithmic arithmetic per unit of work (operation counts of the method, see design notes):
-# FP64 flops per Dormand-Prince attempt (6 right-hand sides, 5 stage combinations, error norm)
-FLOP64_PER_ATTEMPT = 1520
+# FP64 flops per Dormand-Prince attempt: 6 right-hand sides of 116 flops (83 products, 30
+# sums, 2 reciprocal square roots, 1 reciprocal in the form with d_c(l.k) taken directly),
+# 6 stage combinations (384), the embedded error estimate (96) and its norm and the step
+# control (50).
+FLOP64_PER_ATTEMPT = 1226
 # dram__bytes_read.sum + dram__bytes_write.sum of geodesic_kernel<float, df64> per DP attempt
-# (1.508 GB for 7,845,744 attempts: the a = 0.94, i = 60 deg image of this workload at 256^2)
-GEO_DF64_DRAM_BYTES_PER_ATTEMPT = 192.2
+# from one ncu capture of the a = 0.94, i = 60 deg image of this workload at 256^2 (1.498 GB
+# for 7,845,744 attempts); None whenever the kernel has changed since the capture
+GEO_DF64_DRAM_BYTES_PER_ATTEMPT = 190.9
 # FP32 flops per transfer sample (2 transport matrices, predictor-corrector, sampling,
 # plasma, coefficients, fluid frame, Stokes step)
 FLOP32_PER_SAMPLE = 3300
 # Nominal peaks from the pool's profiling recipe (no measured FP64/FP32 peak is available):
 # FP64 1.25 TFLOP/s; FP32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
 PEAK_FP64_TFLOPS = 1.25
-# Double-float: FP32 instructions per emulated FP64 flop -- a product costs 7, a sum 11,
-# so an FP64 multiply-add (2 flops) costs 18, i.e. 9 per flop, plus the reciprocal square
-# roots (~20 each); 9.5 on the right-hand side's mix. The emulated peak is the FP32 issue
-# rate (152 SMs x 128 lanes x 2.07 GHz instructions/s) divided by that.
-DF64_INSTR_PER_FLOP = 9.5
+# Double-float: FP32 instructions per emulated FP64 flop -- a product costs 7, a sum 11, a
+# reciprocal or reciprocal square root ~20, an FP32 flop 1. On the attempt's mix (right-hand
+# sides 971 instructions for 116 flops, stage combinations 3360 for 384, error estimate 832
+# for 96, norm and control ~60 for 50) that is 10078 instructions for 1226 flops, 8.2 per
+# flop. The emulated peak is the FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz
+# instructions/s) divided by that.
+DF64_INSTR_PER_FLOP = 8.2
 PEAK_DF64_TFLOPS = 152 * 128 * 2.07e9 / DF64_INSTR_PER_FLOP / 1e12
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -373,8 +379,8 @@ def main():
         roof = {"kernel": "geodesic_kernel (double-float on FP32)", "bound": "alu",
                 "achieved": flop_geo / geo_avg / 1e12, "peak": PEAK_DF64_TFLOPS,
                 "unit": "TFLOP/s",
-                "peak_source": "FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz) / 9.5 FP32 "
-                               "instructions per emulated FP64 flop"}
+                "peak_source": f"FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz) / "
+                               f"{DF64_INSTR_PER_FLOP} FP32 instructions per emulated FP64 flop"}
     else:
         peak = PEAK_FP32_TFLOPS if prec != native.BL_PREC_FP64 else PEAK_FP64_TFLOPS
         roof = {"kernel": "transfer_kernel", "bound": "alu",
@@ -384,7 +390,8 @@ def main():
     # DRAM bytes (read + written) of the dominant kernel per launch: the per-unit figure from
     # one ncu capture of the same kernel on the one-image 256^2 case, scaled by the units of
     # this launch (attempts for the geodesic kernel, samples for the transfer kernel)
-    if roof["kernel"].startswith("geodesic_kernel (double-float"):
+    if (roof["kernel"].startswith("geodesic_kernel (double-float")
+            and GEO_DF64_DRAM_BYTES_PER_ATTEMPT is not None):
         roof["traffic"] = GEO_DF64_DRAM_BYTES_PER_ATTEMPT * attempts
         roof["traffic_note"] = "ncu capture of the 256^2 one-image case, scaled by DP attempts"
     else:

@@ -389,28 +389,63 @@ template <> struct GeoArith<df64> {
     static __device__ __forceinline__ float tof(const df64& g) { return g.hi + g.lo; }
 };
 
-// Eq. (geodesic) right-hand side in arithmetic G (see the double form in bl_math.cuh);
-// returns r at the evaluation point.
+// Eq. (geodesic) right-hand side in arithmetic G; returns r at the evaluation point.
+// With g^ab = eta^ab - f l^a l^b and L = l^a k_a, dx^a/dl = g^ab k_b and
+// dk_c/dl = L (1/2 d_c f L + f d_c L), where d_c L is the derivative at fixed k. Instead of the
+// nine derivatives d_c l_b (bl_math.cuh's form, kept for the transport matrices), d_c L is
+// formed directly: with A = x k_x + y k_y and B = y k_x - x k_y, l_x k_x + l_y k_y =
+// (r A + a B) / (r^2 + a^2) =: L_xy and l_z k_z = z k_z / r, so
+//   d_c L = d_c r V + (r k_x - a k_y, r k_y + a k_x, k_z)_c / (r^2 + a^2 or r),
+//   V = (A - 2 r L_xy) / (r^2 + a^2) - k_z z / r^2,
+// and d_c f = F1 d_c r - [c = z] 2 a^2 z f / (r^4 + a^2 z^2), F1 = f (3 / r - 4 r^3 / (r^4 + a^2 z^2)).
+// The same quantities as the nine-derivative form, in about 40 fewer operations.
 template <class G>
 __device__ __forceinline__ G geodesic_rhs_g(const G y[8], const G& a, const G& m, bool flat, G dy[8]) {
-    KSGeom<G> K;
-    ks_geom<G>(y[1], y[2], y[3], a, m, flat, true, K);
-    const G* k = y + 4;
-    const G L = K.l[1] * k[1] + K.l[2] * k[2] + K.l[3] * k[3] - k[0];
-    const G fL = K.f * L;
-    dy[0] = fL - k[0];
-    dy[1] = k[1] - K.l[1] * fL;
-    dy[2] = k[2] - K.l[2] * fL;
-    dy[3] = k[3] - K.l[3] * fL;
-    constexpr G kZero = G(0), kHalf = G(0.5);
-    dy[4] = kZero;
-    const G halfL = kHalf * L;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const G S = K.dl[c][0] * k[1] + K.dl[c][1] * k[2] + K.dl[c][2] * k[3];
-        dy[5 + c] = L * (K.df[c] * halfL + K.f * S);
-    }
-    return K.r;
+    constexpr G c0 = G(0), c2 = G(2), c3 = G(3), c4 = G(4), cHalf = G(0.5), c1 = G(1);
+    const G x = y[1], yy = y[2], z = y[3];
+    const G kt = y[4], kx = y[5], ky = y[6], kz = y[7];
+    // r (Eq. cks_aux:r), f and l as in ks_geom: two reciprocal square roots, one reciprocal
+    const G aa = a * a;
+    const G q = x * x + yy * yy + z * z - aa;
+    const G D2 = q * q + c4 * aa * z * z;
+    const G iD = rsqrt(D2);
+    const G r2 = cHalf * (q + D2 * iD);
+    const G ir = rsqrt(r2);
+    const G r = r2 * ir;
+    const G s4 = r2 * r2 + aa * z * z;
+    const G P = r2 + aa;
+    const G iPs = c1 / (P * s4);
+    const G is4 = P * iPs;
+    const G iP = s4 * iPs;
+    const G f = flat ? c0 : c2 * m * r * r2 * is4;
+    const G lx = (r * x + a * yy) * iP, ly = (r * yy - a * x) * iP, lz = z * ir;
+    // L = l^a k_a (l^t = -1)
+    const G A_ = x * kx + yy * ky;
+    const G B_ = yy * kx - x * ky;
+    const G Lxy = (r * A_ + a * B_) * iP;
+    const G L = Lxy + lz * kz - kt;
+    const G fL = f * L;
+    dy[0] = fL - kt;
+    dy[1] = kx - lx * fL;
+    dy[2] = ky - ly * fL;
+    dy[3] = kz - lz * fL;
+    dy[4] = c0;
+    // d_c r
+    const G riD = r * iD;
+    const G drx = riD * x, dry = riD * yy, drz = z * P * ir * iD;
+    // d_c L at fixed k, and d_c f
+    const G V = (A_ - c2 * r * Lxy) * iP - kz * ir * lz;
+    const G Sx = drx * V + (r * kx - a * ky) * iP;
+    const G Sy = dry * V + (r * ky + a * kx) * iP;
+    const G Sz = drz * V + kz * ir;
+    const G F1 = f * (c3 * ir - c4 * r2 * r * is4);
+    const G dfx = F1 * drx, dfy = F1 * dry;
+    const G dfz = F1 * drz - c2 * aa * z * f * is4;
+    const G halfL = cHalf * L;
+    dy[5] = L * (dfx * halfL + f * Sx);
+    dy[6] = L * (dfy * halfL + f * Sy);
+    dy[7] = L * (dfz * halfL + f * Sz);
+    return r;
 }
 
 template <> struct DPCoef<df64> {
