@@ -1491,7 +1491,7 @@ int blacklight_mlp_grad(const float* params, int64_t n, const float* inputs, con
         BL_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * BL_MLP_PARAMS, st));
         BL_CUDA(cudaMemsetAsync(dloss, 0, sizeof(float), st));
         bl::mlp::train_kernel<<<(unsigned)((n + 127) / 128), 128, bl::mlp::kTrainSmem, st>>>(
-            params, n, inputs, targets, 0, n, (double)n, grad, dloss, err);
+            params, n, inputs, targets, 0, n, (double)n, grad, dloss, nullptr, nullptr, err);
         ++g_launches;
         BL_CUDA(cudaGetLastError());
         float h = 0.0f;
@@ -1520,29 +1520,35 @@ int blacklight_mlp_train(const bl_mlp_train_t* cfg, float* params, float* loss_h
     if (!rc) rc = mlp_train_attr();
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    float* buf = nullptr;    // grad, m, v [BL_MLP_PARAMS] each, loss
-    const size_t bytes = sizeof(float) * (3 * (size_t)BL_MLP_PARAMS + 1);
+    // m, v [BL_MLP_PARAMS] each, then per-tile gradient sums [tiles][trained parameters] and
+    // per-tile losses [tiles]: the tiles' sums are reduced in a fixed order, so a training run
+    // is reproducible bit for bit
+    const int64_t tiles = cfg->batch / 128;
+    const size_t n_part = (size_t)tiles * bl::mlp::kOffMean;
+    float* buf = nullptr;
+    const size_t bytes = sizeof(float) * (2 * (size_t)BL_MLP_PARAMS + n_part + (size_t)tiles);
     cudaError_t e = cudaMallocAsync((void**)&buf, bytes, st);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e)); }
-    float *grad = buf, *m = buf + BL_MLP_PARAMS, *v = buf + 2 * BL_MLP_PARAMS, *loss = buf + 3 * BL_MLP_PARAMS;
+    float *m = buf, *v = buf + BL_MLP_PARAMS, *part = buf + 2 * BL_MLP_PARAMS,
+          *part_loss = part + n_part;
     rc = with_tc_flag(st, [&](int* err) -> int {
         BL_CUDA(cudaMemsetAsync(buf, 0, bytes, st));
-        const unsigned blocks = (unsigned)(cfg->batch / 128);
+        const unsigned blocks = (unsigned)tiles;
         const double b1 = cfg->beta1, b2 = cfg->beta2;
         double p1 = 1.0, p2 = 1.0;
         for (int64_t t = 0; t < cfg->steps; ++t) {
             const int64_t first = (int64_t)((t * (int64_t)cfg->batch) % cfg->n);
             bl::mlp::train_kernel<<<blocks, 128, bl::mlp::kTrainSmem, st>>>(
                 params, cfg->n, cfg->inputs, cfg->targets, first, cfg->batch, (double)cfg->batch,
-                grad, loss, err);
+                nullptr, nullptr, part, part_loss, err);
             const double frac = cfg->steps > 1 ? (double)t / (double)(cfg->steps - 1) : 0.0;
             const double lr = cfg->lr_start * pow(cfg->lr_end / cfg->lr_start, frac);
             p1 *= b1;
             p2 *= b2;
             bl::mlp::adam_kernel<<<(bl::mlp::kOffMean + 255) / 256, 256, 0, st>>>(
-                params, grad, m, v, (float)lr, (float)b1, (float)b2, (float)cfg->eps,
-                (float)(1.0 - p1), (float)(1.0 - p2), loss, loss_history ? loss_history + t : nullptr,
-                (float)(1.0 / (7.0 * cfg->batch)));
+                params, part, (int)tiles, m, v, (float)lr, (float)b1, (float)b2, (float)cfg->eps,
+                (float)(1.0 - p1), (float)(1.0 - p2), part_loss,
+                loss_history ? loss_history + t : nullptr, (float)(1.0 / (7.0 * cfg->batch)));
             g_launches += 2;
             BL_CUDA(cudaGetLastError());
         }

@@ -329,15 +329,20 @@ constexpr int kCZ1 = 0, kCZ2 = 64, kCZ3 = 128, kCdH2 = 160, kCdW3 = 224, kCdH1 =
               kCdW2 = 368, kCdW1 = 448;
 constexpr uint32_t kTrainCols = 512;
 
-// Gradients of the mean squared error over n_total samples x 7 outputs, accumulated into
-// grad[kParams] (atomically), and the summed squared error into *loss. The grid covers
-// `count` samples starting at sample `first` of the n-sample set (wrapping around).
+// Gradients of the mean squared error over n_total samples x 7 outputs and the summed squared
+// error; block b takes the 128-sample tile b of the `count` samples starting at sample `first`
+// of the n-sample set (wrapping around). With part == nullptr the tiles add into grad[kParams]
+// and *loss atomically (summation order, and so the last bits, vary between runs). Otherwise
+// tile b stores its own sums, part[b][kOffMean] (every trained parameter) and part_loss[b], for
+// a reduction in a fixed order (adam_kernel), which makes training reproducible bit for bit.
 __global__ void __launch_bounds__(128, 1) train_kernel(const float* __restrict__ P, int64_t n,
                                                        const float* __restrict__ in,
                                                        const float* __restrict__ tg,
                                                        int64_t first, int64_t count,
                                                        double n_total, float* __restrict__ grad,
-                                                       float* __restrict__ loss, int* err) {
+                                                       float* __restrict__ loss,
+                                                       float* __restrict__ part,
+                                                       float* __restrict__ part_loss, int* err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     float* b2 = (float*)(sm + kTF32);
     float* b3 = b2 + 64;
@@ -494,7 +499,9 @@ __global__ void __launch_bounds__(128, 1) train_kernel(const float* __restrict__
         barrier();
         if (t == 0) {
             tc::fence_after_sync();
-            atomicAdd(loss, red[0] + red[1] + red[2] + red[3]);
+            const float tile_loss = red[0] + red[1] + red[2] + red[3];
+            if (part_loss) part_loss[blockIdx.x] = tile_loss;
+            else atomicAdd(loss, tile_loss);
             tc::gemm_bf16(tm + kCdH2, sm + kTdZ3, sm + kTW3T, 64, 16);
             tc::gemm_bf16(tm + kCdW3, sm + kTdZ3T, sm + kTH2T, 80, 128);
             tc::mma_commit(bar);
@@ -537,6 +544,11 @@ __global__ void __launch_bounds__(128, 1) train_kernel(const float* __restrict__
         }
         if (!(ok = wait())) break;
         // ---- accumulate this tile's weight gradients (rows = units: lanes 0-63)
+        float* const own = part ? part + (size_t)blockIdx.x * kOffMean : nullptr;
+        auto put = [&](int idx, float val) {
+            if (own) own[idx] = val;
+            else atomicAdd(&grad[idx], val);
+        };
         if (warp < 2) {
             const int j = t;                    // unit of layers 1 and 2
             for (int c = 0; c < 5; ++c) {       // dW2 columns 0-63, db2 in column 64
@@ -544,13 +556,13 @@ __global__ void __launch_bounds__(128, 1) train_kernel(const float* __restrict__
                 tc::tmem_ld16(tc::tmem_lane_addr(tm, kCdW2 + 16 * c), v);
                 for (int q = 0; q < 16; ++q) {
                     const int col = 16 * c + q;
-                    if (col < 64) atomicAdd(&grad[kOffW2 + 64 * j + col], v[q]);
-                    else if (col == 64) atomicAdd(&grad[kOffB2 + j], v[q]);
+                    if (col < 64) put(kOffW2 + 64 * j + col, v[q]);
+                    else if (col == 64) put(kOffB2 + j, v[q]);
                 }
             }
             float v[16];
             tc::tmem_ld16(tc::tmem_lane_addr(tm, kCdW1), v);
-            for (int q = 0; q < 4; ++q) atomicAdd(&grad[kOffW1 + 4 * j + q], v[q]);
+            for (int q = 0; q < 4; ++q) put(kOffW1 + 4 * j + q, v[q]);
         }
         if (warp == 0) {
             for (int c = 0; c < 5; ++c) {       // dW3 rows 0-6, db3 in column 64
@@ -559,8 +571,8 @@ __global__ void __launch_bounds__(128, 1) train_kernel(const float* __restrict__
                 if (lane < kOut)
                     for (int q = 0; q < 16; ++q) {
                         const int col = 16 * c + q;
-                        if (col < 64) atomicAdd(&grad[kOffW3 + 64 * lane + col], v[q]);
-                        else if (col == 64) atomicAdd(&grad[kOffB3 + lane], v[q]);
+                        if (col < 64) put(kOffW3 + 64 * lane + col, v[q]);
+                        else if (col == 64) put(kOffB3 + lane, v[q]);
                     }
             }
         }
@@ -578,22 +590,26 @@ __global__ void __launch_bounds__(128, 1) train_kernel(const float* __restrict__
 // One Adam step (Kingma & Ba 2015) on every trained parameter; clears the gradient. c1, c2
 // are the bias corrections 1 - beta1^t, 1 - beta2^t. Also moves the step's summed squared
 // error into loss_hist (mean over n_total x 7) and clears it.
-__global__ void adam_kernel(float* __restrict__ P, float* __restrict__ grad, float* __restrict__ m,
-                            float* __restrict__ v, float lr, float beta1, float beta2, float eps,
-                            float c1, float c2, float* loss, float* loss_hist, float inv_count) {
+__global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ part, int n_tiles,
+                            float* __restrict__ m, float* __restrict__ v, float lr, float beta1,
+                            float beta2, float eps, float c1, float c2,
+                            const float* __restrict__ part_loss, float* loss_hist,
+                            float inv_count) {
+    // one Adam step from the tiles' gradient sums, added in tile order
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0 && loss_hist) {
-        *loss_hist = *loss * inv_count;
+        float l = 0.0f;
+        for (int b = 0; b < n_tiles; ++b) l += part_loss[b];
+        *loss_hist = l * inv_count;
     }
-    if (i == 0) *loss = 0.0f;
     if (i >= kOffMean) return;
-    const float g = grad[i];
+    float g = 0.0f;
+    for (int b = 0; b < n_tiles; ++b) g += part[(size_t)b * kOffMean + i];
     const float mi = beta1 * m[i] + (1.0f - beta1) * g;
     const float vi = beta2 * v[i] + (1.0f - beta2) * g * g;
     m[i] = mi;
     v[i] = vi;
     P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    grad[i] = 0.0f;
 }
 
 // n uniform samples of the input box (SplitMix64 stream `seed`: draws 3i, 3i+1, 3i+2) and
