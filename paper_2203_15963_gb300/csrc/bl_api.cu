@@ -259,6 +259,10 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
     d.n_rays = (int64_t)c.n * c.n;
 }
 
+// Dynamic shared memory of a geodesic-kernel CTA: the stage derivatives, 7 x 8 values of 8
+// bytes for each of its 128 threads.
+constexpr size_t kGeoSmem = BL_GEO_K_SMEM ? (size_t)7 * 8 * 128 * 8 : 0;
+
 struct DevInfo {
     int sms = 0;
     int geo_blocks[3] = {0, 0, 0};  // per SM, indexed by precision: [fp64, mixed, fast]
@@ -303,9 +307,17 @@ int dev_info(DevInfo& out) {
     DevInfo& di = cache[dev];
     if (di.sms == 0) {
         BL_CUDA(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[0], bl::geodesic_kernel<double, double>, 128, 0));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[1], bl::geodesic_kernel<float, double>, 128, 0));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[2], bl::geodesic_kernel<float, bl::df64>, 128, 0));
+        if (kGeoSmem > 0) {   // the stage derivatives exceed the default 48 KB of shared memory
+            BL_CUDA(cudaFuncSetAttribute(bl::geodesic_kernel<double, double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGeoSmem));
+            BL_CUDA(cudaFuncSetAttribute(bl::geodesic_kernel<float, double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGeoSmem));
+            BL_CUDA(cudaFuncSetAttribute(bl::geodesic_kernel<float, bl::df64>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGeoSmem));
+        }
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[0], bl::geodesic_kernel<double, double>, 128, kGeoSmem));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[1], bl::geodesic_kernel<float, double>, 128, kGeoSmem));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[2], bl::geodesic_kernel<float, bl::df64>, 128, kGeoSmem));
         for (int i = 0; i < 3; ++i)
             if (di.geo_blocks[i] < 1) di.geo_blocks[i] = 1;
         int rc = occ_transfer_all<double, double>(di.tr_occ[0]);
@@ -400,15 +412,15 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
             }
         } else if (precision == BL_PREC_FP64) {
             bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
-            bl::geodesic_kernel<double, double><<<geo_grid, 128, 0, st>>>(
+            bl::geodesic_kernel<double, double><<<geo_grid, 128, kGeoSmem, st>>>(
                 d_desc, n_images, b, e, hdr, sink, record, cfg.bs);
         } else {
             bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
             if (precision == BL_PREC_MIXED)
-                bl::geodesic_kernel<float, double><<<geo_grid, 128, 0, st>>>(
+                bl::geodesic_kernel<float, double><<<geo_grid, 128, kGeoSmem, st>>>(
                     d_desc, n_images, b, e, hdr, sink, record, cfg.bs);
             else
-                bl::geodesic_kernel<float, bl::df64><<<geo_grid, 128, 0, st>>>(
+                bl::geodesic_kernel<float, bl::df64><<<geo_grid, 128, kGeoSmem, st>>>(
                     d_desc, n_images, b, e, hdr, sink, record, cfg.bs);
         }
         ++g_launches;

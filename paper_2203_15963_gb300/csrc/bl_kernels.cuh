@@ -501,6 +501,10 @@ __device__ __forceinline__ bool append_record(const RecordSink<R>& S, int64_t ra
 #ifndef BL_GEO_MIN_CTAS
 #define BL_GEO_MIN_CTAS 3
 #endif
+// Stage derivatives of the geodesic kernel in dynamic shared memory (1) or a local array (0).
+#ifndef BL_GEO_K_SMEM
+#define BL_GEO_K_SMEM 1
+#endif
 // Records of a subdivided step from the FP32 quartic about the step's start (coefficients
 // y0, d0 = h f0, c2, c3, c4 per component): nsub samples at the centres of equal parts.
 template <class R>
@@ -586,7 +590,17 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
     int64_t opix = 0;   // output index of the current ray
     int64_t wray = 0;   // index of the current ray within this wave
     G y[8];
-    G K[7][8];          // K[0] = f(y); K[1..6] stage derivatives of the current attempt
+    // K(0, c) = f(y); K(1..6, c) stage derivatives of the current attempt. In shared memory
+    // (thread-fastest, conflict-free): 448 B a thread, which as a local array would take 172 KB
+    // of L1 per SM and miss to L2.
+#if BL_GEO_K_SMEM
+    extern __shared__ __align__(16) unsigned char geo_smem[];
+    G* const Kt = reinterpret_cast<G*>(geo_smem) + threadIdx.x;
+#define KX(j, c) Kt[((j) * 8 + (c)) * 128]
+#else
+    G Kl[7][8];
+#define KX(j, c) Kl[j][c]
+#endif
     G h = G(0);
     double nnorm = 0.0;
     bool been_inside = false, prev_rej = false;
@@ -635,7 +649,12 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
             max_steps = im.max_steps;
             want_aux = record && im.aux != nullptr;
             aux_len = aux_lam = 0.0;
-            r_cur = A::to(geodesic_rhs_g<G>(y, a, m, flat, K[0]));
+            {
+                G f0[8];
+                r_cur = A::to(geodesic_rhs_g<G>(y, a, m, flat, f0));
+#pragma unroll
+                for (int c = 0; c < 8; ++c) KX(0, c) = f0[c];
+            }
             h = A::from(-im.h0_frac * (r_cam - im.r_hor));
             been_inside = r_cur < r_cam;
             prev_rej = false;
@@ -650,12 +669,15 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
         for (int st = 1; st < 7; ++st) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                G acc = DPCoef<G>::a(st, 0) * K[0][c];
+                G acc = DPCoef<G>::a(st, 0) * KX(0, c);
 #pragma unroll 1
-                for (int j = 1; j < st; ++j) acc = acc + DPCoef<G>::a(st, j) * K[j][c];
+                for (int j = 1; j < st; ++j) acc = acc + DPCoef<G>::a(st, j) * KX(j, c);
                 ys[c] = y[c] + h * acc;
             }
-            const G rr = geodesic_rhs_g<G>(ys, a, m, flat, K[st]);
+            G fs[8];
+            const G rr = geodesic_rhs_g<G>(ys, a, m, flat, fs);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) KX(st, c) = fs[c];
             if (st == 6) {
                 r5 = kNative ? A::to(rr) : (double)A::tof(rr);
 #pragma unroll
@@ -671,9 +693,9 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
             G errv[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                G acc = DPCoef<G>::e(0) * K[0][c];
+                G acc = DPCoef<G>::e(0) * KX(0, c);
 #pragma unroll 1
-                for (int j = 2; j < 7; ++j) acc = acc + DPCoef<G>::e(j) * K[j][c];
+                for (int j = 2; j < 7; ++j) acc = acc + DPCoef<G>::e(j) * KX(j, c);
                 errv[c] = h * acc;
             }
             if constexpr (kNative) {
@@ -711,9 +733,9 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
                 {
-                    G acc = DPCoef<G>::m(0) * K[0][c];
+                    G acc = DPCoef<G>::m(0) * KX(0, c);
 #pragma unroll 1
-                    for (int j = 2; j < 7; ++j) acc = acc + DPCoef<G>::m(j) * K[j][c];
+                    for (int j = 2; j < 7; ++j) acc = acc + DPCoef<G>::m(j) * KX(j, c);
                     ym[c] = y[c] + (kHalf * h) * acc;
                 }
                 const double r0 = r_cur, r1 = r5;
@@ -772,9 +794,9 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                     float y0f[8], d0f[8], c2f[8], c3f[8], c4f[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        const G d0 = h * K[0][c];
+                        const G d0 = h * KX(0, c);
                         const G D1 = y5[c] - y[c] - d0;
-                        const G D2 = h * K[6][c] - d0;
+                        const G D2 = h * KX(6, c) - d0;
                         const G D3 = ym[c] - y[c] - kHalf * d0;
                         y0f[c] = A::tof(y[c]);
                         d0f[c] = A::tof(d0);
@@ -788,9 +810,9 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         y0d[c] = A::to(y[c]);
-                        d0[c] = hd * A::to(K[0][c]);
+                        d0[c] = hd * A::to(KX(0, c));
                         const double D1 = A::to(y5[c]) - y0d[c] - d0[c];
-                        const double D2 = hd * A::to(K[6][c]) - d0[c];
+                        const double D2 = hd * A::to(KX(6, c)) - d0[c];
                         const double D3 = A::to(ym[c]) - y0d[c] - 0.5 * d0[c];
                         c2[c] = -5.0 * D1 + D2 + 16.0 * D3;
                         c3[c] = 14.0 * D1 - 3.0 * D2 - 32.0 * D3;
@@ -812,7 +834,7 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                 if (!ok) { status = BL_RAY_OVERFLOW; done = true; }
             }
 #pragma unroll
-            for (int c = 0; c < 8; ++c) { y[c] = y5[c]; K[0][c] = K[6][c]; }
+            for (int c = 0; c < 8; ++c) { y[c] = y5[c]; KX(0, c) = KX(6, c); }
             if constexpr (kNative) {
                 double fac = (eps == 0.0) ? 10.0 : 0.9 * pow(eps, -0.2);
                 fac = fmin(10.0, fmax(0.2, fac));
@@ -877,6 +899,7 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
         }
     }
 }
+#undef KX
 
 // Per-image constant in the transfer arithmetic.
 template <class T>
