@@ -649,35 +649,39 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
             max_steps = im.max_steps;
             want_aux = record && im.aux != nullptr;
             aux_len = aux_lam = 0.0;
-            {
-                G f0[8];
-                r_cur = A::to(geodesic_rhs_g<G>(y, a, m, flat, f0));
-#pragma unroll
-                for (int c = 0; c < 8; ++c) KX(0, c) = f0[c];
-            }
             h = A::from(-im.h0_frac * (r_cam - im.r_hor));
-            been_inside = r_cur < r_cam;
             prev_rej = false;
         }
         // ---- one Dormand-Prince attempt (Table tab:dp) ----
         // Rolled stage loop: one right-hand-side body run six times keeps the kernel small
-        // enough for the instruction cache. K[0] holds f(y) (first same as last), K[s] the
-        // stage derivatives; stage 6 is evaluated at the fifth-order solution y5.
+        // enough for the instruction cache. K(0) holds f(y) (first same as last), K(s) the
+        // stage derivatives; stage 6 is evaluated at the fifth-order solution y5. A ray's first
+        // attempt starts at stage 0, which evaluates f(y) at the stage point y, so that the
+        // set-up path needs no copy of the right-hand side.
         G ys[8], y5[8];
         double r5 = 0.0;
 #pragma unroll 1
-        for (int st = 1; st < 7; ++st) {
+        for (int st = need ? 0 : 1; st < 7; ++st) {
+            if (st == 0) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                G acc = DPCoef<G>::a(st, 0) * KX(0, c);
+                for (int c = 0; c < 8; ++c) ys[c] = y[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    G acc = DPCoef<G>::a(st, 0) * KX(0, c);
 #pragma unroll 1
-                for (int j = 1; j < st; ++j) acc = acc + DPCoef<G>::a(st, j) * KX(j, c);
-                ys[c] = y[c] + h * acc;
+                    for (int j = 1; j < st; ++j) acc = acc + DPCoef<G>::a(st, j) * KX(j, c);
+                    ys[c] = y[c] + h * acc;
+                }
             }
             G fs[8];
             const G rr = geodesic_rhs_g<G>(ys, a, m, flat, fs);
 #pragma unroll
             for (int c = 0; c < 8; ++c) KX(st, c) = fs[c];
+            if (st == 0) {
+                r_cur = A::to(rr);
+                been_inside = r_cur < r_cam;
+            }
             if (st == 6) {
                 r5 = kNative ? A::to(rr) : (double)A::tof(rr);
 #pragma unroll
@@ -1551,20 +1555,53 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
             active = true;
         }
         const ImageDesc& im = imgs[q];
-        // record idx was prefetched into nxt; start fetching idx - 1 before using it
+        // idx < 0: every sample is in, and this iteration only takes the last half-step to the
+        // camera node and reads the pixel out (sharing the transport code of the sample steps)
+        const bool finishing = idx < 0;
         T cur[kRecVals];
+        T nxt_t = T(0);   // the sample's coordinate time
+        if (!finishing) {
+            // record idx was prefetched into nxt; start fetching idx - 1 before using it
 #pragma unroll
-        for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
-        const T nxt_t = (T)nxt[13];   // the sample's coordinate time
-        if (idx > 0) load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
+            for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
+            nxt_t = (T)nxt[13];
+            if (idx > 0) load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
+        }
         if (!kUnpol && started) {
-            // merged N half-steps from the previous sample to this one
+            // merged N half-steps from the previous sample to this one (to the camera node on
+            // the finishing iteration, where the far half is empty)
             T A0[4][4], A1[4][4];
             const T kp[4] = {kt, prev[3], prev[4], prev[5]};
             const T kn[4] = {kt, prev[9], prev[10], prev[11]};
             transport_matrix<T>(prev, kp, a, m, flat, A0);
             transport_matrix<T>(prev + 6, kn, a, m, flat, A1);
-            coh_pc_step(N, A0, A1, T(0.5) * (prev[12] + cur[12]));
+            coh_pc_step(N, A0, A1, T(0.5) * (prev[12] + (finishing ? T(0) : cur[12])));
+        }
+        if (finishing) {
+            const int64_t npix = im.n_rays;
+            T sv[4] = {Iu, T(0), T(0), T(0)};
+            if constexpr (!kUnpol) {
+                // read out in the camera basis at the camera-side node
+                KSGeom<T> G;
+                ks_geom<T>(prev[6], prev[7], prev[8], a, m, flat, false, G);
+                T hv[4], vv[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if constexpr (std::is_same<T, float>::value) { hv[c] = im.f_hh[c]; vv[c] = im.f_vv[c]; }
+                    else { hv[c] = im.hh[c]; vv[c] = im.vv[c]; }
+                }
+                T hl[4], vl[4];
+                lower4(G, hv, hl);
+                lower4(G, vv, vl);
+                coh_to_stokes(N, hl, vl, sv);
+            }
+            for (int c = 0; c < 4; ++c) {
+                if (im.dtype == 0) ((double*)im.stokes)[c * npix + opix] = (double)sv[c];
+                else ((float*)im.stokes)[c * npix + opix] = (float)sv[c];
+            }
+            if constexpr (kAux) if (im.aux) aux_finish(im, opix, AX);
+            active = false;
+            continue;
         }
         {
             const T xs[3] = {cur[0], cur[1], cur[2]};
@@ -1604,50 +1641,8 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
 #pragma unroll
         for (int c = 0; c < kRecVals; ++c) prev[c] = cur[c];
         --idx;
-        if (idx < 0 && kUnpol) {
-            const int64_t npix = im.n_rays;
-            const T sv[4] = {Iu, T(0), T(0), T(0)};
-            for (int c = 0; c < 4; ++c) {
-                if (im.dtype == 0) ((double*)im.stokes)[c * npix + opix] = (double)sv[c];
-                else ((float*)im.stokes)[c * npix + opix] = (float)sv[c];
-            }
-            if constexpr (kAux) if (im.aux) aux_finish(im, opix, AX);
-            active = false;
-        } else if (idx < 0) {
-            // last half-step to the camera node, then read out in the camera basis
-            if (started) {
-                T A0[4][4], A1[4][4];
-                const T kp[4] = {kt, prev[3], prev[4], prev[5]};
-                const T kn[4] = {kt, prev[9], prev[10], prev[11]};
-                transport_matrix<T>(prev, kp, a, m, flat, A0);
-                transport_matrix<T>(prev + 6, kn, a, m, flat, A1);
-                coh_pc_step(N, A0, A1, T(0.5) * prev[12]);
-            }
-            KSGeom<T> G;
-            ks_geom<T>(prev[6], prev[7], prev[8], a, m, flat, false, G);
-            T hv[4], vv[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if constexpr (std::is_same<T, float>::value) { hv[c] = im.f_hh[c]; vv[c] = im.f_vv[c]; }
-                else { hv[c] = im.hh[c]; vv[c] = im.vv[c]; }
-            }
-            T hl[4], vl[4];
-            lower4(G, hv, hl);
-            lower4(G, vv, vl);
-            T s[4];
-            coh_to_stokes(N, hl, vl, s);
-            const int64_t npix = im.n_rays;
-            const int64_t pix = opix;
-            for (int c = 0; c < 4; ++c) {
-                if (im.dtype == 0) ((double*)im.stokes)[c * npix + pix] = (double)s[c];
-                else ((float*)im.stokes)[c * npix + pix] = (float)s[c];
-            }
-            if constexpr (kAux) if (im.aux) aux_finish(im, pix, AX);
-            active = false;
-        }
     }
 }
-
 // ---------------------------------------------------------------------------------------
 // Transfer with the learned coefficient model (FP32). The same per-sample work as
 // transfer_kernel, but the loop runs in lockstep across the CTA: every iteration each of the
