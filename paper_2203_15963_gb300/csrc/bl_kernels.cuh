@@ -1723,19 +1723,45 @@ __global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __re
         KSGeom<T> G;
         Plasma<T> P;
         T kl[4], ku[4], kdu = T(0), nu_fl = T(0), cth = T(0);
+        // idx < 0: every sample is in; this iteration takes the last half-step to the camera
+        // node and reads the pixel out (its row of the tile is masked)
+        const bool finishing = work && idx < 0;
+        T ts = T(0);   // the sample's coordinate time
         if (work) {
+            if (!finishing) {
 #pragma unroll
-            for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
-            const T ts = (T)nxt[13];   // the sample's coordinate time
-            if (idx > 0) load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
+                for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
+                ts = (T)nxt[13];
+                if (idx > 0) load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
+            }
             if (started) {
                 T A0[4][4], A1[4][4];
                 const T kp[4] = {kt, prev[3], prev[4], prev[5]};
                 const T kn[4] = {kt, prev[9], prev[10], prev[11]};
                 transport_matrix<T>(prev, kp, a, m, flat, A0);
                 transport_matrix<T>(prev + 6, kn, a, m, flat, A1);
-                coh_pc_step(N, A0, A1, T(0.5) * (prev[12] + cur[12]));
+                coh_pc_step(N, A0, A1, T(0.5) * (prev[12] + (finishing ? T(0) : cur[12])));
             }
+            if (finishing) {
+                KSGeom<T> Gc;
+                ks_geom<T>(prev[6], prev[7], prev[8], a, m, flat, false, Gc);
+                T hv[4], vv[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) { hv[c] = im.f_hh[c]; vv[c] = im.f_vv[c]; }
+                T hl[4], vl[4];
+                lower4(Gc, hv, hl);
+                lower4(Gc, vv, vl);
+                T st[4];
+                coh_to_stokes(N, hl, vl, st);
+                const int64_t npix = im.n_rays;
+                for (int c = 0; c < 4; ++c) {
+                    if (im.dtype == 0) ((double*)im.stokes)[c * npix + opix] = (double)st[c];
+                    else ((float*)im.stokes)[c * npix + opix] = (float)st[c];
+                }
+                active = false;
+            }
+        }
+        if (work && !finishing) {
             const T xs[3] = {cur[0], cur[1], cur[2]};
             ks_geom<T>(xs[0], xs[1], xs[2], a, m, flat, false, G);
             samp = plasma_at<T, kSlow>(im, xs, ts, G, P);
@@ -1774,36 +1800,10 @@ __global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __re
             stokes_to_coh(e1, e2, s1, N);
             started = true;
         }
-        if (!work) continue;
+        if (!work || finishing) continue;
 #pragma unroll
         for (int c = 0; c < kRecVals; ++c) prev[c] = cur[c];
         --idx;
-        if (idx < 0) {
-            if (started) {
-                T A0[4][4], A1[4][4];
-                const T kp[4] = {kt, prev[3], prev[4], prev[5]};
-                const T kn[4] = {kt, prev[9], prev[10], prev[11]};
-                transport_matrix<T>(prev, kp, a, m, flat, A0);
-                transport_matrix<T>(prev + 6, kn, a, m, flat, A1);
-                coh_pc_step(N, A0, A1, T(0.5) * prev[12]);
-            }
-            KSGeom<T> Gc;
-            ks_geom<T>(prev[6], prev[7], prev[8], a, m, flat, false, Gc);
-            T hv[4], vv[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) { hv[c] = im.f_hh[c]; vv[c] = im.f_vv[c]; }
-            T hl[4], vl[4];
-            lower4(Gc, hv, hl);
-            lower4(Gc, vv, vl);
-            T st[4];
-            coh_to_stokes(N, hl, vl, st);
-            const int64_t npix = im.n_rays;
-            for (int c = 0; c < 4; ++c) {
-                if (im.dtype == 0) ((double*)im.stokes)[c * npix + opix] = (double)st[c];
-                else ((float*)im.stokes)[c * npix + opix] = (float)st[c];
-            }
-            active = false;
-        }
     }
     if (!tc_ok && threadIdx.x == 0) atomicAdd(&ctr->mlp_timeouts, 1ull);
     mlp::fwd_finish(S, phase, tc_ok);
