@@ -415,6 +415,36 @@ __device__ __forceinline__ void stokes_step(const T c[8], const T s0[4], T dl, T
     }
     // Taylor degree: ||Z|| <= 1/2, truncation 2^-(m+1)/(m+1)! below the type's rounding.
     constexpr int m = sizeof(T) == 8 ? 13 : 8;
+    if (s <= 1) {
+        // Only the action on [s0; 1] is needed: with A = [Z z; 0 0] (scaled), exp(A) x is
+        // x + A (x + A/2 (x + ... (x + A x / m))), the last component staying 1, so each term
+        // is one 4x4 matrix-vector product (16 FMAs) instead of a matrix product (64). The
+        // scaled map is applied 2^s times (at most twice) in place of the squarings.
+        T v[4] = {s0[0], s0[1], s0[2], s0[3]};
+#pragma unroll 1
+        for (int rep = 0; rep < (1 << s); ++rep) {
+            T t[4] = {v[0], v[1], v[2], v[3]};
+#pragma unroll
+            for (int k = m; k >= 1; --k) {
+                const T ik = T(1) / T(k);
+                T tn[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    T acc = z[i];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc += Z[i][q] * t[q];
+                    tn[i] = v[i] + acc * ik;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) t[i] = tn[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = t[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) s1[i] = v[i];
+        return;
+    }
     // E = I + Z (I + Z/2 (I + Z/3 (...))),  t = (I + Z/2 (I + Z/3 (...))) z  (phi_1(Z) z)
     T E[4][4], tv[4];
 #pragma unroll
