@@ -733,14 +733,31 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
         } else if (eps <= 1.0) {
             // accepted: samples of this step (camera side first)
             if (record) {
+                // FP32 records (fast and mixed forms): the midpoint's increment
+                // (h/2) sum_j b_mid,j k_j and the quartic coefficients are formed in FP32 from the
+                // state; they move a record by about one FP32 ulp and leave the integration and
+                // its step decisions untouched. FP64 records (FP64 form): all in double.
+                constexpr bool kFRec = sizeof(R) == sizeof(float);
                 G ym[8];
+                float ymf[8], incm[8];
+                if constexpr (kFRec) {
+                    const float hh = 0.5f * A::tof(h);
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
-                {
-                    G acc = DPCoef<G>::m(0) * KX(0, c);
+                    for (int c = 0; c < 8; ++c) {
+                        float acc = c_dpf.m[0].x * A::tof(KX(0, c));
 #pragma unroll 1
-                    for (int j = 2; j < 7; ++j) acc = acc + DPCoef<G>::m(j) * KX(j, c);
-                    ym[c] = y[c] + (kHalf * h) * acc;
+                        for (int j = 2; j < 7; ++j) acc = fmaf(c_dpf.m[j].x, A::tof(KX(j, c)), acc);
+                        incm[c] = hh * acc;
+                        if constexpr (!kNative) ymf[c] = y[c].hi + (y[c].lo + incm[c]);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        G acc = DPCoef<G>::m(0) * KX(0, c);
+#pragma unroll 1
+                        for (int j = 2; j < 7; ++j) acc = acc + DPCoef<G>::m(j) * KX(j, c);
+                        ym[c] = y[c] + (kHalf * h) * acc;
+                    }
                 }
                 const double r0 = r_cur, r1 = r5;
                 const double hd = kNative ? A::to(h) : (double)A::tof(h);
@@ -748,7 +765,14 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                 if constexpr (kNative) {
                     double ymd[8];
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) ymd[c] = A::to(ym[c]);
+                    for (int c = 0; c < 8; ++c) {
+                        if constexpr (kFRec) {
+                            ymd[c] = A::to(y[c]) + (double)incm[c];
+                            ymf[c] = (float)ymd[c];
+                        } else {
+                            ymd[c] = A::to(ym[c]);
+                        }
+                    }
                     KSGeom<double> Gm;
                     ks_geom<double>(ymd[1], ymd[2], ymd[3], im_spin(imgs, q), im_mass(imgs, q), flat, false, Gm);
                     const double L = -ymd[4] + Gm.l[1] * ymd[5] + Gm.l[2] * ymd[6] + Gm.l[3] * ymd[7];
@@ -756,9 +780,6 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                     rmid = Gm.r;
                     fmid = Gm.f;
                 } else {
-                    float ymf[8];
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) ymf[c] = A::tof(ym[c]);
                     KSGeom<float> Gm;
                     ks_geom<float>(ymf[1], ymf[2], ymf[3], (float)im_spin(imgs, q), (float)im_mass(imgs, q),
                                    flat, false, Gm);
@@ -791,22 +812,30 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                 }
                 bool ok = true;
                 if (nsub == 1) {
-                    ok = append_record(sink, wray, nrec, ym, y, fabs(hd));
-                } else if (sizeof(R) == sizeof(float)) {
+                    if constexpr (kFRec) {
+                        float yf[8];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) yf[c] = A::tof(y[c]);
+                        ok = append_record(sink, wray, nrec, ymf, yf, fabs(hd));
+                    } else {
+                        ok = append_record(sink, wray, nrec, ym, y, fabs(hd));
+                    }
+                } else if constexpr (kFRec) {
                     // float records: the quartic through y0, y1, h f0, h f1 and y_mid
-                    // (Shampine 1986), evaluated in FP32 about y0
+                    // (Shampine 1986), in FP32 about y0 (y_mid - y0 is the midpoint increment)
+                    const float hf = A::tof(h);
                     float y0f[8], d0f[8], c2f[8], c3f[8], c4f[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        const G d0 = h * KX(0, c);
-                        const G D1 = y5[c] - y[c] - d0;
-                        const G D2 = h * KX(6, c) - d0;
-                        const G D3 = ym[c] - y[c] - kHalf * d0;
+                        const float d0 = hf * A::tof(KX(0, c));
+                        const float D1 = A::tof(y5[c] - y[c]) - d0;
+                        const float D2 = hf * A::tof(KX(6, c)) - d0;
+                        const float D3 = incm[c] - 0.5f * d0;
                         y0f[c] = A::tof(y[c]);
-                        d0f[c] = A::tof(d0);
-                        c2f[c] = A::tof(kM5 * D1 + D2 + k16 * D3);
-                        c3f[c] = A::tof(k14 * D1 - kThree * D2 - k32 * D3);
-                        c4f[c] = A::tof(kM8 * D1 + k2c * D2 + k16 * D3);
+                        d0f[c] = d0;
+                        c2f[c] = -5.0f * D1 + D2 + 16.0f * D3;
+                        c3f[c] = 14.0f * D1 - 3.0f * D2 - 32.0f * D3;
+                        c4f[c] = -8.0f * D1 + 2.0f * D2 + 16.0f * D3;
                     }
                     ok = emit_quartic_f(sink, wray, nrec, y0f, d0f, c2f, c3f, c4f, nsub, fabs(hd));
                 } else {
