@@ -87,6 +87,36 @@ __device__ __forceinline__ df64 sqrt(const df64& x) {
     if (x.hi <= 0.0f) return df64(0.0f, 0.0f);
     return x * rsqrt(x);
 }
+// Dot product sum_j a_j x_j of double-float operands without renormalising after each term:
+// the high parts of the products are added with TwoSum, and every rounding error and low-order
+// cross product goes into one float; one Fast2Sum at the end returns the double-float result.
+// This is the compensated dot product Dot2 of Ogita, Rump & Oishi (2005, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26, Algorithm 5.3) with the operands' low words folded into the
+// error term; its error is of order eps^2 sum_j |a_j x_j|, as for sums of double-float
+// products, in 12 FP32 instructions a term instead of 18. The rounded product and the TwoSum
+// use the _rn intrinsics, which the compiler never fuses into an FMA.
+struct DFDot {
+    float s, c;
+    __device__ __forceinline__ void first(const df64& a, const df64& x) {
+        s = __fmul_rn(a.hi, x.hi);
+        c = fmaf(a.hi, x.hi, -s);
+        c = fmaf(a.hi, x.lo, c);
+        c = fmaf(a.lo, x.hi, c);
+    }
+    __device__ __forceinline__ void add(const df64& a, const df64& x) {
+        const float p = __fmul_rn(a.hi, x.hi);
+        float q = fmaf(a.hi, x.hi, -p);
+        q = fmaf(a.hi, x.lo, q);
+        q = fmaf(a.lo, x.hi, q);
+        const float t = __fadd_rn(s, p);
+        const float z = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+        s = t;
+        c += e + q;
+    }
+    __device__ __forceinline__ df64 get() const { return df_fast_two_sum(s, c); }
+};
+
 __device__ __forceinline__ df64& operator+=(df64& x, const df64& y) { x = x + y; return x; }
 __device__ __forceinline__ df64& operator-=(df64& x, const df64& y) { x = x - y; return x; }
 __device__ __forceinline__ df64& operator*=(df64& x, const df64& y) { x = x * y; return x; }

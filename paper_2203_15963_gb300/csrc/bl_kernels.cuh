@@ -454,6 +454,22 @@ template <> struct DPCoef<df64> {
     static __device__ __forceinline__ df64 m(int j) { const float2 v = c_dpf.m[j]; return df64(v.x, v.y); }
 };
 
+// Accumulator of a sum of coefficient x stage-derivative products in the integrator
+// arithmetic: the compensated double-float dot product, or plain (fused) double.
+template <class G> struct StageDot;
+template <> struct StageDot<double> {
+    double s;
+    __device__ __forceinline__ void first(double a, double x) { s = a * x; }
+    __device__ __forceinline__ void add(double a, double x) { s = s + a * x; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct StageDot<df64> {
+    DFDot d;
+    __device__ __forceinline__ void first(const df64& a, const df64& x) { d.first(a, x); }
+    __device__ __forceinline__ void add(const df64& a, const df64& x) { d.add(a, x); }
+    __device__ __forceinline__ df64 get() const { return d.get(); }
+};
+
 template <class R, class G>
 __device__ __forceinline__ R to_rec(const G& v) {
     if constexpr (sizeof(R) == sizeof(float)) return (R)GeoArith<G>::tof(v);
@@ -668,10 +684,11 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
             } else {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    G acc = DPCoef<G>::a(st, 0) * KX(0, c);
+                    StageDot<G> acc;
+                    acc.first(DPCoef<G>::a(st, 0), KX(0, c));
 #pragma unroll 1
-                    for (int j = 1; j < st; ++j) acc = acc + DPCoef<G>::a(st, j) * KX(j, c);
-                    ys[c] = y[c] + h * acc;
+                    for (int j = 1; j < st; ++j) acc.add(DPCoef<G>::a(st, j), KX(j, c));
+                    ys[c] = y[c] + h * acc.get();
                 }
             }
             G fs[8];
@@ -697,10 +714,11 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
             G errv[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                G acc = DPCoef<G>::e(0) * KX(0, c);
+                StageDot<G> acc;
+                acc.first(DPCoef<G>::e(0), KX(0, c));
 #pragma unroll 1
-                for (int j = 2; j < 7; ++j) acc = acc + DPCoef<G>::e(j) * KX(j, c);
-                errv[c] = h * acc;
+                for (int j = 2; j < 7; ++j) acc.add(DPCoef<G>::e(j), KX(j, c));
+                errv[c] = h * acc.get();
             }
             if constexpr (kNative) {
                 double num = 0.0, den = 1.0;
