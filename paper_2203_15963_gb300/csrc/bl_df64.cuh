@@ -115,7 +115,22 @@ struct DFDot {
         c += e + q;
     }
     __device__ __forceinline__ df64 get() const { return df_fast_two_sum(s, c); }
+    // y + h (s + c) in one pass (no renormalisation of the sum first): the product's high part
+    // enters a TwoSum with y.hi, everything else the low word, one Fast2Sum at the end
+    __device__ __forceinline__ df64 axpy(const df64& h, const df64& y) const {
+        const float p = __fmul_rn(h.hi, s);
+        float q = fmaf(h.hi, s, -p);
+        q = fmaf(h.hi, c, q);
+        q = fmaf(h.lo, s, q);
+        const float t = __fadd_rn(y.hi, p);
+        const float z = __fsub_rn(t, y.hi);
+        const float e = __fadd_rn(__fsub_rn(y.hi, __fsub_rn(t, z)), __fsub_rn(p, z));
+        return df_fast_two_sum(t, y.lo + q + e);
+    }
 };
+
+// x 2^k for a double-float x: exact, both words scaled (k a small integer power of two in f)
+__device__ __forceinline__ df64 df_scale(const df64& x, float f) { return df64(x.hi * f, x.lo * f); }
 
 __device__ __forceinline__ df64& operator+=(df64& x, const df64& y) { x = x + y; return x; }
 __device__ __forceinline__ df64& operator-=(df64& x, const df64& y) { x = x - y; return x; }

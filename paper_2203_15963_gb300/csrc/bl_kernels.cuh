@@ -389,6 +389,10 @@ template <> struct GeoArith<df64> {
     static __device__ __forceinline__ float tof(const df64& g) { return g.hi + g.lo; }
 };
 
+// Exact scaling by a power of two in the integrator arithmetic.
+__device__ __forceinline__ double scale2(double x, float f) { return x * (double)f; }
+__device__ __forceinline__ df64 scale2(const df64& x, float f) { return df_scale(x, f); }
+
 // Eq. (geodesic) right-hand side in arithmetic G; returns r at the evaluation point.
 // With g^ab = eta^ab - f l^a l^b and L = l^a k_a, dx^a/dl = g^ab k_b and
 // dk_c/dl = L (1/2 d_c f L + f d_c L), where d_c L is the derivative at fixed k. Instead of the
@@ -401,23 +405,24 @@ template <> struct GeoArith<df64> {
 // The same quantities as the nine-derivative form, in about 40 fewer operations.
 template <class G>
 __device__ __forceinline__ G geodesic_rhs_g(const G y[8], const G& a, const G& m, bool flat, G dy[8]) {
-    constexpr G c0 = G(0), c2 = G(2), c3 = G(3), c4 = G(4), cHalf = G(0.5), c1 = G(1);
+    constexpr G c0 = G(0), c3 = G(3), c1 = G(1);
     const G x = y[1], yy = y[2], z = y[3];
     const G kt = y[4], kx = y[5], ky = y[6], kz = y[7];
     // r (Eq. cks_aux:r), f and l as in ks_geom: two reciprocal square roots, one reciprocal
     const G aa = a * a;
     const G q = x * x + yy * yy + z * z - aa;
-    const G D2 = q * q + c4 * aa * z * z;
+    const G aaz2 = aa * z * z;
+    const G D2 = q * q + scale2(aaz2, 4.0f);
     const G iD = rsqrt(D2);
-    const G r2 = cHalf * (q + D2 * iD);
+    const G r2 = scale2(q + D2 * iD, 0.5f);
     const G ir = rsqrt(r2);
     const G r = r2 * ir;
-    const G s4 = r2 * r2 + aa * z * z;
+    const G s4 = r2 * r2 + aaz2;
     const G P = r2 + aa;
     const G iPs = c1 / (P * s4);
     const G is4 = P * iPs;
     const G iP = s4 * iPs;
-    const G f = flat ? c0 : c2 * m * r * r2 * is4;
+    const G f = flat ? c0 : scale2(m, 2.0f) * r * r2 * is4;
     const G lx = (r * x + a * yy) * iP, ly = (r * yy - a * x) * iP, lz = z * ir;
     // L = l^a k_a (l^t = -1)
     const G A_ = x * kx + yy * ky;
@@ -434,14 +439,14 @@ __device__ __forceinline__ G geodesic_rhs_g(const G y[8], const G& a, const G& m
     const G riD = r * iD;
     const G drx = riD * x, dry = riD * yy, drz = z * P * ir * iD;
     // d_c L at fixed k, and d_c f
-    const G V = (A_ - c2 * r * Lxy) * iP - kz * ir * lz;
+    const G V = (A_ - scale2(r, 2.0f) * Lxy) * iP - kz * ir * lz;
     const G Sx = drx * V + (r * kx - a * ky) * iP;
     const G Sy = dry * V + (r * ky + a * kx) * iP;
     const G Sz = drz * V + kz * ir;
-    const G F1 = f * (c3 * ir - c4 * r2 * r * is4);
+    const G F1 = f * (c3 * ir - scale2(r2, 4.0f) * r * is4);
     const G dfx = F1 * drx, dfy = F1 * dry;
-    const G dfz = F1 * drz - c2 * aa * z * f * is4;
-    const G halfL = cHalf * L;
+    const G dfz = F1 * drz - scale2(aa, 2.0f) * z * f * is4;
+    const G halfL = scale2(L, 0.5f);
     dy[5] = L * (dfx * halfL + f * Sx);
     dy[6] = L * (dfy * halfL + f * Sy);
     dy[7] = L * (dfz * halfL + f * Sz);
@@ -462,13 +467,16 @@ template <> struct StageDot<double> {
     __device__ __forceinline__ void first(double a, double x) { s = a * x; }
     __device__ __forceinline__ void add(double a, double x) { s = s + a * x; }
     __device__ __forceinline__ double get() const { return s; }
+    __device__ __forceinline__ double axpy(double h, double y) const { return y + h * s; }
 };
 template <> struct StageDot<df64> {
     DFDot d;
     __device__ __forceinline__ void first(const df64& a, const df64& x) { d.first(a, x); }
     __device__ __forceinline__ void add(const df64& a, const df64& x) { d.add(a, x); }
     __device__ __forceinline__ df64 get() const { return d.get(); }
+    __device__ __forceinline__ df64 axpy(const df64& h, const df64& y) const { return d.axpy(h, y); }
 };
+
 
 template <class R, class G>
 __device__ __forceinline__ R to_rec(const G& v) {
@@ -688,7 +696,7 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                     acc.first(DPCoef<G>::a(st, 0), KX(0, c));
 #pragma unroll 1
                     for (int j = 1; j < st; ++j) acc.add(DPCoef<G>::a(st, j), KX(j, c));
-                    ys[c] = y[c] + h * acc.get();
+                    ys[c] = acc.axpy(h, y[c]);
                 }
             }
             G fs[8];
