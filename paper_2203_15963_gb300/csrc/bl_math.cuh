@@ -136,53 +136,85 @@ __device__ __forceinline__ double geodesic_rhs(const double y[8], double a, doub
 // contraction is C_ed = k^c Gamma_ecd = 1/2 (D_ed + P_de - P_ed) with
 //   D_ed = k^c d_c g_ed,  P_me = d_m g_ec k^c,  and A = -g^{-1} C.
 // ---------------------------------------------------------------------------------------
+// The needed contractions are formed directly from r, f and l (no 3x3 table d_c l_b):
+//   k.grad r, d_c f = F1 d_c r - [c = z] 2 a^2 z f / s4 with F1 = f (3 / r - 4 r^3 / s4),
+//   kdl_e = k^c d_c l_e, M_m = d_m (l_c) k^c (fixed k), the curl Q_de = d_d l_e - d_e l_d,
+// D is symmetric and W_ed = P_de - P_ed antisymmetric, so C_ed = (D_ed + W_ed) / 2 and
+// C_de = (D_ed - W_ed) / 2 from the 10 + 6 independent entries.
 template <class T>
-__device__ __forceinline__ void transport_matrix(const T x[3], const T klo[4], T a, T m,
+__device__ __forceinline__ void transport_matrix(const T xv[3], const T klo[4], T a, T m,
                                                  bool flat, T A[4][4]) {
-    KSGeom<T> G;
-    ks_geom<T>(x[0], x[1], x[2], a, m, flat, true, G);
-    T ku[4];
-    raise4(G, klo, ku);
-    const T* l = G.l;
-    T kdf = ku[1] * G.df[0] + ku[2] * G.df[1] + ku[3] * G.df[2];
-    T kdl[4];
-    kdl[0] = T(0);
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-        kdl[b + 1] = ku[1] * G.dl[0][b] + ku[2] * G.dl[1][b] + ku[3] * G.dl[2][b];
-    const T Lp = ku[0] * l[0] + ku[1] * l[1] + ku[2] * l[2] + ku[3] * l[3];   // l_c k^c
-    T Mv[4];
-    Mv[0] = T(0);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) Mv[c + 1] = G.dl[c][0] * ku[1] + G.dl[c][1] * ku[2] + G.dl[c][2] * ku[3];
-    // P[m][e] = d_m f l_e Lp + f (d_m l_e Lp + l_e M_m), zero for m = t.
-    T P[4][4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) P[0][e] = T(0);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const T dle = (e == 0) ? T(0) : G.dl[c][e - 1];
-            P[c + 1][e] = G.df[c] * l[e] * Lp + G.f * (dle * Lp + l[e] * Mv[c + 1]);
-        }
-    }
+    constexpr T c0 = T(0), c1 = T(1), c2 = T(2), c3 = T(3), c4 = T(4), cHalf = T(0.5);
+    const T x = xv[0], y = xv[1], z = xv[2];
+    const T aa = a * a;
+    const T q = x * x + y * y + z * z - aa;
+    const T aaz2 = aa * z * z;
+    const T D2 = q * q + c4 * aaz2;
+    const T iD = rsqrt(D2);
+    const T r2 = cHalf * (q + D2 * iD);
+    const T ir = rsqrt(r2);
+    const T r = r2 * ir;
+    const T s4 = r2 * r2 + aaz2;
+    const T P = r2 + aa;
+    const T iPs = c1 / (P * s4);
+    const T is4 = P * iPs;
+    const T iP = s4 * iPs;
+    const T f = flat ? c0 : c2 * m * r * r2 * is4;
+    const T lx = (r * x + a * y) * iP, ly = (r * y - a * x) * iP, lz = z * ir;
+    // k^a = g^ab k_b
+    const T lw = -klo[0] + lx * klo[1] + ly * klo[2] + lz * klo[3];
+    const T kt = -klo[0] + f * lw, kx = klo[1] - f * lx * lw, ky = klo[2] - f * ly * lw,
+            kz = klo[3] - f * lz * lw;
+    // d_c r, k.grad r, d_c f
+    const T riD = r * iD;
+    const T drx = riD * x, dry = riD * y, drz = z * P * ir * iD;
+    const T kdr = kx * drx + ky * dry + kz * drz;
+    const T F1 = f * (c3 * ir - c4 * r2 * r * is4);
+    const T fz = c2 * aa * z * f * is4;
+    const T df[4] = {c0, F1 * drx, F1 * dry, F1 * drz - fz};
+    const T kdf = F1 * kdr - kz * fz;
+    const T t2 = c2 * r * iP;
+    // kdl_e = k^c d_c l_e (l_t constant)
+    const T kdl[4] = {c0, (kdr * x + r * kx + a * ky) * iP - t2 * kdr * lx,
+                      (kdr * y + r * ky - a * kx) * iP - t2 * kdr * ly, (kz - lz * kdr) * ir};
+    const T l[4] = {c1, lx, ly, lz};
+    const T Lp = kt + lx * kx + ly * ky + lz * kz;       // l_c k^c
+    // M_m = d_m (l_c) k^c at fixed k: with A' = x k^x + y k^y, B' = y k^x - x k^y
+    const T Ap = x * kx + y * ky, Bp = y * kx - x * ky;
+    const T Lxy = (r * Ap + a * Bp) * iP;
+    const T V = (Ap - c2 * r * Lxy) * iP - kz * ir * lz;
+    const T M[4] = {c0, drx * V + (r * kx - a * ky) * iP, dry * V + (r * ky + a * kx) * iP,
+                    drz * V + kz * ir};
+    // curl of l: Q_xy = d_x l_y - d_y l_x, Q_xz, Q_yz
+    const T Qxy = -c2 * a * iP - t2 * (drx * ly - dry * lx);
+    const T Qxz = -lz * drx * ir - drz * x * iP + t2 * drz * lx;
+    const T Qyz = -lz * dry * ir - drz * y * iP + t2 * drz * ly;
+    const T fLp = f * Lp;
     T C[4][4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
+    for (int e = 0; e < 4; ++e) {
 #pragma unroll
-        for (int d = 0; d < 4; ++d) {
-            const T De = kdf * l[e] * l[d] + G.f * (kdl[e] * l[d] + l[e] * kdl[d]);
-            C[e][d] = T(0.5) * (De + P[d][e] - P[e][d]);
+        for (int d = e; d < 4; ++d) {
+            const T Ded = kdf * l[e] * l[d] + f * (kdl[e] * l[d] + l[e] * kdl[d]);
+            // Q_de = d_d l_e - d_e l_d (zero with a time index)
+            T Qde = c0;
+            if (e == 1 && d == 2) Qde = -Qxy;
+            if (e == 1 && d == 3) Qde = -Qxz;
+            if (e == 2 && d == 3) Qde = -Qyz;
+            const T Wed = Lp * (df[d] * l[e] - df[e] * l[d]) + fLp * Qde +
+                          f * (l[e] * M[d] - l[d] * M[e]);
+            C[e][d] = cHalf * (Ded + Wed);
+            C[d][e] = cHalf * (Ded - Wed);
         }
-    // A = -g^{-1} C with g^{ae} = eta^{ae} - f l^a l^e, l^a = (-1, l1, l2, l3).
-    const T lu[4] = {-l[0], l[1], l[2], l[3]};
+    }
+    // A = -g^{-1} C with g^{ae} = eta^{ae} - f l^a l^e, l^a = (-1, l1, l2, l3)
+    const T lu[4] = {-c1, lx, ly, lz};
 #pragma unroll
     for (int d = 0; d < 4; ++d) {
         const T lc = lu[0] * C[0][d] + lu[1] * C[1][d] + lu[2] * C[2][d] + lu[3] * C[3][d];
-        A[0][d] = -(-C[0][d] - G.f * lu[0] * lc);
+        A[0][d] = C[0][d] + f * lu[0] * lc;
 #pragma unroll
-        for (int e = 1; e < 4; ++e) A[e][d] = -(C[e][d] - G.f * lu[e] * lc);
+        for (int e = 1; e < 4; ++e) A[e][d] = -C[e][d] + f * lu[e] * lc;
     }
 }
 
