@@ -9,8 +9,9 @@
 //   double-length addition (Dekker 1971) and the FMA product of double-words (Joldes,
 //   Muller & Popescu 2017, "Tight and rigorous error bounds for basic building blocks of
 //   double-word arithmetic", structure of their Alg. 12);
-//   1/x and 1/sqrt(x): one Newton step in df64 from the float approximation, which doubles
-//   the number of correct bits.
+//   1/x and 1/sqrt(x): a Newton step to second order from the correctly rounded float value,
+//   with the residual formed exactly by FMAs (the refinement used for double-word
+//   reciprocals, e.g. in Hida, Li & Bailey's QD library).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -70,18 +71,29 @@ __device__ __forceinline__ df64 df_mul_f(const df64& x, float b) {
     p.lo = fmaf(x.lo, b, p.lo);
     return df_fast_two_sum(p.hi, p.lo);
 }
+// 1/x: correctly rounded FP32 seed y0, residual e = 1 - x y0 (|e| <= 2^-24) formed with FMAs
+// (the product x.hi y0 is exact inside the first one), then 1/x = y0 / (1 - e) =
+// y0 (1 + e + e^2 + ...) to second order; relative error ~1e-14 (2^-46.5).
 __device__ __forceinline__ df64 rcp(const df64& x) {
-    const float y0 = __fdividef(1.0f, x.hi);   // ~2 ulp seed; the Newton step below refines it
-    // y1 = y0 + y0 (1 - x y0)
-    const df64 r = df64(1.0f, 0.0f) - df_mul_f(x, y0);
-    return df64(y0, 0.0f) + df_mul_f(r, y0);
+    const float y0 = __frcp_rn(x.hi);
+    float e = fmaf(-x.hi, y0, 1.0f);
+    e = fmaf(-x.lo, y0, e);
+    const float t = fmaf(e, e, e);
+    return df_fast_two_sum(y0, __fmul_rn(y0, t));
 }
 __device__ __forceinline__ df64 operator/(const df64& x, const df64& y) { return x * rcp(y); }
+// 1/sqrt(x): correctly rounded FP32 seed y0, residual u = x y0^2 - 1 formed with an exact
+// product (p + ep = x.hi y0) and FMAs, then 1/sqrt(x) = y0 (1 + u)^(-1/2) =
+// y0 (1 - u/2 + 3 u^2 / 8 - ...) to second order; relative error ~1e-14.
 __device__ __forceinline__ df64 rsqrt(const df64& x) {
-    const float y0 = rsqrtf(x.hi);
-    // y1 = y0 + y0 (1 - x y0^2) / 2
-    const df64 r = df64(1.0f, 0.0f) - df_mul_f(df_mul_f(x, y0), y0);
-    return df64(y0, 0.0f) + df_mul_f(r, 0.5f * y0);
+    const float y0 = __frsqrt_rn(x.hi);
+    const float p = __fmul_rn(x.hi, y0);
+    const float ep = fmaf(x.hi, y0, -p);
+    float u = fmaf(p, y0, -1.0f);
+    u = fmaf(ep, y0, u);
+    u = fmaf(x.lo * y0, y0, u);
+    const float t = u * fmaf(0.375f, u, -0.5f);
+    return df_fast_two_sum(y0, __fmul_rn(y0, t));
 }
 __device__ __forceinline__ df64 sqrt(const df64& x) {
     if (x.hi <= 0.0f) return df64(0.0f, 0.0f);
