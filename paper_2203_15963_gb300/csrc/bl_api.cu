@@ -259,9 +259,9 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
     d.n_rays = (int64_t)c.n * c.n;
 }
 
-// Dynamic shared memory of a geodesic-kernel CTA: the stage derivatives, 7 x 8 values of 8
-// bytes for each of its 128 threads.
-constexpr size_t kGeoSmem = BL_GEO_K_SMEM ? (size_t)7 * 8 * 128 * 8 : 0;
+// Dynamic shared memory of a geodesic-kernel CTA: the stage derivatives, 7 stages x 7
+// components (k_t's are zero) of 8 bytes for each of its 128 threads.
+constexpr size_t kGeoSmem = BL_GEO_K_SMEM ? (size_t)7 * 7 * 128 * 8 : 0;
 
 struct DevInfo {
     int sms = 0;

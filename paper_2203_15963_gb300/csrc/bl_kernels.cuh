@@ -617,14 +617,18 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
     // K(0, c) = f(y); K(1..6, c) stage derivatives of the current attempt. In shared memory
     // (thread-fastest, conflict-free): 448 B a thread, which as a local array would take 172 KB
     // of L1 per SM and miss to L2.
+    // The k_t component is constant along the ray (dk_t/dl = 0), so its derivatives are not
+    // stored: 7 slots a stage, and KR(j, 4) reads as an exact zero.
+#define KSLOT(c) ((c) < 4 ? (c) : (c) - 1)
 #if BL_GEO_K_SMEM
     extern __shared__ __align__(16) unsigned char geo_smem[];
     G* const Kt = reinterpret_cast<G*>(geo_smem) + threadIdx.x;
-#define KX(j, c) Kt[((j) * 8 + (c)) * 128]
+#define KX(j, c) Kt[((j) * 7 + KSLOT(c)) * 128]
 #else
-    G Kl[7][8];
-#define KX(j, c) Kl[j][c]
+    G Kl[7][7];
+#define KX(j, c) Kl[j][KSLOT(c)]
 #endif
+#define KR(j, c) ((c) == 4 ? G(0) : KX(j, c))
     G h = G(0);
     double nnorm = 0.0;
     bool been_inside = false, prev_rej = false;
@@ -692,6 +696,7 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
             } else {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
+                    if (c == 4) { ys[4] = y[4]; continue; }
                     StageDot<G> acc;
                     acc.first(DPCoef<G>::a(st, 0), KX(0, c));
 #pragma unroll 1
@@ -702,7 +707,7 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
             G fs[8];
             const G rr = geodesic_rhs_g<G>(ys, a, m, flat, fs);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) KX(st, c) = fs[c];
+            for (int c = 0; c < 8; ++c) if (c != 4) KX(st, c) = fs[c];
             if (st == 0) {
                 r_cur = A::to(rr);
                 been_inside = r_cur < r_cam;
@@ -722,6 +727,7 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
             G errv[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
+                if (c == 4) { errv[4] = G(0); continue; }
                 StageDot<G> acc;
                 acc.first(DPCoef<G>::e(0), KX(0, c));
 #pragma unroll 1
@@ -770,18 +776,18 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                     const float hh = 0.5f * A::tof(h);
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        float acc = c_dpf.m[0].x * A::tof(KX(0, c));
+                        float acc = c_dpf.m[0].x * A::tof(KR(0, c));
 #pragma unroll 1
-                        for (int j = 2; j < 7; ++j) acc = fmaf(c_dpf.m[j].x, A::tof(KX(j, c)), acc);
+                        for (int j = 2; j < 7; ++j) acc = fmaf(c_dpf.m[j].x, A::tof(KR(j, c)), acc);
                         incm[c] = hh * acc;
                         if constexpr (!kNative) ymf[c] = y[c].hi + (y[c].lo + incm[c]);
                     }
                 } else {
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        G acc = DPCoef<G>::m(0) * KX(0, c);
+                        G acc = DPCoef<G>::m(0) * KR(0, c);
 #pragma unroll 1
-                        for (int j = 2; j < 7; ++j) acc = acc + DPCoef<G>::m(j) * KX(j, c);
+                        for (int j = 2; j < 7; ++j) acc = acc + DPCoef<G>::m(j) * KR(j, c);
                         ym[c] = y[c] + (kHalf * h) * acc;
                     }
                 }
@@ -853,9 +859,9 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                     float y0f[8], d0f[8], c2f[8], c3f[8], c4f[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        const float d0 = hf * A::tof(KX(0, c));
+                        const float d0 = hf * A::tof(KR(0, c));
                         const float D1 = A::tof(y5[c] - y[c]) - d0;
-                        const float D2 = hf * A::tof(KX(6, c)) - d0;
+                        const float D2 = hf * A::tof(KR(6, c)) - d0;
                         const float D3 = incm[c] - 0.5f * d0;
                         y0f[c] = A::tof(y[c]);
                         d0f[c] = d0;
@@ -869,9 +875,9 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         y0d[c] = A::to(y[c]);
-                        d0[c] = hd * A::to(KX(0, c));
+                        d0[c] = hd * A::to(KR(0, c));
                         const double D1 = A::to(y5[c]) - y0d[c] - d0[c];
-                        const double D2 = hd * A::to(KX(6, c)) - d0[c];
+                        const double D2 = hd * A::to(KR(6, c)) - d0[c];
                         const double D3 = A::to(ym[c]) - y0d[c] - 0.5 * d0[c];
                         c2[c] = -5.0 * D1 + D2 + 16.0 * D3;
                         c3[c] = 14.0 * D1 - 3.0 * D2 - 32.0 * D3;
@@ -893,7 +899,7 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                 if (!ok) { status = BL_RAY_OVERFLOW; done = true; }
             }
 #pragma unroll
-            for (int c = 0; c < 8; ++c) { y[c] = y5[c]; KX(0, c) = KX(6, c); }
+            for (int c = 0; c < 8; ++c) { y[c] = y5[c]; if (c != 4) KX(0, c) = KX(6, c); }
             if constexpr (kNative) {
                 double fac = (eps == 0.0) ? 10.0 : 0.9 * pow(eps, -0.2);
                 fac = fmin(10.0, fmax(0.2, fac));
@@ -959,6 +965,8 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
     }
 }
 #undef KX
+#undef KR
+#undef KSLOT
 
 // Per-image constant in the transfer arithmetic.
 template <class T>
