@@ -445,9 +445,10 @@ const char* blacklight_strerror(int code);
 const char* blacklight_last_error_detail(void);
 /* Kernels launched by this thread since the last reset (launch accounting for benchmarks). */
 uint64_t blacklight_launch_count(int reset);
-/* Device time of the geodesic kernel (ms[0]) and transfer kernel (ms[1]) of this thread's
- * last call made with BL_TIMING; waits for that call's work. Returns 0, or BL_EINVAL if no
- * timed call was made. */
+/* Device time of the geodesic phase (ms[0]: the rays' initial states and the geodesic kernel)
+ * and of the transfer kernel (ms[1]) of this thread's last call made with BL_TIMING, summed
+ * over its waves; waits for that call's work. Returns 0, or BL_EINVAL if no timed call was
+ * made. */
 int blacklight_last_kernel_ms(float ms[2]);
 
 #ifdef __cplusplus

@@ -55,7 +55,7 @@ constexpr int64_t kChunksPerRay = 16;
 constexpr int64_t kWaveRays = 1 << 20;
 
 struct Layout {
-    size_t counters, descs, hdr, chunks, pool, total;
+    size_t counters, descs, hdr, init, chunks, pool, total;
     int64_t rays;          // rays of the whole call
     int64_t wave;          // rays per wave (the workspace holds one wave)
     int64_t pool_chunks;
@@ -73,6 +73,7 @@ Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precis
     L.counters = off; off = align_up(off + sizeof(bl::Counters));
     L.descs = off;    off = align_up(off + sizeof(bl::ImageDesc) * (size_t)n_images);
     L.hdr = off;      off = align_up(off + sizeof(bl::RayHdr) * (size_t)L.wave);
+    L.init = off;     off = align_up(off + sizeof(bl::RayInit) * (size_t)L.wave);
     L.chunks = off;   off = align_up(off + sizeof(int32_t) * bl::kMaxChunks * (size_t)L.wave);
     L.pool = off;     off = align_up(off + rec * bl::kChunk * (size_t)L.pool_chunks);
     L.total = off;
@@ -410,18 +411,30 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
                 bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
                 bl::geodesic_rk_kernel<float><<<rk_grid, 128, 0, st>>>(d_desc, n_images, b, e, hdr, sink, record, cfg.bs);
             }
-        } else if (precision == BL_PREC_FP64) {
-            bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
-            bl::geodesic_kernel<double, double><<<geo_grid, 128, kGeoSmem, st>>>(
-                d_desc, n_images, b, e, hdr, sink, record, cfg.bs);
         } else {
-            bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
-            if (precision == BL_PREC_MIXED)
-                bl::geodesic_kernel<float, double><<<geo_grid, 128, kGeoSmem, st>>>(
-                    d_desc, n_images, b, e, hdr, sink, record, cfg.bs);
-            else
-                bl::geodesic_kernel<float, bl::df64><<<geo_grid, 128, kGeoSmem, st>>>(
-                    d_desc, n_images, b, e, hdr, sink, record, cfg.bs);
+            // double-float form: the wave's pixel initial states first, then the integrator
+            bl::RayInit* init = (bl::RayInit*)(ws + L.init);
+            if (precision == BL_PREC_FAST) {
+                const int64_t wn = e - b;
+                const int64_t ib = (wn + 255) / 256, icap = (int64_t)di.sms * 8;
+                bl::ray_init_kernel<<<(unsigned)(ib < icap ? (ib > 0 ? ib : 1) : icap), 256, 0, st>>>(
+                    d_desc, n_images, b, e, cfg.bs, init);
+                ++g_launches;
+                BL_CUDA(cudaGetLastError());
+            }
+            if (precision == BL_PREC_FP64) {
+                bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
+                bl::geodesic_kernel<double, double><<<geo_grid, 128, kGeoSmem, st>>>(
+                    d_desc, n_images, b, e, hdr, sink, record, cfg.bs, init);
+            } else {
+                bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
+                if (precision == BL_PREC_MIXED)
+                    bl::geodesic_kernel<float, double><<<geo_grid, 128, kGeoSmem, st>>>(
+                        d_desc, n_images, b, e, hdr, sink, record, cfg.bs, init);
+                else
+                    bl::geodesic_kernel<float, bl::df64><<<geo_grid, 128, kGeoSmem, st>>>(
+                        d_desc, n_images, b, e, hdr, sink, record, cfg.bs, init);
+            }
         }
         ++g_launches;
         BL_CUDA(cudaGetLastError());

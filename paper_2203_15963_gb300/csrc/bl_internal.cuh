@@ -75,6 +75,13 @@ struct RayHdr {
     int32_t status;  // BL_RAY_*
 };
 
+// Initial state of a ray (Sec. 2.1, camera pixel): y = (x^a, k_a) and the frequency
+// normalisation, written by ray_init_kernel before the geodesic kernel of a wave.
+struct RayInit {
+    double y[8];
+    double nnorm;
+};
+
 // Rays taken from a device block list (adaptive levels) instead of consecutive image ranges:
 // ray r traces pixel (bx B + r % B, by B + (r / B) % B) of image q, where (q, bx, by) =
 // entries[r / B^2]; the number of blocks is read from the device, so a kernel earlier in the
