@@ -126,6 +126,15 @@ struct DFDot {
         s = t;
         c += e + q;
     }
+    // adds a double-float term (not a product): its high word through TwoSum, its low word
+    // to the error term
+    __device__ __forceinline__ void add_term(const df64& t) {
+        const float u = __fadd_rn(s, t.hi);
+        const float z = __fsub_rn(u, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(u, z)), __fsub_rn(t.hi, z));
+        s = u;
+        c += e + t.lo;
+    }
     __device__ __forceinline__ df64 get() const { return df_fast_two_sum(s, c); }
     // y + h (s + c) in one pass (no renormalisation of the sum first): the product's high part
     // enters a TwoSum with y.hi, everything else the low word, one Fast2Sum at the end

@@ -406,6 +406,33 @@ template <> struct GeoArith<df64> {
     static __device__ __forceinline__ float tof(const df64& g) { return g.hi + g.lo; }
 };
 
+// Short sums of products in the integrator arithmetic: plain expressions in double, the
+// compensated accumulator (one renormalisation per sum) in double-float.
+__device__ __forceinline__ double g_fma(double a, double b, double c) { return a * b + c; }
+__device__ __forceinline__ double g_dot2(double a, double b, double c, double d) { return a * b + c * d; }
+__device__ __forceinline__ double g_dot3(double a, double b, double c, double d, double e,
+                                         double f) { return a * b + c * d + e * f; }
+__device__ __forceinline__ df64 g_fma(const df64& a, const df64& b, const df64& c) {
+    DFDot s;
+    s.first(a, b);
+    s.add_term(c);
+    return s.get();
+}
+__device__ __forceinline__ df64 g_dot2(const df64& a, const df64& b, const df64& c, const df64& d) {
+    DFDot s;
+    s.first(a, b);
+    s.add(c, d);
+    return s.get();
+}
+__device__ __forceinline__ df64 g_dot3(const df64& a, const df64& b, const df64& c, const df64& d,
+                                       const df64& e, const df64& f) {
+    DFDot s;
+    s.first(a, b);
+    s.add(c, d);
+    s.add(e, f);
+    return s.get();
+}
+
 // Exact scaling by a power of two in the integrator arithmetic.
 __device__ __forceinline__ double scale2(double x, float f) { return x * (double)f; }
 __device__ __forceinline__ df64 scale2(const df64& x, float f) { return df_scale(x, f); }
@@ -427,46 +454,47 @@ __device__ __forceinline__ G geodesic_rhs_g(const G y[8], const G& a, const G& m
     const G kt = y[4], kx = y[5], ky = y[6], kz = y[7];
     // r (Eq. cks_aux:r), f and l as in ks_geom: two reciprocal square roots, one reciprocal
     const G aa = a * a;
-    const G q = x * x + yy * yy + z * z - aa;
+    const G q = g_dot3(x, x, yy, yy, z, z) - aa;
     const G aaz2 = aa * z * z;
-    const G D2 = q * q + scale2(aaz2, 4.0f);
+    const G D2 = g_fma(q, q, scale2(aaz2, 4.0f));
     const G iD = rsqrt(D2);
-    const G r2 = scale2(q + D2 * iD, 0.5f);
+    const G r2 = scale2(g_fma(D2, iD, q), 0.5f);
     const G ir = rsqrt(r2);
     const G r = r2 * ir;
-    const G s4 = r2 * r2 + aaz2;
+    const G s4 = g_fma(r2, r2, aaz2);
     const G P = r2 + aa;
     const G iPs = c1 / (P * s4);
     const G is4 = P * iPs;
     const G iP = s4 * iPs;
     const G f = flat ? c0 : scale2(m, 2.0f) * r * r2 * is4;
-    const G lx = (r * x + a * yy) * iP, ly = (r * yy - a * x) * iP, lz = z * ir;
+    const G lx = g_dot2(r, x, a, yy) * iP, ly = g_dot2(r, yy, -a, x) * iP, lz = z * ir;
     // L = l^a k_a (l^t = -1)
-    const G A_ = x * kx + yy * ky;
-    const G B_ = yy * kx - x * ky;
-    const G Lxy = (r * A_ + a * B_) * iP;
-    const G L = Lxy + lz * kz - kt;
+    const G A_ = g_dot2(x, kx, yy, ky);
+    const G B_ = g_dot2(yy, kx, -x, ky);
+    const G Lxy = g_dot2(r, A_, a, B_) * iP;
+    const G L = g_fma(lz, kz, Lxy - kt);
     const G fL = f * L;
     dy[0] = fL - kt;
-    dy[1] = kx - lx * fL;
-    dy[2] = ky - ly * fL;
-    dy[3] = kz - lz * fL;
+    dy[1] = g_fma(-lx, fL, kx);
+    dy[2] = g_fma(-ly, fL, ky);
+    dy[3] = g_fma(-lz, fL, kz);
     dy[4] = c0;
     // d_c r
     const G riD = r * iD;
     const G drx = riD * x, dry = riD * yy, drz = z * P * ir * iD;
     // d_c L at fixed k, and d_c f
-    const G V = (A_ - scale2(r, 2.0f) * Lxy) * iP - kz * ir * lz;
-    const G Sx = drx * V + (r * kx - a * ky) * iP;
-    const G Sy = dry * V + (r * ky + a * kx) * iP;
-    const G Sz = drz * V + kz * ir;
-    const G F1 = f * (c3 * ir - scale2(r2, 4.0f) * r * is4);
+    const G w = kz * ir;
+    const G V = g_dot2(g_fma(-scale2(r, 2.0f), Lxy, A_), iP, -w, lz);
+    const G Sx = g_dot2(drx, V, g_dot2(r, kx, -a, ky), iP);
+    const G Sy = g_dot2(dry, V, g_dot2(r, ky, a, kx), iP);
+    const G Sz = g_fma(drz, V, w);
+    const G F1 = f * g_dot2(c3, ir, -(scale2(r2, 4.0f) * r), is4);
     const G dfx = F1 * drx, dfy = F1 * dry;
-    const G dfz = F1 * drz - scale2(aa, 2.0f) * z * f * is4;
+    const G dfz = g_fma(F1, drz, -(scale2(aa, 2.0f) * z * f * is4));
     const G halfL = scale2(L, 0.5f);
-    dy[5] = L * (dfx * halfL + f * Sx);
-    dy[6] = L * (dfy * halfL + f * Sy);
-    dy[7] = L * (dfz * halfL + f * Sz);
+    dy[5] = L * g_dot2(dfx, halfL, f, Sx);
+    dy[6] = L * g_dot2(dfy, halfL, f, Sy);
+    dy[7] = L * g_dot2(dfz, halfL, f, Sz);
     return r;
 }
 
