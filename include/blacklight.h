@@ -237,9 +237,13 @@ int blacklight_trace_host(const bl_camera_t* cam, const bl_metric_t* met, const 
 
 /* blacklight_trace_batch with HOST buffers: grids[q].prim (and coef_mlp) and every pointer in
  * outs[q] are host pointers (pinned memory copies fastest). A grid whose prim pointer appears
- * in several images is copied to the device once; all images are then traced in one batched
- * launch and the outputs copied back. Stream-ordered on `stream`, synchronous; device scratch
- * is allocated and freed inside. flags: BL_UNPOLARIZED (BL_ASYNC and BL_TIMING are ignored). */
+ * in several images is copied to the device once (and repacked to the cell layout there);
+ * all images are then traced in one batched launch and the outputs copied back. The grid
+ * copies run on a non-blocking stream the library keeps for each device, concurrently with
+ * the camera and geodesic kernels on `stream` (which do not read the grids); the transfer
+ * kernel waits for them. Synchronous: returns after `stream` has finished the call's work;
+ * device scratch is allocated and freed inside. flags: BL_UNPOLARIZED (BL_ASYNC and BL_TIMING
+ * are ignored). */
 int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
                                 const bl_metric_t* mets, const bl_grid_t* grids,
                                 const double* freqs_hz, const bl_out_t* outs, void* stream,

@@ -361,6 +361,7 @@ struct LaunchCfg {
     int integrator = BL_INT_DP;
     bool keep_bad = false;  // leave the bad-ray count of earlier launches in place
     bl::BlockSource bs{nullptr, nullptr, 0};   // rays from a device block list (adaptive)
+    cudaEvent_t gate = nullptr;   // the first transfer launch waits for it (grids still arriving)
 };
 
 // The kernel sequence of one trace on prepared workspace whose image descriptors are already
@@ -440,6 +441,8 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
         BL_CUDA(cudaGetLastError());
         if (timing) BL_CUDA(cudaEventRecord(g_ev[2 * w + 1], st));
         if (transfer) {
+            // the geodesic kernel does not read the grids: only the transfer waits for them
+            if (w == 0 && cfg.gate) BL_CUDA(cudaStreamWaitEvent(st, cfg.gate, 0));
             const float* fpool = (const float*)(ws + L.pool);
             const double* dpool = (const double*)(ws + L.pool);
             if (mlp) {
@@ -557,7 +560,8 @@ int check_batch(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* me
 
 int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
                const bl_grid_t* grids, const double* freqs, const bl_out_t* outs, void* workspace,
-               size_t workspace_bytes, void* stream, uint32_t flags, bool transfer) {
+               size_t workspace_bytes, void* stream, uint32_t flags, bool transfer,
+               cudaEvent_t gate = nullptr) {
     g_detail[0] = 0;
     int precision = -1;
     {
@@ -607,6 +611,7 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
     }
     LaunchCfg cfg;
     if (flags & BL_UNPOLARIZED) cfg.feat |= bl::kFUnpol;
+    cfg.gate = gate;
     rc = launch_all(n_images, descs, ws, L, precision, transfer, st, (flags & BL_TIMING) != 0, mlp,
                     cfg);
     if (rc == 0) rc = finish(ws, L, st, !(flags & BL_ASYNC));
@@ -1631,6 +1636,20 @@ int blacklight_mlp_coefficients(const float* params, int64_t n, const double* in
 
 namespace {
 
+// A non-blocking stream per device for input copies that overlap kernels on the caller's
+// stream (created once, kept for the process).
+int copy_stream(cudaStream_t* out) {
+    static std::mutex mu;
+    static std::vector<cudaStream_t> streams;
+    int dev = 0;
+    BL_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)streams.size() <= dev) streams.resize(dev + 1, nullptr);
+    if (!streams[dev]) BL_CUDA(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+    *out = streams[dev];
+    return 0;
+}
+
 // Plane -> cell repacking of n_snap snapshots of `per_snap` cells (stream-ordered).
 int launch_grid_pack(const float* planes, float* cells, int64_t per_snap, int64_t n_snap,
                      cudaStream_t st) {
@@ -1682,12 +1701,14 @@ int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
     }
     cudaStream_t st = (cudaStream_t)stream;
     // distinct grids (by host pointer), their sizes and offsets in one device allocation.
-    // Grids given in the plane layout are copied through one staging region and repacked
-    // into the cell layout on the device (each trilinear corner then costs two vector loads).
+    // Grids given in the plane layout are copied into staging regions of their own and
+    // repacked into the cell layout on the device (each trilinear corner then costs two vector
+    // loads). The copies run on a side stream while the geodesic kernel, which does not read
+    // the grids, runs on `stream`; only the transfer kernel waits for them.
     std::vector<const float*> uniq;
     std::vector<size_t> gsz, goff;
     std::vector<int> gidx(n_images), gfirst;
-    size_t off = 0, stage = 0;
+    size_t off = 0;
     for (int q = 0; q < n_images; ++q) {
         const bl_grid_t& g = grids[q];
         const size_t bytes = sizeof(float) * 8 * (size_t)g.n_r * g.n_theta * g.n_phi *
@@ -1702,7 +1723,6 @@ int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
             goff.push_back(off);
             gfirst.push_back(q);
             off = align_up(off + bytes);
-            if (g.layout == BL_GRID_PLANES && bytes > stage) stage = bytes;
         } else if (gsz[k] < bytes) {
             return fail(BL_EINVAL, "grids[%d] shares its prim pointer with a smaller grid", q);
         } else if (grids[gfirst[k]].layout != g.layout) {
@@ -1710,8 +1730,9 @@ int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
         }
         gidx[q] = k;
     }
-    const size_t o_stage = off;
-    off = align_up(off + stage);
+    std::vector<size_t> ostage(uniq.size(), 0);
+    for (size_t u = 0; u < uniq.size(); ++u)
+        if (grids[gfirst[u]].layout == BL_GRID_PLANES) { ostage[u] = off; off = align_up(off + gsz[u]); }
     const size_t o_mlp = off;
     if (grids[0].coef_mlp) off = align_up(off + sizeof(float) * BL_MLP_PARAMS);
     std::vector<size_t> o_out(n_images);
@@ -1733,21 +1754,36 @@ int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
     cudaError_t e = cudaMallocAsync((void**)&dev, off, st);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync(%zu): %s", off, cudaGetErrorString(e)); }
     int rc = 0;
+    // side stream for the input copies: it starts after the allocation on `stream`, and
+    // `gate` marks the end of its work (the transfer kernel and every exit path wait for it)
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_alloc = nullptr, gate = nullptr;
+    rc = copy_stream(&cs);
+    if (!rc && (e = cudaEventCreateWithFlags(&ev_alloc, cudaEventDisableTiming)) != cudaSuccess)
+        rc = cuda_fail(e, "cudaEventCreate");
+    if (!rc && (e = cudaEventCreateWithFlags(&gate, cudaEventDisableTiming)) != cudaSuccess)
+        rc = cuda_fail(e, "cudaEventCreate");
+    if (!rc && (e = cudaEventRecord(ev_alloc, st)) != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
+    if (!rc && (e = cudaStreamWaitEvent(cs, ev_alloc, 0)) != cudaSuccess) rc = cuda_fail(e, "cudaStreamWaitEvent");
     for (size_t u = 0; u < uniq.size() && !rc; ++u) {
         const bl_grid_t& g = grids[gfirst[u]];
         const bool pack = g.layout == BL_GRID_PLANES;
-        e = cudaMemcpyAsync(dev + (pack ? o_stage : goff[u]), uniq[u], gsz[u],
-                            cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(dev + (pack ? ostage[u] : goff[u]), uniq[u], gsz[u],
+                            cudaMemcpyHostToDevice, cs);
         if (e != cudaSuccess) rc = cuda_fail(e, "copy grid to device");
-        if (!rc && pack)   // stream order: the next copy into the staging region waits for it
-            rc = launch_grid_pack((const float*)(dev + o_stage), (float*)(dev + goff[u]),
+        if (!rc && pack)
+            rc = launch_grid_pack((const float*)(dev + ostage[u]), (float*)(dev + goff[u]),
                                   (int64_t)g.n_r * g.n_theta * g.n_phi,
-                                  g.n_snapshots > 1 ? g.n_snapshots : 1, st);
+                                  g.n_snapshots > 1 ? g.n_snapshots : 1, cs);
     }
     if (!rc && grids[0].coef_mlp) {
         e = cudaMemcpyAsync(dev + o_mlp, grids[0].coef_mlp, sizeof(float) * BL_MLP_PARAMS,
-                            cudaMemcpyHostToDevice, st);
+                            cudaMemcpyHostToDevice, cs);
         if (e != cudaSuccess) rc = cuda_fail(e, "copy coefficient model to device");
+    }
+    if (cs && gate) {
+        e = cudaEventRecord(gate, cs);
+        if (!rc && e != cudaSuccess) rc = cuda_fail(e, "cudaEventRecord");
     }
     std::vector<bl_grid_t> dg(grids, grids + n_images);
     std::vector<bl_out_t> dout(outs, outs + n_images);
@@ -1767,7 +1803,9 @@ int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
     }
     if (!rc)
         rc = trace_impl(n_images, cams, mets, dg.data(), freqs_hz, dout.data(), dev + o_ws, L.total,
-                        stream, BL_ASYNC | (flags & BL_UNPOLARIZED), true);
+                        stream, BL_ASYNC | (flags & BL_UNPOLARIZED), true, gate);
+    // whatever happened above, nothing on `stream` (results, the free) may overtake the copies
+    if (gate) cudaStreamWaitEvent(st, gate, 0);
     for (int q = 0; q < n_images && rc >= 0; ++q) {
         const size_t npix = (size_t)cams[q].n * cams[q].n;
         const size_t es = outs[q].dtype == 0 ? sizeof(double) : sizeof(float);
@@ -1792,6 +1830,8 @@ int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
     cudaFreeAsync(dev, st);
     cudaError_t se = cudaStreamSynchronize(st);
     if (rc == 0 && se != cudaSuccess) rc = cuda_fail(se, "cudaStreamSynchronize");
+    if (ev_alloc) cudaEventDestroy(ev_alloc);
+    if (gate) cudaEventDestroy(gate);
     return rc;
 }
 
