@@ -1487,18 +1487,29 @@ __device__ __forceinline__ void fluid_basis(const KSGeom<T>& G, const Plasma<T>&
 // N12 = (U + iV)/2.
 template <class T>
 __device__ __forceinline__ void coh_to_stokes(const Coh<T>& n, const T e1l[4], const T e2l[4], T s[4]) {
+    // n11 = e1 R e1, n22 = e2 R e2, n12 = e1 (R + i I) e2, through R e1, R e2 and I e2
     T R[4][4], I[4][4];
     coh_unpack(n, R, I);
-    T n11 = T(0), n22 = T(0), n12r = T(0), n12i = T(0);
+    T v1[4], v2[4], w2[4];
 #pragma unroll
-    for (int a_ = 0; a_ < 4; ++a_)
+    for (int a_ = 0; a_ < 4; ++a_) {
+        T x1 = T(0), x2 = T(0), xi = T(0);
 #pragma unroll
         for (int b_ = 0; b_ < 4; ++b_) {
-            n11 += e1l[a_] * e1l[b_] * R[a_][b_];
-            n22 += e2l[a_] * e2l[b_] * R[a_][b_];
-            n12r += e1l[a_] * e2l[b_] * R[a_][b_];
-            n12i += e1l[a_] * e2l[b_] * I[a_][b_];
+            x1 += R[a_][b_] * e1l[b_];
+            x2 += R[a_][b_] * e2l[b_];
+            if (b_ != a_) xi += I[a_][b_] * e2l[b_];
         }
+        v1[a_] = x1; v2[a_] = x2; w2[a_] = xi;
+    }
+    T n11 = T(0), n22 = T(0), n12r = T(0), n12i = T(0);
+#pragma unroll
+    for (int a_ = 0; a_ < 4; ++a_) {
+        n11 += e1l[a_] * v1[a_];
+        n22 += e2l[a_] * v2[a_];
+        n12r += e1l[a_] * v2[a_];
+        n12i += e1l[a_] * w2[a_];
+    }
     s[0] = n11 + n22;
     s[1] = n11 - n22;
     s[2] = T(2) * n12r;
@@ -1507,19 +1518,26 @@ __device__ __forceinline__ void coh_to_stokes(const Coh<T>& n, const T e1l[4], c
 
 template <class T>
 __device__ __forceinline__ void stokes_to_coh(const T e1[4], const T e2[4], const T s[4], Coh<T>& n) {
+    // N = p e1 e1 + q e2 e2 + u (e1 e2 + e2 e1) + i v (e1 e2 - e2 e1), with the vectors
+    // scaled once
     const T p = T(0.5) * (s[0] + s[1]), qv = T(0.5) * (s[0] - s[1]), uu = T(0.5) * s[2], vv = T(0.5) * s[3];
+    T pe1[4], qe2[4], ue1[4], ue2[4], ve1[4];
+#pragma unroll
+    for (int a_ = 0; a_ < 4; ++a_) {
+        pe1[a_] = p * e1[a_]; qe2[a_] = qv * e2[a_]; ue1[a_] = uu * e1[a_]; ue2[a_] = uu * e2[a_];
+        ve1[a_] = vv * e1[a_];
+    }
     int k = 0;
 #pragma unroll
     for (int a_ = 0; a_ < 4; ++a_)
 #pragma unroll
-        for (int b_ = a_; b_ < 4; ++b_) {
-            n.re[k++] = p * e1[a_] * e1[b_] + qv * e2[a_] * e2[b_] + uu * (e1[a_] * e2[b_] + e2[a_] * e1[b_]);
-        }
+        for (int b_ = a_; b_ < 4; ++b_)
+            n.re[k++] = pe1[a_] * e1[b_] + qe2[a_] * e2[b_] + ue1[a_] * e2[b_] + ue2[a_] * e1[b_];
     k = 0;
 #pragma unroll
     for (int a_ = 0; a_ < 4; ++a_)
 #pragma unroll
-        for (int b_ = a_ + 1; b_ < 4; ++b_) n.im[k++] = vv * (e1[a_] * e2[b_] - e2[a_] * e1[b_]);
+        for (int b_ = a_ + 1; b_ < 4; ++b_) n.im[k++] = ve1[a_] * e2[b_] - ve1[b_] * e2[a_];
 }
 
 // One sample record as 16-byte vector loads (records are 16-byte aligned).

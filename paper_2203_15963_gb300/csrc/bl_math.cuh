@@ -358,8 +358,19 @@ __device__ __forceinline__ void synchrotron_coefficients(T ne, T th, T bg, T nu,
         out[5] = out[2] * ibnu;
     }
     const T X = th * sqrt(T(1.4142135623730951e3) * sth * nub / nu);
-    const T fm = T(2.011) * exp(-pow(X, T(1.035)) / T(4.7)) -
-                 cos(T(0.5) * X) * exp(-pow(X, T(1.2)) / T(2.73)) - T(0.011) * exp(-X / T(47.2));
+    // X^1.035 and X^1.2: in FP32 as exponentials of one shared logarithm (X = 0 gives
+    // log X = -inf and both powers 0, as pow does)
+    T p1, p2;
+    if constexpr (sizeof(T) == 4) {
+        const T lX = log(X);
+        p1 = exp(T(1.035) * lX);
+        p2 = exp(T(1.2) * lX);
+    } else {
+        p1 = pow(X, T(1.035));
+        p2 = pow(X, T(1.2));
+    }
+    const T fm = T(2.011) * exp(-p1 / T(4.7)) - cos(T(0.5) * X) * exp(-p2 / T(2.73)) -
+                 T(0.011) * exp(-X / T(47.2));
     const T gm = T(1) - T(0.11) * log1p(T(0.035) * X);
     const T base = ne * T(kE * kE / (kMe * kC));
     out[6] = base * nub * nub * sth2 / (nu * nu * nu) * fm * (k1 / k2 + T(6) * th);
