@@ -751,15 +751,24 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
 #pragma unroll
                 for (int c = 0; c < 8; ++c) ys[c] = y[c];
             } else {
+                // earlier stages outer (rolled), components inner: each coefficient is read
+                // once per stage term; every component keeps its order of operations
+                StageDot<G> acc[8];
+                {
+                    const G a0 = DPCoef<G>::a(st, 0);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    if (c == 4) { ys[4] = y[4]; continue; }
-                    StageDot<G> acc;
-                    acc.first(DPCoef<G>::a(st, 0), KX(0, c));
-#pragma unroll 1
-                    for (int j = 1; j < st; ++j) acc.add(DPCoef<G>::a(st, j), KX(j, c));
-                    ys[c] = acc.axpy(h, y[c]);
+                    for (int c = 0; c < 8; ++c)
+                        if (c != 4) acc[c].first(a0, KX(0, c));
                 }
+#pragma unroll 1
+                for (int j = 1; j < st; ++j) {
+                    const G aj = DPCoef<G>::a(st, j);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (c != 4) acc[c].add(aj, KX(j, c));
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) ys[c] = (c == 4) ? y[4] : acc[c].axpy(h, y[c]);
             }
             G fs[8];
             const G rr = geodesic_rhs_g<G>(ys, a, m, flat, fs);
@@ -782,14 +791,23 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
         bool finite = true;
         {
             G errv[8];
+            {
+                StageDot<G> acc[8];
+                {
+                    const G e0 = DPCoef<G>::e(0);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                if (c == 4) { errv[4] = G(0); continue; }
-                StageDot<G> acc;
-                acc.first(DPCoef<G>::e(0), KX(0, c));
+                    for (int c = 0; c < 8; ++c)
+                        if (c != 4) acc[c].first(e0, KX(0, c));
+                }
 #pragma unroll 1
-                for (int j = 2; j < 7; ++j) acc.add(DPCoef<G>::e(j), KX(j, c));
-                errv[c] = h * acc.get();
+                for (int j = 2; j < 7; ++j) {
+                    const G ej = DPCoef<G>::e(j);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (c != 4) acc[c].add(ej, KX(j, c));
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) errv[c] = (c == 4) ? G(0) : h * acc[c].get();
             }
             if constexpr (kNative) {
                 double num = 0.0, den = 1.0;
