@@ -849,12 +849,22 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                 float ymf[8], incm[8];
                 if constexpr (kFRec) {
                     const float hh = 0.5f * A::tof(h);
+                    float acc[8];
+                    {
+                        const float m0 = c_dpf.m[0].x;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) acc[c] = m0 * A::tof(KR(0, c));
+                    }
+#pragma unroll 1
+                    for (int j = 2; j < 7; ++j) {
+                        const float mj = c_dpf.m[j].x;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            if (c != 4) acc[c] = fmaf(mj, A::tof(KX(j, c)), acc[c]);
+                    }
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        float acc = c_dpf.m[0].x * A::tof(KR(0, c));
-#pragma unroll 1
-                        for (int j = 2; j < 7; ++j) acc = fmaf(c_dpf.m[j].x, A::tof(KR(j, c)), acc);
-                        incm[c] = hh * acc;
+                        incm[c] = hh * acc[c];
                         if constexpr (!kNative) ymf[c] = y[c].hi + (y[c].lo + incm[c]);
                     }
                 } else {
