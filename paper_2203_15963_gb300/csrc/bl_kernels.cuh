@@ -1278,8 +1278,9 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
     const T th = acos(cth);
     const T sth = sqrt(T(1) - cth * cth);
     const T twopi = T(2.0 * kPi);
+    // atan2 lies in (-pi, pi] and atan(a / r) in (-pi/2, pi/2), so |ph| < 3 pi/2 and one wrap
+    // puts it in [0, 2 pi) (fmod by 2 pi would return such a value unchanged)
     T ph = atan2(x[1], x[0]) - atan(a / r);
-    ph = fmod(ph, twopi);
     if (ph < T(0)) ph += twopi;
     if (ph >= twopi) ph -= twopi;
     const int nr = im.nr, nt = im.nt, np = im.nph;

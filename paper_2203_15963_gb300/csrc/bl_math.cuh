@@ -8,9 +8,19 @@
 
 namespace bl {
 
-// float / double forms of the CUDA Bessel I_0, I_1 (only the double names are overloaded)
-__device__ __forceinline__ float cyl_bessel_i0(float x) { return cyl_bessel_i0f(x); }
-__device__ __forceinline__ float cyl_bessel_i1(float x) { return cyl_bessel_i1f(x); }
+// Modified Bessel I_0, I_1 for 0 <= x <= 3.75 (used for x <= 2). FP32: the polynomials of
+// Abramowitz & Stegun 9.8.1 and 9.8.3 in t = x / 3.75 (|error| < 1.6e-7 for I_0, 8e-9 for
+// I_1 / x, below FP32 rounding); FP64: CUDA's double functions.
+__device__ __forceinline__ float cyl_bessel_i0(float x) {
+    const float t = x * (1.0f / 3.75f), t2 = t * t;
+    return 1.0f + t2 * (3.5156229f + t2 * (3.0899424f + t2 * (1.2067492f + t2 * (0.2659732f +
+           t2 * (0.0360768f + t2 * 0.0045813f)))));
+}
+__device__ __forceinline__ float cyl_bessel_i1(float x) {
+    const float t = x * (1.0f / 3.75f), t2 = t * t;
+    return x * (0.5f + t2 * (0.87890594f + t2 * (0.51498869f + t2 * (0.15084934f + t2 * (0.02658733f +
+           t2 * (0.00301532f + t2 * 0.00032411f))))));
+}
 __device__ __forceinline__ double cyl_bessel_i0(double x) { return ::cyl_bessel_i0(x); }
 __device__ __forceinline__ double cyl_bessel_i1(double x) { return ::cyl_bessel_i1(x); }
 
