@@ -279,7 +279,12 @@ struct DevInfo {
 
 template <class T, class R, int F>
 int occ_transfer(int* out) {
-    BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bl::transfer_kernel<T, R, F>, 128, 0));
+    if constexpr (std::is_same<T, double>::value) {
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bl::transfer_kernel_fp64<F>,
+                                                              bl::kTransferFp64Threads, 0));
+    } else {
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bl::transfer_kernel<T, R, F>, 128, 0));
+    }
     if (*out < 1) *out = 1;
     return 0;
 }
@@ -337,20 +342,35 @@ int dev_info(DevInfo& out) {
     return 0;
 }
 
-// One launch of the transfer variant with feature bits F.
+// One launch of the transfer variant with feature bits F (grid: CTAs; the FP64 kernel runs
+// CTAs of kTransferFp64Threads threads).
 template <class T, class R>
 void launch_transfer(int feat, unsigned grid, cudaStream_t st, const bl::ImageDesc* d, int n,
                      int64_t b, int64_t e, const bl::RayHdr* hdr, const R* pool,
                      const int32_t* chunks, bl::Counters* ctr, bl::BlockSource bs) {
-    switch (feat & 7) {
-        case 0: bl::transfer_kernel<T, R, 0><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-        case 1: bl::transfer_kernel<T, R, 1><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-        case 2: bl::transfer_kernel<T, R, 2><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-        case 3: bl::transfer_kernel<T, R, 3><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-        case 4: bl::transfer_kernel<T, R, 4><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-        case 5: bl::transfer_kernel<T, R, 5><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-        case 6: bl::transfer_kernel<T, R, 6><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-        default: bl::transfer_kernel<T, R, 7><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+    if constexpr (std::is_same<T, double>::value) {
+        constexpr int th = bl::kTransferFp64Threads;
+        switch (feat & 7) {
+            case 0: bl::transfer_kernel_fp64<0><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 1: bl::transfer_kernel_fp64<1><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 2: bl::transfer_kernel_fp64<2><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 3: bl::transfer_kernel_fp64<3><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 4: bl::transfer_kernel_fp64<4><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 5: bl::transfer_kernel_fp64<5><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 6: bl::transfer_kernel_fp64<6><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            default: bl::transfer_kernel_fp64<7><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+        }
+    } else {
+        switch (feat & 7) {
+            case 0: bl::transfer_kernel<T, R, 0><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 1: bl::transfer_kernel<T, R, 1><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 2: bl::transfer_kernel<T, R, 2><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 3: bl::transfer_kernel<T, R, 3><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 4: bl::transfer_kernel<T, R, 4><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 5: bl::transfer_kernel<T, R, 5><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 6: bl::transfer_kernel<T, R, 6><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            default: bl::transfer_kernel<T, R, 7><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+        }
     }
 }
 

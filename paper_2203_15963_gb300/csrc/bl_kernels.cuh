@@ -1648,13 +1648,12 @@ __device__ __forceinline__ void aux_finish(const ImageDesc& im, int64_t pix, con
 }
 
 template <class T, class R, int kF>
-__global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restrict__ imgs,
-                                                       int n_images, int64_t ray_begin,
-                                                       int64_t ray_end,
-                                                       const RayHdr* __restrict__ hdr,
-                                                       const R* __restrict__ pool,
-                                                       const int32_t* __restrict__ chunks,
-                                                       Counters* ctr, BlockSource bs) {
+__device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs,
+                                              int n_images, int64_t ray_begin, int64_t ray_end,
+                                              const RayHdr* __restrict__ hdr,
+                                              const R* __restrict__ pool,
+                                              const int32_t* __restrict__ chunks,
+                                              Counters* ctr, BlockSource bs) {
     constexpr bool kSlow = (kF & kFSlow) != 0;
     constexpr bool kUnpol = (kF & kFUnpol) != 0;
     constexpr bool kAux = (kF & kFAux) != 0;
@@ -1810,6 +1809,33 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
         --idx;
     }
 }
+// The transfer kernel: FP32 (mixed and fast forms) at up to 128 registers, 4 CTAs of 128
+// threads an SM; FP64 capped at 96 registers in CTAs of 64 threads, which keeps 20 warps an SM
+// resident instead of 8 (measured 835 -> 650 ms on the 9-image step; the FP32 kernel is
+// fastest uncapped).
+template <class T, class R, int kF>
+__global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restrict__ imgs,
+                                                       int n_images, int64_t ray_begin,
+                                                       int64_t ray_end,
+                                                       const RayHdr* __restrict__ hdr,
+                                                       const R* __restrict__ pool,
+                                                       const int32_t* __restrict__ chunks,
+                                                       Counters* ctr, BlockSource bs) {
+    transfer_body<T, R, kF>(imgs, n_images, ray_begin, ray_end, hdr, pool, chunks, ctr, bs);
+}
+constexpr int kTransferFp64Threads = 64;
+template <int kF>
+__global__ void __maxnreg__(96) transfer_kernel_fp64(const ImageDesc* __restrict__ imgs,
+                                                     int n_images, int64_t ray_begin,
+                                                     int64_t ray_end,
+                                                     const RayHdr* __restrict__ hdr,
+                                                     const double* __restrict__ pool,
+                                                     const int32_t* __restrict__ chunks,
+                                                     Counters* ctr, BlockSource bs) {
+    transfer_body<double, double, kF>(imgs, n_images, ray_begin, ray_end, hdr, pool, chunks,
+                                      ctr, bs);
+}
+
 // ---------------------------------------------------------------------------------------
 // Transfer with the learned coefficient model (FP32). The same per-sample work as
 // transfer_kernel, but the loop runs in lockstep across the CTA: every iteration each of the
