@@ -37,23 +37,24 @@ GRID = (256, 128, 128)
 # control (50).
 FLOP64_PER_ATTEMPT = 1214
 # dram__bytes_read.sum + dram__bytes_write.sum of geodesic_kernel<float, df64> per DP attempt
-# from one ncu capture of the a = 0.94, i = 60 deg image of this workload at 256^2 (1.159 GB
-# for 7,845,744 attempts); None whenever the kernel has changed since the capture
-GEO_DF64_DRAM_BYTES_PER_ATTEMPT = 147.8
+# from one ncu capture of the a = 0.94, i = 60 deg image of this workload at 256^2; None
+# whenever the kernel has changed since the capture
+GEO_DF64_DRAM_BYTES_PER_ATTEMPT = None
 # FP32 flops per transfer sample (2 transport matrices, predictor-corrector, sampling,
 # plasma, coefficients, fluid frame, Stokes step)
 FLOP32_PER_SAMPLE = 3300
 # Nominal peaks from the pool's profiling recipe (no measured FP64/FP32 peak is available):
 # FP64 1.25 TFLOP/s; FP32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
 PEAK_FP64_TFLOPS = 1.25
-# Double-float: FP32 instructions per emulated FP64 flop as implemented -- a product 7, a sum
-# 11, a scaling by a power of two 2, a reciprocal or reciprocal square root ~20, a term of a
+# Double-float: FP32 instructions per emulated FP64 flop as implemented -- a product 7 (4 inside
+# a chain of products), a sum 11, a scaling by a power of two 2, a reciprocal ~9 and a
+# reciprocal square root ~12 (hardware seed and one second-order step), a term of a
 # compensated sum of products 12 (first product 4, a plain term 7, the final renormalisation
-# 3, y + h sum 15), an FP32 flop 1. On the attempt's mix (right-hand sides 774 instructions for
+# 3, y + h sum 15), an FP32 flop 1. On the attempt's mix (right-hand sides 719 instructions for
 # 114 flops, stage combinations 2352 for 384, error estimate 576 for 96, norm and control ~60
-# for 50) that is 7632 instructions for 1214 flops, 6.3 per flop. The emulated peak is the
+# for 50) that is 7302 instructions for 1214 flops, 6.0 per flop. The emulated peak is the
 # FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz instructions/s) divided by that.
-DF64_INSTR_PER_FLOP = 6.3
+DF64_INSTR_PER_FLOP = 6.0
 PEAK_DF64_TFLOPS = 152 * 128 * 2.07e9 / DF64_INSTR_PER_FLOP / 1e12
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 

@@ -9,7 +9,7 @@
 //   double-length addition (Dekker 1971) and the FMA product of double-words (Joldes,
 //   Muller & Popescu 2017, "Tight and rigorous error bounds for basic building blocks of
 //   double-word arithmetic", structure of their Alg. 12);
-//   1/x and 1/sqrt(x): a Newton step to second order from the correctly rounded float value,
+//   1/x and 1/sqrt(x): a Newton step to second order from the hardware float approximation,
 //   with the residual formed exactly by FMAs (the refinement used for double-word
 //   reciprocals, e.g. in Hida, Li & Bailey's QD library).
 #pragma once
@@ -66,27 +66,36 @@ __device__ __forceinline__ df64 operator*(const df64& x, const df64& y) {
     p.lo = fmaf(x.lo, y.hi, p.lo);
     return df_fast_two_sum(p.hi, p.lo);
 }
+// x y without the final renormalisation: (p, e) with p the rounded product and |e| about one
+// ulp of p, valid as an operand of a further product or sum (used inside product chains)
+__device__ __forceinline__ df64 df_mul_nn(const df64& x, const df64& y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return df64(p, e);
+}
 __device__ __forceinline__ df64 df_mul_f(const df64& x, float b) {
     df64 p = df_two_prod(x.hi, b);
     p.lo = fmaf(x.lo, b, p.lo);
     return df_fast_two_sum(p.hi, p.lo);
 }
-// 1/x: correctly rounded FP32 seed y0, residual e = 1 - x y0 (|e| <= 2^-24) formed with FMAs
-// (the product x.hi y0 is exact inside the first one), then 1/x = y0 / (1 - e) =
-// y0 (1 + e + e^2 + ...) to second order; relative error ~1e-14 (2^-46.5).
+// 1/x: hardware FP32 seed y0 (~1 ulp), residual e = 1 - x y0 formed with FMAs (the product
+// x.hi y0 is exact inside the first one), then 1/x = y0 / (1 - e) = y0 (1 + e + e^2 + ...)
+// to second order; relative error ~5e-14.
 __device__ __forceinline__ df64 rcp(const df64& x) {
-    const float y0 = __frcp_rn(x.hi);
+    const float y0 = __fdividef(1.0f, x.hi);
     float e = fmaf(-x.hi, y0, 1.0f);
     e = fmaf(-x.lo, y0, e);
     const float t = fmaf(e, e, e);
     return df_fast_two_sum(y0, __fmul_rn(y0, t));
 }
 __device__ __forceinline__ df64 operator/(const df64& x, const df64& y) { return x * rcp(y); }
-// 1/sqrt(x): correctly rounded FP32 seed y0, residual u = x y0^2 - 1 formed with an exact
+// 1/sqrt(x): hardware FP32 seed y0 (~1 ulp), residual u = x y0^2 - 1 formed with an exact
 // product (p + ep = x.hi y0) and FMAs, then 1/sqrt(x) = y0 (1 + u)^(-1/2) =
-// y0 (1 - u/2 + 3 u^2 / 8 - ...) to second order; relative error ~1e-14.
+// y0 (1 - u/2 + 3 u^2 / 8 - ...) to second order; relative error ~7e-14.
 __device__ __forceinline__ df64 rsqrt(const df64& x) {
-    const float y0 = __frsqrt_rn(x.hi);
+    const float y0 = rsqrtf(x.hi);
     const float p = __fmul_rn(x.hi, y0);
     const float ep = fmaf(x.hi, y0, -p);
     float u = fmaf(p, y0, -1.0f);

@@ -433,6 +433,14 @@ __device__ __forceinline__ df64 g_dot3(const df64& a, const df64& b, const df64&
     return s.get();
 }
 
+// 1/x in the integrator arithmetic (no multiplication by an exact 1 in double-float).
+__device__ __forceinline__ double g_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ df64 g_rcp(const df64& x) { return rcp(x); }
+
+// A product inside a chain of products: unnormalised in double-float, plain in double.
+__device__ __forceinline__ double g_mul_nn(double a, double b) { return a * b; }
+__device__ __forceinline__ df64 g_mul_nn(const df64& a, const df64& b) { return df_mul_nn(a, b); }
+
 // Exact scaling by a power of two in the integrator arithmetic.
 __device__ __forceinline__ double scale2(double x, float f) { return x * (double)f; }
 __device__ __forceinline__ df64 scale2(const df64& x, float f) { return df_scale(x, f); }
@@ -449,13 +457,13 @@ __device__ __forceinline__ df64 scale2(const df64& x, float f) { return df_scale
 // The same quantities as the nine-derivative form, in about 40 fewer operations.
 template <class G>
 __device__ __forceinline__ G geodesic_rhs_g(const G y[8], const G& a, const G& m, bool flat, G dy[8]) {
-    constexpr G c0 = G(0), c3 = G(3), c1 = G(1);
+    constexpr G c0 = G(0), c3 = G(3);
     const G x = y[1], yy = y[2], z = y[3];
     const G kt = y[4], kx = y[5], ky = y[6], kz = y[7];
     // r (Eq. cks_aux:r), f and l as in ks_geom: two reciprocal square roots, one reciprocal
     const G aa = a * a;
     const G q = g_dot3(x, x, yy, yy, z, z) - aa;
-    const G aaz2 = aa * z * z;
+    const G aaz2 = g_mul_nn(aa, z) * z;
     const G D2 = g_fma(q, q, scale2(aaz2, 4.0f));
     const G iD = rsqrt(D2);
     const G r2 = scale2(g_fma(D2, iD, q), 0.5f);
@@ -463,10 +471,10 @@ __device__ __forceinline__ G geodesic_rhs_g(const G y[8], const G& a, const G& m
     const G r = r2 * ir;
     const G s4 = g_fma(r2, r2, aaz2);
     const G P = r2 + aa;
-    const G iPs = c1 / (P * s4);
+    const G iPs = g_rcp(P * s4);
     const G is4 = P * iPs;
     const G iP = s4 * iPs;
-    const G f = flat ? c0 : scale2(m, 2.0f) * r * r2 * is4;
+    const G f = flat ? c0 : g_mul_nn(g_mul_nn(scale2(m, 2.0f), r), r2) * is4;
     const G lx = g_dot2(r, x, a, yy) * iP, ly = g_dot2(r, yy, -a, x) * iP, lz = z * ir;
     // L = l^a k_a (l^t = -1)
     const G A_ = g_dot2(x, kx, yy, ky);
@@ -481,7 +489,7 @@ __device__ __forceinline__ G geodesic_rhs_g(const G y[8], const G& a, const G& m
     dy[4] = c0;
     // d_c r
     const G riD = r * iD;
-    const G drx = riD * x, dry = riD * yy, drz = z * P * ir * iD;
+    const G drx = riD * x, dry = riD * yy, drz = g_mul_nn(g_mul_nn(z, P), ir) * iD;
     // d_c L at fixed k, and d_c f
     const G w = kz * ir;
     const G V = g_dot2(g_fma(-scale2(r, 2.0f), Lxy, A_), iP, -w, lz);
@@ -490,7 +498,7 @@ __device__ __forceinline__ G geodesic_rhs_g(const G y[8], const G& a, const G& m
     const G Sz = g_fma(drz, V, w);
     const G F1 = f * g_dot2(c3, ir, -(scale2(r2, 4.0f) * r), is4);
     const G dfx = F1 * drx, dfy = F1 * dry;
-    const G dfz = g_fma(F1, drz, -(scale2(aa, 2.0f) * z * f * is4));
+    const G dfz = g_fma(F1, drz, -(g_mul_nn(g_mul_nn(scale2(aa, 2.0f), z), f) * is4));
     const G halfL = scale2(L, 0.5f);
     dy[5] = L * g_dot2(dfx, halfL, f, Sx);
     dy[6] = L * g_dot2(dfy, halfL, f, Sy);
