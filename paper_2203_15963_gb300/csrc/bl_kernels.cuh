@@ -528,6 +528,7 @@ template <> struct StageDot<df64> {
     __device__ __forceinline__ void add(const df64& a, const df64& x) { d.add(a, x); }
     __device__ __forceinline__ df64 get() const { return d.get(); }
     __device__ __forceinline__ df64 axpy(const df64& h, const df64& y) const { return d.axpy(h, y); }
+    __device__ __forceinline__ float value_f() const { return d.s + d.c; }
 };
 
 
@@ -799,6 +800,7 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
         bool finite = true;
         {
             G errv[8];
+            float errf[8];
             {
                 StageDot<G> acc[8];
                 {
@@ -814,8 +816,15 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                     for (int c = 0; c < 8; ++c)
                         if (c != 4) acc[c].add(ej, KX(j, c));
                 }
+                if constexpr (kNative) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) errv[c] = (c == 4) ? G(0) : h * acc[c].get();
+                    for (int c = 0; c < 8; ++c) errv[c] = (c == 4) ? G(0) : h * acc[c].get();
+                } else {
+                    // the double-float form uses the estimate in FP32 only: h_hi (s + c) there
+                    const float hf = A::tof(h);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) errf[c] = (c == 4) ? 0.0f : hf * acc[c].value_f();
+                }
             }
             if constexpr (kNative) {
                 double num = 0.0, den = 1.0;
@@ -832,7 +841,7 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                 const float ta = (float)tol_abs, tr = (float)tol_rel;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const float err = fabsf(A::tof(errv[c]));
+                    const float err = fabsf(errf[c]);
                     const float sc = ta + tr * fmaxf(fabsf(A::tof(y[c])), fabsf(A::tof(y5[c])));
                     finite = finite && isfinite(err) && isfinite(A::tof(y5[c]));
                     if (err * den > num * sc) { num = err; den = sc; }
