@@ -1290,14 +1290,14 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
     const T a = ic<T>(im, kcSpin);
     const T r = G.r;
     if (!(r >= ic<T>(im, kcRmin) && r <= ic<T>(im, kcRmax))) return false;
-    T cth = x[2] / r;
+    T cth = fq(x[2], r);
     cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
     const T th = acos(cth);
     const T sth = sqrt(T(1) - cth * cth);
     const T twopi = T(2.0 * kPi);
     // atan2 lies in (-pi, pi] and atan(a / r) in (-pi/2, pi/2), so |ph| < 3 pi/2 and one wrap
     // puts it in [0, 2 pi) (fmod by 2 pi would return such a value unchanged)
-    T ph = atan2(x[1], x[0]) - atan(a / r);
+    T ph = atan2(x[1], x[0]) - atan(fq(a, r));
     if (ph < T(0)) ph += twopi;
     if (ph >= twopi) ph -= twopi;
     const int nr = im.nr, nt = im.nt, np = im.nph;
@@ -1327,9 +1327,9 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
     const T dth = T(kPi) / T(nt);
     const T dph = twopi / T(np);
     if (im.interp == 0) {
-        int i = (int)floor((log(r) - lrmin) / dlr);
-        int j = (int)floor(th / dth);
-        int k = (int)floor(ph / dph);
+        int i = (int)floor(fq(log(r) - lrmin, dlr));
+        int j = (int)floor(fq(th, dth));
+        int k = (int)floor(fq(ph, dph));
         i = min(max(i, 0), nr - 1);
         j = min(max(j, 0), nt - 1);
         k = ((k % np) + np) % np;
@@ -1357,7 +1357,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
         int i0, j0;
         T wr, wt;
         {
-            T fi = (log(r) - lrmin) / dlr - T(0.5);
+            T fi = fq(log(r) - lrmin, dlr) - T(0.5);
             if (nr == 1) { i0 = 0; wr = T(0); }
             else {
                 fi = fi < T(0) ? T(0) : (fi > T(nr - 1) ? T(nr - 1) : fi);
@@ -1367,7 +1367,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
             }
         }
         {
-            T fj = th / dth - T(0.5);
+            T fj = fq(th, dth) - T(0.5);
             if (nt == 1) { j0 = 0; wt = T(0); }
             else {
                 fj = fj < T(0) ? T(0) : (fj > T(nt - 1) ? T(nt - 1) : fj);
@@ -1377,7 +1377,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
             }
         }
         const int i1 = nr == 1 ? 0 : i0 + 1, j1 = nt == 1 ? 0 : j0 + 1;
-        const T fk = ph / dph - T(0.5);
+        const T fk = fq(ph, dph) - T(0.5);
         const T fkf = floor(fk);
         const int k0 = (((int)fkf) % np + np) % np;
         const int k1 = (k0 + 1) % np;
@@ -1444,27 +1444,27 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
     const T lv = G.l[1] * v[0] + G.l[2] * v[1] + G.l[3] * v[2];
     const T un = sqrt(T(1) + v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + f * lv * lv);
     P.u[0] = un * sqrt(T(1) + f);
-    const T sh = f / (T(1) + f) * P.u[0];
+    const T sh = fq(f, T(1) + f) * P.u[0];
 #pragma unroll
     for (int c = 0; c < 3; ++c) P.u[c + 1] = v[c] - G.l[c + 1] * sh;
     lower4(G, P.u, P.ul);
     P.b[0] = B[0] * P.ul[1] + B[1] * P.ul[2] + B[2] * P.ul[3];
-    const T iut = T(1) / P.u[0];
+    const T iut = fq(T(1), P.u[0]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) P.b[c + 1] = (B[c] + P.b[0] * P.u[c + 1]) * iut;
     P.bsq = dot4(G, P.b, P.b);
     const T rho = pv[0];
     const T p = ic<T>(im, kcGam1) * pv[1];
     if (!(rho > T(0)) || !(p > T(0)) || !(P.bsq > T(0))) return false;
-    if (P.bsq / rho > ic<T>(im, kcSigma)) return false;
-    const T binv = P.bsq / (T(2) * p);
+    if (fq(P.bsq, rho) > ic<T>(im, kcSigma)) return false;
+    const T binv = fq(P.bsq, T(2) * p);
     const T b2 = binv * binv;
-    const T ratio = (ic<T>(im, kcRhigh) + b2 * ic<T>(im, kcRlow)) / (T(1) + b2);
+    const T ratio = fq(ic<T>(im, kcRhigh) + b2 * ic<T>(im, kcRlow), T(1) + b2);
     const T rr = ic<T>(im, kcNeNi);
-    const T th_e = ic<T>(im, kcTePre) * (p / rho) * (rr + T(1)) / (rr + ratio);
+    const T th_e = fq(ic<T>(im, kcTePre) * fq(p, rho) * (rr + T(1)), rr + ratio);
     if (!(th_e >= T(0.05))) return false;
     P.th = th_e;
-    P.ne = rho * ic<T>(im, kcNePre) / (T(1) + T(1) / rr);
+    P.ne = fq(rho * ic<T>(im, kcNePre), T(1) + fq(T(1), rr));
     P.bg = sqrt(P.bsq) * ic<T>(im, kcBgPre);
     P.rho = rho;
     P.p = p;
@@ -1478,7 +1478,7 @@ template <class T>
 __device__ __forceinline__ void fluid_basis(const KSGeom<T>& G, const Plasma<T>& P, const T kl[4],
                                             const T ku[4], T e1[4], T e2[4], T e1l[4], T e2l[4]) {
     const T kdu = kl[0] * P.u[0] + kl[1] * P.u[1] + kl[2] * P.u[2] + kl[3] * P.u[3];
-    const T iw = T(-1) / kdu;
+    const T iw = fq(T(-1), kdu);
     T e3[4], e3l[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) { e3[c] = (ku[c] + kdu * P.u[c]) * iw; e3l[c] = (kl[c] + kdu * P.ul[c]) * iw; }
@@ -1798,11 +1798,11 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
                 const T kdu = kl[0] * P.u[0] + kl[1] * P.u[1] + kl[2] * P.u[2] + kl[3] * P.u[3];
                 const T kdb = kl[0] * P.b[0] + kl[1] * P.b[1] + kl[2] * P.b[2] + kl[3] * P.b[3];
                 const T nu_fl = nu_norm * (-kdu);
-                T cth = kdb / ((-kdu) * sqrt(P.bsq));
+                T cth = fq(kdb, (-kdu) * sqrt(P.bsq));
                 cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
                 T co[8];
                 synchrotron_coefficients<T>(P.ne, P.th, P.bg, nu_fl, cth, co);
-                const T g = ic<T>(im, kcFreq) / nu_fl;
+                const T g = fq(ic<T>(im, kcFreq), nu_fl);
                 const T path = ic<T>(im, kcLen) * (-kdu);
                 const T eg = g * g * g * path;
                 const T coef[8] = {co[0] * eg, co[1] * eg, co[2] * eg, co[3] * path,
@@ -1981,7 +1981,7 @@ __global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __re
                 kdu = kl[0] * P.u[0] + kl[1] * P.u[1] + kl[2] * P.u[2] + kl[3] * P.u[3];
                 const T kdb = kl[0] * P.b[0] + kl[1] * P.b[1] + kl[2] * P.b[2] + kl[3] * P.b[3];
                 nu_fl = nu_norm * (-kdu);
-                cth = kdb / ((-kdu) * sqrt(P.bsq));
+                cth = fq(kdb, (-kdu) * sqrt(P.bsq));
                 cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
             }
         }
@@ -1997,7 +1997,7 @@ __global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __re
             T co[8];
             if (use) mlp::coefficients_from(o, P.ne, P.th, P.bg, nu_fl, cth, co);
             else synchrotron_coefficients<T>(P.ne, P.th, P.bg, nu_fl, cth, co);
-            const T g = ic<T>(im, kcFreq) / nu_fl;
+            const T g = fq(ic<T>(im, kcFreq), nu_fl);
             const T path = ic<T>(im, kcLen) * (-kdu);
             const T eg = g * g * g * path;
             const T coef[8] = {co[0] * eg, co[1] * eg, co[2] * eg, co[3] * path,

@@ -24,6 +24,15 @@ __device__ __forceinline__ float cyl_bessel_i1(float x) {
 __device__ __forceinline__ double cyl_bessel_i0(double x) { return ::cyl_bessel_i0(x); }
 __device__ __forceinline__ double cyl_bessel_i1(double x) { return ::cyl_bessel_i1(x); }
 
+// Quotient a / b on the coefficient and transport path: in FP32 the hardware reciprocal times
+// a (__fdividef: within 2 ulp for |b| < 2^126, far inside the FP32 form's error budget), in
+// FP64 the IEEE quotient.
+template <class T>
+__device__ __forceinline__ T fq(T a, T b) {
+    if constexpr (sizeof(T) == 4) return __fdividef(a, b);
+    else return a / b;
+}
+
 // CGS constants (CODATA 2018; IAU 2015 nominal solar mass).
 constexpr double kC = 2.99792458e10;
 constexpr double kE = 4.80320471e-10;
@@ -166,7 +175,7 @@ __device__ __forceinline__ void transport_matrix(const T xv[3], const T klo[4], 
     const T r = r2 * ir;
     const T s4 = r2 * r2 + aaz2;
     const T P = r2 + aa;
-    const T iPs = c1 / (P * s4);
+    const T iPs = fq(c1, P * s4);
     const T is4 = P * iPs;
     const T iP = s4 * iPs;
     const T f = flat ? c0 : c2 * m * r * r2 * is4;
@@ -308,18 +317,18 @@ __device__ __forceinline__ void bessel_k012_scaled(T x, T& k0, T& k1, T& k2) {
         const T p1 = T(1) + t2 * (T(0.15443144) + t2 * (T(-0.67278579) + t2 * (T(-0.18156897) +
                      t2 * (T(-0.01919402) + t2 * (T(-0.00110404) + t2 * T(-0.00004686))))));
         const T K0 = -lg * i0 + p0;
-        const T K1 = (x * lg * i1 + p1) / x;
+        const T K1 = fq(x * lg * i1 + p1, x);
         k0 = K0 * ex;
         k1 = K1 * ex;
     } else {
-        const T u = T(2) / x;
+        const T u = fq(T(2), x);
         const T sx = rsqrt(x);
         k0 = sx * (T(1.25331414) + u * (T(-0.07832358) + u * (T(0.02189568) + u * (T(-0.01062446) +
                    u * (T(0.00587872) + u * (T(-0.00251540) + u * T(0.00053208)))))));
         k1 = sx * (T(1.25331414) + u * (T(0.23498619) + u * (T(-0.03655620) + u * (T(0.01504268) +
                    u * (T(-0.00780353) + u * (T(0.00325614) + u * T(-0.00068245)))))));
     }
-    k2 = k0 + T(2) / x * k1;
+    k2 = k0 + fq(T(2), x) * k1;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -341,33 +350,33 @@ __device__ __forceinline__ void synchrotron_coefficients(T ne, T th, T bg, T nu,
     const T sth2 = T(1) - cth * cth;
     const T sth = sqrt(sth2 > T(0) ? sth2 : T(0));
     const T nub = T(kE / (2.0 * kPi * kMe * kC)) * bg;
-    const T z = T(1) / th;
+    const T z = fq(T(1), th);
     T k0, k1, k2;
     bessel_k012_scaled(z, k0, k1, k2);
     if (sth > T(0)) {
-        const T x = nu / (T(1.5) * nub * sth * th * th);
+        const T x = fq(nu, T(1.5) * nub * sth * th * th);
         const T x13 = cbrt(x);
-        const T ix13 = T(1) / x13;
+        const T ix13 = fq(T(1), x13);
         const T ix23 = ix13 * ix13;
         const T ex = exp(T(-1.8899) * x13);
         const T ii = T(2.5651) * (T(1) + T(1.92) * ix13 + T(0.9977) * ix23) * ex;
         const T iq = T(2.5651) * (T(1) + T(0.932) * ix13 + T(0.4998) * ix23) * ex;
-        const T iv = (T(1.8138) / x + T(3.423) * ix23 + T(0.02955) * rsqrt(x) + T(2.0377) * ix13) * ex;
+        const T iv = (fq(T(1.8138), x) + T(3.423) * ix23 + T(0.02955) * rsqrt(x) + T(2.0377) * ix13) * ex;
         // n e^2 nu / (sqrt3 c) / K_2(z) = n e^2 nu / (sqrt3 c) exp(-z) / (exp(z) K_2) * exp(z)...
         // 1 / K_2(z) = exp(z) / k2 (k2 is scaled).
-        const T pre = ne * T(kE * kE / (1.7320508075688772 * kC)) * nu * (exp(z) / k2);
+        const T pre = ne * T(kE * kE / (1.7320508075688772 * kC)) * nu * fq(exp(z), k2);
         out[0] = pre * ii;
         out[1] = pre * iq;
-        out[2] = pre * (T(4) / (T(3) * th)) * (cth / sth) * iv;
-        const T hkt = T(kH / (kMe * kC * kC)) * nu / th;
+        out[2] = pre * fq(T(4), T(3) * th) * fq(cth, sth) * iv;
+        const T hkt = fq(T(kH / (kMe * kC * kC)) * nu, th);
         // 1 / B_nu = c^2 expm1(h nu / k T) / (2 h nu^3), ordered to stay inside float range
-        const T cnu = T(kC) / nu;
-        const T ibnu = expm1(hkt) * (cnu * cnu) * (T(0.5 / kH) / nu);
+        const T cnu = fq(T(kC), nu);
+        const T ibnu = expm1(hkt) * (cnu * cnu) * fq(T(0.5 / kH), nu);
         out[3] = out[0] * ibnu;
         out[4] = out[1] * ibnu;
         out[5] = out[2] * ibnu;
     }
-    const T X = th * sqrt(T(1.4142135623730951e3) * sth * nub / nu);
+    const T X = th * sqrt(fq(T(1.4142135623730951e3) * sth * nub, nu));
     // X^1.035 and X^1.2: in FP32 as exponentials of one shared logarithm (X = 0 gives
     // log X = -inf and both powers 0, as pow does)
     T p1, p2;
@@ -379,12 +388,12 @@ __device__ __forceinline__ void synchrotron_coefficients(T ne, T th, T bg, T nu,
         p1 = pow(X, T(1.035));
         p2 = pow(X, T(1.2));
     }
-    const T fm = T(2.011) * exp(-p1 / T(4.7)) - cos(T(0.5) * X) * exp(-p2 / T(2.73)) -
-                 T(0.011) * exp(-X / T(47.2));
+    const T fm = T(2.011) * exp(-fq(p1, T(4.7))) - cos(T(0.5) * X) * exp(-fq(p2, T(2.73))) -
+                 T(0.011) * exp(-fq(X, T(47.2)));
     const T gm = T(1) - T(0.11) * log1p(T(0.035) * X);
     const T base = ne * T(kE * kE / (kMe * kC));
-    out[6] = base * nub * nub * sth2 / (nu * nu * nu) * fm * (k1 / k2 + T(6) * th);
-    out[7] = T(2) * base * nub * cth / (nu * nu) * (k0 / k2) * gm;
+    out[6] = base * nub * nub * sth2 / (nu * nu * nu) * fm * (fq(k1, k2) + T(6) * th);
+    out[7] = T(2) * base * nub * cth / (nu * nu) * fq(k0, k2) * gm;
 }
 
 // ---------------------------------------------------------------------------------------
