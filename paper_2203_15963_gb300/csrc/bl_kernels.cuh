@@ -1327,7 +1327,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
     const T dth = T(kPi) / T(nt);
     const T dph = twopi / T(np);
     if (im.interp == 0) {
-        int i = (int)floor(fq(log(r) - lrmin, dlr));
+        int i = (int)floor(fq(flog(r) - lrmin, dlr));
         int j = (int)floor(fq(th, dth));
         int k = (int)floor(fq(ph, dph));
         i = min(max(i, 0), nr - 1);
@@ -1357,7 +1357,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
         int i0, j0;
         T wr, wt;
         {
-            T fi = fq(log(r) - lrmin, dlr) - T(0.5);
+            T fi = fq(flog(r) - lrmin, dlr) - T(0.5);
             if (nr == 1) { i0 = 0; wr = T(0); }
             else {
                 fi = fi < T(0) ? T(0) : (fi > T(nr - 1) ? T(nr - 1) : fi);
@@ -1430,7 +1430,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
     }
     // spherical -> Cartesian KS vectors (Jacobian columns d x^a / d(r, theta, phi))
     T sph, cph;
-    sincos(ph, &sph, &cph);
+    fsincos_2pi(ph, &sph, &cph);
     const T J[3][3] = {{sth * cph, cth * (r * cph - a * sph), sth * (-r * sph - a * cph)},
                        {sth * sph, cth * (r * sph + a * cph), sth * (r * cph - a * sph)},
                        {cth, -r * sth, T(0)}};

@@ -33,6 +33,41 @@ __device__ __forceinline__ T fq(T a, T b) {
     else return a / b;
 }
 
+// exp, log, cube root, cos and sin-cos on the FP32 coefficient path through the hardware
+// approximations: __expf within 2 + 1.2 |x| ulp, __logf within 2^-21.4 absolute on [0.5, 2]
+// and 3 ulp elsewhere, the cube root as 2^(log2(x) / 3) from those two, __cosf and __sincosf
+// within about 2^-21 absolute for |x| <= pi (the arguments here are reduced to [-pi, pi] or
+// multiply terms that vanish where they are not). FP64: the libm functions.
+template <class T>
+__device__ __forceinline__ T fexp(T x) {
+    if constexpr (sizeof(T) == 4) return __expf(x);
+    else return exp(x);
+}
+template <class T>
+__device__ __forceinline__ T flog(T x) {
+    if constexpr (sizeof(T) == 4) return __logf(x);
+    else return log(x);
+}
+template <class T>
+__device__ __forceinline__ T fcbrt(T x) {   // x >= 0
+    if constexpr (sizeof(T) == 4) return __expf(__logf(x) * (1.0f / 3.0f));
+    else return cbrt(x);
+}
+template <class T>
+__device__ __forceinline__ T fcos(T x) {
+    if constexpr (sizeof(T) == 4) return __cosf(x);
+    else return cos(x);
+}
+// sin and cos of an angle in [0, 2 pi)
+template <class T>
+__device__ __forceinline__ void fsincos_2pi(T x, T* s, T* c) {
+    if constexpr (sizeof(T) == 4) {
+        __sincosf(x > 3.14159265f ? x - 6.28318531f : x, s, c);
+    } else {
+        sincos(x, s, c);
+    }
+}
+
 // CGS constants (CODATA 2018; IAU 2015 nominal solar mass).
 constexpr double kC = 2.99792458e10;
 constexpr double kE = 4.80320471e-10;
@@ -308,8 +343,8 @@ __device__ __forceinline__ void bessel_k012_scaled(T x, T& k0, T& k1, T& k2) {
     if (x <= T(2)) {
         const T t = T(0.5) * x;
         const T t2 = t * t;
-        const T lg = log(t);
-        const T ex = exp(x);
+        const T lg = flog(t);
+        const T ex = fexp(x);
         const T i0 = cyl_bessel_i0(x);
         const T i1 = cyl_bessel_i1(x);
         const T p0 = T(-0.57721566) + t2 * (T(0.42278420) + t2 * (T(0.23069756) + t2 * (T(0.03488590) +
@@ -355,16 +390,16 @@ __device__ __forceinline__ void synchrotron_coefficients(T ne, T th, T bg, T nu,
     bessel_k012_scaled(z, k0, k1, k2);
     if (sth > T(0)) {
         const T x = fq(nu, T(1.5) * nub * sth * th * th);
-        const T x13 = cbrt(x);
+        const T x13 = fcbrt(x);
         const T ix13 = fq(T(1), x13);
         const T ix23 = ix13 * ix13;
-        const T ex = exp(T(-1.8899) * x13);
+        const T ex = fexp(T(-1.8899) * x13);
         const T ii = T(2.5651) * (T(1) + T(1.92) * ix13 + T(0.9977) * ix23) * ex;
         const T iq = T(2.5651) * (T(1) + T(0.932) * ix13 + T(0.4998) * ix23) * ex;
         const T iv = (fq(T(1.8138), x) + T(3.423) * ix23 + T(0.02955) * rsqrt(x) + T(2.0377) * ix13) * ex;
         // n e^2 nu / (sqrt3 c) / K_2(z) = n e^2 nu / (sqrt3 c) exp(-z) / (exp(z) K_2) * exp(z)...
         // 1 / K_2(z) = exp(z) / k2 (k2 is scaled).
-        const T pre = ne * T(kE * kE / (1.7320508075688772 * kC)) * nu * fq(exp(z), k2);
+        const T pre = ne * T(kE * kE / (1.7320508075688772 * kC)) * nu * fq(fexp(z), k2);
         out[0] = pre * ii;
         out[1] = pre * iq;
         out[2] = pre * fq(T(4), T(3) * th) * fq(cth, sth) * iv;
@@ -381,15 +416,15 @@ __device__ __forceinline__ void synchrotron_coefficients(T ne, T th, T bg, T nu,
     // log X = -inf and both powers 0, as pow does)
     T p1, p2;
     if constexpr (sizeof(T) == 4) {
-        const T lX = log(X);
-        p1 = exp(T(1.035) * lX);
-        p2 = exp(T(1.2) * lX);
+        const T lX = flog(X);
+        p1 = fexp(T(1.035) * lX);
+        p2 = fexp(T(1.2) * lX);
     } else {
         p1 = pow(X, T(1.035));
         p2 = pow(X, T(1.2));
     }
-    const T fm = T(2.011) * exp(-fq(p1, T(4.7))) - cos(T(0.5) * X) * exp(-fq(p2, T(2.73))) -
-                 T(0.011) * exp(-fq(X, T(47.2)));
+    const T fm = T(2.011) * fexp(-fq(p1, T(4.7))) - fcos(T(0.5) * X) * fexp(-fq(p2, T(2.73))) -
+                 T(0.011) * fexp(-fq(X, T(47.2)));
     const T gm = T(1) - T(0.11) * log1p(T(0.035) * X);
     const T base = ne * T(kE * kE / (kMe * kC));
     out[6] = base * nub * nub * sth2 / (nu * nu * nu) * fm * (fq(k1, k2) + T(6) * th);
