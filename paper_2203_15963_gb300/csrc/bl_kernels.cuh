@@ -1293,11 +1293,11 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
     T cth = fq(x[2], r);
     cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
     const T th = acos(cth);
-    const T sth = sqrt(T(1) - cth * cth);
+    const T sth = fsqrt(T(1) - cth * cth);
     const T twopi = T(2.0 * kPi);
-    // atan2 lies in (-pi, pi] and atan(a / r) in (-pi/2, pi/2), so |ph| < 3 pi/2 and one wrap
+    // phi = arg(x + i y) - arg(r + i a) = arg((x + i y)(r - i a)), in (-pi, pi]; one wrap
     // puts it in [0, 2 pi) (fmod by 2 pi would return such a value unchanged)
-    T ph = atan2(x[1], x[0]) - atan(fq(a, r));
+    T ph = atan2(x[1] * r - x[0] * a, x[0] * r + x[1] * a);
     if (ph < T(0)) ph += twopi;
     if (ph >= twopi) ph -= twopi;
     const int nr = im.nr, nt = im.nt, np = im.nph;
@@ -1442,8 +1442,8 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
     }
     const T f = G.f;
     const T lv = G.l[1] * v[0] + G.l[2] * v[1] + G.l[3] * v[2];
-    const T un = sqrt(T(1) + v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + f * lv * lv);
-    P.u[0] = un * sqrt(T(1) + f);
+    const T un = fsqrt(T(1) + v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + f * lv * lv);
+    P.u[0] = un * fsqrt(T(1) + f);
     const T sh = fq(f, T(1) + f) * P.u[0];
 #pragma unroll
     for (int c = 0; c < 3; ++c) P.u[c + 1] = v[c] - G.l[c + 1] * sh;
@@ -1465,7 +1465,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
     if (!(th_e >= T(0.05))) return false;
     P.th = th_e;
     P.ne = fq(rho * ic<T>(im, kcNePre), T(1) + fq(T(1), rr));
-    P.bg = sqrt(P.bsq) * ic<T>(im, kcBgPre);
+    P.bg = fsqrt(P.bsq) * ic<T>(im, kcBgPre);
     P.rho = rho;
     P.p = p;
     P.binv = binv;
@@ -1798,7 +1798,7 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
                 const T kdu = kl[0] * P.u[0] + kl[1] * P.u[1] + kl[2] * P.u[2] + kl[3] * P.u[3];
                 const T kdb = kl[0] * P.b[0] + kl[1] * P.b[1] + kl[2] * P.b[2] + kl[3] * P.b[3];
                 const T nu_fl = nu_norm * (-kdu);
-                T cth = fq(kdb, (-kdu) * sqrt(P.bsq));
+                T cth = fq(kdb, (-kdu) * fsqrt(P.bsq));
                 cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
                 T co[8];
                 synchrotron_coefficients<T>(P.ne, P.th, P.bg, nu_fl, cth, co);
@@ -1981,7 +1981,7 @@ __global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __re
                 kdu = kl[0] * P.u[0] + kl[1] * P.u[1] + kl[2] * P.u[2] + kl[3] * P.u[3];
                 const T kdb = kl[0] * P.b[0] + kl[1] * P.b[1] + kl[2] * P.b[2] + kl[3] * P.b[3];
                 nu_fl = nu_norm * (-kdu);
-                cth = fq(kdb, (-kdu) * sqrt(P.bsq));
+                cth = fq(kdb, (-kdu) * fsqrt(P.bsq));
                 cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
             }
         }

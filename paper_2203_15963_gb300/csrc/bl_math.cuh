@@ -58,6 +58,18 @@ __device__ __forceinline__ T fcos(T x) {
     if constexpr (sizeof(T) == 4) return __cosf(x);
     else return cos(x);
 }
+// Square root on the FP32 coefficient path: the PTX approximate square root (sqrt.approx.f32,
+// a relative error of about 2^-23, sqrt(0) = 0); FP64: the IEEE square root.
+template <class T>
+__device__ __forceinline__ T fsqrt(T x) {
+    if constexpr (sizeof(T) == 4) {
+        float y;
+        asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    } else {
+        return sqrt(x);
+    }
+}
 // sin and cos of an angle in [0, 2 pi)
 template <class T>
 __device__ __forceinline__ void fsincos_2pi(T x, T* s, T* c) {
@@ -383,7 +395,7 @@ __device__ __forceinline__ void synchrotron_coefficients(T ne, T th, T bg, T nu,
     for (int q = 0; q < 8; ++q) out[q] = T(0);
     if (!(ne > T(0)) || !(th > T(0)) || !(bg > T(0))) return;
     const T sth2 = T(1) - cth * cth;
-    const T sth = sqrt(sth2 > T(0) ? sth2 : T(0));
+    const T sth = fsqrt(sth2 > T(0) ? sth2 : T(0));
     const T nub = T(kE / (2.0 * kPi * kMe * kC)) * bg;
     const T z = fq(T(1), th);
     T k0, k1, k2;
@@ -411,7 +423,7 @@ __device__ __forceinline__ void synchrotron_coefficients(T ne, T th, T bg, T nu,
         out[4] = out[1] * ibnu;
         out[5] = out[2] * ibnu;
     }
-    const T X = th * sqrt(fq(T(1.4142135623730951e3) * sth * nub, nu));
+    const T X = th * fsqrt(fq(T(1.4142135623730951e3) * sth * nub, nu));
     // X^1.035 and X^1.2: in FP32 as exponentials of one shared logarithm (X = 0 gives
     // log X = -inf and both powers 0, as pow does)
     T p1, p2;
