@@ -310,14 +310,17 @@ __device__ __forceinline__ void coh_axpy(const Coh<T>& base, const Coh<T>& n, co
                                          T h, Coh<T>& out) {
     T R[4][4], I[4][4];
     coh_unpack(n, R, I);
-    T AR[4][4], AI[4][4];   // A N
+    T AR[4][4], AI[4][4];   // A N (the diagonal of A I is not needed, and I_jj = 0)
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             T sr = T(0), si = T(0);
 #pragma unroll
-            for (int d = 0; d < 4; ++d) { sr += A[i][d] * R[d][j]; si += A[i][d] * I[d][j]; }
+            for (int d = 0; d < 4; ++d) {
+                sr += A[i][d] * R[d][j];
+                if (d != j) si += A[i][d] * I[d][j];
+            }
             AR[i][j] = sr;
             AI[i][j] = si;
         }
