@@ -1436,10 +1436,12 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
                        {cth, -r * sth, T(0)}};
     T v[3], B[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 2; ++c) {
         v[c] = J[c][0] * pv[2] + J[c][1] * pv[3] + J[c][2] * pv[4];
         B[c] = J[c][0] * pv[5] + J[c][1] * pv[6] + J[c][2] * pv[7];
     }
+    v[2] = J[2][0] * pv[2] + J[2][1] * pv[3];   // J[2][2] = d z / d phi = 0
+    B[2] = J[2][0] * pv[5] + J[2][1] * pv[6];
     const T f = G.f;
     const T lv = G.l[1] * v[0] + G.l[2] * v[1] + G.l[3] * v[2];
     const T un = fsqrt(T(1) + v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + f * lv * lv);

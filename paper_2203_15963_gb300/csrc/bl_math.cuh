@@ -256,17 +256,27 @@ __device__ __forceinline__ void transport_matrix(const T xv[3], const T klo[4], 
     const T Qxz = -lz * drx * ir - drz * x * iP + t2 * drz * lx;
     const T Qyz = -lz * dry * ir - drz * y * iP + t2 * drz * ly;
     const T fLp = f * Lp;
+    // C = (D + W) / 2 on and above the diagonal, (D - W) / 2 below, with
+    // D_ed = kdf l_e l_d + f (kdl_e l_d + l_e kdl_d) and
+    // W_ed = Lp (df_d l_e - df_e l_d) + f Lp Q_de + f (l_e M_d - l_d M_e),
+    // Q_de = d_d l_e - d_e l_d. The time index is written out (l_0 = 1, kdl_0 = df_0 = M_0 = 0,
+    // Q_0d = 0, W_ee = 0): IEEE arithmetic may not drop a product with a zero by itself.
     T C[4][4];
+    C[0][0] = cHalf * kdf;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
+    for (int d = 1; d < 4; ++d) {
+        const T D0 = kdf * l[d] + f * kdl[d];
+        const T W0 = Lp * df[d] + f * M[d];
+        C[0][d] = cHalf * (D0 + W0);
+        C[d][0] = cHalf * (D0 - W0);
+    }
 #pragma unroll
-        for (int d = e; d < 4; ++d) {
+    for (int e = 1; e < 4; ++e) {
+        C[e][e] = cHalf * (kdf * l[e] * l[e] + f * (c2 * (kdl[e] * l[e])));
+#pragma unroll
+        for (int d = e + 1; d < 4; ++d) {
             const T Ded = kdf * l[e] * l[d] + f * (kdl[e] * l[d] + l[e] * kdl[d]);
-            // Q_de = d_d l_e - d_e l_d (zero with a time index)
-            T Qde = c0;
-            if (e == 1 && d == 2) Qde = -Qxy;
-            if (e == 1 && d == 3) Qde = -Qxz;
-            if (e == 2 && d == 3) Qde = -Qyz;
+            const T Qde = (d == 2) ? -Qxy : (e == 1 ? -Qxz : -Qyz);
             const T Wed = Lp * (df[d] * l[e] - df[e] * l[d]) + fLp * Qde +
                           f * (l[e] * M[d] - l[d] * M[e]);
             C[e][d] = cHalf * (Ded + Wed);
@@ -500,16 +510,24 @@ __device__ __forceinline__ void stokes_step(const T c[8], const T s0[4], T dl, T
         }
         return;
     }
-    // Z = -M dl, z = J dl; infinity norm of the augmented matrix.
+    // Z = -M dl, z = J dl; infinity norm of the augmented matrix. M_02 = M_13 = M_20 = M_31 = 0
+    // and J_2 = 0 (no U terms) are left out of the sums below: IEEE arithmetic may not drop a
+    // product with a zero by itself.
+    auto mz = [](int i, int j) {
+        return (i == 0 && j == 2) || (i == 1 && j == 3) || (i == 2 && j == 0) || (i == 3 && j == 1);
+    };
     T Z[4][4], z[4];
     T nrm = T(0);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         T rs = T(0);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) { Z[i][j] = -M[i][j] * dl; rs += fabs(Z[i][j]); }
-        z[i] = J[i] * dl;
-        rs += fabs(z[i]);
+        for (int j = 0; j < 4; ++j) {
+            Z[i][j] = mz(i, j) ? T(0) : -M[i][j] * dl;
+            if (!mz(i, j)) rs += fabs(Z[i][j]);
+        }
+        z[i] = i == 2 ? T(0) : J[i] * dl;
+        if (i != 2) rs += fabs(z[i]);
         nrm = rs > nrm ? rs : nrm;
     }
     int s = 0;
@@ -522,8 +540,9 @@ __device__ __forceinline__ void stokes_step(const T c[8], const T s0[4], T dl, T
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) Z[i][j] *= sc;
-        z[i] *= sc;
+        for (int j = 0; j < 4; ++j)
+            if (!mz(i, j)) Z[i][j] *= sc;
+        if (i != 2) z[i] *= sc;
     }
     // Taylor degree: ||Z|| <= 1/2, truncation 2^-(m+1)/(m+1)! below the type's rounding.
     constexpr int m = sizeof(T) == 8 ? 13 : 8;
@@ -544,7 +563,8 @@ __device__ __forceinline__ void stokes_step(const T c[8], const T s0[4], T dl, T
                 for (int i = 0; i < 4; ++i) {
                     T acc = z[i];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc += Z[i][q] * t[q];
+                    for (int q = 0; q < 4; ++q)
+                        if (!mz(i, q)) acc += Z[i][q] * t[q];
                     tn[i] = v[i] + acc * ik;
                 }
 #pragma unroll
