@@ -23,7 +23,7 @@ using ::fabs;
 using ::rsqrt;
 using ::sqrt;
 
-struct df64 {
+struct __align__(8) df64 {
     float hi, lo;
     __host__ __device__ constexpr df64() : hi(0.0f), lo(0.0f) {}
     __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}

@@ -178,9 +178,19 @@ __device__ __forceinline__ void hidden_epilogue(FwdSmem& S, const float* bias) {
     for (int c = 0; c < 4; ++c) {
         float v[16];
         tc::tmem_ld16(tc::tmem_lane_addr(S.tmem, 16 * c), v);
+        // 8 consecutive columns of a row are one 16-byte row of a core matrix: one vector store
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-            tc::st_bf16(S.h, t, 16 * c + j, 64, silu(v[j] + (bias ? bias[16 * c + j] : 0.0f)));
+        for (int g = 0; g < 2; ++g) {
+            uint32_t w[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int j = 8 * g + 2 * p;
+                w[p] = tc::pack_bf16x2(silu(v[j] + (bias ? bias[16 * c + j] : 0.0f)),
+                                       silu(v[j + 1] + (bias ? bias[16 * c + j + 1] : 0.0f)));
+            }
+            *reinterpret_cast<uint4*>(S.h + tc::kmajor(t, 16 * c + 8 * g, 64)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
     }
 }
 
@@ -195,8 +205,10 @@ __device__ __forceinline__ void issue_barrier_then(FwdSmem& S) {
 __device__ __forceinline__ bool fwd_tile(FwdSmem& S, uint32_t& phase, const float f[3], bool valid,
                                          float o[7]) {
     const int t = threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) tc::st_bf16(S.x, t, k, 16, valid ? f[k] : 0.0f);
+    // columns 0-3 of the row: the three inputs and the constant 1 of the first-layer bias
+    *reinterpret_cast<uint2*>(S.x + tc::kmajor(t, 0, 16)) =
+        make_uint2(tc::pack_bf16x2(valid ? f[0] : 0.0f, valid ? f[1] : 0.0f),
+                   tc::pack_bf16x2(valid ? f[2] : 0.0f, 1.0f));
     issue_barrier_then(S);
     if (t == 0) {
         tc::fence_after_sync();

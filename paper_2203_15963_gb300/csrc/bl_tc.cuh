@@ -31,6 +31,12 @@ __device__ __forceinline__ void st_bf16(unsigned char* tile, int r, int k, int K
     *reinterpret_cast<__nv_bfloat16*>(tile + kmajor(r, k, K)) = __float2bfloat16_rn(v);
 }
 
+// two floats rounded to bf16 (nearest even) and packed, a in the low half (the lower column)
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
 // Shared-memory matrix descriptor: start address, leading / stride byte offsets (all >> 4),
 // descriptor version 1 (bits 46-47), base offset 0, no swizzle (bits 61-63 = 0).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
