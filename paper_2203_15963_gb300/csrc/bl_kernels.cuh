@@ -1992,7 +1992,7 @@ __global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __re
                                                   samp ? nu_fl : 1.0f, samp ? cth : 0.0f);
         const bool use = samp && mi.ok && P.ne > T(0);
         float o[7];
-        tc_ok = mlp::fwd_tile(S, phase, mi.f, use, o);
+        tc_ok = mlp::fwd_tile<true>(S, phase, mi.f, use, o);
         if (!tc_ok) break;
         // ---- phase B: Stokes step at this sample
         if (samp) {

@@ -31,6 +31,15 @@ constexpr float kLxLo = -3.0f, kLxHi = 6.0f, kLtLo = -1.0f, kLtHi = 2.0f;
 constexpr long long kWaitCycles = 1ll << 31;   // ~1 s at 2 GHz
 
 __device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+// z sigma(z) = z/2 (1 + tanh(z/2)) with the hardware tanh (relative error about 2^-11, below
+// the bf16 rounding of the stored activation, 2^-9): one special-function operation instead
+// of two. Inference inside the fused transfer only; training keeps silu above.
+__device__ __forceinline__ float silu_tanh(float z) {
+    const float hz = 0.5f * z;
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(hz));
+    return fmaf(hz, t, hz);
+}
 __device__ __forceinline__ float silu_grad(float z) {
     const float s = __fdividef(1.0f, 1.0f + __expf(-z));
     return s * (1.0f + z * (1.0f - s));
@@ -172,7 +181,9 @@ __device__ __forceinline__ bool cta_wait(FwdSmem& S, uint32_t& phase) {
 
 // hidden layer epilogue: 64 accumulator columns of this thread's row (+ bias), SiLU, BF16
 // row of the next A operand
+template <bool kTanh>
 __device__ __forceinline__ void hidden_epilogue(FwdSmem& S, const float* bias) {
+    auto act = [](float z) { return kTanh ? silu_tanh(z) : silu(z); };
     const int t = threadIdx.x;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -185,8 +196,8 @@ __device__ __forceinline__ void hidden_epilogue(FwdSmem& S, const float* bias) {
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
                 const int j = 8 * g + 2 * p;
-                w[p] = tc::pack_bf16x2(silu(v[j] + (bias ? bias[16 * c + j] : 0.0f)),
-                                       silu(v[j + 1] + (bias ? bias[16 * c + j + 1] : 0.0f)));
+                w[p] = tc::pack_bf16x2(act(v[j] + (bias ? bias[16 * c + j] : 0.0f)),
+                                       act(v[j + 1] + (bias ? bias[16 * c + j + 1] : 0.0f)));
             }
             *reinterpret_cast<uint4*>(S.h + tc::kmajor(t, 16 * c + 8 * g, 64)) =
                 make_uint4(w[0], w[1], w[2], w[3]);
@@ -201,7 +212,10 @@ __device__ __forceinline__ void issue_barrier_then(FwdSmem& S) {
 }
 
 // Forward pass of this thread's sample (f[3]; rows whose thread passes valid = false are
-// computed on zero inputs and ignored). Returns false if a tensor-core wait timed out.
+// computed on zero inputs and ignored; a tile without a valid row issues no MMA and leaves o
+// at zero). kTanh selects the hardware-tanh activation. Returns false if a tensor-core wait
+// timed out.
+template <bool kTanh = false>
 __device__ __forceinline__ bool fwd_tile(FwdSmem& S, uint32_t& phase, const float f[3], bool valid,
                                          float o[7]) {
     const int t = threadIdx.x;
@@ -209,14 +223,21 @@ __device__ __forceinline__ bool fwd_tile(FwdSmem& S, uint32_t& phase, const floa
     *reinterpret_cast<uint2*>(S.x + tc::kmajor(t, 0, 16)) =
         make_uint2(tc::pack_bf16x2(valid ? f[0] : 0.0f, valid ? f[1] : 0.0f),
                    tc::pack_bf16x2(valid ? f[2] : 0.0f, 1.0f));
-    issue_barrier_then(S);
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    if (!__syncthreads_or(valid)) {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int k = 0; k < kOut; ++k) o[k] = 0.0f;
+        return true;
+    }
     if (t == 0) {
         tc::fence_after_sync();
         tc::gemm_bf16(S.tmem, S.x, S.w1, 64, 16);
         tc::mma_commit(&S.bar);
     }
     if (!cta_wait(S, phase)) return false;
-    hidden_epilogue(S, nullptr);                 // first-layer bias is in W1
+    hidden_epilogue<kTanh>(S, nullptr);          // first-layer bias is in W1
     issue_barrier_then(S);
     if (t == 0) {
         tc::fence_after_sync();
@@ -224,7 +245,7 @@ __device__ __forceinline__ bool fwd_tile(FwdSmem& S, uint32_t& phase, const floa
         tc::mma_commit(&S.bar);
     }
     if (!cta_wait(S, phase)) return false;
-    hidden_epilogue(S, S.b2);
+    hidden_epilogue<kTanh>(S, S.b2);
     issue_barrier_then(S);
     if (t == 0) {
         tc::fence_after_sync();
