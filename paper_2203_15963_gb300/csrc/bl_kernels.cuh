@@ -769,8 +769,9 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                     for (int c = 0; c < 8; ++c)
                         if (c != 4) acc[c].first(a0, KX(0, c));
                 }
+                // the last row's second coefficient (b_2 of the fifth-order weights) is zero
 #pragma unroll 1
-                for (int j = 1; j < st; ++j) {
+                for (int j = st == 6 ? 2 : 1; j < st; ++j) {
                     const G aj = DPCoef<G>::a(st, j);
 #pragma unroll
                     for (int c = 0; c < 8; ++c)
