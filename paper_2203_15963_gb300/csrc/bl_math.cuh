@@ -35,7 +35,7 @@ __device__ __forceinline__ T fq(T a, T b) {
 
 // exp, log, cube root, cos and sin-cos on the FP32 coefficient path through the hardware
 // approximations: __expf within 2 + 1.2 |x| ulp, __logf within 2^-21.4 absolute on [0.5, 2]
-// and 3 ulp elsewhere, the cube root as 2^(log2(x) / 3) from those two, __cosf and __sincosf
+// and 3 ulp elsewhere, the cube root as exp(log(x) / 3) from those two, __cosf and __sincosf
 // within about 2^-21 absolute for |x| <= pi (the arguments here are reduced to [-pi, pi] or
 // multiply terms that vanish where they are not). FP64: the libm functions.
 template <class T>
@@ -59,7 +59,8 @@ __device__ __forceinline__ T fcos(T x) {
     else return cos(x);
 }
 // Square root on the FP32 coefficient path: the PTX approximate square root (sqrt.approx.f32,
-// a relative error of about 2^-23, sqrt(0) = 0); FP64: the IEEE square root.
+// within about one ulp, sqrt(0) = 0, without the IEEE form's correction steps); FP64: the IEEE
+// square root.
 template <class T>
 __device__ __forceinline__ T fsqrt(T x) {
     if constexpr (sizeof(T) == 4) {
