@@ -258,6 +258,18 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
     d.aux = o.aux;
     d.ray_offset = offset;
     d.n_rays = (int64_t)c.n * c.n;
+    d.ilv = 0;
+}
+
+// Queue the rays of a batch of equal images interleaved (see setup_ray) when every image has
+// the same number of rays, a whole number of kIlvBlock-ray blocks, at consecutive offsets.
+// Scheduling only: each ray's result is the same in either queue order.
+void set_interleave(std::vector<bl::ImageDesc>& d) {
+    const size_t n = d.size();
+    bool eq = n > 1 && d[0].n_rays > 0 && d[0].n_rays % bl::kIlvBlock == 0;
+    for (size_t q = 0; q < n && eq; ++q)
+        eq = d[q].n_rays == d[0].n_rays && d[q].ray_offset == (int64_t)q * d[0].n_rays;
+    for (auto& x : d) x.ilv = eq ? (int32_t)n : 0;
 }
 
 // Dynamic shared memory of a geodesic-kernel CTA: the stage derivatives, 7 stages x 7
@@ -601,6 +613,7 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
                   transfer ? freqs[q] : 1.0, outs[q], off);
         off += (int64_t)cams[q].n * cams[q].n;
     }
+    set_interleave(descs);
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = (char*)workspace;
     bool own = false;
@@ -1218,6 +1231,7 @@ int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_m
         if (P->descs[q].aux) P->feat |= bl::kFAux;
         off += (int64_t)cams[q].n * cams[q].n;
     }
+    set_interleave(P->descs);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMalloc((void**)&P->ws, P->L.total);
     if (e != cudaSuccess) {

@@ -16,6 +16,10 @@ template <> struct RecStride<float> { static constexpr int v = 16; };    // 64 B
 constexpr int kChunk = 32;          // records per pool chunk
 constexpr int kMaxChunks = 128;     // chunks per ray -> at most 4096 samples per ray
 
+// Rays of the images of a batch are queued in blocks of this many consecutive rays of one
+// image when the batch interleaves its images.
+constexpr int64_t kIlvBlock = 256;
+
 struct ImageDesc {
     // camera (Sec. 2.1)
     double cam_r, cam_th, cam_ph, u_p[3], k_p[3], width, psi;
@@ -24,7 +28,9 @@ struct ImageDesc {
     double mass, spin, r_in_over_rhor, tol_abs, tol_rel, ds_max, h0_frac;
     int64_t max_steps;
     int32_t flat, precision;
-    int32_t integrator, pad3_;
+    int32_t integrator;
+    int32_t ilv;            // > 1: the batch's rays are queued interleaved over ilv images
+                            // in blocks of kIlvBlock rays (same value in every descriptor)
     double f_step;
     // grid and plasma (Secs. 2.4-2.5)
     const float* prim;

@@ -155,7 +155,11 @@ __device__ __forceinline__ int64_t ray_pixel(const ImageDesc& im, int64_t p, int
 }
 
 // Image, pixel and output index of global ray `ray`: from the device block list when there is
-// one (adaptive levels), else from the images' consecutive ray ranges.
+// one (adaptive levels); for a batch of equal images, from the interleaved queue (blocks of
+// kIlvBlock rays taken from the images in turn: the last rays handed out are then every image's
+// last blocks, which in Morton order lie at the image corners, rather than one image's last
+// quarter, which holds part of the photon ring and its longest rays); else from the images'
+// consecutive ray ranges.
 __device__ __forceinline__ void setup_ray(const ImageDesc* imgs, int n_images, const BlockSource& bs,
                                           int64_t ray, int& q, int64_t& opix, int& i, int& j) {
     if (bs.entries) {
@@ -167,6 +171,11 @@ __device__ __forceinline__ void setup_ray(const ImageDesc* imgs, int n_images, c
         i = bs.entries[3 * blk + 1] * B + r % B;
         j = bs.entries[3 * blk + 2] * B + r / B;
         opix = ray;
+    } else if (imgs[0].ilv > 1) {
+        // equal images interleaved: block b of the queue is block b / ilv of image b % ilv
+        const int64_t b = ray / kIlvBlock, nb = imgs[0].ilv;
+        q = (int)(b % nb);
+        opix = ray_pixel(imgs[q], (b / nb) * kIlvBlock + (ray - b * kIlvBlock), i, j);
     } else {
         q = find_image(imgs, n_images, ray);
         opix = ray_pixel(imgs[q], ray - imgs[q].ray_offset, i, j);
