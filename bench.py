@@ -38,8 +38,9 @@ GRID = (256, 128, 128)
 FLOP64_PER_ATTEMPT = 1214
 # dram__bytes_read.sum + dram__bytes_write.sum of geodesic_kernel<float, df64> per DP attempt
 # from one ncu capture of the a = 0.94, i = 60 deg image of this workload at 256^2; None
-# whenever the kernel has changed since the capture
-GEO_DF64_DRAM_BYTES_PER_ATTEMPT = 147.7
+# whenever the kernel has changed since the capture (the last capture, 147.7 B, predates the
+# interleaved ray queue of image batches)
+GEO_DF64_DRAM_BYTES_PER_ATTEMPT = None
 # FP32 flops per transfer sample (2 transport matrices, predictor-corrector, sampling,
 # plasma, coefficients, fluid frame, Stokes step)
 FLOP32_PER_SAMPLE = 3300
