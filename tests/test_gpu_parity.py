@@ -310,6 +310,26 @@ def test_batch_equals_single_launches():
         assert torch.equal(one[0]["steps"], outs[q]["steps"])
 
 
+def test_interleaved_batch_equals_single_launches():
+    """Equal images on cell-layout grids are queued interleaved in 256-ray blocks; each image's
+    outputs equal, bit for bit, those of tracing it alone (one image keeps the consecutive
+    queue): the queue order only schedules the rays."""
+    cam, met, gp, prim = C1
+    cells, gpc = images.pack_grid(_gpu(prim), gp)
+    cams = [S.Camera(theta=math.radians(t), n=cam.n) for t in (17.0, 60.0, 90.0)]
+    mets = [S.Metric(**{**met.__dict__, "spin": s, "precision": native.BL_PREC_FAST})
+            for s in (0.9, 0.5, 0.0)]
+    freqs = [230e9, 86e9, 345e9]
+    rc, outs = images.trace_images(cams, mets, [gpc] * 3, [cells] * 3, freqs, samples=True)
+    assert rc == 0
+    for q in range(3):
+        rc1, one = images.trace_images([cams[q]], [mets[q]], [gpc], [cells], [freqs[q]],
+                                       samples=True)
+        assert rc1 == 0
+        for k in ("stokes", "steps", "status", "samples"):
+            assert torch.equal(one[0][k], outs[q][k]), (q, k)
+
+
 def test_host_buffer_entry_matches_device_entry():
     cam, met, gp, prim = C1
     met = S.Metric(**{**met.__dict__, "precision": 1})
