@@ -296,7 +296,7 @@ def build_workload_host():
             cams.append(S.Camera(theta=math.radians(inc), n=N_PIX))
             mets.append(S.Metric(spin=spin))
             gps.append(gp)
-    return dict(cams=cams, mets=mets, gps=gps, prims_host=prims_host)
+    return dict(gp=gp, cams=cams, mets=mets, gps=gps, prims_host=prims_host)
 
 
 def main():
