@@ -74,6 +74,7 @@ def lib():
         L.ora_metric_sks.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _D]
         L.ora_christoffel.argtypes = [_D, C.c_double, C.c_double, C.c_int, _D]
         L.ora_geodesic_rhs.argtypes = [_D, C.c_double, C.c_double, C.c_int, _D]
+        L.ora_set_rhs_perturbation.argtypes = [C.c_int32]
         L.ora_dp_tableau.argtypes = [_D] * 5
         L.ora_r_of_x.argtypes = [_D, C.c_double]
         L.ora_r_of_x.restype = C.c_double
@@ -159,6 +160,12 @@ def christoffel(x, mass, spin, flat=0):
     g = _f64(64)
     lib().ora_christoffel(_p(x), mass, spin, flat, _p(g))
     return g.reshape(4, 4, 4)
+
+
+def set_rhs_perturbation(ulps: int) -> None:
+    """Test knob: every later oracle geodesic right-hand side is scaled by (1 + ulps 2^-52);
+    0 switches it off."""
+    lib().ora_set_rhs_perturbation(int(ulps))
 
 
 def geodesic_rhs(y, mass, spin, flat=0):

@@ -98,6 +98,13 @@ void christoffel(const double x[4], double m, double a, int flat, double gam[64]
             }
 }
 
+// Test knob, off (0) unless a test sets it: every right-hand-side component is scaled by
+// (1 + k 2^-52), a perturbation of about k ulps, which shows how far the adaptive step
+// control carries rounding-level differences to the end of a geodesic.
+static int g_rhs_perturb_ulps = 0;
+
+void set_rhs_perturbation(int ulps) { g_rhs_perturb_ulps = ulps; }
+
 // Eq. (geodesic) in Hamiltonian form with H = 1/2 g^{ab} k_a k_b:
 // dx^a/dl = dH/dk_a = g^{ab} k_b,  dk_t/dl = 0,  dk_a/dl = -dH/dx^a.
 void geodesic_rhs(const double y[8], double m, double a, int flat, double dy[8]) {
@@ -117,6 +124,10 @@ void geodesic_rhs(const double y[8], double m, double a, int flat, double dy[8])
     }
     dy[4] = 0.0;
     for (int i = 0; i < 3; ++i) dy[5 + i] = -h.d[i];
+    if (g_rhs_perturb_ulps != 0) {
+        const double s = 1.0 + g_rhs_perturb_ulps * 0x1p-52;
+        for (int i = 0; i < 8; ++i) dy[i] *= s;
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -614,6 +625,7 @@ void ora_metric_sks(double r, double theta, double mass, double spin, double g_l
 void ora_christoffel(const double x[4], double mass, double spin, int flat, double gam[64]) {
     ora::christoffel(x, mass, spin, flat, gam);
 }
+void ora_set_rhs_perturbation(int32_t ulps) { ora::set_rhs_perturbation(ulps); }
 void ora_geodesic_rhs(const double y[8], double mass, double spin, int flat, double dy[8]) {
     ora::geodesic_rhs(y, mass, spin, flat, dy);
 }

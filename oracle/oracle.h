@@ -13,8 +13,7 @@
  *     matrix (scaling and squaring + Taylor series, long double);
  *   - modified Bessel functions come from trapezoid quadrature of their integral form.
  *
- * Readings of points the paper leaves open are listed in the repository's design notes and
- * restated next to the code that takes them.
+ * Each reading of a point the paper leaves open is stated next to the code that takes it.
  *
  * Parity unpinned: the polarized synchrotron fitting functions (the paper cites them without
  * printing them) are pinned only at their limits, by Kirchhoff's law, by symmetry, and (total
@@ -77,6 +76,9 @@ void ora_metric_cks(const double x[4], double mass, double spin, int flat,
 void ora_metric_sks(double r, double theta, double mass, double spin, double g_lo[16]);
 void ora_christoffel(const double x[4], double mass, double spin, int flat, double gam[64]);
 void ora_geodesic_rhs(const double y[8], double mass, double spin, int flat, double dy[8]);
+/* Test knob: scale every geodesic right-hand-side component by (1 + ulps 2^-52) in all later
+ * oracle calls of this process (0, the default, switches it off). */
+void ora_set_rhs_perturbation(int32_t ulps);
 void ora_dp_tableau(double a[49], double b5[7], double b4[7], double bmid[7], double c[7]);
 double ora_r_of_x(const double x[4], double spin);
 

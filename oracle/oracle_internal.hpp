@@ -66,6 +66,7 @@ void metric_cks(const double x[4], double m, double a, int flat, double glo[16],
 void metric_lo_deriv(const double x[4], double m, double a, int flat, double dg[64]);
 void christoffel(const double x[4], double m, double a, int flat, double gam[64]);
 void geodesic_rhs(const double y[8], double m, double a, int flat, double dy[8]);
+void set_rhs_perturbation(int ulps);
 void metric_sks(double r, double th, double m, double a, double g[16]);
 void sks_to_cks_point(double r, double th, double ph, double a, double x[4]);
 void sks_jacobian(double r, double th, double ph, double a, double jac[9]);

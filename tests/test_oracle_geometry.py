@@ -378,3 +378,74 @@ def test_iyer_hansen_deflection():
     assert len(errs) == 37
     print("max deflection error", max(errs))
     assert max(errs) < 1e-5, max(errs)
+
+
+def _escaped_end_states(met, cam, pix):
+    out = []
+    for (i, j) in pix:
+        x, k, _, _, _ = O.camera_pixel(cam, met, i, j)
+        out.append(O.geodesic(met, cam.r, np.concatenate([x, k])))
+    return out
+
+
+def test_dp_step_count_and_error_scale_with_tolerance():
+    """Order of the adaptive Dormand-Prince integration (geodesics section, Table tab:dp): with
+    the error of the embedded pair O(h^5), the controller's steps scale as tol^(-1/5) and the
+    end-state error as tol. A tol = 1e-13 run is the reference for the others. An error
+    estimate of the wrong order, a wrong weight in either solution, or a norm that ignores a
+    component breaks one of these slopes."""
+    import dataclasses
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    import endpoints as E
+    cam = S.Camera(theta=math.radians(60.0), n=16)
+    pix = [(i, 8) for i in range(0, 16, 2)]
+    tols = [1e-7, 1e-8, 1e-9, 1e-10, 1e-11, 1e-13]
+    runs = {t: _escaped_end_states(dataclasses.replace(S.Metric(spin=0.9), tol_abs=t, tol_rel=t),
+                                   cam, pix) for t in tols}
+    ref = runs[1e-13]
+    esc = [q for q, r in enumerate(ref) if r["status"] == 2]
+    assert len(esc) >= 5
+    acc = {t: np.mean([runs[t][q]["accepted"] for q in esc]) for t in tols}
+    slope_n = np.polyfit(np.log10([1e-9, 1e-10, 1e-11, 1e-13]),
+                         np.log10([acc[t] for t in (1e-9, 1e-10, 1e-11, 1e-13)]), 1)[0]
+    assert -0.22 <= slope_n <= -0.18, slope_n
+    err = {}
+    for t in tols[:-1]:
+        assert all(runs[t][q]["status"] == 2 for q in esc)
+        err[t] = np.median([E.camera_sphere_error(runs[t][q]["end"], ref[q]["end"], 1.0, 0.9,
+                                                  cam.r) for q in esc])
+    slope_e = np.polyfit(np.log10(tols[:-1]), np.log10([err[t] for t in tols[:-1]]), 1)[0]
+    assert 0.85 <= slope_e <= 1.15, slope_e
+    assert 0.1 * 1e-8 <= err[1e-8] <= 10 * 1e-8, err[1e-8]
+
+
+def test_endpoint_sensitivity_to_one_ulp():
+    """How far the adaptive integration carries a rounding-level difference: the oracle
+    against itself with every right-hand side scaled by (1 + 2^-52), on the 32^2, a = 0.9,
+    i = 17 deg camera. Typical rays agree to rounding, but rays that graze the photon orbit
+    amplify it (geodesics diverge exponentially there), so a few per cent exceed 1e-10 --
+    no FP64 integration that rounds differently from the oracle (the GPU kernels among them)
+    can meet a 1e-10 endpoint bound on every ray. The GPU parity test bounds each ray by this
+    measured sensitivity instead."""
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    import endpoints as E
+    cam = S.Camera(theta=math.radians(17.0), n=32)
+    met = S.Metric(spin=0.9)
+    prim = np.zeros((8, 1, 1, 1), dtype=np.float32)
+    gp1 = S.GridParams(n_r=1, n_theta=1, n_phi=1)
+    a = O.trace(cam, met, gp1, prim, 230e9)
+    O.set_rhs_perturbation(1)
+    try:
+        b = O.trace(cam, met, gp1, prim, 230e9)
+    finally:
+        O.set_rhs_perturbation(0)
+    same = a["attempts"] == b["attempts"]
+    assert same.mean() >= 0.97
+    w = E.cut_free_error(b["end"][same], a["end"][same])
+    print("1-ulp sensitivity: median %.2e p99 %.2e max %.2e, above 1e-10: %.2f%%" % (
+        np.median(w), np.percentile(w, 99), w.max(), 100 * np.mean(w > 1e-10)))
+    assert np.median(w) < 1e-13
+    assert 0.002 <= np.mean(w > 1e-10) <= 0.1
+    assert w.max() < 1e-7

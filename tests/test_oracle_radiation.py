@@ -165,6 +165,50 @@ def test_emissivity_fits_vs_exact_quadrature(te, x):
     assert c[1] == pytest.approx(jq, rel=0.08, abs=0)
 
 
+def _circular_kernel(x):
+    """x K_1/3(x) + int_x^inf K_1/3(t) dt: the frequency shape of one ultra-relativistic
+    electron's circularly polarized synchrotron emission (Legg & Westfold 1968, ApJ 154, 499;
+    Melrose 1971), which enters at order cot(theta) / gamma relative to the total intensity."""
+    val, _ = integrate.quad(lambda t: special.kv(1.0 / 3.0, t), x, np.inf, limit=200)
+    return x * special.kv(1.0 / 3.0, x) + val
+
+
+def _exact_thermal_v(ne, te, b, nu, ct):
+    """Exact thermal circular emissivity: the thermal average of the single-electron kernel
+    (4 cot(theta) / (3 gamma)) (x K_1/3(x) + int_x^inf K_1/3) with the prefactor and
+    Maxwell-Juttner weight of _exact_thermal."""
+    st = math.sqrt(1 - ct * ct)
+    nub = E * b / (2 * math.pi * ME * C)
+    pre = math.sqrt(3) * E ** 3 * b * st / (4 * math.pi * ME * C ** 2)
+    k2 = special.kv(2, 1 / te)
+
+    def kern(g):
+        xc = nu / (1.5 * g * g * nub * st)
+        beta = math.sqrt(1 - 1 / (g * g))
+        return (ne * g * g * beta * math.exp(-g / te) / (te * k2) *
+                (4.0 * ct / st / (3.0 * g)) * _circular_kernel(xc))
+
+    gmax = 60 * te + 10
+    val, _ = integrate.quad(kern, 1.0 + 1e-9, gmax, limit=400, epsrel=1e-9)
+    return pre * val
+
+
+@pytest.mark.parametrize("te,x,ct", [(10.0, 3.0, 0.5), (10.0, 30.0, 0.5), (30.0, 300.0, 0.5),
+                                     (5.0, 10.0, -0.3), (20.0, 1.0, 0.8), (50.0, 1000.0, 0.2)])
+def test_circular_emissivity_fit_vs_exact_quadrature(te, x, ct):
+    """j_V of the coefficient fits (cot(theta) form, Sec. 2.5) against quadrature of the exact
+    thermal circular emissivity integral: sign (odd in cos(theta_B)) and size agree to the
+    fit's accuracy; a dropped term of the shape function, a cos for the cot, or a lost 4/3
+    fails it."""
+    ne, b = 1e6, 20.0
+    st = math.sqrt(1 - ct * ct)
+    nub = E * b / (2 * math.pi * ME * C)
+    nu = x * 1.5 * nub * st * te * te
+    c = O.coefficients(ne, te, b, nu, ct)
+    jv = _exact_thermal_v(ne, te, b, nu, ct)
+    assert c[2] == pytest.approx(jv, rel=0.02, abs=0)
+
+
 def test_rotativities_high_frequency_limit():
     ne, te, b, ct = 1e6, 8.0, 20.0, 0.6
     st = math.sqrt(1 - ct * ct)
