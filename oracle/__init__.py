@@ -163,8 +163,8 @@ def christoffel(x, mass, spin, flat=0):
 
 
 def set_rhs_perturbation(ulps: int) -> None:
-    """Test knob: every later oracle geodesic right-hand side is scaled by (1 + ulps 2^-52);
-    0 switches it off."""
+    """Test knob: component i of every later oracle geodesic right-hand side is scaled by
+    (1 + (-1)^i ulps 2^-52); 0 switches it off."""
     lib().ora_set_rhs_perturbation(int(ulps))
 
 

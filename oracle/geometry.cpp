@@ -98,9 +98,10 @@ void christoffel(const double x[4], double m, double a, int flat, double gam[64]
             }
 }
 
-// Test knob, off (0) unless a test sets it: every right-hand-side component is scaled by
-// (1 + k 2^-52), a perturbation of about k ulps, which shows how far the adaptive step
-// control carries rounding-level differences to the end of a geodesic.
+// Test knob, off (0) unless a test sets it: right-hand-side component i is scaled by
+// (1 + (-1)^i k 2^-52), a perturbation of about k ulps (alternating in sign: a common factor
+// would only rescale the affine parameter, which leaves the path unchanged), which shows how
+// far the adaptive step control carries rounding-level differences to the end of a geodesic.
 static int g_rhs_perturb_ulps = 0;
 
 void set_rhs_perturbation(int ulps) { g_rhs_perturb_ulps = ulps; }
@@ -125,8 +126,8 @@ void geodesic_rhs(const double y[8], double m, double a, int flat, double dy[8])
     dy[4] = 0.0;
     for (int i = 0; i < 3; ++i) dy[5 + i] = -h.d[i];
     if (g_rhs_perturb_ulps != 0) {
-        const double s = 1.0 + g_rhs_perturb_ulps * 0x1p-52;
-        for (int i = 0; i < 8; ++i) dy[i] *= s;
+        for (int i = 0; i < 8; ++i)
+            dy[i] *= 1.0 + ((i & 1) ? -1.0 : 1.0) * g_rhs_perturb_ulps * 0x1p-52;
     }
 }
 

@@ -76,8 +76,8 @@ void ora_metric_cks(const double x[4], double mass, double spin, int flat,
 void ora_metric_sks(double r, double theta, double mass, double spin, double g_lo[16]);
 void ora_christoffel(const double x[4], double mass, double spin, int flat, double gam[64]);
 void ora_geodesic_rhs(const double y[8], double mass, double spin, int flat, double dy[8]);
-/* Test knob: scale every geodesic right-hand-side component by (1 + ulps 2^-52) in all later
- * oracle calls of this process (0, the default, switches it off). */
+/* Test knob: scale geodesic right-hand-side component i by (1 + (-1)^i ulps 2^-52) in all
+ * later oracle calls of this process (0, the default, switches it off). */
 void ora_set_rhs_perturbation(int32_t ulps);
 void ora_dp_tableau(double a[49], double b5[7], double b4[7], double bmid[7], double c[7]);
 double ora_r_of_x(const double x[4], double spin);

@@ -64,18 +64,19 @@ void coefficients(double ne, double th_e, double bg, double nu, double cth, doub
     double k2x = bessel_kx(2.0, z);   // exp(z) K_2(z)
     double k1x = bessel_kx(1.0, z);
     double k0x = bessel_kx(0.0, z);
-    // 1 / K_2(z) = exp(z) / (exp(z) K_2(z))
-    double inv_k2 = std::exp(z) / k2x;
     if (sth > 0.0) {
         double nucp = 1.5 * nub * sth * th_e * th_e;
         double x = nu / nucp;
         double x13 = std::cbrt(x);
         double x23 = x13 * x13;
-        double ex = std::exp(-1.8899 * x13);
+        // 1 / K_2(z) = exp(z) / (exp(z) K_2(z)); exp(z) joins the shape functions' factor
+        // exp(-1.8899 x^1/3) in one exponential, which stays finite (and underflows to 0)
+        // for cold plasma where exp(z) = exp(1 / Theta_e) alone overflows
+        double ex = std::exp(z - 1.8899 * x13);
         double ii = 2.5651 * (1.0 + 1.92 / x13 + 0.9977 / x23) * ex;
         double iq = 2.5651 * (1.0 + 0.932 / x13 + 0.4998 / x23) * ex;
         double iv = (1.8138 / x + 3.423 / x23 + 0.02955 / std::sqrt(x) + 2.0377 / x13) * ex;
-        double pre = ne * E_CHARGE * E_CHARGE * nu / (std::sqrt(3.0) * C_LIGHT) * inv_k2;
+        double pre = ne * E_CHARGE * E_CHARGE * nu / (std::sqrt(3.0) * C_LIGHT) / k2x;
         out[0] = pre * ii;
         out[1] = pre * iq;
         out[2] = pre * 4.0 / (3.0 * th_e) * (cth / sth) * iv;
@@ -182,7 +183,8 @@ static int32_t sample_snapshot(const ora_grid* gr, const float* data, double a, 
 
 // ---------------------------------------------------------------------------------------
 // Plasma state at a sample point (Secs. 2 and 2.5). Returns 1 if the point carries plasma
-// (inside the grid, sigma <= sigma_cut, positive density, pressure, field and Theta_e >= 0.05).
+// (inside the grid, finite interpolated data, sigma <= sigma_cut, positive density, pressure
+// and field: the sigma cut is the only data cut of the paper's default set-up).
 // u, b are contravariant CKS components.
 // ---------------------------------------------------------------------------------------
 int32_t plasma(const ora_grid* gr, const ora_metric* met, const double x[4], double u[4],
@@ -190,6 +192,10 @@ int32_t plasma(const ora_grid* gr, const ora_metric* met, const double x[4], dou
     const double m = met->mass, a = met->spin;
     double prim[8];
     if (!sample_grid(gr, a, x, prim)) return 0;
+    // non-finite data carry no plasma (the paper does not treat them; read like a sample
+    // outside the grid)
+    for (int q = 0; q < 8; ++q)
+        if (!std::isfinite(prim[q])) return 0;
     double r, th, ph;
     cks_to_sks_point(x, a, &r, &th, &ph);
     double rho = prim[0], ugas = prim[1];
@@ -224,7 +230,6 @@ int32_t plasma(const ora_grid* gr, const ora_metric* met, const double x[4], dou
     double ti_te = (gr->r_high + b2 * gr->r_low) / (1.0 + b2);
     double rr = gr->ne_over_ni;
     double te = gr->mu * M_PROTON / M_ELECTRON * (p / rho) * (rr + 1.0) / (rr + ti_te);
-    if (!(te >= 0.05)) return 0;
     *th_e = te;
     *ne = rho * gr->rho_unit_cgs / (gr->mu * M_PROTON) / (1.0 + 1.0 / rr);
     *bg = std::sqrt(bsq) * C_LIGHT * std::sqrt(4.0 * M_PI * gr->rho_unit_cgs);

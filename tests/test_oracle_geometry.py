@@ -422,7 +422,8 @@ def test_dp_step_count_and_error_scale_with_tolerance():
 
 def test_endpoint_sensitivity_to_one_ulp():
     """How far the adaptive integration carries a rounding-level difference: the oracle
-    against itself with every right-hand side scaled by (1 + 2^-52), on the 32^2, a = 0.9,
+    against itself with its right-hand side perturbed by one ulp (component i scaled by
+    1 + (-1)^i 2^-52), on the 32^2, a = 0.9,
     i = 17 deg camera. Typical rays agree to rounding, but rays that graze the photon orbit
     amplify it (geodesics diverge exponentially there), so a few per cent exceed 1e-10 --
     no FP64 integration that rounds differently from the oracle (the GPU kernels among them)
