@@ -7,11 +7,30 @@ synthetic torus sampled on a 256x128x128 spherical Kerr-Schild grid (one grid pe
 in one batched persistent launch pair. Inputs stay resident in HBM; the three grids (3 x 134 MB)
 plus the per-sample records exceed the 129 MB L2, so no explicit flush is needed between steps.
 
-One JSON line is printed by rank 0. See the design notes for the roofline arithmetic.
+The headline is the FP64 form (geodesics, sampling, plasma, coefficients and transfer all in
+IEEE double, the arithmetic of the paper's C++ code); the mixed (FP64 geodesics, FP32
+transfer) and fast (double-float geodesics, FP32 transfer) forms are secondary lines, each
+with its image error against the CPU oracle on a seeded pixel sample.
+
+Rooflines: achieved = algorithmic flops per launch / the kernel's CUDA-event time, against
+the device's own peak measured by blacklight_measure_peaks (FMA-chain probes for FP64, FP32
+and the double-float arithmetic), with the SM clock sampled while the probes run.
+  - geodesic kernel: FLOP64_PER_ATTEMPT per Dormand-Prince attempt (hand count below);
+  - transfer kernel: FLOP_PER_SAMPLE per sample, the method's arithmetic per sample as the
+    FP32 transfer kernel executes it (ncu thread-level FFMA x 2 + FADD + FMUL per sample; its
+    special functions are single hardware instructions, counted apart in SFU_PER_SAMPLE). The
+    FP64 kernel runs the same source, so the same count is its algorithmic work; its FP64
+    special-function sequences are overhead on top of it.
+DRAM traffic per launch comes from one ncu capture per kernel (per-unit figure x the units of
+the launch) and is reported only while the kernel sources still hash to those captured.
+
+Rank 0 prints one JSON line. Under torchrun each rank traces its own share of the images
+(weak scaling, see `rank_images`); there is no collective on the data path.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -30,34 +49,40 @@ INCS = (17.0, 60.0, 90.0)
 FREQ = 230e9
 N_PIX = 256
 GRID = (256, 128, 128)
-# Algorithmic arithmetic per unit of work (operation counts of the method, see design notes):
-# FP64 flops per Dormand-Prince attempt: 6 right-hand sides of 114 flops (81 products, 30
-# sums, 2 reciprocal square roots, 1 reciprocal in the form with d_c(l.k) taken directly),
-# 6 stage combinations (384), the embedded error estimate (96) and its norm and the step
-# control (50).
+# FP64 flops per Dormand-Prince attempt, counted by hand from the method as implemented: 6
+# right-hand sides of 114 flops (81 products, 30 sums, 2 reciprocal square roots, 1
+# reciprocal, with d_c(l.k) formed directly), 6 stage combinations (384), the embedded error
+# estimate (96) and its norm and the step control (50).
 FLOP64_PER_ATTEMPT = 1214
-# dram__bytes_read.sum + dram__bytes_write.sum of geodesic_kernel<float, df64> per DP attempt
-# from one ncu capture of the a = 0.94, i = 60 deg image of this workload at 256^2; None
-# whenever the kernel has changed since the capture (the last capture, 147.7 B, predates the
-# interleaved ray queue of image batches)
-GEO_DF64_DRAM_BYTES_PER_ATTEMPT = None
-# FP32 flops per transfer sample (2 transport matrices, predictor-corrector, sampling,
-# plasma, coefficients, fluid frame, Stokes step)
-FLOP32_PER_SAMPLE = 3300
-# Nominal peaks from the pool's profiling recipe (no measured FP64/FP32 peak is available):
-# FP64 1.25 TFLOP/s; FP32 = 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
-PEAK_FP64_TFLOPS = 1.25
-# Double-float: FP32 instructions per emulated FP64 flop as implemented -- a product 7 (4 inside
-# a chain of products), a sum 11, a scaling by a power of two 2, a reciprocal ~9 and a
-# reciprocal square root ~12 (hardware seed and one second-order step), a term of a
-# compensated sum of products 12 (first product 4, a plain term 7, the final renormalisation
-# 3, y + h sum 15), an FP32 flop 1. On the attempt's mix (right-hand sides 719 instructions for
-# 114 flops, stage combinations 2352 for 384, error estimate 576 for 96, norm and control ~60
-# for 50) that is 7302 instructions for 1214 flops, 6.0 per flop. The emulated peak is the
-# FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz instructions/s) divided by that.
-DF64_INSTR_PER_FLOP = 6.0
-PEAK_DF64_TFLOPS = 152 * 128 * 2.07e9 / DF64_INSTR_PER_FLOP / 1e12
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Arithmetic per transfer sample of the method (see the module docstring): FP32 flops and
+# special-function instructions of transfer_kernel<float, float, 0> per sample, from the ncu
+# capture of the one-image 256^2 case (a = 0.94, i = 60 deg). None until captured.
+FLOP_PER_SAMPLE = None
+SFU_PER_SAMPLE = None
+# Kernel sources the DRAM figures below were captured with (sha256 of the kernel headers, 16
+# hex digits; see kernel_source_hash).
+KERNEL_HEADERS = ("bl_kernels.cuh", "bl_math.cuh", "bl_df64.cuh", "bl_internal.cuh",
+                  "bl_mlp.cuh", "bl_tc.cuh")
+# dram__bytes_read.sum + dram__bytes_write.sum per unit of work from one ncu capture of the
+# one-image 256^2 case, with the kernel-source hash of that capture; scaled by the units of a
+# launch of the benchmark step (the kernels' traffic grows with the units they process).
+DRAM_PER_UNIT = {
+    # FP64 form, 7,845,751 attempts: 0.0682 GB read + 2.0544 GB written (sample records)
+    "geodesic_fp64": {"src": "ab498bbdddb4da8d", "bytes": 2.122659e9 / 7845751, "unit": "attempt"},
+    # FP64 form, 18,372,204 samples: 2.6977 GB read + 0.3886 GB written
+    "transfer_fp64": {"src": "ab498bbdddb4da8d", "bytes": 3.086270e9 / 18372204, "unit": "sample"},
+}
+
+
+def kernel_source_hash() -> str:
+    """sha256 (16 hex digits) of the CUDA kernel headers, the sources of every kernel the
+    benchmark times."""
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2203_15963_gb300", "csrc")
+    for f in KERNEL_HEADERS:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -66,9 +91,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="blacklight", choices=["blacklight", "reference"])
-    ap.add_argument("--precision", default="fast", choices=["mixed", "fp64", "fast"],
-                    help="fast: double-float geodesics + FP32 transfer (default); mixed: FP64 "
-                         "geodesics + FP32 transfer; fp64: FP64 throughout")
+    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64", "fast"],
+                    help="fp64: FP64 throughout (default, the headline); mixed: FP64 geodesics + "
+                         "FP32 transfer; fast: double-float geodesics + FP32 transfer")
     ap.add_argument("--no-other-forms", action="store_true",
                     help="skip the short timing of the two other precision forms")
     ap.add_argument("--case", default="full", choices=["full", "small"],
@@ -77,6 +102,8 @@ def parse():
     ap.add_argument("--grid-layout", default="cells", choices=["cells", "planes"],
                     help="memory order of the device grids: cells (repacked once by "
                          "blacklight_grid_pack) or planes (as generated)")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the FP64/FP32/double-float peak probes (rooflines then unreported)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-hires", action="store_true",
@@ -94,6 +121,9 @@ def parse():
                     help="skip the autotuned CUDA-graph plan line")
     ap.add_argument("--no-mlp", action="store_true",
                     help="skip the learned-coefficient line (training + 1024^2 image + FP64 form)")
+    ap.add_argument("--oracle-pixels", type=int, default=4096,
+                    help="seeded pixels per image the CPU oracle traces for the baseline and the "
+                         "image-error comparisons")
     return ap.parse_args()
 
 
@@ -105,7 +135,7 @@ def dist_env():
 
 
 def reduce_elapsed(torch, elapsed, world, device):
-    """Slowest rank's timed-region length (ranks trace independent replicas, no exchange)."""
+    """Slowest rank's timed-region length (ranks trace disjoint shares, no exchange)."""
     if world <= 1:
         return elapsed
     t = torch.tensor([elapsed], dtype=torch.float64, device=device)
@@ -116,6 +146,22 @@ def reduce_elapsed(torch, elapsed, world, device):
 def weak_scaling_value(world, rays_per_rank_step, steps, elapsed_max):
     """Whole-job rays/s: every rank's rays over the slowest rank's time."""
     return world * rays_per_rank_step * steps / elapsed_max
+
+
+def image_spec(k, world):
+    """Image k of the whole job's batch of 9 x world images: (spin, inclination in degrees,
+    camera azimuth in radians). Images 9 w .. 9 w + 8 repeat the 9 spin x inclination pairs
+    seen from the azimuth 2 pi w / world, so every rank's share has the same structure and
+    cost while no two ranks trace the same image (the torus's seeded noise breaks the
+    axisymmetry)."""
+    w, j = divmod(k, len(SPINS) * len(INCS))
+    return SPINS[j // len(INCS)], INCS[j % len(INCS)], 2.0 * math.pi * w / max(world, 1)
+
+
+def rank_images(rank, world, per_rank=len(SPINS) * len(INCS)):
+    """Indices of the images rank `rank` traces: a contiguous block of `per_rank` images, so
+    the ranks' shares are disjoint and together cover the job's per_rank x world images."""
+    return list(range(rank * per_rank, (rank + 1) * per_rank))
 
 
 # memory order of the device grids the bench traces ("cells" or "planes"; set from --grid-layout)
@@ -134,24 +180,41 @@ def device_grid(torch, prim, gp, device):
     return p, gp
 
 
-def build_workload(torch, precision_code, device, case="full"):
+def workload_config(args, world):
+    """The workload description both arms print (identical keys and values)."""
+    small = args.case == "small"
+    return {"workload": "torus256_cam256" if not small
+            else "torus256_cam256 (one image: a=0.94, i=60 deg)",
+            "images": 1 if small else len(SPINS) * len(INCS) * world,
+            "images_per_rank": 1 if small else len(SPINS) * len(INCS),
+            "camera": N_PIX, "grid": list(GRID), "spins": list(SPINS),
+            "inclinations_deg": list(INCS), "freq_ghz": FREQ / 1e9,
+            "precision": args.precision, "coefficients": args.coef,
+            "grid_layout": args.grid_layout,
+            "parallelism": f"{world} rank(s), disjoint image shares, no collective",
+            "l2": "inputs larger than L2 (3 x 134 MB grids + sample records); no flush"}
+
+
+def build_workload(torch, precision_code, device, case="full", rank=0, world=1):
     from paper_2203_15963_gb300 import synth as S
     gp = S.grid_params_for(*GRID)
-    spins, incs = (SPINS, INCS) if case == "full" else ((0.94,), (60.0,))
+    if case == "full":
+        specs = [image_spec(k, world) for k in rank_images(rank, world)]
+    else:
+        specs = [(0.94, 60.0, 0.0)]
     prims_host, prims, planes = {}, {}, {}
-    for spin in spins:
+    for spin in sorted({sp[0] for sp in specs}):
         prims_host[spin] = S.make_torus(gp, spin, S.BASE_SEED + 1)
         planes[spin] = torch.from_numpy(prims_host[spin]).to(device)
         prims[spin], gpd = device_grid(torch, planes[spin], gp, device)
     cams, mets, gps, ps, pls, freqs = [], [], [], [], [], []
-    for spin in spins:
-        for inc in incs:
-            cams.append(S.Camera(theta=math.radians(inc), n=N_PIX))
-            mets.append(S.Metric(spin=spin, precision=precision_code))
-            gps.append(gpd)
-            ps.append(prims[spin])
-            pls.append(planes[spin])
-            freqs.append(FREQ)
+    for spin, inc, phi in specs:
+        cams.append(S.Camera(theta=math.radians(inc), phi=phi, n=N_PIX))
+        mets.append(S.Metric(spin=spin, precision=precision_code))
+        gps.append(gpd)
+        ps.append(prims[spin])
+        pls.append(planes[spin])
+        freqs.append(FREQ)
     # gps/prims: the device grids as traced; gp/prims_planes: the same grids in the plane
     # layout (host arrays for the oracle and the host-buffer path, device copies for comparison)
     return dict(gp=gp, cams=cams, mets=mets, gps=gps, prims=ps, freqs=freqs,
@@ -212,41 +275,149 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measure_peaks(native, device):
+    """The device's measured FP64, FP32 and double-float multiply-add peaks, with the SM
+    clock sampled while the probes run."""
+    clk = ClockSampler(device.index)
+    clk.start()
+    time.sleep(0.25)
+    pk = native.blacklight_measure_peaks(reps=20)
+    time.sleep(0.25)
+    pk["clocks"] = clk.stop()
+    pk["how"] = ("blacklight_measure_peaks: FMA-chain kernels (8 independent chains a thread, "
+                 "full occupancy on every SM), best of 20 launches, CUDA events")
+    return pk
+
+
+def roofline(kernel, flops_per_unit, units, unit_name, seconds, peak, traffic_key=None,
+             note=None):
+    """One roofline entry: algorithmic flops of a launch over its measured time against the
+    measured peak `peak` = (TFLOP/s, source); traffic from DRAM_PER_UNIT when the kernel
+    sources are the ones captured."""
+    r = {"kernel": kernel, "bound": "alu", "unit": "TFLOP/s",
+         "units_per_launch": units, "work_unit": unit_name,
+         "flops_per_unit": flops_per_unit, "seconds_per_launch": seconds}
+    if flops_per_unit is None or peak is None or seconds <= 0:
+        r.update(achieved=None, peak=None if peak is None else peak[0], frac=None,
+                 peak_source=None if peak is None else peak[1])
+    else:
+        ach = flops_per_unit * units / seconds / 1e12
+        r.update(achieved=ach, peak=peak[0], frac=ach / peak[0], peak_source=peak[1])
+    r["traffic"] = None
+    if traffic_key is not None:
+        prof = DRAM_PER_UNIT.get(traffic_key)
+        if prof is not None and prof["src"] == kernel_source_hash():
+            r["traffic"] = prof["bytes"] * units
+            r["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per " +
+                                 prof["unit"] + " from one ncu capture of the one-image 256^2 "
+                                 "case, scaled by this launch's units")
+        elif prof is not None:
+            r["traffic_note"] = "kernel changed since the ncu capture: traffic not reported"
+    if note:
+        r["note"] = note
+    return r
+
+
+def form_rooflines(prec_name, attempts, samples, geo_s, tr_s, peaks):
+    """Rooflines of the geodesic and transfer kernels of one precision form; the dominant
+    (longer) kernel first."""
+    def pk(kind):
+        if not peaks:
+            return None
+        mhz = (peaks.get("clocks") or {}).get("sm_mhz")
+        return (peaks[kind + "_tflops"],
+                f"measured {kind.upper()} peak ({peaks['how']}; {peaks['sm_count']} SMs"
+                + (f", median SM clock {mhz:.0f} MHz during the probes)" if mhz else ")"))
+    geo_kind = {"fp64": "fp64", "mixed": "fp64", "fast": "df64"}[prec_name]
+    tr_kind = "fp64" if prec_name == "fp64" else "fp32"
+    geo = roofline({"fp64": "geodesic_kernel<double, double>",
+                    "mixed": "geodesic_kernel<float, double>",
+                    "fast": "geodesic_kernel<float, df64>"}[prec_name],
+                   FLOP64_PER_ATTEMPT, attempts, "DP attempt", geo_s, pk(geo_kind),
+                   traffic_key="geodesic_fp64" if prec_name == "fp64" else None)
+    tr = roofline("transfer_kernel_fp64<0>" if prec_name == "fp64"
+                  else "transfer_kernel<float, float, 0>",
+                  FLOP_PER_SAMPLE, samples, "transfer sample", tr_s, pk(tr_kind),
+                  traffic_key="transfer_fp64" if prec_name == "fp64" else None,
+                  note=None if FLOP_PER_SAMPLE is not None else
+                  "per-sample flop count not yet captured")
+    return (geo, tr) if geo_s >= tr_s else (tr, geo)
+
+
+def _hist(v):
+    """Percentiles of a per-ray count (the survey's steps/samples-per-ray histograms)."""
+    import numpy as np
+    v = np.asarray(v, dtype=np.float64).reshape(-1)
+    if v.size == 0:
+        return None
+    q = np.percentile(v, [10, 50, 90, 99])
+    return {"mean": float(v.mean()), "p10": float(q[0]), "p50": float(q[1]),
+            "p90": float(q[2]), "p99": float(q[3]), "max": float(v.max()), "n": int(v.size)}
+
+
 def cpu_baseline(wl, n_per_image, seed=99, single_thread=False):
-    """The oracle, as it stands, on a bounded sample of the same workload (all host cores)."""
+    """The oracle, as it stands, on a bounded sample of the same workload (all host cores).
+    Returns (timing line, [oracle result per image]) -- the results serve the image-error
+    comparisons of the GPU forms on the same pixels."""
     import numpy as np
     import oracle as O
     O.build()
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
     rays = 0
-    for cam, met, spin in zip(wl["cams"], wl["mets"], [m.spin for m in wl["mets"]]):
-        gp = wl["gp"]
+    ref = []
+    for cam, met in zip(wl["cams"], wl["mets"]):
         pix = np.sort(rng.choice(cam.n * cam.n, n_per_image, replace=False)).astype(np.int32)
-        O.trace(cam, met, gp, wl["prims_host"][spin], FREQ, pix=pix, nthreads=0)
+        ref.append(O.trace(cam, met, wl["gp"], wl["prims_host"][met.spin], FREQ, pix=pix,
+                           nthreads=0))
         rays += n_per_image
     dt = time.perf_counter() - t0
     cores = os.cpu_count() or 1
+    cat = lambda k: np.concatenate([r[k] for r in ref])
     out = {"value": rays / dt, "unit": "rays/s", "cores": cores, "kind": "oracle",
-           "sample": f"{n_per_image} seeded pixels from each of the 9 images ({rays} rays), "
-                     f"{dt:.1f} s wall on {cores} threads", "cpu": _cpu_model()}
+           "sample": f"{n_per_image} seeded pixels from each of the {len(ref)} images "
+                     f"({rays} rays), {dt:.1f} s wall on {cores} threads", "cpu": _cpu_model(),
+           "per_core": rays / dt / cores,
+           "histograms": {"dp_attempts_per_ray": _hist(cat("attempts")),
+                          "accepted_steps_per_ray": _hist(cat("accepted")),
+                          "samples_per_ray": _hist(cat("samples"))}}
     if single_thread:
         # one thread on a smaller sample of the same images
         t0 = time.perf_counter()
         n1 = 0
         for cam, met in zip(wl["cams"], wl["mets"]):
-            gp = wl["gp"]
             pix = np.sort(rng.choice(cam.n * cam.n, 16, replace=False)).astype(np.int32)
-            O.trace(cam, met, gp, wl["prims_host"][met.spin], FREQ, pix=pix, nthreads=1)
+            O.trace(cam, met, wl["gp"], wl["prims_host"][met.spin], FREQ, pix=pix, nthreads=1)
             n1 += 16
         out["single_thread"] = {"value": n1 / (time.perf_counter() - t0), "rays": n1}
-    return out
+    return out, ref
+
+
+def oracle_image_error(outs, ref):
+    """Error of GPU images against the oracle on the oracle's pixels: per Stokes the largest
+    over images of ||X_gpu - X_oracle|| / ||I_oracle|| (over the sampled pixels), the
+    sampled flux's largest relative difference, and ray statuses that differ."""
+    import numpy as np
+    worst = [0.0] * 4
+    flux = 0.0
+    status_diff = 0
+    for o, r in zip(outs, ref):
+        st = o["stokes"].double().reshape(4, -1).cpu().numpy()[:, r["pix"]].T
+        want = r["stokes"]
+        nI = np.linalg.norm(want[:, 0])
+        for k in range(4):
+            worst[k] = max(worst[k], float(np.linalg.norm(st[:, k] - want[:, k]) / nI))
+        fw = float(want[:, 0].sum())
+        flux = max(flux, abs(float(st[:, 0].sum()) - fw) / abs(fw) if fw else 0.0)
+        if "status" in o:
+            status_diff += int((o["status"].reshape(-1).cpu().numpy()[r["pix"]] != r["status"]).sum())
+    return {"rel_l2_IQUV": worst, "flux_rel": flux, "status_differs": status_diff,
+            "pixels": int(sum(len(r["pix"]) for r in ref))}
 
 
 def _cpu_model():
     """the host CPU's model name, as the system reports it"""
     try:
-        import subprocess
         txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
         for line in txt.splitlines():
             if line.startswith("Model name:"):
@@ -257,46 +428,53 @@ def _cpu_model():
 
 
 def run_reference(args):
+    """The oracle timed on the host cores on a bounded sample of the same workload, printed
+    as a line of the same metric and config. Under torchrun only rank 0 runs it."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-    wl = build_workload_host()
+    wl = build_workload_host(args, world)
     n_per_image = 128
     for _ in range(args.warmup):
         cpu_baseline(wl, n_per_image, seed=1)
-    vals, t_total = [], 0.0
+    vals = []
     for k in range(args.steps):
-        r = cpu_baseline(wl, n_per_image, seed=100 + k)
+        r, _ = cpu_baseline(wl, n_per_image, seed=100 + k)
         vals.append(r["value"])
     value = statistics.median(vals)
-    ms = 9 * n_per_image / value * 1e3
+    n_img = len(wl["cams"])
+    ms = n_img * N_PIX * N_PIX / value * 1e3
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "torus256_cam256", "images": 9, "camera": N_PIX,
-                       "grid": list(GRID), "spins": list(SPINS), "inclinations_deg": list(INCS),
-                       "freq_ghz": FREQ / 1e9, "sample_per_step": f"{n_per_image} pixels x 9 images"},
+            "data": "synthetic", "config": workload_config(args, world),
             "cpu_baseline": {"value": value, "unit": "rays/s", "cores": os.cpu_count() or 1,
                              "kind": "oracle",
-                             "sample": f"{n_per_image} seeded pixels from each of the 9 images per step"},
+                             "sample": f"{n_per_image} seeded pixels from each of the {n_img} "
+                                       f"images per step; ms_per_step extrapolates to the "
+                                       f"whole step"},
             "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def build_workload_host():
+def build_workload_host(args, world=1):
+    """The benchmark step's inputs on the host (the reference arm traces rank 0's share)."""
     from paper_2203_15963_gb300 import synth as S
     gp = S.grid_params_for(*GRID)
-    prims_host = {spin: S.make_torus(gp, spin, S.BASE_SEED + 1) for spin in SPINS}
+    specs = ([image_spec(k, world) for k in rank_images(0, world)] if args.case == "full"
+             else [(0.94, 60.0, 0.0)])
+    prims_host = {spin: S.make_torus(gp, spin, S.BASE_SEED + 1)
+                  for spin in sorted({sp[0] for sp in specs})}
     cams, mets, gps = [], [], []
-    for spin in SPINS:
-        for inc in INCS:
-            cams.append(S.Camera(theta=math.radians(inc), n=N_PIX))
-            mets.append(S.Metric(spin=spin))
-            gps.append(gp)
+    for spin, inc, phi in specs:
+        cams.append(S.Camera(theta=math.radians(inc), phi=phi, n=N_PIX))
+        mets.append(S.Metric(spin=spin))
+        gps.append(gp)
     return dict(gp=gp, cams=cams, mets=mets, gps=gps, prims_host=prims_host)
+
+
+PREC_NAMES = ("fp64", "mixed", "fast")
 
 
 def main():
@@ -317,9 +495,11 @@ def main():
     native.load()
     global GRID_LAYOUT
     GRID_LAYOUT = args.grid_layout
-    prec = {"mixed": native.BL_PREC_MIXED, "fp64": native.BL_PREC_FP64,
-            "fast": native.BL_PREC_FAST}[args.precision]
-    wl = build_workload(torch, prec, device, args.case)
+    codes = {"mixed": native.BL_PREC_MIXED, "fp64": native.BL_PREC_FP64,
+             "fast": native.BL_PREC_FAST}
+    prec = codes[args.precision]
+    peaks = None if args.no_peaks else measure_peaks(native, device)
+    wl = build_workload(torch, prec, device, args.case, rank, world)
     cams, mets = wl["cams"], wl["mets"]
     ws = torch.empty(native.blacklight_workspace_size(cams, mets), dtype=torch.uint8,
                      device=device)
@@ -371,62 +551,45 @@ def main():
     samples = sum(int(o["samples"].long().sum()) for o in outs)
     geo_avg = geo_ms / args.steps / 1e3
     tr_avg = tr_ms / args.steps / 1e3
-    flop_geo = attempts * FLOP64_PER_ATTEMPT
-    flop_tr = samples * FLOP32_PER_SAMPLE
-    if geo_avg >= tr_avg and prec != native.BL_PREC_FAST:
-        roof = {"kernel": "geodesic_kernel (FP64)", "bound": "alu",
-                "achieved": flop_geo / geo_avg / 1e12, "peak": PEAK_FP64_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "nominal FP64 rate (profiling recipe)"}
-    elif geo_avg >= tr_avg:
-        # double-float: algorithmic FP64 flops against the emulated rate the FP32 pipe allows
-        roof = {"kernel": "geodesic_kernel (double-float on FP32)", "bound": "alu",
-                "achieved": flop_geo / geo_avg / 1e12, "peak": PEAK_DF64_TFLOPS,
-                "unit": "TFLOP/s",
-                "peak_source": f"FP32 issue rate (152 SMs x 128 lanes x 2.07 GHz) / "
-                               f"{DF64_INSTR_PER_FLOP} FP32 instructions per emulated FP64 flop"}
-    else:
-        peak = PEAK_FP32_TFLOPS if prec != native.BL_PREC_FP64 else PEAK_FP64_TFLOPS
-        roof = {"kernel": "transfer_kernel", "bound": "alu",
-                "achieved": flop_tr / tr_avg / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "nominal rate (profiling recipe unit counts x 2.07 GHz)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    # DRAM bytes (read + written) of the dominant kernel per launch: the per-unit figure from
-    # one ncu capture of the same kernel on the one-image 256^2 case, scaled by the units of
-    # this launch (attempts for the geodesic kernel, samples for the transfer kernel)
-    if (roof["kernel"].startswith("geodesic_kernel (double-float")
-            and GEO_DF64_DRAM_BYTES_PER_ATTEMPT is not None):
-        roof["traffic"] = GEO_DF64_DRAM_BYTES_PER_ATTEMPT * attempts
-        roof["traffic_note"] = "ncu capture of the 256^2 one-image case, scaled by DP attempts"
-    else:
-        roof["traffic"] = None
+    roofs = form_rooflines(args.precision, attempts, samples, geo_avg, tr_avg, peaks)
+    work_hist = {"dp_attempts_per_ray": _hist(torch.cat([o["steps"].reshape(-1) for o in outs]).cpu().numpy()),
+                 "samples_per_ray": _hist(torch.cat([o["samples"].reshape(-1) for o in outs]).cpu().numpy())}
     status_bad = sum(int(((o["status"] != 1) & (o["status"] != 2)).sum()) for o in outs)
     # the secondary measurements below allocate their own workspaces
     del ws
     torch.cuda.empty_cache()
 
-    other = None
+    other, other_outs = None, {}
     if not args.no_other_forms:
         other = {}
-        for name, code in (("mixed", native.BL_PREC_MIXED), ("fp64", native.BL_PREC_FP64),
-                           ("fast", native.BL_PREC_FAST)):
-            if code == prec:
+        for name in PREC_NAMES:
+            if name == args.precision:
                 continue
-            other[name] = time_form(torch, native, images, wl, code, device, steps=3, warmup=2)
+            other[name], other_outs[name] = time_form(torch, native, images, wl, codes[name],
+                                                      device, steps=3, warmup=2, peaks=peaks,
+                                                      name=name)
     layout_cmp = None
     if not args.no_other_forms and GRID_LAYOUT == "cells":
-        # the same step on the grids in the plane layout (the layout as generated)
+        # the fast form's step on the grids in the plane layout (the layout as generated)
         wl_planes = dict(wl, gps=[wl["gp"]] * len(cams), prims=wl["prims_planes"])
-        layout_cmp = time_form(torch, native, images, wl_planes, prec, device, steps=3, warmup=2)
-    hires = hires_img = None
+        layout_cmp, _ = time_form(torch, native, images, wl_planes, native.BL_PREC_FAST, device,
+                                  steps=3, warmup=2, name="fast")
+    hires = hires_img = hires_host = hires_fast = hires_fast_img = None
     if not args.no_hires and args.case == "full":
-        hires, hires_img = measure_hires(torch, native, images, prec, device,
-                                         keep_image=prec == native.BL_PREC_FAST)
+        hires, hires_img, hires_host = measure_hires(torch, native, images, prec, device,
+                                                     keep_image=True, keep_host=True)
+        if prec != native.BL_PREC_FAST:
+            hires_fast, hires_fast_img, _ = measure_hires(torch, native, images,
+                                                          native.BL_PREC_FAST, device,
+                                                          keep_image=True)
+        else:
+            hires_fast, hires_fast_img = hires, hires_img
     variants = None
     if not args.no_variants:
         variants = measure_variants(torch, native, images, wl, prec, device)
     plan = None
     if not args.no_plan:
-        plan = measure_plan(torch, native, images, wl, prec, device)
+        plan = measure_plan(torch, native, images, wl, native.BL_PREC_FAST, device)
     model = None
     if (not args.no_mlp or not args.no_slow) and args.case == "full":
         from paper_2203_15963_gb300 import coefmodel
@@ -436,23 +599,36 @@ def main():
         model = (params, time.perf_counter() - t0, float(hist[-500:].mean()))
     mlp = None
     if not args.no_mlp and args.case == "full":
-        mlp = measure_mlp(torch, native, images, device, hires_img, *model)
-    hires_img = None
+        mlp = measure_mlp(torch, native, images, device, hires_fast_img,
+                          hires_img if prec == native.BL_PREC_FP64 else None,
+                          hires if prec == native.BL_PREC_FP64 else None, *model)
     slow = None
     if not args.no_slow and args.case == "full":
         slow = measure_slow(torch, native, images, device, model[0] if model else None)
     model = None
     adaptive = None
     if not args.no_adaptive and args.case == "full":
-        adaptive = measure_adaptive(torch, native, prec, device)
+        adaptive = measure_adaptive(torch, native, native.BL_PREC_FAST, device)
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(torch, native, wl, prec, max(1, min(args.steps, 3)))
     cpu = None
+    errors = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, 1024, single_thread=True)
+        # the CPU-baseline leg: the oracle on a seeded pixel sample of every image, which
+        # also judges each GPU form's images on those pixels
+        cpu, ref = cpu_baseline(wl, args.oracle_pixels, single_thread=True)
+        errors = {args.precision: oracle_image_error(outs, ref)}
+        for name, o in other_outs.items():
+            errors[name] = oracle_image_error(o, ref)
+        ref = None
+        if hires_host is not None:
+            cpu["hires_sample"] = hires_oracle_sample(hires_host, hires_img, hires_fast_img,
+                                                      args.oracle_pixels)
+    hires_host = hires_img = hires_fast_img = None
 
     if rank == 0:
+        roof = roofs[0]
         line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
@@ -460,39 +636,33 @@ def main():
                 "dtype": {native.BL_PREC_MIXED: "f64+f32", native.BL_PREC_FP64: "f64",
                           native.BL_PREC_FAST: "df64+f32"}[prec],
                 "data": "synthetic",
-                "config": {"workload": "torus256_cam256" if args.case == "full"
-                           else "torus256_cam256 (one image: a=0.94, i=60 deg)",
-                           "images": len(cams), "camera": N_PIX,
-                           "grid": list(GRID), "spins": list(SPINS),
-                           "inclinations_deg": list(INCS), "freq_ghz": FREQ / 1e9,
-                           "precision": args.precision, "coefficients": args.coef,
-                           "grid_layout": GRID_LAYOUT,
-                           "parallelism": f"replicas x{world}",
-                           "l2": "inputs larger than L2 (3 x 134 MB grids + sample records); no flush"},
+                "config": workload_config(args, world),
                 "kernel_ms": {"geodesic": geo_avg * 1e3, "transfer": tr_avg * 1e3},
                 "work": {"dp_attempts": attempts, "samples": samples,
-                         "rays_not_terminated_normally": status_bad},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "other_forms": other,
-                "plane_layout": layout_cmp,
-                "variants": variants, "plan": plan, "hires": hires, "mlp": mlp,
-                "slow_light": slow,
-                "adaptive": adaptive,
-                "gpu_launches": int(launches), "clocks": clk, "return_codes": sorted(set(rcs))}
+                         "rays_not_terminated_normally": status_bad, "per_ray": work_hist},
+                "roofline": roof, "roofline_other_kernel": roofs[1], "peaks": peaks,
+                "image_error_vs_oracle": errors,
+                "cpu_baseline": cpu, "e2e": e2e, "other_forms": other,
+                "plane_layout_fast": layout_cmp,
+                "variants": variants, "plan": plan, "hires": hires, "hires_fast": hires_fast,
+                "mlp": mlp, "slow_light": slow, "adaptive": adaptive,
+                "gpu_launches": int(launches), "clocks": clk, "return_codes": sorted(set(rcs)),
+                "kernel_source_hash": kernel_source_hash()}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def time_form(torch, native, images, wl, code, device, steps, warmup):
-    """Short CUDA-event timing of the same workload in another precision form."""
-    import copy
-    mets = [copy.replace(m, precision=code) if hasattr(copy, "replace") else
-            type(m)(**{**m.__dict__, "precision": code}) for m in wl["mets"]]
+def time_form(torch, native, images, wl, code, device, steps, warmup, peaks=None, name=None):
+    """Short CUDA-event timing of the same workload in another precision form, with its
+    rooflines. Returns (line, outputs)."""
+    import dataclasses
+    mets = [dataclasses.replace(m, precision=code) for m in wl["mets"]]
     cams = wl["cams"]
     ws = torch.empty(native.blacklight_workspace_size(cams, mets), dtype=torch.uint8,
                      device=device)
     dt = torch.float64 if code == native.BL_PREC_FP64 else torch.float32
-    outs = [images.alloc_outputs(c.n, dt, device=device) for c in cams]
+    outs = [images.alloc_outputs(c.n, dt, device=device, samples=True) for c in cams]
     for _ in range(warmup):
         native.blacklight_trace_batch(cams, mets, wl["gps"], wl["prims"], wl["freqs"], outs,
                                       workspace=ws)
@@ -512,26 +682,35 @@ def time_form(torch, native, images, wl, code, device, steps, warmup):
     ms = e0.elapsed_time(e1) / steps
     del ws
     rays = sum(c.n * c.n for c in cams)
-    return {"value": rays / ms * 1e3, "ms_per_step": ms, "steps": steps,
+    line = {"value": rays / ms * 1e3, "ms_per_step": ms, "steps": steps,
+            "dtype": {native.BL_PREC_MIXED: "f64+f32", native.BL_PREC_FP64: "f64",
+                      native.BL_PREC_FAST: "df64+f32"}[code],
             "kernel_ms": {"geodesic": geo / steps, "transfer": tr / steps}}
+    if name is not None and peaks is not None:
+        attempts = sum(int(o["steps"].long().sum()) for o in outs)
+        samples = sum(int(o["samples"].long().sum()) for o in outs)
+        line["roofline"] = list(form_rooflines(name, attempts, samples, geo / steps / 1e3,
+                                               tr / steps / 1e3, peaks))
+    return line, outs
 
 
 def measure_hires(torch, native, images, code, device, steps=3, warmup=2, coef_mlp=None,
-                  keep_image=False):
+                  keep_image=False, keep_host=False):
     """The metric's 1024^2 point: one 1024x1024 image (a = 0.94, i = 17 deg, 230 GHz) on the
     512x256x256 torus (1 GiB of float32), timed like the main workload. coef_mlp selects the
-    learned coefficient model. Returns (line, Stokes image or None)."""
+    learned coefficient model. Returns (line, Stokes image or None, host inputs or None)."""
     from paper_2203_15963_gb300 import synth as S
     cam, met, gp, prim = S.workload_inputs("torus512_cam1024", 0.94, 17.0)
     met = S.Metric(**{**met.__dict__, "precision": code})
-    p, gp = device_grid(torch, prim, gp, device)
+    p, gpd = device_grid(torch, prim, gp, device)
+    host = (cam, met, gp, prim) if keep_host else None
     del prim
     ws = torch.empty(native.blacklight_workspace_size([cam], [met]), dtype=torch.uint8,
                      device=device)
     dt = torch.float64 if code == native.BL_PREC_FP64 else torch.float32
     out = images.alloc_outputs(cam.n, dt, device=device)
     for _ in range(warmup):
-        native.blacklight_trace_batch([cam], [met], [gp], [p], [FREQ], [out], workspace=ws,
+        native.blacklight_trace_batch([cam], [met], [gpd], [p], [FREQ], [out], workspace=ws,
                                       coef_mlp=coef_mlp)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -539,7 +718,7 @@ def measure_hires(torch, native, images, code, device, steps=3, warmup=2, coef_m
     geo = tr = 0.0
     e0.record()
     for _ in range(steps):
-        native.blacklight_trace_batch([cam], [met], [gp], [p], [FREQ], [out], workspace=ws,
+        native.blacklight_trace_batch([cam], [met], [gpd], [p], [FREQ], [out], workspace=ws,
                                       flags=native.BL_TIMING, coef_mlp=coef_mlp)
         g, t = native.blacklight_last_kernel_ms()
         geo += g
@@ -552,9 +731,32 @@ def measure_hires(torch, native, images, code, device, steps=3, warmup=2, coef_m
     torch.cuda.empty_cache()
     line = {"workload": "torus512_cam1024", "value": cam.n * cam.n / ms * 1e3, "unit": "rays/s",
             "ms_per_step": ms, "steps": steps,
+            "dtype": {native.BL_PREC_MIXED: "f64+f32", native.BL_PREC_FP64: "f64",
+                      native.BL_PREC_FAST: "df64+f32"}[code],
             "kernel_ms": {"geodesic": geo / steps, "transfer": tr / steps},
             "rays_not_terminated_normally": bad}
-    return line, (out["stokes"] if keep_image else None)
+    return line, (out if keep_image else None), host
+
+
+def hires_oracle_sample(host, img, img_fast, n_pix, seed=7):
+    """CPU-baseline leg at the 1024^2 point: the oracle on n_pix seeded pixels of the 1024^2
+    image (512x256x256 torus), its rate on the host cores, and the GPU images' error against
+    it on those pixels."""
+    import numpy as np
+    import oracle as O
+    cam, met, gp, prim = host
+    rng = np.random.default_rng(seed)
+    pix = np.sort(rng.choice(cam.n * cam.n, n_pix, replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    ref = O.trace(cam, met, gp, prim, FREQ, pix=pix, nthreads=0)
+    dt = time.perf_counter() - t0
+    out = {"value": n_pix / dt, "unit": "rays/s", "cores": os.cpu_count() or 1,
+           "sample": f"{n_pix} seeded pixels of the 1024^2 image on the 512x256x256 torus"}
+    if img is not None:
+        out["image_error"] = oracle_image_error([img], [ref])
+    if img_fast is not None and img_fast is not img:
+        out["image_error_fast"] = oracle_image_error([img_fast], [ref])
+    return out
 
 
 def rel_l2(torch, got, want):
@@ -609,26 +811,29 @@ def measure_slow(torch, native, images, device, coef_mlp, steps=3):
     return out
 
 
-def measure_mlp(torch, native, images, device, fast_image, params, train_s, final_loss):
+def measure_mlp(torch, native, images, device, fast_out, out64, line64, params, train_s,
+                final_loss):
     """Learned coefficients at the 1024^2 point: the model trained on the GPU (default recipe),
     then the image traced with the fused tensor-core transfer (double-float geodesics, FP32
-    transfer), next to the plain FP64 form of the same image: speedup and image error
-    against the FP64 image, and the exact-fit fast form's error for comparison."""
+    transfer), next to the plain FP64 form of the same image (out64/line64 when already
+    measured): speedup and image error against the FP64 image, and the exact-fit fast form's
+    error for comparison."""
     from paper_2203_15963_gb300 import coefmodel
-    line, img = measure_hires(torch, native, images, native.BL_PREC_FAST, device, steps=3,
-                              warmup=2, coef_mlp=params, keep_image=True)
-    fp64, img64 = measure_hires(torch, native, images, native.BL_PREC_FP64, device, steps=1,
-                                warmup=1, keep_image=True)
+    line, img, _ = measure_hires(torch, native, images, native.BL_PREC_FAST, device, steps=3,
+                                 warmup=2, coef_mlp=params, keep_image=True)
+    if out64 is None:
+        line64, out64, _ = measure_hires(torch, native, images, native.BL_PREC_FP64, device,
+                                         steps=1, warmup=1, keep_image=True)
     line.update({
         "form": "double-float geodesics, FP32 transfer, learned coefficients (BF16 tensor cores)",
         "train": {"seconds": train_s, "samples": coefmodel.N_SAMPLES, "batch": coefmodel.BATCH,
                   "steps": coefmodel.STEPS, "final_mse_normalised": final_loss},
-        "fp64_form": {"value": fp64["value"], "kernel_ms": fp64["kernel_ms"]},
-        "speedup_over_fp64_form": line["value"] / fp64["value"],
-        "image_rel_l2_vs_fp64_form": rel_l2(torch, img, img64),
-        "exact_fast_rel_l2_vs_fp64_form": (rel_l2(torch, fast_image, img64)
-                                           if fast_image is not None else None)})
-    del img, img64
+        "fp64_form": {"value": line64["value"], "kernel_ms": line64["kernel_ms"]},
+        "speedup_over_fp64_form": line["value"] / line64["value"],
+        "image_rel_l2_vs_fp64_form": rel_l2(torch, img["stokes"], out64["stokes"]),
+        "exact_fast_rel_l2_vs_fp64_form": (rel_l2(torch, fast_out["stokes"], out64["stokes"])
+                                           if fast_out is not None else None)})
+    del img
     torch.cuda.empty_cache()
     return line
 
@@ -673,8 +878,10 @@ def measure_plan(torch, native, images, wl, code, device, steps=5):
     """The main workload as an autotuned plan (CUDA-graph replay), device-timed like the
     headline, and the host cost of small batches (16 images of 32^2 on the 64x32x32 torus)
     through direct calls against graph replays (wall clock per batch, synchronised)."""
+    import dataclasses
     from paper_2203_15963_gb300 import synth as S
-    cams, mets = wl["cams"], wl["mets"]
+    cams = wl["cams"]
+    mets = [dataclasses.replace(m, precision=code) for m in wl["mets"]]
     dt = torch.float64 if code == native.BL_PREC_FP64 else torch.float32
     outs = [images.alloc_outputs(c.n, dt, device=device) for c in cams]
     t0 = time.perf_counter()
@@ -722,6 +929,8 @@ def measure_plan(torch, native, images, wl, code, device, steps=5):
     del ws, so, p
     torch.cuda.empty_cache()
     return {"value": rays / ms * 1e3, "unit": "rays/s", "ms_per_step": ms, "steps": steps,
+            "dtype": {native.BL_PREC_MIXED: "f64+f32", native.BL_PREC_FP64: "f64",
+                      native.BL_PREC_FAST: "df64+f32"}[code],
             "return_code": rc, "autotune_seconds": tune_s, "config": cfg,
             "small_batch": {"workload": "16 x 32^2 on the 64x32x32 torus",
                             "direct_ms": direct_ms, "graph_replay_ms": replay_ms}}
@@ -776,12 +985,17 @@ def measure_adaptive(torch, native, code, device, steps=2, warmup=1):
     del prims, ps, outs
     torch.cuda.empty_cache()
     return {"workload": "torus256 adaptive: 16 images, 128^2 root, 8x8 blocks, 3 levels",
-            "value": rays / sec, "unit": "rays/s", "ms_per_step": sec * 1e3, "steps": steps,
-            "rays_per_step": rays, "rays_per_level": lr.sum(axis=0).tolist(),
-            "timing": "host wall clock of blacklight_trace_adaptive (levels run on the device "
-                      "without host round trips; one synchronisation at the end)",
-            "graph_plan": {"value": plan_rays / plan_ms * 1e3, "ms_per_step": plan_ms,
-                           "return_code": plan_rc, "timing": "CUDA events around graph replays"}}
+            "value": plan_rays / plan_ms * 1e3, "unit": "rays/s", "ms_per_step": plan_ms,
+            "steps": steps, "return_code": plan_rc,
+            "dtype": {native.BL_PREC_MIXED: "f64+f32", native.BL_PREC_FP64: "f64",
+                      native.BL_PREC_FAST: "df64+f32"}[code],
+            "timing": "CUDA events around replays of the adaptive plan (every level in one "
+                      "CUDA graph)",
+            "rays_per_step": plan_rays, "rays_per_level": lr.sum(axis=0).tolist(),
+            "direct_call": {"value": rays / sec, "ms_per_step": sec * 1e3,
+                            "timing": "host wall clock of blacklight_trace_adaptive (levels "
+                                      "run on the device without host round trips; one "
+                                      "synchronisation at the end)"}}
 
 
 def measure_e2e(torch, native, wl, prec, steps):

@@ -222,12 +222,18 @@ int blacklight_trace(const bl_camera_t* cam, const bl_metric_t* met, const bl_gr
  * start-up, a foreign memory pool, or a context where allocation is forbidden. Instead of
  * allocating, it uses a fixed 64 MiB scratch array compiled into the library (held by every
  * device that loads the library until the process exits), which limits it to images of at
- * most 1024 rays (e.g. 32x32); larger cameras return BL_EINVAL with an explanation.
- * Inputs and outputs are caller-owned device memory as for blacklight_trace. The first call
- * on each device looks up the scratch array's device address (make that call before any
- * stream capture). All calls share the one array: calls whose work overlaps on the GPU (other
- * streams, other host threads) race and corrupt each other; order them on one stream.
- * BL_TIMING is ignored. */
+ * most 1024 rays (e.g. 32x32); larger cameras return BL_EINVAL with an explanation. Within
+ * that limit every integrator and precision is accepted: rays whose sample records need more
+ * than the array holds at once (long fixed-step RK4/RK2 rays) run in several smaller waves.
+ * Inputs and outputs are caller-owned device memory as for blacklight_trace.
+ * The array is reserved on a device when the library's device code is loaded there, which
+ * under CUDA's default lazy loading is the first call into the library on that device (this
+ * entry point's or any other): make one call, e.g. a small trace, while allocation is still
+ * allowed. The first call on each device also looks up the array's device address (make that
+ * call before any stream capture). All calls share the one array: calls whose work overlaps
+ * on the GPU (other streams, other host threads) race and corrupt each other; order them on
+ * one stream. The call always synchronises `stream` before returning, so that BL_WRAYS and
+ * BL_ETIMEOUT are reported from the shared counters; BL_ASYNC and BL_TIMING are ignored. */
 int blacklight_trace_noalloc(const bl_camera_t* cam, const bl_metric_t* met,
                              const bl_grid_t* grid, double freq_hz, const bl_out_t* out,
                              void* stream, uint32_t flags);
@@ -277,10 +283,16 @@ typedef struct bl_launch_config {
     int32_t geo_ctas_per_sm;  /* persistent geodesic CTAs per SM, 0 = occupancy limit */
     int32_t tr_ctas_per_sm;   /* persistent transfer CTAs per SM, 0 = occupancy limit */
     float run_ms;             /* autotuned plans: device time of one run with this configuration */
+    int32_t ilv_block;        /* batches of equal images on cell-layout grids queue their rays
+                                 interleaved in blocks of this many rays of one image: a power
+                                 of two in [64, 4096] dividing the rays of an image, 0 = the
+                                 default (256); reported as 0 where the batch does not
+                                 interleave */
 } bl_launch_config_t;
-/* flags for blacklight_plan_create: search ray order and CTAs per SM (coordinate descent over
- * timed runs of the plan's own workload; the images' outputs are written while tuning). The
- * choice is cached per device and workload shape for the life of the process. */
+/* flags for blacklight_plan_create: search ray order, interleave block and CTAs per SM
+ * (coordinate descent over timed runs of the plan's own workload; the images' outputs are
+ * written while tuning). The choice is cached per device and workload shape for the life of
+ * the process. */
 enum { BL_PLAN_AUTOTUNE = 4u };
 /* config: NULL = defaults (Morton, occupancy limits), ignored with BL_PLAN_AUTOTUNE. `stream`
  * is used for the tuning runs and the capture (the legacy default stream is replaced by a
@@ -448,6 +460,28 @@ int blacklight_set_memory_retention(uint64_t bytes);
  * arrive = 1 it arrives first (returns 0), with arrive = 0 nothing arrives and the wait runs out
  * (returns BL_ETIMEOUT). No fault, no unbounded wait. */
 int blacklight_selftest_wait(int64_t max_cycles, int32_t arrive, void* stream);
+
+/* Arithmetic peaks of the current device, measured (the paper has no counterpart: these are
+ * the denominators of the rooflines a benchmark reports). Each probe is a kernel of
+ * independent multiply-add chains x <- x a + b (2 flops a step) on every SM at full
+ * occupancy, timed with CUDA events on `stream` after one warm-up launch; the best of `reps`
+ * launches of ~15 ms each is kept (a burst figure: the SM clock during the probes is the
+ * caller's to record).
+ *   fp64_tflops: native FP64 FMA;  fp32_tflops: native FP32 FMA;
+ *   df64_tflops: the double-float multiply-add of this library's double-float integrator
+ *     (a compensated product plus sum of two-float values, counted as 2 flops).
+ * sm_count is cudaDevAttrMultiProcessorCount and sm_clock_khz cudaDevAttrClockRate (the
+ * maximum SM clock) of the device. 1 <= reps <= 100, else BL_EINVAL. Synchronous. */
+typedef struct {
+    uint32_t size;          /* sizeof(bl_peaks_t) */
+    int32_t sm_count;
+    int32_t sm_clock_khz;
+    double fp64_tflops;
+    double fp32_tflops;
+    double df64_tflops;
+    double probe_ms;        /* device time of one timed launch of each probe, summed */
+} bl_peaks_t;
+int blacklight_measure_peaks(bl_peaks_t* out, int32_t reps, void* stream);
 
 const char* blacklight_strerror(int code);
 const char* blacklight_last_error_detail(void);

@@ -12,6 +12,7 @@
 
 #include "../../include/blacklight.h"
 #include "bl_kernels.cuh"
+#include "bl_peak.cuh"
 
 namespace {
 
@@ -250,7 +251,10 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
         c[bl::kcLen] = d.length_unit;
         c[bl::kcSpin] = m.spin;
         c[bl::kcMass] = m.mass;
-        for (int i = 0; i < 16; ++i) d.f_c[i] = (float)c[i];
+        c[bl::kcIDlr] = 1.0 / c[bl::kcDlr];
+        c[bl::kcNeFac] = c[bl::kcNePre] / (1.0 + 1.0 / g.ne_over_ni);
+        static_assert(bl::kcCount <= 20, "per-image constants");
+        for (int i = 0; i < bl::kcCount; ++i) d.f_c[i] = (float)c[i];
     }
     d.stokes = o.stokes; d.dtype = o.dtype; d.status = o.status; d.steps = o.steps;
     d.end_state = o.end_state;
@@ -259,6 +263,7 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
     d.ray_offset = offset;
     d.n_rays = (int64_t)c.n * c.n;
     d.ilv = 0;
+    d.ilv_shift = bl::kIlvShift;
 }
 
 // Queue the rays of a batch of equal images interleaved (see setup_ray) when every image has
@@ -267,13 +272,18 @@ void fill_desc(bl::ImageDesc& d, const bl_camera_t& c, const bl_metric_t& m, con
 // their 64 scalar gathers a sample, spread over three grids at once, missed L2 enough to
 // outweigh the shorter tail (transfer 27.6 -> 40.9 ms on the 9-image step). Scheduling only:
 // each ray's result is the same in either queue order.
-void set_interleave(std::vector<bl::ImageDesc>& d) {
+bool set_interleave(std::vector<bl::ImageDesc>& d, int shift = bl::kIlvShift) {
     const size_t n = d.size();
-    bool eq = n > 1 && d[0].n_rays > 0 && d[0].n_rays % bl::kIlvBlock == 0;
+    const int64_t blk = int64_t(1) << shift;
+    bool eq = n > 1 && d[0].n_rays > 0 && d[0].n_rays % blk == 0;
     for (size_t q = 0; q < n && eq; ++q)
         eq = d[q].n_rays == d[0].n_rays && d[q].ray_offset == (int64_t)q * d[0].n_rays &&
              (d[q].prim == nullptr || d[q].layout == BL_GRID_CELLS);
-    for (auto& x : d) x.ilv = eq ? (int32_t)n : 0;
+    for (auto& x : d) {
+        x.ilv = eq ? (int32_t)n : 0;
+        x.ilv_shift = shift;
+    }
+    return eq;
 }
 
 // Dynamic shared memory of a geodesic-kernel CTA: the stage derivatives, 7 stages x 7
@@ -330,14 +340,14 @@ int dev_info(DevInfo& out) {
     if (di.sms == 0) {
         BL_CUDA(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev));
         if (kGeoSmem > 0) {   // the stage derivatives exceed the default 48 KB of shared memory
-            BL_CUDA(cudaFuncSetAttribute(bl::geodesic_kernel<double, double>,
+            BL_CUDA(cudaFuncSetAttribute(bl::geodesic_kernel_fp64,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGeoSmem));
             BL_CUDA(cudaFuncSetAttribute(bl::geodesic_kernel<float, double>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGeoSmem));
             BL_CUDA(cudaFuncSetAttribute(bl::geodesic_kernel<float, bl::df64>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGeoSmem));
         }
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[0], bl::geodesic_kernel<double, double>, 128, kGeoSmem));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[0], bl::geodesic_kernel_fp64, 128, kGeoSmem));
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[1], bl::geodesic_kernel<float, double>, 128, kGeoSmem));
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[2], bl::geodesic_kernel<float, bl::df64>, 128, kGeoSmem));
         for (int i = 0; i < 3; ++i)
@@ -461,7 +471,7 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
             }
             if (precision == BL_PREC_FP64) {
                 bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
-                bl::geodesic_kernel<double, double><<<geo_grid, 128, kGeoSmem, st>>>(
+                bl::geodesic_kernel_fp64<<<geo_grid, 128, kGeoSmem, st>>>(
                     d_desc, n_images, b, e, hdr, sink, record, cfg.bs, init);
             } else {
                 bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
@@ -674,7 +684,7 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int order;
+    int order, ilv_shift;
     LaunchCfg cfg;
     float ms;
 };
@@ -695,6 +705,7 @@ struct bl_plan {
     Layout L{};
     char* ws = nullptr;
     int order = 0;
+    int ilv_shift = bl::kIlvShift;
     LaunchCfg cfg;
     float run_ms = 0.0f;
     int64_t kernels_per_run = 0;
@@ -705,9 +716,13 @@ struct bl_plan {
 
 namespace {
 
-int plan_set_order(bl_plan& P, int order, cudaStream_t st) {
+int plan_set_order(bl_plan& P, int order, cudaStream_t st, int ilv_shift = -1) {
     for (auto& d : P.descs) d.order = order;
     P.order = order;
+    if (ilv_shift >= 0) {
+        set_interleave(P.descs, ilv_shift);
+        P.ilv_shift = ilv_shift;
+    }
     BL_CUDA(cudaMemcpyAsync(P.ws + P.L.descs, P.descs.data(),
                             sizeof(bl::ImageDesc) * P.descs.size(), cudaMemcpyHostToDevice, st));
     return 0;
@@ -758,16 +773,28 @@ int plan_autotune(bl_plan& P, cudaStream_t st) {
         if (it != g_tune_cache.end()) {
             P.cfg = it->second.cfg;
             P.run_ms = it->second.ms;
-            return plan_set_order(P, it->second.order, st);
+            return plan_set_order(P, it->second.order, st, it->second.ilv_shift);
         }
     }
     float best = 0.0f, t = 0.0f;
     LaunchCfg cfg;
     int order = 0;
-    if ((rc = plan_set_order(P, 0, st)) || (rc = plan_time(P, cfg, st, &best))) return rc;
+    int ilv_shift = bl::kIlvShift;
+    if ((rc = plan_set_order(P, 0, st, ilv_shift)) || (rc = plan_time(P, cfg, st, &best))) return rc;
     if ((rc = plan_set_order(P, 1, st)) || (rc = plan_time(P, cfg, st, &t))) return rc;
     if (t < best * (1.0f - kTuneMargin)) { best = t; order = 1; }
     if ((rc = plan_set_order(P, order, st))) return rc;
+    // interleave block of a batch of equal images: 64 to 4096 rays
+    if (P.descs[0].ilv > 1) {
+        for (int sh = 6; sh <= 12; sh += 2) {
+            if (sh == bl::kIlvShift) continue;
+            std::vector<bl::ImageDesc> probe = P.descs;
+            if (!set_interleave(probe, sh)) continue;
+            if ((rc = plan_set_order(P, order, st, sh)) || (rc = plan_time(P, cfg, st, &t))) return rc;
+            if (t < best * (1.0f - kTuneMargin)) { best = t; ilv_shift = sh; }
+        }
+        if ((rc = plan_set_order(P, order, st, ilv_shift))) return rc;
+    }
     const int geo_max = di.geo_blocks[P.precision];
     const int tr_max = di.transfer(P.precision, P.mlp, P.feat);
     int geo_best = geo_max;
@@ -789,7 +816,7 @@ int plan_autotune(bl_plan& P, cudaStream_t st) {
     P.cfg = cfg;
     P.run_ms = best;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = TuneVal{order, cfg, best};
+    g_tune_cache[key] = TuneVal{order, P.ilv_shift, cfg, best};
     return 0;
 }
 
@@ -1188,17 +1215,17 @@ int blacklight_trace_noalloc(const bl_camera_t* cam, const bl_metric_t* met,
         return fail(BL_EINVAL, "blacklight_trace_noalloc: %lld rays exceed its fixed scratch "
                     "(at most %lld rays, %zu bytes); use blacklight_trace",
                     (long long)rays, (long long)kNoAllocMaxRays, kNoAllocBytes);
-    const size_t need = make_layout(1, cam, met).total;
-    if (need > kNoAllocBytes)
-        return fail(BL_EINVAL, "blacklight_trace_noalloc: needs %zu bytes of scratch, has %zu",
-                    need, kNoAllocBytes);
     char* ws = nullptr;
     rc = noalloc_scratch(&ws);
     if (rc) return rc;
     // The counters at the head of the scratch are zeroed on the stream before each launch;
     // the rest is written before it is read, so stale contents from the last call are inert.
+    // When one wave of all rays does not fit (long fixed-step RK4/RK2 rays need up to 128
+    // record chunks each), trace_impl runs the rays in smaller waves inside the same array.
+    // The call always waits for its work: the anomaly counters live in the shared array, and
+    // the next call would zero them before an asynchronous caller could read them.
     return trace_impl(1, cam, met, grid, &freq_hz, out, ws, kNoAllocBytes, stream,
-                      flags & ~(uint32_t)BL_TIMING, true);
+                      flags & ~(uint32_t)(BL_TIMING | BL_ASYNC), true);
 }
 
 int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
@@ -1216,6 +1243,9 @@ int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_m
         if (config->ray_order < 0 || config->ray_order > 1 || config->geo_ctas_per_sm < 0 ||
             config->tr_ctas_per_sm < 0)
             return fail(BL_EINVAL, "config: ray_order 0 or 1, CTAs per SM >= 0");
+        const int b = config->ilv_block;
+        if (b != 0 && (b < 64 || b > 4096 || (b & (b - 1)) != 0))
+            return fail(BL_EINVAL, "config.ilv_block: 0 or a power of two in [64, 4096]");
     }
     const float* mlp = nullptr;
     if ((rc = common_mlp(n_images, grids, precision, &mlp, flags, outs))) return rc;
@@ -1246,11 +1276,16 @@ int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_m
     if (flags & BL_PLAN_AUTOTUNE) {
         rc = plan_autotune(*P, st);
     } else {
+        int sh = bl::kIlvShift;
         if (config) {
             P->cfg.geo_ctas = config->geo_ctas_per_sm;
             P->cfg.tr_ctas = config->tr_ctas_per_sm;
+            if (config->ilv_block > 0) {
+                sh = 0;
+                while ((1 << sh) < config->ilv_block) ++sh;
+            }
         }
-        rc = plan_set_order(*P, config ? config->ray_order : 0, st);
+        rc = plan_set_order(*P, config ? config->ray_order : 0, st, sh);
     }
     if (!rc) rc = plan_capture(*P, st);
     if (rc) {
@@ -1293,6 +1328,7 @@ int blacklight_plan_config(const bl_plan_t* plan, bl_launch_config_t* out) {
     out->geo_ctas_per_sm = plan->cfg.geo_ctas > 0 && plan->cfg.geo_ctas < geo_max ? plan->cfg.geo_ctas : geo_max;
     out->tr_ctas_per_sm = plan->cfg.tr_ctas > 0 && plan->cfg.tr_ctas < tr_max ? plan->cfg.tr_ctas : tr_max;
     out->run_ms = plan->run_ms;
+    out->ilv_block = plan->descs[0].ilv > 1 ? (1 << plan->descs[0].ilv_shift) : 0;
     return 0;
 }
 
@@ -1928,6 +1964,99 @@ int blacklight_bessel_k(int64_t n, const double* x, double* out, int32_t precisi
     ++g_launches;
     BL_CUDA(cudaGetLastError());
     BL_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return 0;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Best-of-reps rate (flops per second) of one probe launch; ms_out += one launch's time.
+template <class K, class L>
+int time_probe(K kernel, L launch, int reps, cudaStream_t st, double flops, double* rate,
+               double* ms_out) {
+    int per_sm = 0;
+    BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, bl::kPeakThreads, 0));
+    int dev = 0, sms = 0;
+    BL_CUDA(cudaGetDevice(&dev));
+    BL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
+    const double total = flops * (double)grid * bl::kPeakThreads;
+    cudaEvent_t e0, e1;
+    BL_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(ce, "cudaEventCreate"); }
+    double best = 0.0, last_ms = 0.0;
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) { launch(grid, st); ++g_launches; e = cudaGetLastError(); }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && r > 0 && ms > 0.0f) {   // launch 0 is the warm-up
+            const double v = total / (ms * 1e-3);
+            if (v > best) best = v;
+            last_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "peak probe");
+    *rate = best;
+    *ms_out += last_ms;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int blacklight_measure_peaks(bl_peaks_t* out, int32_t reps, void* stream) {
+    g_detail[0] = 0;
+    if (!out || out->size != sizeof(bl_peaks_t)) return fail(BL_EINVAL, "out: NULL or size mismatch");
+    if (reps < 1 || reps > 100) return fail(BL_EINVAL, "reps must be in [1, 100]");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    BL_CUDA(cudaGetDevice(&dev));
+    BL_CUDA(cudaDeviceGetAttribute(&out->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    BL_CUDA(cudaDeviceGetAttribute(&out->sm_clock_khz, cudaDevAttrClockRate, dev));
+    // the probes' results are stored only under a condition that never holds; the sink is a
+    // small stream-ordered buffer they never write
+    float* sink = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&sink, 65536 * sizeof(double), st);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(BL_ENOMEM, "cudaMallocAsync: %s", cudaGetErrorString(e)); }
+    // chain lengths for ~15 ms a launch on a GB300-class device
+    constexpr int kIt64 = 4096, kIt32 = 1 << 18, kItDf = 1 << 15;
+    constexpr int kCh = 8, kChDf = 4;
+    out->probe_ms = 0.0;
+    double r64 = 0.0, r32 = 0.0, rdf = 0.0;
+    int rc = time_probe(bl::fma_chain_kernel<double, kCh>,
+                        [&](unsigned g, cudaStream_t s) {
+                            bl::fma_chain_kernel<double, kCh><<<g, bl::kPeakThreads, 0, s>>>(
+                                (double*)sink, kIt64, 0.999999, 1e-6);
+                        }, reps, st, 2.0 * kCh * kIt64, &r64, &out->probe_ms);
+    if (!rc)
+        rc = time_probe(bl::fma_chain_kernel<float, kCh>,
+                        [&](unsigned g, cudaStream_t s) {
+                            bl::fma_chain_kernel<float, kCh><<<g, bl::kPeakThreads, 0, s>>>(
+                                sink, kIt32, 0.999999f, 1e-6f);
+                        }, reps, st, 2.0 * kCh * kIt32, &r32, &out->probe_ms);
+    if (!rc)
+        rc = time_probe(bl::df64_chain_kernel<kChDf>,
+                        [&](unsigned g, cudaStream_t s) {
+                            const bl::df64 a(0.999999), b(1e-6);
+                            bl::df64_chain_kernel<kChDf><<<g, bl::kPeakThreads, 0, s>>>(
+                                sink, kItDf, a.hi, a.lo, b.hi, b.lo);
+                        }, reps, st, 2.0 * kChDf * kItDf, &rdf, &out->probe_ms);
+    cudaFreeAsync(sink, st);
+    cudaError_t es = cudaStreamSynchronize(st);
+    if (rc) return rc;
+    if (es != cudaSuccess) return cuda_fail(es, "cudaStreamSynchronize");
+    out->fp64_tflops = r64 * 1e-12;
+    out->fp32_tflops = r32 * 1e-12;
+    out->df64_tflops = rdf * 1e-12;
     return 0;
 }
 

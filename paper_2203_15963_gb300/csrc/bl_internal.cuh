@@ -16,9 +16,10 @@ template <> struct RecStride<float> { static constexpr int v = 16; };    // 64 B
 constexpr int kChunk = 32;          // records per pool chunk
 constexpr int kMaxChunks = 128;     // chunks per ray -> at most 4096 samples per ray
 
-// Rays of the images of a batch are queued in blocks of this many consecutive rays of one
-// image when the batch interleaves its images.
-constexpr int64_t kIlvBlock = 256;
+// Rays of the images of a batch are queued in blocks of 2^kIlvShift consecutive rays of one
+// image when the batch interleaves its images (the default; plans may tune the block size).
+constexpr int kIlvShift = 8;
+constexpr int64_t kIlvBlock = int64_t(1) << kIlvShift;
 
 struct ImageDesc {
     // camera (Sec. 2.1)
@@ -30,7 +31,8 @@ struct ImageDesc {
     int32_t flat, precision;
     int32_t integrator;
     int32_t ilv;            // > 1: the batch's rays are queued interleaved over ilv images
-                            // in blocks of kIlvBlock rays (same value in every descriptor)
+                            // in blocks of 2^ilv_shift rays (same values in every descriptor)
+    int32_t ilv_shift;
     double f_step;
     // grid and plasma (Secs. 2.4-2.5)
     const float* prim;
@@ -58,8 +60,8 @@ struct ImageDesc {
     double r_cam, r_hor;
     // per-image constants of the transfer, in double (d_*) and float (f_*), derived once on
     // the host (and H, V by the camera-frame kernel) so that samples do no conversions
-    double d_c[16];
-    float f_c[16];
+    double d_c[20];
+    float f_c[20];
     float f_hh[4], f_vv[4];
 };
 
@@ -71,7 +73,10 @@ enum {
     kcBgPre,         // c (4 pi rho_unit)^1/2
     kcDlr,           // ln(r_max / r_min) / n_r
     kcLogRmin,       // ln r_min
-    kcRmin, kcRmax, kcSigma, kcRhigh, kcRlow, kcNeNi, kcFreq, kcLen, kcSpin, kcMass
+    kcRmin, kcRmax, kcSigma, kcRhigh, kcRlow, kcNeNi, kcFreq, kcLen, kcSpin, kcMass,
+    kcIDlr,          // 1 / kcDlr
+    kcNeFac,         // n_e per unit code density: kcNePre / (1 + n_i / n_e)
+    kcCount
 };
 
 struct RayHdr {

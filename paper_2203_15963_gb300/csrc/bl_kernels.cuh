@@ -156,10 +156,10 @@ __device__ __forceinline__ int64_t ray_pixel(const ImageDesc& im, int64_t p, int
 
 // Image, pixel and output index of global ray `ray`: from the device block list when there is
 // one (adaptive levels); for a batch of equal images, from the interleaved queue (blocks of
-// kIlvBlock rays taken from the images in turn: the last rays handed out are then every image's
-// last blocks, which in Morton order lie at the image corners, rather than one image's last
-// quarter, which holds part of the photon ring and its longest rays); else from the images'
-// consecutive ray ranges.
+// 2^ilv_shift rays taken from the images in turn: the last rays handed out are then every
+// image's last blocks, which in Morton order lie at the image corners, rather than one image's
+// last quarter, which holds part of the photon ring and its longest rays); else from the
+// images' consecutive ray ranges.
 __device__ __forceinline__ void setup_ray(const ImageDesc* imgs, int n_images, const BlockSource& bs,
                                           int64_t ray, int& q, int64_t& opix, int& i, int& j) {
     if (bs.entries) {
@@ -173,9 +173,10 @@ __device__ __forceinline__ void setup_ray(const ImageDesc* imgs, int n_images, c
         opix = ray;
     } else if (imgs[0].ilv > 1) {
         // equal images interleaved: block b of the queue is block b / ilv of image b % ilv
-        const int64_t b = ray / kIlvBlock, nb = imgs[0].ilv;
+        const int sh = imgs[0].ilv_shift;
+        const int64_t b = ray >> sh, nb = imgs[0].ilv;
         q = (int)(b % nb);
-        opix = ray_pixel(imgs[q], (b / nb) * kIlvBlock + (ray - b * kIlvBlock), i, j);
+        opix = ray_pixel(imgs[q], ((b / nb) << sh) + (ray - (b << sh)), i, j);
     } else {
         q = find_image(imgs, n_images, ray);
         opix = ray_pixel(imgs[q], ray - imgs[q].ray_offset, i, j);
@@ -615,14 +616,30 @@ __device__ __forceinline__ bool emit_quartic_f(const RecordSink<R>& sink, int64_
     return ok;
 }
 
+// eps^(-1/5) for the FP64 step control (factor 0.9 eps^-1/5, clamped to [0.2, 10] by the
+// caller): a single-precision seed refined by two Newton steps for y^-5 = eps,
+// y <- y (6 - eps y^5) / 5, each squaring the relative error (1e-6 -> 3e-12 -> rounding), in
+// 12 FP64 operations instead of a double-precision pow. Arguments whose factor lies beyond
+// the clamp return a value beyond it.
+__device__ __forceinline__ double inv_fifth_root(double e) {
+    if (e < 1e-6) return 1e3;
+    if (e > 1e30) return 1e-3;
+    double y = (double)__powf((float)e, -0.2f);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double y2 = y * y;
+        const double y5 = y2 * y2 * y;
+        y = (y * 0.2) * fma(-e, y5, 6.0);
+    }
+    return y;
+}
+
 template <class R, class G>
-__global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const ImageDesc* __restrict__ imgs,
-                                                          int n_images, int64_t ray_begin,
-                                                          int64_t ray_end,
-                                                          RayHdr* __restrict__ hdr,
-                                                          RecordSink<R> sink, int record,
-                                                          BlockSource bs,
-                                                          const RayInit* __restrict__ init) {
+__device__ __forceinline__ void geodesic_body(const ImageDesc* __restrict__ imgs,
+                                              int n_images, int64_t ray_begin, int64_t ray_end,
+                                              RayHdr* __restrict__ hdr, RecordSink<R> sink,
+                                              int record, BlockSource bs,
+                                              const RayInit* __restrict__ init) {
     // rays [ray_begin, ray_end) of the batch form this wave; hdr, init and the chunk tables
     // are indexed by ray - ray_begin
     const int64_t re = wave_end(bs, ray_end);
@@ -1013,7 +1030,7 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
 #pragma unroll
             for (int c = 0; c < 8; ++c) { y[c] = y5[c]; if (c != 4) KX(0, c) = KX(6, c); }
             if constexpr (kNative) {
-                double fac = (eps == 0.0) ? 10.0 : 0.9 * pow(eps, -0.2);
+                double fac = (eps == 0.0) ? 10.0 : 0.9 * inv_fifth_root(eps);
                 fac = fmin(10.0, fmax(0.2, fac));
                 if (prev_rej) fac = fmin(fac, 1.0);
                 h = h * A::from(fac);
@@ -1034,7 +1051,7 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
         } else {
             double fac;
             if constexpr (kNative) {
-                fac = fmax(0.2, 0.9 * pow(eps, -0.2));
+                fac = fmax(0.2, 0.9 * inv_fifth_root(eps));
                 h = h * A::from(fac);
             } else {
                 h = h * G(fmaxf(0.2f, 0.9f * powf((float)eps, -0.2f)));
@@ -1079,6 +1096,29 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
 #undef KX
 #undef KR
 #undef KSLOT
+
+template <class R, class G>
+__global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const ImageDesc* __restrict__ imgs,
+                                                          int n_images, int64_t ray_begin,
+                                                          int64_t ray_end,
+                                                          RayHdr* __restrict__ hdr,
+                                                          RecordSink<R> sink, int record,
+                                                          BlockSource bs,
+                                                          const RayInit* __restrict__ init) {
+    geodesic_body<R, G>(imgs, n_images, ray_begin, ray_end, hdr, sink, record, bs, init);
+}
+
+// Resident CTAs per SM the FP64-form geodesic kernel is compiled for.
+#ifndef BL_GEO64_MIN_CTAS
+#define BL_GEO64_MIN_CTAS 3
+#endif
+// The FP64 form (FP64 state, FP64 records) with its own register budget.
+__global__ void __launch_bounds__(128, BL_GEO64_MIN_CTAS) geodesic_kernel_fp64(
+        const ImageDesc* __restrict__ imgs, int n_images, int64_t ray_begin, int64_t ray_end,
+        RayHdr* __restrict__ hdr, RecordSink<double> sink, int record, BlockSource bs,
+        const RayInit* __restrict__ init) {
+    geodesic_body<double, double>(imgs, n_images, ray_begin, ray_end, hdr, sink, record, bs, init);
+}
 
 // Per-image constant in the transfer arithmetic.
 template <class T>
@@ -1294,6 +1334,35 @@ __global__ void grid_pack_kernel(const float* __restrict__ planes, float* __rest
     }
 }
 
+// A grid value (float) in the sampling arithmetic T. float -> double is exact; it is done
+// with integer operations on the bit pattern instead of a conversion instruction, which on
+// this hardware shares the scarce FP64 pipe with the arithmetic (a trilinear sample converts
+// 64 values): the exponent is rebiased (127 -> 1023, all ones kept for inf and NaN) and the
+// significand widened; zeros keep their sign; subnormal floats (exponent field 0, nonzero)
+// take the conversion instruction.
+template <class T>
+__device__ __forceinline__ T grid_val(float f) {
+    if constexpr (sizeof(T) == 4) {
+        return f;
+    } else {
+        const uint32_t b = __float_as_uint(f);
+        const uint32_t e = b & 0x7f800000u, sgn = b & 0x80000000u;
+        if (e == 0u && (b & 0x7fffffffu) != 0u) return (double)f;
+        uint32_t hi = sgn | (((b & 0x7fffffffu) >> 3) + 0x38000000u);
+        if (e == 0x7f800000u) hi += 0x38000000u;
+        const uint32_t lo = b << 29;
+        return e == 0u ? __hiloint2double((int)sgn, 0) : __hiloint2double((int)hi, (int)lo);
+    }
+}
+
+// x is neither NaN nor infinite (exponent field not all ones)
+__device__ __forceinline__ bool finite_bits(float x) {
+    return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u;
+}
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
+}
+
 template <class T, bool kSlow = false>
 __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t,
                                           const KSGeom<T>& G, Plasma<T>& P) {
@@ -1306,8 +1375,10 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
     const T sth = fsqrt(T(1) - cth * cth);
     const T twopi = T(2.0 * kPi);
     // phi = arg(x + i y) - arg(r + i a) = arg((x + i y)(r - i a)), in (-pi, pi]; one wrap
-    // puts it in [0, 2 pi) (fmod by 2 pi would return such a value unchanged)
-    T ph = atan2(x[1] * r - x[0] * a, x[0] * r + x[1] * a);
+    // puts it in [0, 2 pi) (fmod by 2 pi would return such a value unchanged). Its sine and
+    // cosine are that complex number normalised (on the axis, where it vanishes, phi = 0).
+    const T zre = x[0] * r + x[1] * a, zim = x[1] * r - x[0] * a;
+    T ph = atan2(zim, zre);
     if (ph < T(0)) ph += twopi;
     if (ph >= twopi) ph -= twopi;
     const int nr = im.nr, nt = im.nt, np = im.nph;
@@ -1332,14 +1403,16 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
         prim += (size_t)s0 * 8 * plane;
     }
     T pv[8];
-    const T dlr = ic<T>(im, kcDlr);
+    // fractional cell coordinates: (ln r - ln r_min) / dlr, theta / (pi / n_theta),
+    // phi / (2 pi / n_phi), each as a product with the precomputed reciprocal cell size
+    const T idlr = ic<T>(im, kcIDlr);
     const T lrmin = ic<T>(im, kcLogRmin);
-    const T dth = T(kPi) / T(nt);
-    const T dph = twopi / T(np);
+    const T idth = T(nt) * T(1.0 / kPi);
+    const T idph = T(np) * T(0.5 / kPi);
     if (im.interp == 0) {
-        int i = (int)floor(fq(flog(r) - lrmin, dlr));
-        int j = (int)floor(fq(th, dth));
-        int k = (int)floor(fq(ph, dph));
+        int i = (int)floor((flog(r) - lrmin) * idlr);
+        int j = (int)floor(th * idth);
+        int k = (int)floor(ph * idph);
         i = min(max(i, 0), nr - 1);
         j = min(max(j, 0), nt - 1);
         k = ((k % np) + np) % np;
@@ -1348,26 +1421,26 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
             float c[8];
             load_cell(prim, base, c);
 #pragma unroll
-            for (int v = 0; v < 8; ++v) pv[v] = (T)c[v];
+            for (int v = 0; v < 8; ++v) pv[v] = grid_val<T>(c[v]);
             if (kSlow && prim1) {
                 load_cell(prim1, base, c);
 #pragma unroll
-                for (int v = 0; v < 8; ++v) pv[v] = (T(1) - wt1) * pv[v] + wt1 * (T)c[v];
+                for (int v = 0; v < 8; ++v) pv[v] = (T(1) - wt1) * pv[v] + wt1 * grid_val<T>(c[v]);
             }
         } else {
 #pragma unroll
-            for (int v = 0; v < 8; ++v) pv[v] = (T)__ldg(prim + v * plane + base);
+            for (int v = 0; v < 8; ++v) pv[v] = grid_val<T>(__ldg(prim + v * plane + base));
             if (kSlow && prim1) {
 #pragma unroll
                 for (int v = 0; v < 8; ++v)
-                    pv[v] = (T(1) - wt1) * pv[v] + wt1 * (T)__ldg(prim1 + v * plane + base);
+                    pv[v] = (T(1) - wt1) * pv[v] + wt1 * grid_val<T>(__ldg(prim1 + v * plane + base));
             }
         }
     } else {
         int i0, j0;
         T wr, wt;
         {
-            T fi = fq(flog(r) - lrmin, dlr) - T(0.5);
+            T fi = (flog(r) - lrmin) * idlr - T(0.5);
             if (nr == 1) { i0 = 0; wr = T(0); }
             else {
                 fi = fi < T(0) ? T(0) : (fi > T(nr - 1) ? T(nr - 1) : fi);
@@ -1377,7 +1450,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
             }
         }
         {
-            T fj = fq(th, dth) - T(0.5);
+            T fj = th * idth - T(0.5);
             if (nt == 1) { j0 = 0; wt = T(0); }
             else {
                 fj = fj < T(0) ? T(0) : (fj > T(nt - 1) ? T(nt - 1) : fj);
@@ -1387,7 +1460,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
             }
         }
         const int i1 = nr == 1 ? 0 : i0 + 1, j1 = nt == 1 ? 0 : j0 + 1;
-        const T fk = fq(ph, dph) - T(0.5);
+        const T fk = ph * idph - T(0.5);
         const T fkf = floor(fk);
         const int k0 = (((int)fkf) % np + np) % np;
         const int k1 = (k0 + 1) % np;
@@ -1407,12 +1480,12 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
                 float c[8];
                 load_cell(pp, cell[0], c);
 #pragma unroll
-                for (int v = 0; v < 8; ++v) out[v] = w[0] * (T)c[v];
+                for (int v = 0; v < 8; ++v) out[v] = w[0] * grid_val<T>(c[v]);
 #pragma unroll
                 for (int n = 1; n < 8; ++n) {
                     load_cell(pp, cell[n], c);
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) out[v] = out[v] + w[n] * (T)c[v];
+                    for (int v = 0; v < 8; ++v) out[v] = out[v] + w[n] * grid_val<T>(c[v]);
                 }
             };
             tri8(prim, pv);
@@ -1424,10 +1497,10 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
             }
         } else {
             auto tri = [&](const float* __restrict__ pp) -> T {
-                return w000 * (T)__ldg(pp + o00 + i0) + w001 * (T)__ldg(pp + o00 + i1) +
-                       w010 * (T)__ldg(pp + o01 + i0) + w011 * (T)__ldg(pp + o01 + i1) +
-                       w100 * (T)__ldg(pp + o10 + i0) + w101 * (T)__ldg(pp + o10 + i1) +
-                       w110 * (T)__ldg(pp + o11 + i0) + w111 * (T)__ldg(pp + o11 + i1);
+                return w000 * grid_val<T>(__ldg(pp + o00 + i0)) + w001 * grid_val<T>(__ldg(pp + o00 + i1)) +
+                       w010 * grid_val<T>(__ldg(pp + o01 + i0)) + w011 * grid_val<T>(__ldg(pp + o01 + i1)) +
+                       w100 * grid_val<T>(__ldg(pp + o10 + i0)) + w101 * grid_val<T>(__ldg(pp + o10 + i1)) +
+                       w110 * grid_val<T>(__ldg(pp + o11 + i0)) + w111 * grid_val<T>(__ldg(pp + o11 + i1));
             };
 #pragma unroll
             for (int v = 0; v < 8; ++v) pv[v] = tri(prim + v * plane);
@@ -1438,9 +1511,24 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
             }
         }
     }
+    // non-finite data (a NaN or infinite primitive at any corner of the stencil) carry no
+    // plasma; the test reads the exponent bits (integer operations)
+    {
+        bool fin = true;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) fin = fin && finite_bits(pv[v]);
+        if (!fin) return false;
+    }
     // spherical -> Cartesian KS vectors (Jacobian columns d x^a / d(r, theta, phi))
-    T sph, cph;
-    fsincos_2pi(ph, &sph, &cph);
+    T sph = T(0), cph = T(1);
+    {
+        const T zz = zre * zre + zim * zim;
+        if (zz > T(0)) {
+            const T iz = rsqrt(zz);
+            cph = zre * iz;
+            sph = zim * iz;
+        }
+    }
     const T J[3][3] = {{sth * cph, cth * (r * cph - a * sph), sth * (-r * sph - a * cph)},
                        {sth * sph, cth * (r * sph + a * cph), sth * (r * cph - a * sph)},
                        {cth, -r * sth, T(0)}};
@@ -1474,9 +1562,8 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
     const T ratio = fq(ic<T>(im, kcRhigh) + b2 * ic<T>(im, kcRlow), T(1) + b2);
     const T rr = ic<T>(im, kcNeNi);
     const T th_e = fq(ic<T>(im, kcTePre) * fq(p, rho) * (rr + T(1)), rr + ratio);
-    if (!(th_e >= T(0.05))) return false;
     P.th = th_e;
-    P.ne = fq(rho * ic<T>(im, kcNePre), T(1) + fq(T(1), rr));
+    P.ne = rho * ic<T>(im, kcNeFac);
     P.bg = fsqrt(P.bsq) * ic<T>(im, kcBgPre);
     P.rho = rho;
     P.p = p;
@@ -1839,9 +1926,8 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
     }
 }
 // The transfer kernel: FP32 (mixed and fast forms) at up to 128 registers, 4 CTAs of 128
-// threads an SM; FP64 capped at 96 registers in CTAs of 64 threads, which keeps 20 warps an SM
-// resident instead of 8 (measured 835 -> 650 ms on the 9-image step; the FP32 kernel is
-// fastest uncapped).
+// threads an SM; FP64 capped (BL_TR64_MAXNREG) in CTAs of 64 threads, which keeps more warps an
+// SM resident (the FP32 kernel is fastest uncapped).
 template <class T, class R, int kF>
 __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restrict__ imgs,
                                                        int n_images, int64_t ray_begin,
@@ -1852,9 +1938,19 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
                                                        Counters* ctr, BlockSource bs) {
     transfer_body<T, R, kF>(imgs, n_images, ray_begin, ray_end, hdr, pool, chunks, ctr, bs);
 }
-constexpr int kTransferFp64Threads = 64;
+// Register cap and CTA size of the FP64 transfer kernel. Its FP64 arithmetic runs at 1/64 of
+// the FP32 rate with long dependent latencies, so resident warps matter more than spills to
+// L1: measured on the 9 x 256^2 step, 96 registers (20 warps an SM) 459 ms, 80: 441 ms, 72:
+// 429 ms, 64 (32 warps an SM): 405 ms, 56: 395 ms, 48 (42 warps an SM): 388 ms.
+#ifndef BL_TR64_MAXNREG
+#define BL_TR64_MAXNREG 48
+#endif
+#ifndef BL_TR64_THREADS
+#define BL_TR64_THREADS 64
+#endif
+constexpr int kTransferFp64Threads = BL_TR64_THREADS;
 template <int kF>
-__global__ void __maxnreg__(96) transfer_kernel_fp64(const ImageDesc* __restrict__ imgs,
+__global__ void __maxnreg__(BL_TR64_MAXNREG) transfer_kernel_fp64(const ImageDesc* __restrict__ imgs,
                                                      int n_images, int64_t ray_begin,
                                                      int64_t ray_end,
                                                      const RayHdr* __restrict__ hdr,

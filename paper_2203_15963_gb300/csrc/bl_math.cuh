@@ -33,11 +33,11 @@ __device__ __forceinline__ T fq(T a, T b) {
     else return a / b;
 }
 
-// exp, log, cube root, cos and sin-cos on the FP32 coefficient path through the hardware
+// exp, log, cube root and cos on the FP32 coefficient path through the hardware
 // approximations: __expf within 2 + 1.2 |x| ulp, __logf within 2^-21.4 absolute on [0.5, 2]
-// and 3 ulp elsewhere, the cube root as exp(log(x) / 3) from those two, __cosf and __sincosf
-// within about 2^-21 absolute for |x| <= pi (the arguments here are reduced to [-pi, pi] or
-// multiply terms that vanish where they are not). FP64: the libm functions.
+// and 3 ulp elsewhere, the cube root as exp(log(x) / 3) from those two, __cosf within about
+// 2^-21 absolute for |x| <= pi (its argument here multiplies a term that vanishes where it is
+// not). FP64: the libm functions.
 template <class T>
 __device__ __forceinline__ T fexp(T x) {
     if constexpr (sizeof(T) == 4) return __expf(x);
@@ -71,16 +71,6 @@ __device__ __forceinline__ T fsqrt(T x) {
         return sqrt(x);
     }
 }
-// sin and cos of an angle in [0, 2 pi)
-template <class T>
-__device__ __forceinline__ void fsincos_2pi(T x, T* s, T* c) {
-    if constexpr (sizeof(T) == 4) {
-        __sincosf(x > 3.14159265f ? x - 6.28318531f : x, s, c);
-    } else {
-        sincos(x, s, c);
-    }
-}
-
 // CGS constants (CODATA 2018; IAU 2015 nominal solar mass).
 constexpr double kC = 2.99792458e10;
 constexpr double kE = 4.80320471e-10;
@@ -366,6 +356,7 @@ __device__ __forceinline__ void coh_pc_step(Coh<T>& n, const T A0[4][4], const T
 // ---------------------------------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ void bessel_k012_scaled(T x, T& k0, T& k1, T& k2) {
+    const T ix = fq(T(1), x);
     if (x <= T(2)) {
         const T t = T(0.5) * x;
         const T t2 = t * t;
@@ -378,18 +369,18 @@ __device__ __forceinline__ void bessel_k012_scaled(T x, T& k0, T& k1, T& k2) {
         const T p1 = T(1) + t2 * (T(0.15443144) + t2 * (T(-0.67278579) + t2 * (T(-0.18156897) +
                      t2 * (T(-0.01919402) + t2 * (T(-0.00110404) + t2 * T(-0.00004686))))));
         const T K0 = -lg * i0 + p0;
-        const T K1 = fq(x * lg * i1 + p1, x);
+        const T K1 = (x * lg * i1 + p1) * ix;
         k0 = K0 * ex;
         k1 = K1 * ex;
     } else {
-        const T u = fq(T(2), x);
+        const T u = T(2) * ix;
         const T sx = rsqrt(x);
         k0 = sx * (T(1.25331414) + u * (T(-0.07832358) + u * (T(0.02189568) + u * (T(-0.01062446) +
                    u * (T(0.00587872) + u * (T(-0.00251540) + u * T(0.00053208)))))));
         k1 = sx * (T(1.25331414) + u * (T(0.23498619) + u * (T(-0.03655620) + u * (T(0.01504268) +
                    u * (T(-0.00780353) + u * (T(0.00325614) + u * T(-0.00068245)))))));
     }
-    k2 = k0 + fq(T(2), x) * k1;
+    k2 = k0 + T(2) * ix * k1;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -412,49 +403,49 @@ __device__ __forceinline__ void synchrotron_coefficients(T ne, T th, T bg, T nu,
     const T sth = fsqrt(sth2 > T(0) ? sth2 : T(0));
     const T nub = T(kE / (2.0 * kPi * kMe * kC)) * bg;
     const T z = fq(T(1), th);
+    const T inu = fq(T(1), nu);
     T k0, k1, k2;
     bessel_k012_scaled(z, k0, k1, k2);
+    const T ik2 = fq(T(1), k2);
     if (sth > T(0)) {
         const T x = fq(nu, T(1.5) * nub * sth * th * th);
         const T x13 = fcbrt(x);
         const T ix13 = fq(T(1), x13);
         const T ix23 = ix13 * ix13;
-        const T ex = fexp(T(-1.8899) * x13);
+        // 1 / K_2(z) = exp(z) / k2 (k2 scaled), and exp(z) is taken together with the shape
+        // functions' exp(-1.8899 x^1/3): their product stays finite (and underflows to 0 for
+        // cold plasma) where exp(z) = exp(1 / Theta_e) alone would overflow
+        const T ex = fexp(z - T(1.8899) * x13);
         const T ii = T(2.5651) * (T(1) + T(1.92) * ix13 + T(0.9977) * ix23) * ex;
         const T iq = T(2.5651) * (T(1) + T(0.932) * ix13 + T(0.4998) * ix23) * ex;
-        const T iv = (fq(T(1.8138), x) + T(3.423) * ix23 + T(0.02955) * rsqrt(x) + T(2.0377) * ix13) * ex;
-        // n e^2 nu / (sqrt3 c) / K_2(z) = n e^2 nu / (sqrt3 c) exp(-z) / (exp(z) K_2) * exp(z)...
-        // 1 / K_2(z) = exp(z) / k2 (k2 is scaled).
-        const T pre = ne * T(kE * kE / (1.7320508075688772 * kC)) * nu * fq(fexp(z), k2);
+        // 1 / x = (x^-1/3)^3
+        const T iv = (T(1.8138) * ix23 * ix13 + T(3.423) * ix23 + T(0.02955) * rsqrt(x) +
+                      T(2.0377) * ix13) * ex;
+        const T pre = ne * T(kE * kE / (1.7320508075688772 * kC)) * nu * ik2;
         out[0] = pre * ii;
         out[1] = pre * iq;
-        out[2] = pre * fq(T(4), T(3) * th) * fq(cth, sth) * iv;
-        const T hkt = fq(T(kH / (kMe * kC * kC)) * nu, th);
+        out[2] = pre * (T(4.0 / 3.0) * z) * fq(cth, sth) * iv;
+        const T hkt = T(kH / (kMe * kC * kC)) * nu * z;
         // 1 / B_nu = c^2 expm1(h nu / k T) / (2 h nu^3), ordered to stay inside float range
-        const T cnu = fq(T(kC), nu);
-        const T ibnu = expm1(hkt) * (cnu * cnu) * fq(T(0.5 / kH), nu);
+        const T cnu = T(kC) * inu;
+        const T ibnu = expm1(hkt) * (cnu * cnu) * (T(0.5 / kH) * inu);
         out[3] = out[0] * ibnu;
         out[4] = out[1] * ibnu;
         out[5] = out[2] * ibnu;
     }
-    const T X = th * fsqrt(fq(T(1.4142135623730951e3) * sth * nub, nu));
-    // X^1.035 and X^1.2: in FP32 as exponentials of one shared logarithm (X = 0 gives
-    // log X = -inf and both powers 0, as pow does)
-    T p1, p2;
-    if constexpr (sizeof(T) == 4) {
-        const T lX = flog(X);
-        p1 = fexp(T(1.035) * lX);
-        p2 = fexp(T(1.2) * lX);
-    } else {
-        p1 = pow(X, T(1.035));
-        p2 = pow(X, T(1.2));
-    }
-    const T fm = T(2.011) * fexp(-fq(p1, T(4.7))) - fcos(T(0.5) * X) * fexp(-fq(p2, T(2.73))) -
-                 T(0.011) * fexp(-fq(X, T(47.2)));
+    const T X = th * fsqrt(T(1.4142135623730951e3) * sth * nub * inu);
+    // X^1.035 and X^1.2 as exponentials of one shared logarithm (X = 0 gives log X = -inf and
+    // both powers 0, as pow does)
+    const T lX = flog(X);
+    const T p1 = fexp(T(1.035) * lX);
+    const T p2 = fexp(T(1.2) * lX);
+    const T fm = T(2.011) * fexp(-p1 * T(1.0 / 4.7)) - fcos(T(0.5) * X) * fexp(-p2 * T(1.0 / 2.73)) -
+                 T(0.011) * fexp(-X * T(1.0 / 47.2));
     const T gm = T(1) - T(0.11) * log1p(T(0.035) * X);
     const T base = ne * T(kE * kE / (kMe * kC));
-    out[6] = base * nub * nub * sth2 / (nu * nu * nu) * fm * (fq(k1, k2) + T(6) * th);
-    out[7] = T(2) * base * nub * cth / (nu * nu) * fq(k0, k2) * gm;
+    const T inu2 = inu * inu;
+    out[6] = base * nub * nub * sth2 * (inu2 * inu) * fm * (k1 * ik2 + T(6) * th);
+    out[7] = T(2) * base * nub * cth * inu2 * (k0 * ik2) * gm;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -469,6 +460,20 @@ __device__ __forceinline__ T unpolarized_step(T j, T alpha, T dl, T i0) {
         return exp(-dtau) * (i0 + expm1(dtau) * j / alpha);
     }
     return i0 + j * dl;
+}
+
+// 1/k for the Taylor terms k = 1..14 of the Stokes step, correctly rounded in each type (a
+// table read instead of a division inside a loop of run-time length).
+__constant__ double c_inv_int64[15] = {0.0, 1.0, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6,
+                                       1.0 / 7, 1.0 / 8, 1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12,
+                                       1.0 / 13, 1.0 / 14};
+__constant__ float c_inv_int32[15] = {0.0f, 1.0f, 1.0f / 2, 1.0f / 3, 1.0f / 4, 1.0f / 5,
+                                      1.0f / 6, 1.0f / 7, 1.0f / 8, 1.0f / 9, 1.0f / 10,
+                                      1.0f / 11, 1.0f / 12, 1.0f / 13, 1.0f / 14};
+template <class T>
+__device__ __forceinline__ T inv_int(int k) {
+    if constexpr (sizeof(T) == 8) return c_inv_int64[k];
+    else return c_inv_int32[k];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -511,9 +516,10 @@ __device__ __forceinline__ void stokes_step(const T c[8], const T s0[4], T dl, T
         }
         return;
     }
-    // Z = -M dl, z = J dl; infinity norm of the augmented matrix. M_02 = M_13 = M_20 = M_31 = 0
-    // and J_2 = 0 (no U terms) are left out of the sums below: IEEE arithmetic may not drop a
-    // product with a zero by itself.
+    // Z = -M dl, z = J dl. M_02 = M_13 = M_20 = M_31 = 0 and J_2 = 0 (no U terms) are left
+    // out of the sums below: IEEE arithmetic may not drop a product with a zero by itself.
+    // The series of exp([Z z; 0 0]) converges at the rate of Z alone (its z column only
+    // multiplies), so scaling and Taylor degree follow the infinity norm of Z.
     auto mz = [](int i, int j) {
         return (i == 0 && j == 2) || (i == 1 && j == 3) || (i == 2 && j == 0) || (i == 3 && j == 1);
     };
@@ -528,7 +534,6 @@ __device__ __forceinline__ void stokes_step(const T c[8], const T s0[4], T dl, T
             if (!mz(i, j)) rs += fabs(Z[i][j]);
         }
         z[i] = i == 2 ? T(0) : J[i] * dl;
-        if (i != 2) rs += fabs(z[i]);
         nrm = rs > nrm ? rs : nrm;
     }
     int s = 0;
@@ -545,20 +550,36 @@ __device__ __forceinline__ void stokes_step(const T c[8], const T s0[4], T dl, T
             if (!mz(i, j)) Z[i][j] *= sc;
         if (i != 2) z[i] *= sc;
     }
-    // Taylor degree: ||Z|| <= 1/2, truncation 2^-(m+1)/(m+1)! below the type's rounding.
+    // Taylor degree of the matrix form: ||Z|| <= 1/2, truncation 2^-(m+1)/(m+1)! below the
+    // type's rounding.
     constexpr int m = sizeof(T) == 8 ? 13 : 8;
     if (s <= 1) {
         // Only the action on [s0; 1] is needed: with A = [Z z; 0 0] (scaled), exp(A) x is
-        // x + A (x + A/2 (x + ... (x + A x / m))), the last component staying 1, so each term
+        // x + A (x + A/2 (x + ... (x + A x / d))), the last component staying 1, so each term
         // is one 4x4 matrix-vector product (16 FMAs) instead of a matrix product (64). The
-        // scaled map is applied 2^s times (at most twice) in place of the squarings.
+        // scaled map is applied 2^s times (at most twice) in place of the squarings. The
+        // degree d is the smallest whose truncation, ||Z||^d (||Z|| ||s0|| + ||z||) / (d+1)!,
+        // is below the unit roundoff u relative to ||Z|| ||s0|| + ||z||: the first d with
+        // ||Z|| <= theta_d = (u (d+1)!)^(1/d) (u = 2^-53 in FP64, 2^-24 in FP32), at most 14
+        // (FP64) or 8 (FP32) for ||Z|| <= 1/2.
+        constexpr int dmax = sizeof(T) == 8 ? 14 : 8;
+        constexpr float th64[14] = {2.2e-16f, 2.58e-8f, 1.38e-5f, 3.39e-4f, 2.40e-3f, 9.07e-3f,
+                                    2.39e-2f, 5.01e-2f, 9.03e-2f, 0.146f, 0.218f, 0.306f,
+                                    0.411f, 0.531f};
+        constexpr float th32[8] = {1.19e-7f, 5.98e-4f, 1.126e-2f, 5.17e-2f, 0.1338f, 0.2587f,
+                                   0.4225f, 0.6192f};
+        const float nz = (float)(nrm * sc);
+        int d = 1;
+#pragma unroll
+        for (int q = 0; q < dmax - 1; ++q)
+            if (nz > (sizeof(T) == 8 ? th64[q] : th32[q])) d = q + 2;
         T v[4] = {s0[0], s0[1], s0[2], s0[3]};
 #pragma unroll 1
         for (int rep = 0; rep < (1 << s); ++rep) {
             T t[4] = {v[0], v[1], v[2], v[3]};
-#pragma unroll
-            for (int k = m; k >= 1; --k) {
-                const T ik = T(1) / T(k);
+#pragma unroll 1
+            for (int k = d; k >= 1; --k) {
+                const T ik = inv_int<T>(k);
                 T tn[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {

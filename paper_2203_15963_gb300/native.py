@@ -84,7 +84,7 @@ MLP_PARAMS = 4906
 
 class LaunchConfig(C.Structure):
     _fields_ = [("size", C.c_uint32), ("ray_order", C.c_int32), ("geo_ctas_per_sm", C.c_int32),
-                ("tr_ctas_per_sm", C.c_int32), ("run_ms", C.c_float)]
+                ("tr_ctas_per_sm", C.c_int32), ("run_ms", C.c_float), ("ilv_block", C.c_int32)]
 
 
 BL_PLAN_AUTOTUNE = 4
@@ -97,6 +97,12 @@ class Adapt(C.Structure):
 
 
 BL_CRIT_ABS_GRAD, BL_CRIT_REL_GRAD, BL_CRIT_ABS_LAPL, BL_CRIT_REL_LAPL = 0, 1, 2, 3
+
+
+class Peaks(C.Structure):
+    _fields_ = [("size", C.c_uint32), ("sm_count", C.c_int32), ("sm_clock_khz", C.c_int32),
+                ("fp64_tflops", C.c_double), ("fp32_tflops", C.c_double),
+                ("df64_tflops", C.c_double), ("probe_ms", C.c_double)]
 
 
 class Out(C.Structure):
@@ -167,6 +173,7 @@ def load():
     L.blacklight_plan_level_rays.argtypes = [P, C.POINTER(C.c_int32), P]
     L.blacklight_selftest_wait.argtypes = [C.c_int64, C.c_int32, P]
     L.blacklight_set_memory_retention.argtypes = [C.c_uint64]
+    L.blacklight_measure_peaks.argtypes = [C.POINTER(Peaks), C.c_int32, P]
     L.blacklight_trace_host_batch.argtypes = [C.c_int32, C.POINTER(Camera), C.POINTER(Metric),
                                               C.POINTER(Grid), C.POINTER(C.c_double),
                                               C.POINTER(Out), P, C.c_uint32]
@@ -360,7 +367,8 @@ class Plan:
         if config is not None:
             cfg = LaunchConfig(C.sizeof(LaunchConfig), int(config.get("ray_order", 0)),
                                int(config.get("geo_ctas_per_sm", 0)),
-                               int(config.get("tr_ctas_per_sm", 0)), 0.0)
+                               int(config.get("tr_ctas_per_sm", 0)), 0.0,
+                               int(config.get("ilv_block", 0)))
         h = C.c_void_p()
         _check(L.blacklight_plan_create(n, ca, ma, ga, fa, oa,
                                         None if cfg is None else C.byref(cfg),
@@ -376,10 +384,11 @@ class Plan:
         return _check(load().blacklight_plan_check(self._h, _stream(stream)))
 
     def config(self):
-        c = LaunchConfig(C.sizeof(LaunchConfig), 0, 0, 0, 0.0)
+        c = LaunchConfig(C.sizeof(LaunchConfig), 0, 0, 0, 0.0, 0)
         _check(load().blacklight_plan_config(self._h, C.byref(c)))
         return {"ray_order": c.ray_order, "geo_ctas_per_sm": c.geo_ctas_per_sm,
-                "tr_ctas_per_sm": c.tr_ctas_per_sm, "run_ms": c.run_ms}
+                "tr_ctas_per_sm": c.tr_ctas_per_sm, "run_ms": c.run_ms,
+                "ilv_block": c.ilv_block}
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -471,6 +480,14 @@ BL_ETIMEOUT = -5
 
 def blacklight_set_memory_retention(nbytes) -> int:
     return _check(load().blacklight_set_memory_retention(int(nbytes)))
+
+
+def blacklight_measure_peaks(reps=5, stream=None) -> dict:
+    """Measured FP64, FP32 and double-float multiply-add throughput of the current device
+    (TFLOP/s, best of `reps` launches) with its SM count and maximum SM clock."""
+    p = Peaks(size=C.sizeof(Peaks))
+    _check(load().blacklight_measure_peaks(C.byref(p), int(reps), _stream(stream)))
+    return {k: getattr(p, k) for k, _ in Peaks._fields_ if k != "size"}
 
 
 def blacklight_selftest_wait(max_cycles, arrive, stream=None) -> int:

@@ -86,7 +86,36 @@ def test_forward_matches_oracle_with_bf16_operands():
     assert np.max(np.abs(got - want) / sc) <= 0.1
 
 
+def _grad_abs(p, F, O, forward_roundings=6):
+    """Magnitude bound of each gradient element's terms: the float64 backward pass of the same
+    network with every operand replaced by its absolute value (|W|, |activations|, |SiLU'|),
+    started from |E| plus the forward rounding error of the outputs, forward_roundings u
+    (|H2| |W3|^T + |b3|) with u the bfloat16 unit roundoff."""
+    d = M.unpack(p)
+    n = F.shape[0]
+    Y, c = M.forward(p, F, False)
+    T = (np.asarray(O, dtype=np.float64) - M.trend(p, F)) / d["scale"]
+    AY = np.abs(c["H2"]) @ np.abs(d["W3"]).T + np.abs(d["b3"])
+    dY = 2.0 / (n * M.N_OUT) * (np.abs(Y - T) + forward_roundings * 2.0 ** -9 * AY)
+    g = dict(W3=dY.T @ np.abs(c["H2"]), b3=dY.sum(axis=0))
+    dZ2 = (dY @ np.abs(d["W3"])) * np.abs(M.silu_grad(c["Z2"]))
+    g["W2"] = dZ2.T @ np.abs(c["H1"])
+    g["b2"] = dZ2.sum(axis=0)
+    dZ1 = (dZ2 @ np.abs(d["W2"])) * np.abs(M.silu_grad(c["Z1"]))
+    g["W1"] = dZ1.T @ np.abs(c["F"])
+    g["mean"], g["scale"], g["A"] = np.zeros(M.N_OUT), np.zeros(M.N_OUT), np.zeros((M.N_OUT, 3))
+    return M.pack(g)
+
+
 def test_gradient_matches_oracle():
+    """The tensor-core gradient element by element against the plain float64 backward pass.
+    The kernels round every matrix-product operand to bfloat16 (unit roundoff u = 2^-9) and
+    accumulate in FP32; a term of any gradient element passes through at most nine such
+    roundings (inputs, W1, H1, W2, H2, W3, the output errors and the two back-propagated
+    errors), so |g_gpu - g_64| <= 9 u g_abs, g_abs the same gradient with every operand
+    replaced by its magnitude (cancellation between terms is what makes a relative bound per
+    element impossible). FP32 accumulation adds ~n 2^-24 g_abs, negligible. The oracle with
+    the same bf16 operand rounding is a secondary, tighter check."""
     p = _params(3)
     x = _inputs(424, 4)                         # 3 full tiles and a partial one
     rng = np.random.default_rng(5)
@@ -96,17 +125,21 @@ def test_gradient_matches_oracle():
     loss = native.blacklight_mlp_grad(_gpu(p), _gpu(x), _gpu(o), g)
     got = g.double().cpu().numpy()
     F = _features(x)
-    lq, want_q = M.loss_and_grad(p, F, o, quant=True)
     l64, want = M.loss_and_grad(p, F, o, quant=False)
+    bound = 9 * 2.0 ** -9 * _grad_abs(p, F, o)
+    tr = slice(0, M.OFF_MEAN)
+    ratio = np.abs(got[tr] - want[tr]) / bound[tr]
+    print("gradient |gpu - float64| / bound: max %.3f median %.3f" % (ratio.max(), np.median(ratio)))
+    assert np.all(ratio <= 1.0), int(np.argmax(ratio))
+    assert loss == pytest.approx(l64, rel=9 * 2.0 ** -9)
+    # secondary: the oracle rounding the same operands to bfloat16 agrees to FP32 summation
+    lq, want_q = M.loss_and_grad(p, F, o, quant=True)
     assert loss == pytest.approx(lq, rel=1e-4)
     blocks = {"W1": (M.OFF_W1, M.OFF_W2), "W2": (M.OFF_W2, M.OFF_B2), "b2": (M.OFF_B2, M.OFF_W3),
               "W3": (M.OFF_W3, M.OFF_B3), "b3": (M.OFF_B3, M.OFF_MEAN)}
     for name, (a, b) in blocks.items():
         eq = np.linalg.norm(got[a:b] - want_q[a:b]) / np.linalg.norm(want_q[a:b])
-        e64 = np.linalg.norm(got[a:b] - want[a:b]) / np.linalg.norm(want[a:b])
-        print(name, "rel err vs oracle bf16", eq, "vs float64", e64)
         assert eq <= 3e-3, name
-        assert e64 <= 5e-2, name
     assert np.all(got[M.OFF_MEAN:] == 0.0)
 
 
@@ -228,5 +261,5 @@ def test_image_ablation_trained_model_vs_untrained_and_exact(trained):
     untrained = _rel_l2(_image(cam, met, gp, prim, native.BL_PREC_FAST, init), want)
     print("rel-L2 exact fits", exact, "trained model", learned, "untrained model", untrained)
     assert max(exact) <= 1e-5
-    assert max(learned) <= 1.5e-3
+    assert max(learned) <= 1e-3       # the image tolerance for the learned form
     assert max(learned) * 50 <= max(untrained)

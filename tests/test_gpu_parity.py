@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle on the same seeded inputs.
 
-Tolerances (written here, derived in the design notes):
+Tolerances (each derived where it is asserted):
   - geodesic end states, FP64: 1e-10 relative for rays whose accept/reject sequence matches
     (same attempt count); rays whose sequence differs are counted and must be rare;
   - images: per-Stokes relative L2 ||X_gpu - X_oracle|| / ||I_oracle|| <= 1e-3 and total flux
@@ -135,6 +135,17 @@ def test_stokes_step_vs_oracle(precision, tol):
 @pytest.mark.parametrize("precision", [0, 2])
 @pytest.mark.parametrize("spin,inc,n", [(0.9, 17.0, 32), (0.0, 60.0, 16), (0.94, 90.0, 37)])
 def test_geodesic_endpoints_vs_oracle(spin, inc, n, precision):
+    """End states of the adaptive Dormand-Prince geodesics (geodesics section) against the
+    oracle. Each ray is judged against its own conditioning: the oracle is run again with its
+    right-hand side perturbed by one ulp (component i scaled by 1 +- (-1)^i 2^-52), and the
+    larger difference of the two runs from the plain one (`sens`) is how far a one-ulp change
+    travels along that ray. Typical rays keep it at rounding level; rays grazing the photon
+    orbit amplify it by up to ~1e6 (the pinned oracle-against-itself spread), which no FP64
+    integration that rounds differently can avoid. So: every well-conditioned ray (sens <=
+    1e-13) meets the 1e-10 endpoint bound in FP64; every ray stays within a fixed multiple of
+    its own sensitivity; and rays whose step sequences differ are compared after both are
+    carried back to the camera sphere r = r_cam, where they must agree to 1e-7."""
+    import endpoints as E
     cam = S.Camera(theta=math.radians(inc), n=n)
     met = S.Metric(spin=spin, precision=precision)
     end = torch.empty((n, n, 8), dtype=torch.float64, device=DEV)
@@ -147,46 +158,52 @@ def test_geodesic_endpoints_vs_oracle(spin, inc, n, precision):
     prim = np.zeros((8, 1, 1, 1), dtype=np.float32)
     gp1 = S.GridParams(n_r=1, n_theta=1, n_phi=1)
     ora = O.trace(cam, met, gp1, prim, 230e9)
+    perturbed = []
+    try:
+        for k in (1, -1):
+            O.set_rhs_perturbation(k)
+            perturbed.append(O.trace(cam, met, gp1, prim, 230e9))
+    finally:
+        O.set_rhs_perturbation(0)
     assert np.array_equal(g_st, ora["status"])
     same = g_at == ora["attempts"]
-    assert same.mean() >= 0.97, same.mean()
-    # The stopping point of the last (long) step slides along the ray with the controller's
-    # rounding, so compare quantities that do not depend on where the ray is cut: the final
-    # momentum, the position transverse to it, and the constant L_z. The adaptive step
-    # control amplifies rounding-level differences in the right-hand side by ~1e6 for rays
-    # that graze the photon ring: the oracle against itself, with its right-hand side
-    # perturbed by one ulp, shows median ~1e-15, 99th percentile 2-4e-10 and 1-3% of rays
-    # above 1e-10. The bounds below are that spread: typical rays agree to rounding, >= 95%
-    # of rays within 1e-10, every ray within 1e-8.
-    ge, oe = g_end[same], ora["end"][same]
-    kg, ko = ge[:, 5:8], oe[:, 5:8]
-    kn = np.linalg.norm(ko, axis=1)
-    khat = ko / kn[:, None]
-
-    def perp(x):
-        return x - np.sum(x * khat, axis=1)[:, None] * khat
-
-    ek = np.linalg.norm(kg - ko, axis=1) / kn
-    ex = np.linalg.norm(perp(ge[:, 1:4]) - perp(oe[:, 1:4]), axis=1) / np.linalg.norm(oe[:, 1:4], axis=1)
-    lz_g = ge[:, 1] * ge[:, 6] - ge[:, 2] * ge[:, 5]
-    lz_o = oe[:, 1] * oe[:, 6] - oe[:, 2] * oe[:, 5]
-    el = np.abs(lz_g - lz_o) / (np.abs(lz_o) + 1.0)
-    worst = np.maximum(np.maximum(ek, ex), el)
-    print("endpoint rel diff: median %.2e  p99 %.2e  max %.2e" % (np.median(worst),
-          np.percentile(worst, 99), worst.max()))
+    for orp in perturbed:
+        same &= orp["attempts"] == ora["attempts"]
+    assert same.mean() >= 0.95, same.mean()
+    err = E.cut_free_error(g_end[same], ora["end"][same])
+    sens = np.max([E.cut_free_error(orp["end"][same], ora["end"][same]) for orp in perturbed],
+                  axis=0)
+    # the GPU's right-hand side rounds differently from the oracle's by up to ~1e3 one-ulp
+    # perturbations' worth, so a ray whose one-ulp sensitivity is at most 1e-13 must meet 1e-10
+    well = sens <= 1e-13
+    ratio = err / np.maximum(sens, 1e-16)
+    print("endpoints: median %.2e p99 %.2e max %.2e; well-conditioned %.1f%% (max %.2e); "
+          "max err/sens %.1f" % (np.median(err), np.percentile(err, 99), err.max(),
+                                 100 * well.mean(), err[well].max() if well.any() else 0,
+                                 ratio.max()))
+    # k_t is conserved exactly on each side; the two camera set-ups round differently
+    assert np.allclose(g_end[:, 4], ora["end"][:, 4], rtol=1e-14, atol=0)
     if precision == 0:
-        assert np.median(worst) < 1e-12
-        assert np.mean(worst <= 1e-10) >= 0.95
-        assert worst.max() < 1e-8
+        assert well.mean() >= 0.85
+        assert np.median(err) < 1e-13
+        assert np.all(err[well] <= 1e-10)
+        assert np.all(err <= np.maximum(1e-10, 1e4 * sens))
+        cam_tol = 1e-7
     else:
         # double-float geodesics round at 2^-48 instead of 2^-53 and steer the step size in
         # FP32, which moves the step sequence at ~1e-7 relative: measured median ~5e-14,
         # 99th percentile ~4e-7
-        assert np.median(worst) < 1e-11
-        assert np.mean(worst <= 1e-6) >= 0.95
-        assert worst.max() < 1e-5
-    # k_t is conserved exactly on each side; the two camera set-ups round differently
-    assert np.allclose(ge[:, 4], oe[:, 4], rtol=1e-14, atol=0)
+        assert np.median(err) < 1e-11
+        assert np.mean(err <= 1e-6) >= 0.95
+        assert err.max() < 1e-5
+        cam_tol = 1e-5
+    # rays whose step sequences differ: compared on the camera sphere (escaped rays; a ray
+    # that ends at the horizon has no camera-sphere point)
+    other = np.where(~same)[0]
+    for i in other:
+        if g_st[i] == 2:
+            e = E.camera_sphere_error(g_end[i], ora["end"][i], met.mass, spin, cam.r)
+            assert e <= cam_tol, (i, e)
 
 
 # ------------------------------ images ---------------------------------------------------
@@ -219,36 +236,52 @@ def test_image_mixed_vs_oracle(c1_oracle, precision):
     assert abs(_flux(g["stokes"]) / _flux(c1_oracle["stokes"]) - 1) <= 1e-4
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
-def test_full_size_workload_sampled(precision):
-    """256x256 camera on the 256x128x128 torus (the benchmark workload), checked against the
-    oracle on a seeded sample of pixels."""
+@pytest.fixture(scope="module")
+def full_size_oracle():
+    """The oracle on 4096 seeded pixels of the benchmark's a = 0.94, i = 60 deg image."""
     cam, met, gp, prim = S.workload_inputs("torus256_cam256", 0.94, 60.0)
+    rng = np.random.default_rng(123)
+    pix = np.sort(rng.choice(cam.n * cam.n, 4096, replace=False)).astype(np.int32)
+    return (cam, met, gp, prim), pix, O.trace(cam, met, gp, prim, 230e9, pix=pix)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_full_size_workload_sampled(precision, full_size_oracle):
+    """256x256 camera on the 256x128x128 torus (the benchmark workload), checked against the
+    oracle on 4096 seeded pixels."""
+    (cam, met, gp, prim), pix, ora = full_size_oracle
     g = _gpu_image(cam, met, gp, prim, 230e9, precision)
     assert g["rc"] == 0
-    rng = np.random.default_rng(123)
-    pix = np.sort(rng.choice(cam.n * cam.n, 192, replace=False)).astype(np.int32)
-    ora = O.trace(cam, met, gp, prim, 230e9, pix=pix)
     err = _rel_l2(g["stokes"][pix], ora["stokes"])
     print("full-size sampled rel-L2", precision, err)
     assert max(err) <= 1e-3
+    if precision == 0:   # FP64: rounding order and the Bessel polynomials only (~1e-9)
+        assert max(err) <= 1e-7
     assert abs(np.sum(g["stokes"][pix, 0]) / np.sum(ora["stokes"][:, 0]) - 1) <= 1e-4
     assert np.array_equal(g["status"][pix], ora["status"])
 
 
-@pytest.mark.parametrize("precision", [1, 2])
-def test_hires_workload_sampled(precision):
-    """1024x1024 camera on the 512x256x256 torus, checked against the oracle on a seeded
-    sample of pixels."""
+@pytest.fixture(scope="module")
+def hires_oracle():
+    """The oracle on 4096 seeded pixels of the 1024^2 image on the 512x256x256 torus."""
     cam, met, gp, prim = S.workload_inputs("torus512_cam1024", 0.94, 17.0)
+    rng = np.random.default_rng(321)
+    pix = np.sort(rng.choice(cam.n * cam.n, 4096, replace=False)).astype(np.int32)
+    return (cam, met, gp, prim), pix, O.trace(cam, met, gp, prim, 230e9, pix=pix)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_hires_workload_sampled(precision, hires_oracle):
+    """1024x1024 camera on the 512x256x256 torus, checked against the oracle on 4096 seeded
+    pixels."""
+    (cam, met, gp, prim), pix, ora = hires_oracle
     g = _gpu_image(cam, met, gp, prim, 230e9, precision)
     assert g["rc"] == 0
-    rng = np.random.default_rng(321)
-    pix = np.sort(rng.choice(cam.n * cam.n, 160, replace=False)).astype(np.int32)
-    ora = O.trace(cam, met, gp, prim, 230e9, pix=pix)
     err = _rel_l2(g["stokes"][pix], ora["stokes"])
     print("1024^2 sampled rel-L2", precision, err)
     assert max(err) <= 1e-3
+    if precision == 0:
+        assert max(err) <= 1e-7
     assert abs(np.sum(g["stokes"][pix, 0]) / np.sum(ora["stokes"][:, 0]) - 1) <= 1e-4
     assert np.array_equal(g["status"][pix], ora["status"])
 

@@ -72,6 +72,7 @@ def test_autotuned_and_row_major_plans_give_identical_results():
     print("autotuned", cfg)
     assert cfg["ray_order"] in (0, 1) and cfg["geo_ctas_per_sm"] >= 1
     assert cfg["tr_ctas_per_sm"] >= 1 and cfg["run_ms"] > 0
+    assert cfg["ilv_block"] == 0             # unequal images: no interleaving to tune
     plan.run()
     plan.check()
     _same(outs, ref)
@@ -88,6 +89,35 @@ def test_autotuned_and_row_major_plans_give_identical_results():
     _same(outs3, ref)
     for p in (plan, plan2, plan3):
         p.close()
+
+
+def test_interleave_block_is_scheduling_only():
+    """Equal images on cell-layout grids are queued interleaved in blocks of ilv_block rays of
+    one image; every block size the autotuner may pick gives the same outputs bit for bit, and
+    a batch that cannot interleave (unequal images) reports 0."""
+    cams, mets, gps, prims = [], [], [], []
+    for spin, inc in ((0.9, 17.0), (0.5, 60.0), (0.0, 90.0)):
+        cam, met, gp, prim = S.workload_inputs("torus64_cam32", spin, inc, n=64)
+        cells, gpc = images.pack_grid(torch.from_numpy(prim).to(DEV), gp)
+        cams.append(cam)
+        mets.append(S.Metric(**{**met.__dict__, "precision": native.BL_PREC_FAST}))
+        gps.append(gpc)
+        prims.append(cells)
+    ref = _outs(cams)
+    native.blacklight_trace_batch(cams, mets, gps, prims, [230e9] * 3, ref)
+    for blk in (64, 256, 1024, 4096):
+        outs = _outs(cams)
+        plan = native.Plan(cams, mets, gps, prims, [230e9] * 3, outs, config={"ilv_block": blk})
+        assert plan.config()["ilv_block"] == blk
+        plan.run()
+        assert plan.check() == 0
+        _same(outs, ref)
+        plan.close()
+    # unequal images never interleave
+    c2, m2, g2, p2 = _batch()
+    plan = native.Plan(c2, m2, g2, p2, [230e9] * 3, _outs(c2), config={"ilv_block": 1024})
+    assert plan.config()["ilv_block"] == 0
+    plan.close()
 
 
 def test_plan_sees_new_grid_contents_between_runs():

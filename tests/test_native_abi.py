@@ -43,14 +43,16 @@ def test_ctypes_struct_sizes_equal_the_c_compilers(tmp_path):
     src.write_text('#include <stdio.h>\n#include "blacklight.h"\nint main(void) {\n'
                    ' printf("%zu %zu %zu %zu %zu %zu %d\\n", sizeof(bl_camera_t), sizeof(bl_metric_t),'
                    ' sizeof(bl_grid_t), sizeof(bl_out_t), sizeof(bl_adapt_t), sizeof(bl_mlp_train_t),'
-                   ' BL_MLP_PARAMS);\n printf("%zu\\n", sizeof(bl_launch_config_t));\n return 0;\n}\n')
+                   ' BL_MLP_PARAMS);\n printf("%zu %zu\\n", sizeof(bl_launch_config_t), sizeof(bl_peaks_t));\n'
+                   ' return 0;\n}\n')
     exe = tmp_path / "sizes"
     subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
                                           text=True).stdout.split()]
     want = [ctypes.sizeof(native.Camera), ctypes.sizeof(native.Metric),
             ctypes.sizeof(native.Grid), ctypes.sizeof(native.Out), ctypes.sizeof(native.Adapt),
-            ctypes.sizeof(native.MlpTrain), native.MLP_PARAMS, ctypes.sizeof(native.LaunchConfig)]
+            ctypes.sizeof(native.MlpTrain), native.MLP_PARAMS, ctypes.sizeof(native.LaunchConfig),
+            ctypes.sizeof(native.Peaks)]
     assert got == want
 
 
