@@ -1941,9 +1941,10 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
 // Register cap and CTA size of the FP64 transfer kernel. Its FP64 arithmetic runs at 1/64 of
 // the FP32 rate with long dependent latencies, so resident warps matter more than spills to
 // L1: measured on the 9 x 256^2 step, 96 registers (20 warps an SM) 459 ms, 80: 441 ms, 72:
-// 429 ms, 64 (32 warps an SM): 405 ms, 56: 395 ms, 48 (42 warps an SM): 388 ms.
+// 429 ms, 64 (32 warps an SM): 405 ms, 56: 395 ms, 48 (42 warps an SM): 385 ms, 40: 373 ms,
+// 32 (64 warps, the SM's limit): 349 ms.
 #ifndef BL_TR64_MAXNREG
-#define BL_TR64_MAXNREG 48
+#define BL_TR64_MAXNREG 32
 #endif
 #ifndef BL_TR64_THREADS
 #define BL_TR64_THREADS 64

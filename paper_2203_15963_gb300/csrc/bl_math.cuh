@@ -483,122 +483,74 @@ __device__ __forceinline__ T inv_int(int k) {
 // exponential taken by a Horner-form Taylor polynomial, then squared s times. For
 // alpha_I dl >= 100 the steady state M^{-1} J is returned (Eq. unpolarized's tau_max rule).
 // ---------------------------------------------------------------------------------------
+// Steady state M^{-1} J of the polarized step (optical depth alpha_I dl >= 100, the polarized
+// form of Eq. unpolarized's tau_max rule): Gaussian elimination with partial pivoting on
+// [M | J]. Out of line: rarely taken, and kept off the transfer loop's instruction footprint.
 template <class T>
-__device__ __forceinline__ void stokes_step(const T c[8], const T s0[4], T dl, T s1[4]) {
+struct StokesV {
+    T v[4];
+};
+template <class T>
+struct StokesC {
+    T c[8];
+};
+
+template <class T>
+__device__ __noinline__ StokesV<T> stokes_steady(const StokesC<T> cc) {
+    const T* c = cc.c;
+    StokesV<T> out;
+    T* s1 = out.v;
     const T aI = c[3], aQ = c[4], aV = c[5], rQ = c[6], rV = c[7];
     const T M[4][4] = {{aI, aQ, T(0), aV}, {aQ, aI, rV, T(0)}, {T(0), -rV, aI, rQ}, {aV, T(0), -rQ, aI}};
     const T J[4] = {c[0], c[1], T(0), c[2]};
-    if (aI * dl >= T(100)) {
-        // Gaussian elimination with partial pivoting on [M | J].
-        T a[4][5];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) a[i][j] = M[i][j];
-            a[i][4] = J[i];
-        }
-        for (int col = 0; col < 4; ++col) {
-            int p = col;
-            for (int i = col + 1; i < 4; ++i)
-                if (fabs(a[i][col]) > fabs(a[p][col])) p = i;
-            if (p != col)
-                for (int j = 0; j < 5; ++j) { T t = a[p][j]; a[p][j] = a[col][j]; a[col][j] = t; }
-            const T inv = T(1) / a[col][col];
-            for (int i = col + 1; i < 4; ++i) {
-                const T fct = a[i][col] * inv;
-                for (int j = col; j < 5; ++j) a[i][j] -= fct * a[col][j];
-            }
-        }
-        for (int i = 3; i >= 0; --i) {
-            T s = a[i][4];
-            for (int j = i + 1; j < 4; ++j) s -= a[i][j] * s1[j];
-            s1[i] = s / a[i][i];
-        }
-        return;
-    }
-    // Z = -M dl, z = J dl. M_02 = M_13 = M_20 = M_31 = 0 and J_2 = 0 (no U terms) are left
-    // out of the sums below: IEEE arithmetic may not drop a product with a zero by itself.
-    // The series of exp([Z z; 0 0]) converges at the rate of Z alone (its z column only
-    // multiplies), so scaling and Taylor degree follow the infinity norm of Z.
-    auto mz = [](int i, int j) {
-        return (i == 0 && j == 2) || (i == 1 && j == 3) || (i == 2 && j == 0) || (i == 3 && j == 1);
-    };
-    T Z[4][4], z[4];
-    T nrm = T(0);
+    // Gaussian elimination with partial pivoting on [M | J].
+    T a[4][5];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        T rs = T(0);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            Z[i][j] = mz(i, j) ? T(0) : -M[i][j] * dl;
-            if (!mz(i, j)) rs += fabs(Z[i][j]);
+        for (int j = 0; j < 4; ++j) a[i][j] = M[i][j];
+        a[i][4] = J[i];
+    }
+    for (int col = 0; col < 4; ++col) {
+        int p = col;
+        for (int i = col + 1; i < 4; ++i)
+            if (fabs(a[i][col]) > fabs(a[p][col])) p = i;
+        if (p != col)
+            for (int j = 0; j < 5; ++j) { T t = a[p][j]; a[p][j] = a[col][j]; a[col][j] = t; }
+        const T inv = T(1) / a[col][col];
+        for (int i = col + 1; i < 4; ++i) {
+            const T fct = a[i][col] * inv;
+            for (int j = col; j < 5; ++j) a[i][j] -= fct * a[col][j];
         }
-        z[i] = i == 2 ? T(0) : J[i] * dl;
-        nrm = rs > nrm ? rs : nrm;
     }
-    int s = 0;
-    if (nrm > T(0.5)) {
-        int e;
-        frexp(nrm / T(0.5), &e);
-        s = e;   // nrm / 2^s <= 0.5
+    for (int i = 3; i >= 0; --i) {
+        T s = a[i][4];
+        for (int j = i + 1; j < 4; ++j) s -= a[i][j] * s1[j];
+        s1[i] = s / a[i][i];
     }
+    return out;
+}
+
+// exp([Z z; 0 0]) applied to [s0; 1] for a scaled ||Z|| <= 1/2 that needed s >= 2 halvings:
+// the Taylor polynomial of degree m of the matrix and of phi_1(Z) z, then s squarings of the
+// augmented matrix. Out of line: rare (||M dl|| > 1), and large.
+template <class T>
+__device__ __noinline__ StokesV<T> stokes_expm(const StokesC<T> cc, T dl, int s,
+                                               const StokesV<T> sv0) {
+    const T* s0 = sv0.v;
+    StokesV<T> out;
+    T* s1 = out.v;
+    // Z = -M dl 2^-s, z = J dl 2^-s (as in stokes_step, rebuilt here off the common path)
+    const T aI = cc.c[3], aQ = cc.c[4], aV = cc.c[5], rQ = cc.c[6], rV = cc.c[7];
     const T sc = ldexp(T(1), -s);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (!mz(i, j)) Z[i][j] *= sc;
-        if (i != 2) z[i] *= sc;
-    }
-    // Taylor degree of the matrix form: ||Z|| <= 1/2, truncation 2^-(m+1)/(m+1)! below the
-    // type's rounding.
+    const T dls = dl * sc;
+    const T Z[4][4] = {{-aI * dls, -aQ * dls, T(0), -aV * dls},
+                       {-aQ * dls, -aI * dls, -rV * dls, T(0)},
+                       {T(0), rV * dls, -aI * dls, -rQ * dls},
+                       {-aV * dls, T(0), rQ * dls, -aI * dls}};
+    const T z[4] = {cc.c[0] * dls, cc.c[1] * dls, T(0), cc.c[2] * dls};
+    // Taylor degree: ||Z|| <= 1/2, truncation 2^-(m+1)/(m+1)! below the type's rounding.
     constexpr int m = sizeof(T) == 8 ? 13 : 8;
-    if (s <= 1) {
-        // Only the action on [s0; 1] is needed: with A = [Z z; 0 0] (scaled), exp(A) x is
-        // x + A (x + A/2 (x + ... (x + A x / d))), the last component staying 1, so each term
-        // is one 4x4 matrix-vector product (16 FMAs) instead of a matrix product (64). The
-        // scaled map is applied 2^s times (at most twice) in place of the squarings. The
-        // degree d is the smallest whose truncation, ||Z||^d (||Z|| ||s0|| + ||z||) / (d+1)!,
-        // is below the unit roundoff u relative to ||Z|| ||s0|| + ||z||: the first d with
-        // ||Z|| <= theta_d = (u (d+1)!)^(1/d) (u = 2^-53 in FP64, 2^-24 in FP32), at most 14
-        // (FP64) or 8 (FP32) for ||Z|| <= 1/2.
-        constexpr int dmax = sizeof(T) == 8 ? 14 : 8;
-        constexpr float th64[14] = {2.2e-16f, 2.58e-8f, 1.38e-5f, 3.39e-4f, 2.40e-3f, 9.07e-3f,
-                                    2.39e-2f, 5.01e-2f, 9.03e-2f, 0.146f, 0.218f, 0.306f,
-                                    0.411f, 0.531f};
-        constexpr float th32[8] = {1.19e-7f, 5.98e-4f, 1.126e-2f, 5.17e-2f, 0.1338f, 0.2587f,
-                                   0.4225f, 0.6192f};
-        const float nz = (float)(nrm * sc);
-        int d = 1;
-#pragma unroll
-        for (int q = 0; q < dmax - 1; ++q)
-            if (nz > (sizeof(T) == 8 ? th64[q] : th32[q])) d = q + 2;
-        T v[4] = {s0[0], s0[1], s0[2], s0[3]};
-#pragma unroll 1
-        for (int rep = 0; rep < (1 << s); ++rep) {
-            T t[4] = {v[0], v[1], v[2], v[3]};
-#pragma unroll 1
-            for (int k = d; k >= 1; --k) {
-                const T ik = inv_int<T>(k);
-                T tn[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    T acc = z[i];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (!mz(i, q)) acc += Z[i][q] * t[q];
-                    tn[i] = v[i] + acc * ik;
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) t[i] = tn[i];
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) v[i] = t[i];
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) s1[i] = v[i];
-        return;
-    }
     // E = I + Z (I + Z/2 (I + Z/3 (...))),  t = (I + Z/2 (I + Z/3 (...))) z  (phi_1(Z) z)
     T E[4][4], tv[4];
 #pragma unroll
@@ -678,6 +630,112 @@ __device__ __forceinline__ void stokes_step(const T c[8], const T s0[4], T dl, T
         for (int j = 0; j < 4; ++j) acc += E[i][j] * s0[j];
         s1[i] = acc;
     }
+    return out;
+}
+
+template <class T>
+__device__ __forceinline__ void stokes_step(const T c[8], const T s0[4], T dl, T s1[4]) {
+    const T aI = c[3], aQ = c[4], aV = c[5], rQ = c[6], rV = c[7];
+    const T M[4][4] = {{aI, aQ, T(0), aV}, {aQ, aI, rV, T(0)}, {T(0), -rV, aI, rQ}, {aV, T(0), -rQ, aI}};
+    const T J[4] = {c[0], c[1], T(0), c[2]};
+    if (aI * dl >= T(100)) {
+        StokesC<T> cc;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) cc.c[i] = c[i];
+        const StokesV<T> r = stokes_steady<T>(cc);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) s1[i] = r.v[i];
+        return;
+    }
+    // Z = -M dl, z = J dl. M_02 = M_13 = M_20 = M_31 = 0 and J_2 = 0 (no U terms) are left
+    // out of the sums below: IEEE arithmetic may not drop a product with a zero by itself.
+    // The series of exp([Z z; 0 0]) converges at the rate of Z alone (its z column only
+    // multiplies), so scaling and Taylor degree follow the infinity norm of Z.
+    auto mz = [](int i, int j) {
+        return (i == 0 && j == 2) || (i == 1 && j == 3) || (i == 2 && j == 0) || (i == 3 && j == 1);
+    };
+    T Z[4][4], z[4];
+    T nrm = T(0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        T rs = T(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            Z[i][j] = mz(i, j) ? T(0) : -M[i][j] * dl;
+            if (!mz(i, j)) rs += fabs(Z[i][j]);
+        }
+        z[i] = i == 2 ? T(0) : J[i] * dl;
+        nrm = rs > nrm ? rs : nrm;
+    }
+    int s = 0;
+    if (nrm > T(0.5)) {
+        int e;
+        frexp(nrm / T(0.5), &e);
+        s = e;   // nrm / 2^s <= 0.5
+    }
+    const T sc = ldexp(T(1), -s);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (!mz(i, j)) Z[i][j] *= sc;
+        if (i != 2) z[i] *= sc;
+    }
+    if (s <= 1) {
+        // Only the action on [s0; 1] is needed: with A = [Z z; 0 0] (scaled), exp(A) x is
+        // x + A (x + A/2 (x + ... (x + A x / d))), the last component staying 1, so each term
+        // is one 4x4 matrix-vector product (16 FMAs) instead of a matrix product (64). The
+        // scaled map is applied 2^s times (at most twice) in place of the squarings. The
+        // degree d is the smallest whose truncation, ||Z||^d (||Z|| ||s0|| + ||z||) / (d+1)!,
+        // is below the unit roundoff u relative to ||Z|| ||s0|| + ||z||: the first d with
+        // ||Z|| <= theta_d = (u (d+1)!)^(1/d) (u = 2^-53 in FP64, 2^-24 in FP32), at most 14
+        // (FP64) or 8 (FP32) for ||Z|| <= 1/2.
+        constexpr int dmax = sizeof(T) == 8 ? 14 : 8;
+        constexpr float th64[14] = {2.2e-16f, 2.58e-8f, 1.38e-5f, 3.39e-4f, 2.40e-3f, 9.07e-3f,
+                                    2.39e-2f, 5.01e-2f, 9.03e-2f, 0.146f, 0.218f, 0.306f,
+                                    0.411f, 0.531f};
+        constexpr float th32[8] = {1.19e-7f, 5.98e-4f, 1.126e-2f, 5.17e-2f, 0.1338f, 0.2587f,
+                                   0.4225f, 0.6192f};
+        const float nz = (float)(nrm * sc);
+        int d = 1;
+#pragma unroll
+        for (int q = 0; q < dmax - 1; ++q)
+            if (nz > (sizeof(T) == 8 ? th64[q] : th32[q])) d = q + 2;
+        T v[4] = {s0[0], s0[1], s0[2], s0[3]};
+#pragma unroll 1
+        for (int rep = 0; rep < (1 << s); ++rep) {
+            T t[4] = {v[0], v[1], v[2], v[3]};
+#pragma unroll 1
+            for (int k = d; k >= 1; --k) {
+                const T ik = inv_int<T>(k);
+                T tn[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    T acc = z[i];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (!mz(i, q)) acc += Z[i][q] * t[q];
+                    tn[i] = v[i] + acc * ik;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) t[i] = tn[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = t[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) s1[i] = v[i];
+        return;
+    }
+    StokesC<T> cc;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) cc.c[i] = c[i];
+    StokesV<T> v0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v0.v[i] = s0[i];
+    const StokesV<T> r = stokes_expm<T>(cc, dl, s, v0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s1[i] = r.v[i];
 }
 
 }  // namespace bl
