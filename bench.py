@@ -56,9 +56,10 @@ GRID = (256, 128, 128)
 FLOP64_PER_ATTEMPT = 1214
 # Arithmetic per transfer sample of the method (see the module docstring): FP32 flops and
 # special-function instructions of transfer_kernel<float, float, 0> per sample, from the ncu
-# capture of the one-image 256^2 case (a = 0.94, i = 60 deg). None until captured.
-FLOP_PER_SAMPLE = None
-SFU_PER_SAMPLE = None
+# capture of the one-image 256^2 case (a = 0.94, i = 60 deg; 18,372,183 samples):
+# 2 x 5.48e9 FFMA + 3.29e9 FMUL + 0.33e9 FADD thread instructions, 3.17e8 MUFU.
+FLOP_PER_SAMPLE = 848
+SFU_PER_SAMPLE = 17.2
 # Kernel sources the DRAM figures below were captured with (sha256 of the kernel headers, 16
 # hex digits; see kernel_source_hash).
 KERNEL_HEADERS = ("bl_kernels.cuh", "bl_math.cuh", "bl_df64.cuh", "bl_internal.cuh",
@@ -66,11 +67,20 @@ KERNEL_HEADERS = ("bl_kernels.cuh", "bl_math.cuh", "bl_df64.cuh", "bl_internal.c
 # dram__bytes_read.sum + dram__bytes_write.sum per unit of work from one ncu capture of the
 # one-image 256^2 case, with the kernel-source hash of that capture; scaled by the units of a
 # launch of the benchmark step (the kernels' traffic grows with the units they process).
+# fp64_instr: thread-level DFMA + DMUL + DADD instructions per unit from the same capture,
+# which gives the FP64 pipe's issue rate beside the algorithmic roofline.
 DRAM_PER_UNIT = {
-    # FP64 form, 7,845,751 attempts: 0.0682 GB read + 2.0544 GB written (sample records)
-    "geodesic_fp64": {"src": "ab498bbdddb4da8d", "bytes": 2.122659e9 / 7845751, "unit": "attempt"},
-    # FP64 form, 18,372,204 samples: 2.6977 GB read + 0.3886 GB written
-    "transfer_fp64": {"src": "ab498bbdddb4da8d", "bytes": 3.086270e9 / 18372204, "unit": "sample"},
+    # FP64 form, 7,845,751 attempts: 0.069 GB read + 2.055 GB written (sample records)
+    "geodesic_fp64": {"src": "580eca31e8d48cd5", "bytes": 270.3, "unit": "attempt",
+                      "fp64_instr": 1090.4},
+    # FP64 form, 18,372,204 samples: 6.199 GB read + 9.716 GB written (records and grid
+    # 1.4 GB; the rest is register spill traffic of the 32-register build, see DESIGN)
+    "transfer_fp64": {"src": "580eca31e8d48cd5", "bytes": 844.8, "unit": "sample",
+                      "fp64_instr": 682.4},
+    # fast form, 7,845,744 attempts: 0.024 GB read + 1.135 GB written
+    "geodesic_df64": {"src": "580eca31e8d48cd5", "bytes": 147.7, "unit": "attempt"},
+    # fast form, 18,372,183 samples: 1.392 GB read + 0.004 GB written
+    "transfer_fp32": {"src": "580eca31e8d48cd5", "bytes": 76.0, "unit": "sample"},
 }
 
 
@@ -311,6 +321,14 @@ def roofline(kernel, flops_per_unit, units, unit_name, seconds, peak, traffic_ke
             r["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum per " +
                                  prof["unit"] + " from one ncu capture of the one-image 256^2 "
                                  "case, scaled by this launch's units")
+            if "fp64_instr" in prof and peak is not None and seconds > 0:
+                rate = prof["fp64_instr"] * units / seconds / 1e9
+                r["fp64_pipe_issue"] = {
+                    "ginstr_per_s": rate, "peak_ginstr_per_s": peak[0] * 1e3 / 2,
+                    "frac": rate / (peak[0] * 1e3 / 2),
+                    "note": "DFMA + DMUL + DADD thread instructions per unit from the ncu "
+                            "capture (special-function sequences included) x units / time, "
+                            "against the measured FP64 FMA rate in instructions"}
         elif prof is not None:
             r["traffic_note"] = "kernel changed since the ncu capture: traffic not reported"
     if note:
@@ -330,17 +348,18 @@ def form_rooflines(prec_name, attempts, samples, geo_s, tr_s, peaks):
                 + (f", median SM clock {mhz:.0f} MHz during the probes)" if mhz else ")"))
     geo_kind = {"fp64": "fp64", "mixed": "fp64", "fast": "df64"}[prec_name]
     tr_kind = "fp64" if prec_name == "fp64" else "fp32"
-    geo = roofline({"fp64": "geodesic_kernel<double, double>",
+    geo = roofline({"fp64": "geodesic_kernel_fp64",
                     "mixed": "geodesic_kernel<float, double>",
                     "fast": "geodesic_kernel<float, df64>"}[prec_name],
                    FLOP64_PER_ATTEMPT, attempts, "DP attempt", geo_s, pk(geo_kind),
-                   traffic_key="geodesic_fp64" if prec_name == "fp64" else None)
+                   traffic_key={"fp64": "geodesic_fp64", "fast": "geodesic_df64"}.get(prec_name))
     tr = roofline("transfer_kernel_fp64<0>" if prec_name == "fp64"
                   else "transfer_kernel<float, float, 0>",
                   FLOP_PER_SAMPLE, samples, "transfer sample", tr_s, pk(tr_kind),
-                  traffic_key="transfer_fp64" if prec_name == "fp64" else None,
-                  note=None if FLOP_PER_SAMPLE is not None else
-                  "per-sample flop count not yet captured")
+                  traffic_key="transfer_fp64" if prec_name == "fp64" else "transfer_fp32",
+                  note=("algorithmic flops: the method's per-sample arithmetic as the FP32 "
+                        f"kernel executes it ({FLOP_PER_SAMPLE} flops, plus {SFU_PER_SAMPLE} "
+                        "special-function instructions not counted as flops)"))
     return (geo, tr) if geo_s >= tr_s else (tr, geo)
 
 

@@ -56,14 +56,15 @@ constexpr int64_t kChunksPerRay = 16;
 constexpr int64_t kWaveRays = 1 << 20;
 
 struct Layout {
-    size_t counters, descs, hdr, init, chunks, pool, total;
+    size_t counters, descs, hdr, init, chunks, pool, mlp_y, total;
     int64_t rays;          // rays of the whole call
     int64_t wave;          // rays per wave (the workspace holds one wave)
     int64_t pool_chunks;
 };
 
+// mlp: room for the learned model's outputs, 8 floats for every record of the pool
 Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precision,
-                        bool transfer, int64_t cpr = kChunksPerRay) {
+                        bool transfer, int64_t cpr = kChunksPerRay, bool mlp = false) {
     Layout L{};
     L.rays = rays;
     L.wave = wave;
@@ -77,28 +78,30 @@ Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precis
     L.init = off;     off = align_up(off + sizeof(bl::RayInit) * (size_t)L.wave);
     L.chunks = off;   off = align_up(off + sizeof(int32_t) * bl::kMaxChunks * (size_t)L.wave);
     L.pool = off;     off = align_up(off + rec * bl::kChunk * (size_t)L.pool_chunks);
+    L.mlp_y = off;
+    if (mlp && transfer) off = align_up(off + 8 * sizeof(float) * bl::kChunk * (size_t)L.pool_chunks);
     L.total = off;
     return L;
 }
 
 Layout make_layout_rays(int32_t n_images, int64_t rays, int precision, bool transfer = true,
-                        int64_t cpr = kChunksPerRay) {
+                        int64_t cpr = kChunksPerRay, bool mlp = false) {
     return make_layout_wave(n_images, rays, rays < kWaveRays ? rays : kWaveRays, precision,
-                            transfer, cpr);
+                            transfer, cpr, mlp);
 }
 
 // The largest wave (>= 1 ray) whose layout fits in `bytes`; wave = 0 if none does.
 Layout fit_layout(int32_t n_images, int64_t rays, int precision, bool transfer, size_t bytes,
-                  int64_t cpr) {
-    Layout L = make_layout_rays(n_images, rays, precision, transfer, cpr);
+                  int64_t cpr, bool mlp = false) {
+    Layout L = make_layout_rays(n_images, rays, precision, transfer, cpr, mlp);
     if (L.total <= bytes) return L;
     int64_t lo = 0, hi = L.wave;        // total(lo) fits (or lo = 0), total(hi) does not
     while (hi - lo > 1) {
         const int64_t mid = lo + (hi - lo) / 2;
-        if (make_layout_wave(n_images, rays, mid, precision, transfer, cpr).total <= bytes) lo = mid;
+        if (make_layout_wave(n_images, rays, mid, precision, transfer, cpr, mlp).total <= bytes) lo = mid;
         else hi = mid;
     }
-    return make_layout_wave(n_images, rays, lo, precision, transfer, cpr);
+    return make_layout_wave(n_images, rays, lo, precision, transfer, cpr, mlp);
 }
 
 int64_t count_rays(int32_t n_images, const bl_camera_t* cams) {
@@ -123,9 +126,10 @@ int64_t chunks_per_ray(int32_t n_images, const bl_camera_t* cams, const bl_metri
     return c < bl::kMaxChunks ? c : bl::kMaxChunks;
 }
 
-Layout make_layout(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets) {
+Layout make_layout(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
+                   bool mlp = false) {
     return make_layout_rays(n_images, count_rays(n_images, cams), mets[0].precision, true,
-                            chunks_per_ray(n_images, cams, mets));
+                            chunks_per_ray(n_images, cams, mets), mlp);
 }
 
 int check_camera(const bl_camera_t* c, int q) {
@@ -295,6 +299,8 @@ struct DevInfo {
     int geo_blocks[3] = {0, 0, 0};  // per SM, indexed by precision: [fp64, mixed, fast]
     int tr_occ[2][8] = {};          // transfer variants: [double, float][feature bits]
     int tr_mlp_occ[2] = {0, 0};     // learned-coefficient transfer: [fast light, slow light]
+    int mi_occ[2] = {0, 0};         // learned-coefficient model inputs: [fast, slow light]
+    int fwd_pool_occ = 0;           // the model over the sample pool
     int rk_occ[2] = {0, 0};         // RK2/RK4 geodesic kernel: [double records, float records]
     // CTAs per SM of the transfer variant a launch uses
     int transfer(int precision, const float* mlp, int feat) const {
@@ -355,8 +361,14 @@ int dev_info(DevInfo& out) {
         int rc = occ_transfer_all<double, double>(di.tr_occ[0]);
         if (!rc) rc = occ_transfer_all<float, float>(di.tr_occ[1]);
         if (rc) { di.sms = 0; return rc; }
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_occ[0], bl::transfer_mlp_kernel<float, false>, 128, 0));
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_occ[1], bl::transfer_mlp_kernel<float, true>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_occ[0], bl::transfer_learned_kernel<false>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_mlp_occ[1], bl::transfer_learned_kernel<true>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.mi_occ[0], bl::mlp_inputs_kernel<false>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.mi_occ[1], bl::mlp_inputs_kernel<true>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.fwd_pool_occ, bl::mlp::forward_pool_kernel, 128, 0));
+        for (int i = 0; i < 2; ++i)
+            if (di.mi_occ[i] < 1) di.mi_occ[i] = 1;
+        if (di.fwd_pool_occ < 1) di.fwd_pool_occ = 1;
         for (int i = 0; i < 2; ++i)
             if (di.tr_mlp_occ[i] < 1) di.tr_mlp_occ[i] = 1;
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.rk_occ[0], bl::geodesic_rk_kernel<double>, 128, 0));
@@ -373,7 +385,8 @@ int dev_info(DevInfo& out) {
 template <class T, class R>
 void launch_transfer(int feat, unsigned grid, cudaStream_t st, const bl::ImageDesc* d, int n,
                      int64_t b, int64_t e, const bl::RayHdr* hdr, const R* pool,
-                     const int32_t* chunks, bl::Counters* ctr, bl::BlockSource bs) {
+                     const int32_t* chunks, bl::Counters* ctr, bl::BlockSource bs,
+                     const float* mlp_y = nullptr, const float* mlp_params = nullptr) {
     if constexpr (std::is_same<T, double>::value) {
         constexpr int th = bl::kTransferFp64Threads;
         switch (feat & 7) {
@@ -387,15 +400,26 @@ void launch_transfer(int feat, unsigned grid, cudaStream_t st, const bl::ImageDe
             default: bl::transfer_kernel_fp64<7><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
         }
     } else {
+        const float* my = mlp_y;
+        const float* mp = mlp_params;
+        if (feat & bl::kFMlp) {
+            if constexpr (std::is_same<R, float>::value) {
+                if (feat & bl::kFSlow)
+                    bl::transfer_learned_kernel<true><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp);
+                else
+                    bl::transfer_learned_kernel<false><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp);
+            }
+            return;
+        }
         switch (feat & 7) {
-            case 0: bl::transfer_kernel<T, R, 0><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            case 1: bl::transfer_kernel<T, R, 1><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            case 2: bl::transfer_kernel<T, R, 2><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            case 3: bl::transfer_kernel<T, R, 3><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            case 4: bl::transfer_kernel<T, R, 4><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            case 5: bl::transfer_kernel<T, R, 5><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            case 6: bl::transfer_kernel<T, R, 6><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            default: bl::transfer_kernel<T, R, 7><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 0: bl::transfer_kernel<T, R, 0><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
+            case 1: bl::transfer_kernel<T, R, 1><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
+            case 2: bl::transfer_kernel<T, R, 2><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
+            case 3: bl::transfer_kernel<T, R, 3><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
+            case 4: bl::transfer_kernel<T, R, 4><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
+            case 5: bl::transfer_kernel<T, R, 5><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
+            case 6: bl::transfer_kernel<T, R, 6><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
+            default: bl::transfer_kernel<T, R, 7><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
         }
     }
 }
@@ -492,12 +516,27 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
             const float* fpool = (const float*)(ws + L.pool);
             const double* dpool = (const double*)(ws + L.pool);
             if (mlp) {
+                // learned coefficients in three passes: the model inputs of every record, the
+                // model over the record pool in full tensor-core tiles, then the transfer
+                // reading the model's outputs
+                float* mpool = (float*)(ws + L.pool);
+                float* my = (float*)(ws + L.mlp_y);
+                const unsigned mi_grid = (unsigned)(di.sms * di.mi_occ[slow ? 1 : 0]);
                 if (slow)
-                    bl::transfer_mlp_kernel<float, true><<<tr_grid, 128, 0, st>>>(
-                        d_desc, n_images, b, e, hdr, fpool, chunks, mlp, ctr, cfg.bs);
+                    bl::mlp_inputs_kernel<true><<<mi_grid, 128, 0, st>>>(
+                        d_desc, n_images, b, e, hdr, mpool, chunks, ctr, cfg.bs);
                 else
-                    bl::transfer_mlp_kernel<float, false><<<tr_grid, 128, 0, st>>>(
-                        d_desc, n_images, b, e, hdr, fpool, chunks, mlp, ctr, cfg.bs);
+                    bl::mlp_inputs_kernel<false><<<mi_grid, 128, 0, st>>>(
+                        d_desc, n_images, b, e, hdr, mpool, chunks, ctr, cfg.bs);
+                ++g_launches;
+                BL_CUDA(cudaGetLastError());
+                bl::mlp::forward_pool_kernel<<<(unsigned)(di.sms * di.fwd_pool_occ), 128, 0, st>>>(
+                    mlp, fpool, &ctr->pool_next, (unsigned long long)L.pool_chunks, my,
+                    &ctr->mlp_timeouts);
+                ++g_launches;
+                BL_CUDA(cudaGetLastError());
+                launch_transfer<float, float>(cfg.feat | bl::kFMlp, tr_grid, st, d_desc, n_images, b,
+                                              e, hdr, fpool, chunks, ctr, cfg.bs, my, mlp);
             } else if (precision != BL_PREC_FP64) {
                 launch_transfer<float, float>(cfg.feat, tr_grid, st, d_desc, n_images, b, e, hdr,
                                               fpool, chunks, ctr, cfg.bs);
@@ -617,7 +656,9 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
     // geodesics only: no records, so no pool
     const int64_t rays = count_rays(n_images, cams);
     const int64_t cpr = chunks_per_ray(n_images, cams, mets);
-    Layout L = make_layout_rays(n_images, rays, precision, transfer, cpr);
+    // learned coefficients (validated below) need room for the model's outputs
+    const bool use_mlp = transfer && grids && grids[0].coef_mlp != nullptr;
+    Layout L = make_layout_rays(n_images, rays, precision, transfer, cpr, use_mlp);
     std::vector<bl::ImageDesc> descs(n_images);
     int64_t off = 0;
     static const bl_grid_t kNoGrid = {sizeof(bl_grid_t), nullptr, 1, 1, 1, 1.0, 2.0, 4.0 / 3.0,
@@ -635,11 +676,11 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
         if ((uintptr_t)ws % kAlign)
             return fail(BL_EINVAL, "workspace must be %zu-byte aligned", kAlign);
         // a workspace smaller than the default layout runs the rays in more, smaller waves
-        L = fit_layout(n_images, rays, precision, transfer, workspace_bytes, cpr);
+        L = fit_layout(n_images, rays, precision, transfer, workspace_bytes, cpr, use_mlp);
         if (L.wave < 1)
             return fail(BL_EINVAL, "workspace too small: %zu < %zu bytes (one ray)",
                         workspace_bytes,
-                        make_layout_wave(n_images, rays, 1, precision, transfer, cpr).total);
+                        make_layout_wave(n_images, rays, 1, precision, transfer, cpr, use_mlp).total);
         int rc = device_pointer(ws, "workspace");
         if (rc) return rc;
     } else {
@@ -972,7 +1013,7 @@ int adapt_prepare(AdaptRun& R, int32_t n_images, const bl_camera_t* cams, const 
         R.max_cap_rays = std::max(R.max_cap_rays, R.cap_blocks[l] * b2);
     }
     R.L = make_layout_rays(n_images, R.max_cap_rays, R.precision, true,
-                           chunks_per_ray(n_images, cams, mets));
+                           chunks_per_ray(n_images, cams, mets), R.mlp != nullptr);
     // one allocation: trace workspace, descriptors, block lists, counts, flags, Stokes, outputs
     const int levels = R.max_level + 1;
     size_t off = 0;
@@ -1256,7 +1297,7 @@ int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_m
     P->precision = precision;
     P->mlp = mlp;
     P->L = make_layout_rays(n_images, count_rays(n_images, cams), precision, true,
-                            chunks_per_ray(n_images, cams, mets));
+                            chunks_per_ray(n_images, cams, mets), mlp != nullptr);
     P->descs.resize(n_images);
     int64_t off = 0;
     for (int q = 0; q < n_images; ++q) {
@@ -1821,7 +1862,7 @@ int blacklight_trace_host_batch(int32_t n_images, const bl_camera_t* cams,
         if (outs[q].end_state) off = align_up(off + npix * 64);
         if (outs[q].aux) off = align_up(off + (size_t)BL_AUX_COUNT * npix * es);
     }
-    const Layout L = make_layout(n_images, cams, mets);
+    const Layout L = make_layout(n_images, cams, mets, grids[0].coef_mlp != nullptr);
     const size_t o_ws = off;
     off = align_up(off + L.total);
     char* dev = nullptr;

@@ -107,6 +107,7 @@ struct Counters {
     unsigned long long next_ray_geo;
     unsigned long long next_ray_tr;
     unsigned long long pool_next;
+    unsigned long long next_ray_mi;    // learned-coefficient model inputs: rays handed out
     unsigned long long bad_rays;
     unsigned long long mlp_timeouts;   // CTAs whose tensor-core wait ran out (never expected)
 };

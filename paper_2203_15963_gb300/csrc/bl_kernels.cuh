@@ -1711,6 +1711,11 @@ __device__ __forceinline__ const R* record_ptr(const R* __restrict__ pool, const
     const int32_t ch = chunks[ray * kMaxChunks + idx / kChunk];
     return pool + ((int64_t)ch * kChunk + (idx % kChunk)) * RecStride<R>::v;
 }
+// Position of record idx of a ray in the pool (records counted from the pool's start).
+__device__ __forceinline__ int64_t record_index(const int32_t* __restrict__ chunks, int64_t ray,
+                                                int32_t idx) {
+    return (int64_t)chunks[ray * kMaxChunks + idx / kChunk] * kChunk + (idx % kChunk);
+}
 
 // ---------------------------------------------------------------------------------------
 // Persistent transfer kernel (Sec. 2.3.2). Each lane replays one ray's samples from the
@@ -1722,7 +1727,7 @@ __device__ __forceinline__ const R* record_ptr(const R* __restrict__ pool, const
 // ---------------------------------------------------------------------------------------
 // Features of a transfer-kernel variant (compile-time, so that each variant carries only the
 // registers it needs).
-enum { kFSlow = 1, kFUnpol = 2, kFAux = 4 };
+enum { kFSlow = 1, kFUnpol = 2, kFAux = 4, kFMlp = 8 };
 
 // Auxiliary accumulators of one ray (Sec. 4, "Auxiliary Images"): I_j, tau and the lambda-,
 // emission- and tau-weighted sums of rho, n_e, p, Theta_e, B, sigma, beta^-1.
@@ -1769,10 +1774,17 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
                                               const RayHdr* __restrict__ hdr,
                                               const R* __restrict__ pool,
                                               const int32_t* __restrict__ chunks,
-                                              Counters* ctr, BlockSource bs) {
+                                              Counters* ctr, BlockSource bs,
+                                              const float* __restrict__ mlp_y,
+                                              const float* __restrict__ mlp_params) {
     constexpr bool kSlow = (kF & kFSlow) != 0;
     constexpr bool kUnpol = (kF & kFUnpol) != 0;
     constexpr bool kAux = (kF & kFAux) != 0;
+    // learned coefficients: the model's outputs come from the pool pass (mlp_y, 8 floats a
+    // record), the record's last value flags the samples the model evaluated
+    constexpr bool kMlp = (kF & kFMlp) != 0;
+    static_assert(!kMlp || std::is_same<R, float>::value, "the learned model needs FP32 records");
+    int64_t nxt_k = 0;
     const int64_t re = wave_end(bs, ray_end);
     const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
     int64_t wray = 0;
@@ -1822,6 +1834,7 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
             }
             idx = hd.nrec - 1;
             load_record<R>(record_ptr(pool, chunks, wray, idx), nxt);
+            if constexpr (kMlp) nxt_k = record_index(chunks, wray, idx);
             kt = (T)hd.kt;
             nu_norm = (T)(hd.nnorm * im.freq);
             a = ic<T>(im, kcSpin);
@@ -1842,12 +1855,21 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
         const bool finishing = idx < 0;
         T cur[kRecVals];
         T nxt_t = T(0);   // the sample's coordinate time
+        int64_t cur_k = 0;
+        bool cur_flag = false;
         if (!finishing) {
             // record idx was prefetched into nxt; start fetching idx - 1 before using it
 #pragma unroll
             for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
             nxt_t = (T)nxt[13];
-            if (idx > 0) load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
+            if constexpr (kMlp) {
+                cur_k = nxt_k;
+                cur_flag = __float_as_uint((float)nxt[15]) != 0u;
+            }
+            if (idx > 0) {
+                load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
+                if constexpr (kMlp) nxt_k = record_index(chunks, wray, idx - 1);
+            }
         }
         if (!kUnpol && started) {
             // merged N half-steps from the previous sample to this one (to the camera node on
@@ -1900,7 +1922,22 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
                 T cth = fq(kdb, (-kdu) * fsqrt(P.bsq));
                 cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
                 T co[8];
-                synchrotron_coefficients<T>(P.ne, P.th, P.bg, nu_fl, cth, co);
+                bool learned = false;
+                if constexpr (kMlp) {
+                    const mlp::ModelIn mi = mlp::model_inputs(P.th, P.bg, nu_fl, cth);
+                    if (cur_flag && mi.ok && P.ne > T(0)) {
+                        // (loaded here: loading them one sample ahead with the record measured
+                        // slower, 61.2 against 58.9 ms at 1024^2)
+                        const float4* yq = reinterpret_cast<const float4*>(mlp_y + 8 * cur_k);
+                        const float4 y0 = __ldg(yq), y1 = __ldg(yq + 1);
+                        const float y[7] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z};
+                        float o[7];
+                        mlp::model_outputs_from_y(mlp_params, y, mi.f, o);
+                        mlp::coefficients_from(o, P.ne, P.th, P.bg, nu_fl, cth, co);
+                        learned = true;
+                    }
+                }
+                if (!learned) synchrotron_coefficients<T>(P.ne, P.th, P.bg, nu_fl, cth, co);
                 const T g = fq(ic<T>(im, kcFreq), nu_fl);
                 const T path = ic<T>(im, kcLen) * (-kdu);
                 const T eg = g * g * g * path;
@@ -1935,8 +1972,11 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
                                                        const RayHdr* __restrict__ hdr,
                                                        const R* __restrict__ pool,
                                                        const int32_t* __restrict__ chunks,
-                                                       Counters* ctr, BlockSource bs) {
-    transfer_body<T, R, kF>(imgs, n_images, ray_begin, ray_end, hdr, pool, chunks, ctr, bs);
+                                                       Counters* ctr, BlockSource bs,
+                                                       const float* __restrict__ mlp_y,
+                                                       const float* __restrict__ mlp_params) {
+    transfer_body<T, R, kF>(imgs, n_images, ray_begin, ray_end, hdr, pool, chunks, ctr, bs,
+                            mlp_y, mlp_params);
 }
 // Register cap and CTA size of the FP64 transfer kernel. Its FP64 arithmetic runs at 1/64 of
 // the FP32 rate with long dependent latencies, so resident warps matter more than spills to
@@ -1949,6 +1989,19 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
 #ifndef BL_TR64_THREADS
 #define BL_TR64_THREADS 64
 #endif
+// The transfer of the learned-coefficient form (its model outputs from the pool pass),
+// compiled for 4 resident CTAs an SM (128 registers; uncapped it takes 142 registers and 3
+// CTAs, measured 62.5 against 58.9 ms at 1024^2).
+template <bool kSlow>
+__global__ void __launch_bounds__(128, 4) transfer_learned_kernel(
+        const ImageDesc* __restrict__ imgs, int n_images, int64_t ray_begin, int64_t ray_end,
+        const RayHdr* __restrict__ hdr, const float* __restrict__ pool,
+        const int32_t* __restrict__ chunks, Counters* ctr, BlockSource bs,
+        const float* __restrict__ mlp_y, const float* __restrict__ mlp_params) {
+    transfer_body<float, float, kFMlp | (kSlow ? kFSlow : 0)>(
+        imgs, n_images, ray_begin, ray_end, hdr, pool, chunks, ctr, bs, mlp_y, mlp_params);
+}
+
 constexpr int kTransferFp64Threads = BL_TR64_THREADS;
 template <int kF>
 __global__ void __maxnreg__(BL_TR64_MAXNREG) transfer_kernel_fp64(const ImageDesc* __restrict__ imgs,
@@ -1959,173 +2012,67 @@ __global__ void __maxnreg__(BL_TR64_MAXNREG) transfer_kernel_fp64(const ImageDes
                                                      const int32_t* __restrict__ chunks,
                                                      Counters* ctr, BlockSource bs) {
     transfer_body<double, double, kF>(imgs, n_images, ray_begin, ray_end, hdr, pool, chunks,
-                                      ctr, bs);
+                                      ctr, bs, nullptr, nullptr);
 }
 
 // ---------------------------------------------------------------------------------------
-// Transfer with the learned coefficient model (FP32). The same per-sample work as
-// transfer_kernel, but the loop runs in lockstep across the CTA: every iteration each of the
-// 128 threads contributes one row (its sample's model inputs, or a masked row) to a
-// 128-sample tensor-core tile of the perceptron, so the coefficient evaluation of the whole
-// CTA is three chained MMAs. Samples outside the model's domain use the exact fits.
+// Learned coefficients, first pass: the model inputs of every sample record. One warp takes a
+// ray, its lanes 32 consecutive records at a time (the records of a chunk lie together in the
+// pool): geometry, plasma state and the fluid-frame frequency and pitch angle at the sample,
+// as the transfer computes them, then the model's input row (mlp::input_row) into the record's
+// last 8 bytes -- zeros where the sample has no plasma or lies outside the model's domain.
 // ---------------------------------------------------------------------------------------
-template <class R, bool kSlow>
-__global__ void __launch_bounds__(128) transfer_mlp_kernel(const ImageDesc* __restrict__ imgs,
-                                                           int n_images, int64_t ray_begin,
-                                                           int64_t ray_end,
-                                                           const RayHdr* __restrict__ hdr,
-                                                           const R* __restrict__ pool,
-                                                           const int32_t* __restrict__ chunks,
-                                                           const float* __restrict__ mlp_params,
-                                                           Counters* ctr, BlockSource bs) {
+template <bool kSlow>
+__global__ void __launch_bounds__(128) mlp_inputs_kernel(const ImageDesc* __restrict__ imgs,
+                                                         int n_images, int64_t ray_begin,
+                                                         int64_t ray_end,
+                                                         const RayHdr* __restrict__ hdr,
+                                                         float* __restrict__ pool,
+                                                         const int32_t* __restrict__ chunks,
+                                                         Counters* ctr, BlockSource bs) {
     using T = float;
-    __shared__ mlp::FwdSmem S;
-    mlp::fwd_init(S, mlp_params);
-    uint32_t phase = 0;
-    bool tc_ok = true;
+    const int lane = threadIdx.x & 31;
     const int64_t re = wave_end(bs, ray_end);
     const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
-    int64_t wray = 0;
-    bool active = false;
-    int64_t ray = 0, opix = 0;
-    int q = 0, pi = 0, pj = 0;
-    int32_t idx = 0;
-    Coh<T> N;
-    bool started = false;
-    T prev[kRecVals];
-    R nxt[RecStride<R>::v];
-    T kt = T(0), a = T(0), m = T(0), nu_norm = T(0);
-    bool flat = false;
-
-    bool exhausted = false;
-    while (tc_ok) {
-        const bool need = !active && !exhausted;
-        const unsigned long long got = warp_refill(&ctr->next_ray_tr, need);
-        if (need) {
-            if ((int64_t)got >= total_rays) exhausted = true;
-            else { wray = (int64_t)got; ray = ray_begin + wray; }
-        }
-        bool work = active || (need && !exhausted);
-        if (!__syncthreads_or(work)) break;
-        if (work && !active) {
-            setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
-            const ImageDesc& im = imgs[q];
-            const RayHdr hd = hdr[wray];
-            if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) {
-                const int64_t npix = im.n_rays;
-                const double val = hd.status == BL_RAY_OVERFLOW ? nan("") : 0.0;
-                for (int c = 0; c < 4; ++c) {
-                    if (im.dtype == 0) ((double*)im.stokes)[c * npix + opix] = val;
-                    else ((float*)im.stokes)[c * npix + opix] = (float)val;
-                }
-                work = false;
-            } else {
-                idx = hd.nrec - 1;
-                load_record<R>(record_ptr(pool, chunks, wray, idx), nxt);
-                kt = (T)hd.kt;
-                nu_norm = (T)(hd.nnorm * im.freq);
-                a = ic<T>(im, kcSpin);
-                m = ic<T>(im, kcMass);
-                flat = im.flat != 0;
-#pragma unroll
-                for (int c = 0; c < 10; ++c) N.re[c] = T(0);
-#pragma unroll
-                for (int c = 0; c < 6; ++c) N.im[c] = T(0);
-                started = false;
-                active = true;
-            }
-        }
+    while (true) {
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicAdd(&ctr->next_ray_mi, 1ull);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if ((int64_t)got >= total_rays) break;
+        const int64_t wray = (int64_t)got, ray = ray_begin + wray;
+        int q, pi, pj;
+        int64_t opix;
+        setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
+        const RayHdr hd = hdr[wray];
+        if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) continue;
         const ImageDesc& im = imgs[q];
-        // ---- phase A: transport to this sample, plasma state
-        T cur[kRecVals];
-        bool samp = false;
-        KSGeom<T> G;
-        Plasma<T> P;
-        T kl[4], ku[4], kdu = T(0), nu_fl = T(0), cth = T(0);
-        // idx < 0: every sample is in; this iteration takes the last half-step to the camera
-        // node and reads the pixel out (its row of the tile is masked)
-        const bool finishing = work && idx < 0;
-        T ts = T(0);   // the sample's coordinate time
-        if (work) {
-            if (!finishing) {
-#pragma unroll
-                for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
-                ts = (T)nxt[13];
-                if (idx > 0) load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
-            }
-            if (started) {
-                T A0[4][4], A1[4][4];
-                const T kp[4] = {kt, prev[3], prev[4], prev[5]};
-                const T kn[4] = {kt, prev[9], prev[10], prev[11]};
-                transport_matrix<T>(prev, kp, a, m, flat, A0);
-                transport_matrix<T>(prev + 6, kn, a, m, flat, A1);
-                coh_pc_step(N, A0, A1, T(0.5) * (prev[12] + (finishing ? T(0) : cur[12])));
-            }
-            if (finishing) {
-                KSGeom<T> Gc;
-                ks_geom<T>(prev[6], prev[7], prev[8], a, m, flat, false, Gc);
-                T hv[4], vv[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) { hv[c] = im.f_hh[c]; vv[c] = im.f_vv[c]; }
-                T hl[4], vl[4];
-                lower4(Gc, hv, hl);
-                lower4(Gc, vv, vl);
-                T st[4];
-                coh_to_stokes(N, hl, vl, st);
-                const int64_t npix = im.n_rays;
-                for (int c = 0; c < 4; ++c) {
-                    if (im.dtype == 0) ((double*)im.stokes)[c * npix + opix] = (double)st[c];
-                    else ((float*)im.stokes)[c * npix + opix] = (float)st[c];
-                }
-                active = false;
-            }
-        }
-        if (work && !finishing) {
-            const T xs[3] = {cur[0], cur[1], cur[2]};
+        const T kt = (T)hd.kt, nu_norm = (T)(hd.nnorm * im.freq);
+        const T a = ic<T>(im, kcSpin), m = ic<T>(im, kcMass);
+        const bool flat = im.flat != 0;
+        for (int32_t base = 0; base < hd.nrec; base += 32) {
+            const int32_t idx = base + lane;
+            if (idx >= hd.nrec) break;
+            float* rec = pool + record_index(chunks, wray, idx) * RecStride<float>::v;
+            float v[RecStride<float>::v];
+            load_record<float>(rec, v);
+            const T xs[3] = {v[0], v[1], v[2]};
+            KSGeom<T> G;
             ks_geom<T>(xs[0], xs[1], xs[2], a, m, flat, false, G);
-            samp = plasma_at<T, kSlow>(im, xs, ts, G, P);
-            if (samp) {
-                kl[0] = kt; kl[1] = cur[3]; kl[2] = cur[4]; kl[3] = cur[5];
-                raise4(G, kl, ku);
-                kdu = kl[0] * P.u[0] + kl[1] * P.u[1] + kl[2] * P.u[2] + kl[3] * P.u[3];
+            Plasma<T> P;
+            uint2 row = make_uint2(0u, 0u);
+            if (plasma_at<T, kSlow>(im, xs, v[13], G, P)) {
+                const T kl[4] = {kt, v[3], v[4], v[5]};
+                const T kdu = kl[0] * P.u[0] + kl[1] * P.u[1] + kl[2] * P.u[2] + kl[3] * P.u[3];
                 const T kdb = kl[0] * P.b[0] + kl[1] * P.b[1] + kl[2] * P.b[2] + kl[3] * P.b[3];
-                nu_fl = nu_norm * (-kdu);
-                cth = fq(kdb, (-kdu) * fsqrt(P.bsq));
+                const T nu_fl = nu_norm * (-kdu);
+                T cth = fq(kdb, (-kdu) * fsqrt(P.bsq));
                 cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
+                const mlp::ModelIn mi = mlp::model_inputs(P.th, P.bg, nu_fl, cth);
+                if (mi.ok && P.ne > T(0)) row = mlp::input_row(mi.f);
             }
+            *reinterpret_cast<uint2*>(rec + 14) = row;
         }
-        // ---- coefficients: one tensor-core tile for the CTA
-        const mlp::ModelIn mi = mlp::model_inputs(samp ? P.th : 0.0f, samp ? P.bg : 0.0f,
-                                                  samp ? nu_fl : 1.0f, samp ? cth : 0.0f);
-        const bool use = samp && mi.ok && P.ne > T(0);
-        float o[7];
-        tc_ok = mlp::fwd_tile<true>(S, phase, mi.f, use, o);
-        if (!tc_ok) break;
-        // ---- phase B: Stokes step at this sample
-        if (samp) {
-            T co[8];
-            if (use) mlp::coefficients_from(o, P.ne, P.th, P.bg, nu_fl, cth, co);
-            else synchrotron_coefficients<T>(P.ne, P.th, P.bg, nu_fl, cth, co);
-            const T g = fq(ic<T>(im, kcFreq), nu_fl);
-            const T path = ic<T>(im, kcLen) * (-kdu);
-            const T eg = g * g * g * path;
-            const T coef[8] = {co[0] * eg, co[1] * eg, co[2] * eg, co[3] * path,
-                               co[4] * path, co[5] * path, co[6] * path, co[7] * path};
-            T e1[4], e2[4], e1l[4], e2l[4];
-            fluid_basis<T>(G, P, kl, ku, e1, e2, e1l, e2l);
-            T s0[4], s1[4];
-            coh_to_stokes(N, e1l, e2l, s0);
-            stokes_step<T>(coef, s0, cur[12], s1);
-            stokes_to_coh(e1, e2, s1, N);
-            started = true;
-        }
-        if (!work || finishing) continue;
-#pragma unroll
-        for (int c = 0; c < kRecVals; ++c) prev[c] = cur[c];
-        --idx;
     }
-    if (!tc_ok && threadIdx.x == 0) atomicAdd(&ctr->mlp_timeouts, 1ull);
-    mlp::fwd_finish(S, phase, tc_ok);
 }
 
 // ---------------------------------------------------------------------------------------

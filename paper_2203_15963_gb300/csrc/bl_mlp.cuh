@@ -18,6 +18,7 @@
 // least-squares affine fit of the targets and its residual's standard deviation), so the
 // network learns only the non-linear remainder.
 #pragma once
+#include "bl_internal.cuh"
 #include "bl_math.cuh"
 #include "bl_tc.cuh"
 
@@ -33,7 +34,7 @@ constexpr long long kWaitCycles = 1ll << 31;   // ~1 s at 2 GHz
 __device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 // z sigma(z) = z/2 (1 + tanh(z/2)) with the hardware tanh (relative error about 2^-11, below
 // the bf16 rounding of the stored activation, 2^-9): one special-function operation instead
-// of two. Inference inside the fused transfer only; training keeps silu above.
+// of two. Inference in the trace only; training keeps silu above.
 __device__ __forceinline__ float silu_tanh(float z) {
     const float hz = 0.5f * z;
     float t;
@@ -215,6 +216,57 @@ __device__ __forceinline__ void issue_barrier_then(FwdSmem& S) {
 // computed on zero inputs and ignored; a tile without a valid row issues no MMA and leaves o
 // at zero). kTanh selects the hardware-tanh activation. Returns false if a tensor-core wait
 // timed out.
+// Columns 0-3 of a sample's A-operand row as two packed bf16 pairs: the three inputs and the
+// constant 1 of the first-layer bias.
+__device__ __forceinline__ uint2 input_row(const float f[3]) {
+    return make_uint2(tc::pack_bf16x2(f[0], f[1]), tc::pack_bf16x2(f[2], 1.0f));
+}
+
+// The network of a tile whose rows arrive packed (input_row); o is y = W3 h2 + b3 before the
+// affine output map. Same waits and masking as fwd_tile.
+template <bool kTanh>
+__device__ __forceinline__ bool fwd_tile_y(FwdSmem& S, uint32_t& phase, uint2 row, bool valid,
+                                           float y[7]) {
+    const int t = threadIdx.x;
+    *reinterpret_cast<uint2*>(S.x + tc::kmajor(t, 0, 16)) = valid ? row : make_uint2(0u, 0u);
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    if (!__syncthreads_or(valid)) {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int k = 0; k < kOut; ++k) y[k] = 0.0f;
+        return true;
+    }
+    if (t == 0) {
+        tc::fence_after_sync();
+        tc::gemm_bf16(S.tmem, S.x, S.w1, 64, 16);
+        tc::mma_commit(&S.bar);
+    }
+    if (!cta_wait(S, phase)) return false;
+    hidden_epilogue<kTanh>(S, nullptr);          // first-layer bias is in W1
+    issue_barrier_then(S);
+    if (t == 0) {
+        tc::fence_after_sync();
+        tc::gemm_bf16(S.tmem, S.h, S.w2, 64, 64);
+        tc::mma_commit(&S.bar);
+    }
+    if (!cta_wait(S, phase)) return false;
+    hidden_epilogue<kTanh>(S, S.b2);
+    issue_barrier_then(S);
+    if (t == 0) {
+        tc::fence_after_sync();
+        tc::gemm_bf16(S.tmem, S.h, S.w3, 16, 64);
+        tc::mma_commit(&S.bar);
+    }
+    if (!cta_wait(S, phase)) return false;
+    float v[16];
+    tc::tmem_ld16(tc::tmem_lane_addr(S.tmem, 0), v);
+#pragma unroll
+    for (int k = 0; k < kOut; ++k) y[k] = v[k] + S.b3[k];
+    tc::fence_before_sync();
+    return true;
+}
+
 template <bool kTanh = false>
 __device__ __forceinline__ bool fwd_tile(FwdSmem& S, uint32_t& phase, const float f[3], bool valid,
                                          float o[7]) {
@@ -298,6 +350,54 @@ __global__ void __launch_bounds__(128) forward_kernel(const float* __restrict__ 
     }
     if (!ok && threadIdx.x == 0) atomicExch(err, 1);
     fwd_finish(S, phase, ok);
+}
+
+// The learned model over a trace's sample records (the middle pass of the learned-coefficient
+// transfer): record k of the pool carries its sample's input row in its last 8 bytes (values
+// 14-15, written by the model-input kernel; zero where the sample has no plasma or lies
+// outside the model's domain); the model's outputs o[7] (padded to 8) go to out[8 k ..].
+// Tiles of 128 consecutive records over the pool's used chunks, several CTAs an SM, no
+// lockstep with the transfer. The used record count is read on the device (the pool cursor
+// after the geodesic kernel), so the launch needs no host round trip.
+__global__ void __launch_bounds__(128) forward_pool_kernel(const float* __restrict__ P,
+                                                           const float* __restrict__ pool,
+                                                           const unsigned long long* __restrict__ pool_next,
+                                                           unsigned long long pool_chunks,
+                                                           float* __restrict__ out,
+                                                           unsigned long long* timeouts) {
+    __shared__ FwdSmem S;
+    fwd_init(S, P);
+    uint32_t phase = 0;
+    bool ok = true;
+    const unsigned long long used_chunks = *pool_next < pool_chunks ? *pool_next : pool_chunks;
+    const int64_t n = (int64_t)used_chunks * kChunk;
+    const int64_t tiles = (n + 127) / 128;
+    for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const int64_t k = tile * 128 + threadIdx.x;
+        uint2 row = make_uint2(0u, 0u);
+        if (k < n) row = __ldg(reinterpret_cast<const uint2*>(pool + 16 * k + 14));
+        const bool valid = row.y != 0u;          // the constant-1 column is set
+        float y[7];
+        ok = fwd_tile_y<true>(S, phase, row, valid, y);
+        if (ok && valid) {
+            float4* q = reinterpret_cast<float4*>(out + 8 * k);
+            q[0] = make_float4(y[0], y[1], y[2], y[3]);
+            q[1] = make_float4(y[4], y[5], y[6], 0.0f);
+        }
+    }
+    if (!ok && threadIdx.x == 0) atomicAdd(timeouts, 1ull);
+    fwd_finish(S, phase, ok);
+}
+
+// The affine output map o = offset + scale y + A f of the model, for a sample whose inputs f
+// were those of its packed row (the transfer reads y from the pool pass and applies it).
+__device__ __forceinline__ void model_outputs_from_y(const float* __restrict__ P, const float y[7],
+                                                     const float f[3], float o[7]) {
+#pragma unroll
+    for (int k = 0; k < kOut; ++k)
+        o[k] = __ldg(P + kOffMean + k) + __ldg(P + kOffScale + k) * y[k] +
+               __ldg(P + kOffA + 3 * k) * f[0] + __ldg(P + kOffA + 3 * k + 1) * f[1] +
+               __ldg(P + kOffA + 3 * k + 2) * f[2];
 }
 
 // coefficients [n][8] of plasma samples in [n][5] (n_e, Theta_e, B, nu, cos theta_B): the
