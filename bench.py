@@ -353,8 +353,8 @@ def form_rooflines(prec_name, attempts, samples, geo_s, tr_s, peaks):
                     "fast": "geodesic_kernel<float, df64>"}[prec_name],
                    FLOP64_PER_ATTEMPT, attempts, "DP attempt", geo_s, pk(geo_kind),
                    traffic_key={"fp64": "geodesic_fp64", "fast": "geodesic_df64"}.get(prec_name))
-    tr = roofline("transfer_kernel_fp64<0>" if prec_name == "fp64"
-                  else "transfer_kernel<float, float, 0>",
+    tr = roofline("transfer phase: fp64_samples_kernel + transport_fp64_kernel"
+                  if prec_name == "fp64" else "transfer_kernel<float, float, 0>",
                   FLOP_PER_SAMPLE, samples, "transfer sample", tr_s, pk(tr_kind),
                   traffic_key="transfer_fp64" if prec_name == "fp64" else "transfer_fp32",
                   note=("algorithmic flops: the method's per-sample arithmetic as the FP32 "

@@ -56,11 +56,19 @@ constexpr int64_t kChunksPerRay = 16;
 constexpr int64_t kWaveRays = 1 << 20;
 
 struct Layout {
-    size_t counters, descs, hdr, init, chunks, pool, mlp_y, total;
+    size_t counters, descs, hdr, init, chunks, pool, mlp_y, pre, pre_flag, total;
     int64_t rays;          // rays of the whole call
     int64_t wave;          // rays per wave (the workspace holds one wave)
     int64_t pool_chunks;
 };
+
+// The FP64 transfer runs as two passes (fp64_samples_kernel, then the transport and Stokes
+// steps) when set; 0 keeps the single fused kernel.
+#ifndef BL_TR64_SPLIT
+#define BL_TR64_SPLIT 1
+#endif
+constexpr bool kFp64Split = BL_TR64_SPLIT != 0;
+
 
 // mlp: room for the learned model's outputs, 8 floats for every record of the pool
 Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precision,
@@ -80,6 +88,14 @@ Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precis
     L.pool = off;     off = align_up(off + rec * bl::kChunk * (size_t)L.pool_chunks);
     L.mlp_y = off;
     if (mlp && transfer) off = align_up(off + 8 * sizeof(float) * bl::kChunk * (size_t)L.pool_chunks);
+    // FP64 form: the sample pass's coefficients and basis, and a flag byte, a pool record
+    L.pre = off;
+    L.pre_flag = off;
+    if (precision == BL_PREC_FP64 && transfer && kFp64Split) {
+        off = align_up(off + bl::kPreVals * sizeof(double) * bl::kChunk * (size_t)L.pool_chunks);
+        L.pre_flag = off;
+        off = align_up(off + bl::kChunk * (size_t)L.pool_chunks);
+    }
     L.total = off;
     return L;
 }
@@ -300,11 +316,15 @@ struct DevInfo {
     int tr_occ[2][8] = {};          // transfer variants: [double, float][feature bits]
     int tr_mlp_occ[2] = {0, 0};     // learned-coefficient transfer: [fast light, slow light]
     int mi_occ[2] = {0, 0};         // learned-coefficient model inputs: [fast, slow light]
+    int pre_occ[2] = {0, 0};        // FP64 sample pass: [fast, slow light]
+    int tr_pre_occ[2] = {0, 0};     // FP64 transfer after the sample pass: [fast, slow light]
     int fwd_pool_occ = 0;           // the model over the sample pool
     int rk_occ[2] = {0, 0};         // RK2/RK4 geodesic kernel: [double records, float records]
     // CTAs per SM of the transfer variant a launch uses
     int transfer(int precision, const float* mlp, int feat) const {
         if (mlp) return tr_mlp_occ[(feat & bl::kFSlow) ? 1 : 0];
+        if (precision == BL_PREC_FP64 && kFp64Split && !(feat & (bl::kFUnpol | bl::kFAux)))
+            return tr_pre_occ[(feat & bl::kFSlow) ? 1 : 0];
         return tr_occ[precision == BL_PREC_FP64 ? 0 : 1][feat & 7];
     }
 };
@@ -368,6 +388,14 @@ int dev_info(DevInfo& out) {
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.fwd_pool_occ, bl::mlp::forward_pool_kernel, 128, 0));
         for (int i = 0; i < 2; ++i)
             if (di.mi_occ[i] < 1) di.mi_occ[i] = 1;
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.pre_occ[0], bl::fp64_samples_kernel<false>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.pre_occ[1], bl::fp64_samples_kernel<true>, 128, 0));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.tr_pre_occ[0], bl::transport_fp64_kernel, bl::kTransferFp64Threads, 0));
+        di.tr_pre_occ[1] = di.tr_pre_occ[0];
+        for (int i = 0; i < 2; ++i) {
+            if (di.pre_occ[i] < 1) di.pre_occ[i] = 1;
+            if (di.tr_pre_occ[i] < 1) di.tr_pre_occ[i] = 1;
+        }
         if (di.fwd_pool_occ < 1) di.fwd_pool_occ = 1;
         for (int i = 0; i < 2; ++i)
             if (di.tr_mlp_occ[i] < 1) di.tr_mlp_occ[i] = 1;
@@ -386,40 +414,38 @@ template <class T, class R>
 void launch_transfer(int feat, unsigned grid, cudaStream_t st, const bl::ImageDesc* d, int n,
                      int64_t b, int64_t e, const bl::RayHdr* hdr, const R* pool,
                      const int32_t* chunks, bl::Counters* ctr, bl::BlockSource bs,
-                     const float* mlp_y = nullptr, const float* mlp_params = nullptr) {
+                     bl::SideIn side = bl::SideIn{nullptr, nullptr, nullptr, nullptr}) {
     if constexpr (std::is_same<T, double>::value) {
         constexpr int th = bl::kTransferFp64Threads;
         switch (feat & 7) {
-            case 0: bl::transfer_kernel_fp64<0><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            case 1: bl::transfer_kernel_fp64<1><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            case 2: bl::transfer_kernel_fp64<2><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            case 3: bl::transfer_kernel_fp64<3><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            case 4: bl::transfer_kernel_fp64<4><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            case 5: bl::transfer_kernel_fp64<5><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            case 6: bl::transfer_kernel_fp64<6><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
-            default: bl::transfer_kernel_fp64<7><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs); break;
+            case 0: bl::transfer_kernel_fp64<0><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            case 1: bl::transfer_kernel_fp64<1><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            case 2: bl::transfer_kernel_fp64<2><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            case 3: bl::transfer_kernel_fp64<3><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            case 4: bl::transfer_kernel_fp64<4><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            case 5: bl::transfer_kernel_fp64<5><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            case 6: bl::transfer_kernel_fp64<6><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            default: bl::transfer_kernel_fp64<7><<<grid, th, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
         }
     } else {
-        const float* my = mlp_y;
-        const float* mp = mlp_params;
         if (feat & bl::kFMlp) {
             if constexpr (std::is_same<R, float>::value) {
                 if (feat & bl::kFSlow)
-                    bl::transfer_learned_kernel<true><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp);
+                    bl::transfer_learned_kernel<true><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side);
                 else
-                    bl::transfer_learned_kernel<false><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp);
+                    bl::transfer_learned_kernel<false><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side);
             }
             return;
         }
         switch (feat & 7) {
-            case 0: bl::transfer_kernel<T, R, 0><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
-            case 1: bl::transfer_kernel<T, R, 1><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
-            case 2: bl::transfer_kernel<T, R, 2><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
-            case 3: bl::transfer_kernel<T, R, 3><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
-            case 4: bl::transfer_kernel<T, R, 4><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
-            case 5: bl::transfer_kernel<T, R, 5><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
-            case 6: bl::transfer_kernel<T, R, 6><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
-            default: bl::transfer_kernel<T, R, 7><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, my, mp); break;
+            case 0: bl::transfer_kernel<T, R, 0><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            case 1: bl::transfer_kernel<T, R, 1><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            case 2: bl::transfer_kernel<T, R, 2><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            case 3: bl::transfer_kernel<T, R, 3><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            case 4: bl::transfer_kernel<T, R, 4><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            case 5: bl::transfer_kernel<T, R, 5><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            case 6: bl::transfer_kernel<T, R, 6><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
+            default: bl::transfer_kernel<T, R, 7><<<grid, 128, 0, st>>>(d, n, b, e, hdr, pool, chunks, ctr, bs, side); break;
         }
     }
 }
@@ -536,10 +562,27 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
                 ++g_launches;
                 BL_CUDA(cudaGetLastError());
                 launch_transfer<float, float>(cfg.feat | bl::kFMlp, tr_grid, st, d_desc, n_images, b,
-                                              e, hdr, fpool, chunks, ctr, cfg.bs, my, mlp);
+                                              e, hdr, fpool, chunks, ctr, cfg.bs,
+                                              bl::SideIn{my, mlp, nullptr, nullptr});
             } else if (precision != BL_PREC_FP64) {
                 launch_transfer<float, float>(cfg.feat, tr_grid, st, d_desc, n_images, b, e, hdr,
                                               fpool, chunks, ctr, cfg.bs);
+            } else if (kFp64Split && !(cfg.feat & (bl::kFUnpol | bl::kFAux))) {
+                // FP64 in two passes: the sample pass, then transport and Stokes steps
+                double* pre = (double*)(ws + L.pre);
+                unsigned char* pflag = (unsigned char*)(ws + L.pre_flag);
+                const unsigned pre_grid = (unsigned)(di.sms * di.pre_occ[slow ? 1 : 0]);
+                if (slow)
+                    bl::fp64_samples_kernel<true><<<pre_grid, 128, 0, st>>>(
+                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag);
+                else
+                    bl::fp64_samples_kernel<false><<<pre_grid, 128, 0, st>>>(
+                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag);
+                ++g_launches;
+                BL_CUDA(cudaGetLastError());
+                bl::transport_fp64_kernel<<<tr_grid, bl::kTransferFp64Threads, 0, st>>>(
+                    d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs,
+                    bl::SideIn{nullptr, nullptr, pre, pflag});
             } else {
                 launch_transfer<double, double>(cfg.feat, tr_grid, st, d_desc, n_images, b, e,
                                                 hdr, dpool, chunks, ctr, cfg.bs);

@@ -103,6 +103,18 @@ struct BlockSource {
     int32_t block;                        // B
 };
 
+// Side inputs of the transfer variants that split their per-sample work over passes: the
+// learned model's outputs (8 floats a pool record) and its parameters, or, in the FP64 form,
+// each record's precomputed scaled coefficients and fluid-frame basis (24 doubles a pool
+// record) with a flag byte (1: the sample carries plasma).
+struct SideIn {
+    const float* mlp_y;
+    const float* mlp_params;
+    const double* pre;
+    const unsigned char* pre_flag;
+};
+constexpr int kPreVals = 24;
+
 struct Counters {
     unsigned long long next_ray_geo;
     unsigned long long next_ray_tr;

@@ -1774,9 +1774,9 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
                                               const RayHdr* __restrict__ hdr,
                                               const R* __restrict__ pool,
                                               const int32_t* __restrict__ chunks,
-                                              Counters* ctr, BlockSource bs,
-                                              const float* __restrict__ mlp_y,
-                                              const float* __restrict__ mlp_params) {
+                                              Counters* ctr, BlockSource bs, SideIn side) {
+    const float* __restrict__ mlp_y = side.mlp_y;
+    const float* __restrict__ mlp_params = side.mlp_params;
     constexpr bool kSlow = (kF & kFSlow) != 0;
     constexpr bool kUnpol = (kF & kFUnpol) != 0;
     constexpr bool kAux = (kF & kFAux) != 0;
@@ -1784,6 +1784,7 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
     // record), the record's last value flags the samples the model evaluated
     constexpr bool kMlp = (kF & kFMlp) != 0;
     static_assert(!kMlp || std::is_same<R, float>::value, "the learned model needs FP32 records");
+    constexpr bool kIdx = kMlp;   // the transfer needs each record's pool index
     int64_t nxt_k = 0;
     const int64_t re = wave_end(bs, ray_end);
     const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
@@ -1834,7 +1835,7 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
             }
             idx = hd.nrec - 1;
             load_record<R>(record_ptr(pool, chunks, wray, idx), nxt);
-            if constexpr (kMlp) nxt_k = record_index(chunks, wray, idx);
+            if constexpr (kIdx) nxt_k = record_index(chunks, wray, idx);
             kt = (T)hd.kt;
             nu_norm = (T)(hd.nnorm * im.freq);
             a = ic<T>(im, kcSpin);
@@ -1862,13 +1863,11 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
 #pragma unroll
             for (int c = 0; c < kRecVals; ++c) cur[c] = (T)nxt[c];
             nxt_t = (T)nxt[13];
-            if constexpr (kMlp) {
-                cur_k = nxt_k;
-                cur_flag = __float_as_uint((float)nxt[15]) != 0u;
-            }
+            if constexpr (kIdx) cur_k = nxt_k;
+            if constexpr (kMlp) cur_flag = __float_as_uint((float)nxt[15]) != 0u;
             if (idx > 0) {
                 load_record<R>(record_ptr(pool, chunks, wray, idx - 1), nxt);
-                if constexpr (kMlp) nxt_k = record_index(chunks, wray, idx - 1);
+                if constexpr (kIdx) nxt_k = record_index(chunks, wray, idx - 1);
             }
         }
         if (!kUnpol && started) {
@@ -1973,10 +1972,8 @@ __global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restri
                                                        const R* __restrict__ pool,
                                                        const int32_t* __restrict__ chunks,
                                                        Counters* ctr, BlockSource bs,
-                                                       const float* __restrict__ mlp_y,
-                                                       const float* __restrict__ mlp_params) {
-    transfer_body<T, R, kF>(imgs, n_images, ray_begin, ray_end, hdr, pool, chunks, ctr, bs,
-                            mlp_y, mlp_params);
+                                                       SideIn side) {
+    transfer_body<T, R, kF>(imgs, n_images, ray_begin, ray_end, hdr, pool, chunks, ctr, bs, side);
 }
 // Register cap and CTA size of the FP64 transfer kernel. Its FP64 arithmetic runs at 1/64 of
 // the FP32 rate with long dependent latencies, so resident warps matter more than spills to
@@ -1996,10 +1993,9 @@ template <bool kSlow>
 __global__ void __launch_bounds__(128, 4) transfer_learned_kernel(
         const ImageDesc* __restrict__ imgs, int n_images, int64_t ray_begin, int64_t ray_end,
         const RayHdr* __restrict__ hdr, const float* __restrict__ pool,
-        const int32_t* __restrict__ chunks, Counters* ctr, BlockSource bs,
-        const float* __restrict__ mlp_y, const float* __restrict__ mlp_params) {
+        const int32_t* __restrict__ chunks, Counters* ctr, BlockSource bs, SideIn side) {
     transfer_body<float, float, kFMlp | (kSlow ? kFSlow : 0)>(
-        imgs, n_images, ray_begin, ray_end, hdr, pool, chunks, ctr, bs, mlp_y, mlp_params);
+        imgs, n_images, ray_begin, ray_end, hdr, pool, chunks, ctr, bs, side);
 }
 
 constexpr int kTransferFp64Threads = BL_TR64_THREADS;
@@ -2010,9 +2006,216 @@ __global__ void __maxnreg__(BL_TR64_MAXNREG) transfer_kernel_fp64(const ImageDes
                                                      const RayHdr* __restrict__ hdr,
                                                      const double* __restrict__ pool,
                                                      const int32_t* __restrict__ chunks,
-                                                     Counters* ctr, BlockSource bs) {
+                                                     Counters* ctr, BlockSource bs,
+                                                     SideIn side) {
     transfer_body<double, double, kF>(imgs, n_images, ray_begin, ray_end, hdr, pool, chunks,
-                                      ctr, bs, nullptr, nullptr);
+                                      ctr, bs, side);
+}
+
+
+// ---------------------------------------------------------------------------------------
+// FP64 form, first pass of the transfer: everything a sample needs that does not depend on
+// the ray's running coherency -- geometry, plasma state, the scaled synchrotron coefficients
+// and the fluid-frame basis -- for every record, written per record (kPreVals doubles and a
+// flag byte). One warp takes a ray, its lanes 32 consecutive records at a time: no
+// sequential dependency, so all lanes work and the FP64 latencies overlap. The arithmetic is
+// that of the transfer kernel's sample step, operation for operation. The second pass
+// (transport_fp64_kernel) runs the transport and the Stokes steps.
+// ---------------------------------------------------------------------------------------
+// Resident CTAs an SM of the FP64 sample pass (16: 32 registers, the SM's 64 warps; measured
+// on the 9 x 256^2 step with the transport pass at 32 registers: 4 CTAs 326.3 ms for both
+// passes, 8: 324.4, 16: 322.7; the single fused kernel 346.7 ms).
+#ifndef BL_PRE64_MIN_CTAS
+#define BL_PRE64_MIN_CTAS 16
+#endif
+template <bool kSlow>
+__global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(const ImageDesc* __restrict__ imgs,
+                                                           int n_images, int64_t ray_begin,
+                                                           int64_t ray_end,
+                                                           const RayHdr* __restrict__ hdr,
+                                                           const double* __restrict__ pool,
+                                                           const int32_t* __restrict__ chunks,
+                                                           Counters* ctr, BlockSource bs,
+                                                           double* __restrict__ pre,
+                                                           unsigned char* __restrict__ pre_flag) {
+    using T = double;
+    const int lane = threadIdx.x & 31;
+    const int64_t re = wave_end(bs, ray_end);
+    const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
+    while (true) {
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicAdd(&ctr->next_ray_mi, 1ull);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if ((int64_t)got >= total_rays) break;
+        const int64_t wray = (int64_t)got, ray = ray_begin + wray;
+        int q, pi, pj;
+        int64_t opix;
+        setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
+        const RayHdr hd = hdr[wray];
+        if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) continue;
+        const ImageDesc& im = imgs[q];
+        const T kt = hd.kt, nu_norm = hd.nnorm * im.freq;
+        const T a = ic<T>(im, kcSpin), m = ic<T>(im, kcMass);
+        const bool flat = im.flat != 0;
+        for (int32_t base = 0; base < hd.nrec; base += 32) {
+            const int32_t idx = base + lane;
+            if (idx >= hd.nrec) break;
+            const int64_t k = record_index(chunks, wray, idx);
+            T cur[RecStride<double>::v];
+            load_record<double>(pool + k * RecStride<double>::v, cur);
+            const T xs[3] = {cur[0], cur[1], cur[2]};
+            KSGeom<T> G;
+            ks_geom<T>(xs[0], xs[1], xs[2], a, m, flat, false, G);
+            Plasma<T> P;
+            unsigned char flag = 0;
+            if (plasma_at<T, kSlow>(im, xs, cur[13], G, P)) {
+                const T kl[4] = {kt, cur[3], cur[4], cur[5]};
+                T ku[4];
+                raise4(G, kl, ku);
+                const T kdu = kl[0] * P.u[0] + kl[1] * P.u[1] + kl[2] * P.u[2] + kl[3] * P.u[3];
+                const T kdb = kl[0] * P.b[0] + kl[1] * P.b[1] + kl[2] * P.b[2] + kl[3] * P.b[3];
+                const T nu_fl = nu_norm * (-kdu);
+                T cth = fq(kdb, (-kdu) * fsqrt(P.bsq));
+                cth = cth > T(1) ? T(1) : (cth < T(-1) ? T(-1) : cth);
+                T co[8];
+                synchrotron_coefficients<T>(P.ne, P.th, P.bg, nu_fl, cth, co);
+                const T g = fq(ic<T>(im, kcFreq), nu_fl);
+                const T path = ic<T>(im, kcLen) * (-kdu);
+                const T eg = g * g * g * path;
+                T v[kPreVals] = {co[0] * eg, co[1] * eg, co[2] * eg, co[3] * path,
+                                 co[4] * path, co[5] * path, co[6] * path, co[7] * path};
+                fluid_basis<T>(G, P, kl, ku, v + 8, v + 12, v + 16, v + 20);
+                double2* out = reinterpret_cast<double2*>(pre + kPreVals * k);
+#pragma unroll
+                for (int i = 0; i < kPreVals / 2; ++i) out[i] = make_double2(v[2 * i], v[2 * i + 1]);
+                flag = 1;
+            }
+            pre_flag[k] = flag;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// FP64 form, second pass of the transfer: along each ray from the source end, the merged N
+// half-steps of the predictor-corrector (Table tab:pc) and, at every sample the first pass
+// found plasma at, the Stokes step with that pass's coefficients and basis; at the camera
+// node the read-out in the camera basis. The same operations in the same order as the single
+// kernel (transfer_body), with a smaller live state: only N and the two records of the
+// current half-steps, re-read from the pool instead of carried (FP64 registers are the
+// scarce resource; their spills were the kernel's main stall).
+// ---------------------------------------------------------------------------------------
+#ifndef BL_TRANSPORT64_MAXNREG
+#define BL_TRANSPORT64_MAXNREG 32
+#endif
+__global__ void __maxnreg__(BL_TRANSPORT64_MAXNREG) transport_fp64_kernel(
+        const ImageDesc* __restrict__ imgs, int n_images, int64_t ray_begin, int64_t ray_end,
+        const RayHdr* __restrict__ hdr, const double* __restrict__ pool,
+        const int32_t* __restrict__ chunks, Counters* ctr, BlockSource bs, SideIn side) {
+    using T = double;
+    const int64_t re = wave_end(bs, ray_end);
+    const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
+    int64_t wray = 0, ray = 0, opix = 0;
+    bool active = false, started = false;
+    int q = 0, pi = 0, pj = 0;
+    int32_t idx = 0;
+    Coh<T> N;
+    T kt = T(0), a = T(0), m = T(0);
+    bool flat = false;
+    bool exhausted = false;
+    while (true) {
+        const bool need = !active && !exhausted;
+        const unsigned long long got = warp_refill(&ctr->next_ray_tr, need);
+        if (need) {
+            if ((int64_t)got >= total_rays) exhausted = true;
+            else { wray = (int64_t)got; ray = ray_begin + wray; }
+        }
+        if (!__any_sync(0xffffffffu, active || (need && !exhausted))) break;
+        if (!active && !(need && !exhausted)) continue;
+        if (!active) {
+            setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
+            const ImageDesc& im = imgs[q];
+            const RayHdr hd = hdr[wray];
+            if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) {
+                const int64_t npix = im.n_rays;
+                const double val = hd.status == BL_RAY_OVERFLOW ? nan("") : 0.0;
+                for (int s = 0; s < 4; ++s) ((double*)im.stokes)[s * npix + opix] = val;
+                continue;
+            }
+            idx = hd.nrec - 1;
+            kt = hd.kt;
+            a = ic<T>(im, kcSpin);
+            m = ic<T>(im, kcMass);
+            flat = im.flat != 0;
+#pragma unroll
+            for (int c = 0; c < 10; ++c) N.re[c] = T(0);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) N.im[c] = T(0);
+            started = false;
+            active = true;
+        }
+        const ImageDesc& im = imgs[q];
+        const bool finishing = idx < 0;
+        // this sample's segment length (none on the finishing half-step to the camera node)
+        T dl_cur = T(0);
+        int64_t cur_k = 0;
+        if (!finishing) {
+            cur_k = record_index(chunks, wray, idx);
+            dl_cur = __ldg(pool + cur_k * RecStride<double>::v + 12);
+        }
+        if (started || finishing) {
+            // the previous sample's record: its point and node carry the two half-steps
+            const double* pr = pool + record_index(chunks, wray, idx + 1) * RecStride<double>::v;
+            if (started) {
+                const T h = T(0.5) * (__ldg(pr + 12) + dl_cur);
+                T A[4][4];
+                Coh<T> nh;
+                {
+                    const T x0[3] = {__ldg(pr), __ldg(pr + 1), __ldg(pr + 2)};
+                    const T k0[4] = {kt, __ldg(pr + 3), __ldg(pr + 4), __ldg(pr + 5)};
+                    transport_matrix<T>(x0, k0, a, m, flat, A);
+                }
+                coh_axpy(N, N, A, T(0.5) * h, nh);
+                {
+                    const T x1[3] = {__ldg(pr + 6), __ldg(pr + 7), __ldg(pr + 8)};
+                    const T k1[4] = {kt, __ldg(pr + 9), __ldg(pr + 10), __ldg(pr + 11)};
+                    transport_matrix<T>(x1, k1, a, m, flat, A);
+                }
+                Coh<T> out;
+                coh_axpy(N, nh, A, h, out);
+                N = out;
+            }
+            if (finishing) {
+                // read out in the camera basis at the camera-side node of the last record
+                KSGeom<T> G;
+                ks_geom<T>(__ldg(pr + 6), __ldg(pr + 7), __ldg(pr + 8), a, m, flat, false, G);
+                T hl[4], vl[4];
+                lower4(G, im.hh, hl);
+                lower4(G, im.vv, vl);
+                T sv[4];
+                coh_to_stokes(N, hl, vl, sv);
+                const int64_t npix = im.n_rays;
+                for (int c = 0; c < 4; ++c) ((double*)im.stokes)[c * npix + opix] = sv[c];
+                active = false;
+                continue;
+            }
+        }
+        if (side.pre_flag[cur_k]) {
+            const double2* pq = reinterpret_cast<const double2*>(side.pre + kPreVals * cur_k);
+            T v[kPreVals];
+#pragma unroll
+            for (int i = 0; i < kPreVals / 2; ++i) {
+                const double2 d = __ldg(pq + i);
+                v[2 * i] = d.x;
+                v[2 * i + 1] = d.y;
+            }
+            T s0[4], s1[4];
+            coh_to_stokes(N, v + 16, v + 20, s0);
+            stokes_step<T>(v, s0, dl_cur, s1);
+            stokes_to_coh(v + 8, v + 12, s1, N);
+            started = true;
+        }
+        --idx;
+    }
 }
 
 // ---------------------------------------------------------------------------------------
