@@ -306,9 +306,10 @@ bool set_interleave(std::vector<bl::ImageDesc>& d, int shift = bl::kIlvShift) {
     return eq;
 }
 
-// Dynamic shared memory of a geodesic-kernel CTA: the stage derivatives, 7 stages x 7
-// components (k_t's are zero) of 8 bytes for each of its 128 threads.
-constexpr size_t kGeoSmem = BL_GEO_K_SMEM ? (size_t)7 * 7 * 128 * 8 : 0;
+// Dynamic shared memory of a mixed- or double-float-form geodesic CTA: the stage derivatives,
+// 7 stages x 7 components (k_t's are zero) of 8 bytes for each of its 128 threads. The FP64
+// form keeps them in local memory and takes no dynamic shared memory.
+constexpr size_t kGeoSmem = (size_t)7 * 7 * 128 * 8;
 
 struct DevInfo {
     int sms = 0;
@@ -365,15 +366,12 @@ int dev_info(DevInfo& out) {
     DevInfo& di = cache[dev];
     if (di.sms == 0) {
         BL_CUDA(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev));
-        if (kGeoSmem > 0) {   // the stage derivatives exceed the default 48 KB of shared memory
-            BL_CUDA(cudaFuncSetAttribute(bl::geodesic_kernel_fp64,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGeoSmem));
-            BL_CUDA(cudaFuncSetAttribute(bl::geodesic_kernel<float, double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGeoSmem));
-            BL_CUDA(cudaFuncSetAttribute(bl::geodesic_kernel<float, bl::df64>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGeoSmem));
-        }
-        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[0], bl::geodesic_kernel_fp64, 128, kGeoSmem));
+        // the stage derivatives exceed the default 48 KB of shared memory
+        BL_CUDA(cudaFuncSetAttribute(bl::geodesic_kernel<float, double>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGeoSmem));
+        BL_CUDA(cudaFuncSetAttribute(bl::geodesic_kernel<float, bl::df64>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGeoSmem));
+        BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[0], bl::geodesic_kernel_fp64, 128, 0));
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[1], bl::geodesic_kernel<float, double>, 128, kGeoSmem));
         BL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&di.geo_blocks[2], bl::geodesic_kernel<float, bl::df64>, 128, kGeoSmem));
         for (int i = 0; i < 3; ++i)
@@ -521,7 +519,7 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
             }
             if (precision == BL_PREC_FP64) {
                 bl::RecordSink<double> sink{(double*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};
-                bl::geodesic_kernel_fp64<<<geo_grid, 128, kGeoSmem, st>>>(
+                bl::geodesic_kernel_fp64<<<geo_grid, 128, 0, st>>>(
                     d_desc, n_images, b, e, hdr, sink, record, cfg.bs, init);
             } else {
                 bl::RecordSink<float> sink{(float*)(ws + L.pool), chunks, (unsigned long long)L.pool_chunks, ctr};

@@ -589,10 +589,18 @@ __device__ __forceinline__ bool append_record(const RecordSink<R>& S, int64_t ra
 #ifndef BL_GEO_MIN_CTAS
 #define BL_GEO_MIN_CTAS 3
 #endif
-// Stage derivatives of the geodesic kernel in dynamic shared memory (1) or a local array (0).
-#ifndef BL_GEO_K_SMEM
-#define BL_GEO_K_SMEM 1
-#endif
+// Stage derivatives of a geodesic kernel: in dynamic shared memory, thread-fastest (the
+// double-float and mixed forms), or a per-thread local array (the FP64 form, whose high
+// occupancy leaves no shared memory for them).
+template <class G, bool kSmem> struct KStore;
+template <class G> struct KStore<G, true> {
+    G* p;
+    __device__ __forceinline__ G& at(int j, int s) { return p[(j * 7 + s) * 128]; }
+};
+template <class G> struct KStore<G, false> {
+    G k[7][7];
+    __device__ __forceinline__ G& at(int j, int s) { return k[j][s]; }
+};
 // Records of a subdivided step from the FP32 quartic about the step's start (coefficients
 // y0, d0 = h f0, c2, c3, c4 per component): nsub samples at the centres of equal parts.
 template <class R>
@@ -634,7 +642,7 @@ __device__ __forceinline__ double inv_fifth_root(double e) {
     return y;
 }
 
-template <class R, class G>
+template <class R, class G, bool kKsmem>
 __device__ __forceinline__ void geodesic_body(const ImageDesc* __restrict__ imgs,
                                               int n_images, int64_t ray_begin, int64_t ray_end,
                                               RayHdr* __restrict__ hdr, RecordSink<R> sink,
@@ -701,14 +709,12 @@ __device__ __forceinline__ void geodesic_body(const ImageDesc* __restrict__ imgs
     // The k_t component is constant along the ray (dk_t/dl = 0), so its derivatives are not
     // stored: 7 slots a stage, and KR(j, 4) reads as an exact zero.
 #define KSLOT(c) ((c) < 4 ? (c) : (c) - 1)
-#if BL_GEO_K_SMEM
-    extern __shared__ __align__(16) unsigned char geo_smem[];
-    G* const Kt = reinterpret_cast<G*>(geo_smem) + threadIdx.x;
-#define KX(j, c) Kt[((j) * 7 + KSLOT(c)) * 128]
-#else
-    G Kl[7][7];
-#define KX(j, c) Kl[j][KSLOT(c)]
-#endif
+    KStore<G, kKsmem> Ks;
+    if constexpr (kKsmem) {
+        extern __shared__ __align__(16) unsigned char geo_smem[];
+        Ks.p = reinterpret_cast<G*>(geo_smem) + threadIdx.x;
+    }
+#define KX(j, c) Ks.at(j, KSLOT(c))
 #define KR(j, c) ((c) == 4 ? G(0) : KX(j, c))
     G h = G(0);
     double nnorm = 0.0;
@@ -1105,19 +1111,24 @@ __global__ void __launch_bounds__(128, BL_GEO_MIN_CTAS) geodesic_kernel(const Im
                                                           RecordSink<R> sink, int record,
                                                           BlockSource bs,
                                                           const RayInit* __restrict__ init) {
-    geodesic_body<R, G>(imgs, n_images, ray_begin, ray_end, hdr, sink, record, bs, init);
+    geodesic_body<R, G, true>(imgs, n_images, ray_begin, ray_end, hdr, sink, record, bs, init);
 }
 
-// Resident CTAs per SM the FP64-form geodesic kernel is compiled for.
+// Resident CTAs per SM the FP64-form geodesic kernel is compiled for: 16 (32 registers, the
+// SM's 64 warps; stage derivatives in local memory) measured 189.7 ms on the 9 x 256^2 step,
+// against 199.6 ms at 3 CTAs with them in shared memory (4: 203.9; in local memory 4: 201.7,
+// 6: 202.7, 8: 207.6). The mixed form (FP32 records, whose midpoints are formed in FP32)
+// stays in the shared-memory kernel at 3 CTAs: 148.8 ms there against 160.5 ms in this one.
 #ifndef BL_GEO64_MIN_CTAS
-#define BL_GEO64_MIN_CTAS 3
+#define BL_GEO64_MIN_CTAS 16
 #endif
 // The FP64 form (FP64 state, FP64 records) with its own register budget.
 __global__ void __launch_bounds__(128, BL_GEO64_MIN_CTAS) geodesic_kernel_fp64(
         const ImageDesc* __restrict__ imgs, int n_images, int64_t ray_begin, int64_t ray_end,
         RayHdr* __restrict__ hdr, RecordSink<double> sink, int record, BlockSource bs,
         const RayInit* __restrict__ init) {
-    geodesic_body<double, double>(imgs, n_images, ray_begin, ray_end, hdr, sink, record, bs, init);
+    geodesic_body<double, double, false>(imgs, n_images, ray_begin, ray_end, hdr, sink, record, bs,
+                                         init);
 }
 
 // Per-image constant in the transfer arithmetic.
