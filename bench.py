@@ -365,7 +365,7 @@ def form_rooflines(prec_name, attempts, samples, geo_s, tr_s, peaks):
 
 
 def _hist(v):
-    """Percentiles of a per-ray count (the survey's steps/samples-per-ray histograms)."""
+    """Percentiles of a per-ray count (DP attempts or sample records per ray)."""
     import numpy as np
     v = np.asarray(v, dtype=np.float64).reshape(-1)
     if v.size == 0:
