@@ -197,7 +197,14 @@ enum { BL_ASYNC = 1u, BL_TIMING = 2u, BL_UNPOLARIZED = 8u };
  * buffer, 256-byte aligned, the call uses instead: blacklight_workspace_size() bytes give the
  * default waves; a
  * smaller buffer is accepted and runs smaller waves (BL_EINVAL if it cannot hold one ray).
- * Results do not depend on the wave size. */
+ * Results do not depend on the wave size.
+ * Ray order (scheduling only; results do not depend on it): a DP batch of at least 65536 rays
+ * whose images all have n a multiple of 8 is queued as 8x8 pixel blocks, longest predicted
+ * work first. The prediction is the DP attempt count of each block's centre ray, integrated
+ * beforehand with the double-float geodesic kernel (1/64 of the rays, no transfer, at most 512
+ * attempts a ray; in BL_PREC_FAST with both tolerances 1000 times larger, capped at 1e-3;
+ * five extra launches). Other batches queue each image's rays in Morton order (n a power of
+ * two) or rows. */
 int blacklight_trace_batch(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
                            const bl_grid_t* grids, const double* freqs_hz, const bl_out_t* outs,
                            void* workspace, size_t workspace_bytes, void* stream,
@@ -279,7 +286,10 @@ int blacklight_geodesics(const bl_camera_t* cam, const bl_metric_t* met, const b
 typedef struct bl_plan bl_plan_t;
 typedef struct bl_launch_config {
     uint32_t size;
-    int32_t ray_order;        /* 0 Morton order within each image (n a power of two), 1 rows */
+    int32_t ray_order;        /* 0 Morton order within each image (n a power of two), 1 rows,
+                                 2 the work-ordered queue of 8x8 blocks described at
+                                 blacklight_trace_batch (the default where the batch allows it;
+                                 BL_EINVAL elsewhere) */
     int32_t geo_ctas_per_sm;  /* persistent geodesic CTAs per SM, 0 = occupancy limit */
     int32_t tr_ctas_per_sm;   /* persistent transfer CTAs per SM, 0 = occupancy limit */
     float run_ms;             /* autotuned plans: device time of one run with this configuration */
@@ -294,7 +304,8 @@ typedef struct bl_launch_config {
  * written while tuning). The choice is cached per device and workload shape for the life of
  * the process. */
 enum { BL_PLAN_AUTOTUNE = 4u };
-/* config: NULL = defaults (Morton, occupancy limits), ignored with BL_PLAN_AUTOTUNE. `stream`
+/* config: NULL = defaults (the work-ordered queue where the batch allows it, else Morton;
+ * occupancy limits), ignored with BL_PLAN_AUTOTUNE. `stream`
  * is used for the tuning runs and the capture (the legacy default stream is replaced by a
  * private stream for the capture). */
 int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,

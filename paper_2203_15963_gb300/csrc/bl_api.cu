@@ -56,11 +56,33 @@ constexpr int64_t kChunksPerRay = 16;
 constexpr int64_t kWaveRays = 1 << 20;
 
 struct Layout {
-    size_t counters, descs, hdr, init, chunks, pool, mlp_y, pre, pre_flag, total;
+    size_t counters, descs, hdr, init, chunks, pool, mlp_y, pre, pre_flag, pred, total;
     int64_t rays;          // rays of the whole call
     int64_t wave;          // rays per wave (the workspace holds one wave)
     int64_t pool_chunks;
+    int64_t pred_blocks;   // blocks of the work-ordered queue (0: the queue is not reordered)
 };
+
+// The work-ordered queue's scratch (after the layout's other regions): the predictor's
+// counters, image descriptors, 1 x 1 block list, attempt counts, ray headers and initial
+// states, the sorted block list and the two list lengths.
+struct PredOff {
+    size_t ctr, descs, list, cost, hdr, init, sorted, count, end;
+};
+PredOff pred_offsets(size_t base, int32_t n_images, int64_t nb) {
+    PredOff o{};
+    size_t off = base;
+    o.ctr = off;    off = align_up(off + sizeof(bl::Counters));
+    o.descs = off;  off = align_up(off + sizeof(bl::ImageDesc) * (size_t)n_images);
+    o.list = off;   off = align_up(off + 3 * sizeof(int32_t) * (size_t)nb);
+    o.cost = off;   off = align_up(off + sizeof(int32_t) * (size_t)nb);
+    o.hdr = off;    off = align_up(off + sizeof(bl::RayHdr) * (size_t)nb);
+    o.init = off;   off = align_up(off + sizeof(bl::RayInit) * (size_t)nb);
+    o.sorted = off; off = align_up(off + 3 * sizeof(int32_t) * (size_t)nb);
+    o.count = off;  off = align_up(off + 2 * sizeof(unsigned long long));
+    o.end = off;
+    return o;
+}
 
 // The FP64 transfer runs as two passes (fp64_samples_kernel, then the transport and Stokes
 // steps) when set; 0 keeps the single fused kernel.
@@ -72,9 +94,11 @@ constexpr bool kFp64Split = BL_TR64_SPLIT != 0;
 
 // mlp: room for the learned model's outputs, 8 floats for every record of the pool
 Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precision,
-                        bool transfer, int64_t cpr = kChunksPerRay, bool mlp = false) {
+                        bool transfer, int64_t cpr = kChunksPerRay, bool mlp = false,
+                        int64_t pred_blocks = 0) {
     Layout L{};
     L.rays = rays;
+    L.pred_blocks = pred_blocks;
     L.wave = wave;
     L.pool_chunks = transfer ? L.wave * cpr : 0;
     const size_t rec = precision != BL_PREC_FP64 ? sizeof(float) * bl::RecStride<float>::v
@@ -96,28 +120,30 @@ Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precis
         L.pre_flag = off;
         off = align_up(off + bl::kChunk * (size_t)L.pool_chunks);
     }
+    L.pred = off;
+    if (pred_blocks > 0) off = pred_offsets(off, n_images, pred_blocks).end;
     L.total = off;
     return L;
 }
 
 Layout make_layout_rays(int32_t n_images, int64_t rays, int precision, bool transfer = true,
-                        int64_t cpr = kChunksPerRay, bool mlp = false) {
+                        int64_t cpr = kChunksPerRay, bool mlp = false, int64_t pred_blocks = 0) {
     return make_layout_wave(n_images, rays, rays < kWaveRays ? rays : kWaveRays, precision,
-                            transfer, cpr, mlp);
+                            transfer, cpr, mlp, pred_blocks);
 }
 
 // The largest wave (>= 1 ray) whose layout fits in `bytes`; wave = 0 if none does.
 Layout fit_layout(int32_t n_images, int64_t rays, int precision, bool transfer, size_t bytes,
-                  int64_t cpr, bool mlp = false) {
-    Layout L = make_layout_rays(n_images, rays, precision, transfer, cpr, mlp);
+                  int64_t cpr, bool mlp = false, int64_t pred_blocks = 0) {
+    Layout L = make_layout_rays(n_images, rays, precision, transfer, cpr, mlp, pred_blocks);
     if (L.total <= bytes) return L;
     int64_t lo = 0, hi = L.wave;        // total(lo) fits (or lo = 0), total(hi) does not
     while (hi - lo > 1) {
         const int64_t mid = lo + (hi - lo) / 2;
-        if (make_layout_wave(n_images, rays, mid, precision, transfer, cpr, mlp).total <= bytes) lo = mid;
+        if (make_layout_wave(n_images, rays, mid, precision, transfer, cpr, mlp, pred_blocks).total <= bytes) lo = mid;
         else hi = mid;
     }
-    return make_layout_wave(n_images, rays, lo, precision, transfer, cpr, mlp);
+    return make_layout_wave(n_images, rays, lo, precision, transfer, cpr, mlp, pred_blocks);
 }
 
 int64_t count_rays(int32_t n_images, const bl_camera_t* cams) {
@@ -142,10 +168,24 @@ int64_t chunks_per_ray(int32_t n_images, const bl_camera_t* cams, const bl_metri
     return c < bl::kMaxChunks ? c : bl::kMaxChunks;
 }
 
+// Blocks of the work-ordered queue for a batch, or 0 where it is not used: DP integration
+// (the fixed-step integrators' work hardly varies), every image's n a multiple of the block
+// size, and at least kCostMinRays rays (below that the prediction's own latency, about that of
+// the longest predicted ray, is not repaid).
+constexpr int64_t kCostMinRays = 1 << 16;
+int64_t cost_blocks(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets) {
+    if (mets[0].integrator != BL_INT_DP) return 0;
+    for (int q = 0; q < n_images; ++q)
+        if (cams[q].n % bl::kCostBlock) return 0;
+    const int64_t rays = count_rays(n_images, cams);
+    return rays >= kCostMinRays ? rays / ((int64_t)bl::kCostBlock * bl::kCostBlock) : 0;
+}
+
 Layout make_layout(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* mets,
                    bool mlp = false) {
     return make_layout_rays(n_images, count_rays(n_images, cams), mets[0].precision, true,
-                            chunks_per_ray(n_images, cams, mets), mlp);
+                            chunks_per_ray(n_images, cams, mets), mlp,
+                            cost_blocks(n_images, cams, mets));
 }
 
 int check_camera(const bl_camera_t* c, int q) {
@@ -454,15 +494,16 @@ struct LaunchCfg {
     int feat = 0;           // transfer variant: bl::kFSlow | kFUnpol | kFAux
     int integrator = BL_INT_DP;
     bool keep_bad = false;  // leave the bad-ray count of earlier launches in place
-    bl::BlockSource bs{nullptr, nullptr, 0};   // rays from a device block list (adaptive)
+    bl::BlockSource bs{nullptr, nullptr, 0, 0};   // rays from a device block list (adaptive)
     cudaEvent_t gate = nullptr;   // the first transfer launch waits for it (grids still arriving)
+    bool cost_order = true;       // work-ordered queue where the layout has room for it
 };
 
 // The kernel sequence of one trace on prepared workspace whose image descriptors are already
 // on the device: counter reset, camera frames, then one geodesic + transfer pair per wave of
 // rays, in stream order (the part a plan captures in a CUDA graph).
 int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, bool transfer,
-                   cudaStream_t st, bool timing, const float* mlp, const LaunchCfg& cfg) {
+                   cudaStream_t st, bool timing, const float* mlp, const LaunchCfg& cfg_in) {
     DevInfo di;
     int rc = dev_info(di);
     if (rc) return rc;
@@ -479,11 +520,43 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
     bl::ImageDesc* d_desc = (bl::ImageDesc*)(ws + L.descs);
     bl::RayHdr* hdr = (bl::RayHdr*)(ws + L.hdr);
     int32_t* chunks = (int32_t*)(ws + L.chunks);
-    BL_CUDA(cudaMemsetAsync(ctr, 0, cfg.keep_bad ? offsetof(bl::Counters, bad_rays)
-                                                 : sizeof(bl::Counters), st));
+    BL_CUDA(cudaMemsetAsync(ctr, 0, cfg_in.keep_bad ? offsetof(bl::Counters, bad_rays)
+                                                    : sizeof(bl::Counters), st));
     bl::camera_frame_kernel<<<(n_images + 63) / 64, 64, 0, st>>>(d_desc, n_images);
     ++g_launches;
     BL_CUDA(cudaGetLastError());
+    LaunchCfg cfg = cfg_in;
+    if (L.pred_blocks > 0 && cfg.cost_order && !cfg.bs.entries) {
+        // work-ordered queue: list the blocks' centre rays, integrate them (double-float
+        // geodesics, attempt counts only), sort the blocks by their counts, longest first
+        const int64_t nb = L.pred_blocks;
+        const PredOff po = pred_offsets(L.pred, n_images, nb);
+        bl::Counters* pctr = (bl::Counters*)(ws + po.ctr);
+        bl::ImageDesc* pdesc = (bl::ImageDesc*)(ws + po.descs);
+        int32_t* plist = (int32_t*)(ws + po.list);
+        int32_t* pcost = (int32_t*)(ws + po.cost);
+        int32_t* psorted = (int32_t*)(ws + po.sorted);
+        unsigned long long* pcount = (unsigned long long*)(ws + po.count);
+        BL_CUDA(cudaMemsetAsync(pctr, 0, sizeof(bl::Counters), st));
+        const int64_t lb = (nb + 255) / 256, lcap = (int64_t)di.sms * 8;
+        bl::cost_list_kernel<<<(unsigned)(lb < lcap ? lb : lcap), 256, 0, st>>>(d_desc, n_images, nb,
+                                                                                plist, pcount);
+        bl::cost_descs_kernel<<<(n_images + 63) / 64, 64, 0, st>>>(
+            d_desc, pdesc, n_images, pcost, precision == BL_PREC_FAST ? BL_COST_TOL_SCALE : 1.0);
+        const bl::BlockSource pbs{plist, pcount, 1, 0};
+        bl::ray_init_kernel<<<(unsigned)(lb < lcap ? lb : lcap), 256, 0, st>>>(
+            pdesc, n_images, 0, nb, pbs, (bl::RayInit*)(ws + po.init));
+        // few rays: at most one CTA an SM, so each runs at its latency
+        const int64_t pg = (nb + 127) / 128, pcap = (int64_t)di.sms * di.geo_blocks[2];
+        bl::RecordSink<float> psink{nullptr, nullptr, 0ull, pctr};
+        bl::geodesic_kernel<float, bl::df64><<<(unsigned)(pg < pcap ? pg : pcap), 128, kGeoSmem, st>>>(
+            pdesc, n_images, 0, nb, (bl::RayHdr*)(ws + po.hdr), psink, 0, pbs,
+            (const bl::RayInit*)(ws + po.init));
+        bl::cost_sort_kernel<<<1, 1024, 0, st>>>(pcost, plist, nb, psorted, pcount + 1);
+        g_launches += 5;
+        BL_CUDA(cudaGetLastError());
+        cfg.bs = bl::BlockSource{psorted, pcount + 1, bl::kCostBlock, 1};
+    }
     const int pidx = precision;
     auto pick = [](int want, int occ) { return want > 0 && want < occ ? want : occ; };
     const unsigned geo_grid = (unsigned)(di.sms * pick(cfg.geo_ctas, di.geo_blocks[pidx]));
@@ -699,7 +772,8 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
     const int64_t cpr = chunks_per_ray(n_images, cams, mets);
     // learned coefficients (validated below) need room for the model's outputs
     const bool use_mlp = transfer && grids && grids[0].coef_mlp != nullptr;
-    Layout L = make_layout_rays(n_images, rays, precision, transfer, cpr, use_mlp);
+    const int64_t pb = cost_blocks(n_images, cams, mets);
+    Layout L = make_layout_rays(n_images, rays, precision, transfer, cpr, use_mlp, pb);
     std::vector<bl::ImageDesc> descs(n_images);
     int64_t off = 0;
     static const bl_grid_t kNoGrid = {sizeof(bl_grid_t), nullptr, 1, 1, 1, 1.0, 2.0, 4.0 / 3.0,
@@ -717,11 +791,11 @@ int trace_impl(int32_t n_images, const bl_camera_t* cams, const bl_metric_t* met
         if ((uintptr_t)ws % kAlign)
             return fail(BL_EINVAL, "workspace must be %zu-byte aligned", kAlign);
         // a workspace smaller than the default layout runs the rays in more, smaller waves
-        L = fit_layout(n_images, rays, precision, transfer, workspace_bytes, cpr, use_mlp);
+        L = fit_layout(n_images, rays, precision, transfer, workspace_bytes, cpr, use_mlp, pb);
         if (L.wave < 1)
             return fail(BL_EINVAL, "workspace too small: %zu < %zu bytes (one ray)",
                         workspace_bytes,
-                        make_layout_wave(n_images, rays, 1, precision, transfer, cpr, use_mlp).total);
+                        make_layout_wave(n_images, rays, 1, precision, transfer, cpr, use_mlp, pb).total);
         int rc = device_pointer(ws, "workspace");
         if (rc) return rc;
     } else {
@@ -798,8 +872,9 @@ struct bl_plan {
 
 namespace {
 
+// order 0: Morton within each image, 1: rows, 2: the work-ordered queue of 8 x 8 blocks
 int plan_set_order(bl_plan& P, int order, cudaStream_t st, int ilv_shift = -1) {
-    for (auto& d : P.descs) d.order = order;
+    for (auto& d : P.descs) d.order = order == 2 ? 0 : order;
     P.order = order;
     if (ilv_shift >= 0) {
         set_interleave(P.descs, ilv_shift);
@@ -823,6 +898,7 @@ int plan_time(bl_plan& P, const LaunchCfg& cfg, cudaStream_t st, float* ms) {
         LaunchCfg c = cfg;
         c.feat = P.feat;
         c.integrator = P.descs[0].integrator;
+        c.cost_order = P.order == 2;
         if (!rc) rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, c);
         if (!rc && it > 0) {
             if ((ce = cudaEventRecord(e1, st)) != cudaSuccess) rc = cuda_fail(ce, "record");
@@ -860,14 +936,19 @@ int plan_autotune(bl_plan& P, cudaStream_t st) {
     }
     float best = 0.0f, t = 0.0f;
     LaunchCfg cfg;
-    int order = 0;
+    // ray order: the work-ordered queue where the batch allows it, else Morton; then the others
+    int order = P.L.pred_blocks > 0 ? 2 : 0;
     int ilv_shift = bl::kIlvShift;
-    if ((rc = plan_set_order(P, 0, st, ilv_shift)) || (rc = plan_time(P, cfg, st, &best))) return rc;
-    if ((rc = plan_set_order(P, 1, st)) || (rc = plan_time(P, cfg, st, &t))) return rc;
-    if (t < best * (1.0f - kTuneMargin)) { best = t; order = 1; }
+    if ((rc = plan_set_order(P, order, st, ilv_shift)) || (rc = plan_time(P, cfg, st, &best))) return rc;
+    for (int o = 0; o < 2; ++o) {
+        if (o == order) continue;
+        if ((rc = plan_set_order(P, o, st)) || (rc = plan_time(P, cfg, st, &t))) return rc;
+        if (t < best * (1.0f - kTuneMargin)) { best = t; order = o; }
+    }
     if ((rc = plan_set_order(P, order, st))) return rc;
-    // interleave block of a batch of equal images: 64 to 4096 rays
-    if (P.descs[0].ilv > 1) {
+    // interleave block of a batch of equal images: 64 to 4096 rays (not used by the
+    // work-ordered queue)
+    if (P.descs[0].ilv > 1 && order != 2) {
         for (int sh = 6; sh <= 12; sh += 2) {
             if (sh == bl::kIlvShift) continue;
             std::vector<bl::ImageDesc> probe = P.descs;
@@ -928,6 +1009,7 @@ int plan_capture(bl_plan& P, cudaStream_t user) {
             LaunchCfg c = P.cfg;
             c.feat = P.feat;
             c.integrator = P.descs[0].integrator;
+            c.cost_order = P.order == 2;
             rc = launch_kernels(P.n_images, P.ws, P.L, P.precision, true, st, false, P.mlp, c);
         }
         cudaGraph_t g = nullptr;
@@ -1322,9 +1404,13 @@ int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_m
     if (rc) return rc;
     if (config && !(flags & BL_PLAN_AUTOTUNE)) {
         if (config->size != sizeof(bl_launch_config_t)) return fail(BL_EINVAL, "config.size mismatch");
-        if (config->ray_order < 0 || config->ray_order > 1 || config->geo_ctas_per_sm < 0 ||
+        if (config->ray_order < 0 || config->ray_order > 2 || config->geo_ctas_per_sm < 0 ||
             config->tr_ctas_per_sm < 0)
-            return fail(BL_EINVAL, "config: ray_order 0 or 1, CTAs per SM >= 0");
+            return fail(BL_EINVAL, "config: ray_order 0, 1 or 2, CTAs per SM >= 0");
+        if (config->ray_order == 2 && cost_blocks(n_images, cams, mets) == 0)
+            return fail(BL_EINVAL, "config.ray_order 2 needs DP integration, every n a multiple "
+                                   "of %d and at least %lld rays", bl::kCostBlock,
+                        (long long)kCostMinRays);
         const int b = config->ilv_block;
         if (b != 0 && (b < 64 || b > 4096 || (b & (b - 1)) != 0))
             return fail(BL_EINVAL, "config.ilv_block: 0 or a power of two in [64, 4096]");
@@ -1338,7 +1424,8 @@ int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_m
     P->precision = precision;
     P->mlp = mlp;
     P->L = make_layout_rays(n_images, count_rays(n_images, cams), precision, true,
-                            chunks_per_ray(n_images, cams, mets), mlp != nullptr);
+                            chunks_per_ray(n_images, cams, mets), mlp != nullptr,
+                            cost_blocks(n_images, cams, mets));
     P->descs.resize(n_images);
     int64_t off = 0;
     for (int q = 0; q < n_images; ++q) {
@@ -1367,7 +1454,7 @@ int blacklight_plan_create(int32_t n_images, const bl_camera_t* cams, const bl_m
                 while ((1 << sh) < config->ilv_block) ++sh;
             }
         }
-        rc = plan_set_order(*P, config ? config->ray_order : 0, st, sh);
+        rc = plan_set_order(*P, config ? config->ray_order : (P->L.pred_blocks > 0 ? 2 : 0), st, sh);
     }
     if (!rc) rc = plan_capture(*P, st);
     if (rc) {
@@ -1410,7 +1497,7 @@ int blacklight_plan_config(const bl_plan_t* plan, bl_launch_config_t* out) {
     out->geo_ctas_per_sm = plan->cfg.geo_ctas > 0 && plan->cfg.geo_ctas < geo_max ? plan->cfg.geo_ctas : geo_max;
     out->tr_ctas_per_sm = plan->cfg.tr_ctas > 0 && plan->cfg.tr_ctas < tr_max ? plan->cfg.tr_ctas : tr_max;
     out->run_ms = plan->run_ms;
-    out->ilv_block = plan->descs[0].ilv > 1 ? (1 << plan->descs[0].ilv_shift) : 0;
+    out->ilv_block = plan->descs[0].ilv > 1 && plan->order != 2 ? (1 << plan->descs[0].ilv_shift) : 0;
     return 0;
 }
 

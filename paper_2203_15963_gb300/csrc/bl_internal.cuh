@@ -101,6 +101,8 @@ struct BlockSource {
     const int32_t* entries;               // [blocks][3] or nullptr (image ranges)
     const unsigned long long* count;      // blocks in the list
     int32_t block;                        // B
+    int32_t pix_out;                      // 1: outputs at the pixel (cost-ordered queue of a
+                                          // whole-image trace); 0: at the ray's list index
 };
 
 // Side inputs of the transfer variants that split their per-sample work over passes: the
