@@ -56,7 +56,8 @@ constexpr int64_t kChunksPerRay = 16;
 constexpr int64_t kWaveRays = 1 << 20;
 
 struct Layout {
-    size_t counters, descs, hdr, init, chunks, pool, mlp_y, pre, pre_flag, pred, total;
+    size_t counters, descs, hdr, init, chunks, pool, mlp_y, pre, pre_flag, tkey, tperm, thist,
+        pred, total;
     int64_t rays;          // rays of the whole call
     int64_t wave;          // rays per wave (the workspace holds one wave)
     int64_t pool_chunks;
@@ -115,10 +116,16 @@ Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precis
     // FP64 form: the sample pass's coefficients and basis, and a flag byte, a pool record
     L.pre = off;
     L.pre_flag = off;
+    // and the transport pass's work order: each ray's work, the wave's rays longest first,
+    // the histogram of the counting sort
+    L.tkey = L.tperm = L.thist = off;
     if (precision == BL_PREC_FP64 && transfer && kFp64Split) {
         off = align_up(off + bl::kPreVals * sizeof(double) * bl::kChunk * (size_t)L.pool_chunks);
         L.pre_flag = off;
         off = align_up(off + bl::kChunk * (size_t)L.pool_chunks);
+        L.tkey = off;   off = align_up(off + sizeof(int32_t) * (size_t)L.wave);
+        L.tperm = off;  off = align_up(off + sizeof(int32_t) * (size_t)L.wave);
+        L.thist = off;  off = align_up(off + sizeof(unsigned int) * bl::kCostBuckets);
     }
     L.pred = off;
     if (pred_blocks > 0) off = pred_offsets(off, n_images, pred_blocks).end;
@@ -640,20 +647,32 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
                                               fpool, chunks, ctr, cfg.bs);
             } else if (kFp64Split && !(cfg.feat & (bl::kFUnpol | bl::kFAux))) {
                 // FP64 in two passes: the sample pass, then transport and Stokes steps
+                // then the transport pass takes the wave's rays longest first (a counting sort
+                // of the sample pass's work estimates)
                 double* pre = (double*)(ws + L.pre);
                 unsigned char* pflag = (unsigned char*)(ws + L.pre_flag);
+                int32_t* tkey = (int32_t*)(ws + L.tkey);
+                int32_t* tperm = (int32_t*)(ws + L.tperm);
+                unsigned int* thist = (unsigned int*)(ws + L.thist);
+                BL_CUDA(cudaMemsetAsync(thist, 0, sizeof(unsigned int) * bl::kCostBuckets, st));
                 const unsigned pre_grid = (unsigned)(di.sms * di.pre_occ[slow ? 1 : 0]);
                 if (slow)
                     bl::fp64_samples_kernel<true><<<pre_grid, 128, 0, st>>>(
-                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag);
+                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag, tkey,
+                        thist);
                 else
                     bl::fp64_samples_kernel<false><<<pre_grid, 128, 0, st>>>(
-                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag);
-                ++g_launches;
+                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag, tkey,
+                        thist);
+                bl::work_scan_kernel<<<1, 1024, 0, st>>>(thist);
+                const int64_t sb = (e - b + 255) / 256, scap = (int64_t)di.sms * 8;
+                bl::work_scatter_kernel<<<(unsigned)(sb < scap ? (sb > 0 ? sb : 1) : scap), 256, 0, st>>>(
+                    tkey, cfg.bs, b, e, thist, tperm);
+                g_launches += 3;
                 BL_CUDA(cudaGetLastError());
                 bl::transport_fp64_kernel<<<tr_grid, bl::kTransferFp64Threads, 0, st>>>(
                     d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs,
-                    bl::SideIn{nullptr, nullptr, pre, pflag});
+                    bl::SideIn{nullptr, nullptr, pre, pflag}, tperm);
             } else {
                 launch_transfer<double, double>(cfg.feat, tr_grid, st, d_desc, n_images, b, e,
                                                 hdr, dpool, chunks, ctr, cfg.bs);

@@ -369,26 +369,18 @@ __global__ void cost_descs_kernel(const ImageDesc* __restrict__ src, ImageDesc* 
     }
 }
 
-// One CTA of 1024 threads: counting sort of the blocks by predicted attempts, descending
-// (equal counts in any order), into the block list (image, bx, by) of the trace.
-__global__ void __launch_bounds__(1024) cost_sort_kernel(const int32_t* __restrict__ cost,
-                                                         const int32_t* __restrict__ list,
-                                                         int64_t n_blocks,
-                                                         int32_t* __restrict__ sorted,
-                                                         unsigned long long* __restrict__ count) {
-    constexpr int B = kCostBlock;
-    __shared__ unsigned int start[kCostBuckets];
+// Bucket of a cost in a descending counting sort (larger costs in lower buckets).
+__device__ __forceinline__ int cost_bucket(int32_t c) {
+    const int v = c < 0 ? 0 : (c > kCostBuckets - 1 ? kCostBuckets - 1 : c);
+    return kCostBuckets - 1 - v;
+}
+
+// In one CTA of 1024 threads: start[] (kCostBuckets counts, shared memory) becomes its
+// exclusive prefix sum; ends with a barrier.
+__device__ __forceinline__ void bucket_scan(unsigned int* start) {
     __shared__ unsigned int warp_sum[32];
     const int t = threadIdx.x;
-    auto bucket = [](int32_t c) {
-        const int v = c < 0 ? 0 : (c > kCostBuckets - 1 ? kCostBuckets - 1 : c);
-        return kCostBuckets - 1 - v;
-    };
-    for (int b = t; b < kCostBuckets; b += 1024) start[b] = 0u;
-    __syncthreads();
-    for (int64_t k = t; k < n_blocks; k += 1024) atomicAdd(&start[bucket(cost[k])], 1u);
-    __syncthreads();
-    // exclusive scan: each thread its 4 consecutive buckets, then across threads
+    // each thread its 4 consecutive buckets, then across threads
     constexpr int kPer = kCostBuckets / 1024;
     unsigned int v[kPer], sum = 0u;
 #pragma unroll
@@ -416,13 +408,63 @@ __global__ void __launch_bounds__(1024) cost_sort_kernel(const int32_t* __restri
 #pragma unroll
     for (int i = 0; i < kPer; ++i) { start[kPer * t + i] = run; run += v[i]; }
     __syncthreads();
+}
+
+// One CTA of 1024 threads: counting sort of the blocks by predicted attempts, descending
+// (equal counts in any order), into the block list (image, bx, by) of the trace.
+__global__ void __launch_bounds__(1024) cost_sort_kernel(const int32_t* __restrict__ cost,
+                                                         const int32_t* __restrict__ list,
+                                                         int64_t n_blocks,
+                                                         int32_t* __restrict__ sorted,
+                                                         unsigned long long* __restrict__ count) {
+    constexpr int B = kCostBlock;
+    __shared__ unsigned int start[kCostBuckets];
+    const int t = threadIdx.x;
+    for (int b = t; b < kCostBuckets; b += 1024) start[b] = 0u;
+    __syncthreads();
+    for (int64_t k = t; k < n_blocks; k += 1024) atomicAdd(&start[cost_bucket(cost[k])], 1u);
+    __syncthreads();
+    bucket_scan(start);
     for (int64_t k = t; k < n_blocks; k += 1024) {
-        const unsigned int pos = atomicAdd(&start[bucket(cost[k])], 1u);
+        const unsigned int pos = atomicAdd(&start[cost_bucket(cost[k])], 1u);
         sorted[3 * (int64_t)pos] = list[3 * k];
         sorted[3 * (int64_t)pos + 1] = list[3 * k + 1] / B;
         sorted[3 * (int64_t)pos + 2] = list[3 * k + 2] / B;
     }
     if (t == 0) *count = (unsigned long long)n_blocks;
+}
+
+// The FP64 transport pass's queue: the sample pass histograms each ray's transport work
+// (hist, global, kCostBuckets counts, zeroed per wave) and stores it in key[wray]; the scan
+// turns the histogram into bucket starts, and the scatter lists the wave's rays longest first
+// in perm (equal work in any order).
+__global__ void __launch_bounds__(1024) work_scan_kernel(unsigned int* __restrict__ hist) {
+    __shared__ unsigned int start[kCostBuckets];
+    for (int b = threadIdx.x; b < kCostBuckets; b += 1024) start[b] = hist[b];
+    __syncthreads();
+    bucket_scan(start);
+    for (int b = threadIdx.x; b < kCostBuckets; b += 1024) hist[b] = start[b];
+}
+// (the wave's rays as the sample pass counted them: a device block list may hold fewer than
+// the launch covers; lanes of a warp with equal buckets take their places with one atomic)
+__global__ void work_scatter_kernel(const int32_t* __restrict__ key, BlockSource bs,
+                                    int64_t ray_begin, int64_t ray_end,
+                                    unsigned int* __restrict__ start, int32_t* __restrict__ perm) {
+    const int64_t re = wave_end(bs, ray_end);
+    const int64_t n = re > ray_begin ? re - ray_begin : 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < n; w0 += stride) {
+        const int64_t w = w0 + threadIdx.x;
+        const bool on = w < n;
+        const int b = on ? cost_bucket(key[w]) : -1 - lane;   // idle lanes in buckets of their own
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(same) - 1;
+        unsigned int base = 0u;
+        if (on && lane == leader) base = atomicAdd(&start[b], (unsigned int)__popc(same));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (on) perm[base + __popc(same & ((1u << lane) - 1u))] = (int32_t)w;
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -2170,9 +2212,19 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
                                                            const int32_t* __restrict__ chunks,
                                                            Counters* ctr, BlockSource bs,
                                                            double* __restrict__ pre,
-                                                           unsigned char* __restrict__ pre_flag) {
+                                                           unsigned char* __restrict__ pre_flag,
+                                                           int32_t* __restrict__ tkey,
+                                                           unsigned int* __restrict__ thist) {
     using T = double;
     const int lane = threadIdx.x & 31;
+    // the transport pass's work for the ray: its steps from the farthest plasma sample to the
+    // camera, and half a step for each plasma sample's Stokes step
+    auto put_key = [&](int64_t wray, int32_t k) {
+        if (lane == 0 && tkey) {
+            tkey[wray] = k;
+            atomicAdd(&thist[cost_bucket(k)], 1u);
+        }
+    };
     const int64_t re = wave_end(bs, ray_end);
     const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
     while (true) {
@@ -2185,11 +2237,15 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
         int64_t opix;
         setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
         const RayHdr hd = hdr[wray];
-        if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) continue;
+        if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) {
+            put_key(wray, 0);
+            continue;
+        }
         const ImageDesc& im = imgs[q];
         const T kt = hd.kt, nu_norm = hd.nnorm * im.freq;
         const T a = ic<T>(im, kcSpin), m = ic<T>(im, kcMass);
         const bool flat = im.flat != 0;
+        int32_t hi = -1, npl = 0;
         for (int32_t base = 0; base < hd.nrec; base += 32) {
             const int32_t idx = base + lane;
             if (idx >= hd.nrec) break;
@@ -2222,9 +2278,17 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
 #pragma unroll
                 for (int i = 0; i < kPreVals / 2; ++i) out[i] = make_double2(v[2 * i], v[2 * i + 1]);
                 flag = 1;
+                hi = idx;
+                ++npl;
             }
             pre_flag[k] = flag;
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            npl += __shfl_xor_sync(0xffffffffu, npl, o);
+        }
+        put_key(wray, hi + 1 + (npl >> 1));
     }
 }
 
@@ -2243,7 +2307,8 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
 __global__ void __maxnreg__(BL_TRANSPORT64_MAXNREG) transport_fp64_kernel(
         const ImageDesc* __restrict__ imgs, int n_images, int64_t ray_begin, int64_t ray_end,
         const RayHdr* __restrict__ hdr, const double* __restrict__ pool,
-        const int32_t* __restrict__ chunks, Counters* ctr, BlockSource bs, SideIn side) {
+        const int32_t* __restrict__ chunks, Counters* ctr, BlockSource bs, SideIn side,
+        const int32_t* __restrict__ perm) {
     using T = double;
     const int64_t re = wave_end(bs, ray_end);
     const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
@@ -2260,7 +2325,11 @@ __global__ void __maxnreg__(BL_TRANSPORT64_MAXNREG) transport_fp64_kernel(
         const unsigned long long got = warp_refill(&ctr->next_ray_tr, need);
         if (need) {
             if ((int64_t)got >= total_rays) exhausted = true;
-            else { wray = (int64_t)got; ray = ray_begin + wray; }
+            else {
+                // the sample pass's work order (longest first) where there is one
+                wray = perm ? (int64_t)perm[got] : (int64_t)got;
+                ray = ray_begin + wray;
+            }
         }
         if (!__any_sync(0xffffffffu, active || (need && !exhausted))) break;
         if (!active && !(need && !exhausted)) continue;

@@ -59,8 +59,8 @@ def test_work_ordered_trace_equals_morton_plan(precision):
     assert native.blacklight_trace_batch(cams, mets, gps, prims, [FREQ] * 4, direct) == 0
     # camera frames, the prediction (block list, descriptors, initial states, centre-ray
     # geodesics, sort), then the wave: geodesics and transfer, and the rays' initial states in
-    # the fast form or the sample pass of the FP64 transfer
-    launches = 8 if precision == native.BL_PREC_MIXED else 9
+    # the fast form, or in the FP64 form the sample pass and the transport pass's work order
+    launches = {native.BL_PREC_FAST: 9, native.BL_PREC_MIXED: 8, native.BL_PREC_FP64: 11}[precision]
     assert native.blacklight_launch_count() == launches
     assert float(sum(o["stokes"][0].double().sum() for o in direct)) > 0.0
     morton = _outs(cams, dt)

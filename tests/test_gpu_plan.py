@@ -56,8 +56,9 @@ def test_plan_replay_equals_direct_batch(precision):
         plan.run()
         assert plan.check() == 0
         # camera frames + one wave: geodesics and transfer, and the rays' initial states in the
-        # fast form or the sample pass of the FP64 transfer
-        assert native.blacklight_launch_count() == 4
+        # fast form, or in the FP64 form the sample pass and the transport pass's work order
+        # (scan and scatter of a counting sort)
+        assert native.blacklight_launch_count() == (6 if precision == native.BL_PREC_FP64 else 4)
         _same(outs, direct)
     plan.close()
 
