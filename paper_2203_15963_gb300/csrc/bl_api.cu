@@ -56,8 +56,8 @@ constexpr int64_t kChunksPerRay = 16;
 constexpr int64_t kWaveRays = 1 << 20;
 
 struct Layout {
-    size_t counters, descs, hdr, init, chunks, pool, mlp_y, pre, pre_flag, tkey, tperm, thist,
-        pred, total;
+    size_t counters, descs, hdr, init, chunks, pool, mlp_y, pre, pre_flag, tkey, tperm, tfirst,
+        thist, pred, total;
     int64_t rays;          // rays of the whole call
     int64_t wave;          // rays per wave (the workspace holds one wave)
     int64_t pool_chunks;
@@ -117,14 +117,15 @@ Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precis
     L.pre = off;
     L.pre_flag = off;
     // and the transport pass's work order: each ray's work, the wave's rays longest first,
-    // the histogram of the counting sort
-    L.tkey = L.tperm = L.thist = off;
+    // each ray's first transported sample, the histogram of the counting sort
+    L.tkey = L.tperm = L.tfirst = L.thist = off;
     if (precision == BL_PREC_FP64 && transfer && kFp64Split) {
         off = align_up(off + bl::kPreVals * sizeof(double) * bl::kChunk * (size_t)L.pool_chunks);
         L.pre_flag = off;
         off = align_up(off + bl::kChunk * (size_t)L.pool_chunks);
         L.tkey = off;   off = align_up(off + sizeof(int32_t) * (size_t)L.wave);
         L.tperm = off;  off = align_up(off + sizeof(int32_t) * (size_t)L.wave);
+        L.tfirst = off; off = align_up(off + sizeof(int32_t) * (size_t)L.wave);
         L.thist = off;  off = align_up(off + sizeof(unsigned int) * bl::kCostBuckets);
     }
     L.pred = off;
@@ -653,17 +654,18 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
                 unsigned char* pflag = (unsigned char*)(ws + L.pre_flag);
                 int32_t* tkey = (int32_t*)(ws + L.tkey);
                 int32_t* tperm = (int32_t*)(ws + L.tperm);
+                int32_t* tfirst = (int32_t*)(ws + L.tfirst);
                 unsigned int* thist = (unsigned int*)(ws + L.thist);
                 BL_CUDA(cudaMemsetAsync(thist, 0, sizeof(unsigned int) * bl::kCostBuckets, st));
                 const unsigned pre_grid = (unsigned)(di.sms * di.pre_occ[slow ? 1 : 0]);
                 if (slow)
                     bl::fp64_samples_kernel<true><<<pre_grid, 128, 0, st>>>(
                         d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag, tkey,
-                        thist);
+                        thist, tfirst);
                 else
                     bl::fp64_samples_kernel<false><<<pre_grid, 128, 0, st>>>(
                         d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag, tkey,
-                        thist);
+                        thist, tfirst);
                 bl::work_scan_kernel<<<1, 1024, 0, st>>>(thist);
                 const int64_t sb = (e - b + 255) / 256, scap = (int64_t)di.sms * 8;
                 bl::work_scatter_kernel<<<(unsigned)(sb < scap ? (sb > 0 ? sb : 1) : scap), 256, 0, st>>>(
@@ -672,7 +674,7 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
                 BL_CUDA(cudaGetLastError());
                 bl::transport_fp64_kernel<<<tr_grid, bl::kTransferFp64Threads, 0, st>>>(
                     d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs,
-                    bl::SideIn{nullptr, nullptr, pre, pflag}, tperm);
+                    bl::SideIn{nullptr, nullptr, pre, pflag, tfirst}, tperm);
             } else {
                 launch_transfer<double, double>(cfg.feat, tr_grid, st, d_desc, n_images, b, e,
                                                 hdr, dpool, chunks, ctr, cfg.bs);

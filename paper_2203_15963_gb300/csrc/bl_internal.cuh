@@ -114,6 +114,7 @@ struct SideIn {
     const float* mlp_params;
     const double* pre;
     const unsigned char* pre_flag;
+    const int32_t* first;    // FP64 transport pass: each ray's farthest plasma sample, or -1
 };
 constexpr int kPreVals = 24;
 

@@ -2214,13 +2214,16 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
                                                            double* __restrict__ pre,
                                                            unsigned char* __restrict__ pre_flag,
                                                            int32_t* __restrict__ tkey,
-                                                           unsigned int* __restrict__ thist) {
+                                                           unsigned int* __restrict__ thist,
+                                                           int32_t* __restrict__ tfirst) {
     using T = double;
     const int lane = threadIdx.x & 31;
-    // the transport pass's work for the ray: its steps from the farthest plasma sample to the
-    // camera, and half a step for each plasma sample's Stokes step
-    auto put_key = [&](int64_t wray, int32_t k) {
+    // for the transport pass: the ray's farthest plasma sample (where its transport starts; -1:
+    // none), and its work: the steps from there to the camera and half a step for each plasma
+    // sample's Stokes step
+    auto put_key = [&](int64_t wray, int32_t first, int32_t k) {
         if (lane == 0 && tkey) {
+            tfirst[wray] = first;
             tkey[wray] = k;
             atomicAdd(&thist[cost_bucket(k)], 1u);
         }
@@ -2238,7 +2241,7 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
         setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
         const RayHdr hd = hdr[wray];
         if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) {
-            put_key(wray, 0);
+            put_key(wray, -1, 0);
             continue;
         }
         const ImageDesc& im = imgs[q];
@@ -2288,7 +2291,7 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
             hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
             npl += __shfl_xor_sync(0xffffffffu, npl, o);
         }
-        put_key(wray, hi + 1 + (npl >> 1));
+        put_key(wray, hi, hi + 1 + (npl >> 1));
     }
 }
 
@@ -2343,7 +2346,9 @@ __global__ void __maxnreg__(BL_TRANSPORT64_MAXNREG) transport_fp64_kernel(
                 for (int s = 0; s < 4; ++s) ((double*)im.stokes)[s * npix + opix] = val;
                 continue;
             }
-            idx = hd.nrec - 1;
+            // from the farthest plasma sample where the sample pass found it (the records
+            // beyond it leave N = 0 untouched); with none, straight to the read-out
+            idx = side.first ? side.first[wray] : hd.nrec - 1;
             kt = hd.kt;
             a = ic<T>(im, kcSpin);
             m = ic<T>(im, kcMass);
