@@ -70,18 +70,19 @@ KERNEL_HEADERS = ("bl_kernels.cuh", "bl_math.cuh", "bl_df64.cuh", "bl_internal.c
 # fp64_instr: thread-level DFMA + DMUL + DADD instructions per unit from the same capture,
 # which gives the FP64 pipe's issue rate beside the algorithmic roofline.
 DRAM_PER_UNIT = {
-    # FP64 form, 7,845,751 attempts: 0.067 GB read + 2.054 GB written (sample records)
-    "geodesic_fp64": {"src": "f95f226a6a661cfd", "bytes": 270.3, "unit": "attempt",
+    # FP64 form, 7,845,751 attempts: 0.663 GB read + 5.343 GB written (the FP64 records and the
+    # stage derivatives, held in local memory at 16 CTAs an SM)
+    "geodesic_fp64": {"src": "ce25265838878bb9", "bytes": 765.5, "unit": "attempt",
                       "fp64_instr": 1090.4},
-    # FP64 form, 18,372,204 samples, both transfer passes: fp64_samples_kernel 4.574 + 3.986
-    # GB (465.9 B a sample: records, grid gathers, 193 B of results written, spills) and
-    # transport_fp64_kernel 3.042 + 2.556 GB (304.7 B: records, those results, spills)
-    "transfer_fp64": {"src": "f95f226a6a661cfd", "bytes": 770.6, "unit": "sample",
-                      "fp64_instr": 670.8},
-    # fast form, 7,845,744 attempts: 0.025 GB read + 1.135 GB written
-    "geodesic_df64": {"src": "f95f226a6a661cfd", "bytes": 147.8, "unit": "attempt"},
-    # fast form, 18,372,183 samples: 1.390 GB read + 0.004 GB written
-    "transfer_fp32": {"src": "f95f226a6a661cfd", "bytes": 75.9, "unit": "sample"},
+    # FP64 form, 18,372,204 samples, both transfer passes: fp64_samples_kernel 4.926 + 4.472
+    # GB (records, grid gathers, 193 B of results a sample, spills) and transport_fp64_kernel
+    # 1.386 + 1.881 GB (records, those results, spills)
+    "transfer_fp64": {"src": "ce25265838878bb9", "bytes": 689.3, "unit": "sample",
+                      "fp64_instr": 671.0},
+    # fast form, 7,845,744 attempts: 0.024 GB read + 1.135 GB written
+    "geodesic_df64": {"src": "ce25265838878bb9", "bytes": 147.7, "unit": "attempt"},
+    # fast form, 18,372,183 samples: 1.391 GB read + 0.004 GB written
+    "transfer_fp32": {"src": "ce25265838878bb9", "bytes": 75.9, "unit": "sample"},
 }
 
 
