@@ -199,8 +199,8 @@ enum { BL_ASYNC = 1u, BL_TIMING = 2u, BL_UNPOLARIZED = 8u };
  * smaller buffer is accepted and runs smaller waves (BL_EINVAL if it cannot hold one ray).
  * Results do not depend on the wave size.
  * Ray order (scheduling only; results do not depend on it): a DP batch of at least 65536 rays
- * whose images all have n a multiple of 8 is queued as 8x8 pixel blocks, longest predicted
- * work first. The prediction is the DP attempt count of each block's centre ray, integrated
+ * whose images all have n a multiple of 8 and cell-layout grids is queued as 8x8 pixel blocks,
+ * longest predicted work first. The prediction is the DP attempt count of each block's centre ray, integrated
  * beforehand with the double-float geodesic kernel (1/64 of the rays, no transfer, at most 512
  * attempts a ray; in BL_PREC_FAST with both tolerances 1000 times larger, capped at 1e-3;
  * five extra launches). Other batches queue each image's rays in Morton order (n a power of

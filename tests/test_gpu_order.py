@@ -22,15 +22,19 @@ def _lib():
     assert torch.cuda.is_available()
 
 
-def _batch(precision, n=128):
-    """Four 128x128 images (65536 rays: the smallest batch the queue is reordered for)."""
+def _batch(precision, n=128, cells=True):
+    """Four 128x128 images (65536 rays: the smallest batch the queue is reordered for), grids
+    in the cell layout (the plane layout keeps the consecutive queue)."""
     cams, mets, gps, prims = [], [], [], []
     for spin, inc in ((0.94, 17.0), (0.5, 60.0), (0.0, 90.0), (0.94, 60.0)):
         cam, met, gp, prim = S.workload_inputs("torus64_cam32", spin, inc, n=n)
+        p = torch.from_numpy(prim).to(DEV)
+        if cells:
+            p, gp = images.pack_grid(p, gp)
         cams.append(cam)
         mets.append(S.Metric(**{**met.__dict__, "precision": precision}))
         gps.append(gp)
-        prims.append(torch.from_numpy(prim).to(DEV))
+        prims.append(p)
     return cams, mets, gps, prims
 
 
@@ -112,6 +116,17 @@ def test_geodesics_only_path_matches_traced_end_states():
 
 
 def test_work_order_needs_an_eligible_batch():
+    # the same four images on plane-layout grids: Morton by default, order 2 refused
+    cams, mets, gps, prims = _batch(native.BL_PREC_FAST, cells=False)
+    outs = _outs(cams, torch.float32)
+    plan = native.Plan(cams, mets, gps, prims, [FREQ] * 4, outs)
+    assert plan.config()["ray_order"] == 0
+    plan.close()
+    with pytest.raises(native.BlacklightError):
+        native.Plan(cams, mets, gps, prims, [FREQ] * 4, outs, config={"ray_order": 2})
+    native.blacklight_launch_count(reset=True)
+    assert native.blacklight_trace_batch(cams, mets, gps, prims, [FREQ] * 4, outs) == 0
+    assert native.blacklight_launch_count() == 4
     # three small images (fewer than 65536 rays): Morton by default, order 2 refused
     cams, mets, gps, prims = [], [], [], []
     for spin, inc in ((0.9, 17.0), (0.5, 60.0), (0.0, 90.0)):
