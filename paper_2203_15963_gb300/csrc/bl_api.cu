@@ -116,13 +116,15 @@ Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precis
     // FP64 form: the sample pass's coefficients and basis, and a flag byte, a pool record
     L.pre = off;
     L.pre_flag = off;
-    // and the transport pass's work order: each ray's work, the wave's rays longest first,
-    // each ray's first transported sample, the histogram of the counting sort
-    L.tkey = L.tperm = L.tfirst = L.thist = off;
     if (precision == BL_PREC_FP64 && transfer && kFp64Split) {
         off = align_up(off + bl::kPreVals * sizeof(double) * bl::kChunk * (size_t)L.pool_chunks);
         L.pre_flag = off;
         off = align_up(off + bl::kChunk * (size_t)L.pool_chunks);
+    }
+    // the transfer's ray order: each ray's work, the wave's rays longest first, each ray's
+    // first transported sample (FP64 transport pass), the histogram of the counting sort
+    L.tkey = L.tperm = L.tfirst = L.thist = off;
+    if (transfer) {
         L.tkey = off;   off = align_up(off + sizeof(int32_t) * (size_t)L.wave);
         L.tperm = off;  off = align_up(off + sizeof(int32_t) * (size_t)L.wave);
         L.tfirst = off; off = align_up(off + sizeof(int32_t) * (size_t)L.wave);
@@ -468,7 +470,7 @@ template <class T, class R>
 void launch_transfer(int feat, unsigned grid, cudaStream_t st, const bl::ImageDesc* d, int n,
                      int64_t b, int64_t e, const bl::RayHdr* hdr, const R* pool,
                      const int32_t* chunks, bl::Counters* ctr, bl::BlockSource bs,
-                     bl::SideIn side = bl::SideIn{nullptr, nullptr, nullptr, nullptr}) {
+                     bl::SideIn side = bl::SideIn{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}) {
     if constexpr (std::is_same<T, double>::value) {
         constexpr int th = bl::kTransferFp64Threads;
         switch (feat & 7) {
@@ -628,6 +630,22 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
             if (w == 0 && cfg.gate) BL_CUDA(cudaStreamWaitEvent(st, cfg.gate, 0));
             const float* fpool = (const float*)(ws + L.pool);
             const double* dpool = (const double*)(ws + L.pool);
+            int32_t* tkey = (int32_t*)(ws + L.tkey);
+            int32_t* tperm = (int32_t*)(ws + L.tperm);
+            unsigned int* thist = (unsigned int*)(ws + L.thist);
+            const int64_t sb = (e - b + 255) / 256, scap = (int64_t)di.sms * 8;
+            const unsigned sgrid = (unsigned)(sb < scap ? (sb > 0 ? sb : 1) : scap);
+            // the fused transfer's ray order: by the records each ray's transfer processes,
+            // longest first (a counting sort)
+            auto order_by_records = [&]() -> int {
+                BL_CUDA(cudaMemsetAsync(thist, 0, sizeof(unsigned int) * bl::kCostBuckets, st));
+                bl::record_key_kernel<<<sgrid, 256, 0, st>>>(hdr, cfg.bs, b, e, tkey, thist);
+                bl::work_scan_kernel<<<1, 1024, 0, st>>>(thist);
+                bl::work_scatter_kernel<<<sgrid, 256, 0, st>>>(tkey, cfg.bs, b, e, thist, tperm);
+                g_launches += 3;
+                BL_CUDA(cudaGetLastError());
+                return 0;
+            };
             if (mlp) {
                 // learned coefficients in three passes: the model inputs of every record, the
                 // model over the record pool in full tensor-core tiles, then the transfer
@@ -648,22 +666,22 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
                     &ctr->mlp_timeouts);
                 ++g_launches;
                 BL_CUDA(cudaGetLastError());
+                if ((rc = order_by_records())) return rc;
                 launch_transfer<float, float>(cfg.feat | bl::kFMlp, tr_grid, st, d_desc, n_images, b,
                                               e, hdr, fpool, chunks, ctr, cfg.bs,
-                                              bl::SideIn{my, mlp, nullptr, nullptr});
+                                              bl::SideIn{my, mlp, nullptr, nullptr, nullptr, tperm});
             } else if (precision != BL_PREC_FP64) {
+                if ((rc = order_by_records())) return rc;
                 launch_transfer<float, float>(cfg.feat, tr_grid, st, d_desc, n_images, b, e, hdr,
-                                              fpool, chunks, ctr, cfg.bs);
+                                              fpool, chunks, ctr, cfg.bs,
+                                              bl::SideIn{nullptr, nullptr, nullptr, nullptr, nullptr, tperm});
             } else if (kFp64Split && !(cfg.feat & (bl::kFUnpol | bl::kFAux))) {
                 // FP64 in two passes: the sample pass, then transport and Stokes steps
                 // then the transport pass takes the wave's rays longest first (a counting sort
                 // of the sample pass's work estimates)
                 double* pre = (double*)(ws + L.pre);
                 unsigned char* pflag = (unsigned char*)(ws + L.pre_flag);
-                int32_t* tkey = (int32_t*)(ws + L.tkey);
-                int32_t* tperm = (int32_t*)(ws + L.tperm);
                 int32_t* tfirst = (int32_t*)(ws + L.tfirst);
-                unsigned int* thist = (unsigned int*)(ws + L.thist);
                 BL_CUDA(cudaMemsetAsync(thist, 0, sizeof(unsigned int) * bl::kCostBuckets, st));
                 const unsigned pre_grid = (unsigned)(di.sms * di.pre_occ[slow ? 1 : 0]);
                 if (slow)
@@ -675,17 +693,17 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
                         d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag, tkey,
                         thist, tfirst);
                 bl::work_scan_kernel<<<1, 1024, 0, st>>>(thist);
-                const int64_t sb = (e - b + 255) / 256, scap = (int64_t)di.sms * 8;
-                bl::work_scatter_kernel<<<(unsigned)(sb < scap ? (sb > 0 ? sb : 1) : scap), 256, 0, st>>>(
-                    tkey, cfg.bs, b, e, thist, tperm);
+                bl::work_scatter_kernel<<<sgrid, 256, 0, st>>>(tkey, cfg.bs, b, e, thist, tperm);
                 g_launches += 3;
                 BL_CUDA(cudaGetLastError());
                 bl::transport_fp64_kernel<<<tr_grid, bl::kTransferFp64Threads, 0, st>>>(
                     d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs,
                     bl::SideIn{nullptr, nullptr, pre, pflag, tfirst}, tperm);
             } else {
+                if ((rc = order_by_records())) return rc;
                 launch_transfer<double, double>(cfg.feat, tr_grid, st, d_desc, n_images, b, e,
-                                                hdr, dpool, chunks, ctr, cfg.bs);
+                                                hdr, dpool, chunks, ctr, cfg.bs,
+                                                bl::SideIn{nullptr, nullptr, nullptr, nullptr, nullptr, tperm});
             }
             ++g_launches;
             BL_CUDA(cudaGetLastError());

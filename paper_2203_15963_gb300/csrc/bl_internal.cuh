@@ -84,6 +84,8 @@ struct RayHdr {
     double nnorm;    // frequency normalisation n per unit nu (Sec. 2.1)
     int32_t nrec;    // samples recorded
     int32_t status;  // BL_RAY_*
+    int32_t last_in; // last record of a step that came within 1.001 r_max of the hole (-1:
+                     // none); the records beyond it lie outside the grid and carry no plasma
 };
 
 // Initial state of a ray (Sec. 2.1, camera pixel): y = (x^a, k_a) and the frequency
@@ -115,6 +117,7 @@ struct SideIn {
     const double* pre;
     const unsigned char* pre_flag;
     const int32_t* first;    // FP64 transport pass: each ray's farthest plasma sample, or -1
+    const int32_t* perm;     // the transfer's ray order (wave ray indices), or nullptr
 };
 constexpr int kPreVals = 24;
 

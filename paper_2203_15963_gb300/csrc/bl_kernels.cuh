@@ -893,6 +893,7 @@ __device__ __forceinline__ void geodesic_body(const ImageDesc* __restrict__ imgs
     double r_cur = 0.0;     // r at y
     bool want_aux = false;  // auxiliary images: proper length and affine parameter
     double aux_len = 0.0, aux_lam = 0.0;
+    int32_t last_in = -1;   // last record of a step reaching within 1.001 r_max
 
     bool exhausted = false;
     // All 32 lanes stay in the loop until the whole warp is out of work, so the warp
@@ -1196,6 +1197,7 @@ __device__ __forceinline__ void geodesic_body(const ImageDesc* __restrict__ imgs
                     }
                 }
                 if (!ok) { status = BL_RAY_OVERFLOW; done = true; }
+                else if (kNative && rmin <= r_grid * 1.001) last_in = nrec - 1;
             }
 #pragma unroll
             for (int c = 0; c < 8; ++c) { y[c] = y5[c]; if (c != 4) KX(0, c) = KX(6, c); }
@@ -1253,6 +1255,9 @@ __device__ __forceinline__ void geodesic_body(const ImageDesc* __restrict__ imgs
             hd.nnorm = nnorm;
             hd.nrec = nrec;
             hd.status = status;
+            // (the double-float kernel, issue bound at its register limit, does not track it:
+            // 27.3 -> 29.9 ms when it did; its rays start from the far end)
+            hd.last_in = kNative ? last_in : nrec - 1;
             hdr[wray] = hd;
             if (status != BL_RAY_HORIZON && status != BL_RAY_ESCAPED)
                 atomicAdd(&ctr->bad_rays, 1ull);
@@ -1260,6 +1265,7 @@ __device__ __forceinline__ void geodesic_body(const ImageDesc* __restrict__ imgs
             attempts = 0;
             nrec = 0;
             status = 0;
+            last_in = -1;
         }
     }
 }
@@ -1467,6 +1473,7 @@ __global__ void __launch_bounds__(128, 3) geodesic_rk_kernel(const ImageDesc* __
             hd.nnorm = nnorm;
             hd.nrec = nrec;
             hd.status = status;
+            hd.last_in = nrec - 1;   // (fixed-step integrators: no skip)
             hdr[wray] = hd;
             if (status != BL_RAY_HORIZON && status != BL_RAY_ESCAPED)
                 atomicAdd(&ctr->bad_rays, 1ull);
@@ -1943,6 +1950,41 @@ __device__ __forceinline__ void aux_finish(const ImageDesc& im, int64_t pix, con
     }
 }
 
+// The record a ray's transfer starts from: the far-side records beyond its last step that
+// came within 1.001 r_max of the hole lie outside the grid's shell (their sample radius
+// exceeds r_max by far more than its FP32 rounding), carry no plasma and leave the coherency
+// zero, so the transfer starts at that step's last record (record 0 where no step did, for
+// the read-out at its node).
+__device__ __forceinline__ int32_t transfer_start(const RayHdr& hd) {
+    const int32_t last = hd.nrec - 1;
+    return hd.last_in < last ? (hd.last_in > 0 ? hd.last_in : 0) : last;
+}
+
+// The fused transfer's ray order: each wave ray's records to process (0 for rays without a
+// transfer) into key[] and the histogram of the counting sort (lanes of a warp with equal
+// buckets add with one atomic); work_scan_kernel and work_scatter_kernel finish the order.
+__global__ void record_key_kernel(const RayHdr* __restrict__ hdr, BlockSource bs,
+                                  int64_t ray_begin, int64_t ray_end, int32_t* __restrict__ key,
+                                  unsigned int* __restrict__ hist) {
+    const int64_t re = wave_end(bs, ray_end);
+    const int64_t n = re > ray_begin ? re - ray_begin : 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < n; w0 += stride) {
+        const int64_t w = w0 + threadIdx.x;
+        const bool on = w < n;
+        int b = -1 - lane;
+        if (on) {
+            const RayHdr hd = hdr[w];
+            const int32_t k = (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) ? 0 : transfer_start(hd) + 1;
+            key[w] = k;
+            b = cost_bucket(k);
+        }
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        if (on && lane == __ffs(same) - 1) atomicAdd(&hist[b], (unsigned int)__popc(same));
+    }
+}
+
 template <class T, class R, int kF>
 __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs,
                                               int n_images, int64_t ray_begin, int64_t ray_end,
@@ -1983,7 +2025,11 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
         const unsigned long long got = warp_refill(&ctr->next_ray_tr, need);
         if (need) {
             if ((int64_t)got >= total_rays) exhausted = true;
-            else { wray = (int64_t)got; ray = ray_begin + wray; }
+            else {
+                // the wave's rays in the order of their record counts where there is one
+                wray = side.perm ? (int64_t)side.perm[got] : (int64_t)got;
+                ray = ray_begin + wray;
+            }
         }
         if (!__any_sync(0xffffffffu, active || (need && !exhausted))) break;
         if (!active && !(need && !exhausted)) continue;
@@ -2008,7 +2054,7 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
                 }
                 continue;
             }
-            idx = hd.nrec - 1;
+            idx = transfer_start(hd);
             load_record<R>(record_ptr(pool, chunks, wray, idx), nxt);
             if constexpr (kIdx) nxt_k = record_index(chunks, wray, idx);
             kt = (T)hd.kt;
@@ -2249,9 +2295,11 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
         const T a = ic<T>(im, kcSpin), m = ic<T>(im, kcMass);
         const bool flat = im.flat != 0;
         int32_t hi = -1, npl = 0;
-        for (int32_t base = 0; base < hd.nrec; base += 32) {
+        // records beyond the last one near the grid carry no plasma (transfer_start)
+        const int32_t nrec = hd.last_in + 1 < hd.nrec ? hd.last_in + 1 : hd.nrec;
+        for (int32_t base = 0; base < nrec; base += 32) {
             const int32_t idx = base + lane;
-            if (idx >= hd.nrec) break;
+            if (idx >= nrec) break;
             const int64_t k = record_index(chunks, wray, idx);
             T cur[RecStride<double>::v];
             load_record<double>(pool + k * RecStride<double>::v, cur);

@@ -62,9 +62,10 @@ def test_work_ordered_trace_equals_morton_plan(precision):
     native.blacklight_launch_count(reset=True)
     assert native.blacklight_trace_batch(cams, mets, gps, prims, [FREQ] * 4, direct) == 0
     # camera frames, the prediction (block list, descriptors, initial states, centre-ray
-    # geodesics, sort), then the wave: geodesics and transfer, and the rays' initial states in
-    # the fast form, or in the FP64 form the sample pass and the transport pass's work order
-    launches = {native.BL_PREC_FAST: 9, native.BL_PREC_MIXED: 8, native.BL_PREC_FP64: 11}[precision]
+    # geodesics, sort), then the wave: geodesics, the transfer's ray order (key, scan, scatter;
+    # the FP64 sample pass makes the keys) and the transfer, and the rays' initial states in
+    # the fast form
+    launches = {native.BL_PREC_FAST: 12, native.BL_PREC_MIXED: 11, native.BL_PREC_FP64: 11}[precision]
     assert native.blacklight_launch_count() == launches
     assert float(sum(o["stokes"][0].double().sum() for o in direct)) > 0.0
     morton = _outs(cams, dt)
@@ -126,7 +127,7 @@ def test_work_order_needs_an_eligible_batch():
         native.Plan(cams, mets, gps, prims, [FREQ] * 4, outs, config={"ray_order": 2})
     native.blacklight_launch_count(reset=True)
     assert native.blacklight_trace_batch(cams, mets, gps, prims, [FREQ] * 4, outs) == 0
-    assert native.blacklight_launch_count() == 4
+    assert native.blacklight_launch_count() == 7
     # three small images (fewer than 65536 rays): Morton by default, order 2 refused
     cams, mets, gps, prims = [], [], [], []
     for spin, inc in ((0.9, 17.0), (0.5, 60.0), (0.0, 90.0)):
