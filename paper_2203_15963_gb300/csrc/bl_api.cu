@@ -682,19 +682,23 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
                 double* pre = (double*)(ws + L.pre);
                 unsigned char* pflag = (unsigned char*)(ws + L.pre_flag);
                 int32_t* tfirst = (int32_t*)(ws + L.tfirst);
+                // per wave ray: farthest plasma sample -1 and no plasma samples until found
+                BL_CUDA(cudaMemsetAsync(tfirst, 0xff, sizeof(int32_t) * (size_t)(e - b), st));
+                BL_CUDA(cudaMemsetAsync(tkey, 0, sizeof(int32_t) * (size_t)(e - b), st));
                 BL_CUDA(cudaMemsetAsync(thist, 0, sizeof(unsigned int) * bl::kCostBuckets, st));
                 const unsigned pre_grid = (unsigned)(di.sms * di.pre_occ[slow ? 1 : 0]);
                 if (slow)
                     bl::fp64_samples_kernel<true><<<pre_grid, 128, 0, st>>>(
-                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag, tkey,
-                        thist, tfirst);
+                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag,
+                        tfirst, tkey);
                 else
                     bl::fp64_samples_kernel<false><<<pre_grid, 128, 0, st>>>(
-                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag, tkey,
-                        thist, tfirst);
+                        d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag,
+                        tfirst, tkey);
+                bl::transport_key_kernel<<<sgrid, 256, 0, st>>>(tfirst, tkey, cfg.bs, b, e, thist);
                 bl::work_scan_kernel<<<1, 1024, 0, st>>>(thist);
                 bl::work_scatter_kernel<<<sgrid, 256, 0, st>>>(tkey, cfg.bs, b, e, thist, tperm);
-                g_launches += 3;
+                g_launches += 4;
                 BL_CUDA(cudaGetLastError());
                 bl::transport_fp64_kernel<<<tr_grid, bl::kTransferFp64Threads, 0, st>>>(
                     d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs,

@@ -2238,10 +2238,15 @@ __global__ void __maxnreg__(BL_TR64_MAXNREG) transfer_kernel_fp64(const ImageDes
 // FP64 form, first pass of the transfer: everything a sample needs that does not depend on
 // the ray's running coherency -- geometry, plasma state, the scaled synchrotron coefficients
 // and the fluid-frame basis -- for every record, written per record (kPreVals doubles and a
-// flag byte). One warp takes a ray, its lanes 32 consecutive records at a time: no
-// sequential dependency, so all lanes work and the FP64 latencies overlap. The arithmetic is
-// that of the transfer kernel's sample step, operation for operation. The second pass
-// (transport_fp64_kernel) runs the transport and the Stokes steps.
+// flag byte). The arithmetic is that of the transfer kernel's sample step, operation for
+// operation; the second pass (transport_fp64_kernel) runs the transport and the Stokes steps.
+// Work is compacted per warp: a warp takes rays in turn and tests its records 32 at a time
+// with a conservative FP32 test of the grid's radial shell (records outside get flag 0 at
+// once); the records that pass go to the warp's queue in shared memory, and whenever it holds
+// 32 the warp evaluates them with every lane busy, whatever rays they belong to (a warp per
+// ray left lanes idle on each ray's last 32 records and on records outside the grid: 26.2
+// of 32 lanes active). Each ray's farthest plasma sample and plasma-sample count are combined
+// with atomics (one per ray in a batch) for the transport pass's start and order.
 // ---------------------------------------------------------------------------------------
 // Resident CTAs an SM of the FP64 sample pass (16: 32 registers, the SM's 64 warps; measured
 // on the 9 x 256^2 step with the transport pass at 32 registers: 4 CTAs 326.3 ms for both
@@ -2249,6 +2254,15 @@ __global__ void __maxnreg__(BL_TR64_MAXNREG) transfer_kernel_fp64(const ImageDes
 #ifndef BL_PRE64_MIN_CTAS
 #define BL_PRE64_MIN_CTAS 16
 #endif
+struct SampleItem {
+    int64_t k;       // pool record
+    int32_t wray;    // ray within the wave
+    int32_t idx;     // record within the ray
+    int32_t q;       // image
+    int32_t pad_;
+};
+constexpr int kSampleQueue = 64;   // per warp: fewer than 32 waiting + one batch of 32 tests
+
 template <bool kSlow>
 __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(const ImageDesc* __restrict__ imgs,
                                                            int n_images, int64_t ray_begin,
@@ -2259,55 +2273,33 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
                                                            Counters* ctr, BlockSource bs,
                                                            double* __restrict__ pre,
                                                            unsigned char* __restrict__ pre_flag,
-                                                           int32_t* __restrict__ tkey,
-                                                           unsigned int* __restrict__ thist,
-                                                           int32_t* __restrict__ tfirst) {
+                                                           int32_t* __restrict__ tfirst,
+                                                           int32_t* __restrict__ tnpl) {
     using T = double;
+    __shared__ SampleItem qbuf[4][kSampleQueue];   // 128 threads: 4 warps
     const int lane = threadIdx.x & 31;
-    // for the transport pass: the ray's farthest plasma sample (where its transport starts; -1:
-    // none), and its work: the steps from there to the camera and half a step for each plasma
-    // sample's Stokes step
-    auto put_key = [&](int64_t wray, int32_t first, int32_t k) {
-        if (lane == 0 && tkey) {
-            tfirst[wray] = first;
-            tkey[wray] = k;
-            atomicAdd(&thist[cost_bucket(k)], 1u);
-        }
-    };
-    const int64_t re = wave_end(bs, ray_end);
-    const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
-    while (true) {
-        unsigned long long got = 0;
-        if (lane == 0) got = atomicAdd(&ctr->next_ray_mi, 1ull);
-        got = __shfl_sync(0xffffffffu, got, 0);
-        if ((int64_t)got >= total_rays) break;
-        const int64_t wray = (int64_t)got, ray = ray_begin + wray;
-        int q, pi, pj;
-        int64_t opix;
-        setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
-        const RayHdr hd = hdr[wray];
-        if (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) {
-            put_key(wray, -1, 0);
-            continue;
-        }
-        const ImageDesc& im = imgs[q];
-        const T kt = hd.kt, nu_norm = hd.nnorm * im.freq;
-        const T a = ic<T>(im, kcSpin), m = ic<T>(im, kcMass);
-        const bool flat = im.flat != 0;
-        int32_t hi = -1, npl = 0;
-        // records beyond the last one near the grid carry no plasma (transfer_start)
-        const int32_t nrec = hd.last_in + 1 < hd.nrec ? hd.last_in + 1 : hd.nrec;
-        for (int32_t base = 0; base < nrec; base += 32) {
-            const int32_t idx = base + lane;
-            if (idx >= nrec) break;
-            const int64_t k = record_index(chunks, wray, idx);
+    SampleItem* Q = qbuf[threadIdx.x >> 5];
+    int qn = 0;   // items waiting (warp-uniform)
+
+    // the queue's first n items, lane i taking item i
+    auto evaluate = [&](int n) {
+        bool plasma = false;
+        int32_t wray = -1, idx = -1;
+        if (lane < n) {
+            const SampleItem it = Q[lane];
+            wray = it.wray;
+            idx = it.idx;
+            const RayHdr hd = hdr[it.wray];
+            const ImageDesc& im = imgs[it.q];
+            const T kt = hd.kt, nu_norm = hd.nnorm * im.freq;
+            const T a = ic<T>(im, kcSpin), m = ic<T>(im, kcMass);
+            const bool flat = im.flat != 0;
             T cur[RecStride<double>::v];
-            load_record<double>(pool + k * RecStride<double>::v, cur);
+            load_record<double>(pool + it.k * RecStride<double>::v, cur);
             const T xs[3] = {cur[0], cur[1], cur[2]};
             KSGeom<T> G;
             ks_geom<T>(xs[0], xs[1], xs[2], a, m, flat, false, G);
             Plasma<T> P;
-            unsigned char flag = 0;
             if (plasma_at<T, kSlow>(im, xs, cur[13], G, P)) {
                 const T kl[4] = {kt, cur[3], cur[4], cur[5]};
                 T ku[4];
@@ -2325,21 +2317,123 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
                 T v[kPreVals] = {co[0] * eg, co[1] * eg, co[2] * eg, co[3] * path,
                                  co[4] * path, co[5] * path, co[6] * path, co[7] * path};
                 fluid_basis<T>(G, P, kl, ku, v + 8, v + 12, v + 16, v + 20);
-                double2* out = reinterpret_cast<double2*>(pre + kPreVals * k);
+                double2* out = reinterpret_cast<double2*>(pre + kPreVals * it.k);
 #pragma unroll
                 for (int i = 0; i < kPreVals / 2; ++i) out[i] = make_double2(v[2 * i], v[2 * i + 1]);
-                flag = 1;
-                hi = idx;
-                ++npl;
+                plasma = true;
             }
-            pre_flag[k] = flag;
+            pre_flag[it.k] = plasma ? 1 : 0;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-            npl += __shfl_xor_sync(0xffffffffu, npl, o);
+        // per ray of the batch: its plasma samples lie at increasing lanes (records enter the
+        // queue in order), so the highest lane of a ray's group holds its farthest one
+        const unsigned grp = __match_any_sync(0xffffffffu, plasma ? wray : -1 - lane);
+        if (plasma && lane == 31 - __clz(grp)) {
+            atomicMax(&tfirst[wray], idx);
+            atomicAdd(&tnpl[wray], __popc(grp));
         }
-        put_key(wray, hi, hi + 1 + (npl >> 1));
+    };
+
+    // one loop with one evaluation site (the kernel's code stays small for the instruction
+    // cache): each turn takes a ray if the current one is done, tests its next 32 records, and
+    // evaluates a batch when 32 items wait or, with the rays exhausted, whatever remains
+    const int64_t re = wave_end(bs, ray_end);
+    const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
+    int64_t wray = 0;
+    int32_t base = 0, nrec = 0;
+    int q = 0;
+    float aa = 0.0f, r2lo = 0.0f, r2hi = 0.0f;
+    bool exhausted = false;
+    while (true) {
+        if (base >= nrec && !exhausted) {
+            unsigned long long got = 0;
+            if (lane == 0) got = atomicAdd(&ctr->next_ray_mi, 1ull);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if ((int64_t)got >= total_rays) {
+                exhausted = true;
+            } else {
+                wray = (int64_t)got;
+                int pi, pj;
+                int64_t opix;
+                setup_ray(imgs, n_images, bs, ray_begin + wray, q, opix, pi, pj);
+                const RayHdr hd = hdr[wray];
+                base = 0;
+                nrec = 0;
+                if (hd.status != BL_RAY_OVERFLOW && hd.nrec > 0) {
+                    const ImageDesc& im = imgs[q];
+                    // shell test in FP32 on r^2 with 1e-4 margins (the exact test follows in
+                    // evaluate): 2 r^2 = R^2 - a^2 + ((R^2 - a^2)^2 + 4 a^2 z^2)^1/2
+                    aa = (float)(im.spin * im.spin);
+                    r2lo = (float)(im.r_min * im.r_min * (1.0 - 1e-4));
+                    r2hi = (float)(im.r_max * im.r_max * (1.0 + 1e-4));
+                    // records beyond the last one near the grid carry no plasma
+                    // (transfer_start)
+                    nrec = hd.last_in + 1 < hd.nrec ? hd.last_in + 1 : hd.nrec;
+                }
+            }
+        }
+        if (base < nrec) {
+            const int32_t idx = base + lane;
+            bool cand = false;
+            int64_t k = 0;
+            if (idx < nrec) {
+                k = record_index(chunks, wray, idx);
+                const double* rp = pool + k * RecStride<double>::v;
+                const float x = (float)__ldg(rp), y = (float)__ldg(rp + 1), z = (float)__ldg(rp + 2);
+                const float qq = x * x + y * y + z * z - aa;
+                const float r2 = 0.5f * (qq + sqrtf(qq * qq + 4.0f * aa * z * z));
+                cand = r2 >= r2lo && r2 <= r2hi;
+                if (!cand) pre_flag[k] = 0;
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, cand);
+            if (cand) {
+                SampleItem& it = Q[qn + __popc(mask & ((1u << lane) - 1u))];
+                it.k = k;
+                it.wray = (int32_t)wray;
+                it.idx = idx;
+                it.q = q;
+            }
+            qn += __popc(mask);
+            base += 32;
+            __syncwarp();
+        }
+        if (qn >= 32 || (exhausted && qn > 0)) {
+            const int n = qn < 32 ? qn : 32;
+            evaluate(n);
+            __syncwarp();
+            SampleItem keep;
+            const bool moves = lane < qn - n;
+            if (moves) keep = Q[n + lane];
+            __syncwarp();
+            if (moves) Q[lane] = keep;
+            qn -= n;
+            __syncwarp();
+        }
+        if (exhausted && qn == 0) break;
+    }
+}
+
+// The transport pass's key for each wave ray from the sample pass's results: the farthest
+// plasma sample (tfirst, -1: none) and the plasma-sample count (in key on entry): the steps
+// from there to the camera plus half a step per Stokes step; with the histogram of the
+// counting sort.
+__global__ void transport_key_kernel(const int32_t* __restrict__ tfirst, int32_t* __restrict__ key,
+                                     BlockSource bs, int64_t ray_begin, int64_t ray_end,
+                                     unsigned int* __restrict__ hist) {
+    const int64_t re = wave_end(bs, ray_end);
+    const int64_t n = re > ray_begin ? re - ray_begin : 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < n; w0 += stride) {
+        const int64_t w = w0 + threadIdx.x;
+        const bool on = w < n;
+        int b = -1 - lane;
+        if (on) {
+            const int32_t k = tfirst[w] + 1 + (key[w] >> 1);
+            key[w] = k;
+            b = cost_bucket(k);
+        }
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        if (on && lane == __ffs(same) - 1) atomicAdd(&hist[b], (unsigned int)__popc(same));
     }
 }
 
