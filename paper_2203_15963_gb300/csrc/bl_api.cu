@@ -56,8 +56,8 @@ constexpr int64_t kChunksPerRay = 16;
 constexpr int64_t kWaveRays = 1 << 20;
 
 struct Layout {
-    size_t counters, descs, hdr, init, chunks, pool, mlp_y, pre, pre_flag, tkey, tperm, tfirst,
-        thist, pred, total;
+    size_t counters, descs, hdr, init, chunks, pool, mlp_y, pre, pre_flag, tkey, tnpl, tperm,
+        tfirst, thist, pred, total;
     int64_t rays;          // rays of the whole call
     int64_t wave;          // rays per wave (the workspace holds one wave)
     int64_t pool_chunks;
@@ -123,9 +123,10 @@ Layout make_layout_wave(int32_t n_images, int64_t rays, int64_t wave, int precis
     }
     // the transfer's ray order: each ray's work, the wave's rays longest first, each ray's
     // first transported sample (FP64 transport pass), the histogram of the counting sort
-    L.tkey = L.tperm = L.tfirst = L.thist = off;
+    L.tkey = L.tnpl = L.tperm = L.tfirst = L.thist = off;
     if (transfer) {
         L.tkey = off;   off = align_up(off + sizeof(int32_t) * (size_t)L.wave);
+        L.tnpl = off;   off = align_up(off + sizeof(int32_t) * (size_t)L.wave);
         L.tperm = off;  off = align_up(off + sizeof(int32_t) * (size_t)L.wave);
         L.tfirst = off; off = align_up(off + sizeof(int32_t) * (size_t)L.wave);
         L.thist = off;  off = align_up(off + sizeof(unsigned int) * bl::kCostBuckets);
@@ -641,7 +642,7 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
                 BL_CUDA(cudaMemsetAsync(thist, 0, sizeof(unsigned int) * bl::kCostBuckets, st));
                 bl::record_key_kernel<<<sgrid, 256, 0, st>>>(hdr, cfg.bs, b, e, tkey, thist);
                 bl::work_scan_kernel<<<1, 1024, 0, st>>>(thist);
-                bl::work_scatter_kernel<<<sgrid, 256, 0, st>>>(tkey, cfg.bs, b, e, thist, tperm);
+                bl::work_scatter_kernel<bl::kFusedGroup><<<sgrid, 256, 0, st>>>(tkey, cfg.bs, b, e, thist, tperm);
                 g_launches += 3;
                 BL_CUDA(cudaGetLastError());
                 return 0;
@@ -682,22 +683,23 @@ int launch_kernels(int32_t n_images, char* ws, const Layout& L, int precision, b
                 double* pre = (double*)(ws + L.pre);
                 unsigned char* pflag = (unsigned char*)(ws + L.pre_flag);
                 int32_t* tfirst = (int32_t*)(ws + L.tfirst);
+                int32_t* tnpl = (int32_t*)(ws + L.tnpl);
                 // per wave ray: farthest plasma sample -1 and no plasma samples until found
                 BL_CUDA(cudaMemsetAsync(tfirst, 0xff, sizeof(int32_t) * (size_t)(e - b), st));
-                BL_CUDA(cudaMemsetAsync(tkey, 0, sizeof(int32_t) * (size_t)(e - b), st));
+                BL_CUDA(cudaMemsetAsync(tnpl, 0, sizeof(int32_t) * (size_t)(e - b), st));
                 BL_CUDA(cudaMemsetAsync(thist, 0, sizeof(unsigned int) * bl::kCostBuckets, st));
                 const unsigned pre_grid = (unsigned)(di.sms * di.pre_occ[slow ? 1 : 0]);
                 if (slow)
                     bl::fp64_samples_kernel<true><<<pre_grid, 128, 0, st>>>(
                         d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag,
-                        tfirst, tkey);
+                        tfirst, tnpl);
                 else
                     bl::fp64_samples_kernel<false><<<pre_grid, 128, 0, st>>>(
                         d_desc, n_images, b, e, hdr, dpool, chunks, ctr, cfg.bs, pre, pflag,
-                        tfirst, tkey);
-                bl::transport_key_kernel<<<sgrid, 256, 0, st>>>(tfirst, tkey, cfg.bs, b, e, thist);
+                        tfirst, tnpl);
+                bl::transport_key_kernel<<<sgrid, 256, 0, st>>>(tfirst, tnpl, tkey, cfg.bs, b, e, thist);
                 bl::work_scan_kernel<<<1, 1024, 0, st>>>(thist);
-                bl::work_scatter_kernel<<<sgrid, 256, 0, st>>>(tkey, cfg.bs, b, e, thist, tperm);
+                bl::work_scatter_kernel<bl::kTransportGroup><<<sgrid, 256, 0, st>>>(tkey, cfg.bs, b, e, thist, tperm);
                 g_launches += 4;
                 BL_CUDA(cudaGetLastError());
                 bl::transport_fp64_kernel<<<tr_grid, bl::kTransferFp64Threads, 0, st>>>(

@@ -369,6 +369,28 @@ __global__ void cost_descs_kernel(const ImageDesc* __restrict__ src, ImageDesc* 
     }
 }
 
+// The transfers' ray orders sort groups of G consecutive wave rays by their largest work: the
+// FP64 transport pass groups of a warp's 32 (neighbouring pixels of the geodesic queue, so a
+// warp keeps rays of similar paths through the plasma: 245.7 -> 240.5 ms against single rays
+// on the nine-image step), the FP32 transfer single rays (10.9 ms against 13.2 with groups:
+// its per-sample chain costs the same with or without plasma, and single rays balance better).
+constexpr int kTransportGroup = 32;
+constexpr int kFusedGroup = 1;
+
+// Queue position -> wave ray of an ordered transfer (perm lists the groups longest first);
+// -1 for the positions of a partial last group that hold no ray.
+template <int G>
+__device__ __forceinline__ int64_t ordered_ray(const int32_t* perm, unsigned long long got,
+                                               int64_t n) {
+    const int64_t w = (int64_t)perm[got / G] * G + (int64_t)(got % G);
+    return w < n ? w : -1;
+}
+// Queue length of an ordered transfer over n wave rays.
+template <int G>
+__device__ __forceinline__ int64_t ordered_total(int64_t n) {
+    return (n + G - 1) / G * G;
+}
+
 // Bucket of a cost in a descending counting sort (larger costs in lower buckets).
 __device__ __forceinline__ int cost_bucket(int32_t c) {
     const int v = c < 0 ? 0 : (c > kCostBuckets - 1 ? kCostBuckets - 1 : c);
@@ -447,11 +469,12 @@ __global__ void __launch_bounds__(1024) work_scan_kernel(unsigned int* __restric
 }
 // (the wave's rays as the sample pass counted them: a device block list may hold fewer than
 // the launch covers; lanes of a warp with equal buckets take their places with one atomic)
+template <int G>
 __global__ void work_scatter_kernel(const int32_t* __restrict__ key, BlockSource bs,
                                     int64_t ray_begin, int64_t ray_end,
                                     unsigned int* __restrict__ start, int32_t* __restrict__ perm) {
     const int64_t re = wave_end(bs, ray_end);
-    const int64_t n = re > ray_begin ? re - ray_begin : 0;
+    const int64_t n = ((re > ray_begin ? re - ray_begin : 0) + G - 1) / G;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < n; w0 += stride) {
@@ -1960,6 +1983,29 @@ __device__ __forceinline__ int32_t transfer_start(const RayHdr& hd) {
     return hd.last_in < last ? (hd.last_in > 0 ? hd.last_in : 0) : last;
 }
 
+// A warp's 32 consecutive wave rays (w = lane of the warp's first ray + lane) with keys k
+// (lanes with on = false hold none): the key of each order group -- the group's largest --
+// into key[group] and the histogram of the counting sort (lanes of a warp with equal buckets
+// add with one atomic).
+template <int G>
+__device__ __forceinline__ void group_key(int32_t k, bool on, int64_t w, int32_t* __restrict__ key,
+                                          unsigned int* __restrict__ hist) {
+    static_assert(G == 1 || G == 32, "order groups: single rays or warps");
+    const int lane = threadIdx.x & 31;
+    if constexpr (G == 32) {
+        const int32_t gk = __reduce_max_sync(0xffffffffu, k);
+        if (lane == 0 && gk >= 0) {
+            key[w / 32] = gk;
+            atomicAdd(&hist[cost_bucket(gk)], 1u);
+        }
+    } else {
+        if (on) key[w] = k;
+        const int b = on ? cost_bucket(k) : -1 - lane;
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        if (on && lane == __ffs(same) - 1) atomicAdd(&hist[b], (unsigned int)__popc(same));
+    }
+}
+
 // The fused transfer's ray order: each wave ray's records to process (0 for rays without a
 // transfer) into key[] and the histogram of the counting sort (lanes of a warp with equal
 // buckets add with one atomic); work_scan_kernel and work_scatter_kernel finish the order.
@@ -1969,19 +2015,15 @@ __global__ void record_key_kernel(const RayHdr* __restrict__ hdr, BlockSource bs
     const int64_t re = wave_end(bs, ray_end);
     const int64_t n = re > ray_begin ? re - ray_begin : 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
     for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < n; w0 += stride) {
         const int64_t w = w0 + threadIdx.x;
         const bool on = w < n;
-        int b = -1 - lane;
+        int32_t k = -1;
         if (on) {
             const RayHdr hd = hdr[w];
-            const int32_t k = (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) ? 0 : transfer_start(hd) + 1;
-            key[w] = k;
-            b = cost_bucket(k);
+            k = (hd.status == BL_RAY_OVERFLOW || hd.nrec == 0) ? 0 : transfer_start(hd) + 1;
         }
-        const unsigned same = __match_any_sync(0xffffffffu, b);
-        if (on && lane == __ffs(same) - 1) atomicAdd(&hist[b], (unsigned int)__popc(same));
+        group_key<kFusedGroup>(k, on, w, key, hist);
     }
 }
 
@@ -2004,7 +2046,8 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
     constexpr bool kIdx = kMlp;   // the transfer needs each record's pool index
     int64_t nxt_k = 0;
     const int64_t re = wave_end(bs, ray_end);
-    const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
+    const int64_t n_rays = re > ray_begin ? re - ray_begin : 0;
+    const int64_t total_rays = side.perm ? ordered_total<kFusedGroup>(n_rays) : n_rays;
     int64_t wray = 0;
     bool active = false;
     int64_t ray = 0, opix = 0;
@@ -2027,12 +2070,13 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
             if ((int64_t)got >= total_rays) exhausted = true;
             else {
                 // the wave's rays in the order of their record counts where there is one
-                wray = side.perm ? (int64_t)side.perm[got] : (int64_t)got;
+                wray = side.perm ? ordered_ray<kFusedGroup>(side.perm, got, n_rays) : (int64_t)got;
                 ray = ray_begin + wray;
             }
         }
         if (!__any_sync(0xffffffffu, active || (need && !exhausted))) break;
         if (!active && !(need && !exhausted)) continue;
+        if (!active && wray < 0) continue;   // a partial order group's empty position
         if (!active) {
             setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
             const ImageDesc& im = imgs[q];
@@ -2412,28 +2456,22 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
     }
 }
 
-// The transport pass's key for each wave ray from the sample pass's results: the farthest
-// plasma sample (tfirst, -1: none) and the plasma-sample count (in key on entry): the steps
-// from there to the camera plus half a step per Stokes step; with the histogram of the
-// counting sort.
-__global__ void transport_key_kernel(const int32_t* __restrict__ tfirst, int32_t* __restrict__ key,
+// The transport pass's key for each group of wave rays from the sample pass's results: the
+// farthest plasma sample (tfirst, -1: none) and the plasma-sample count (npl): the steps from
+// there to the camera plus half a step per Stokes step; with the histogram of the counting
+// sort.
+__global__ void transport_key_kernel(const int32_t* __restrict__ tfirst,
+                                     const int32_t* __restrict__ npl, int32_t* __restrict__ key,
                                      BlockSource bs, int64_t ray_begin, int64_t ray_end,
                                      unsigned int* __restrict__ hist) {
     const int64_t re = wave_end(bs, ray_end);
     const int64_t n = re > ray_begin ? re - ray_begin : 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
     for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < n; w0 += stride) {
         const int64_t w = w0 + threadIdx.x;
         const bool on = w < n;
-        int b = -1 - lane;
-        if (on) {
-            const int32_t k = tfirst[w] + 1 + (key[w] >> 1);
-            key[w] = k;
-            b = cost_bucket(k);
-        }
-        const unsigned same = __match_any_sync(0xffffffffu, b);
-        if (on && lane == __ffs(same) - 1) atomicAdd(&hist[b], (unsigned int)__popc(same));
+        const int32_t k = on ? tfirst[w] + 1 + (npl[w] >> 1) : -1;
+        group_key<kTransportGroup>(k, on, w, key, hist);
     }
 }
 
@@ -2456,7 +2494,8 @@ __global__ void __maxnreg__(BL_TRANSPORT64_MAXNREG) transport_fp64_kernel(
         const int32_t* __restrict__ perm) {
     using T = double;
     const int64_t re = wave_end(bs, ray_end);
-    const int64_t total_rays = re > ray_begin ? re - ray_begin : 0;
+    const int64_t n_rays = re > ray_begin ? re - ray_begin : 0;
+    const int64_t total_rays = perm ? ordered_total<kTransportGroup>(n_rays) : n_rays;
     int64_t wray = 0, ray = 0, opix = 0;
     bool active = false, started = false;
     int q = 0, pi = 0, pj = 0;
@@ -2472,12 +2511,13 @@ __global__ void __maxnreg__(BL_TRANSPORT64_MAXNREG) transport_fp64_kernel(
             if ((int64_t)got >= total_rays) exhausted = true;
             else {
                 // the sample pass's work order (longest first) where there is one
-                wray = perm ? (int64_t)perm[got] : (int64_t)got;
+                wray = perm ? ordered_ray<kTransportGroup>(perm, got, n_rays) : (int64_t)got;
                 ray = ray_begin + wray;
             }
         }
         if (!__any_sync(0xffffffffu, active || (need && !exhausted))) break;
         if (!active && !(need && !exhausted)) continue;
+        if (!active && wray < 0) continue;   // a partial order group's empty position
         if (!active) {
             setup_ray(imgs, n_images, bs, ray, q, opix, pi, pj);
             const ImageDesc& im = imgs[q];
