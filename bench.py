@@ -70,19 +70,19 @@ KERNEL_HEADERS = ("bl_kernels.cuh", "bl_math.cuh", "bl_df64.cuh", "bl_internal.c
 # fp64_instr: thread-level DFMA + DMUL + DADD instructions per unit from the same capture,
 # which gives the FP64 pipe's issue rate beside the algorithmic roofline.
 DRAM_PER_UNIT = {
-    # FP64 form, 7,845,751 attempts: 0.663 GB read + 5.343 GB written (the FP64 records and the
+    # FP64 form, 7,845,751 attempts: 0.662 GB read + 5.371 GB written (the FP64 records and the
     # stage derivatives, held in local memory at 16 CTAs an SM)
-    "geodesic_fp64": {"src": "ce25265838878bb9", "bytes": 765.5, "unit": "attempt",
-                      "fp64_instr": 1090.4},
-    # FP64 form, 18,372,204 samples, both transfer passes: fp64_samples_kernel 4.926 + 4.472
+    "geodesic_fp64": {"src": "b70f9eb82a892073", "bytes": 769.0, "unit": "attempt",
+                      "fp64_instr": 1091.2},
+    # FP64 form, 18,372,204 samples, the transfer's launches: fp64_samples_kernel 5.709 + 5.112
     # GB (records, grid gathers, 193 B of results a sample, spills) and transport_fp64_kernel
-    # 1.386 + 1.881 GB (records, those results, spills)
-    "transfer_fp64": {"src": "ce25265838878bb9", "bytes": 689.3, "unit": "sample",
-                      "fp64_instr": 671.0},
-    # fast form, 7,845,744 attempts: 0.024 GB read + 1.135 GB written
-    "geodesic_df64": {"src": "ce25265838878bb9", "bytes": 147.7, "unit": "attempt"},
-    # fast form, 18,372,183 samples: 1.391 GB read + 0.004 GB written
-    "transfer_fp32": {"src": "ce25265838878bb9", "bytes": 75.9, "unit": "sample"},
+    # 1.501 + 2.509 GB (records, those results, spills)
+    "transfer_fp64": {"src": "b70f9eb82a892073", "bytes": 807.2, "unit": "sample",
+                      "fp64_instr": 663.5},
+    # fast form, 7,845,744 attempts: 0.026 GB read + 1.135 GB written
+    "geodesic_df64": {"src": "b70f9eb82a892073", "bytes": 148.0, "unit": "attempt"},
+    # fast form, 18,372,183 samples: 1.423 GB read + 0.004 GB written
+    "transfer_fp32": {"src": "b70f9eb82a892073", "bytes": 77.6, "unit": "sample"},
 }
 
 
