@@ -456,10 +456,10 @@ __global__ void __launch_bounds__(1024) cost_sort_kernel(const int32_t* __restri
     if (t == 0) *count = (unsigned long long)n_blocks;
 }
 
-// The FP64 transport pass's queue: the sample pass histograms each ray's transport work
-// (hist, global, kCostBuckets counts, zeroed per wave) and stores it in key[wray]; the scan
-// turns the histogram into bucket starts, and the scatter lists the wave's rays longest first
-// in perm (equal work in any order).
+// The transfers' queues: a key kernel (record_key_kernel, transport_key_kernel) stores each
+// order group's work in key[] and histograms it (hist, global, kCostBuckets counts, zeroed per
+// wave); the scan turns the histogram into bucket starts, and the scatter lists the groups
+// longest first in perm (equal work in any order).
 __global__ void __launch_bounds__(1024) work_scan_kernel(unsigned int* __restrict__ hist) {
     __shared__ unsigned int start[kCostBuckets];
     for (int b = threadIdx.x; b < kCostBuckets; b += 1024) start[b] = hist[b];
@@ -467,8 +467,9 @@ __global__ void __launch_bounds__(1024) work_scan_kernel(unsigned int* __restric
     bucket_scan(start);
     for (int b = threadIdx.x; b < kCostBuckets; b += 1024) hist[b] = start[b];
 }
-// (the wave's rays as the sample pass counted them: a device block list may hold fewer than
-// the launch covers; lanes of a warp with equal buckets take their places with one atomic)
+// (over the wave's order groups of G rays, as the key kernel counted them: a device block
+// list may hold fewer rays than the launch covers; lanes of a warp with equal buckets take
+// their places with one atomic)
 template <int G>
 __global__ void work_scatter_kernel(const int32_t* __restrict__ key, BlockSource bs,
                                     int64_t ray_begin, int64_t ray_end,
