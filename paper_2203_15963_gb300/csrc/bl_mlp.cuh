@@ -356,9 +356,12 @@ __global__ void __launch_bounds__(128) forward_kernel(const float* __restrict__ 
 // transfer): record k of the pool carries its sample's input row in its last 8 bytes (values
 // 14-15, written by the model-input kernel; zero where the sample has no plasma or lies
 // outside the model's domain); the model's outputs o[7] (padded to 8) go to out[8 k ..].
-// Tiles of 128 consecutive records over the pool's used chunks, several CTAs an SM, no
-// lockstep with the transfer. The used record count is read on the device (the pool cursor
-// after the geodesic kernel), so the launch needs no host round trip.
+// Each CTA scans its share of the pool's used records 128 at a time and queues the records
+// that carry an input row in shared memory; whenever 128 wait it runs the network on a full
+// tile of them (each row of a tile is computed independently of the others, so the outputs do
+// not depend on which records share a tile). The used record count is read on the device (the
+// pool cursor after the geodesic kernel), so the launch needs no host round trip.
+constexpr int kPoolQueue = 256;   // fewer than 128 waiting + one scanned batch of 128
 __global__ void __launch_bounds__(128) forward_pool_kernel(const float* __restrict__ P,
                                                            const float* __restrict__ pool,
                                                            const unsigned long long* __restrict__ pool_next,
@@ -366,26 +369,64 @@ __global__ void __launch_bounds__(128) forward_pool_kernel(const float* __restri
                                                            float* __restrict__ out,
                                                            unsigned long long* timeouts) {
     __shared__ FwdSmem S;
+    __shared__ int64_t qrec[kPoolQueue];   // (the rows are read again at evaluation: 2 KB
+                                           // more of queue would cost a CTA an SM)
+    __shared__ int wsum[4];
     fwd_init(S, P);
     uint32_t phase = 0;
     bool ok = true;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const unsigned long long used_chunks = *pool_next < pool_chunks ? *pool_next : pool_chunks;
     const int64_t n = (int64_t)used_chunks * kChunk;
     const int64_t tiles = (n + 127) / 128;
-    for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        const int64_t k = tile * 128 + threadIdx.x;
-        uint2 row = make_uint2(0u, 0u);
-        if (k < n) row = __ldg(reinterpret_cast<const uint2*>(pool + 16 * k + 14));
-        const bool valid = row.y != 0u;          // the constant-1 column is set
-        float y[7];
-        ok = fwd_tile_y<true>(S, phase, row, valid, y);
-        if (ok && valid) {
-            float4* q = reinterpret_cast<float4*>(out + 8 * k);
-            q[0] = make_float4(y[0], y[1], y[2], y[3]);
-            q[1] = make_float4(y[4], y[5], y[6], 0.0f);
+    int qn = 0;   // records waiting (the same on every thread)
+    for (int64_t tile = blockIdx.x; ok; tile += gridDim.x) {
+        const bool more = tile < tiles;
+        if (more) {
+            // scan 128 records; the ones with an input row join the queue in record order
+            const int64_t k = tile * 128 + t;
+            uint2 row = make_uint2(0u, 0u);
+            if (k < n) row = __ldg(reinterpret_cast<const uint2*>(pool + 16 * k + 14));
+            const bool valid = row.y != 0u;          // the constant-1 column is set
+            const unsigned mask = __ballot_sync(0xffffffffu, valid);
+            if (lane == 0) wsum[wid] = __popc(mask);
+            __syncthreads();
+            int off = __popc(mask & ((1u << lane) - 1u)), total = 0;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                if (w < wid) off += wsum[w];
+                total += wsum[w];
+            }
+            if (valid) qrec[qn + off] = k;
+            qn += total;
+            __syncthreads();
         }
+        if (qn >= 128 || (!more && qn > 0)) {
+            const int m = qn < 128 ? qn : 128;
+            const bool valid = t < m;
+            const int64_t k = valid ? qrec[t] : 0;
+            const uint2 row = valid ? __ldg(reinterpret_cast<const uint2*>(pool + 16 * k + 14))
+                                    : make_uint2(0u, 0u);
+            float y[7];
+            ok = fwd_tile_y<true>(S, phase, row, valid, y);
+            if (ok && valid) {
+                float4* q = reinterpret_cast<float4*>(out + 8 * k);
+                q[0] = make_float4(y[0], y[1], y[2], y[3]);
+                q[1] = make_float4(y[4], y[5], y[6], 0.0f);
+            }
+            // the waiting remainder moves to the queue's front
+            const bool moves = t < qn - m;
+            int64_t keep_rec = 0;
+            __syncthreads();
+            if (moves) keep_rec = qrec[m + t];
+            __syncthreads();
+            if (moves) qrec[t] = keep_rec;
+            qn -= m;
+            __syncthreads();
+        }
+        if (!more && qn == 0) break;
     }
-    if (!ok && threadIdx.x == 0) atomicAdd(timeouts, 1ull);
+    if (!ok && t == 0) atomicAdd(timeouts, 1ull);
     fwd_finish(S, phase, ok);
 }
 
