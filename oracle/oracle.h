@@ -16,8 +16,8 @@
  * Each reading of a point the paper leaves open is stated next to the code that takes it.
  *
  * Parity unpinned: the polarized synchrotron fitting functions (the paper cites them without
- * printing them) are pinned only at their limits, by Kirchhoff's law, by symmetry, and (total
- * and linear emissivity) against quadrature of the exact emissivity integral.
+ * printing them) are pinned only at their limits, by Kirchhoff's law, by symmetry, and (total,
+ * linear and circular emissivity) against quadrature of the exact emissivity integrals.
  */
 #ifndef BL_ORACLE_H
 #define BL_ORACLE_H
