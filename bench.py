@@ -73,19 +73,19 @@ TRAFFIC_HEADERS = ("bl_kernels.cuh", "bl_math.cuh", "bl_df64.cuh", "bl_internal.
 # fp64_instr: thread-level DFMA + DMUL + DADD instructions per unit from the same capture,
 # which gives the FP64 pipe's issue rate beside the algorithmic roofline.
 DRAM_PER_UNIT = {
-    # FP64 form, 7,845,751 attempts: 0.662 GB read + 5.371 GB written (the FP64 records and the
+    # FP64 form, 7,845,751 attempts: 0.622 GB read + 5.193 GB written (the FP64 records and the
     # stage derivatives, held in local memory at 16 CTAs an SM)
-    "geodesic_fp64": {"src": "b779c3c4826945f9", "bytes": 769.0, "unit": "attempt",
+    "geodesic_fp64": {"src": "958df7db1476d091", "bytes": 741.1, "unit": "attempt",
                       "fp64_instr": 1091.2},
-    # FP64 form, 18,372,204 samples, the transfer's launches: fp64_samples_kernel 5.709 + 5.112
+    # FP64 form, 18,372,204 samples, the transfer's launches: fp64_samples_kernel 5.871 + 5.342
     # GB (records, grid gathers, 193 B of results a sample, spills) and transport_fp64_kernel
-    # 1.501 + 2.509 GB (records, those results, spills)
-    "transfer_fp64": {"src": "b779c3c4826945f9", "bytes": 807.2, "unit": "sample",
-                      "fp64_instr": 663.5},
+    # 1.503 + 2.447 GB (records, those results, spills)
+    "transfer_fp64": {"src": "958df7db1476d091", "bytes": 825.4, "unit": "sample",
+                      "fp64_instr": 659.3},
     # fast form, 7,845,744 attempts: 0.026 GB read + 1.135 GB written
-    "geodesic_df64": {"src": "b779c3c4826945f9", "bytes": 148.0, "unit": "attempt"},
-    # fast form, 18,372,183 samples: 1.423 GB read + 0.004 GB written
-    "transfer_fp32": {"src": "b779c3c4826945f9", "bytes": 77.6, "unit": "sample"},
+    "geodesic_df64": {"src": "958df7db1476d091", "bytes": 148.0, "unit": "attempt"},
+    # fast form, 18,372,183 samples: 1.420 GB read + 0.004 GB written
+    "transfer_fp32": {"src": "958df7db1476d091", "bytes": 77.5, "unit": "sample"},
 }
 
 

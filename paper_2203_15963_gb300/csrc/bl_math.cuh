@@ -10,7 +10,7 @@ namespace bl {
 
 // Modified Bessel I_0, I_1 for 0 <= x <= 3.75 (used for x <= 2). FP32: the polynomials of
 // Abramowitz & Stegun 9.8.1 and 9.8.3 in t = x / 3.75 (|error| < 1.6e-7 for I_0, 8e-9 for
-// I_1 / x, below FP32 rounding); FP64: CUDA's double functions.
+// I_1 / x, below FP32 rounding).
 __device__ __forceinline__ float cyl_bessel_i0(float x) {
     const float t = x * (1.0f / 3.75f), t2 = t * t;
     return 1.0f + t2 * (3.5156229f + t2 * (3.0899424f + t2 * (1.2067492f + t2 * (0.2659732f +
@@ -21,8 +21,32 @@ __device__ __forceinline__ float cyl_bessel_i1(float x) {
     return x * (0.5f + t2 * (0.87890594f + t2 * (0.51498869f + t2 * (0.15084934f + t2 * (0.02658733f +
            t2 * (0.00301532f + t2 * 0.00032411f))))));
 }
-__device__ __forceinline__ double cyl_bessel_i0(double x) { return ::cyl_bessel_i0(x); }
-__device__ __forceinline__ double cyl_bessel_i1(double x) { return ::cyl_bessel_i1(x); }
+// FP64 (used for 0 <= x <= 2 only): the defining power series, I_0(x) = sum_k t^k / (k!)^2
+// and I_1(x) = (x/2) sum_k t^k / (k! (k+1)!) with t = x^2 / 4 <= 1, summed by Horner's rule
+// through k = 12 (the next terms are below 2e-18 of the sums); all terms are positive, so
+// the sums are accurate to a few units in the last place.
+__constant__ double c_i0_series[13] = {
+    1.0, 1.0, 1.0 / 4.0, 1.0 / 36.0, 1.0 / 576.0, 1.0 / 14400.0, 1.0 / 518400.0,
+    1.0 / 25401600.0, 1.0 / 1625702400.0, 1.0 / 131681894400.0, 1.0 / 13168189440000.0,
+    1.0 / 1593350922240000.0, 1.0 / 229442532802560000.0};
+__constant__ double c_i1_series[13] = {
+    1.0, 1.0 / 2.0, 1.0 / 12.0, 1.0 / 144.0, 1.0 / 2880.0, 1.0 / 86400.0, 1.0 / 3628800.0,
+    1.0 / 203212800.0, 1.0 / 14631321600.0, 1.0 / 1316818944000.0, 1.0 / 144850083840000.0,
+    1.0 / 19120211066880000.0, 1.0 / 2982752926433280000.0};
+__device__ __forceinline__ double cyl_bessel_i0(double x) {
+    const double t = 0.25 * x * x;
+    double s = c_i0_series[12];
+#pragma unroll
+    for (int k = 11; k >= 0; --k) s = fma(s, t, c_i0_series[k]);
+    return s;
+}
+__device__ __forceinline__ double cyl_bessel_i1(double x) {
+    const double t = 0.25 * x * x;
+    double s = c_i1_series[12];
+#pragma unroll
+    for (int k = 11; k >= 0; --k) s = fma(s, t, c_i1_series[k]);
+    return 0.5 * x * s;
+}
 
 // Quotient a / b on the coefficient and transport path: in FP32 the hardware reciprocal times
 // a (__fdividef: within 2 ulp for |b| < 2^126, far inside the FP32 form's error budget), in
@@ -350,28 +374,29 @@ __device__ __forceinline__ void coh_pc_step(Coh<T>& n, const T A0[4][4], const T
 }
 
 // ---------------------------------------------------------------------------------------
-// Modified Bessel functions K_0, K_1 (scaled by exp(x)) from the polynomial approximations
-// of Abramowitz & Stegun 9.8.5-9.8.8 (|error| < 2.2e-7 relative to the scaled value);
-// K_2 from the recurrence K_2 = K_0 + (2/x) K_1.
+// Modified Bessel functions K_0, K_1 from the polynomial approximations of Abramowitz &
+// Stegun 9.8.5-9.8.8 (|error| < 2.2e-7 relative to the scaled value); K_2 from the
+// recurrence K_2 = K_0 + (2/x) K_1. bessel_k012 takes x and 1/x and returns K_n(x) itself
+// for x <= 2 (false) and exp(x) K_n(x) for x > 2 (true), where K_n alone underflows for
+// large x: callers that only need ratios, or fold exp(x) into an exponential of their own,
+// skip the exp(x) of the small-argument branch.
 // ---------------------------------------------------------------------------------------
 template <class T>
-__device__ __forceinline__ void bessel_k012_scaled(T x, T& k0, T& k1, T& k2) {
-    const T ix = fq(T(1), x);
+__device__ __forceinline__ bool bessel_k012(T x, T ix, T& k0, T& k1, T& k2) {
+    bool scaled;
     if (x <= T(2)) {
         const T t = T(0.5) * x;
         const T t2 = t * t;
         const T lg = flog(t);
-        const T ex = fexp(x);
         const T i0 = cyl_bessel_i0(x);
         const T i1 = cyl_bessel_i1(x);
         const T p0 = T(-0.57721566) + t2 * (T(0.42278420) + t2 * (T(0.23069756) + t2 * (T(0.03488590) +
                      t2 * (T(0.00262698) + t2 * (T(0.00010750) + t2 * T(0.00000740))))));
         const T p1 = T(1) + t2 * (T(0.15443144) + t2 * (T(-0.67278579) + t2 * (T(-0.18156897) +
                      t2 * (T(-0.01919402) + t2 * (T(-0.00110404) + t2 * T(-0.00004686))))));
-        const T K0 = -lg * i0 + p0;
-        const T K1 = (x * lg * i1 + p1) * ix;
-        k0 = K0 * ex;
-        k1 = K1 * ex;
+        k0 = -lg * i0 + p0;
+        k1 = (x * lg * i1 + p1) * ix;
+        scaled = false;
     } else {
         const T u = T(2) * ix;
         const T sx = rsqrt(x);
@@ -379,8 +404,21 @@ __device__ __forceinline__ void bessel_k012_scaled(T x, T& k0, T& k1, T& k2) {
                    u * (T(0.00587872) + u * (T(-0.00251540) + u * T(0.00053208)))))));
         k1 = sx * (T(1.25331414) + u * (T(0.23498619) + u * (T(-0.03655620) + u * (T(0.01504268) +
                    u * (T(-0.00780353) + u * (T(0.00325614) + u * T(-0.00068245)))))));
+        scaled = true;
     }
     k2 = k0 + T(2) * ix * k1;
+    return scaled;
+}
+
+// exp(x) K_n(x), n = 0, 1, 2, at every x (the stage entry point and the model's targets).
+template <class T>
+__device__ __forceinline__ void bessel_k012_scaled(T x, T& k0, T& k1, T& k2) {
+    if (!bessel_k012(x, fq(T(1), x), k0, k1, k2)) {
+        const T ex = fexp(x);
+        k0 = k0 * ex;
+        k1 = k1 * ex;
+        k2 = k2 * ex;
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -404,22 +442,26 @@ __device__ __forceinline__ void synchrotron_coefficients(T ne, T th, T bg, T nu,
     const T nub = T(kE / (2.0 * kPi * kMe * kC)) * bg;
     const T z = fq(T(1), th);
     const T inu = fq(T(1), nu);
+    // K_n(z), scaled by exp(z) only for z > 2 (1 / z = Theta_e)
     T k0, k1, k2;
-    bessel_k012_scaled(z, k0, k1, k2);
+    const bool kscaled = bessel_k012(z, th, k0, k1, k2);
     const T ik2 = fq(T(1), k2);
+    // 1 / x = 3/2 nu_B sin(theta) Theta^2 / nu; X^2 = (sqrt 2 1e3 / 1.5) / x, so X and the
+    // emissivity's x^-1/2 share one square root
+    const T ix = T(1.5) * nub * sth * th * th * inu;
+    const T six = fsqrt(ix);
     if (sth > T(0)) {
-        const T x = fq(nu, T(1.5) * nub * sth * th * th);
-        const T x13 = fcbrt(x);
-        const T ix13 = fq(T(1), x13);
+        const T ix13 = fcbrt(ix);
+        const T x13 = fq(T(1), ix13);
         const T ix23 = ix13 * ix13;
-        // 1 / K_2(z) = exp(z) / k2 (k2 scaled), and exp(z) is taken together with the shape
-        // functions' exp(-1.8899 x^1/3): their product stays finite (and underflows to 0 for
-        // cold plasma) where exp(z) = exp(1 / Theta_e) alone would overflow
-        const T ex = fexp(z - T(1.8899) * x13);
+        // 1 / K_2(z) = exp(z) / k2 where k2 is scaled, and exp(z) is then taken together with
+        // the shape functions' exp(-1.8899 x^1/3): their product stays finite (and underflows
+        // to 0 for cold plasma) where exp(z) = exp(1 / Theta_e) alone would overflow
+        const T ex = fexp((kscaled ? z : T(0)) - T(1.8899) * x13);
         const T ii = T(2.5651) * (T(1) + T(1.92) * ix13 + T(0.9977) * ix23) * ex;
         const T iq = T(2.5651) * (T(1) + T(0.932) * ix13 + T(0.4998) * ix23) * ex;
         // 1 / x = (x^-1/3)^3
-        const T iv = (T(1.8138) * ix23 * ix13 + T(3.423) * ix23 + T(0.02955) * rsqrt(x) +
+        const T iv = (T(1.8138) * ix23 * ix13 + T(3.423) * ix23 + T(0.02955) * six +
                       T(2.0377) * ix13) * ex;
         const T pre = ne * T(kE * kE / (1.7320508075688772 * kC)) * nu * ik2;
         out[0] = pre * ii;
@@ -433,7 +475,7 @@ __device__ __forceinline__ void synchrotron_coefficients(T ne, T th, T bg, T nu,
         out[4] = out[1] * ibnu;
         out[5] = out[2] * ibnu;
     }
-    const T X = th * fsqrt(T(1.4142135623730951e3) * sth * nub * inu);
+    const T X = T(30.705195677312716) * six;
     // X^1.035 and X^1.2 as exponentials of one shared logarithm (X = 0 gives log X = -inf and
     // both powers 0, as pow does)
     const T lX = flog(X);
