@@ -17,10 +17,11 @@ the device's own peak measured by blacklight_measure_peaks (FMA-chain probes for
 and the double-float arithmetic), with the SM clock sampled while the probes run.
   - geodesic kernel: FLOP64_PER_ATTEMPT per Dormand-Prince attempt (hand count below);
   - transfer kernel: FLOP_PER_SAMPLE per sample, the method's arithmetic per sample as the
-    FP32 transfer kernel executes it (ncu thread-level FFMA x 2 + FADD + FMUL per sample; its
-    special functions are single hardware instructions, counted apart in SFU_PER_SAMPLE). The
-    FP64 kernel runs the same source, so the same count is its algorithmic work; its FP64
-    special-function sequences are overhead on top of it.
+    FP32 transfer kernel executes it with the stencil field test on (ncu thread-level FFMA x 2
+    + FADD + FMUL per sample; its special functions are single hardware instructions, counted
+    apart in SFU_PER_SAMPLE). The FP64 passes run the same source with the same test, so the
+    same count is their algorithmic work; their FP64 special-function sequences are overhead
+    on top of it.
 DRAM traffic per launch comes from one ncu capture per kernel (per-unit figure x the units of
 the launch) and is reported only while the kernel sources still hash to those captured.
 
@@ -55,11 +56,15 @@ GRID = (256, 128, 128)
 # estimate (96) and its norm and the step control (50).
 FLOP64_PER_ATTEMPT = 1214
 # Arithmetic per transfer sample of the method (see the module docstring): FP32 flops and
-# special-function instructions of transfer_kernel<float, float, 0> per sample, from the ncu
-# capture of the one-image 256^2 case (a = 0.94, i = 60 deg; 18,372,183 samples):
-# 2 x 5.48e9 FFMA + 3.29e9 FMUL + 0.33e9 FADD thread instructions, 3.17e8 MUFU.
-FLOP_PER_SAMPLE = 848
-SFU_PER_SAMPLE = 17.2
+# special-function instructions of transfer_kernel<float, float, 0> per sample with the
+# stencil field test on (a sample whose lookup stencil carries no magnetic field stops after
+# the lookup), from the ncu capture of the one-image 256^2 case on plane-layout grids (a =
+# 0.94, i = 60 deg; 18,372,183 samples): 2 x 4.397e9 FFMA + 2.661e9 FMUL + 0.703e9 FADD
+# thread instructions, 2.43e8 MUFU. (Without the test, as the cell-layout FP32 transfer runs
+# for its record-count queue, the kernel executes 848 flops a sample: the difference is work
+# the method does not need.)
+FLOP_PER_SAMPLE = 662
+SFU_PER_SAMPLE = 13.2
 # The CUDA kernel headers (their code hash is printed with the results), and the ones the
 # kernels of the table below are built from: the geodesic and exact-fit transfer kernels
 # instantiate nothing of the learned model's headers (bl_mlp.cuh, bl_tc.cuh), so a change
@@ -73,19 +78,20 @@ TRAFFIC_HEADERS = ("bl_kernels.cuh", "bl_math.cuh", "bl_df64.cuh", "bl_internal.
 # fp64_instr: thread-level DFMA + DMUL + DADD instructions per unit from the same capture,
 # which gives the FP64 pipe's issue rate beside the algorithmic roofline.
 DRAM_PER_UNIT = {
-    # FP64 form, 7,845,751 attempts: 0.622 GB read + 5.193 GB written (the FP64 records and the
+    # FP64 form, 7,845,751 attempts: 0.677 GB read + 5.398 GB written (the FP64 records and the
     # stage derivatives, held in local memory at 16 CTAs an SM)
-    "geodesic_fp64": {"src": "958df7db1476d091", "bytes": 741.1, "unit": "attempt",
+    "geodesic_fp64": {"src": "c20dc1578110e077", "bytes": 774.3, "unit": "attempt",
                       "fp64_instr": 1091.2},
-    # FP64 form, 18,372,204 samples, the transfer's launches: fp64_samples_kernel 5.871 + 5.342
-    # GB (records, grid gathers, 193 B of results a sample, spills) and transport_fp64_kernel
-    # 1.503 + 2.447 GB (records, those results, spills)
-    "transfer_fp64": {"src": "958df7db1476d091", "bytes": 825.4, "unit": "sample",
-                      "fp64_instr": 659.3},
+    # FP64 form, 18,372,204 samples, the transfer's launches: fp64_samples_kernel 4.190 + 3.815
+    # GB (records, the stencils' field values, grid gathers, 193 B of results a plasma sample,
+    # spills) and transport_fp64_kernel 1.501 + 2.439 GB (records, those results, spills)
+    "transfer_fp64": {"src": "c20dc1578110e077", "bytes": 650.2, "unit": "sample",
+                      "fp64_instr": 405.4},
     # fast form, 7,845,744 attempts: 0.026 GB read + 1.135 GB written
-    "geodesic_df64": {"src": "958df7db1476d091", "bytes": 148.0, "unit": "attempt"},
-    # fast form, 18,372,183 samples: 1.420 GB read + 0.004 GB written
-    "transfer_fp32": {"src": "958df7db1476d091", "bytes": 77.5, "unit": "sample"},
+    "geodesic_df64": {"src": "c20dc1578110e077", "bytes": 147.9, "unit": "attempt"},
+    # fast form on cell-layout grids (record-count queue, no field test), 18,372,183 samples:
+    # 1.434 GB read + 0.006 GB written
+    "transfer_fp32": {"src": "c20dc1578110e077", "bytes": 78.4, "unit": "sample"},
 }
 
 

@@ -1,6 +1,7 @@
 // Kernels of the Blacklight hot path: camera frame, persistent geodesic kernel (FP64) and
 // persistent transfer kernel (FP64 or FP32). Included by bl_api.cu only.
 #pragma once
+#include <climits>
 #include <type_traits>
 
 #include "bl_df64.cuh"
@@ -1569,9 +1570,31 @@ __device__ __forceinline__ bool finite_bits(double x) {
     return (__double2hiint(x) & 0x7ff00000) != 0x7ff00000;
 }
 
+// Fused multiply-add in T, written out: the grid sums below fix their rounding in the source
+// (a sum of two products may otherwise be fused either way), so that both grid layouts and
+// every kernel variant produce the same bits.
+__device__ __forceinline__ float t_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double t_fma(double a, double b, double c) { return fma(a, b, c); }
+
+// The bit patterns of a cell's three magnetic-field components OR-ed together (values 5..7:
+// B^r, B^theta, B^phi); with the sign bit cleared it is zero exactly when the field is +-0.
+__device__ __forceinline__ unsigned int cell_field_bits(const float* __restrict__ prim, int layout,
+                                                        size_t plane, size_t cell) {
+    if (layout == 1) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(prim) + 2 * cell + 1);
+        return __float_as_uint(v.y) | __float_as_uint(v.z) | __float_as_uint(v.w);
+    }
+    return __float_as_uint(__ldg(prim + 5 * plane + cell)) |
+           __float_as_uint(__ldg(prim + 6 * plane + cell)) |
+           __float_as_uint(__ldg(prim + 7 * plane + cell));
+}
+
+// field_test: first read the stencil's magnetic field alone and return false (no plasma) when
+// every corner's field is zero -- exact (b = 0 fails the b^2 > 0 test below), and it skips the
+// interpolation and the plasma state at such samples.
 template <class T, bool kSlow = false>
 __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t,
-                                          const KSGeom<T>& G, Plasma<T>& P) {
+                                          const KSGeom<T>& G, Plasma<T>& P, bool field_test) {
     const T a = ic<T>(im, kcSpin);
     const T r = G.r;
     if (!(r >= ic<T>(im, kcRmin) && r <= ic<T>(im, kcRmax))) return false;
@@ -1623,6 +1646,13 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
         j = min(max(j, 0), nt - 1);
         k = ((k % np) + np) % np;
         const size_t base = ((size_t)k * nt + j) * nr + i;
+        // a cell without magnetic field holds no plasma (b = 0, below): its field
+        // components alone decide that
+        if (field_test) {
+            unsigned int fb = cell_field_bits(prim, im.layout, plane, base);
+            if (kSlow && prim1) fb |= cell_field_bits(prim1, im.layout, plane, base);
+            if ((fb & 0x7fffffffu) == 0u) return false;
+        }
         if (im.layout == 1) {
             float c[8];
             load_cell(prim, base, c);
@@ -1631,7 +1661,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
             if (kSlow && prim1) {
                 load_cell(prim1, base, c);
 #pragma unroll
-                for (int v = 0; v < 8; ++v) pv[v] = (T(1) - wt1) * pv[v] + wt1 * grid_val<T>(c[v]);
+                for (int v = 0; v < 8; ++v) pv[v] = t_fma(wt1, grid_val<T>(c[v]), (T(1) - wt1) * pv[v]);
             }
         } else {
 #pragma unroll
@@ -1639,7 +1669,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
             if (kSlow && prim1) {
 #pragma unroll
                 for (int v = 0; v < 8; ++v)
-                    pv[v] = (T(1) - wt1) * pv[v] + wt1 * grid_val<T>(__ldg(prim1 + v * plane + base));
+                    pv[v] = t_fma(wt1, grid_val<T>(__ldg(prim1 + v * plane + base)), (T(1) - wt1) * pv[v]);
             }
         }
     } else {
@@ -1673,6 +1703,19 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
         const T wp = fk - fkf;
         const size_t o00 = ((size_t)k0 * nt + j0) * nr, o01 = ((size_t)k0 * nt + j1) * nr;
         const size_t o10 = ((size_t)k1 * nt + j0) * nr, o11 = ((size_t)k1 * nt + j1) * nr;
+        // a stencil whose eight cells carry no magnetic field holds no plasma (b = 0, below):
+        // the field components alone decide that, before the interpolation
+        if (field_test) {
+            const size_t cell[8] = {o00 + i0, o00 + i1, o01 + i0, o01 + i1,
+                                    o10 + i0, o10 + i1, o11 + i0, o11 + i1};
+            unsigned int fb = 0u;
+#pragma unroll
+            for (int n = 0; n < 8; ++n) {
+                fb |= cell_field_bits(prim, im.layout, plane, cell[n]);
+                if (kSlow && prim1) fb |= cell_field_bits(prim1, im.layout, plane, cell[n]);
+            }
+            if ((fb & 0x7fffffffu) == 0u) return false;
+        }
         const T w000 = (T(1) - wp) * (T(1) - wt) * (T(1) - wr), w001 = (T(1) - wp) * (T(1) - wt) * wr;
         const T w010 = (T(1) - wp) * wt * (T(1) - wr), w011 = (T(1) - wp) * wt * wr;
         const T w100 = wp * (T(1) - wt) * (T(1) - wr), w101 = wp * (T(1) - wt) * wr;
@@ -1691,7 +1734,7 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
                 for (int n = 1; n < 8; ++n) {
                     load_cell(pp, cell[n], c);
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) out[v] = out[v] + w[n] * grid_val<T>(c[v]);
+                    for (int v = 0; v < 8; ++v) out[v] = t_fma(w[n], grid_val<T>(c[v]), out[v]);
                 }
             };
             tri8(prim, pv);
@@ -1699,21 +1742,27 @@ __device__ __forceinline__ bool plasma_at(const ImageDesc& im, const T x[3], T t
                 T pv1[8];
                 tri8(prim1, pv1);
 #pragma unroll
-                for (int v = 0; v < 8; ++v) pv[v] = (T(1) - wt1) * pv[v] + wt1 * pv1[v];
+                for (int v = 0; v < 8; ++v) pv[v] = t_fma(wt1, pv1[v], (T(1) - wt1) * pv[v]);
             }
         } else {
+            // accumulated one corner at a time with explicit fused multiply-adds, as the cell
+            // layout does: both layouts round alike
             auto tri = [&](const float* __restrict__ pp) -> T {
-                return w000 * grid_val<T>(__ldg(pp + o00 + i0)) + w001 * grid_val<T>(__ldg(pp + o00 + i1)) +
-                       w010 * grid_val<T>(__ldg(pp + o01 + i0)) + w011 * grid_val<T>(__ldg(pp + o01 + i1)) +
-                       w100 * grid_val<T>(__ldg(pp + o10 + i0)) + w101 * grid_val<T>(__ldg(pp + o10 + i1)) +
-                       w110 * grid_val<T>(__ldg(pp + o11 + i0)) + w111 * grid_val<T>(__ldg(pp + o11 + i1));
+                T acc = w000 * grid_val<T>(__ldg(pp + o00 + i0));
+                acc = t_fma(w001, grid_val<T>(__ldg(pp + o00 + i1)), acc);
+                acc = t_fma(w010, grid_val<T>(__ldg(pp + o01 + i0)), acc);
+                acc = t_fma(w011, grid_val<T>(__ldg(pp + o01 + i1)), acc);
+                acc = t_fma(w100, grid_val<T>(__ldg(pp + o10 + i0)), acc);
+                acc = t_fma(w101, grid_val<T>(__ldg(pp + o10 + i1)), acc);
+                acc = t_fma(w110, grid_val<T>(__ldg(pp + o11 + i0)), acc);
+                return t_fma(w111, grid_val<T>(__ldg(pp + o11 + i1)), acc);
             };
 #pragma unroll
             for (int v = 0; v < 8; ++v) pv[v] = tri(prim + v * plane);
             if (kSlow && prim1) {
 #pragma unroll
                 for (int v = 0; v < 8; ++v)
-                    pv[v] = (T(1) - wt1) * pv[v] + wt1 * tri(prim1 + v * plane);
+                    pv[v] = t_fma(wt1, tri(prim1 + v * plane), (T(1) - wt1) * pv[v]);
             }
         }
     }
@@ -2045,6 +2094,16 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
     constexpr bool kMlp = (kF & kFMlp) != 0;
     static_assert(!kMlp || std::is_same<R, float>::value, "the learned model needs FP32 records");
     constexpr bool kIdx = kMlp;   // the transfer needs each record's pool index
+    // the stencil field test of plasma_at: always in the FP64 form; in FP32 where the rays are
+    // not queued by record count -- that order predicts a ray's cost from its records, which
+    // stops holding once field-free records are cheap (nine 256^2 images, fast form: cell-layout
+    // grids in the record-count order 11.6 ms with the test switched off there, 13.3 with it on;
+    // plane-layout grids in the consecutive queue 18.9 ms with the test, 25.8 before it). A
+    // run-time switch in one kernel, so that both queue orders run the same arithmetic; FP32
+    // compiles it into the plain polarized and unpolarized variants only, which keeps the
+    // register budgets of the slow-light, auxiliary-image and learned variants.
+    constexpr bool kFieldTestable = sizeof(T) == sizeof(double) || (!kSlow && !kAux && !kMlp);
+    const bool field_test = kFieldTestable && (sizeof(T) == sizeof(double) || side.perm == nullptr);
     int64_t nxt_k = 0;
     const int64_t re = wave_end(bs, ray_end);
     const int64_t n_rays = re > ray_begin ? re - ray_begin : 0;
@@ -2177,7 +2236,7 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
             KSGeom<T> G;
             ks_geom<T>(xs[0], xs[1], xs[2], a, m, flat, false, G);
             Plasma<T> P;
-            if (plasma_at<T, kSlow>(im, xs, nxt_t, G, P)) {
+            if (plasma_at<T, kSlow>(im, xs, nxt_t, G, P, field_test)) {
                 const T kl[4] = {kt, cur[3], cur[4], cur[5]};
                 T ku[4];
                 raise4(G, kl, ku);
@@ -2227,11 +2286,15 @@ __device__ __forceinline__ void transfer_body(const ImageDesc* __restrict__ imgs
         --idx;
     }
 }
-// The transfer kernel: FP32 (mixed and fast forms) at up to 128 registers, 4 CTAs of 128
-// threads an SM; FP64 capped (BL_TR64_MAXNREG) in CTAs of 64 threads, which keeps more warps an
-// SM resident (the FP32 kernel is fastest uncapped).
+// The transfer kernel: FP32 (mixed and fast forms) in CTAs of 128 threads, the polarized and
+// unpolarized variants held to 4 CTAs an SM (128 registers; with the field test uncapped they
+// take 142 and 3 CTAs), the slow-light and auxiliary-image variants uncapped; FP64 capped
+// (BL_TR64_MAXNREG) in CTAs of 64 threads, which keeps more warps an SM resident.
+#ifndef BL_TR32_MIN_CTAS
+#define BL_TR32_MIN_CTAS 4
+#endif
 template <class T, class R, int kF>
-__global__ void __launch_bounds__(128) transfer_kernel(const ImageDesc* __restrict__ imgs,
+__global__ void __launch_bounds__(128, (kF & (kFSlow | kFAux)) ? 0 : BL_TR32_MIN_CTAS) transfer_kernel(const ImageDesc* __restrict__ imgs,
                                                        int n_images, int64_t ray_begin,
                                                        int64_t ray_end,
                                                        const RayHdr* __restrict__ hdr,
@@ -2299,6 +2362,83 @@ __global__ void __maxnreg__(BL_TR64_MAXNREG) transfer_kernel_fp64(const ImageDes
 #ifndef BL_PRE64_MIN_CTAS
 #define BL_PRE64_MIN_CTAS 16
 #endif
+// Cell index along one axis of the grid lookup (plasma_at) from a fractional coordinate u
+// (trilinear: u = cell coordinate - 1/2, the stencil's lower cell, clamped so that both cells
+// exist; nearest: u = cell coordinate, the cell, clamped).
+__device__ __forceinline__ int lookup_cell(float u, int n, bool tri) {
+    if (tri) {
+        if (n == 1) return 0;
+        u = fminf(fmaxf(u, 0.0f), (float)(n - 1));
+        const int i = (int)floorf(u);
+        return i > n - 2 ? n - 2 : i;
+    }
+    const int i = (int)floorf(u);
+    return min(max(i, 0), n - 1);
+}
+// The cell a coordinate known to within +-m maps to, or -1 when the interval straddles a
+// cell boundary (the map u -> cell is monotone, so equal ends fix every point between).
+__device__ __forceinline__ int certain_cell(float u, float m, int n, bool tri) {
+    const int lo = lookup_cell(u - m, n, tri), hi = lookup_cell(u + m, n, tri);
+    return lo == hi ? lo : -1;
+}
+__device__ __forceinline__ int certain_cell_periodic(float u, float m) {
+    const float lo = floorf(u - m), hi = floorf(u + m);
+    return lo == hi ? (int)lo : INT_MIN;
+}
+
+// Whether the grid lookup of a sample at this position (plasma_at, one snapshot) certainly
+// reads a stencil whose corners all carry zero magnetic field -- the sample then has b = 0
+// and no synchrotron plasma (plasma_at requires b^2 > 0), whatever else the cells hold. The
+// stencil is located in FP32 from the record's FP32 position: r^2 as the radial shell test
+// forms it, theta = atan2(sin, cos) with sin^2 = (x^2 + y^2) / (r^2 + a^2) and cos = z / r
+// (x^2 + y^2 = (r^2 + a^2) sin^2 theta in Cartesian Kerr-Schild), the azimuth as plasma_at
+// forms it. Each fractional coordinate carries a margin of 1e-3 cells plus four times a bound
+// on its FP32 error (the rounding of r^2 grows with (R^2 + a^2) / r^2, R^2 = x^2 + y^2 + z^2)
+// and the rounding of the FP32 scale factors;
+// a coordinate whose margin interval straddles a cell boundary, or a point within 1e-15 of
+// the axis, is reported as not certain (false: the FP64 lookup decides). A true answer is
+// exact: the FP64 lookup then reads the same stencil and returns no plasma.
+__device__ __forceinline__ bool stencil_field_free(const ImageDesc& im, float x, float y, float z,
+                                                   float r2, float aa) {
+    const float rho2 = x * x + y * y;
+    if (!(rho2 > 1e-30f)) return false;
+    const float R2 = rho2 + z * z;
+    const float eps = 3e-7f * (R2 + aa) / r2 + 2e-7f;
+    const float r = sqrtf(r2);
+    const float a = im.f_c[kcSpin];
+    const float th = atan2f(sqrtf(rho2 / (r2 + aa)), z / r);
+    float ph = atan2f(y * r - x * a, x * r + y * a);
+    const float twopi = 6.28318530717958648f;
+    if (ph < 0.0f) ph += twopi;
+    if (ph >= twopi) ph -= twopi;
+    const int nr = im.nr, nt = im.nt, np = im.nph;
+    const bool tri = im.interp != 0;
+    const float off = tri ? 0.5f : 0.0f;
+    const float idlr = im.f_c[kcIDlr];
+    const float idth = (float)nt * 0.318309886183790672f;
+    const float idph = (float)np * 0.159154943091895336f;
+    // margins: the coordinate's own FP32 error, and 4e-7 |u| for the FP32 scale factors
+    const float ur = (logf(r) - im.f_c[kcLogRmin]) * idlr - off;
+    const float ut = th * idth - off;
+    const float up = ph * idph - off;
+    const int i0 = certain_cell(ur, 1e-3f + idlr * (4.0f * eps + 1e-6f) + 4e-7f * fabsf(ur), nr, tri);
+    const int j0 = certain_cell(ut, 1e-3f + idth * (4.0f * eps + 1e-6f) + 4e-7f * fabsf(ut), nt, tri);
+    const int kf = certain_cell_periodic(up, 1e-3f + idph * (2.0f * eps + 1e-6f) + 4e-7f * fabsf(up));
+    if (i0 < 0 || j0 < 0 || kf == INT_MIN) return false;
+    const int k0 = ((kf % np) + np) % np;
+    const int i1 = (tri && nr > 1) ? i0 + 1 : i0, j1 = (tri && nt > 1) ? j0 + 1 : j0;
+    const int k1 = tri ? (k0 + 1) % np : k0;
+    const size_t plane = (size_t)np * nt * nr;
+    unsigned int bits = 0u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const size_t cell = ((size_t)((c & 4) ? k1 : k0) * nt + ((c & 2) ? j1 : j0)) * nr +
+                            ((c & 1) ? i1 : i0);
+        bits |= cell_field_bits(im.prim, im.layout, plane, cell);
+    }
+    return (bits & 0x7fffffffu) == 0u;   // +-0 in every field component of every corner
+}
+
 struct SampleItem {
     int64_t k;       // pool record
     int32_t wray;    // ray within the wave
@@ -2345,7 +2485,7 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
             KSGeom<T> G;
             ks_geom<T>(xs[0], xs[1], xs[2], a, m, flat, false, G);
             Plasma<T> P;
-            if (plasma_at<T, kSlow>(im, xs, cur[13], G, P)) {
+            if (plasma_at<T, kSlow>(im, xs, cur[13], G, P, true)) {
                 const T kl[4] = {kt, cur[3], cur[4], cur[5]};
                 T ku[4];
                 raise4(G, kl, ku);
@@ -2427,6 +2567,9 @@ __global__ void __launch_bounds__(128, BL_PRE64_MIN_CTAS) fp64_samples_kernel(co
                 const float qq = x * x + y * y + z * z - aa;
                 const float r2 = 0.5f * (qq + sqrtf(qq * qq + 4.0f * aa * z * z));
                 cand = r2 >= r2lo && r2 <= r2hi;
+                // a stencil without magnetic field holds no plasma (stencil_field_free);
+                // one snapshot only
+                if (!kSlow && cand) cand = !stencil_field_free(imgs[q], x, y, z, r2, aa);
                 if (!cand) pre_flag[k] = 0;
             }
             const unsigned mask = __ballot_sync(0xffffffffu, cand);
@@ -2653,7 +2796,7 @@ __global__ void __launch_bounds__(128) mlp_inputs_kernel(const ImageDesc* __rest
             ks_geom<T>(xs[0], xs[1], xs[2], a, m, flat, false, G);
             Plasma<T> P;
             uint2 row = make_uint2(0u, 0u);
-            if (plasma_at<T, kSlow>(im, xs, v[13], G, P)) {
+            if (plasma_at<T, kSlow>(im, xs, v[13], G, P, false)) {
                 const T kl[4] = {kt, v[3], v[4], v[5]};
                 const T kdu = kl[0] * P.u[0] + kl[1] * P.u[1] + kl[2] * P.u[2] + kl[3] * P.u[3];
                 const T kdb = kl[0] * P.b[0] + kl[1] * P.b[1] + kl[2] * P.b[2] + kl[3] * P.b[3];
