@@ -15,7 +15,8 @@ with its image error against the CPU oracle on a seeded pixel sample.
 Rooflines: achieved = algorithmic flops per launch / the kernel's CUDA-event time, against
 the device's own peak measured by blacklight_measure_peaks (FMA-chain probes for FP64, FP32
 and the double-float arithmetic), with the SM clock sampled while the probes run.
-  - geodesic kernel: FLOP64_PER_ATTEMPT per Dormand-Prince attempt (hand count below);
+  - geodesic kernel: FLOP64_PER_ATTEMPT per Dormand-Prince attempt (hand count below), and in
+    the FP64 form FLOP64_EMIT_PER_RECORD per sample record for its FP64 sample emission;
   - transfer kernel: FLOP_PER_SAMPLE per sample, the method's arithmetic per sample as the
     FP32 transfer kernel executes it with the stencil field test on (ncu thread-level FFMA x 2
     + FADD + FMUL per sample; its special functions are single hardware instructions, counted
@@ -55,6 +56,15 @@ GRID = (256, 128, 128)
 # reciprocal, with d_c(l.k) formed directly), 6 stage combinations (384), the embedded error
 # estimate (96) and its norm and the step control (50).
 FLOP64_PER_ATTEMPT = 1214
+# FP64 flops per sample record of the sample emission inside the geodesic kernel (Sec. 2.2's
+# sample points), a lower bound counted from the method as implemented, FP64 form only (the
+# other forms emit their records in FP32): an accepted step that is not subdivided costs 136
+# (Shampine midpoint 91 over the 7 varying components, geometry at the midpoint 35, L and
+# k^t 8, ds 2) for its one record; a step split into n sub-samples costs 242 + 108 n (the
+# midpoint and geometry, the quartic's coefficients 154, then a sample point 56, a node 48 and
+# 4 for its parameters and length a record, the first node being the step's start), i.e. at
+# least 108 a record.
+FLOP64_EMIT_PER_RECORD = 108
 # Arithmetic per transfer sample of the method (see the module docstring): FP32 flops and
 # special-function instructions of transfer_kernel<float, float, 0> per sample with the
 # stencil field test on (a sample whose lookup stencil carries no magnetic field stops after
@@ -368,11 +378,19 @@ def form_rooflines(prec_name, attempts, samples, geo_s, tr_s, peaks):
                 + (f", median SM clock {mhz:.0f} MHz during the probes)" if mhz else ")"))
     geo_kind = {"fp64": "fp64", "mixed": "fp64", "fast": "df64"}[prec_name]
     tr_kind = "fp64" if prec_name == "fp64" else "fp32"
+    geo_flops, geo_note = FLOP64_PER_ATTEMPT, None
+    if prec_name == "fp64" and attempts > 0:
+        # the FP64 form's sample emission (FP64 records) is part of the kernel's method work
+        geo_flops = FLOP64_PER_ATTEMPT + FLOP64_EMIT_PER_RECORD * samples / attempts
+        geo_note = (f"algorithmic flops: {FLOP64_PER_ATTEMPT} a Dormand-Prince attempt plus at "
+                    f"least {FLOP64_EMIT_PER_RECORD} a sample record of the FP64 sample emission "
+                    f"({samples} records for {attempts} attempts)")
     geo = roofline({"fp64": "geodesic_kernel_fp64",
                     "mixed": "geodesic_kernel<float, double>",
                     "fast": "geodesic_kernel<float, df64>"}[prec_name],
-                   FLOP64_PER_ATTEMPT, attempts, "DP attempt", geo_s, pk(geo_kind),
-                   traffic_key={"fp64": "geodesic_fp64", "fast": "geodesic_df64"}.get(prec_name))
+                   geo_flops, attempts, "DP attempt", geo_s, pk(geo_kind),
+                   traffic_key={"fp64": "geodesic_fp64", "fast": "geodesic_df64"}.get(prec_name),
+                   note=geo_note)
     tr = roofline("transfer phase: fp64_samples_kernel + transport_fp64_kernel"
                   if prec_name == "fp64" else "transfer_kernel<float, float, 0>",
                   FLOP_PER_SAMPLE, samples, "transfer sample", tr_s, pk(tr_kind),
