@@ -762,8 +762,12 @@ def measure_hires(torch, native, images, code, device, steps=3, warmup=2, coef_m
     p, gpd = device_grid(torch, prim, gp, device)
     host = (cam, met, gp, prim) if keep_host else None
     del prim
-    ws = torch.empty(native.blacklight_workspace_size([cam], [met]), dtype=torch.uint8,
-                     device=device)
+    # the learned model's outputs need room beyond blacklight_workspace_size (8 floats a pool
+    # record): that line lets the library size its scratch (one wave, from the stream-ordered
+    # memory pool, which keeps it between calls)
+    ws = (None if coef_mlp is not None else
+          torch.empty(native.blacklight_workspace_size([cam], [met]), dtype=torch.uint8,
+                      device=device))
     dt = torch.float64 if code == native.BL_PREC_FP64 else torch.float32
     out = images.alloc_outputs(cam.n, dt, device=device)
     for _ in range(warmup):
