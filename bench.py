@@ -764,10 +764,12 @@ def measure_hires(torch, native, images, code, device, steps=3, warmup=2, coef_m
     del prim
     # the learned model's outputs need room beyond blacklight_workspace_size (8 floats a pool
     # record): that line lets the library size its scratch (one wave, from the stream-ordered
-    # memory pool, which keeps it between calls)
+    # memory pool, told to keep it between calls as the end-to-end line does)
     ws = (None if coef_mlp is not None else
           torch.empty(native.blacklight_workspace_size([cam], [met]), dtype=torch.uint8,
                       device=device))
+    if ws is None:
+        native.blacklight_set_memory_retention(2 ** 64 - 1)
     dt = torch.float64 if code == native.BL_PREC_FP64 else torch.float32
     out = images.alloc_outputs(cam.n, dt, device=device)
     for _ in range(warmup):
@@ -787,6 +789,8 @@ def measure_hires(torch, native, images, code, device, steps=3, warmup=2, coef_m
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    if ws is None:
+        native.blacklight_set_memory_retention(0)
     bad = int(((out["status"] != 1) & (out["status"] != 2)).sum())
     del ws, p
     torch.cuda.empty_cache()
