@@ -2,11 +2,11 @@
 b = 0 and no synchrotron plasma, so the library skips its interpolation and plasma state (the
 FP64 sample pass decides it in FP32 from the record's position with a margin on every axis).
 The skip must be exact. Here the torus keeps its field only in alternating 2x2x2 blocks of
-cells, so that a large share of the samples lie on stencils that straddle a field / no-field
-boundary: the FP64 image must still match the oracle to the full-size bound (a wrongly skipped
-emitting sample moves a pixel by far more), and the FP32 transfer with the test (plane-layout
-grid, consecutive queue) must equal the one without it (cell layout, record-count queue) bit
-for bit."""
+cells (shifted from snapshot to snapshot in a slow-light series), so that a large share of the
+samples lie on stencils that straddle a field / no-field boundary: the FP64 image must still
+match the oracle to the full-size bound (a wrongly skipped emitting sample moves a pixel by far
+more), and the FP32 transfer with the test (plane-layout grid, consecutive queue) must equal
+the one without it (cell layout, record-count queue) bit for bit."""
 import dataclasses
 
 import numpy as np
@@ -22,19 +22,27 @@ DEV = "cuda"
 FREQ = 230e9
 
 
+def _blocky(workload, spin, inc):
+    """The workload's torus with its field kept only in alternating 2x2x2 blocks of cells (in a
+    snapshot series, the blocks shift by one block from snapshot to snapshot)."""
+    cam, met, gp, prim = S.workload_inputs(workload, spin, inc, n=48)
+    prim = np.array(prim, copy=True)
+    k, j, i = np.meshgrid(np.arange(gp.n_phi), np.arange(gp.n_theta), np.arange(gp.n_r),
+                          indexing="ij")
+    snaps = prim if prim.ndim == 5 else prim[None]
+    for s_ in range(snaps.shape[0]):
+        keep = ((i // 2 + j // 2 + k // 2 + s_) % 2 == 0).astype(np.float32)
+        for v in (5, 6, 7):
+            snaps[s_, v] *= keep
+    return cam, met, gp, prim
+
+
 @pytest.fixture(scope="module")
 def blocky():
     native.build()
     native.load()
     O.build()
-    cam, met, gp, prim = S.workload_inputs("torus64_cam32", 0.9, 60.0, n=48)
-    prim = np.array(prim, copy=True)
-    k, j, i = np.meshgrid(np.arange(gp.n_phi), np.arange(gp.n_theta), np.arange(gp.n_r),
-                          indexing="ij")
-    keep = ((i // 2 + j // 2 + k // 2) % 2 == 0).astype(np.float32)
-    for v in (5, 6, 7):
-        prim[v] *= keep
-    return cam, met, gp, prim
+    return _blocky("torus64_cam32", 0.9, 60.0)
 
 
 def _trace(cam, met, gp, prim_dev, dtype):
@@ -45,9 +53,14 @@ def _trace(cam, met, gp, prim_dev, dtype):
     return out
 
 
-@pytest.mark.parametrize("layout", ["planes", "cells"])
-def test_fp64_image_with_blocky_field_matches_oracle(blocky, layout):
-    cam, met, gp, prim = blocky
+@pytest.mark.parametrize("layout,interp,slow", [("planes", 1, False), ("cells", 1, False),
+                                                 ("cells", 0, False), ("cells", 1, True),
+                                                 ("planes", 0, True)])
+def test_fp64_image_with_blocky_field_matches_oracle(blocky, layout, interp, slow):
+    """Trilinear and nearest lookup, one snapshot and a slow-light series (the stencil must be
+    field-free in both snapshots a sample interpolates between)."""
+    cam, met, gp, prim = _blocky("torus64_slow4_cam32", 0.9, 60.0) if slow else blocky
+    gp = dataclasses.replace(gp, interp=interp)
     met = dataclasses.replace(met, precision=native.BL_PREC_FP64)
     p = torch.from_numpy(prim).to(DEV)
     g = gp
